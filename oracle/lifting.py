@@ -1,0 +1,246 @@
+"""CNN lifting wavelet transform, FP64 (test infrastructure only).
+
+Follows Section 3.1 and Fig. 2 of the paper: a 1-D lifting step splits a
+signal into even and odd samples, predicts the odd samples from the even ones
+(HP = odd - P(even)) and updates the even samples from the highpass
+(LP = even + U(HP)); the inverse runs the same two steps backwards, so it
+reconstructs perfectly for any P and U. A 2-D level applies the 1-D step
+along rows first, then along columns. P and U are "residual CNN modules": a
+fixed linear lifting filter plus a trainable CNN residual. With integer
+rounding of the P and U outputs the transform maps integers to integers and
+is losslessly invertible (the Fig. 2 caption).
+
+Readings (the paper defers the filter details to its references):
+* linear parts are the LeGall 5/3 filters: P_lin(e)[n] = (e[n] + e[n+1]) / 2
+  and U_lin(h)[n] = (h[n-1] + h[n]) / 4, with whole-sample symmetric
+  extension at both ends (e[N] = e[N-1], h[-1] = h[0]);
+* the CNN residual is conv3x3(1->F), tanh, conv3x3(F->F), tanh,
+  conv3x3(F->1), zero padding, applied to the 2-D array of even samples (for
+  P) or of highpass samples (for U); one net per direction and operator,
+  shared by all levels;
+* integer mode takes floor(P) and floor(U + 1/2), decided in FP32, so
+  that with the CNN residuals at zero it is exactly the reversible 5/3
+  lifting of JPEG 2000.
+
+Pins: perfect reconstruction for random weights, the exact integer round
+trip, the LeGall 5/3 integer lifting of JPEG 2000 (CNN residual zero) checked
+against a direct textbook formula, and the 2-D Haar basis functions for the
+Haar special case (tests/test_oracle_lifting.py).
+
+The temporal transform (Section 3.3) is the same lifting idea along the
+frame axis with identity motion: H = f_odd - P_t(f_even) and
+L = f_even + U_t(H) with P_t(v) = v + CNN(v) and U_t(v) = v / 2 + CNN(v)
+(Haar linear parts; motion compensation is not modelled).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def conv2d(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Cross-correlation with zero padding ('same' size).
+
+    x: [H, W, Cin], w: [Cout, Cin, kh, kw], b: [Cout] -> [H, W, Cout];
+    out[y, x, o] = b[o] + sum_{i,dy,dx} w[o, i, dy, dx] x[y+dy-kh//2, x+dx-kw//2, i].
+    """
+    H, W, Cin = x.shape
+    Cout, Cin2, kh, kw = w.shape
+    assert Cin == Cin2
+    ph, pw = kh // 2, kw // 2
+    xp = np.zeros((H + 2 * ph, W + 2 * pw, Cin))
+    xp[ph:ph + H, pw:pw + W, :] = x
+    out = np.empty((H, W, Cout))
+    out[...] = b
+    for dy in range(kh):
+        for dx in range(kw):
+            out += xp[dy:dy + H, dx:dx + W, :] @ w[:, :, dy, dx].T
+    return out
+
+
+def lift_cnn(v: np.ndarray, net: dict) -> np.ndarray:
+    """CNN residual of a predict/update filter on a 2-D array v -> same shape."""
+    t = np.tanh(conv2d(v[:, :, None], net["w1"], net["b1"]))
+    t = np.tanh(conv2d(t, net["w2"], net["b2"]))
+    return conv2d(t, net["w3"], net["b3"])[:, :, 0]
+
+
+def net_of(tensors: dict, prefix: str) -> dict:
+    return {k: tensors[prefix + k] for k in ("w1", "b1", "w2", "b2", "w3", "b3")}
+
+
+def _shift(a: np.ndarray, axis: int, delta: int) -> np.ndarray:
+    """a[n + delta] along `axis`, clamped to the valid index range."""
+    n = a.shape[axis]
+    idx = np.clip(np.arange(n) + delta, 0, n - 1)
+    return np.take(a, idx, axis=axis)
+
+
+def round_int(v: np.ndarray, half: float) -> np.ndarray:
+    """floor(v + half) with the decision taken in FP32 (the kernels'
+    precision; the paper fixes none), returned as FP64 integers."""
+    f32 = np.float32
+    return np.floor((v.astype(f32) + f32(half)).astype(f32)).astype(np.float64)
+
+
+def predict(e: np.ndarray, axis: int, net: dict | None, lossless: bool,
+            linear: str = "53") -> np.ndarray:
+    """P(e) = (e[n] + e[n+1]) / 2 + CNN_P(e); floor(P) in integer mode.
+
+    linear="haar" replaces the linear part by P_lin(e)[n] = e[n].
+    """
+    v = e.copy() if linear == "haar" else 0.5 * (e + _shift(e, axis, +1))
+    if net is not None:
+        v = v + lift_cnn(e, net)
+    return round_int(v, 0.0) if lossless else v
+
+
+def update(h: np.ndarray, axis: int, net: dict | None, lossless: bool,
+           linear: str = "53") -> np.ndarray:
+    """U(h) = (h[n-1] + h[n]) / 4 + CNN_U(h); floor(U + 1/2) in integer mode.
+
+    linear="haar" replaces the linear part by U_lin(h)[n] = h[n] / 2.
+    """
+    v = 0.5 * h if linear == "haar" else 0.25 * (_shift(h, axis, -1) + h)
+    if net is not None:
+        v = v + lift_cnn(h, net)
+    return round_int(v, 0.5) if lossless else v
+
+
+def lift_fwd(x: np.ndarray, axis: int, netP, netU, lossless: bool,
+             linear: str = "53"):
+    """One 1-D forward lifting step along `axis`: returns (LP, HP)."""
+    n = x.shape[axis]
+    assert n % 2 == 0
+    e = np.take(x, np.arange(0, n, 2), axis=axis)
+    o = np.take(x, np.arange(1, n, 2), axis=axis)
+    hp = o - predict(e, axis, netP, lossless, linear)
+    lp = e + update(hp, axis, netU, lossless, linear)
+    return lp, hp
+
+
+def lift_inv(lp: np.ndarray, hp: np.ndarray, axis: int, netP, netU,
+             lossless: bool, linear: str = "53"):
+    """Inverse of lift_fwd: undo the update, undo the predict, merge."""
+    e = lp - update(hp, axis, netU, lossless, linear)
+    o = hp + predict(e, axis, netP, lossless, linear)
+    shape = list(e.shape)
+    shape[axis] *= 2
+    x = np.empty(shape)
+    sl_e = [slice(None)] * x.ndim
+    sl_o = [slice(None)] * x.ndim
+    sl_e[axis] = slice(0, None, 2)
+    sl_o[axis] = slice(1, None, 2)
+    x[tuple(sl_e)] = e
+    x[tuple(sl_o)] = o
+    return x
+
+
+class Lifting:
+    """The four predict/update nets of the 2-D lifting transform."""
+
+    def __init__(self, tensors: dict | None, linear: str = "53"):
+        self.linear = linear
+        if tensors is None:
+            self.rP = self.rU = self.cP = self.cU = None
+        else:
+            self.rP = net_of(tensors, "lift.row.P.")
+            self.rU = net_of(tensors, "lift.row.U.")
+            self.cP = net_of(tensors, "lift.col.P.")
+            self.cU = net_of(tensors, "lift.col.U.")
+
+    def fwd_level(self, x: np.ndarray, lossless: bool):
+        """One 2-D level: rows first, then columns -> (LL, HL, LH, HH).
+
+        HL is the row-highpass / column-lowpass band, LH the row-lowpass /
+        column-highpass band.
+        """
+        a = self.linear
+        lo, hi = lift_fwd(x, 1, self.rP, self.rU, lossless, a)
+        LL, LH = lift_fwd(lo, 0, self.cP, self.cU, lossless, a)
+        HL, HH = lift_fwd(hi, 0, self.cP, self.cU, lossless, a)
+        return LL, HL, LH, HH
+
+    def inv_level(self, LL, HL, LH, HH, lossless: bool) -> np.ndarray:
+        """Inverse of fwd_level: columns first, then rows."""
+        a = self.linear
+        lo = lift_inv(LL, LH, 0, self.cP, self.cU, lossless, a)
+        hi = lift_inv(HL, HH, 0, self.cP, self.cU, lossless, a)
+        return lift_inv(lo, hi, 1, self.rP, self.rU, lossless, a)
+
+    def forward(self, x: np.ndarray, levels: int, lossless: bool):
+        """Multi-level DWT; returns subbands in coding order.
+
+        Order (Fig. 1 red arrows): LL_L, HL_L, LH_L, HH_L, HL_{L-1}, ...,
+        HH_1, i.e. 3 * levels + 1 subbands.
+        """
+        details = []
+        cur = x
+        for _ in range(levels):
+            cur, HL, LH, HH = self.fwd_level(cur, lossless)
+            details.append((HL, LH, HH))
+        out = [cur]
+        for HL, LH, HH in reversed(details):
+            out += [HL, LH, HH]
+        return out
+
+    def inverse(self, sb: list, levels: int, lossless: bool) -> np.ndarray:
+        """Inverse of forward (subbands in coding order)."""
+        cur = sb[0]
+        for lv in range(levels):
+            HL, LH, HH = sb[1 + 3 * lv: 4 + 3 * lv]
+            cur = self.inv_level(cur, HL, LH, HH, lossless)
+        return cur
+
+
+def subband_shapes(h: int, w: int, levels: int):
+    """(height, width, level) of each subband in coding order."""
+    out = [(h >> levels, w >> levels, levels)]
+    for lv in range(levels, 0, -1):
+        out += [(h >> lv, w >> lv, lv)] * 3
+    return out
+
+
+def _tnet(tensors, op):
+    return net_of(tensors, f"tlift.{op}.")
+
+
+def temporal_forward(frames: list, tensors: dict, tlevels: int):
+    """Temporal lifting over a GOP of 2^tlevels frames (identity motion).
+
+    Returns the temporal subbands in order [L_T, H_T, H_{T-1}..., H_1], the
+    H bands of each level in frame order.
+    """
+    nP, nU = _tnet(tensors, "P"), _tnet(tensors, "U")
+    cur = list(frames)
+    highs = []
+    for _ in range(tlevels):
+        lows, hs = [], []
+        for m in range(len(cur) // 2):
+            fe, fo = cur[2 * m], cur[2 * m + 1]
+            h = fo - (fe + lift_cnn(fe, nP))
+            l = fe + (0.5 * h + lift_cnn(h, nU))
+            lows.append(l)
+            hs.append(h)
+        highs.append(hs)
+        cur = lows
+    out = list(cur)
+    for hs in reversed(highs):
+        out += hs
+    return out
+
+
+def temporal_inverse(bands: list, tensors: dict, tlevels: int):
+    """Inverse of temporal_forward."""
+    nP, nU = _tnet(tensors, "P"), _tnet(tensors, "U")
+    cur = [bands[0]]
+    pos = 1
+    for _ in range(tlevels):
+        hs = bands[pos:pos + len(cur)]
+        pos += len(cur)
+        nxt = []
+        for l, h in zip(cur, hs):
+            fe = l - (0.5 * h + lift_cnn(h, nU))
+            fo = h + (fe + lift_cnn(fe, nP))
+            nxt += [fe, fo]
+        cur = nxt
+    return cur

@@ -1,0 +1,79 @@
+"""Pins of the oracle codec: coefficients survive the entropy coder exactly,
+lossless mode is exact, fine quantisation approaches perfect reconstruction,
+and the container rejects streams of another model or corrupted payloads."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import codec as K
+
+
+def _blob(ll_mode=0, C=8, levels=4, seed=0):
+    cfg = S.ModelConfig(levels=levels, C=C, ll_mode=ll_mode)
+    return S.pack_blob(cfg, S.random_model(cfg, seed))
+
+
+@pytest.mark.parametrize("ll_mode", [0, 1])
+def test_symbols_roundtrip_exactly(ll_mode):
+    blob = _blob(ll_mode)
+    model = K.Model(blob)
+    img = S.gray_sinusoids(40, 56, seed=1)          # padded to 48 x 64
+    planes, colour = K.colour_forward(img, False, 8)
+    planes = [K.pad_plane(p, 16) for p in planes]
+    bs, qenc = K.encode_planes(model, planes, width=56, height=40, bitdepth=8,
+                               colour=colour, q=8.0, chunk=64)
+    hd, qdec = K.decode_symbols(model, bs)
+    for a, b in zip(qenc[0], qdec[0]):
+        assert np.array_equal(a, b)
+    assert hd["n_chunks"] > 13 * 4                   # chunking exercised
+
+
+def test_lossless_rgb_exact_12bit():
+    blob = _blob(0, levels=5)
+    img = S.lossless_blobs(40, 72, seed=3)
+    bs = K.encode_image(blob, img, lossless=True, bitdepth=12)
+    out = K.decode_image(blob, bs)
+    assert out.dtype == np.uint16
+    assert np.array_equal(out, img)
+
+
+def test_fine_quantiser_nearly_perfect():
+    blob = _blob(0)
+    img = S.rgb_natural(32, 48, seed=4)
+    bs = K.encode_image(blob, img, q=1.0 / 64.0)
+    out = K.decode_image(blob, bs)
+    assert np.max(np.abs(out.astype(int) - img.astype(int))) <= 1
+
+
+def test_psnr_falls_with_coarser_quantiser():
+    blob = _blob(0)
+    img = S.gray_sinusoids(64, 64, seed=5)
+    ps = []
+    for q in (4.0, 16.0):
+        out = K.decode_image(blob, K.encode_image(blob, img, q=q))
+        mse = np.mean((out.astype(float) - img) ** 2)
+        ps.append(10 * np.log10(255 ** 2 / mse))
+    assert ps[0] > ps[1] > 20.0
+
+
+def test_wrong_model_and_corruption_rejected():
+    blob = _blob(0)
+    other = _blob(0, seed=1)
+    img = S.gray_sinusoids(32, 32, seed=6)
+    bs = K.encode_image(blob, img, q=8.0)
+    with pytest.raises(ValueError):
+        K.decode_image(other, bs)
+    bad = bytearray(bs)
+    bad[-3] ^= 0x5A
+    with pytest.raises(ValueError):
+        K.decode_image(blob, bytes(bad))
+
+
+def test_gop_roundtrip_close():
+    bl = _blob(0, seed=2)
+    bh = _blob(0, seed=3)
+    frames = S.video_gop(32, 48, 8, seed=7)
+    gs = K.encode_gop(bl, bh, frames, q=1.0 / 32.0)
+    out = K.decode_gop(bl, bh, gs)
+    assert out.shape == frames.shape
+    assert np.max(np.abs(out.astype(int) - frames.astype(int))) <= 1

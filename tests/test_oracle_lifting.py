@@ -1,0 +1,160 @@
+"""Pins of the oracle's lifting transform (Section 3.1, Fig. 2, Section 3.4).
+
+Each test checks the oracle against something other than itself: the
+perfect-reconstruction property the lifting structure guarantees for any
+P/U, the JPEG 2000 reversible 5/3 transform written out from its textbook
+definition, the LeGall 5/3 synthesis filters, the closed-form 2-D Haar basis
+functions (the subband impulse responses of Section 3.4 for a Haar linear
+part), and scipy's 2-D correlation for the CNN convolutions.
+"""
+import numpy as np
+import pytest
+from scipy.signal import correlate2d
+
+import synthetic as S
+from oracle import lifting as LF
+
+
+def _model(levels=4, seed=0):
+    cfg = S.ModelConfig(levels=levels, C=8)
+    return S.random_model(cfg, seed)
+
+
+def test_conv2d_matches_scipy_correlation():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(9, 13, 3))
+    w = rng.normal(size=(2, 3, 3, 3))
+    b = rng.normal(size=2)
+    out = LF.conv2d(x, w, b)
+    for o in range(2):
+        ref = b[o] + sum(correlate2d(x[:, :, i], w[o, i], mode="same",
+                                     boundary="fill") for i in range(3))
+        np.testing.assert_allclose(out[:, :, o], ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("levels,shape", [(4, (64, 48)), (5, (96, 64)), (1, (6, 10))])
+def test_float_perfect_reconstruction_any_weights(levels, shape):
+    t = _model(levels, seed=3)
+    lift = LF.Lifting(t)
+    x = np.random.default_rng(1).uniform(-128, 127, shape)
+    sb = lift.forward(x, levels, lossless=False)
+    y = lift.inverse(sb, levels, lossless=False)
+    assert np.max(np.abs(y - x)) < 1e-9
+
+
+def test_integer_lifting_exact_roundtrip_12bit_5_levels():
+    t = _model(5, seed=4)
+    lift = LF.Lifting(t)
+    x = np.random.default_rng(2).integers(0, 4096, (64, 96)).astype(np.float64) - 2048
+    sb = lift.forward(x, 5, lossless=True)
+    for s in sb:
+        assert np.all(s == np.round(s))
+    y = lift.inverse(sb, 5, lossless=True)
+    assert np.array_equal(y, x)
+
+
+def _jpeg2000_53_rows(x):
+    """Reversible 5/3 of ITU-T T.800 along axis 1, from its definition:
+    d[n] = x[2n+1] - floor((x[2n] + x[2n+2]) / 2),
+    s[n] = x[2n] + floor((d[n-1] + d[n] + 2) / 4), symmetric extension."""
+    H, W = x.shape
+    N = W // 2
+    xi = x.astype(np.int64)
+    d = np.zeros((H, N), dtype=np.int64)
+    s = np.zeros((H, N), dtype=np.int64)
+    for n in range(N):
+        right = xi[:, 2 * n + 2] if 2 * n + 2 < W else xi[:, 2 * n]   # x[W] = x[W-2]
+        d[:, n] = xi[:, 2 * n + 1] - np.floor_divide(xi[:, 2 * n] + right, 2)
+    for n in range(N):
+        left = d[:, n - 1] if n > 0 else d[:, 0]                     # d[-1] = d[0]
+        s[:, n] = xi[:, 2 * n] + np.floor_divide(left + d[:, n] + 2, 4)
+    return s, d
+
+
+def test_integer_mode_without_cnn_is_jpeg2000_reversible_53():
+    x = np.random.default_rng(5).integers(-2048, 2048, (6, 20)).astype(np.float64)
+    lp, hp = LF.lift_fwd(x, 1, None, None, lossless=True)
+    s, d = _jpeg2000_53_rows(x)
+    assert np.array_equal(lp, s)
+    assert np.array_equal(hp, d)
+    lp0, hp0 = LF.lift_fwd(x.T, 0, None, None, lossless=True)
+    assert np.array_equal(lp0.T, s) and np.array_equal(hp0.T, d)
+
+
+def test_float_53_synthesis_filters():
+    """Inverse 1-D step without CNN: the LeGall 5/3 synthesis filters
+    g0 = [1/2, 1, 1/2] and g1 = [-1/8, -1/4, 3/4, -1/4, -1/8]."""
+    N = 8
+    lp = np.zeros((1, N)); hp = np.zeros((1, N))
+    lp[0, 3] = 1.0
+    x = LF.lift_inv(lp, hp, 1, None, None, lossless=False)[0]
+    ref = np.zeros(2 * N); ref[5:8] = [0.5, 1.0, 0.5]
+    np.testing.assert_allclose(x, ref, atol=0)
+    lp[:] = 0; hp[0, 3] = 1.0
+    x = LF.lift_inv(lp, hp, 1, None, None, lossless=False)[0]
+    ref = np.zeros(2 * N); ref[5:10] = [-0.125, -0.25, 0.75, -0.25, -0.125]
+    np.testing.assert_allclose(x, ref, atol=0)
+
+
+def _haar_1d(kind, level, n):
+    """Closed-form 1-D Haar synthesis function of the lifting pair
+    L = (e + o) / 2, H = o - e at `level` (support 2^level)."""
+    f = np.zeros(n)
+    s = 1 << level
+    if kind == "L":
+        f[:s] = 1.0
+    else:
+        f[:s // 2] = -0.5
+        f[s // 2:s] = 0.5
+    return f
+
+
+def test_subband_impulse_responses_are_haar_basis_functions():
+    """Section 3.4: an impulse placed in each of the 13 subbands of an
+    all-zero 16x16 latent (4 levels, level-4 subbands 1x1) and inverse
+    transformed; with a Haar linear part and no CNN residual the responses
+    are the 2-D Haar basis functions (outer product of the column and row
+    synthesis functions)."""
+    levels = 4
+    lift = LF.Lifting(None, linear="haar")
+    shapes = LF.subband_shapes(16, 16, levels)
+    assert len(shapes) == 13 and shapes[0][:2] == (1, 1)
+    names = ["LL"] + ["HL", "LH", "HH"] * levels
+    for i, (h, w, lv) in enumerate(shapes):
+        sb = [np.zeros((hh, ww)) for hh, ww, _ in shapes]
+        sb[i][0, 0] = 7.0
+        x = lift.inverse(sb, levels, lossless=False)
+        nm = names[i]
+        row_kind = "H" if nm in ("HL", "HH") else "L"   # HL: row highpass
+        col_kind = "H" if nm in ("LH", "HH") else "L"
+        ref = 7.0 * np.outer(_haar_1d(col_kind, lv, 16), _haar_1d(row_kind, lv, 16))
+        np.testing.assert_allclose(x, ref, atol=1e-12, err_msg=f"subband {i} {nm}{lv}")
+
+
+def test_subband_geometry():
+    shapes = LF.subband_shapes(512, 768, 4)
+    assert len(shapes) == 13
+    assert shapes[0] == (32, 48, 4)
+    assert [s[2] for s in shapes] == [4, 4, 4, 4, 3, 3, 3, 2, 2, 2, 1, 1, 1]
+    assert sum(h * w for h, w, _ in shapes) == 512 * 768
+    shapes5 = LF.subband_shapes(2176, 3840, 5)
+    assert len(shapes5) == 16 and shapes5[0][:2] == (68, 120)
+
+
+def test_forward_coefficient_count_and_order():
+    t = _model(4, seed=6)
+    lift = LF.Lifting(t)
+    x = np.random.default_rng(7).uniform(-100, 100, (32, 48))
+    sb = lift.forward(x, 4, lossless=False)
+    assert [s.shape for s in sb] == [(h, w) for h, w, _ in LF.subband_shapes(32, 48, 4)]
+
+
+def test_temporal_lifting_perfect_reconstruction():
+    t = _model(4, seed=8)
+    rng = np.random.default_rng(9)
+    frames = [rng.uniform(-128, 127, (16, 24)) for _ in range(8)]
+    bands = LF.temporal_forward(frames, t, 3)
+    assert len(bands) == 8
+    back = LF.temporal_inverse(bands, t, 3)
+    for a, b in zip(frames, back):
+        assert np.max(np.abs(a - b)) < 1e-9
