@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Decode benchmark of the pWave++ path on GB300.
+
+Metric: decoded MPix/s and p50/p99 decode latency. Workload (the batched
+image configuration): a batch of 24 synthetic RGB 768x512 images (gradient +
+rectangles + 1/f texture), 4-level CNN lifting, context model with 64
+channels and the four-step LL model, quantiser steps {4, 8, 16, 32} (six
+images each), random-init weights (seed 0). One step = one batched decode of
+the 24 streams: stream parsing, CDF table bank, ConvLSTM + four-step context
+passes with rANS decoding for all 13 subbands, dequantisation, inverse
+lifting and colour conversion.
+
+value: device-resident streams -> device images, CUDA events on the
+library's stream, L2 flushed (256 MB write) between timed steps (outside the
+events). e2e: the same decode through the C ABI from host streams to host
+images, host wall clock around each call. roofline: the dominant kernel class
+from the library's own CUDA-event timing. cpu_baseline: the CPU oracle
+decoding a bounded sample (one 256x256 RGB crop of the workload).
+
+With --impl reference the CPU oracle is timed instead (each step decodes one
+128x128 RGB crop of the workload) and one JSON line with "impl": "reference"
+is printed. Multi-GPU (torchrun, N > 1): every rank decodes its own batch
+(replicas, weak scaling); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BATCH = 24
+H, W = 512, 768
+QSTEPS = (4.0, 8.0, 16.0, 32.0)
+WORKLOAD = "batch of 24 RGB 768x512 images, 4-level CNN lifting, 64-ch four-step context model, q in {4,8,16,32}"
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_inputs(seed_base: int):
+    import synthetic as S
+    imgs = [S.rgb_natural(H, W, seed=seed_base + i) for i in range(BATCH)]
+    qs = [QSTEPS[i % 4] for i in range(BATCH)]
+    return imgs, qs
+
+
+def model_blob():
+    import synthetic as S
+    cfg = S.ModelConfig(levels=4, C=64, F=16, ll_mode=0)
+    return S.pack_blob(cfg, S.random_model(cfg, 0))
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                pass
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_decode_sample(crop: int):
+    """Time the CPU oracle decoding one crop x crop RGB image of the workload."""
+    import synthetic as S
+    from oracle import codec as K
+    blob = model_blob()
+    img = S.rgb_natural(H, W, seed=1)[:crop, :crop]
+    bs = K.encode_image(blob, img, q=8.0)
+    t0 = time.perf_counter()
+    K.decode_image(blob, bs)
+    dt = time.perf_counter() - t0
+    return crop * crop, dt
+
+
+def blas_threads() -> int:
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads", 0) for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    crop = 128
+    for _ in range(args.warmup):
+        cpu_oracle_decode_sample(crop)
+    times = []
+    for _ in range(args.steps):
+        px, dt = cpu_oracle_decode_sample(crop)
+        times.append(dt)
+    total = sum(times)
+    value = px * len(times) / total / 1e6
+    cores = blas_threads()
+    line = {
+        "impl": "reference", "metric": "decoded MPix/s", "value": value, "unit": "MPix/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": BATCH, "precision": "fp64 oracle",
+                   "sample": f"one {crop}x{crop} RGB crop per step"},
+        "cpu_baseline": {"value": value, "unit": "MPix/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{crop}x{crop} RGB crop of image 1, q=8, decode only"},
+        "e2e": {"value": value, "unit": "MPix/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)),
+                       "p99": 1e3 * float(np.percentile(times, 99))},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_info()
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2405_12631_gb300 as pw
+
+    stream = torch.cuda.current_stream(dev)
+    codec = pw.Codec(local, args.precision, stream=stream.cuda_stream)
+    blob = model_blob()
+    model = codec.load_model(blob)
+    imgs, qs = make_inputs(1 + 1000 * rank)
+    streams = []
+    for q in QSTEPS:
+        idx = [i for i in range(BATCH) if qs[i] == q]
+        enc = codec.encode_batch(model, [imgs[i] for i in idx], q=q)
+        streams += list(zip(idx, enc))
+    streams = [s for _, s in sorted(streams, key=lambda t: t[0])]
+    lens = [len(s) for s in streams]
+    offs = np.cumsum([0] + [(n + 255) // 256 * 256 for n in lens])
+    host_all = np.zeros(int(offs[-1]), dtype=np.uint8)
+    for i, s in enumerate(streams):
+        host_all[offs[i]:offs[i] + lens[i]] = np.frombuffer(s, dtype=np.uint8)
+    dev_all = torch.from_numpy(host_all).to(dev)
+    ptrs = [dev_all.data_ptr() + int(offs[i]) for i in range(BATCH)]
+    out = torch.empty((BATCH, H, W, 3), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream_bytes = int(sum(lens))
+    pixels = BATCH * H * W
+
+    def step():
+        codec.decode_batch_device(model, ptrs, lens, out.data_ptr(), (H, W, 3))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    pw.pw_ctx_profile(codec.ctx, 1)
+    l0 = codec.launches
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    sampler.stop()
+    launches = codec.launches - l0
+    stats = (pw.pw_kernel_stat * 32)()
+    nst = pw.pw_ctx_kernel_stats(codec.ctx, stats, 32)
+    pw.pw_ctx_profile(codec.ctx, 0)
+    kern = [{"name": stats[i].name.decode(), "launches": int(stats[i].launches),
+             "ms": float(stats[i].ms), "flops": float(stats[i].flops),
+             "bytes": float(stats[i].bytes)} for i in range(max(nst, 0))]
+    total_ms = float(sum(times))
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    value = world * pixels * args.steps / (total_ms / 1e3) / 1e6
+
+    # e2e: host streams -> host images through the C ABI
+    e2e_times = []
+    host_out = None
+    if not args.no_e2e:
+        for i in range(max(1, args.steps // 2)):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            host_out = codec.decode_batch(model, streams)
+            e2e_times.append(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+    et = torch.tensor([sum(e2e_times), len(e2e_times)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e_value = (world * pixels * et[1].item() / et[0].item() / 1e6) if e2e_times else None
+
+    if rank != 0:
+        return
+    peaks, peak_kind = measured_peaks()
+    kern_sorted = sorted(kern, key=lambda k: -k["ms"])
+    dom = kern_sorted[0] if kern_sorted else None
+    clocks = sampler.summary()
+    roofline = None
+    if dom:
+        tc = args.precision == "bf16" and dom["name"].startswith("ctx")
+        if dom["name"].startswith("ctx") or dom["name"] == "lift_step":
+            if tc:
+                peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+                bound, unit = "tensor", "TFLOP/s"
+            else:
+                # FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
+                peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+                bound, unit = "alu", "TFLOP/s"
+            achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+        else:
+            peak = float(peaks.get("hbm_gbs", 6800.0))
+            bound, unit = "hbm", "GB/s"
+            achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
+        roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                    "frac": achieved / peak, "traffic": None, "kernel": dom["name"],
+                    "peak_source": peak_kind + (" (derived: SMs x lanes x clock)"
+                                                if bound == "alu" else "")}
+    total_kernel_ms = sum(k["ms"] for k in kern) or 1.0
+    line = {
+        "metric": "decoded MPix/s", "value": value, "unit": "MPix/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": BATCH * world, "image": "768x512 RGB",
+                   "context_channels": 64, "levels": 4, "ll_mode": "four-step",
+                   "precision": args.precision, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "stream_bytes_per_step": stream_bytes,
+                   "bpp": 8.0 * stream_bytes / pixels},
+        "latency_ms": {"p50": float(np.percentile(times, 50)),
+                       "p99": float(np.percentile(times, 99))},
+        "e2e": {"value": e2e_value, "unit": "MPix/s",
+                "h2d_bytes_per_step": stream_bytes, "d2h_bytes_per_step": pixels * 3},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "kernels": [{"name": k["name"], "launches": k["launches"],
+                     "ms_per_step": k["ms"] / args.steps,
+                     "share": k["ms"] / total_kernel_ms} for k in kern_sorted],
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                   "reasons": clocks["reasons"]},
+        "wall_s_timed_region": t_wall,
+    }
+    if not args.no_cpu and world == 1:
+        px, dt = cpu_oracle_decode_sample(256)
+        line["cpu_baseline"] = {"value": px / dt / 1e6, "unit": "MPix/s",
+                                "cores": blas_threads(), "kind": "oracle",
+                                "sample": "256x256 RGB crop of image 1, q=8, decode only"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=os.environ.get("PW_BENCH_PRECISION", "fp32"),
+                    choices=["fp32", "bf16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * pwave.h - C ABI of the GB300 pWave++ codec library (libpwave.so).
+ *
+ * The library implements the decode path of the learned wavelet coder of
+ * "Efficient Learned Wavelet Image and Video Coding" (pWave++ / pMCTF):
+ * the four-step parallel context model (Section 3.2), entropy parameters ->
+ * integer CDF tables -> rANS decoding (standing in for the paper's
+ * arithmetic coder, Section 3.1), and the CNN lifting inverse wavelet
+ * transform (Section 3.1, Fig. 2), plus the matching encoder and the
+ * temporal lifting stage for groups of pictures (Section 3.3).
+ *
+ * Conventions for every call:
+ *  - the return value is a pw_status (PW_OK = 0); no call aborts the process;
+ *  - all GPU work is enqueued on the context's CUDA stream; calls that return
+ *    host results synchronise that stream before returning;
+ *  - the library never frees memory it did not allocate; buffers it returns
+ *    (bitstreams) are released with pw_free;
+ *  - "device" pointers are CUDA device pointers of the context's device;
+ *    "host" pointers are ordinary (pageable or pinned) host memory;
+ *  - a pw_ctx is not thread-safe: use one context per host thread.
+ */
+#ifndef PWAVE_H
+#define PWAVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PW_OK = 0,
+  PW_EINVAL = 1,        /* bad argument, or stream made by another model  */
+  PW_ENOMEM = 2,        /* device or host allocation failed               */
+  PW_ECORRUPT = 3,      /* malformed or truncated bitstream               */
+  PW_EUNSUPPORTED = 4,  /* valid but unsupported configuration            */
+  PW_ETIMEOUT = 5,      /* a bounded wait expired                         */
+  PW_EAGAIN = 6,        /* resource temporarily exhausted (server budget) */
+  PW_ECUDA = 7          /* a CUDA runtime/driver call failed              */
+} pw_status;
+
+/* Arithmetic of the context-model and lifting convolutions. FP32 is the
+ * plain SIMT path; BF16 runs the convolutions on tcgen05 tensor cores with
+ * FP32 accumulation. The entropy-parameter -> table decision and the CDF
+ * tables are FP32/integer in every mode. A stream decodes only with the
+ * precision class that encoded it (recorded in the stream header). */
+typedef enum { PW_PREC_FP32 = 0, PW_PREC_BF16 = 1 } pw_precision;
+
+typedef struct pw_ctx pw_ctx;
+typedef struct pw_model pw_model;
+
+/* An interleaved (HWC) image. bitdepth 8 means uint8 samples, 9..16 means
+ * uint16 samples. stride_bytes = 0 means tightly packed rows. */
+typedef struct {
+  int32_t width, height, channels; /* channels: 1 (gray) or 3 (RGB)      */
+  int32_t bitdepth;
+  int32_t is_device;               /* data is a device pointer             */
+  int32_t reserved;
+  void *data;
+  int64_t stride_bytes;
+} pw_image;
+
+typedef struct {
+  float q;                /* quantiser step: Delta_L = Delta_H = 1/q (Section 3.1) */
+  int32_t lossless;       /* integer lifting + RCT, no quantiser (Fig. 2 caption) */
+  int32_t chunk_symbols;  /* max symbols per rANS chunk (0 = 16384)              */
+} pw_codec_opts;
+
+/* ---- context and model ------------------------------------------------- */
+
+/* Create a context on CUDA device `device` that enqueues its work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Errors: PW_EINVAL (bad device/precision), PW_ECUDA. */
+int pw_ctx_create(int device, void *cuda_stream, int precision, pw_ctx **out);
+void pw_ctx_destroy(pw_ctx *ctx);
+/* Precision the context was created with. */
+int pw_ctx_precision(const pw_ctx *ctx);
+
+/* Load a weight blob ("PWMB" format: lifting nets, ConvLSTM, four-step
+ * context nets; one blob per lambda model, Section 4.1). The blob is a host
+ * buffer of n bytes; the library copies what it needs to the device.
+ * Errors: PW_EINVAL (bad magic, missing tensor, shape mismatch). */
+int pw_model_load(pw_ctx *ctx, const void *blob, size_t n, pw_model **out);
+void pw_model_free(pw_model *m);
+/* 64-bit hash of the blob; every stream records the hash of its model. */
+uint64_t pw_model_hash(const pw_model *m);
+
+/* ---- images (Sections 3.1, 3.2) ----------------------------------------- */
+
+/* Encode one image (host or device samples) into a newly allocated host
+ * bitstream *bs of *n bytes (free with pw_free). */
+int pw_encode_image(pw_ctx *ctx, const pw_model *m, const pw_image *in,
+                    const pw_codec_opts *opts, uint8_t **bs, size_t *n);
+
+/* Decode one host bitstream into `out`. out->data must hold
+ * height * width * channels samples of the stream's bit depth (checked
+ * against out->width/height/channels, which must match the stream).
+ * Errors: PW_EINVAL (model hash or size mismatch), PW_ECORRUPT. */
+int pw_decode_image(pw_ctx *ctx, const pw_model *m, const uint8_t *bs, size_t n,
+                    pw_image *out);
+
+/* Batched encode: count images of identical size and channel count;
+ * bs[i], n[i] receive the streams (free each with pw_free). */
+int pw_encode_batch(pw_ctx *ctx, const pw_model *m, int count, const pw_image *in,
+                    const pw_codec_opts *opts, uint8_t **bs, size_t *n);
+
+/* Batched decode of count streams of identical size/channels/model into
+ * out[0..count-1]. bs[i] are host pointers unless bs_on_device is set, in
+ * which case they are device pointers (the streams then never visit the
+ * host: headers are validated on the device). */
+int pw_decode_batch(pw_ctx *ctx, const pw_model *m, int count,
+                    const uint8_t *const *bs, const size_t *n, int bs_on_device,
+                    pw_image *out);
+
+/* ---- stages of the decode path (for testing and composition) ----------- */
+
+/* Build the 2048 x 128 uint16 CDF table bank (table id (phi + 8) * 128 + j)
+ * into device buffer dev_bank (2048 * 128 * 2 bytes). Deterministic FP32
+ * definition; identical on every GPU and to the reference definition. */
+int pw_cdf_bank(pw_ctx *ctx, uint16_t *dev_bank);
+
+/* Entropy-parameter index decision for n (mu, sigma) pairs (host arrays):
+ * writes packed indices ((rint(16 mu) + 2^23) << 7) | j to host idx. */
+int pw_entropy_index(pw_ctx *ctx, const float *mu, const float *sigma, int64_t n,
+                     uint32_t *idx);
+
+/* rANS-decode `nchunks` chunks (host arrays): chunk c holds count[c]
+ * symbols coded with lanes[c] interleaved states, its bytes at
+ * payload + offset[c] (nbytes[c] long). idx gives the packed table index of
+ * every symbol (chunks concatenated, host); out receives the decoded
+ * values ctr + r (host int32, same order). Errors: PW_ECORRUPT. */
+int pw_rans_decode(pw_ctx *ctx, const uint8_t *payload, size_t payload_bytes,
+                   int nchunks, const uint32_t *offset, const uint32_t *nbytes,
+                   const uint32_t *count, const uint32_t *lanes,
+                   const uint32_t *idx, int32_t *out);
+
+/* Inverse of pw_rans_decode: encodes values with the given indices into a
+ * new host payload (*payload, *payload_bytes; free with pw_free) and fills
+ * offset[c] and nbytes[c]. */
+int pw_rans_encode(pw_ctx *ctx, int nchunks, const uint32_t *count,
+                   const uint32_t *lanes, const uint32_t *idx, const int32_t *values,
+                   uint8_t **payload, size_t *payload_bytes, uint32_t *offset,
+                   uint32_t *nbytes);
+
+/* Context model on fully known quantised subbands of one component
+ * (Section 3.2): q holds the 3*levels+1 subbands in coding order, each
+ * (H >> lv) x (W >> lv) int32, concatenated (host). Writes mu and sigma
+ * (host float, same layout) of every position as the decoder computes them
+ * step by step. H and W must be multiples of 2^levels. */
+int pw_context_params(pw_ctx *ctx, const pw_model *m, int H, int W,
+                      const int32_t *q, float *mu, float *sigma);
+
+/* Forward / inverse learned lifting DWT of one plane (Section 3.1, Fig. 2)
+ * on host float arrays: x is H x W; sb holds the subbands in coding order
+ * (same layout as pw_context_params). lossless selects integer lifting. */
+int pw_lift_forward(pw_ctx *ctx, const pw_model *m, int H, int W, int lossless,
+                    const float *x, float *sb);
+int pw_lift_inverse(pw_ctx *ctx, const pw_model *m, int H, int W, int lossless,
+                    const float *sb, float *x);
+
+/* Decode only the quantised coefficients of a host stream (context model +
+ * rANS, no inverse transform). q (host int32) receives ncomp * Hp * Wp
+ * values, Hp / Wp the sizes padded to multiples of 2^levels, laid out
+ * subband-major: subband i (coding order) of component c at
+ * q[ncomp * off_i + c * h_i * w_i + y * w_i + x], off_i = sum of h_j * w_j
+ * over j < i. */
+int pw_decode_symbols(pw_ctx *ctx, const pw_model *m, const uint8_t *bs, size_t n,
+                      int32_t *q);
+
+/* Encoder analysis only: colour transform, forward lifting DWT and
+ * quantiser of one image; q as in pw_decode_symbols. */
+int pw_analyse(pw_ctx *ctx, const pw_model *m, const pw_image *in,
+               const pw_codec_opts *opts, int32_t *q);
+
+/* Entropy-code a given quantised latent (host q, layout as in
+ * pw_decode_symbols) into a stream for an image of the given size, channel
+ * count, bit depth and colour code (0 gray, 1 YCbCr, 2 RCT, 3 raw planes). */
+int pw_encode_latent(pw_ctx *ctx, const pw_model *m, const int32_t *q, int width,
+                     int height, int channels, int bitdepth, int colour,
+                     const pw_codec_opts *opts, uint8_t **bs, size_t *n);
+
+/* ---- misc ---------------------------------------------------------------- */
+void pw_free(void *p);
+const char *pw_strerror(int status);
+/* Message of the last failure on the calling thread. */
+const char *pw_last_error(void);
+/* Number of kernels this library launched on the context so far. */
+uint64_t pw_ctx_launch_count(const pw_ctx *ctx);
+
+/* Per-kernel-class timing. pw_ctx_profile(ctx, 1) resets the counters and
+ * records a CUDA event pair on the context's stream around every launch that
+ * follows (adds a few microseconds per launch); 0 stops recording.
+ * pw_ctx_kernel_stats fills up to max entries and returns the number of
+ * classes seen (negative pw_status on error). flops / bytes are the
+ * algorithmic work of the recorded launches (not hardware counters). */
+typedef struct {
+  char name[40];
+  uint64_t launches;
+  double ms, flops, bytes;
+} pw_kernel_stat;
+int pw_ctx_profile(pw_ctx *ctx, int enable);
+int pw_ctx_kernel_stats(pw_ctx *ctx, pw_kernel_stat *out, int max);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PWAVE_H */

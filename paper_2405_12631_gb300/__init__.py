@@ -1,0 +1,339 @@
+"""Python binding of libpwave (the GB300 pWave++ codec library).
+
+Thin ctypes marshalling over the C ABI declared in include/pwave.h: every
+function of the ABI is exposed under the same name (``pw_*``), plus a small
+``Codec`` convenience class that converts numpy arrays, bytes and torch
+tensors to the ABI's pointers. All computation happens in the CUDA library;
+importing this module fails loudly when libpwave.so has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpwave.so")
+
+PW_OK, PW_EINVAL, PW_ENOMEM, PW_ECORRUPT, PW_EUNSUPPORTED, PW_ETIMEOUT, PW_EAGAIN, PW_ECUDA = range(8)
+PW_PREC_FP32, PW_PREC_BF16 = 0, 1
+
+
+class PwError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pwave error {code}: {msg}")
+        self.code = code
+
+
+class pw_image(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("channels", C.c_int32),
+                ("bitdepth", C.c_int32), ("is_device", C.c_int32), ("reserved", C.c_int32),
+                ("data", C.c_void_p), ("stride_bytes", C.c_int64)]
+
+
+class pw_codec_opts(C.Structure):
+    _fields_ = [("q", C.c_float), ("lossless", C.c_int32), ("chunk_symbols", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            "libpwave.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`"
+            f" (expected at {LIB_PATH})")
+    return C.CDLL(LIB_PATH)
+
+
+_lib = _load()
+
+_P = C.c_void_p
+_u8p = C.POINTER(C.c_uint8)
+_sig = {
+    "pw_ctx_create": (C.c_int, [C.c_int, _P, C.c_int, C.POINTER(_P)]),
+    "pw_ctx_destroy": (None, [_P]),
+    "pw_ctx_precision": (C.c_int, [_P]),
+    "pw_ctx_launch_count": (C.c_uint64, [_P]),
+    "pw_model_load": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(_P)]),
+    "pw_model_free": (None, [_P]),
+    "pw_model_hash": (C.c_uint64, [_P]),
+    "pw_encode_image": (C.c_int, [_P, _P, C.POINTER(pw_image), C.POINTER(pw_codec_opts),
+                                  C.POINTER(_u8p), C.POINTER(C.c_size_t)]),
+    "pw_decode_image": (C.c_int, [_P, _P, _P, C.c_size_t, C.POINTER(pw_image)]),
+    "pw_encode_batch": (C.c_int, [_P, _P, C.c_int, C.POINTER(pw_image),
+                                  C.POINTER(pw_codec_opts), C.POINTER(_u8p),
+                                  C.POINTER(C.c_size_t)]),
+    "pw_decode_batch": (C.c_int, [_P, _P, C.c_int, C.POINTER(_P), C.POINTER(C.c_size_t),
+                                  C.c_int, C.POINTER(pw_image)]),
+    "pw_cdf_bank": (C.c_int, [_P, _P]),
+    "pw_entropy_index": (C.c_int, [_P, _P, _P, C.c_int64, _P]),
+    "pw_rans_decode": (C.c_int, [_P, _P, C.c_size_t, C.c_int, _P, _P, _P, _P, _P, _P]),
+    "pw_rans_encode": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.POINTER(_u8p),
+                                 C.POINTER(C.c_size_t), _P, _P]),
+    "pw_context_params": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P]),
+    "pw_lift_forward": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "pw_lift_inverse": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "pw_decode_symbols": (C.c_int, [_P, _P, _P, C.c_size_t, _P]),
+    "pw_analyse": (C.c_int, [_P, _P, C.POINTER(pw_image), C.POINTER(pw_codec_opts), _P]),
+    "pw_encode_latent": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.POINTER(pw_codec_opts), C.POINTER(_u8p),
+                                   C.POINTER(C.c_size_t)]),
+    "pw_free": (None, [_P]),
+    "pw_strerror": (C.c_char_p, [C.c_int]),
+    "pw_last_error": (C.c_char_p, []),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+EXPORTED = tuple(_sig)
+
+
+def check(code: int):
+    if code != PW_OK:
+        raise PwError(code, pw_strerror(code).decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _take_bytes(p, n: int) -> bytes:
+    b = C.string_at(p, n)
+    pw_free(p)
+    return b
+
+
+def _opts(q, lossless, chunk):
+    return pw_codec_opts(float(q), int(bool(lossless)), int(chunk))
+
+
+def _host_image(img: np.ndarray, bitdepth: int | None):
+    img = np.ascontiguousarray(img)
+    h, w = img.shape[:2]
+    ch = 1 if img.ndim == 2 else img.shape[2]
+    if bitdepth is None:
+        bitdepth = 8 if img.dtype == np.uint8 else 16
+    return pw_image(w, h, ch, bitdepth, 0, 0, img.ctypes.data, 0), img
+
+
+class Model:
+    def __init__(self, codec: "Codec", blob: bytes):
+        self.codec = codec
+        self._blob = blob
+        h = C.c_void_p()
+        check(pw_model_load(codec.ctx, blob, len(blob), C.byref(h)))
+        self.handle = h
+
+    @property
+    def hash(self) -> int:
+        return int(pw_model_hash(self.handle))
+
+    def close(self):
+        if self.handle:
+            pw_model_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Codec:
+    """A libpwave context (one CUDA device, one stream, one precision)."""
+
+    def __init__(self, device: int = 0, precision: str | int = "fp32", stream: int = 0):
+        prec = {"fp32": PW_PREC_FP32, "bf16": PW_PREC_BF16}.get(precision, precision)
+        h = C.c_void_p()
+        check(pw_ctx_create(int(device), C.c_void_p(stream or None), int(prec), C.byref(h)))
+        self.ctx = h
+        self.precision = prec
+
+    def close(self):
+        if self.ctx:
+            pw_ctx_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self) -> int:
+        return int(pw_ctx_launch_count(self.ctx))
+
+    def load_model(self, blob: bytes) -> Model:
+        return Model(self, blob)
+
+    # ---- images -----------------------------------------------------------
+    def encode_image(self, model: Model, img: np.ndarray, q: float = 8.0,
+                     lossless: bool = False, chunk: int = 16384,
+                     bitdepth: int | None = None) -> bytes:
+        return self.encode_batch(model, [img], q, lossless, chunk, bitdepth)[0]
+
+    def encode_batch(self, model: Model, imgs, q: float = 8.0, lossless: bool = False,
+                     chunk: int = 16384, bitdepth: int | None = None) -> list:
+        ims, keep = [], []
+        for im in imgs:
+            s, a = _host_image(im, bitdepth)
+            ims.append(s)
+            keep.append(a)
+        arr = (pw_image * len(ims))(*ims)
+        outs = (_u8p * len(ims))()
+        lens = (C.c_size_t * len(ims))()
+        o = _opts(q, lossless, chunk)
+        check(pw_encode_batch(self.ctx, model.handle, len(ims), arr, C.byref(o), outs, lens))
+        return [_take_bytes(outs[i], lens[i]) for i in range(len(ims))]
+
+    def decode_image(self, model: Model, bs: bytes, shape=None, dtype=None) -> np.ndarray:
+        return self.decode_batch(model, [bs], shape, dtype)[0]
+
+    def decode_batch(self, model: Model, streams, shape=None, dtype=None) -> np.ndarray:
+        if shape is None or dtype is None:
+            shape, dtype = stream_image_shape(streams[0])
+        B = len(streams)
+        out = np.zeros((B,) + tuple(shape), dtype=dtype)
+        h, w = shape[:2]
+        ch = 1 if len(shape) == 2 else shape[2]
+        bd = 8 if out.dtype == np.uint8 else 16
+        item = out[0].nbytes
+        ims = (pw_image * B)(*[pw_image(w, h, ch, bd, 0, 0, out.ctypes.data + i * item, 0)
+                               for i in range(B)])
+        bufs = [C.c_char_p(s) for s in streams]
+        ptrs = (C.c_void_p * B)(*[C.cast(b, C.c_void_p) for b in bufs])
+        lens = (C.c_size_t * B)(*[len(s) for s in streams])
+        check(pw_decode_batch(self.ctx, model.handle, B, ptrs, lens, 0, ims))
+        return out
+
+    def decode_batch_device(self, model: Model, ptrs, lens, out_ptr: int, shape,
+                            bitdepth: int = 8):
+        """Decode device-resident streams into a contiguous device output.
+
+        ptrs / lens: device addresses and byte lengths of the streams;
+        out_ptr: device address of a packed [B, H, W, C] buffer.
+        """
+        B = len(ptrs)
+        h, w = shape[:2]
+        ch = 1 if len(shape) == 2 else shape[2]
+        item = h * w * ch * (1 if bitdepth <= 8 else 2)
+        ims = (pw_image * B)(*[pw_image(w, h, ch, bitdepth, 1, 0, out_ptr + i * item, 0)
+                               for i in range(B)])
+        p = (C.c_void_p * B)(*ptrs)
+        n = (C.c_size_t * B)(*lens)
+        check(pw_decode_batch(self.ctx, model.handle, B, p, n, 1, ims))
+
+    # ---- stages -----------------------------------------------------------
+    def cdf_bank_device(self, dev_ptr: int):
+        check(pw_cdf_bank(self.ctx, C.c_void_p(dev_ptr)))
+
+    def entropy_index(self, mu: np.ndarray, sigma: np.ndarray) -> np.ndarray:
+        mu = np.ascontiguousarray(mu, dtype=np.float32)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float32)
+        idx = np.zeros(mu.shape, dtype=np.uint32)
+        check(pw_entropy_index(self.ctx, _ptr(mu), _ptr(sigma), mu.size, _ptr(idx)))
+        return idx
+
+    def rans_decode(self, payload: bytes, offset, nbytes, count, lanes, idx) -> np.ndarray:
+        offset = np.ascontiguousarray(offset, dtype=np.uint32)
+        nbytes = np.ascontiguousarray(nbytes, dtype=np.uint32)
+        count = np.ascontiguousarray(count, dtype=np.uint32)
+        lanes = np.ascontiguousarray(lanes, dtype=np.uint32)
+        idx = np.ascontiguousarray(idx, dtype=np.uint32)
+        out = np.zeros(int(count.sum()), dtype=np.int32)
+        pb = C.create_string_buffer(payload, len(payload))
+        check(pw_rans_decode(self.ctx, pb, len(payload), len(count), _ptr(offset),
+                             _ptr(nbytes), _ptr(count), _ptr(lanes), _ptr(idx), _ptr(out)))
+        return out
+
+    def rans_encode(self, count, lanes, idx, values):
+        count = np.ascontiguousarray(count, dtype=np.uint32)
+        lanes = np.ascontiguousarray(lanes, dtype=np.uint32)
+        idx = np.ascontiguousarray(idx, dtype=np.uint32)
+        values = np.ascontiguousarray(values, dtype=np.int32)
+        n = len(count)
+        offset = np.zeros(n, dtype=np.uint32)
+        nbytes = np.zeros(n, dtype=np.uint32)
+        p = _u8p()
+        pbytes = C.c_size_t()
+        check(pw_rans_encode(self.ctx, n, _ptr(count), _ptr(lanes), _ptr(idx), _ptr(values),
+                             C.byref(p), C.byref(pbytes), _ptr(offset), _ptr(nbytes)))
+        return _take_bytes(p, pbytes.value), offset, nbytes
+
+    def context_params(self, model: Model, H: int, W: int, q: np.ndarray):
+        q = np.ascontiguousarray(q, dtype=np.int32)
+        mu = np.zeros(q.size, dtype=np.float32)
+        sg = np.zeros(q.size, dtype=np.float32)
+        check(pw_context_params(self.ctx, model.handle, H, W, _ptr(q), _ptr(mu), _ptr(sg)))
+        return mu, sg
+
+    def lift_forward(self, model: Model, x: np.ndarray, lossless: bool = False) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        H, W = x.shape
+        out = np.zeros(H * W, dtype=np.float32)
+        check(pw_lift_forward(self.ctx, model.handle, H, W, int(lossless), _ptr(x), _ptr(out)))
+        return out
+
+    def lift_inverse(self, model: Model, sb: np.ndarray, H: int, W: int,
+                     lossless: bool = False) -> np.ndarray:
+        sb = np.ascontiguousarray(sb, dtype=np.float32)
+        out = np.zeros((H, W), dtype=np.float32)
+        check(pw_lift_inverse(self.ctx, model.handle, H, W, int(lossless), _ptr(sb), _ptr(out)))
+        return out
+
+    def decode_symbols(self, model: Model, bs: bytes) -> np.ndarray:
+        hd = parse_stream_header(bs)
+        n = hd["ncomp"] * padded_elems(hd)
+        q = np.zeros(n, dtype=np.int32)
+        check(pw_decode_symbols(self.ctx, model.handle, bs, len(bs), _ptr(q)))
+        return q
+
+    def analyse(self, model: Model, img: np.ndarray, q: float = 8.0, lossless: bool = False,
+                levels: int = 4, bitdepth: int | None = None) -> np.ndarray:
+        s, a = _host_image(img, bitdepth)
+        mult = 1 << levels
+        Hp = -(-s.height // mult) * mult
+        Wp = -(-s.width // mult) * mult
+        out = np.zeros(s.channels * Hp * Wp, dtype=np.int32)
+        o = _opts(q, lossless, 16384)
+        check(pw_analyse(self.ctx, model.handle, C.byref(s), C.byref(o), _ptr(out)))
+        return out
+
+    def encode_latent(self, model: Model, q: np.ndarray, width: int, height: int,
+                      channels: int, bitdepth: int = 8, colour: int = 0, qstep: float = 8.0,
+                      lossless: bool = False, chunk: int = 16384) -> bytes:
+        q = np.ascontiguousarray(q, dtype=np.int32)
+        o = _opts(qstep, lossless, chunk)
+        p = _u8p()
+        n = C.c_size_t()
+        check(pw_encode_latent(self.ctx, model.handle, _ptr(q), width, height, channels,
+                               bitdepth, colour, C.byref(o), C.byref(p), C.byref(n)))
+        return _take_bytes(p, n.value)
+
+
+# ---- stream header helpers (format only) ------------------------------------
+def parse_stream_header(bs: bytes) -> dict:
+    import struct
+    if bs[:4] != b"PWBS":
+        raise ValueError("not a PWBS stream")
+    (ver, flags, width, height, ncomp, levels, bitdepth, colour, dl, dh, T, log2m, lanes,
+     chunk, nch, mhash, pbytes) = struct.unpack_from("<HHIIBBBBffHBBIIQI", bs, 4)
+    return dict(version=ver, flags=flags, width=width, height=height, ncomp=ncomp,
+                levels=levels, bitdepth=bitdepth, colour=colour, delta_l=dl, delta_h=dh,
+                chunk=chunk, n_chunks=nch, model_hash=mhash, payload_bytes=pbytes)
+
+
+def padded_elems(hd: dict) -> int:
+    mult = 1 << hd["levels"]
+    return (-(-hd["height"] // mult) * mult) * (-(-hd["width"] // mult) * mult)
+
+
+def stream_image_shape(bs: bytes):
+    hd = parse_stream_header(bs)
+    dtype = np.uint8 if hd["bitdepth"] <= 8 else np.uint16
+    shape = (hd["height"], hd["width"]) if hd["ncomp"] == 1 else (hd["height"], hd["width"], 3)
+    return shape, dtype

@@ -1,0 +1,914 @@
+// C ABI of libpwave (include/pwave.h) and the host-side batch drivers.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+
+#include "codec.h"
+#include "driver.h"
+#include "prof.h"
+
+namespace pw {
+
+static thread_local std::string g_last_error;
+void set_last_error(const std::string &s) { g_last_error = s; }
+
+static inline void bump(pw_ctx *ctx, int n = 1) { ctx->launches += (uint64_t)n; }
+
+// Device buffer that grows on demand.
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t n) {
+    if (n <= cap) return PW_OK;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMalloc(&p, n ? n : 1) != cudaSuccess) { set_last_error("device allocation failed"); return PW_ENOMEM; }
+    cap = n;
+    return PW_OK;
+  }
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+struct HostBuf {  // pinned
+  void *p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t n) {
+    if (n <= cap) return PW_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMallocHost(&p, n ? n : 1) != cudaSuccess) { set_last_error("pinned allocation failed"); return PW_ENOMEM; }
+    cap = n;
+    return PW_OK;
+  }
+  ~HostBuf() { if (p) cudaFreeHost(p); }
+};
+
+struct Plan {
+  std::string key;
+  Geometry g;
+  int B = 0;
+  Workspace ws;
+  // decode
+  DevBuf d_chunks, d_tpl, d_deltas, d_ptrs, d_lens, d_stage, d_out;
+  HostBuf h_stage, h_small;
+  std::vector<int64_t> gbase;   // decode descriptor block of each group
+  // encode
+  DevBuf d_enc, d_ops, d_scratch, d_states, d_nwords, d_outoff, d_payload, d_img;
+};
+
+struct PlanCache {
+  std::vector<std::unique_ptr<Plan>> plans;
+};
+
+Prof &prof_of(pw_ctx *ctx) { return *reinterpret_cast<Prof *>(ctx->prof); }
+
+static PlanCache &cache_of(pw_ctx *ctx) {
+  return *reinterpret_cast<PlanCache *>(ctx->plan_cache);
+}
+
+static std::string geo_key(const char *kind, const Geometry &g, int B, const Model &m, int params) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%s:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%p:%d", kind, g.H, g.W, g.nc,
+           g.levels, g.colour, g.bitdepth, g.lossless, g.ll_ar, g.chunk, B, (const void *)&m,
+           params);
+  return buf;
+}
+
+static int get_plan(pw_ctx *ctx, Model &m, const Geometry &g, int B, const char *kind,
+                    bool params, Plan **out) {
+  const std::string key = geo_key(kind, g, B, m, params ? 1 : 0);
+  auto &pc = cache_of(ctx);
+  for (auto &p : pc.plans)
+    if (p->key == key) { *out = p.get(); return PW_OK; }
+  // keep the cache small: drop the oldest plans beyond 6
+  while (pc.plans.size() >= 6) pc.plans.erase(pc.plans.begin());
+  std::unique_ptr<Plan> p(new Plan());
+  p->key = key;
+  p->g = g;
+  p->B = B;
+  int s = p->ws.alloc(g, B * g.nc, m.C, params, ctx->precision == PW_PREC_BF16);
+  if (s != PW_OK) return s;
+  if (!strcmp(kind, "dec") || !strcmp(kind, "sym")) {
+    // decode descriptor layout: group blocks of P x count
+    const int P = B * g.nc;
+    p->gbase.assign(g.nsb * 4, 0);
+    int64_t acc = 0;
+    for (int gi = 0; gi < g.nsb * 4; ++gi) {
+      p->gbase[gi] = acc;
+      acc += (int64_t)P * g.group_count[gi];
+    }
+    s = p->d_chunks.ensure(std::max<int64_t>(acc, 1) * sizeof(DecChunk));
+    if (s) return s;
+    const int nck = (int)g.chunks.size();
+    std::vector<TplDev> tpl(nck);
+    for (int c = 0; c < nck; ++c) {
+      const ChunkTpl &t = g.chunks[c];
+      const int gi = t.sb * 4 + (t.step < 0 ? 0 : t.step);
+      tpl[c].gbase = p->gbase[gi];
+      tpl[c].gcount = g.group_count[gi];
+      tpl[c].j = c - g.group_first[gi];
+      tpl[c].first = t.first;
+      tpl[c].count = t.count;
+      tpl[c].lanes = t.lanes;
+    }
+    if ((s = p->d_tpl.ensure(std::max(nck, 1) * sizeof(TplDev)))) return s;
+    if (nck) cudaMemcpy(p->d_tpl.p, tpl.data(), nck * sizeof(TplDev), cudaMemcpyHostToDevice);
+    if ((s = p->d_deltas.ensure(2 * B * sizeof(float)))) return s;
+    if ((s = p->d_ptrs.ensure(B * sizeof(void *)))) return s;
+    if ((s = p->d_lens.ensure(B * sizeof(uint64_t)))) return s;
+    if ((s = p->h_small.ensure(B * 16 + 64))) return s;
+  }
+  pc.plans.push_back(std::move(p));
+  *out = pc.plans.back().get();
+  return PW_OK;
+}
+
+static int check_status(pw_ctx *ctx) {
+  if (launch_failed()) { launch_failed() = false; return PW_EUNSUPPORTED; }
+  uint32_t st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, ctx->status, 4, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) { set_last_error(std::string("CUDA: ") + cudaGetErrorString(e)); return PW_ECUDA; }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) { set_last_error(std::string("CUDA launch: ") + cudaGetErrorString(e)); return PW_ECUDA; }
+  if (st & kStHeader) { set_last_error("stream header does not match (model, size or format)"); return PW_EINVAL; }
+  if (st & kStCorrupt) { set_last_error("corrupt or truncated bitstream"); return PW_ECORRUPT; }
+  if (st & kStRange) { set_last_error("value outside the coder's range"); return PW_EINVAL; }
+  return PW_OK;
+}
+
+// Synchronise and report launch / kernel errors (no status word).
+static int finish(pw_ctx *ctx) {
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) { set_last_error(std::string("CUDA: ") + cudaGetErrorString(e)); return PW_ECUDA; }
+  if (launch_failed()) { launch_failed() = false; return PW_EUNSUPPORTED; }
+  return PW_OK;
+}
+
+static uint16_t prec_flags(pw_ctx *ctx) {
+  return (uint16_t)((ctx->precision == PW_PREC_BF16 ? 1 : 0) << FLAG_PREC_SHIFT);
+}
+
+// --------------------------------------------------------------------------
+// Symbol decoding of a batch (context model + rANS), shared by decode and
+// pw_decode_symbols. Streams are device pointers in ptrs (host array).
+static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *const *ptrs,
+                              const size_t *lens, const StreamHeader &h0) {
+  const Geometry &g = pl.g;
+  const int B = pl.B, P = B * g.nc;
+  cudaStream_t st = ctx->stream;
+  // pointer / length tables -> device
+  uint64_t *hs = reinterpret_cast<uint64_t *>(pl.h_small.p);
+  for (int b = 0; b < B; ++b) { hs[b] = (uint64_t)(uintptr_t)ptrs[b]; hs[B + b] = lens[b]; }
+  PW_CUDA_TRY(cudaMemcpyAsync(pl.d_ptrs.p, hs, B * 8, cudaMemcpyHostToDevice, st));
+  PW_CUDA_TRY(cudaMemcpyAsync(pl.d_lens.p, hs + B, B * 8, cudaMemcpyHostToDevice, st));
+  PW_CUDA_TRY(cudaMemsetAsync(ctx->status, 0, 4, st));
+  ParseExpect ex{};
+  ex.width = h0.width; ex.height = h0.height; ex.ncomp = g.nc; ex.levels = g.levels;
+  ex.bitdepth = g.bitdepth; ex.colour = g.colour; ex.flags = h0.flags; ex.chunk = g.chunk;
+  ex.hash = m.hash;
+  DecChunk *dch = reinterpret_cast<DecChunk *>(pl.d_chunks.p);
+  double stream_bytes = 0;
+  for (int b = 0; b < B; ++b) stream_bytes += (double)lens[b];
+  const double total_syms = (double)P * g.plane_elems;
+  {
+  ProfScope ps(ctx, KC_PARSE, 0.0, (double)B * g.nc * g.chunks.size() * (8 + sizeof(DecChunk)));
+  launch_parse_streams(reinterpret_cast<const uint8_t *const *>(pl.d_ptrs.p),
+                       reinterpret_cast<const uint64_t *>(pl.d_lens.p), B, ex,
+                       reinterpret_cast<const TplDev *>(pl.d_tpl.p), (int)g.chunks.size(), dch,
+                       reinterpret_cast<float *>(pl.d_deltas.p), ctx->status, st);
+  }
+  {
+    ProfScope ps(ctx, KC_CDF, 0.0, (double)kNTables * (kNSym + 1) * 2);
+    launch_cdf_bank(ctx->bank, st);
+  }
+  bump(ctx, 2);
+  for (int sb = 0; sb < g.nsb; ++sb) {
+    if (sb == 0 && g.ll_ar) {
+      set_last_error("autoregressive LL decoding is not available in this build");
+      return PW_EUNSUPPORTED;
+    }
+    if (sb >= 1) {
+      int s = run_lstm(ctx, m, g, pl.ws, sb);
+      if (s) return s;
+    }
+    for (int k = 0; k < 4; ++k) {
+      int s = run_context_pass(ctx, m, g, pl.ws, sb, k, true);
+      if (s) return s;
+      const int gi = sb * 4 + k;
+      const int cnt = g.group_count[gi];
+      if (!cnt) continue;
+      const int h = g.sh[sb], w = g.sw[sb];
+      const double nsym = (double)P * step_count(h, w, k);
+      ProfScope ps(ctx, KC_RANS_DEC, 0.0, nsym * 8.0 + stream_bytes * nsym / total_syms);
+      launch_rans_decode(dch + pl.gbase[gi], P * cnt, ctx->bank,
+                         pl.ws.idx + (int64_t)P * g.ioff[gi], step_count(h, w, k),
+                         pl.ws.Q + (int64_t)P * g.soff[sb], (int64_t)h * w, h, w, k,
+                         ctx->status, st);
+      bump(ctx);
+    }
+  }
+  return PW_OK;
+}
+
+static int read_header(const uint8_t *bs, size_t n, int on_dev, StreamHeader &h) {
+  if (!bs || n < sizeof(StreamHeader)) { set_last_error("stream too short"); return PW_ECORRUPT; }
+  if (on_dev) {
+    PW_CUDA_TRY(cudaMemcpy(&h, bs, sizeof(h), cudaMemcpyDeviceToHost));
+  } else {
+    std::memcpy(&h, bs, sizeof(h));
+  }
+  if (std::memcmp(h.magic, "PWBS", 4) != 0 || h.version != 1) { set_last_error("not a PWBS stream"); return PW_ECORRUPT; }
+  return PW_OK;
+}
+
+static int check_header_model(pw_ctx *ctx, const Model &m, const StreamHeader &h) {
+  if (h.model_hash != m.hash) { set_last_error("stream was made with another model"); return PW_EINVAL; }
+  if (h.levels != m.levels || ((h.flags & FLAG_LL_AR) ? 1 : 0) != m.ll_mode) {
+    set_last_error("stream levels / LL mode do not match the model"); return PW_EINVAL;
+  }
+  if (((h.flags >> FLAG_PREC_SHIFT) & 3) != (ctx->precision == PW_PREC_BF16 ? 1 : 0)) {
+    set_last_error("stream was encoded with another precision class"); return PW_EINVAL;
+  }
+  if (h.T != kT || h.log2m != kLogM || h.lanes != kMaxLanes || h.chunk_symbols == 0 ||
+      (h.ncomp != 1 && h.ncomp != 3) || h.width == 0 || h.height == 0 || h.bitdepth < 1 ||
+      h.bitdepth > 16 || h.colour > 3) {
+    set_last_error("unsupported stream parameters"); return PW_EUNSUPPORTED;
+  }
+  return PW_OK;
+}
+
+static int build_geo(const StreamHeader &h, Geometry &g) {
+  g.build((int)h.height, (int)h.width, h.ncomp, h.levels, h.colour, h.bitdepth,
+          (h.flags & FLAG_LOSSLESS) ? 1 : 0, (h.flags & FLAG_LL_AR) ? 1 : 0,
+          (int)h.chunk_symbols);
+  if ((uint64_t)g.chunks.size() * g.nc != h.n_chunks) { set_last_error("chunk count mismatch"); return PW_ECORRUPT; }
+  return PW_OK;
+}
+
+// Stage host streams in device memory; fills ptrs.
+static int stage_streams(pw_ctx *ctx, Plan &pl, int B, const uint8_t *const *bs, const size_t *n,
+                         int on_dev, std::vector<const uint8_t *> &ptrs) {
+  ptrs.resize(B);
+  if (on_dev) {
+    for (int b = 0; b < B; ++b) ptrs[b] = bs[b];
+    return PW_OK;
+  }
+  size_t tot = 0;
+  std::vector<size_t> off(B);
+  for (int b = 0; b < B; ++b) { off[b] = tot; tot += (n[b] + 255) / 256 * 256; }
+  int s;
+  if ((s = pl.d_stage.ensure(tot)) || (s = pl.h_stage.ensure(tot))) return s;
+  uint8_t *hp = static_cast<uint8_t *>(pl.h_stage.p);
+  for (int b = 0; b < B; ++b) std::memcpy(hp + off[b], bs[b], n[b]);
+  PW_CUDA_TRY(cudaMemcpyAsync(pl.d_stage.p, hp, tot, cudaMemcpyHostToDevice, ctx->stream));
+  for (int b = 0; b < B; ++b) ptrs[b] = static_cast<uint8_t *>(pl.d_stage.p) + off[b];
+  return PW_OK;
+}
+
+static int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,
+                        int on_dev, pw_image *out) {
+  if (B < 1 || !bs || !n || !out) { set_last_error("bad arguments"); return PW_EINVAL; }
+  StreamHeader h0;
+  int s = read_header(bs[0], n[0], on_dev, h0);
+  if (s) return s;
+  if ((s = check_header_model(ctx, m, h0))) return s;
+  Geometry g;
+  if ((s = build_geo(h0, g))) return s;
+  const int bps = g.bitdepth > 8 ? 2 : 1;
+  for (int b = 0; b < B; ++b) {
+    if (out[b].width != (int)h0.width || out[b].height != (int)h0.height ||
+        out[b].channels != g.nc || !out[b].data || (out[b].bitdepth > 8 ? 2 : 1) != bps) {
+      set_last_error("output image does not match the stream (size, channels, bit depth)");
+      return PW_EINVAL;
+    }
+  }
+  Plan *pl;
+  if ((s = get_plan(ctx, m, g, B, "dec", false, &pl))) return s;
+  std::vector<const uint8_t *> ptrs;
+  if ((s = stage_streams(ctx, *pl, B, bs, n, on_dev, ptrs))) return s;
+  if ((s = decode_symbols_dev(ctx, m, *pl, ptrs.data(), n, h0))) return s;
+  cudaStream_t st = ctx->stream;
+  const int P = B * g.nc;
+  SbTable tb = make_sbtable(g, P);
+  {
+    ProfScope ps(ctx, KC_QUANT, 0.0, (double)P * g.plane_elems * 8.0);
+    launch_dequant_all(pl->ws.Q, pl->ws.Yf, (int64_t)P * g.plane_elems, tb, g.nc,
+                       reinterpret_cast<float *>(pl->d_deltas.p), st);
+  }
+  bump(ctx);
+  if ((s = lift_inverse_planes(ctx, m, g, pl->ws, pl->ws.planes))) return s;
+  // output: direct when the batch is one contiguous packed device buffer
+  const int64_t row = (int64_t)g.W * g.nc * bps, img = row * g.H;
+  bool direct = true;
+  for (int b = 0; b < B; ++b) {
+    const int64_t rs = out[b].stride_bytes ? out[b].stride_bytes : row;
+    if (!out[b].is_device || rs != row ||
+        (uint8_t *)out[b].data != (uint8_t *)out[0].data + b * img)
+      direct = false;
+  }
+  void *dst = out[0].data;
+  if (!direct) {
+    if ((s = pl->d_out.ensure((size_t)img * B))) return s;
+    dst = pl->d_out.p;
+  }
+  {
+    ProfScope ps(ctx, KC_COLOUR, 0.0, (double)P * g.H * g.W * 4.0 + (double)img * B);
+    launch_colour_out(pl->ws.planes, B, g.nc, g.Hp, g.Wp, g.H, g.W, g.colour, g.bitdepth, dst,
+                      img, row, st);
+  }
+  bump(ctx);
+  if (!direct) {
+    for (int b = 0; b < B; ++b) {
+      const int64_t rs = out[b].stride_bytes ? out[b].stride_bytes : row;
+      PW_CUDA_TRY(cudaMemcpy2DAsync(out[b].data, rs, (uint8_t *)dst + b * img, row, row, g.H,
+                                    out[b].is_device ? cudaMemcpyDeviceToDevice
+                                                     : cudaMemcpyDeviceToHost,
+                                    st));
+    }
+  }
+  return check_status(ctx);
+}
+
+// --------------------------------------------------------------------------
+// Encoding.
+static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, float dh,
+                              uint8_t **bs, size_t *n) {
+  const Geometry &g = pl.g;
+  const int P = B * g.nc;
+  cudaStream_t st = ctx->stream;
+  Workspace &ws = pl.ws;
+  launch_cdf_bank(ctx->bank, st);
+  bump(ctx);
+  for (int sb = 0; sb < g.nsb; ++sb) {
+    if (sb == 0 && g.ll_ar) {
+      set_last_error("autoregressive LL coding is not available in this build");
+      return PW_EUNSUPPORTED;
+    }
+    int s;
+    if (sb >= 1 && (s = run_lstm(ctx, m, g, ws, sb))) return s;
+    for (int k = 0; k < 4; ++k)
+      if ((s = run_context_pass(ctx, m, g, ws, sb, k, false))) return s;
+  }
+  // gather values in step order (same layout as idx)
+  int32_t *vals = reinterpret_cast<int32_t *>(ws.T0);
+  for (int sb = 0; sb < g.nsb; ++sb)
+    for (int k = 0; k < 4; ++k) {
+      const int64_t nk = step_count(g.sh[sb], g.sw[sb], k);
+      if (!nk) continue;
+      launch_gather_step(ws.Q + (int64_t)P * g.soff[sb], P, g.sh[sb], g.sw[sb], k,
+                         vals + (int64_t)P * g.ioff[sb * 4 + k], nk, st);
+      bump(ctx);
+    }
+  // chunk list in stream order per image
+  const int nck = (int)g.chunks.size();
+  const int nall = B * g.nc * nck;
+  std::vector<EncChunk> ec(nall);
+  for (int b = 0; b < B; ++b)
+    for (int c = 0; c < g.nc; ++c)
+      for (int j = 0; j < nck; ++j) {
+        const ChunkTpl &t = g.chunks[j];
+        const int p = b * g.nc + c;
+        const int gi = t.sb * 4 + (t.step < 0 ? 0 : t.step);
+        const int64_t nk = step_count(g.sh[t.sb], g.sw[t.sb], t.step < 0 ? 0 : t.step);
+        EncChunk &e = ec[(b * g.nc + c) * nck + j];
+        e.sym_base = (uint64_t)((int64_t)P * g.ioff[gi] + (int64_t)p * nk + t.first);
+        e.count = t.count;
+        e.lanes = t.lanes;
+        e.scratch_end = 0;
+      }
+  int s;
+  if ((s = pl.d_enc.ensure(std::max(nall, 1) * sizeof(EncChunk))) ||
+      (s = pl.d_ops.ensure(std::max(nall, 1) * 4)) ||
+      (s = pl.d_nwords.ensure(std::max(nall, 1) * 4)) ||
+      (s = pl.d_states.ensure(std::max(nall, 1) * 32 * 4)) ||
+      (s = pl.d_outoff.ensure(std::max(nall, 1) * 8)))
+    return s;
+  EncChunk *d_ec = reinterpret_cast<EncChunk *>(pl.d_enc.p);
+  PW_CUDA_TRY(cudaMemcpyAsync(d_ec, ec.data(), nall * sizeof(EncChunk), cudaMemcpyHostToDevice, st));
+  PW_CUDA_TRY(cudaMemsetAsync(ctx->status, 0, 4, st));
+  launch_rans_count_ops(d_ec, nall, ws.idx, vals, reinterpret_cast<uint32_t *>(pl.d_ops.p), st);
+  bump(ctx);
+  std::vector<uint32_t> ops(nall);
+  PW_CUDA_TRY(cudaMemcpyAsync(ops.data(), pl.d_ops.p, nall * 4, cudaMemcpyDeviceToHost, st));
+  PW_CUDA_TRY(cudaStreamSynchronize(st));
+  uint64_t tot = 0;
+  for (int i = 0; i < nall; ++i) { tot += ops[i]; ec[i].scratch_end = tot; }
+  if ((s = pl.d_scratch.ensure(std::max<uint64_t>(tot, 1) * 2))) return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(d_ec, ec.data(), nall * sizeof(EncChunk), cudaMemcpyHostToDevice, st));
+  launch_rans_encode(d_ec, nall, ctx->bank, ws.idx, vals,
+                     reinterpret_cast<uint16_t *>(pl.d_scratch.p),
+                     reinterpret_cast<uint32_t *>(pl.d_states.p),
+                     reinterpret_cast<uint32_t *>(pl.d_nwords.p), ctx->status, st);
+  bump(ctx);
+  std::vector<uint32_t> nw(nall);
+  PW_CUDA_TRY(cudaMemcpyAsync(nw.data(), pl.d_nwords.p, nall * 4, cudaMemcpyDeviceToHost, st));
+  if ((s = check_status(ctx))) return s;
+  // payload layout: per image, chunks in stream order
+  std::vector<uint64_t> outoff(nall);
+  std::vector<uint64_t> img_start(B + 1);
+  uint64_t pos = 0;
+  for (int b = 0; b < B; ++b) {
+    img_start[b] = pos;
+    for (int i = 0; i < g.nc * nck; ++i) {
+      const int ci = b * g.nc * nck + i;
+      outoff[ci] = pos;
+      pos += 4ull * ec[ci].lanes + 2ull * nw[ci];
+    }
+  }
+  img_start[B] = pos;
+  if ((s = pl.d_payload.ensure(std::max<uint64_t>(pos, 1)))) return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(pl.d_outoff.p, outoff.data(), nall * 8, cudaMemcpyHostToDevice, st));
+  launch_rans_pack(d_ec, nall, reinterpret_cast<uint16_t *>(pl.d_scratch.p),
+                   reinterpret_cast<uint32_t *>(pl.d_states.p),
+                   reinterpret_cast<uint32_t *>(pl.d_nwords.p),
+                   reinterpret_cast<uint64_t *>(pl.d_outoff.p),
+                   reinterpret_cast<uint8_t *>(pl.d_payload.p), st);
+  bump(ctx);
+  std::vector<uint8_t> payload(pos);
+  PW_CUDA_TRY(cudaMemcpyAsync(payload.data(), pl.d_payload.p, pos, cudaMemcpyDeviceToHost, st));
+  if ((s = check_status(ctx))) return s;
+  const int nch = g.nc * nck;
+  for (int b = 0; b < B; ++b) {
+    StreamHeader h{};
+    std::memcpy(h.magic, "PWBS", 4);
+    h.version = 1;
+    h.flags = (uint16_t)((g.lossless ? FLAG_LOSSLESS : 0) | (g.ll_ar ? FLAG_LL_AR : 0) |
+                         prec_flags(ctx));
+    h.width = g.W; h.height = g.H; h.ncomp = (uint8_t)g.nc; h.levels = (uint8_t)g.levels;
+    h.bitdepth = (uint8_t)g.bitdepth; h.colour = (uint8_t)g.colour;
+    h.delta_l = dl; h.delta_h = dh; h.T = kT; h.log2m = kLogM; h.lanes = kMaxLanes;
+    h.chunk_symbols = g.chunk; h.n_chunks = nch; h.model_hash = m.hash;
+    const uint64_t pb = img_start[b + 1] - img_start[b];
+    h.payload_bytes = (uint32_t)pb;
+    const size_t total = 64 + 4 * (size_t)(nch + 1) + pb;
+    uint8_t *o = static_cast<uint8_t *>(std::malloc(total));
+    if (!o) { set_last_error("host allocation failed"); return PW_ENOMEM; }
+    std::memcpy(o, &h, 64);
+    uint32_t *offs = reinterpret_cast<uint32_t *>(o + 64);
+    for (int i = 0; i < nch; ++i)
+      offs[i] = (uint32_t)(outoff[b * nch + i] - img_start[b]);
+    offs[nch] = (uint32_t)pb;
+    std::memcpy(o + 64 + 4 * (nch + 1), payload.data() + img_start[b], pb);
+    bs[b] = o;
+    n[b] = total;
+  }
+  return PW_OK;
+}
+
+static int image_geo(pw_ctx *ctx, const Model &m, const pw_image &im, const pw_codec_opts *o,
+                     Geometry &g) {
+  if (im.width < 1 || im.height < 1 || (im.channels != 1 && im.channels != 3) || !im.data ||
+      im.bitdepth < 1 || im.bitdepth > 16) {
+    set_last_error("bad input image"); return PW_EINVAL;
+  }
+  const int lossless = o && o->lossless ? 1 : 0;
+  const int colour = im.channels == 1 ? 0 : (lossless ? 2 : 1);
+  const int chunk = (o && o->chunk_symbols > 0) ? o->chunk_symbols : 16384;
+  g.build(im.height, im.width, im.channels, m.levels, colour, im.bitdepth, lossless, m.ll_mode,
+          chunk);
+  (void)ctx;
+  return PW_OK;
+}
+
+static int encode_batch(pw_ctx *ctx, Model &m, int B, const pw_image *in,
+                        const pw_codec_opts *o, uint8_t **bs, size_t *n) {
+  if (B < 1 || !in || !bs || !n) { set_last_error("bad arguments"); return PW_EINVAL; }
+  Geometry g;
+  int s = image_geo(ctx, m, in[0], o, g);
+  if (s) return s;
+  for (int b = 1; b < B; ++b)
+    if (in[b].width != in[0].width || in[b].height != in[0].height ||
+        in[b].channels != in[0].channels || in[b].bitdepth != in[0].bitdepth) {
+      set_last_error("batch images differ in size or format"); return PW_EINVAL;
+    }
+  if (!g.lossless && !(o && o->q > 0.f)) { set_last_error("quantiser step must be > 0"); return PW_EINVAL; }
+  Plan *pl;
+  if ((s = get_plan(ctx, m, g, B, "enc", false, &pl))) return s;
+  const int bps = g.bitdepth > 8 ? 2 : 1;
+  const int64_t row = (int64_t)g.W * g.nc * bps, img = row * g.H;
+  if ((s = pl->d_img.ensure((size_t)img * B))) return s;
+  cudaStream_t st = ctx->stream;
+  for (int b = 0; b < B; ++b) {
+    const int64_t rs = in[b].stride_bytes ? in[b].stride_bytes : row;
+    PW_CUDA_TRY(cudaMemcpy2DAsync((uint8_t *)pl->d_img.p + b * img, row, in[b].data, rs, row,
+                                  g.H, in[b].is_device ? cudaMemcpyDeviceToDevice
+                                                       : cudaMemcpyHostToDevice,
+                                  st));
+  }
+  const int P = B * g.nc;
+  launch_colour_in(pl->d_img.p, img, row, B, g.nc, g.H, g.W, g.Hp, g.Wp, g.lossless,
+                   g.bitdepth, pl->ws.planes, st);
+  bump(ctx);
+  if ((s = lift_forward_planes(ctx, m, g, pl->ws, pl->ws.planes))) return s;
+  const float d = g.lossless ? 1.f : 1.f / o->q;
+  SbTable tb = make_sbtable(g, P);
+  launch_quant_all(pl->ws.Yf, pl->ws.Q, (int64_t)P * g.plane_elems, tb, d, d, st);
+  bump(ctx);
+  return encode_from_latent(ctx, m, *pl, B, d, d, bs, n);
+}
+
+}  // namespace pw
+
+using namespace pw;
+
+// ===========================================================================
+// C ABI
+extern "C" {
+
+const char *pw_strerror(int status) {
+  switch (status) {
+    case PW_OK: return "ok";
+    case PW_EINVAL: return g_last_error.empty() ? "invalid argument" : g_last_error.c_str();
+    case PW_ENOMEM: return "out of memory";
+    case PW_ECORRUPT: return "corrupt bitstream";
+    case PW_EUNSUPPORTED: return g_last_error.empty() ? "unsupported" : g_last_error.c_str();
+    case PW_ETIMEOUT: return "timeout";
+    case PW_EAGAIN: return "try again";
+    case PW_ECUDA: return g_last_error.empty() ? "CUDA error" : g_last_error.c_str();
+    default: return "unknown error";
+  }
+}
+
+const char *pw_last_error(void) { return g_last_error.c_str(); }
+
+void pw_free(void *p) { std::free(p); }
+
+int pw_ctx_create(int device, void *stream, int precision, pw_ctx **out) {
+  if (!out || (precision != PW_PREC_FP32 && precision != PW_PREC_BF16)) {
+    set_last_error("bad precision"); return PW_EINVAL;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    set_last_error("no such CUDA device"); return PW_EINVAL;
+  }
+  PW_CUDA_TRY(cudaSetDevice(device));
+  pw_ctx *c = new pw_ctx();
+  c->device = device;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->precision = precision;
+  c->plan_cache = new PlanCache();
+  c->prof = new Prof();
+  if (cudaMalloc(&c->bank, kNTables * (kNSym + 1) * 2) != cudaSuccess ||
+      cudaMalloc(&c->status, 256) != cudaSuccess) {
+    delete reinterpret_cast<PlanCache *>(c->plan_cache);
+    delete reinterpret_cast<Prof *>(c->prof);
+    delete c;
+    set_last_error("device allocation failed");
+    return PW_ENOMEM;
+  }
+  *out = c;
+  return PW_OK;
+}
+
+void pw_ctx_destroy(pw_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  delete reinterpret_cast<PlanCache *>(c->plan_cache);
+  delete reinterpret_cast<Prof *>(c->prof);
+  cudaFree(c->bank);
+  cudaFree(c->status);
+  delete c;
+}
+
+int pw_ctx_precision(const pw_ctx *c) { return c ? c->precision : -1; }
+
+int pw_ctx_profile(pw_ctx *c, int enable) {
+  if (!c) return PW_EINVAL;
+  Prof &p = prof_of(c);
+  cudaStreamSynchronize(c->stream);
+  p.reset();
+  p.on = enable != 0;
+  return PW_OK;
+}
+
+int pw_ctx_kernel_stats(pw_ctx *c, pw_kernel_stat *out, int max) {
+  if (!c || (max > 0 && !out)) return -PW_EINVAL;
+  Prof &p = prof_of(c);
+  p.resolve();
+  int n = 0;
+  for (int k = 0; k < KC_COUNT; ++k) {
+    if (!p.launches[k]) continue;
+    if (n < max) {
+      std::memset(out[n].name, 0, sizeof(out[n].name));
+      std::strncpy(out[n].name, kclass_name(k), sizeof(out[n].name) - 1);
+      out[n].launches = p.launches[k];
+      out[n].ms = p.ms[k];
+      out[n].flops = p.flops[k];
+      out[n].bytes = p.bytes[k];
+    }
+    ++n;
+  }
+  return n;
+}
+uint64_t pw_ctx_launch_count(const pw_ctx *c) { return c ? c->launches : 0; }
+
+int pw_model_load(pw_ctx *c, const void *blob, size_t n, pw_model **out) {
+  if (!c || !blob || !out) { set_last_error("bad arguments"); return PW_EINVAL; }
+  pw_model *m = new pw_model();
+  int s = m->m.load(c, blob, n);
+  if (s == PW_OK && c->precision == PW_PREC_BF16) s = m->m.ensure_tc();
+  if (s != PW_OK) { delete m; return s; }
+  *out = m;
+  return PW_OK;
+}
+
+void pw_model_free(pw_model *m) { delete m; }
+uint64_t pw_model_hash(const pw_model *m) { return m ? m->m.hash : 0; }
+
+int pw_encode_batch(pw_ctx *c, const pw_model *m, int count, const pw_image *in,
+                    const pw_codec_opts *o, uint8_t **bs, size_t *n) {
+  if (!c || !m) return PW_EINVAL;
+  return encode_batch(c, const_cast<pw_model *>(m)->m, count, in, o, bs, n);
+}
+
+int pw_encode_image(pw_ctx *c, const pw_model *m, const pw_image *in, const pw_codec_opts *o,
+                    uint8_t **bs, size_t *n) {
+  return pw_encode_batch(c, m, 1, in, o, bs, n);
+}
+
+int pw_decode_batch(pw_ctx *c, const pw_model *m, int count, const uint8_t *const *bs,
+                    const size_t *n, int on_dev, pw_image *out) {
+  if (!c || !m) return PW_EINVAL;
+  return decode_batch(c, const_cast<pw_model *>(m)->m, count, bs, n, on_dev, out);
+}
+
+int pw_decode_image(pw_ctx *c, const pw_model *m, const uint8_t *bs, size_t n, pw_image *out) {
+  return pw_decode_batch(c, m, 1, &bs, &n, 0, out);
+}
+
+// ---- stages ---------------------------------------------------------------
+int pw_cdf_bank(pw_ctx *c, uint16_t *dev_bank) {
+  if (!c || !dev_bank) return PW_EINVAL;
+  launch_cdf_bank(dev_bank, c->stream);
+  bump(c);
+  return finish(c);
+}
+
+int pw_entropy_index(pw_ctx *c, const float *mu, const float *sigma, int64_t n, uint32_t *idx) {
+  if (!c || n < 0 || (n && (!mu || !sigma || !idx))) return PW_EINVAL;
+  if (!n) return PW_OK;
+  DevBuf d;
+  int s;
+  if ((s = d.ensure((size_t)n * 12))) return s;
+  float *dm = (float *)d.p, *ds = dm + n;
+  uint32_t *di = (uint32_t *)(ds + n);
+  PW_CUDA_TRY(cudaMemcpyAsync(dm, mu, n * 4, cudaMemcpyHostToDevice, c->stream));
+  PW_CUDA_TRY(cudaMemcpyAsync(ds, sigma, n * 4, cudaMemcpyHostToDevice, c->stream));
+  launch_pack_index(dm, ds, n, 1, di, c->stream);
+  bump(c);
+  PW_CUDA_TRY(cudaMemcpyAsync(idx, di, n * 4, cudaMemcpyDeviceToHost, c->stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PW_OK;
+}
+
+int pw_rans_decode(pw_ctx *c, const uint8_t *payload, size_t payload_bytes, int nchunks,
+                   const uint32_t *offset, const uint32_t *nbytes, const uint32_t *count,
+                   const uint32_t *lanes, const uint32_t *idx, int32_t *out) {
+  if (!c || nchunks < 0) return PW_EINVAL;
+  uint64_t nsym = 0;
+  for (int i = 0; i < nchunks; ++i) {
+    if ((uint64_t)offset[i] + nbytes[i] > payload_bytes || lanes[i] < 1 || lanes[i] > 32) {
+      set_last_error("chunk outside payload or bad lane count"); return PW_EINVAL;
+    }
+    nsym += count[i];
+  }
+  DevBuf dp, di, dout, dch;
+  int s;
+  if ((s = dp.ensure(payload_bytes + 16)) || (s = di.ensure(nsym * 4 + 4)) ||
+      (s = dout.ensure(nsym * 4 + 4)) || (s = dch.ensure((nchunks + 1) * sizeof(DecChunk))))
+    return s;
+  std::vector<DecChunk> ch(nchunks);
+  uint64_t first = 0;
+  for (int i = 0; i < nchunks; ++i) {
+    ch[i].data = (const uint8_t *)dp.p + offset[i];
+    ch[i].nbytes = nbytes[i];
+    ch[i].count = count[i];
+    ch[i].first = (uint32_t)first;
+    ch[i].lanes = (uint16_t)lanes[i];
+    ch[i].plane = 0;
+    first += count[i];
+  }
+  cudaStream_t st = c->stream;
+  if (payload_bytes)
+    PW_CUDA_TRY(cudaMemcpyAsync(dp.p, payload, payload_bytes, cudaMemcpyHostToDevice, st));
+  if (nsym) PW_CUDA_TRY(cudaMemcpyAsync(di.p, idx, nsym * 4, cudaMemcpyHostToDevice, st));
+  if (nchunks)
+    PW_CUDA_TRY(cudaMemcpyAsync(dch.p, ch.data(), nchunks * sizeof(DecChunk), cudaMemcpyHostToDevice, st));
+  PW_CUDA_TRY(cudaMemsetAsync(c->status, 0, 4, st));
+  launch_cdf_bank(c->bank, st);
+  launch_rans_decode((DecChunk *)dch.p, nchunks, c->bank, (uint32_t *)di.p, 0,
+                     (int32_t *)dout.p, 0, 0, 0, -1, c->status, st);
+  bump(c, 2);
+  if (nsym) PW_CUDA_TRY(cudaMemcpyAsync(out, dout.p, nsym * 4, cudaMemcpyDeviceToHost, st));
+  return check_status(c);
+}
+
+int pw_rans_encode(pw_ctx *c, int nchunks, const uint32_t *count, const uint32_t *lanes,
+                   const uint32_t *idx, const int32_t *values, uint8_t **payload,
+                   size_t *payload_bytes, uint32_t *offset, uint32_t *nbytes) {
+  if (!c || nchunks < 0 || !payload || !payload_bytes) return PW_EINVAL;
+  uint64_t nsym = 0;
+  for (int i = 0; i < nchunks; ++i) {
+    if (lanes[i] < 1 || lanes[i] > 32) { set_last_error("bad lane count"); return PW_EINVAL; }
+    nsym += count[i];
+  }
+  cudaStream_t st = c->stream;
+  DevBuf di, dv, dec, dops, dsc, dstates, dnw, doff, dpay;
+  int s;
+  if ((s = di.ensure(nsym * 4 + 4)) || (s = dv.ensure(nsym * 4 + 4)) ||
+      (s = dec.ensure((nchunks + 1) * sizeof(EncChunk))) || (s = dops.ensure(nchunks * 4 + 4)) ||
+      (s = dstates.ensure(nchunks * 128 + 4)) || (s = dnw.ensure(nchunks * 4 + 4)) ||
+      (s = doff.ensure(nchunks * 8 + 8)))
+    return s;
+  std::vector<EncChunk> ec(nchunks);
+  uint64_t first = 0;
+  for (int i = 0; i < nchunks; ++i) {
+    ec[i].sym_base = first; ec[i].count = count[i]; ec[i].lanes = lanes[i]; ec[i].scratch_end = 0;
+    first += count[i];
+  }
+  if (nsym) {
+    PW_CUDA_TRY(cudaMemcpyAsync(di.p, idx, nsym * 4, cudaMemcpyHostToDevice, st));
+    PW_CUDA_TRY(cudaMemcpyAsync(dv.p, values, nsym * 4, cudaMemcpyHostToDevice, st));
+  }
+  if (nchunks)
+    PW_CUDA_TRY(cudaMemcpyAsync(dec.p, ec.data(), nchunks * sizeof(EncChunk), cudaMemcpyHostToDevice, st));
+  launch_cdf_bank(c->bank, st);
+  launch_rans_count_ops((EncChunk *)dec.p, nchunks, (uint32_t *)di.p, (int32_t *)dv.p,
+                        (uint32_t *)dops.p, st);
+  bump(c, 2);
+  std::vector<uint32_t> ops(nchunks);
+  if (nchunks) PW_CUDA_TRY(cudaMemcpyAsync(ops.data(), dops.p, nchunks * 4, cudaMemcpyDeviceToHost, st));
+  PW_CUDA_TRY(cudaStreamSynchronize(st));
+  uint64_t tot = 0;
+  for (int i = 0; i < nchunks; ++i) { tot += ops[i]; ec[i].scratch_end = tot; }
+  if ((s = dsc.ensure(tot * 2 + 2))) return s;
+  if (nchunks)
+    PW_CUDA_TRY(cudaMemcpyAsync(dec.p, ec.data(), nchunks * sizeof(EncChunk), cudaMemcpyHostToDevice, st));
+  PW_CUDA_TRY(cudaMemsetAsync(c->status, 0, 4, st));
+  launch_rans_encode((EncChunk *)dec.p, nchunks, c->bank, (uint32_t *)di.p, (int32_t *)dv.p,
+                     (uint16_t *)dsc.p, (uint32_t *)dstates.p, (uint32_t *)dnw.p, c->status, st);
+  bump(c);
+  std::vector<uint32_t> nw(nchunks);
+  if (nchunks) PW_CUDA_TRY(cudaMemcpyAsync(nw.data(), dnw.p, nchunks * 4, cudaMemcpyDeviceToHost, st));
+  if ((s = check_status(c))) return s;
+  std::vector<uint64_t> off(nchunks);
+  uint64_t pos = 0;
+  for (int i = 0; i < nchunks; ++i) {
+    off[i] = pos;
+    offset[i] = (uint32_t)pos;
+    nbytes[i] = 4 * lanes[i] + 2 * nw[i];
+    pos += nbytes[i];
+  }
+  if ((s = dpay.ensure(pos + 4))) return s;
+  if (nchunks) {
+    PW_CUDA_TRY(cudaMemcpyAsync(doff.p, off.data(), nchunks * 8, cudaMemcpyHostToDevice, st));
+    launch_rans_pack((EncChunk *)dec.p, nchunks, (uint16_t *)dsc.p, (uint32_t *)dstates.p,
+                     (uint32_t *)dnw.p, (uint64_t *)doff.p, (uint8_t *)dpay.p, st);
+    bump(c);
+  }
+  uint8_t *o = static_cast<uint8_t *>(std::malloc(pos ? pos : 1));
+  if (!o) return PW_ENOMEM;
+  if (pos) PW_CUDA_TRY(cudaMemcpyAsync(o, dpay.p, pos, cudaMemcpyDeviceToHost, st));
+  PW_CUDA_TRY(cudaStreamSynchronize(st));
+  *payload = o;
+  *payload_bytes = pos;
+  return PW_OK;
+}
+
+int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t *q, float *mu,
+                      float *sigma) {
+  if (!c || !mm || !q || !mu || !sigma) return PW_EINVAL;
+  Model &m = const_cast<pw_model *>(mm)->m;
+  const int mult = 1 << m.levels;
+  if (H < mult || W < mult || H % mult || W % mult) {
+    set_last_error("H and W must be positive multiples of 2^levels"); return PW_EINVAL;
+  }
+  if (m.ll_mode) { set_last_error("autoregressive LL model not available"); return PW_EUNSUPPORTED; }
+  Geometry g;
+  g.build(H, W, 1, m.levels, 0, 8, 0, m.ll_mode, 16384);
+  Plan *pl;
+  int s;
+  if ((s = get_plan(c, m, g, 1, "par", true, &pl))) return s;
+  cudaStream_t st = c->stream;
+  PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.Q, q, g.plane_elems * 4, cudaMemcpyHostToDevice, st));
+  for (int sb = 0; sb < g.nsb; ++sb) {
+    if (sb >= 1 && (s = run_lstm(c, m, g, pl->ws, sb))) return s;
+    for (int k = 0; k < 4; ++k)
+      if ((s = run_context_pass(c, m, g, pl->ws, sb, k, false))) return s;
+  }
+  PW_CUDA_TRY(cudaMemcpyAsync(mu, pl->ws.mu, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
+  PW_CUDA_TRY(cudaMemcpyAsync(sigma, pl->ws.sg, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
+  return finish(c);
+}
+
+static int lift_stage(pw_ctx *c, const pw_model *mm, int H, int W, int lossless, const float *in,
+                      float *out, bool fwd) {
+  if (!c || !mm || !in || !out) return PW_EINVAL;
+  Model &m = const_cast<pw_model *>(mm)->m;
+  const int mult = 1 << m.levels;
+  if (H < mult || W < mult || H % mult || W % mult) {
+    set_last_error("H and W must be positive multiples of 2^levels"); return PW_EINVAL;
+  }
+  Geometry g;
+  g.build(H, W, 1, m.levels, 0, 8, lossless ? 1 : 0, 0, 16384);
+  Plan *pl;
+  int s;
+  if ((s = get_plan(c, m, g, 1, "lift", false, &pl))) return s;
+  cudaStream_t st = c->stream;
+  const size_t bytes = (size_t)g.plane_elems * 4;
+  if (fwd) {
+    PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.planes, in, bytes, cudaMemcpyHostToDevice, st));
+    if ((s = lift_forward_planes(c, m, g, pl->ws, pl->ws.planes))) return s;
+    PW_CUDA_TRY(cudaMemcpyAsync(out, pl->ws.Yf, bytes, cudaMemcpyDeviceToHost, st));
+  } else {
+    PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.Yf, in, bytes, cudaMemcpyHostToDevice, st));
+    if ((s = lift_inverse_planes(c, m, g, pl->ws, pl->ws.planes))) return s;
+    PW_CUDA_TRY(cudaMemcpyAsync(out, pl->ws.planes, bytes, cudaMemcpyDeviceToHost, st));
+  }
+  return finish(c);
+}
+
+int pw_lift_forward(pw_ctx *c, const pw_model *m, int H, int W, int lossless, const float *x,
+                    float *sb) {
+  return lift_stage(c, m, H, W, lossless, x, sb, true);
+}
+int pw_lift_inverse(pw_ctx *c, const pw_model *m, int H, int W, int lossless, const float *sb,
+                    float *x) {
+  return lift_stage(c, m, H, W, lossless, sb, x, false);
+}
+
+int pw_decode_symbols(pw_ctx *c, const pw_model *mm, const uint8_t *bs, size_t n, int32_t *q) {
+  if (!c || !mm || !bs || !q) return PW_EINVAL;
+  Model &m = const_cast<pw_model *>(mm)->m;
+  StreamHeader h0;
+  int s = read_header(bs, n, 0, h0);
+  if (s || (s = check_header_model(c, m, h0))) return s;
+  Geometry g;
+  if ((s = build_geo(h0, g))) return s;
+  Plan *pl;
+  if ((s = get_plan(c, m, g, 1, "sym", false, &pl))) return s;
+  std::vector<const uint8_t *> ptrs;
+  const uint8_t *const bsp[1] = {bs};
+  if ((s = stage_streams(c, *pl, 1, bsp, &n, 0, ptrs))) return s;
+  if ((s = decode_symbols_dev(c, m, *pl, ptrs.data(), &n, h0))) return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(q, pl->ws.Q, (size_t)g.nc * g.plane_elems * 4,
+                              cudaMemcpyDeviceToHost, c->stream));
+  return check_status(c);
+}
+
+int pw_analyse(pw_ctx *c, const pw_model *mm, const pw_image *in, const pw_codec_opts *o,
+               int32_t *q) {
+  if (!c || !mm || !in || !q) return PW_EINVAL;
+  Model &m = const_cast<pw_model *>(mm)->m;
+  Geometry g;
+  int s = image_geo(c, m, *in, o, g);
+  if (s) return s;
+  if (!g.lossless && !(o && o->q > 0.f)) { set_last_error("quantiser step must be > 0"); return PW_EINVAL; }
+  Plan *pl;
+  if ((s = get_plan(c, m, g, 1, "ana", false, &pl))) return s;
+  const int bps = g.bitdepth > 8 ? 2 : 1;
+  const int64_t row = (int64_t)g.W * g.nc * bps, img = row * g.H;
+  if ((s = pl->d_img.ensure((size_t)img))) return s;
+  cudaStream_t st = c->stream;
+  const int64_t rs = in->stride_bytes ? in->stride_bytes : row;
+  PW_CUDA_TRY(cudaMemcpy2DAsync(pl->d_img.p, row, in->data, rs, row, g.H,
+                                in->is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  launch_colour_in(pl->d_img.p, img, row, 1, g.nc, g.H, g.W, g.Hp, g.Wp, g.lossless, g.bitdepth,
+                   pl->ws.planes, st);
+  bump(c);
+  if ((s = lift_forward_planes(c, m, g, pl->ws, pl->ws.planes))) return s;
+  const float d = g.lossless ? 1.f : 1.f / o->q;
+  SbTable tb = make_sbtable(g, g.nc);
+  launch_quant_all(pl->ws.Yf, pl->ws.Q, (int64_t)g.nc * g.plane_elems, tb, d, d, st);
+  bump(c);
+  PW_CUDA_TRY(cudaMemcpyAsync(q, pl->ws.Q, (size_t)g.nc * g.plane_elems * 4,
+                              cudaMemcpyDeviceToHost, st));
+  return finish(c);
+}
+
+int pw_encode_latent(pw_ctx *c, const pw_model *mm, const int32_t *q, int width, int height,
+                     int channels, int bitdepth, int colour, const pw_codec_opts *o,
+                     uint8_t **bs, size_t *n) {
+  if (!c || !mm || !q || !bs || !n || (channels != 1 && channels != 3) || width < 1 ||
+      height < 1 || colour < 0 || colour > 3)
+    return PW_EINVAL;
+  Model &m = const_cast<pw_model *>(mm)->m;
+  const int lossless = o && o->lossless ? 1 : 0;
+  if (!lossless && !(o && o->q > 0.f)) { set_last_error("quantiser step must be > 0"); return PW_EINVAL; }
+  const int chunk = (o && o->chunk_symbols > 0) ? o->chunk_symbols : 16384;
+  Geometry g;
+  g.build(height, width, channels, m.levels, colour, bitdepth, lossless, m.ll_mode, chunk);
+  Plan *pl;
+  int s;
+  if ((s = get_plan(c, m, g, 1, "lat", false, &pl))) return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.Q, q, (size_t)channels * g.plane_elems * 4,
+                              cudaMemcpyHostToDevice, c->stream));
+  const float d = lossless ? 1.f : 1.f / o->q;
+  return encode_from_latent(c, m, *pl, 1, d, d, bs, n);
+}
+
+}  // extern "C"

@@ -1,0 +1,346 @@
+// Decode / encode drivers of the pWave++ path.
+//
+// Decode (Sections 3.1, 3.2): parse the streams on the device, build the CDF
+// table bank, then for every subband in coding order run the ConvLSTM
+// context prediction (subbands 2..13) and the four coding steps (context
+// fusion net -> entropy parameters -> table indices -> rANS decoding of the
+// step's positions), then dequantise, run the inverse lifting transform
+// level by level and convert colour. Encoding runs the same context kernels
+// on the fully known latent (each step's net masks the positions of later
+// steps, so it sees exactly what the decoder sees) and rANS-encodes.
+#include <algorithm>
+#include <cstring>
+
+#include "codec.h"
+#include "ctx_tc.h"
+#include "prof.h"
+
+namespace pw {
+
+static inline void bump(pw_ctx *ctx, int n = 1) { ctx->launches += (uint64_t)n; }
+
+// ---------------------------------------------------------------------------
+void Geometry::build(int H_, int W_, int nc_, int levels_, int colour_, int bitdepth_,
+                     int lossless_, int ll_ar_, int chunk_) {
+  H = H_; W = W_; nc = nc_; levels = levels_; colour = colour_; bitdepth = bitdepth_;
+  lossless = lossless_; ll_ar = ll_ar_; chunk = chunk_;
+  const int mult = 1 << levels;
+  Hp = (H + mult - 1) / mult * mult;
+  Wp = (W + mult - 1) / mult * mult;
+  nsb = 3 * levels + 1;
+  sh.clear(); sw.clear(); soff.clear();
+  sh.push_back(Hp >> levels); sw.push_back(Wp >> levels);
+  for (int lv = levels; lv >= 1; --lv)
+    for (int o = 0; o < 3; ++o) { sh.push_back(Hp >> lv); sw.push_back(Wp >> lv); }
+  int64_t acc = 0;
+  for (int i = 0; i < nsb; ++i) { soff.push_back(acc); acc += (int64_t)sh[i] * sw[i]; }
+  plane_elems = acc;
+  ioff.assign(nsb * 4, 0);
+  acc = 0;
+  for (int i = 0; i < nsb; ++i)
+    for (int k = 0; k < 4; ++k) {
+      ioff[i * 4 + k] = acc;
+      acc += (i == 0 && ll_ar) ? (k == 0 ? (int64_t)sh[0] * sw[0] : 0)
+                               : step_count(sh[i], sw[i], k);
+    }
+  chunks.clear();
+  group_first.assign(nsb * 4, -1);
+  group_count.assign(nsb * 4, 0);
+  for (int i = 0; i < nsb; ++i) {
+    if (i == 0 && ll_ar) {
+      const int n = sh[0] * sw[0];
+      if (n) {
+        group_first[0] = (int)chunks.size();
+        group_count[0] = 1;
+        chunks.push_back({0, -1, 0u, (uint32_t)n, 1});
+      }
+      continue;
+    }
+    for (int k = 0; k < 4; ++k) {
+      const int n = step_count(sh[i], sw[i], k);
+      group_first[i * 4 + k] = (int)chunks.size();
+      for (int f = 0; f < n; f += chunk) {
+        const int cnt = std::min(chunk, n - f);
+        chunks.push_back({i, k, (uint32_t)f, (uint32_t)cnt, (uint16_t)chunk_lanes(cnt)});
+      }
+      group_count[i * 4 + k] = (int)chunks.size() - group_first[i * 4 + k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+int Workspace::alloc(const Geometry &g, int P_, int C, bool params, bool bf16) {
+  release();
+  P = P_;
+  const int64_t pe = (int64_t)P * g.Hp * g.Wp;
+  const int64_t big = (int64_t)P * g.sh.back() * g.sw.back();  // largest subband
+  auto al = [](int64_t b) { return (b + 255) / 256 * 256; };
+  std::vector<std::pair<void **, int64_t>> parts = {
+      {(void **)&Q, al(pe * 4)},        {(void **)&Yf, al(pe * 4)},
+      {(void **)&idx, al(pe * 4)},      {(void **)&T0, al(pe * 4)},
+      {(void **)&T1, al(pe * 4)},       {(void **)&T2, al(pe * 4)},
+      {(void **)&planes, al(pe * 4)}};
+  if (!bf16) {
+    parts.push_back({(void **)&X, al(big * 2 * C * 4)});
+    parts.push_back({(void **)&X2, al(big * 2 * C * 4)});
+    parts.push_back({(void **)&Z, al(big * C * 4)});
+    parts.push_back({(void **)&U, al(big * 2 * C * 4)});
+    parts.push_back({(void **)&V, al(big * C * 4)});
+    parts.push_back({(void **)&Z2, al(big * C * 4)});
+  }
+  parts.push_back({(void **)&Cst[0], al(big * C * 4)});
+  parts.push_back({(void **)&Cst[1], al(big * C * 4)});
+  if (params) {
+    parts.push_back({(void **)&mu, al(pe * 4)});
+    parts.push_back({(void **)&sg, al(pe * 4)});
+  }
+  int64_t tot = 0;
+  for (auto &p : parts) tot += p.second;
+  if (cudaMalloc(&base, (size_t)tot) != cudaSuccess) {
+    base = nullptr;
+    set_last_error("workspace allocation failed");
+    return PW_ENOMEM;
+  }
+  bytes = (size_t)tot;
+  int64_t o = 0;
+  for (auto &p : parts) { *p.first = base + o; o += p.second; }
+  if (bf16) {
+    int s = tc_workspace_alloc(this, g, C);
+    if (s != PW_OK) return s;
+  }
+  return PW_OK;
+}
+
+void Workspace::release() {
+  if (tc) tc_workspace_free(this);
+  if (base) cudaFree(base);
+  base = nullptr;
+  bytes = 0;
+}
+
+// ---------------------------------------------------------------------------
+// ConvLSTM context prediction for subband sb >= 1 (Section 3.2). The cell
+// state ping-pongs between ws.Cst[0] and ws.Cst[1] (the previous state is
+// read at half resolution when the level changes).
+int run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb) {
+  const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P;
+  const int up = g.sh[sb - 1] < h ? 1 : 0;
+  const int first = sb == 1 ? 1 : 0;
+  if (first) ws.lstm_cur = 0;
+  const int cur = ws.lstm_cur;
+  const int32_t *sprev = ws.Q + (int64_t)P * g.soff[sb - 1];
+  if (ctx->precision == PW_PREC_BF16) {
+    int s = tc_run_lstm(ctx, m, g, ws, sb, sprev, up, first, cur);
+    ws.lstm_cur = cur ^ 1;
+    return s;
+  }
+  const double pix = (double)P * h * w;
+  {
+    ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 3.0 * C * 4));
+    launch_lstm_in(sprev, ws.X2, 2 * C, C, m.lstm_we, m.lstm_be, ws.X, P, h, w, C, up, first,
+                   ctx->stream);
+  }
+  ConvParams a{};
+  a.in = ws.X; a.in_cs = 2 * C; a.in_co = 0; a.cin = 2 * C;
+  a.w = m.lstm_wg; a.b = m.lstm_bg; a.cout_total = 4 * C;
+  a.P = P; a.H = h; a.W = w;
+  a.out = ws.X2; a.out_cs = 2 * C; a.out_co = C;
+  a.c_prev = ws.Cst[cur]; a.c_new = ws.Cst[cur ^ 1]; a.up = up; a.first = first; a.C = C;
+  {
+    ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * 2 * C * 4 * C, pix * 4.0 * (2 * C + 3 * C));
+    launch_conv_simt(3, a, EPI_LSTM, ctx->stream);
+  }
+  ws.lstm_cur = cur ^ 1;
+  bump(ctx, 2);
+  return PW_OK;
+}
+
+// One coding step's context fusion net -> packed table indices.
+int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
+                     int step, bool /*decoding*/) {
+  const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P;
+  StepNetDev &n = (sb == 0) ? m.ll[step] : m.sb[step];
+  const int32_t *Qi = ws.Q + (int64_t)P * g.soff[sb];
+  uint32_t *idx = ws.idx + (int64_t)P * g.ioff[sb * 4 + step];
+  const int64_t nk = step_count(h, w, step);
+  float *mu = ws.mu ? ws.mu + (int64_t)P * g.soff[sb] : nullptr;
+  float *sgp = ws.sg ? ws.sg + (int64_t)P * g.soff[sb] : nullptr;
+  if (ctx->precision == PW_PREC_BF16)
+    return tc_run_step(ctx, m, g, ws, sb, step, n, Qi, idx, nk, mu, sgp);
+  cudaStream_t st = ctx->stream;
+  if (sb == 0 && step == 0) {
+    cudaMemsetAsync(ws.X2, 0, (size_t)P * h * w * 2 * C * 4, st);  // l = 0 for LL
+  }
+  const double pix = (double)P * h * w;
+  auto conv = [&](int ks, const ConvParams &cp, int epi) {
+    const double fl = 2.0 * pix * ks * ks * cp.cin * cp.cout_total;
+    const double by = pix * 4.0 * (cp.cin + cp.cout_total + (cp.res ? cp.cout_total : 0));
+    ProfScope ps(ctx, ks == 3 ? KC_CONV3 : KC_CONV1, fl, by);
+    launch_conv_simt(ks, cp, epi, st);
+  };
+  ConvParams a{};
+  a.P = P; a.H = h; a.W = w;
+  auto base = [&]() {
+    ConvParams b{};
+    b.P = P; b.H = h; b.W = w;
+    return b;
+  };
+  if (step == 0) {
+    a = base();  // z = 1x1(l)
+    a.in = ws.X2; a.in_cs = 2 * C; a.in_co = C; a.cin = C;
+    a.w = n.win; a.b = n.bin; a.cout_total = C;
+    a.out = ws.Z; a.out_cs = C;
+    conv(1, a, EPI_STORE);
+    a = base();  // u = lrelu(1x1 z)
+    a.in = ws.Z; a.in_cs = C; a.cin = C; a.w = n.w1; a.b = n.b1; a.cout_total = C;
+    a.out = ws.U; a.out_cs = C; a.act = 1;
+    conv(1, a, EPI_STORE);
+    {
+      ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * 8.0 * C);
+      launch_dw3x3(ws.U, n.wdw, n.bdw, ws.V, P, h, w, C, st);
+    }
+    a = base();  // z2 = z + 1x1(v)
+    a.in = ws.V; a.in_cs = C; a.cin = C; a.w = n.w2; a.b = n.b2; a.cout_total = C;
+    a.out = ws.Z2; a.out_cs = C; a.res = ws.Z; a.res_cs = C;
+    conv(1, a, EPI_STORE);
+    a = base();  // u2 = lrelu(1x1(C->2C) z2)
+    a.in = ws.Z2; a.in_cs = C; a.cin = C; a.w = n.w3; a.b = n.b3; a.cout_total = 2 * C;
+    a.out = ws.U; a.out_cs = 2 * C; a.act = 1;
+    conv(1, a, EPI_STORE);
+    a = base();  // z3 = z2 + 1x1(2C->C) u2; head
+    a.in = ws.U; a.in_cs = 2 * C; a.cin = 2 * C; a.w = n.w4; a.b = n.b4; a.cout_total = C;
+    a.res = ws.Z2; a.res_cs = C;
+    a.wh = n.wh; a.bh = n.bh; a.step = 0; a.idx = idx; a.idx_stride = nk;
+    a.mu_out = mu; a.sg_out = sgp;
+    conv(1, a, EPI_HEAD);
+    bump(ctx, 6);
+  } else {
+    {
+      ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 4.0 * C));
+      launch_masked_in(Qi, n.wa, n.ba, ws.X2, 2 * C, P, h, w, C, step, st);
+    }
+    a = base();  // z = 1x1(2C->C)[a, l]
+    a.in = ws.X2; a.in_cs = 2 * C; a.cin = 2 * C; a.w = n.wz; a.b = n.bz; a.cout_total = C;
+    a.out = ws.Z; a.out_cs = C;
+    conv(1, a, EPI_STORE);
+    a = base();  // u = lrelu(conv3x3 z)
+    a.in = ws.Z; a.in_cs = C; a.cin = C; a.w = n.c1w; a.b = n.c1b; a.cout_total = C;
+    a.out = ws.U; a.out_cs = C; a.act = 1;
+    conv(3, a, EPI_STORE);
+    a = base();  // z' = z + conv3x3 u; head
+    a.in = ws.U; a.in_cs = C; a.cin = C; a.w = n.c2w; a.b = n.c2b; a.cout_total = C;
+    a.res = ws.Z; a.res_cs = C;
+    a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
+    a.mu_out = mu; a.sg_out = sgp;
+    conv(3, a, EPI_HEAD);
+    bump(ctx, 4);
+  }
+  return PW_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Lifting drivers (Section 3.1, Fig. 2). Subbands in ws.Yf ([sb][P][h][w]).
+static PlaneAcc acc(float *p, int64_t ps, int64_t rs, int64_t cs = 1) { return {p, ps, rs, cs}; }
+
+// One lifting half-step: CNN (9*16 + 9*16*16 + 9*16 MACs per sample) plus
+// the linear part; algorithmic bytes: read src and other, write out (+copy).
+static void lift_step(pw_ctx *ctx, const LiftStepParams &a) {
+  const double n = (double)a.P * a.H * a.W;
+  ProfScope ps(ctx, KC_LIFT, 2.0 * n * (9 * 16 + 9 * 16 * 16 + 9 * 16),
+               n * 4.0 * (a.copy.p ? 4 : 3));
+  launch_lift_step(a, ctx->stream);
+}
+
+int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
+                        float *dst) {
+  const int P = ws.P, L = g.levels;
+  cudaStream_t st = ctx->stream;
+  const int rP = g.lossless ? 1 : 0, rU = g.lossless ? 2 : 0;
+  float *cur = ws.Yf;  // LL_L, plane stride h*w
+  for (int lv = L; lv >= 1; --lv) {
+    const int h = g.Hp >> lv, w = g.Wp >> lv;
+    const int64_t hw = (int64_t)h * w;
+    const int iHL = 1 + 3 * (L - lv);
+    float *HL = ws.Yf + (int64_t)P * g.soff[iHL];
+    float *LH = ws.Yf + (int64_t)P * g.soff[iHL + 1];
+    float *HH = ws.Yf + (int64_t)P * g.soff[iHL + 2];
+    float *Lo = ws.T0, *Hi = ws.T0 + (int64_t)P * 2 * hw, *E = ws.T1;
+    float *X = (lv == 1) ? dst : ws.T2;
+    auto colinv = [&](float *Lb, float *Hb, float *out) {
+      LiftStepParams a{};
+      a.P = P; a.H = h; a.W = w; a.dir = 1;
+      a.src = acc(Hb, hw, w); a.other = acc(Lb, hw, w); a.out = acc(E, hw, w);
+      a.copy = acc(nullptr, 0, 0); a.net = m.lift[1][1]; a.lin = LIN_U53; a.sign = -1;
+      a.round = rU;
+      lift_step(ctx, a);
+      a.src = acc(E, hw, w); a.other = acc(Hb, hw, w);
+      a.out = acc(out + w, 2 * hw, 2 * w); a.copy = acc(out, 2 * hw, 2 * w);
+      a.net = m.lift[1][0]; a.lin = LIN_P53; a.sign = 1; a.round = rP;
+      lift_step(ctx, a);
+    };
+    colinv(cur, LH, Lo);
+    colinv(HL, HH, Hi);
+    LiftStepParams a{};
+    a.P = P; a.H = 2 * h; a.W = w; a.dir = 0;
+    a.src = acc(Hi, 2 * hw, w); a.other = acc(Lo, 2 * hw, w); a.out = acc(E, 2 * hw, w);
+    a.copy = acc(nullptr, 0, 0); a.net = m.lift[0][1]; a.lin = LIN_U53; a.sign = -1;
+    a.round = rU;
+    lift_step(ctx, a);
+    a.src = acc(E, 2 * hw, w); a.other = acc(Hi, 2 * hw, w);
+    a.out = acc(X + 1, 4 * hw, 2 * w, 2); a.copy = acc(X, 4 * hw, 2 * w, 2);
+    a.net = m.lift[0][0]; a.lin = LIN_P53; a.sign = 1; a.round = rP;
+    lift_step(ctx, a);
+    bump(ctx, 6);
+    cur = X;
+  }
+  return PW_OK;
+}
+
+int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
+                        const float *src) {
+  const int P = ws.P, L = g.levels;
+  cudaStream_t st = ctx->stream;
+  const int rP = g.lossless ? 1 : 0, rU = g.lossless ? 2 : 0;
+  float *cur = const_cast<float *>(src);
+  for (int lv = 1; lv <= L; ++lv) {
+    const int h = g.Hp >> lv, w = g.Wp >> lv;
+    const int64_t hw = (int64_t)h * w;
+    const int iHL = 1 + 3 * (L - lv);
+    float *HL = ws.Yf + (int64_t)P * g.soff[iHL];
+    float *LH = ws.Yf + (int64_t)P * g.soff[iHL + 1];
+    float *HH = ws.Yf + (int64_t)P * g.soff[iHL + 2];
+    float *Lo = ws.T0, *Hi = ws.T0 + (int64_t)P * 2 * hw;
+    float *nxt = (lv == L) ? ws.Yf : ((lv & 1) ? ws.T1 : ws.T2);
+    LiftStepParams a{};
+    a.P = P; a.H = 2 * h; a.W = w; a.dir = 0; a.copy = acc(nullptr, 0, 0);
+    // rows: Hi = odd - P(even); Lo = even + U(Hi)
+    a.src = acc(cur, 4 * hw, 2 * w, 2); a.other = acc(cur + 1, 4 * hw, 2 * w, 2);
+    a.out = acc(Hi, 2 * hw, w); a.net = m.lift[0][0]; a.lin = LIN_P53; a.sign = -1;
+    a.round = rP;
+    lift_step(ctx, a);
+    a.src = acc(Hi, 2 * hw, w); a.other = acc(cur, 4 * hw, 2 * w, 2);
+    a.out = acc(Lo, 2 * hw, w); a.net = m.lift[0][1]; a.lin = LIN_U53; a.sign = 1;
+    a.round = rU;
+    lift_step(ctx, a);
+    // columns on Lo -> (LL, LH), on Hi -> (HL, HH)
+    auto colfwd = [&](float *Sb, float *lowout, float *highout) {
+      LiftStepParams b{};
+      b.P = P; b.H = h; b.W = w; b.dir = 1; b.copy = acc(nullptr, 0, 0);
+      b.src = acc(Sb, 2 * hw, 2 * w); b.other = acc(Sb + w, 2 * hw, 2 * w);
+      b.out = acc(highout, hw, w); b.net = m.lift[1][0]; b.lin = LIN_P53; b.sign = -1;
+      b.round = rP;
+      lift_step(ctx, b);
+      b.src = acc(highout, hw, w); b.other = acc(Sb, 2 * hw, 2 * w);
+      b.out = acc(lowout, hw, w); b.net = m.lift[1][1]; b.lin = LIN_U53; b.sign = 1;
+      b.round = rU;
+      lift_step(ctx, b);
+    };
+    colfwd(Lo, nxt, LH);
+    colfwd(Hi, HL, HH);
+    bump(ctx, 6);
+    cur = nxt;
+  }
+  return PW_OK;
+}
+
+}  // namespace pw

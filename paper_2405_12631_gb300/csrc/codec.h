@@ -1,0 +1,137 @@
+// Host-side objects of libpwave: context, model, stream header, plans.
+#pragma once
+
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ctx_kernels.cuh"
+#include "lift_kernels.cuh"
+#include "pw_internal.cuh"
+
+struct pw_ctx;
+
+namespace pw {
+
+struct StepNetDev {
+  // step 1 (DepthConvBlock net)
+  float *win = nullptr, *bin = nullptr, *w1 = nullptr, *b1 = nullptr, *wdw = nullptr,
+        *bdw = nullptr, *w2 = nullptr, *b2 = nullptr, *w3 = nullptr, *b3 = nullptr,
+        *w4 = nullptr, *b4 = nullptr;
+  // steps 2-4 (residual-block nets)
+  float *wa = nullptr, *ba = nullptr, *wz = nullptr, *bz = nullptr, *c1w = nullptr,
+        *c1b = nullptr, *c2w = nullptr, *c2b = nullptr;
+  // head
+  float *wh = nullptr, *bh = nullptr;
+};
+
+// Tensor-core (BF16) copies of the context-model weights, see ctx_tc.cu.
+struct TcWeights;
+
+struct Model {
+  pw_ctx *ctx = nullptr;
+  int levels = 4, C = 32, F = 16, ll_mode = 0;
+  uint64_t hash = 0;
+  std::vector<float *> allocs;
+  std::map<std::string, std::vector<float>> host;
+  LiftNetDev lift[2][2];   // [row, col][P, U]
+  LiftNetDev tlift[2];     // [P, U]
+  float *lstm_we = nullptr, *lstm_be = nullptr, *lstm_wg = nullptr, *lstm_bg = nullptr;
+  StepNetDev sb[4], ll[4];
+  float *ar_w5 = nullptr, *ar_b5 = nullptr, *ar_w1 = nullptr, *ar_b1 = nullptr,
+        *ar_wh = nullptr, *ar_bh = nullptr;
+  TcWeights *tc = nullptr;
+  int load(pw_ctx *c, const void *blob, size_t n);
+  int ensure_tc();   // builds tc on first use (BF16 contexts)
+  void free_tc();
+  ~Model();
+};
+
+#pragma pack(push, 1)
+struct StreamHeader {
+  char magic[4];
+  uint16_t version, flags;
+  uint32_t width, height;
+  uint8_t ncomp, levels, bitdepth, colour;
+  float delta_l, delta_h;
+  uint16_t T;
+  uint8_t log2m, lanes;
+  uint32_t chunk_symbols, n_chunks;
+  uint64_t model_hash;
+  uint32_t payload_bytes;
+  uint8_t reserved[12];
+};
+#pragma pack(pop)
+static_assert(sizeof(StreamHeader) == 64, "stream header is 64 bytes");
+
+enum : uint16_t { FLAG_LOSSLESS = 1, FLAG_LL_AR = 2, FLAG_PREC_SHIFT = 2 };
+
+// One chunk of the per-component layout (same for every image of a class).
+struct ChunkTpl {
+  int sb, step;            // step -1: single-state autoregressive LL chunk
+  uint32_t first, count;
+  uint16_t lanes;
+};
+
+// Geometry shared by all images of a plan.
+struct Geometry {
+  int H = 0, W = 0, Hp = 0, Wp = 0, nc = 1, levels = 4, colour = 0, bitdepth = 8;
+  int lossless = 0, ll_ar = 0, chunk = 16384;
+  int nsb = 13;
+  std::vector<int> sh, sw;          // subband sizes in coding order
+  std::vector<int64_t> soff;        // per-plane element offset of subband i
+  int64_t plane_elems = 0;          // Hp * Wp
+  std::vector<int64_t> ioff;        // [sb * 4 + step] per-plane offset in idx arena
+  std::vector<ChunkTpl> chunks;     // per-component chunk list (stream order)
+  std::vector<int> group_first;     // [sb * 4 + step] first chunk index, or -1
+  std::vector<int> group_count;     // [sb * 4 + step]
+  void build(int H, int W, int nc, int levels, int colour, int bitdepth, int lossless,
+             int ll_ar, int chunk);
+};
+
+// Device buffers for a batch of planes of one geometry.
+struct Workspace {
+  int P = 0;
+  size_t bytes = 0;
+  uint8_t *base = nullptr;
+  int32_t *Q = nullptr;        // quantised latent, [sb][P][h][w]
+  float *Yf = nullptr;         // float latent (dequantised / forward output)
+  uint32_t *idx = nullptr;     // packed table indices, [sb*4+step][P][n]
+  float *X = nullptr, *X2 = nullptr, *Z = nullptr, *U = nullptr, *V = nullptr, *Z2 = nullptr;
+  float *Cst[2] = {nullptr, nullptr};
+  float *T0 = nullptr, *T1 = nullptr, *T2 = nullptr;  // lifting temporaries
+  float *planes = nullptr;     // component planes [P][Hp][Wp]
+  float *mu = nullptr, *sg = nullptr;  // optional parameter outputs [P][Hp*Wp]
+  void *tc = nullptr;          // BF16 activations (tensor-core path)
+  int lstm_cur = 0;            // which Cst holds the current cell state
+  int alloc(const Geometry &g, int P, int C, bool params, bool bf16);
+  void release();
+  ~Workspace() { release(); }
+};
+
+// Host entry points implemented in codec.cu (all on ctx's stream).
+int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
+                     int step, bool decoding);
+int run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb);
+int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
+                        float *dst_planes);
+int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
+                        const float *src_planes);
+
+}  // namespace pw
+
+struct pw_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int precision = PW_PREC_FP32;
+  uint16_t *bank = nullptr;        // CDF table bank (built by k_cdf_bank)
+  uint32_t *status = nullptr;      // device status word
+  uint64_t launches = 0;
+  void *plan_cache = nullptr;      // cached workspaces per geometry (api.cu)
+  void *prof = nullptr;            // per-kernel-class event timing (prof.cpp)
+};
+
+struct pw_model {
+  pw::Model m;
+};

@@ -1,0 +1,79 @@
+// Declarations of the context-model, lifting and entropy kernels' launchers.
+#pragma once
+#include "pw_internal.cuh"
+
+namespace pw {
+
+enum { EPI_STORE = 0, EPI_LSTM = 1, EPI_HEAD = 2 };
+
+// Parameters of the generic NHWC convolution (FP32 SIMT path).
+struct ConvParams {
+  const float *in;      // [P, H, W, in_cs], channels [in_co, in_co + cin)
+  int in_cs, in_co, cin;
+  const float *w;       // [KS*KS][cin][cout_total]
+  const float *b;       // [cout_total]
+  int cout_total;
+  int P, H, W;
+  // EPI_STORE: out = act(acc + b + res)
+  float *out;
+  int out_cs, out_co;
+  int act;
+  const float *res;
+  int res_cs, res_co;
+  // EPI_LSTM: gates -> c_new, h (h written to out at out_cs/out_co)
+  const float *c_prev;  // [P, H >> up, W >> up, C]
+  float *c_new;         // [P, H, W, C]
+  int up, first, C;
+  // EPI_HEAD: z' = res + acc + b; (mu, rho) = wh z' + bh at step positions
+  const float *wh;      // [2][cout_total]
+  const float *bh;      // [2]
+  int step;
+  uint32_t *idx;        // packed indices, [P][idx_stride] in step order
+  int64_t idx_stride;
+  float *mu_out, *sg_out;  // optional [P, H, W]
+};
+
+void launch_conv_simt(int ks, const ConvParams &a, int epi, cudaStream_t st);
+// Set when a launcher found no kernel for its arguments (checked and cleared
+// by the host drivers).
+bool &launch_failed();
+void launch_lstm_in(const int32_t *s_prev, const float *h_prev, int h_cs, int h_co,
+                    const float *we, const float *be, float *X, int P, int H, int W, int C,
+                    int up, int first, cudaStream_t st);
+void launch_masked_in(const int32_t *s, const float *wa, const float *ba, float *out,
+                      int out_cs, int P, int H, int W, int C, int step, cudaStream_t st);
+void launch_dw3x3(const float *in, const float *w, const float *b, float *out, int P, int H,
+                  int W, int C, cudaStream_t st);
+
+// entropy.cu
+struct DecChunk {
+  const uint8_t *data;
+  uint32_t nbytes;
+  uint32_t count;
+  uint32_t first;
+  uint16_t lanes;
+  uint16_t plane;
+};
+struct EncChunk {
+  uint64_t sym_base;     // element offset of the chunk's first symbol (idx / vals)
+  uint64_t scratch_end;  // word index one past the chunk's scratch region
+  uint32_t count, lanes;
+};
+void launch_cdf_bank(uint16_t *bank, cudaStream_t st);
+void launch_rans_decode(const DecChunk *chunks, int nchunks, const uint16_t *bank,
+                        const uint32_t *idx, int64_t idx_stride, int32_t *out,
+                        int64_t out_stride, int h, int w, int step, uint32_t *status,
+                        cudaStream_t st);
+void launch_rans_count_ops(const EncChunk *chunks, int nchunks, const uint32_t *idx,
+                           const int32_t *vals, uint32_t *ops, cudaStream_t st);
+void launch_rans_encode(const EncChunk *chunks, int nchunks, const uint16_t *bank,
+                        const uint32_t *idx, const int32_t *vals, uint16_t *scratch,
+                        uint32_t *states, uint32_t *nwords, uint32_t *status,
+                        cudaStream_t st);
+void launch_rans_pack(const EncChunk *chunks, int nchunks, const uint16_t *scratch,
+                      const uint32_t *states, const uint32_t *nwords,
+                      const uint64_t *out_off, uint8_t *payload, cudaStream_t st);
+void launch_pack_index(const float *mu, const float *s, int64_t n, int is_sigma,
+                       uint32_t *idx, cudaStream_t st);
+
+}  // namespace pw

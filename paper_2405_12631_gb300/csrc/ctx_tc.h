@@ -1,0 +1,13 @@
+// Tensor-core (tcgen05, BF16) context-model path: declarations.
+#pragma once
+#include "codec.h"
+
+namespace pw {
+int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C);
+void tc_workspace_free(Workspace *ws);
+int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
+                const int32_t *sprev, int up, int first, int cur);
+int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb, int step,
+                StepNetDev &n, const int32_t *Qi, uint32_t *idx, int64_t nk, float *mu,
+                float *sg);
+}  // namespace pw

@@ -1,0 +1,266 @@
+// CNN lifting wavelet transform (Section 3.1, Fig. 2), temporal lifting
+// (Section 3.3), colour conversion and the scalar quantiser.
+//
+// One lifting half-step computes v = lin(src) + CNN(src) along a direction
+// and writes out = other + sign * v; the inverse transform runs the steps
+// of the forward transform backwards, so it reconstructs perfectly for any
+// network weights. The CNN residual is conv3x3(1->16), tanh,
+// conv3x3(16->16), tanh, conv3x3(16->1) with zero padding, fused in one
+// kernel per 16x16 output tile (halo of 3, all activations in shared
+// memory). Linear parts: LeGall 5/3 (P = (s[n] + s[n+1]) / 2,
+// U = (s[n-1] + s[n]) / 4, edges clamped = whole-sample symmetric) for the
+// spatial transform; Haar (P = s, U = s / 2) for the temporal one. Integer
+// mode (lossless) rounds P with floor(v) and U with floor(v + 1/2), which
+// makes the transform the JPEG 2000 reversible 5/3 when the CNN is zero.
+#include "pw_internal.cuh"
+#include "lift_kernels.cuh"
+
+namespace pw {
+
+constexpr int LT = 16;            // output tile
+constexpr int LF = 16;            // CNN channels
+constexpr int L1 = LT + 4;        // layer-1 region (20)
+constexpr int L2 = LT + 2;        // layer-2 region (18)
+constexpr int LI = LT + 6;        // input region (22)
+
+struct LiftSmem {
+  float in[LI * LI];
+  float a1[L1 * L1 * LF];
+  float a2[L2 * L2 * LF];
+  float w1[LF * 9], b1[LF], w2[LF * LF * 9], b2[LF], w3[LF * 9], b3[1];
+};
+
+__device__ __forceinline__ float acc_get(const PlaneAcc &a, int p, int y, int x) {
+  return a.p[(int64_t)p * a.ps + (int64_t)y * a.rs + (int64_t)x * a.cs];
+}
+__device__ __forceinline__ void acc_set(const PlaneAcc &a, int p, int y, int x, float v) {
+  a.p[(int64_t)p * a.ps + (int64_t)y * a.rs + (int64_t)x * a.cs] = v;
+}
+
+__global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
+  extern __shared__ float smem_raw[];
+  LiftSmem &S = *reinterpret_cast<LiftSmem *>(smem_raw);
+  const int t = threadIdx.x;
+  const int p = blockIdx.z;
+  const int tiles_x = (a.W + LT - 1) / LT;
+  const int y0 = (blockIdx.x / tiles_x) * LT, x0 = (blockIdx.x % tiles_x) * LT;
+  const bool cnn = a.net.w1 != nullptr;
+
+  for (int e = t; e < LI * LI; e += 256) {
+    int yy = y0 + e / LI - 3, xx = x0 + e % LI - 3;
+    S.in[e] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? acc_get(a.src, p, yy, xx) : 0.f;
+  }
+  if (cnn) {
+    for (int e = t; e < LF * 9; e += 256) { S.w1[e] = a.net.w1[e]; S.w3[e] = a.net.w3[e]; }
+    for (int e = t; e < LF * LF * 9; e += 256) S.w2[e] = a.net.w2[e];
+    if (t < LF) { S.b1[t] = a.net.b1[t]; S.b2[t] = a.net.b2[t]; }
+    if (t == 0) S.b3[0] = a.net.b3[0];
+  }
+  __syncthreads();
+  float r_out = 0.f;
+  if (cnn) {
+    // layer 1 on the 20 x 20 region (origin y0 - 2, x0 - 2)
+    for (int e = t; e < L1 * L1; e += 256) {
+      const int ly = e / L1, lx = e % L1;
+      const int yy = y0 + ly - 2, xx = x0 + lx - 2;
+      const bool inside = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+      float iv[9];
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) iv[tap] = S.in[(ly + tap / 3) * LI + lx + tap % 3];
+#pragma unroll
+      for (int c = 0; c < LF; ++c) {
+        float v = S.b1[c];
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) v = fmaf(S.w1[c * 9 + tap], iv[tap], v);
+        S.a1[e * LF + c] = inside ? tanhf(v) : 0.f;
+      }
+    }
+    __syncthreads();
+    // layer 2 on the 18 x 18 region (origin y0 - 1, x0 - 1)
+    for (int e = t; e < L2 * L2; e += 256) {
+      const int ly = e / L2, lx = e % L2;
+      const int yy = y0 + ly - 1, xx = x0 + lx - 1;
+      const bool inside = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+      float acc[LF];
+#pragma unroll
+      for (int c = 0; c < LF; ++c) acc[c] = S.b2[c];
+      for (int tap = 0; tap < 9; ++tap) {
+        const float *src = &S.a1[((ly + tap / 3) * L1 + lx + tap % 3) * LF];
+#pragma unroll
+        for (int ci = 0; ci < LF; ++ci) {
+          const float v = src[ci];
+#pragma unroll
+          for (int c = 0; c < LF; ++c) acc[c] = fmaf(S.w2[(c * LF + ci) * 9 + tap], v, acc[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < LF; ++c) S.a2[e * LF + c] = inside ? tanhf(acc[c]) : 0.f;
+    }
+    __syncthreads();
+    // layer 3 on the 16 x 16 outputs
+    {
+      const int ly = t / LT, lx = t % LT;
+      float v = S.b3[0];
+      for (int tap = 0; tap < 9; ++tap) {
+        const float *src = &S.a2[((ly + tap / 3) * L2 + lx + tap % 3) * LF];
+#pragma unroll
+        for (int ci = 0; ci < LF; ++ci) v = fmaf(S.w3[ci * 9 + tap], src[ci], v);
+      }
+      r_out = v;
+    }
+  }
+  const int ly = t / LT, lx = t % LT;
+  const int y = y0 + ly, x = x0 + lx;
+  if (y >= a.H || x >= a.W) return;
+  const float s0 = S.in[(ly + 3) * LI + lx + 3];
+  float lin;
+  if (a.lin == LIN_P53) {
+    const float s1 = a.dir == 0 ? (x + 1 < a.W ? S.in[(ly + 3) * LI + lx + 4] : s0)
+                                : (y + 1 < a.H ? S.in[(ly + 4) * LI + lx + 3] : s0);
+    lin = 0.5f * (s0 + s1);
+  } else if (a.lin == LIN_U53) {
+    const float sm = a.dir == 0 ? (x > 0 ? S.in[(ly + 3) * LI + lx + 2] : s0)
+                                : (y > 0 ? S.in[(ly + 2) * LI + lx + 3] : s0);
+    lin = 0.25f * (sm + s0);
+  } else if (a.lin == LIN_ID) {
+    lin = s0;
+  } else {  // LIN_HALF
+    lin = 0.5f * s0;
+  }
+  float v = lin + r_out;
+  if (a.round == 1) v = floorf(v);
+  else if (a.round == 2) v = floorf(v + 0.5f);
+  const float o = acc_get(a.other, p, y, x);
+  acc_set(a.out, p, y, x, a.sign > 0 ? o + v : o - v);
+  if (a.copy.p) acc_set(a.copy, p, y, x, s0);
+}
+
+// Component planes [B][nc][Hp][Wp] -> interleaved samples (crop, inverse
+// colour transform, floor(v + 1/2), clip).
+__global__ void k_colour_out(const float *__restrict__ planes, int B, int nc, int Hp, int Wp,
+                             int H, int W, int colour, int bitdepth, void *out,
+                             int64_t img_stride, int64_t row_stride, int out16) {
+  const int64_t n = (int64_t)B * H * W;
+  const float off = (float)(1 << (bitdepth - 1));
+  const float maxv = (float)((1 << bitdepth) - 1);
+  const float kr = 0.299f, kb = 0.114f, kg = 1.f - 0.299f - 0.114f;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % W);
+    const int y = (int)((e / W) % H);
+    const int b = (int)(e / ((int64_t)W * H));
+    const float *pl = planes + (int64_t)b * nc * Hp * Wp + (int64_t)y * Wp + x;
+    float v[3];
+    if (nc == 1) {
+      v[0] = pl[0] + off;
+    } else {
+      const float Y = pl[0] + off, Cb = pl[(int64_t)Hp * Wp], Cr = pl[2 * (int64_t)Hp * Wp];
+      if (colour == 2) {
+        const float G = Y - floorf((Cb + Cr) * 0.25f);
+        v[0] = Cr + G; v[1] = G; v[2] = Cb + G;
+      } else {
+        const float R = Y + 2.f * (1.f - kr) * Cr;
+        const float Bv = Y + 2.f * (1.f - kb) * Cb;
+        v[0] = R; v[2] = Bv; v[1] = (Y - kr * R - kb * Bv) / kg;
+      }
+    }
+    for (int c = 0; c < nc; ++c) {
+      float s = fminf(fmaxf(floorf(v[c] + 0.5f), 0.f), maxv);
+      const int64_t o = (int64_t)b * img_stride + (int64_t)y * row_stride;
+      if (out16) reinterpret_cast<uint16_t *>((uint8_t *)out + o)[(int64_t)x * nc + c] = (uint16_t)s;
+      else ((uint8_t *)out + o)[(int64_t)x * nc + c] = (uint8_t)s;
+    }
+  }
+}
+
+// Interleaved samples -> component planes [B][nc][Hp][Wp] (colour
+// transform, level shift, whole-sample mirror padding).
+__global__ void k_colour_in(const void *in, int64_t img_stride, int64_t row_stride, int in16,
+                            int B, int nc, int H, int W, int Hp, int Wp, int lossless,
+                            int bitdepth, float *__restrict__ planes) {
+  const int64_t n = (int64_t)B * Hp * Wp;
+  const float off = (float)(1 << (bitdepth - 1));
+  const float kr = 0.299f, kb = 0.114f, kg = 1.f - 0.299f - 0.114f;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % Wp);
+    const int y = (int)((e / Wp) % Hp);
+    const int b = (int)(e / ((int64_t)Wp * Hp));
+    int sy = y < H ? y : 2 * (H - 1) - y;
+    int sx = x < W ? x : 2 * (W - 1) - x;
+    sy = min(max(sy, 0), H - 1);
+    sx = min(max(sx, 0), W - 1);
+    const int64_t o = (int64_t)b * img_stride + (int64_t)sy * row_stride;
+    float s[3];
+    for (int c = 0; c < nc; ++c)
+      s[c] = in16 ? (float)reinterpret_cast<const uint16_t *>((const uint8_t *)in + o)[(int64_t)sx * nc + c]
+                  : (float)((const uint8_t *)in + o)[(int64_t)sx * nc + c];
+    float *pl = planes + (int64_t)b * nc * Hp * Wp + (int64_t)y * Wp + x;
+    const int64_t ps = (int64_t)Hp * Wp;
+    if (nc == 1) {
+      pl[0] = s[0] - off;
+    } else if (lossless) {
+      pl[0] = floorf((s[0] + 2.f * s[1] + s[2]) * 0.25f) - off;
+      pl[ps] = s[2] - s[1];
+      pl[2 * ps] = s[0] - s[1];
+    } else {
+      const float Y = kr * s[0] + kg * s[1] + kb * s[2];
+      pl[0] = Y - off;
+      pl[ps] = (s[2] - Y) / (2.f * (1.f - kb));
+      pl[2 * ps] = (s[0] - Y) / (2.f * (1.f - kr));
+    }
+  }
+}
+
+__global__ void k_quantise(const float *__restrict__ y, int64_t n, float delta,
+                           int32_t *__restrict__ q) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    q[e] = (int32_t)rintf(__fmul_rn(y[e], delta));
+}
+
+__global__ void k_dequantise(const int32_t *__restrict__ q, int64_t n, float delta,
+                             float *__restrict__ y) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = __fdiv_rn((float)q[e], delta);
+}
+
+static int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)(g > 152 * 32 ? 152 * 32 : (g < 1 ? 1 : g));
+}
+
+void launch_lift_step(const LiftStepParams &a, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_lift_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(LiftSmem));
+    attr = true;
+  }
+  const int tiles = ((a.H + LT - 1) / LT) * ((a.W + LT - 1) / LT);
+  dim3 grid(tiles, 1, a.P);
+  k_lift_step<<<grid, 256, sizeof(LiftSmem), st>>>(a);
+}
+void launch_colour_out(const float *planes, int B, int nc, int Hp, int Wp, int H, int W,
+                       int colour, int bitdepth, void *out, int64_t img_stride,
+                       int64_t row_stride, cudaStream_t st) {
+  int64_t n = (int64_t)B * H * W;
+  k_colour_out<<<grid_for(n), 256, 0, st>>>(planes, B, nc, Hp, Wp, H, W, colour, bitdepth,
+                                             out, img_stride, row_stride, bitdepth > 8);
+}
+void launch_colour_in(const void *in, int64_t img_stride, int64_t row_stride, int B, int nc,
+                      int H, int W, int Hp, int Wp, int lossless, int bitdepth, float *planes,
+                      cudaStream_t st) {
+  int64_t n = (int64_t)B * Hp * Wp;
+  k_colour_in<<<grid_for(n), 256, 0, st>>>(in, img_stride, row_stride, bitdepth > 8, B, nc,
+                                            H, W, Hp, Wp, lossless, bitdepth, planes);
+}
+void launch_quantise(const float *y, int64_t n, float delta, int32_t *q, cudaStream_t st) {
+  k_quantise<<<grid_for(n), 256, 0, st>>>(y, n, delta, q);
+}
+void launch_dequantise(const int32_t *q, int64_t n, float delta, float *y, cudaStream_t st) {
+  k_dequantise<<<grid_for(n), 256, 0, st>>>(q, n, delta, y);
+}
+
+}  // namespace pw

@@ -1,0 +1,218 @@
+// Weight-blob parsing and device weight layouts.
+//
+// A blob ("PWMB") holds one lambda model (Section 4.1): the lifting
+// predict/update CNNs (Section 3.1), the temporal lifting nets (Section
+// 3.3), the ConvLSTM context prediction module and the four-step context
+// fusion nets (Section 3.2). Tensors are found by name; their shapes are
+// checked against the configuration in the blob header.
+#include <cstring>
+#include <map>
+
+#include "codec.h"
+
+namespace pw {
+
+namespace {
+
+struct BlobTensor {
+  std::vector<int> shape;
+  const float *data;
+};
+
+uint64_t poly_hash(const uint8_t *p, size_t n) {
+  // h = sum_i (w_i + 1) * P^(i+1) mod 2^64 over little-endian u32 words
+  const uint64_t P = 0x100000001B3ull;
+  uint64_t h = 0, pw = 1;
+  for (size_t i = 0; i + 4 <= n; i += 4) {
+    uint32_t w;
+    std::memcpy(&w, p + i, 4);
+    pw *= P;
+    h += ((uint64_t)w + 1ull) * pw;
+  }
+  return h;
+}
+
+}  // namespace
+
+int Model::load(pw_ctx *c, const void *blob, size_t n) {
+  ctx = c;
+  const uint8_t *b = static_cast<const uint8_t *>(blob);
+  if (n < 32 || std::memcmp(b, "PWMB", 4) != 0) {
+    set_last_error("weight blob: bad magic");
+    return PW_EINVAL;
+  }
+  uint32_t hdr[7];
+  std::memcpy(hdr, b + 4, sizeof(hdr));
+  if (hdr[0] != 1) { set_last_error("weight blob: unsupported version"); return PW_EINVAL; }
+  levels = (int)hdr[1]; C = (int)hdr[2]; F = (int)hdr[3]; ll_mode = (int)hdr[4];
+  const uint32_t nt = hdr[5];
+  if (levels < 1 || levels > 6 || F != 16 || (C != 32 && C != 64 && C != 128) || ll_mode > 1 ||
+      32ull + 64ull * nt > n || (n & 3)) {
+    set_last_error("weight blob: unsupported configuration (levels 1..6, F = 16, C in {32, 64, 128})");
+    return PW_EUNSUPPORTED;
+  }
+  std::map<std::string, BlobTensor> ts;
+  for (uint32_t i = 0; i < nt; ++i) {
+    const uint8_t *r = b + 32 + 64 * i;
+    char name[41];
+    std::memcpy(name, r, 40);
+    name[40] = 0;
+    uint32_t f[6];
+    std::memcpy(f, r + 40, sizeof(f));
+    if (f[0] < 1 || f[0] > 4) { set_last_error("weight blob: bad rank"); return PW_EINVAL; }
+    BlobTensor t;
+    size_t cnt = 1;
+    for (uint32_t d = 0; d < f[0]; ++d) { t.shape.push_back((int)f[1 + d]); cnt *= f[1 + d]; }
+    if ((size_t)f[5] + 4 * cnt > n || (f[5] & 3)) {
+      set_last_error(std::string("weight blob: tensor out of range: ") + name);
+      return PW_EINVAL;
+    }
+    t.data = reinterpret_cast<const float *>(b + f[5]);
+    ts[name] = t;
+  }
+  hash = poly_hash(b, n);
+
+  auto get = [&](const std::string &name, std::vector<int> shape,
+                 std::vector<float> &out) -> bool {
+    auto it = ts.find(name);
+    if (it == ts.end() || it->second.shape != shape) {
+      set_last_error("weight blob: missing or mis-shaped tensor " + name);
+      return false;
+    }
+    size_t cnt = 1;
+    for (int s : shape) cnt *= (size_t)s;
+    out.resize(cnt);
+    std::memcpy(out.data(), it->second.data, cnt * 4);
+    return true;
+  };
+  std::vector<float> t0, t1;
+  // layout converters
+  auto conv_tap_major = [](const std::vector<float> &w, int co, int ci, int k) {
+    // [co][ci][k][k] -> [tap][ci][co]
+    std::vector<float> o((size_t)co * ci * k * k);
+    for (int a = 0; a < co; ++a)
+      for (int c = 0; c < ci; ++c)
+        for (int t = 0; t < k * k; ++t)
+          o[((size_t)t * ci + c) * co + a] = w[((size_t)a * ci + c) * k * k + t];
+    return o;
+  };
+  auto transpose = [](const std::vector<float> &w, int co, int ci) {
+    std::vector<float> o((size_t)co * ci);
+    for (int a = 0; a < co; ++a)
+      for (int c = 0; c < ci; ++c) o[(size_t)c * co + a] = w[(size_t)a * ci + c];
+    return o;
+  };
+
+  int st = PW_OK;
+  auto up = [&](const std::vector<float> &h) -> float * {
+    float *d = nullptr;
+    if (cudaMalloc(&d, h.size() * 4) != cudaSuccess) { st = PW_ENOMEM; return nullptr; }
+    cudaMemcpy(d, h.data(), h.size() * 4, cudaMemcpyHostToDevice);
+    allocs.push_back(d);
+    return d;
+  };
+  host.clear();
+  auto keep = [&](const std::string &name, const std::vector<float> &v) { host[name] = v; };
+
+  // lifting nets: w1 [16,1,3,3], w2 [16,16,3,3], w3 [1,16,3,3] (already [co][ci][9])
+  auto load_lift = [&](const std::string &p, LiftNetDev &n) -> bool {
+    std::vector<float> w1, b1, w2, b2, w3, b3;
+    if (!get(p + "w1", {16, 1, 3, 3}, w1) || !get(p + "b1", {16}, b1) ||
+        !get(p + "w2", {16, 16, 3, 3}, w2) || !get(p + "b2", {16}, b2) ||
+        !get(p + "w3", {1, 16, 3, 3}, w3) || !get(p + "b3", {1}, b3))
+      return false;
+    n.w1 = up(w1); n.b1 = up(b1); n.w2 = up(w2); n.b2 = up(b2); n.w3 = up(w3); n.b3 = up(b3);
+    keep(p + "w2", w2); keep(p + "w1", w1); keep(p + "w3", w3);
+    keep(p + "b1", b1); keep(p + "b2", b2); keep(p + "b3", b3);
+    return true;
+  };
+  const char *dirs[2] = {"row", "col"};
+  const char *ops[2] = {"P", "U"};
+  for (int d = 0; d < 2; ++d)
+    for (int o = 0; o < 2; ++o)
+      if (!load_lift(std::string("lift.") + dirs[d] + "." + ops[o] + ".", lift[d][o]))
+        return PW_EINVAL;
+  for (int o = 0; o < 2; ++o)
+    if (!load_lift(std::string("tlift.") + ops[o] + ".", tlift[o])) return PW_EINVAL;
+
+  // ConvLSTM
+  {
+    std::vector<float> we, be, wg, bg;
+    if (!get("lstm.we", {C, 1, 3, 3}, we) || !get("lstm.be", {C}, be) ||
+        !get("lstm.wg", {4 * C, 2 * C, 3, 3}, wg) || !get("lstm.bg", {4 * C}, bg))
+      return PW_EINVAL;
+    lstm_we = up(we);
+    lstm_be = up(be);
+    // permute output channels: gate * C + ch -> 4 * ch + gate
+    std::vector<float> wgp(wg.size()), bgp(bg.size());
+    for (int g = 0; g < 4; ++g)
+      for (int ch = 0; ch < C; ++ch) {
+        const int o = g * C + ch, o2 = 4 * ch + g;
+        bgp[o2] = bg[o];
+        std::memcpy(&wgp[(size_t)o2 * 2 * C * 9], &wg[(size_t)o * 2 * C * 9], 2 * C * 9 * 4);
+      }
+    lstm_wg = up(conv_tap_major(wgp, 4 * C, 2 * C, 3));
+    lstm_bg = up(bgp);
+    keep("lstm.wg.perm", wgp);
+    keep("lstm.bg.perm", bgp);
+  }
+  // four-step nets
+  auto load_set = [&](const std::string &ns, StepNetDev *nets) -> bool {
+    {
+      StepNetDev &s = nets[0];
+      const std::string p = ns + ".s0.";
+      std::vector<float> w, bb;
+      if (!get(p + "win", {C, C}, w) || !get(p + "bin", {C}, bb)) return false;
+      s.win = up(transpose(w, C, C)); s.bin = up(bb); keep(p + "win", w); keep(p + "bin", bb);
+      if (!get(p + "w1", {C, C}, w) || !get(p + "b1", {C}, bb)) return false;
+      s.w1 = up(transpose(w, C, C)); s.b1 = up(bb); keep(p + "w1", w); keep(p + "b1", bb);
+      if (!get(p + "wdw", {C, 3, 3}, w) || !get(p + "bdw", {C}, bb)) return false;
+      s.wdw = up(w); s.bdw = up(bb);
+      if (!get(p + "w2", {C, C}, w) || !get(p + "b2", {C}, bb)) return false;
+      s.w2 = up(transpose(w, C, C)); s.b2 = up(bb); keep(p + "w2", w); keep(p + "b2", bb);
+      if (!get(p + "w3", {2 * C, C}, w) || !get(p + "b3", {2 * C}, bb)) return false;
+      s.w3 = up(transpose(w, 2 * C, C)); s.b3 = up(bb); keep(p + "w3", w); keep(p + "b3", bb);
+      if (!get(p + "w4", {C, 2 * C}, w) || !get(p + "b4", {C}, bb)) return false;
+      s.w4 = up(transpose(w, C, 2 * C)); s.b4 = up(bb); keep(p + "w4", w); keep(p + "b4", bb);
+      if (!get(p + "wh", {2, C}, w) || !get(p + "bh", {2}, bb)) return false;
+      s.wh = up(w); s.bh = up(bb); keep(p + "wh", w); keep(p + "bh", bb);
+    }
+    for (int k = 1; k < 4; ++k) {
+      StepNetDev &s = nets[k];
+      const std::string p = ns + ".s" + std::to_string(k) + ".";
+      std::vector<float> w, bb;
+      if (!get(p + "wa", {C, 1, 3, 3}, w) || !get(p + "ba", {C}, bb)) return false;
+      s.wa = up(w); s.ba = up(bb);
+      if (!get(p + "wz", {C, 2 * C}, w) || !get(p + "bz", {C}, bb)) return false;
+      s.wz = up(transpose(w, C, 2 * C)); s.bz = up(bb); keep(p + "wz", w); keep(p + "bz", bb);
+      if (!get(p + "w1", {C, C, 3, 3}, w) || !get(p + "b1", {C}, bb)) return false;
+      s.c1w = up(conv_tap_major(w, C, C, 3)); s.c1b = up(bb); keep(p + "w1", w); keep(p + "b1", bb);
+      if (!get(p + "w2", {C, C, 3, 3}, w) || !get(p + "b2", {C}, bb)) return false;
+      s.c2w = up(conv_tap_major(w, C, C, 3)); s.c2b = up(bb); keep(p + "w2", w); keep(p + "b2", bb);
+      if (!get(p + "wh", {2, C}, w) || !get(p + "bh", {2}, bb)) return false;
+      s.wh = up(w); s.bh = up(bb); keep(p + "wh", w); keep(p + "bh", bb);
+    }
+    return true;
+  };
+  if (!load_set("sb", sb)) return PW_EINVAL;
+  if (ll_mode == 0) {
+    if (!load_set("ll", ll)) return PW_EINVAL;
+  } else {
+    std::vector<float> w, bb;
+    if (!get("ar.w5", {C, 1, 5, 5}, w) || !get("ar.b5", {C}, bb)) return PW_EINVAL;
+    ar_w5 = up(w); ar_b5 = up(bb);
+    if (!get("ar.w1", {C, C}, w) || !get("ar.b1", {C}, bb)) return PW_EINVAL;
+    ar_w1 = up(w); ar_b1 = up(bb);
+    if (!get("ar.wh", {2, C}, w) || !get("ar.bh", {2}, bb)) return PW_EINVAL;
+    ar_wh = up(w); ar_bh = up(bb);
+  }
+  cudaDeviceSynchronize();
+  return st;
+}
+
+Model::~Model() {
+  for (float *p : allocs) cudaFree(p);
+  free_tc();
+}
+
+}  // namespace pw
