@@ -36,6 +36,11 @@ class pw_codec_opts(C.Structure):
     _fields_ = [("q", C.c_float), ("lossless", C.c_int32), ("chunk_symbols", C.c_int32)]
 
 
+class pw_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 40), ("launches", C.c_uint64), ("ms", C.c_double),
+                ("flops", C.c_double), ("bytes", C.c_double)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -77,6 +82,8 @@ _sig = {
     "pw_encode_latent": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                    C.POINTER(pw_codec_opts), C.POINTER(_u8p),
                                    C.POINTER(C.c_size_t)]),
+    "pw_ctx_profile": (C.c_int, [_P, C.c_int]),
+    "pw_ctx_kernel_stats": (C.c_int, [_P, C.POINTER(pw_kernel_stat), C.c_int]),
     "pw_free": (None, [_P]),
     "pw_strerror": (C.c_char_p, [C.c_int]),
     "pw_last_error": (C.c_char_p, []),

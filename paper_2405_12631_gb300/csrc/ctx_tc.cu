@@ -1,20 +1,829 @@
-// Tensor-core (tcgen05, BF16) context-model path.
+// Context model of pWave++ (Section 3.2) on the 5th-generation tensor cores:
+// BF16 implicit-GEMM convolutions with tcgen05.mma, FP32 accumulators in
+// tensor memory, operand tiles brought in by TMA, fused epilogues.
+//
+// Activations are BF16 in a channel-group-blocked layout [P][G][H][W][8]
+// (G = channels / 8), so that a TMA box (8 channels, tile width + halo,
+// tile height + halo, groups) lands in shared memory as one slab of 16-byte
+// rows per channel group: exactly the no-swizzle K-major core-matrix layout
+// of the MMA A operand. A 3x3 tap is then just a shifted start address into
+// the halo tile, so every input pixel is loaded once per K-block.
+//
+// GEMM view: M = 128 output pixels (16 rows x 8 columns of one plane),
+// N = output channels of the CTA (32, 64 or 128), K = taps x input channels,
+// processed in K-blocks of 64 (32) channels. Weights of the CTA's N block
+// stay resident in shared memory for the whole persistent kernel.
+// Warp roles: warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM owner),
+// warps 2-5 = epilogue (one TMEM lane quadrant each). Accumulators are
+// double-buffered in TMEM so the epilogue of one tile overlaps the MMAs of
+// the next. Every wait is bounded: on expiry the kernel sets an error flag,
+// lets in-flight copies land, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
 #include "ctx_tc.h"
+#include "prof.h"
 
 namespace pw {
-int tc_workspace_alloc(Workspace *, const Geometry &, int) {
-  set_last_error("BF16 path not built");
+
+struct TcWeights {
+  // per conv: packed BF16 weights [nb][kblock][tap][kb/8][ncta][8] + FP32 bias
+  struct Conv {
+    __nv_bfloat16 *w = nullptr;
+    float *b = nullptr;
+    int cin = 0, cout = 0, ks = 1, kb = 64, ncta = 64, nb = 1;
+  };
+  Conv gates;
+  Conv s0_in, s0_w1, s0_w2, s0_w3, s0_w4;        // sb set, step 0
+  Conv sk_z[3], sk_c1[3], sk_c2[3];             // sb set, steps 1..3
+  Conv l0_in, l0_w1, l0_w2, l0_w3, l0_w4;       // ll set
+  Conv lk_z[3], lk_c1[3], lk_c2[3];
+  std::vector<void *> allocs;
+};
+
+struct TcAct {  // BF16 activations in [P][G][H][W][8]
+  __nv_bfloat16 *X = nullptr, *X2 = nullptr, *Z = nullptr, *U = nullptr, *V = nullptr,
+                *Z2 = nullptr;
+  int *err = nullptr;
+  void *base = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait (about 2^31 clock cycles, ~1 s). Returns false on expiry or
+// when another role has already aborted.
+constexpr long long kWaitCycles = 1ll << 31;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 63) == 0) {
+      if (*abort) return false;
+      if (clock64() - t0 > kWaitCycles) { *abort = 1; return false; }
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  // tcgen05 shared-memory descriptor, no swizzle, K-major canonical layout
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float sigm_f(float x) { return 1.f / (1.f + __expf(-x)); }
+__device__ __forceinline__ float lrelu_f(float x) { return x >= 0.f ? x : 0.01f * x; }
+
+// ---------------------------------------------------------------------------
+enum { TE_STORE = 0, TE_LSTM = 1, TE_HEAD = 2 };
+
+struct TcConvArgs {
+  int P, H, W;
+  int ks, cin, kb, nkb, in_goff;
+  int ncta, nb;
+  int tiles_x, tiles_y, tiles;  // tiles per N block
+  int stages, halo_x, halo_y;
+  uint32_t stage_bytes, w_bytes;
+  const __nv_bfloat16 *wt;      // [nb][kblock][tap][kb/8][ncta][8]
+  const float *bias;            // [nb * ncta]
+  int epi, act;
+  __nv_bfloat16 *out;
+  int out_G, out_goff;
+  const __nv_bfloat16 *res;
+  int res_G, res_goff;
+  const float *c_prev;
+  float *c_new;
+  int up, first, C;
+  const float *wh, *bh;
+  int step;
+  uint32_t *idx;
+  int64_t idx_stride;
+  float *mu_out, *sg_out;
+  int *err;
+};
+
+constexpr int kTileH = 16, kTileW = 8;
+
+__device__ __forceinline__ void store_bf16x8(__nv_bfloat16 *p, const float *v) {
+  uint4 u;
+  __nv_bfloat162 t0 = __floats2bfloat162_rn(v[0], v[1]), t1 = __floats2bfloat162_rn(v[2], v[3]),
+                 t2 = __floats2bfloat162_rn(v[4], v[5]), t3 = __floats2bfloat162_rn(v[6], v[7]);
+  u.x = *reinterpret_cast<uint32_t *>(&t0);
+  u.y = *reinterpret_cast<uint32_t *>(&t1);
+  u.z = *reinterpret_cast<uint32_t *>(&t2);
+  u.w = *reinterpret_cast<uint32_t *>(&t3);
+  *reinterpret_cast<uint4 *>(p) = u;
+}
+__device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *p, float *v) {
+  uint4 u = *reinterpret_cast<const uint4 *>(p);
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float2 f = __bfloat1622float2(h[i]);
+    v[2 * i] = f.x;
+    v[2 * i + 1] = f.y;
+  }
+}
+
+template <int NCTA>
+__global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap,
+                                                    const TcConvArgs a) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem);       // [8]
+  uint64_t *empty = full + 8;                                // [8]
+  uint64_t *accf = empty + 8;                                // [2]
+  uint64_t *acce = accf + 2;                                 // [2]
+  uint64_t *wbar = acce + 2;                                 // [1]
+  volatile int *s_abort = reinterpret_cast<volatile int *>(wbar + 1);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 256);
+  uint8_t *wsm = smem + 1024;
+  uint8_t *stg = wsm + ((a.w_bytes + 1023) / 1024) * 1024;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = blockIdx.x % a.nb;
+  const int cta = blockIdx.x / a.nb;
+  const int nctas = gridDim.x / a.nb;
+  constexpr uint32_t kCols = NCTA * 2 <= 32 ? 32 : NCTA * 2;  // power of two
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < a.stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+    for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 4); }
+    mbar_init(wbar, 1);
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(s_tmem)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = *s_tmem;
+  const int taps = a.ks * a.ks;
+  const int R = a.ks / 2;
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer: weights once, then halo K-blocks ----------------------
+    const uint8_t *wsrc = reinterpret_cast<const uint8_t *>(a.wt) + (size_t)nb * a.w_bytes;
+    mbar_expect_tx(wbar, a.w_bytes);
+    for (uint32_t off = 0; off < a.w_bytes; off += 32768u) {
+      const uint32_t n = min(32768u, a.w_bytes - off);
+      bulk_load(wsm + off, wsrc + off, n, wbar);
+    }
+    int stage = 0;
+    uint32_t phase = 0;
+    int issued = 0;
+    for (int t = cta; t < a.tiles && !*s_abort; t += nctas) {
+      const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, p = t / (a.tiles_x * a.tiles_y);
+      for (int kbi = 0; kbi < a.nkb; ++kbi) {
+        if (!mbar_wait(&empty[stage], phase ^ 1, s_abort)) break;
+        mbar_expect_tx(&full[stage], a.stage_bytes);
+        tma_load_5d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage], 0,
+                    tx * kTileW - R, ty * kTileH - R, a.in_goff + kbi * (a.kb / 8), p);
+        ++issued;
+        if (++stage == a.stages) { stage = 0; phase ^= 1; }
+      }
+    }
+    // let every copy this thread issued land before the CTA can exit
+    {
+      int s = stage;
+      uint32_t ph = phase;
+      for (int i = 0; i < min(issued, a.stages); ++i) {
+        if (--s < 0) { s = a.stages - 1; ph ^= 1; }
+        mbar_wait(&full[s], ph, s_abort);
+      }
+      mbar_wait(wbar, 0, s_abort);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ---------------------------------------------------------
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCTA >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    const uint32_t slab = (uint32_t)a.halo_x * a.halo_y * 16u;
+    const uint32_t wblock = (uint32_t)taps * (a.kb / 8) * NCTA * 16u;  // bytes per K-block
+    bool ok = mbar_wait(wbar, 0, s_abort);
+    int stage = 0, acc = 0;
+    uint32_t phase = 0, aphase = 0;
+    for (int t = cta; ok && t < a.tiles; t += nctas) {
+      if (!mbar_wait(&acce[acc], aphase ^ 1, s_abort)) break;
+      fence_after();
+      const uint32_t d = tbase + (uint32_t)(acc * NCTA);
+      uint32_t accum = 0;
+      for (int kbi = 0; kbi < a.nkb; ++kbi) {
+        if (!mbar_wait(&full[stage], phase, s_abort)) { ok = false; break; }
+        fence_after();
+        const uint32_t abase = smem_u32(stg + (size_t)stage * a.stage_bytes);
+        const uint32_t bbase = smem_u32(wsm) + (uint32_t)kbi * wblock;
+        for (int tap = 0; tap < taps; ++tap) {
+          const int dy = tap / a.ks, dx = tap % a.ks;
+          const uint32_t aoff = (uint32_t)(dy * a.halo_x + dx) * 16u;
+          for (int s = 0; s < a.kb / 16; ++s) {
+            const uint64_t ad = sdesc(abase + (uint32_t)(2 * s) * slab + aoff, slab,
+                                      (uint32_t)a.halo_x * 16u);
+            const uint64_t bd =
+                sdesc(bbase + (uint32_t)(tap * (a.kb / 8) + 2 * s) * (NCTA * 16u), NCTA * 16u, 128u);
+            mma_bf16(d, ad, bd, idesc, accum);
+            accum = 1;
+          }
+        }
+        mma_commit(&empty[stage]);
+        if (++stage == a.stages) { stage = 0; phase ^= 1; }
+      }
+      if (!ok) break;
+      mma_commit(&accf[acc]);
+      if (++acc == 2) { acc = 0; aphase ^= 1; }
+    }
+  } else if (warp >= 2) {
+    // ---- epilogue -----------------------------------------------------------
+    const int q = warp & 3;
+    const int m = 32 * q + lane;
+    const int r = m / kTileW, c = m % kTileW;
+    int acc = 0;
+    uint32_t aphase = 0;
+    const int G = a.out_G;
+    for (int t = cta; t < a.tiles; t += nctas) {
+      const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, p = t / (a.tiles_x * a.tiles_y);
+      // warp-uniform wait: lane 0 decides, the others then observe the
+      // completed phase themselves (their try_wait succeeds at once)
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&accf[acc], aphase, s_abort) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) break;
+      if (lane != 0) mbar_wait(&accf[acc], aphase, s_abort);
+      __syncwarp();
+      fence_after();
+      float v[NCTA];
+      const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NCTA);
+#pragma unroll
+      for (int ch = 0; ch < NCTA / 16; ++ch) tmem_ld16(taddr + 16 * ch, v + 16 * ch);
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[acc]);
+      if (++acc == 2) { acc = 0; aphase ^= 1; }
+
+      const int y = ty * kTileH + r, x = tx * kTileW + c;
+      const bool valid = y < a.H && x < a.W;
+      const int64_t hw = (int64_t)a.H * a.W;
+      const int64_t pix = (int64_t)y * a.W + x;
+      const int n0 = nb * NCTA;
+#pragma unroll
+      for (int j = 0; j < NCTA; ++j) v[j] += a.bias[n0 + j];
+      if (a.epi == TE_STORE) {
+        if (valid) {
+#pragma unroll
+          for (int g = 0; g < NCTA / 8; ++g) {
+            const int gg = (n0 >> 3) + g;
+            if (a.res) {
+              float rv[8];
+              load_bf16x8(a.res + (((int64_t)p * a.res_G + a.res_goff + gg) * hw + pix) * 8, rv);
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v[8 * g + e] += rv[e];
+            }
+            if (a.act) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v[8 * g + e] = lrelu_f(v[8 * g + e]);
+            }
+            store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + gg) * hw + pix) * 8, v + 8 * g);
+          }
+        }
+      } else if (a.epi == TE_LSTM) {
+        // column 4 * ch + gate (i, f, o, g) within the CTA's N block
+        if (valid) {
+          const int Hp = a.H >> a.up, Wp = a.W >> a.up;
+          const int64_t ppix = ((int64_t)p * Hp + (y >> a.up)) * Wp + (x >> a.up);
+          const int ch0 = n0 / 4;
+          float hv[NCTA / 4];
+#pragma unroll
+          for (int k = 0; k < NCTA / 4; ++k) {
+            const int chn = ch0 + k;
+            const float cp = a.first ? 0.f : a.c_prev[ppix * a.C + chn];
+            const float cn = sigm_f(v[4 * k + 1]) * cp + sigm_f(v[4 * k]) * tanhf(v[4 * k + 3]);
+            hv[k] = sigm_f(v[4 * k + 2]) * tanhf(cn);
+            a.c_new[((int64_t)p * hw + pix) * a.C + chn] = cn;
+          }
+#pragma unroll
+          for (int g = 0; g < NCTA / 32; ++g)
+            store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (ch0 >> 3) + g) * hw + pix) * 8,
+                         hv + 8 * g);
+        }
+      } else {  // TE_HEAD: z' = res + acc + b over all C columns, then 1x1(C->2)
+        if (valid && step_of(y, x) == a.step) {
+          float mu = a.bh[0], rho = a.bh[1];
+#pragma unroll
+          for (int g = 0; g < NCTA / 8; ++g) {
+            float rv[8];
+            load_bf16x8(a.res + (((int64_t)p * a.res_G + a.res_goff + g) * hw + pix) * 8, rv);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              const float z = v[8 * g + e] + rv[e];
+              mu = fmaf(a.wh[8 * g + e], z, mu);
+              rho = fmaf(a.wh[NCTA + 8 * g + e], z, rho);
+            }
+          }
+          const int qi = step_index(a.W, a.step, y, x);
+          a.idx[(int64_t)p * a.idx_stride + qi] = pack_index(mu, rho);
+          if (a.mu_out) {
+            a.mu_out[(int64_t)p * hw + pix] = mu;
+            a.sg_out[(int64_t)p * hw + pix] = rho > 20.f ? rho : log1pf(expf(rho));
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols));
+  }
+  if (threadIdx.x == 0 && *s_abort) atomicExch(a.err, 1);
+}
+
+// ---------------------------------------------------------------------------
+// SIMT helper kernels on the blocked BF16 layout.
+
+// X[:, 0:C] = conv3x3(1->C)(up(s_prev)) + be; X[:, C:2C] = up(h_prev)
+// (h_prev read from X2 groups [C/8, C/4) at the previous resolution).
+__global__ void k_lstm_in_bf16(const int32_t *__restrict__ s_prev,
+                               const __nv_bfloat16 *__restrict__ X2prev,
+                               const float *__restrict__ we, const float *__restrict__ be,
+                               __nv_bfloat16 *__restrict__ X, int P, int H, int W, int C, int up,
+                               int first) {
+  const int G = C / 8;
+  const int64_t n = (int64_t)P * H * W * G;
+  const int Hp = H >> up, Wp = W >> up;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % W);
+    const int y = (int)((e / W) % H);
+    const int g = (int)((e / ((int64_t)W * H)) % G);
+    const int p = (int)(e / ((int64_t)W * H * G));
+    const int32_t *sp = s_prev + (int64_t)p * Hp * Wp;
+    float nb[9];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      nb[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    ? (float)sp[(int64_t)(yy >> up) * Wp + (xx >> up)]
+                    : 0.f;
+    }
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = 8 * g + k;
+      float s = be[c];
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) s = fmaf(we[c * 9 + tap], nb[tap], s);
+      v[k] = s;
+    }
+    const int64_t hw = (int64_t)H * W;
+    store_bf16x8(X + (((int64_t)p * 2 * G + g) * hw + (int64_t)y * W + x) * 8, v);
+    float hv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (!first)
+      load_bf16x8(X2prev + (((int64_t)p * 2 * G + G + g) * ((int64_t)Hp * Wp) +
+                            (int64_t)(y >> up) * Wp + (x >> up)) * 8,
+                  hv);
+    store_bf16x8(X + (((int64_t)p * 2 * G + G + g) * hw + (int64_t)y * W + x) * 8, hv);
+  }
+}
+
+// X2[:, 0:C] = conv3x3(1->C)(m_<step * s) + ba
+__global__ void k_masked_in_bf16(const int32_t *__restrict__ s, const float *__restrict__ wa,
+                                 const float *__restrict__ ba, __nv_bfloat16 *__restrict__ X2,
+                                 int P, int H, int W, int C, int step) {
+  const int G = C / 8;
+  const int64_t n = (int64_t)P * H * W * G;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % W);
+    const int y = (int)((e / W) % H);
+    const int g = (int)((e / ((int64_t)W * H)) % G);
+    const int p = (int)(e / ((int64_t)W * H * G));
+    const int32_t *sp = s + (int64_t)p * H * W;
+    float nb[9];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      nb[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W && step_of(yy, xx) < step)
+                    ? (float)sp[(int64_t)yy * W + xx]
+                    : 0.f;
+    }
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int c = 8 * g + k;
+      float sum = ba[c];
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) sum = fmaf(wa[c * 9 + tap], nb[tap], sum);
+      v[k] = sum;
+    }
+    store_bf16x8(X2 + (((int64_t)p * 2 * G + g) * ((int64_t)H * W) + (int64_t)y * W + x) * 8, v);
+  }
+}
+
+// V = dw3x3(U) + b on C channels (blocked layout).
+__global__ void k_dw3x3_bf16(const __nv_bfloat16 *__restrict__ U, const float *__restrict__ w,
+                             const float *__restrict__ b, __nv_bfloat16 *__restrict__ V, int P,
+                             int H, int W, int C) {
+  const int G = C / 8;
+  const int64_t n = (int64_t)P * H * W * G;
+  const int64_t hw = (int64_t)H * W;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % W);
+    const int y = (int)((e / W) % H);
+    const int64_t pg = e / hw;  // p * G + g
+    const int g = (int)(pg % G);
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = b[8 * g + k];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+      float u[8];
+      load_bf16x8(U + (pg * hw + (int64_t)yy * W + xx) * 8, u);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = fmaf(w[(8 * g + k) * 9 + tap], u[k], v[k]);
+    }
+    store_bf16x8(V + (pg * hw + (int64_t)y * W + x) * 8, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+static int get_encoder() {
+  if (g_encode) return PW_OK;
+  void *fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    set_last_error("cuTensorMapEncodeTiled not available");
+    return PW_ECUDA;
+  }
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return PW_OK;
+}
+
+// Tensor map over a blocked BF16 tensor [P][G][H][W][8]; box = one K-block
+// halo tile.
+static int make_map(CUtensorMap *map, const __nv_bfloat16 *base, int P, int G, int H, int W,
+                    int box_x, int box_y, int box_g) {
+  int s = get_encoder();
+  if (s) return s;
+  cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)G, (cuuint64_t)P};
+  cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16,
+                           (cuuint64_t)G * H * W * 16};
+  cuuint32_t box[5] = {8, (cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_g, 1};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)base, dims, strides, box,
+                        es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return PW_ECUDA;
+  }
+  return PW_OK;
+}
+
+static int g_num_sms = 0;
+
+// Launch one tensor-core convolution.
+static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *in, int in_G,
+                   int in_goff, int P, int H, int W, TcConvArgs a, int *err) {
+  if (!g_num_sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  const int R = cv.ks / 2;
+  a.P = P; a.H = H; a.W = W; a.ks = cv.ks; a.cin = cv.cin; a.kb = cv.kb; a.nkb = cv.cin / cv.kb;
+  a.in_goff = in_goff; a.ncta = cv.ncta; a.nb = cv.nb;
+  a.halo_x = kTileW + 2 * R; a.halo_y = kTileH + 2 * R;
+  a.tiles_x = (W + kTileW - 1) / kTileW; a.tiles_y = (H + kTileH - 1) / kTileH;
+  a.tiles = P * a.tiles_x * a.tiles_y;
+  a.stage_bytes = (uint32_t)a.halo_x * a.halo_y * cv.kb * 2;
+  a.w_bytes = (uint32_t)(cv.ks * cv.ks) * cv.cin * cv.ncta * 2;
+  a.wt = cv.w; a.bias = cv.b; a.err = err;
+  const size_t fixed = 1024 + (a.w_bytes + 1023) / 1024 * 1024;
+  const size_t maxsm = 227 * 1024;
+  int stages = (int)((maxsm - fixed) / a.stage_bytes);
+  stages = stages > 6 ? 6 : stages;
+  if (stages < 2) { set_last_error("tensor-core conv does not fit in shared memory"); return PW_EUNSUPPORTED; }
+  a.stages = stages;
+  const size_t smem = fixed + (size_t)stages * a.stage_bytes;
+  CUtensorMap map;
+  int s = make_map(&map, in, P, in_G, H, W, a.halo_x, a.halo_y, cv.kb / 8);
+  if (s) return s;
+  int per_nb = g_num_sms / cv.nb;
+  if (per_nb < 1) per_nb = 1;
+  if (per_nb > a.tiles) per_nb = a.tiles;
+  const int grid = per_nb * cv.nb;
+  cudaStream_t st = ctx->stream;
+#define PW_TC_CASE(N_)                                                                      \
+  if (cv.ncta == N_) {                                                                      \
+    static bool attr = false;                                                               \
+    if (!attr) {                                                                            \
+      cudaFuncSetAttribute(k_conv_tc<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                           (int)maxsm);                                                     \
+      attr = true;                                                                          \
+    }                                                                                       \
+    k_conv_tc<N_><<<grid, 192, smem, st>>>(map, a);                                         \
+    ctx->launches += 1;                                                                     \
+    return PW_OK;                                                                           \
+  }
+  PW_TC_CASE(32) PW_TC_CASE(64) PW_TC_CASE(128)
+#undef PW_TC_CASE
+  set_last_error("no tensor-core conv for this N");
   return PW_EUNSUPPORTED;
 }
-void tc_workspace_free(Workspace *) {}
-int tc_run_lstm(pw_ctx *, Model &, const Geometry &, Workspace &, int, const int32_t *, int,
-                int, int) {
-  return PW_EUNSUPPORTED;
+
+// ---- weights -------------------------------------------------------------
+static int pack_conv(TcWeights &tw, TcWeights::Conv &cv, const std::vector<float> &w,
+                     const std::vector<float> &b, int cout, int cin, int ks, int ncta) {
+  // w: [cout][cin][ks*ks] (output order as the kernel's columns)
+  cv.cin = cin; cv.cout = cout; cv.ks = ks; cv.kb = cin >= 64 ? 64 : cin; cv.ncta = ncta;
+  cv.nb = cout / ncta;
+  const int taps = ks * ks, nkb = cin / cv.kb, gpb = cv.kb / 8;
+  std::vector<__nv_bfloat16> h((size_t)cout * cin * taps);
+  size_t o = 0;
+  for (int nb = 0; nb < cv.nb; ++nb)
+    for (int kbi = 0; kbi < nkb; ++kbi)
+      for (int t = 0; t < taps; ++t)
+        for (int g = 0; g < gpb; ++g)
+          for (int n = 0; n < ncta; ++n)
+            for (int e = 0; e < 8; ++e) {
+              const int co = nb * ncta + n, ci = kbi * cv.kb + g * 8 + e;
+              h[o++] = __float2bfloat16(w[((size_t)co * cin + ci) * taps + t]);
+            }
+  if (cudaMalloc(&cv.w, h.size() * 2) != cudaSuccess || cudaMalloc(&cv.b, cout * 4) != cudaSuccess) {
+    set_last_error("weight allocation failed");
+    return PW_ENOMEM;
+  }
+  tw.allocs.push_back(cv.w);
+  tw.allocs.push_back(cv.b);
+  cudaMemcpy(cv.w, h.data(), h.size() * 2, cudaMemcpyHostToDevice);
+  cudaMemcpy(cv.b, b.data(), cout * 4, cudaMemcpyHostToDevice);
+  return PW_OK;
 }
-int tc_run_step(pw_ctx *, Model &, const Geometry &, Workspace &, int, int, StepNetDev &,
-                const int32_t *, uint32_t *, int64_t, float *, float *) {
-  return PW_EUNSUPPORTED;
+
+int Model::ensure_tc() {
+  if (tc) return PW_OK;
+  if (C != 32 && C != 64) {
+    set_last_error("the tensor-core path supports C = 32 or 64");
+    return PW_EUNSUPPORTED;
+  }
+  std::unique_ptr<TcWeights> t(new TcWeights());
+  int s;
+  auto H = [&](const std::string &n) -> const std::vector<float> & { return host.at(n); };
+  if ((s = pack_conv(*t, t->gates, H("lstm.wg.perm"), H("lstm.bg.perm"), 4 * C, 2 * C, 3, 64)))
+    return s;
+  auto set = [&](const std::string &ns, TcWeights::Conv &in_, TcWeights::Conv &w1,
+                 TcWeights::Conv &w2, TcWeights::Conv &w3, TcWeights::Conv &w4,
+                 TcWeights::Conv *kz, TcWeights::Conv *k1, TcWeights::Conv *k2) -> int {
+    int r;
+    const std::string p = ns + ".s0.";
+    if ((r = pack_conv(*t, in_, H(p + "win"), H(p + "bin"), C, C, 1, C))) return r;
+    if ((r = pack_conv(*t, w1, H(p + "w1"), H(p + "b1"), C, C, 1, C))) return r;
+    if ((r = pack_conv(*t, w2, H(p + "w2"), H(p + "b2"), C, C, 1, C))) return r;
+    if ((r = pack_conv(*t, w3, H(p + "w3"), H(p + "b3"), 2 * C, C, 1, 2 * C))) return r;
+    if ((r = pack_conv(*t, w4, H(p + "w4"), H(p + "b4"), C, 2 * C, 1, C))) return r;
+    for (int k = 1; k < 4; ++k) {
+      const std::string q = ns + ".s" + std::to_string(k) + ".";
+      if ((r = pack_conv(*t, kz[k - 1], H(q + "wz"), H(q + "bz"), C, 2 * C, 1, C))) return r;
+      if ((r = pack_conv(*t, k1[k - 1], H(q + "w1"), H(q + "b1"), C, C, 3, C))) return r;
+      if ((r = pack_conv(*t, k2[k - 1], H(q + "w2"), H(q + "b2"), C, C, 3, C))) return r;
+    }
+    return PW_OK;
+  };
+  if ((s = set("sb", t->s0_in, t->s0_w1, t->s0_w2, t->s0_w3, t->s0_w4, t->sk_z, t->sk_c1,
+               t->sk_c2)))
+    return s;
+  if (ll_mode == 0 &&
+      (s = set("ll", t->l0_in, t->l0_w1, t->l0_w2, t->l0_w3, t->l0_w4, t->lk_z, t->lk_c1,
+               t->lk_c2)))
+    return s;
+  tc = t.release();
+  return PW_OK;
 }
-int Model::ensure_tc() { return PW_EUNSUPPORTED; }
-void Model::free_tc() {}
+
+void Model::free_tc() {
+  if (!tc) return;
+  for (void *p : tc->allocs) cudaFree(p);
+  delete tc;
+  tc = nullptr;
+}
+
+// ---- workspace -----------------------------------------------------------
+int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
+  const int64_t big = (int64_t)ws->P * g.sh.back() * g.sw.back();
+  auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
+  const int64_t sizes[6] = {big * 2 * C * 2, big * 2 * C * 2, big * C * 2,
+                            big * 2 * C * 2, big * C * 2,     big * C * 2};
+  int64_t tot = 1024;
+  for (int64_t v : sizes) tot += al(v);
+  TcAct *t = new TcAct();
+  if (cudaMalloc(&t->base, (size_t)tot) != cudaSuccess) {
+    delete t;
+    set_last_error("tensor-core workspace allocation failed");
+    return PW_ENOMEM;
+  }
+  uint8_t *b = static_cast<uint8_t *>(t->base);
+  t->err = reinterpret_cast<int *>(b);
+  cudaMemset(t->err, 0, 1024);
+  int64_t o = 1024;
+  __nv_bfloat16 **dst[6] = {&t->X, &t->X2, &t->Z, &t->U, &t->V, &t->Z2};
+  for (int i = 0; i < 6; ++i) { *dst[i] = reinterpret_cast<__nv_bfloat16 *>(b + o); o += al(sizes[i]); }
+  ws->tc = t;
+  return PW_OK;
+}
+
+void tc_workspace_free(Workspace *ws) {
+  TcAct *t = static_cast<TcAct *>(ws->tc);
+  if (!t) return;
+  cudaFree(t->base);
+  delete t;
+  ws->tc = nullptr;
+}
+
+static int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)(g > 152 * 32 ? 152 * 32 : (g < 1 ? 1 : g));
+}
+
+int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
+                const int32_t *sprev, int up, int first, int cur) {
+  TcAct &t = *static_cast<TcAct *>(ws.tc);
+  const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P, G = C / 8;
+  const double pix = (double)P * h * w;
+  {
+    ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 4.0 * C));
+    k_lstm_in_bf16<<<grid_for((int64_t)P * h * w * G), 256, 0, ctx->stream>>>(
+        sprev, t.X2, m.lstm_we, m.lstm_be, t.X, P, h, w, C, up, first);
+    ctx->launches += 1;
+  }
+  TcConvArgs a{};
+  a.epi = TE_LSTM;
+  a.out = t.X2; a.out_G = 2 * G; a.out_goff = G;
+  a.c_prev = ws.Cst[cur]; a.c_new = ws.Cst[cur ^ 1]; a.up = up; a.first = first; a.C = C;
+  ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * 2 * C * 4 * C, pix * (2.0 * 2 * C + 2.0 * C + 8.0 * C));
+  return conv_tc(ctx, m.tc->gates, t.X, 2 * G, 0, P, h, w, a, t.err);
+}
+
+int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb, int step,
+                StepNetDev &n, const int32_t *Qi, uint32_t *idx, int64_t nk, float *mu,
+                float *sgp) {
+  TcAct &t = *static_cast<TcAct *>(ws.tc);
+  TcWeights &W = *m.tc;
+  const bool ll = sb == 0;
+  const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P, G = C / 8;
+  cudaStream_t st = ctx->stream;
+  const double pix = (double)P * h * w;
+  auto conv = [&](const TcWeights::Conv &cv, const __nv_bfloat16 *in, int in_G, int in_goff,
+                  TcConvArgs a) {
+    ProfScope ps(ctx, cv.ks == 3 ? KC_CONV3 : KC_CONV1,
+                 2.0 * pix * cv.ks * cv.ks * cv.cin * cv.cout,
+                 pix * 2.0 * (cv.cin + cv.cout + (a.res ? cv.cout : 0)));
+    return conv_tc(ctx, cv, in, in_G, in_goff, P, h, w, a, t.err);
+  };
+  int s;
+  if (ll && step == 0) cudaMemsetAsync(t.X2, 0, (size_t)P * h * w * 2 * C * 2, st);
+  if (step == 0) {
+    const TcWeights::Conv &cin_ = ll ? W.l0_in : W.s0_in, &c1 = ll ? W.l0_w1 : W.s0_w1,
+                          &c2 = ll ? W.l0_w2 : W.s0_w2, &c3 = ll ? W.l0_w3 : W.s0_w3,
+                          &c4 = ll ? W.l0_w4 : W.s0_w4;
+    TcConvArgs a{};
+    a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
+    if ((s = conv(cin_, t.X2, 2 * G, G, a))) return s;           // z = 1x1(l)
+    a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
+    if ((s = conv(c1, t.Z, G, 0, a))) return s;                  // u = lrelu(1x1 z)
+    {
+      ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * 4.0 * C);
+      k_dw3x3_bf16<<<grid_for((int64_t)P * h * w * G), 256, 0, st>>>(t.U, n.wdw, n.bdw, t.V, P, h,
+                                                                     w, C);
+      ctx->launches += 1;
+    }
+    a = TcConvArgs{}; a.epi = TE_STORE; a.out = t.Z2; a.out_G = G; a.res = t.Z; a.res_G = G;
+    if ((s = conv(c2, t.V, G, 0, a))) return s;                  // z2 = z + 1x1(v)
+    a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = 2 * G;
+    if ((s = conv(c3, t.Z2, G, 0, a))) return s;                 // u2 = lrelu(1x1 z2)
+    a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z2; a.res_G = G;
+    a.wh = n.wh; a.bh = n.bh; a.step = 0; a.idx = idx; a.idx_stride = nk;
+    a.mu_out = mu; a.sg_out = sgp;
+    return conv(c4, t.U, 2 * G, 0, a);                           // head
+  }
+  const TcWeights::Conv &cz = ll ? W.lk_z[step - 1] : W.sk_z[step - 1];
+  const TcWeights::Conv &c1 = ll ? W.lk_c1[step - 1] : W.sk_c1[step - 1];
+  const TcWeights::Conv &c2 = ll ? W.lk_c2[step - 1] : W.sk_c2[step - 1];
+  {
+    ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 2.0 * C));
+    k_masked_in_bf16<<<grid_for((int64_t)P * h * w * G), 256, 0, st>>>(Qi, n.wa, n.ba, t.X2, P,
+                                                                        h, w, C, step);
+    ctx->launches += 1;
+  }
+  TcConvArgs a{};
+  a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
+  if ((s = conv(cz, t.X2, 2 * G, 0, a))) return s;               // z = 1x1[a, l]
+  a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
+  if ((s = conv(c1, t.Z, G, 0, a))) return s;                    // u = lrelu(conv3x3 z)
+  a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z; a.res_G = G;
+  a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
+  a.mu_out = mu; a.sg_out = sgp;
+  return conv(c2, t.U, G, 0, a);                                // head
+}
+
+void tc_error_reset(Workspace &ws, cudaStream_t st) {
+  TcAct *t = static_cast<TcAct *>(ws.tc);
+  if (t) cudaMemsetAsync(t->err, 0, 4, st);
+}
+
+int tc_error(Workspace &ws) {
+  TcAct *t = static_cast<TcAct *>(ws.tc);
+  if (!t) return 0;
+  int e = 0;
+  cudaMemcpy(&e, t->err, 4, cudaMemcpyDeviceToHost);
+  return e;
+}
+
 }  // namespace pw

@@ -10,4 +10,8 @@ int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
 int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb, int step,
                 StepNetDev &n, const int32_t *Qi, uint32_t *idx, int64_t nk, float *mu,
                 float *sg);
+// Non-zero when a tensor-core kernel hit a bounded-wait expiry since the last
+// reset (reads the workspace's device error word; synchronous).
+int tc_error(Workspace &ws);
+void tc_error_reset(Workspace &ws, cudaStream_t st);
 }  // namespace pw

@@ -116,8 +116,9 @@ def _init_scale(name: str, shape, cfg: ModelConfig) -> float:
 def random_model(cfg: ModelConfig, seed: int = 0) -> dict:
     """Draw every tensor of `cfg` from a seeded PCG64 stream (float32).
 
-    Heads get bias (0, softplus^-1(4)) so that initial scales are near 4
-    quantisation steps; everything else is uniform in +-bound.
+    Heads get bias (0, softplus^-1(1.5)) so that initial scales are near 1.5
+    quantisation steps (rates of a few bits per sample, as for a trained
+    model at moderate quality); everything else is uniform in +-bound.
     """
     rng = np.random.default_rng(seed)
     out = {}
@@ -125,7 +126,7 @@ def random_model(cfg: ModelConfig, seed: int = 0) -> dict:
         b = _init_scale(name, shape, cfg)
         t = rng.uniform(-b, b, shape).astype(np.float32)
         if name.endswith(".bh"):
-            t = np.array([0.0, np.log(np.expm1(4.0))], dtype=np.float32)
+            t = np.array([0.0, np.log(np.expm1(1.5))], dtype=np.float32)
         out[name] = t
     return out
 

@@ -210,18 +210,26 @@ def test_gpu_roundtrip_symbols_exact(codec, model32, rgb):
 
 
 def test_decode_oracle_stream(codec, model32):
-    """The GPU decodes a stream made by the oracle encoder. Every table index
-    the GPU derives must equal the oracle's, so this holds when no coded
-    position is a certified near-tie; the test asserts the tie set is empty
-    for this input and then requires exact coefficients."""
+    """The GPU decodes a stream made by the oracle encoder. The stream is
+    decodable only if every table index the GPU derives equals the oracle's.
+    The GPU's parameters on the oracle's latent tell whether that holds for
+    this input (mismatches can only sit at certified near-ties); when it
+    holds the decoded coefficients must be exact and the image within one
+    grey level of the oracle's decode."""
     blob, gm, om = model32
     img = S.gray_sinusoids(48, 64, seed=8)
     bs = K.encode_image(blob, img, q=8.0, chunk=256)
     qsb = _oracle_latent(om, img)[0]
     params = K.context_params_all(om, qsb)
-    ties = sum(int(np.sum(E.near_tie(p[0], p[1], TIE_EPS))) for p in params)
-    if ties:
-        pytest.skip(f"{ties} certified near-ties in this input")
+    mu_o = np.concatenate([p[0].reshape(-1) for p in params])
+    sg_o = np.concatenate([p[1].reshape(-1) for p in params])
+    mu_g, sg_g = codec.context_params(gm, 48, 64, _flat([qsb]))
+    a = E.index_decision(mu_g, sg_g)
+    b = E.index_decision(mu_o, sg_o)
+    diff = (a[0] != b[0]) | (a[1] != b[1]) | (a[2] != b[2])
+    assert not np.any(diff & ~E.near_tie(mu_o, sg_o, TIE_EPS))
+    if np.any(diff):
+        pytest.skip(f"{int(diff.sum())} certified near-tie index differences in this input")
     q_g = codec.decode_symbols(gm, bs)
     assert np.array_equal(q_g, _flat([qsb]))
     out = codec.decode_image(gm, bs)
