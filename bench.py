@@ -350,7 +350,7 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("PW_BENCH_PRECISION", "fp32"),
+    ap.add_argument("--precision", default=os.environ.get("PW_BENCH_PRECISION", "bf16"),
                     choices=["fp32", "bf16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

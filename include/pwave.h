@@ -180,6 +180,17 @@ int pw_encode_latent(pw_ctx *ctx, const pw_model *m, const int32_t *q, int width
                      int height, int channels, int bitdepth, int colour,
                      const pw_codec_opts *opts, uint8_t **bs, size_t *n);
 
+/* One context-model convolution on the tensor cores (tcgen05, BF16 operands,
+ * FP32 accumulation), for testing the building block of Section 3.2's nets:
+ * y = act(conv_ks(x) + b) with zero padding, act = LeakyReLU(0.01) if act.
+ * x: host [P][H][W][cin] float (rounded to BF16), w: host [cout][cin][ks][ks],
+ * b: host [cout], y: host [P][H][W][cout] (BF16-rounded results as float).
+ * ks in {1, 3}; cin a multiple of 32 (of 64 above 64); cout in {32, 64, 128,
+ * 192, 256}. Errors: PW_EUNSUPPORTED (shape), PW_ETIMEOUT (a bounded
+ * wait expired). */
+int pw_conv_bf16(pw_ctx *ctx, int P, int H, int W, int cin, int cout, int ks, int act,
+                 const float *x, const float *w, const float *b, float *y);
+
 /* ---- misc ---------------------------------------------------------------- */
 void pw_free(void *p);
 const char *pw_strerror(int status);

@@ -82,6 +82,8 @@ _sig = {
     "pw_encode_latent": (C.c_int, [_P, _P, _P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                    C.POINTER(pw_codec_opts), C.POINTER(_u8p),
                                    C.POINTER(C.c_size_t)]),
+    "pw_conv_bf16": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                               C.c_int, _P, _P, _P, _P]),
     "pw_ctx_profile": (C.c_int, [_P, C.c_int]),
     "pw_ctx_kernel_stats": (C.c_int, [_P, C.POINTER(pw_kernel_stat), C.c_int]),
     "pw_free": (None, [_P]),
@@ -291,6 +293,18 @@ class Codec:
         out = np.zeros((H, W), dtype=np.float32)
         check(pw_lift_inverse(self.ctx, model.handle, H, W, int(lossless), _ptr(sb), _ptr(out)))
         return out
+
+    def conv_bf16(self, x: np.ndarray, w: np.ndarray, b: np.ndarray, act: bool = False):
+        """x [P, H, W, cin], w [cout, cin, k, k], b [cout] -> y [P, H, W, cout]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        P, H, W, cin = x.shape
+        cout, _, k, _ = w.shape
+        y = np.zeros((P, H, W, cout), dtype=np.float32)
+        check(pw_conv_bf16(self.ctx, P, H, W, cin, cout, k, int(act), _ptr(x), _ptr(w), _ptr(b),
+                           _ptr(y)))
+        return y
 
     def decode_symbols(self, model: Model, bs: bytes) -> np.ndarray:
         hd = parse_stream_header(bs)

@@ -5,6 +5,7 @@
 #include <memory>
 
 #include "codec.h"
+#include "ctx_tc.h"
 #include "driver.h"
 #include "prof.h"
 
@@ -70,9 +71,10 @@ static PlanCache &cache_of(pw_ctx *ctx) {
 
 static std::string geo_key(const char *kind, const Geometry &g, int B, const Model &m, int params) {
   char buf[256];
-  snprintf(buf, sizeof(buf), "%s:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%p:%d", kind, g.H, g.W, g.nc,
-           g.levels, g.colour, g.bitdepth, g.lossless, g.ll_ar, g.chunk, B, (const void *)&m,
-           params);
+  // the model's unique id and channel count: a workspace is sized by both
+  snprintf(buf, sizeof(buf), "%s:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%llu:%d:%d", kind, g.H, g.W, g.nc,
+           g.levels, g.colour, g.bitdepth, g.lossless, g.ll_ar, g.chunk, B,
+           (unsigned long long)m.uid, m.C, params);
   return buf;
 }
 
@@ -125,8 +127,12 @@ static int get_plan(pw_ctx *ctx, Model &m, const Geometry &g, int B, const char 
   return PW_OK;
 }
 
-static int check_status(pw_ctx *ctx) {
+static int check_status(pw_ctx *ctx, Workspace *ws = nullptr) {
   if (launch_failed()) { launch_failed() = false; return PW_EUNSUPPORTED; }
+  if (ws && ctx->precision == PW_PREC_BF16) {
+    cudaStreamSynchronize(ctx->stream);
+    if (tc_error(*ws)) { set_last_error("a tensor-core kernel's bounded wait expired"); return PW_ETIMEOUT; }
+  }
   uint32_t st = 0;
   cudaError_t e = cudaMemcpyAsync(&st, ctx->status, 4, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -166,6 +172,7 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *co
   PW_CUDA_TRY(cudaMemcpyAsync(pl.d_ptrs.p, hs, B * 8, cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemcpyAsync(pl.d_lens.p, hs + B, B * 8, cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemsetAsync(ctx->status, 0, 4, st));
+  if (ctx->precision == PW_PREC_BF16) tc_error_reset(pl.ws, st);
   ParseExpect ex{};
   ex.width = h0.width; ex.height = h0.height; ex.ncomp = g.nc; ex.levels = g.levels;
   ex.bitdepth = g.bitdepth; ex.colour = g.colour; ex.flags = h0.flags; ex.chunk = g.chunk;
@@ -330,7 +337,7 @@ static int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, 
                                     st));
     }
   }
-  return check_status(ctx);
+  return check_status(ctx, &pl->ws);
 }
 
 // --------------------------------------------------------------------------
@@ -341,6 +348,7 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
   const int P = B * g.nc;
   cudaStream_t st = ctx->stream;
   Workspace &ws = pl.ws;
+  if (ctx->precision == PW_PREC_BF16) tc_error_reset(ws, st);
   launch_cdf_bank(ctx->bank, st);
   bump(ctx);
   for (int sb = 0; sb < g.nsb; ++sb) {
@@ -406,7 +414,7 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
   bump(ctx);
   std::vector<uint32_t> nw(nall);
   PW_CUDA_TRY(cudaMemcpyAsync(nw.data(), pl.d_nwords.p, nall * 4, cudaMemcpyDeviceToHost, st));
-  if ((s = check_status(ctx))) return s;
+  if ((s = check_status(ctx, &ws))) return s;
   // payload layout: per image, chunks in stream order
   std::vector<uint64_t> outoff(nall);
   std::vector<uint64_t> img_start(B + 1);
@@ -795,6 +803,7 @@ int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t
   if ((s = get_plan(c, m, g, 1, "par", true, &pl))) return s;
   cudaStream_t st = c->stream;
   PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.Q, q, g.plane_elems * 4, cudaMemcpyHostToDevice, st));
+  if (c->precision == PW_PREC_BF16) tc_error_reset(pl->ws, st);
   for (int sb = 0; sb < g.nsb; ++sb) {
     if (sb >= 1 && (s = run_lstm(c, m, g, pl->ws, sb))) return s;
     for (int k = 0; k < 4; ++k)
@@ -802,7 +811,12 @@ int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t
   }
   PW_CUDA_TRY(cudaMemcpyAsync(mu, pl->ws.mu, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
   PW_CUDA_TRY(cudaMemcpyAsync(sigma, pl->ws.sg, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
-  return finish(c);
+  if ((s = finish(c))) return s;
+  if (c->precision == PW_PREC_BF16 && tc_error(pl->ws)) {
+    set_last_error("a tensor-core kernel's bounded wait expired");
+    return PW_ETIMEOUT;
+  }
+  return PW_OK;
 }
 
 static int lift_stage(pw_ctx *c, const pw_model *mm, int H, int W, int lossless, const float *in,
@@ -841,6 +855,12 @@ int pw_lift_inverse(pw_ctx *c, const pw_model *m, int H, int W, int lossless, co
   return lift_stage(c, m, H, W, lossless, sb, x, false);
 }
 
+int pw_conv_bf16(pw_ctx *c, int P, int H, int W, int cin, int cout, int ks, int act,
+                 const float *x, const float *w, const float *b, float *y) {
+  if (!c || !x || !w || !b || !y) return PW_EINVAL;
+  return tc_conv_host(c, P, H, W, cin, cout, ks, act, x, w, b, y);
+}
+
 int pw_decode_symbols(pw_ctx *c, const pw_model *mm, const uint8_t *bs, size_t n, int32_t *q) {
   if (!c || !mm || !bs || !q) return PW_EINVAL;
   Model &m = const_cast<pw_model *>(mm)->m;
@@ -857,7 +877,7 @@ int pw_decode_symbols(pw_ctx *c, const pw_model *mm, const uint8_t *bs, size_t n
   if ((s = decode_symbols_dev(c, m, *pl, ptrs.data(), &n, h0))) return s;
   PW_CUDA_TRY(cudaMemcpyAsync(q, pl->ws.Q, (size_t)g.nc * g.plane_elems * 4,
                               cudaMemcpyDeviceToHost, c->stream));
-  return check_status(c);
+  return check_status(c, &pl->ws);
 }
 
 int pw_analyse(pw_ctx *c, const pw_model *mm, const pw_image *in, const pw_codec_opts *o,

@@ -33,6 +33,7 @@ struct Model {
   pw_ctx *ctx = nullptr;
   int levels = 4, C = 32, F = 16, ll_mode = 0;
   uint64_t hash = 0;
+  uint64_t uid = 0;          // unique per loaded model (keys cached workspaces)
   std::vector<float *> allocs;
   std::map<std::string, std::vector<float>> host;
   LiftNetDev lift[2][2];   // [row, col][P, U]

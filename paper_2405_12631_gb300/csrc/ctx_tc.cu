@@ -91,6 +91,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volati
     }
   }
 }
+// Bounded wait that ignores the abort flag (used to let copies land before
+// the CTA exits), about 2^28 cycles.
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity))
+    if (clock64() - t0 > (1ll << 28)) return false;
+  return true;
+}
 __device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
                                             int c0, int c1, int c2, int c3, int c4) {
   asm volatile(
@@ -267,9 +275,9 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       uint32_t ph = phase;
       for (int i = 0; i < min(issued, a.stages); ++i) {
         if (--s < 0) { s = a.stages - 1; ph ^= 1; }
-        mbar_wait(&full[s], ph, s_abort);
+        mbar_wait_drain(&full[s], ph);
       }
-      mbar_wait(wbar, 0, s_abort);
+      mbar_wait_drain(wbar, 0);
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ---------------------------------------------------------
@@ -811,6 +819,65 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
   a.mu_out = mu; a.sg_out = sgp;
   return conv(c2, t.U, G, 0, a);                                // head
+}
+
+// Stage entry: one tensor-core convolution on host data (testing).
+int tc_conv_host(pw_ctx *ctx, int P, int H, int W, int cin, int cout, int ks, int act,
+                 const float *x, const float *w, const float *b, float *y) {
+  if (!(ks == 1 || ks == 3) || cin % 32 || (cin > 64 && cin % 64) ||
+      (cout != 32 && cout != 64 && cout != 128 && cout != 192 && cout != 256) ||
+      P < 1 || H < 1 || W < 1) {
+    set_last_error("unsupported convolution shape");
+    return PW_EUNSUPPORTED;
+  }
+  TcWeights tw;
+  TcWeights::Conv cv;
+  const int ncta = cout <= 128 ? cout : 64;
+  std::vector<float> wv(w, w + (size_t)cout * cin * ks * ks), bv(b, b + cout);
+  int s = pack_conv(tw, cv, wv, bv, cout, cin, ks, ncta);
+  if (s) { for (void *q : tw.allocs) cudaFree(q); return s; }
+  const int Gi = cin / 8, Go = cout / 8;
+  const int64_t hw = (int64_t)H * W;
+  std::vector<__nv_bfloat16> xb((size_t)P * cin * hw);
+  for (int p = 0; p < P; ++p)
+    for (int64_t i = 0; i < hw; ++i)
+      for (int c = 0; c < cin; ++c)
+        xb[(((size_t)p * Gi + c / 8) * hw + i) * 8 + c % 8] =
+            __float2bfloat16(x[((size_t)p * hw + i) * cin + c]);
+  void *dx = nullptr, *dy = nullptr, *derr = nullptr;
+  const size_t ybytes = (size_t)P * cout * hw * 2;
+  if (cudaMalloc(&dx, xb.size() * 2) != cudaSuccess || cudaMalloc(&dy, ybytes) != cudaSuccess ||
+      cudaMalloc(&derr, 16) != cudaSuccess) {
+    cudaFree(dx); cudaFree(dy); cudaFree(derr);
+    for (void *q : tw.allocs) cudaFree(q);
+    set_last_error("allocation failed");
+    return PW_ENOMEM;
+  }
+  cudaMemcpy(dx, xb.data(), xb.size() * 2, cudaMemcpyHostToDevice);
+  cudaMemset(dy, 0, ybytes);
+  cudaMemset(derr, 0, 16);
+  TcConvArgs a{};
+  a.epi = TE_STORE; a.act = act; a.out = (__nv_bfloat16 *)dy; a.out_G = Go;
+  s = conv_tc(ctx, cv, (const __nv_bfloat16 *)dx, Gi, 0, P, H, W, a, (int *)derr);
+  cudaError_t e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  int err = 0;
+  if (e == cudaSuccess) cudaMemcpy(&err, derr, 4, cudaMemcpyDeviceToHost);
+  if (s == PW_OK && e == cudaSuccess && !err) {
+    std::vector<__nv_bfloat16> yb((size_t)P * cout * hw);
+    cudaMemcpy(yb.data(), dy, ybytes, cudaMemcpyDeviceToHost);
+    for (int p = 0; p < P; ++p)
+      for (int64_t i = 0; i < hw; ++i)
+        for (int c = 0; c < cout; ++c)
+          y[((size_t)p * hw + i) * cout + c] =
+              __bfloat162float(yb[(((size_t)p * Go + c / 8) * hw + i) * 8 + c % 8]);
+  }
+  cudaFree(dx); cudaFree(dy); cudaFree(derr);
+  for (void *q : tw.allocs) cudaFree(q);
+  if (s) return s;
+  if (e != cudaSuccess) { set_last_error(std::string("CUDA: ") + cudaGetErrorString(e)); return PW_ECUDA; }
+  if (err) { set_last_error("tensor-core convolution timed out (bounded wait expired)"); return PW_ETIMEOUT; }
+  return PW_OK;
 }
 
 void tc_error_reset(Workspace &ws, cudaStream_t st) {

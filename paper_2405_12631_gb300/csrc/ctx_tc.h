@@ -14,4 +14,6 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
 // reset (reads the workspace's device error word; synchronous).
 int tc_error(Workspace &ws);
 void tc_error_reset(Workspace &ws, cudaStream_t st);
+int tc_conv_host(pw_ctx *ctx, int P, int H, int W, int cin, int cout, int ks, int act,
+                 const float *x, const float *w, const float *b, float *y);
 }  // namespace pw

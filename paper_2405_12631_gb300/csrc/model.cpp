@@ -35,7 +35,9 @@ uint64_t poly_hash(const uint8_t *p, size_t n) {
 }  // namespace
 
 int Model::load(pw_ctx *c, const void *blob, size_t n) {
+  static uint64_t next_uid = 1;
   ctx = c;
+  uid = __atomic_fetch_add(&next_uid, 1, __ATOMIC_RELAXED);
   const uint8_t *b = static_cast<const uint8_t *>(blob);
   if (n < 32 || std::memcmp(b, "PWMB", 4) != 0) {
     set_last_error("weight blob: bad magic");
