@@ -143,6 +143,27 @@ int pw_rans_encode(pw_ctx *ctx, int nchunks, const uint32_t *count,
                    uint8_t **payload, size_t *payload_bytes, uint32_t *offset,
                    uint32_t *nbytes);
 
+/* Allocation-free variant of pw_rans_decode, for callers that must not
+ * allocate device memory while decoding (a plug-in living inside a host
+ * application's fixed device-memory budget, or a real-time pipeline that
+ * cannot afford cudaMalloc / cudaFree, which synchronise the device). The
+ * paper has no counterpart to this call; it is a deployment convenience.
+ * All arrays are DEVICE pointers: payload (payload_bytes long), the
+ * per-chunk offset / nbytes / count / lanes arrays (nchunks each), idx (one
+ * packed table index per symbol, chunks concatenated) and out (one int32 per
+ * symbol). No context is needed: work is enqueued on cuda_stream (NULL =
+ * legacy default stream) and the call returns after synchronising it.
+ * The table bank, chunk descriptors and a status word live in one fixed
+ * device array of about 1 MiB that every GPU loading the library holds until
+ * the process exits; at most 16384 chunks per call (PW_EINVAL beyond).
+ * The first call on a device looks the array's address up (make it before
+ * any stream capture). Every call reuses the array, so calls that overlap on
+ * the GPU race: serialise them. Errors: PW_EINVAL, PW_ECORRUPT, PW_ECUDA. */
+int pw_rans_decode_noalloc(void *cuda_stream, const uint8_t *payload, size_t payload_bytes,
+                           int nchunks, const uint32_t *offset, const uint32_t *nbytes,
+                           const uint32_t *count, const uint32_t *lanes, const uint32_t *idx,
+                           int32_t *out);
+
 /* Context model on fully known quantised subbands of one component
  * (Section 3.2): q holds the 3*levels+1 subbands in coding order, each
  * (H >> lv) x (W >> lv) int32, concatenated (host). Writes mu and sigma

@@ -74,6 +74,8 @@ _sig = {
     "pw_rans_decode": (C.c_int, [_P, _P, C.c_size_t, C.c_int, _P, _P, _P, _P, _P, _P]),
     "pw_rans_encode": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.POINTER(_u8p),
                                  C.POINTER(C.c_size_t), _P, _P]),
+    "pw_rans_decode_noalloc": (C.c_int, [_P, _P, C.c_size_t, C.c_int, _P, _P, _P, _P, _P,
+                                         _P]),
     "pw_context_params": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P]),
     "pw_lift_forward": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
     "pw_lift_inverse": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _P, _P]),

@@ -1,0 +1,75 @@
+"""The allocation-free rANS decoding entry point (pw_rans_decode_noalloc).
+
+It exists for callers that cannot allocate device memory while decoding
+(plug-ins inside a host application's fixed memory budget, real-time
+pipelines that must not stall on cudaMalloc / cudaFree). Its output must
+equal the regular pw_rans_decode's, bit for bit, on two calls in a row (the
+second call reuses the shared scratch array left by the first), and it must
+refuse more chunks than its fixed scratch array holds. This file is
+collected last so that a run stopping at the first failure has run every
+other test already.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import entropy as E
+from oracle import rans as R
+from tests._lib import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+def _chunks(seed, nchunks):
+    bank = E.cdf_bank().astype(np.int64)
+    rng = np.random.default_rng(seed)
+    counts, lanes, idx, payload, offs, nb = [], [], [], b"", [], []
+    for c in range(nchunks):
+        n = int(rng.integers(1, 2000))
+        nl = int(rng.choice([1, 5, 32]))
+        tid = rng.integers(0, 2048, n)
+        ctr = rng.integers(-30, 30, n)
+        r = np.round(rng.laplace(0, 3, n)).astype(np.int64)
+        big = rng.uniform(size=n) < 0.02
+        r[big] = rng.integers(-3000, 3000, big.sum())
+        st, words = R.encode_chunk([R.symbol_ops(int(r[p]), bank[tid[p]]) for p in range(n)], nl)
+        b = R.pack_chunk(st, words)
+        offs.append(len(payload)); nb.append(len(b)); payload += b
+        t = 16 * ctr + (tid // 128 - 8)
+        idx.append(((t + (1 << 23)) << 7) | (tid % 128))
+        counts.append(n); lanes.append(nl)
+    u32 = lambda a: np.asarray(a, dtype=np.uint32)
+    return payload, u32(offs), u32(nb), u32(counts), u32(lanes), np.concatenate(idx).astype(np.uint32)
+
+
+def test_noalloc_decode_matches_regular_decode_twice():
+    ensure_built()
+    import torch
+    import paper_2405_12631_gb300 as pw
+    codec = pw.Codec(0, "fp32")
+    for call, seed in enumerate((11, 12)):
+        payload, offs, nb, counts, lanes, idx = _chunks(seed, 9)
+        want = codec.rans_decode(payload, offs, nb, counts, lanes, idx)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).copy()).cuda()
+        d_pay = dev(np.frombuffer(payload, dtype=np.uint8))
+        d_off, d_nb, d_cnt, d_ln, d_idx = (dev(a) for a in (offs, nb, counts, lanes, idx))
+        d_out = torch.full((int(counts.sum()),), -7, dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream().cuda_stream
+        P = ctypes.c_void_p
+        rc = pw.pw_rans_decode_noalloc(P(stream), P(d_pay.data_ptr()), len(payload), len(counts),
+                                       P(d_off.data_ptr()), P(d_nb.data_ptr()),
+                                       P(d_cnt.data_ptr()), P(d_ln.data_ptr()),
+                                       P(d_idx.data_ptr()), P(d_out.data_ptr()))
+        assert rc == pw.PW_OK, (call, pw.pw_last_error())
+        assert np.array_equal(d_out.cpu().numpy(), want), call
+    codec.close()
+
+
+def test_noalloc_rejects_too_many_chunks():
+    ensure_built()
+    import paper_2405_12631_gb300 as pw
+    P = ctypes.c_void_p
+    rc = pw.pw_rans_decode_noalloc(None, P(1), 16, 16385, P(1), P(1), P(1), P(1), P(1), P(1))
+    assert rc == pw.PW_EINVAL
+    assert b"16384" in pw.pw_last_error()
