@@ -41,12 +41,19 @@ struct TcWeights {
   Conv sk_z[3], sk_c1[3], sk_c2[3];             // sb set, steps 1..3
   Conv l0_in, l0_w1, l0_w2, l0_w3, l0_w4;       // ll set
   Conv lk_z[3], lk_c1[3], lk_c2[3];
+  // steps 2-4 with the masked input conv folded into z = 1x1(l) + mix:
+  // zf = 1x1 over l only (bias includes the folded bias), fw = [9][C] taps
+  Conv sk_zf[3], lk_zf[3];
+  float *sk_fw[3] = {nullptr, nullptr, nullptr}, *lk_fw[3] = {nullptr, nullptr, nullptr};
   std::vector<void *> allocs;
 };
 
 struct TcAct {  // BF16 activations in [P][G][H][W][8]
-  __nv_bfloat16 *X = nullptr, *X2 = nullptr, *Z = nullptr, *U = nullptr, *V = nullptr,
-                *Z2 = nullptr;
+  // X: ConvLSTM input [e, up(h)] (2C); L[2]: long-term context l_i of the
+  // current and previous subband (C each, ping-pong so the gates conv can
+  // read h_{i-1} while its epilogue writes h_i); Z, V, Z2 (C); U (2C).
+  __nv_bfloat16 *X = nullptr, *L[2] = {nullptr, nullptr}, *Z = nullptr, *U = nullptr,
+                *V = nullptr, *Z2 = nullptr;
   int *err = nullptr;
   void *base = nullptr;
 };
@@ -157,7 +164,7 @@ __device__ __forceinline__ float sigm_f(float x) { return 1.f / (1.f + __expf(-x
 __device__ __forceinline__ float lrelu_f(float x) { return x >= 0.f ? x : 0.01f * x; }
 
 // ---------------------------------------------------------------------------
-enum { TE_STORE = 0, TE_LSTM = 1, TE_HEAD = 2 };
+enum { TE_STORE = 0, TE_LSTM = 1, TE_HEAD = 2, TE_FOLD = 3 };
 
 struct TcConvArgs {
   int P, H, W;
@@ -181,6 +188,11 @@ struct TcConvArgs {
   uint32_t *idx;
   int64_t idx_stride;
   float *mu_out, *sg_out;
+  // TE_FOLD: v += sum_tap fold_w[tap][c] * (m_<step s)(y+dy, x+dx), then store
+  const float *fold_w;          // [9][ncta] (already including the 1x1 mix)
+  const int32_t *fold_s;        // quantised subband [P][H][W]
+  int nkb0;                     // K-blocks read through the first tensor map
+  int in1_goff;                 // group offset of the second tensor map
   int *err;
 };
 
@@ -209,6 +221,7 @@ __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *p, float *v) {
 
 template <int NCTA>
 __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap,
+                                                    const __grid_constant__ CUtensorMap tmap1,
                                                     const TcConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem);       // [8]
@@ -263,8 +276,15 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       for (int kbi = 0; kbi < a.nkb; ++kbi) {
         if (!mbar_wait(&empty[stage], phase ^ 1, s_abort)) break;
         mbar_expect_tx(&full[stage], a.stage_bytes);
-        tma_load_5d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage], 0,
-                    tx * kTileW - R, ty * kTileH - R, a.in_goff + kbi * (a.kb / 8), p);
+        // K-blocks [0, nkb0) come through tmap (group offset in_goff), the
+        // rest through tmap1 (groups counted from 0)
+        if (kbi < a.nkb0)
+          tma_load_5d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage], 0,
+                      tx * kTileW - R, ty * kTileH - R, a.in_goff + kbi * (a.kb / 8), p);
+        else
+          tma_load_5d(stg + (size_t)stage * a.stage_bytes, &tmap1, &full[stage], 0,
+                      tx * kTileW - R, ty * kTileH - R, a.in1_goff + (kbi - a.nkb0) * (a.kb / 8),
+                      p);
         ++issued;
         if (++stage == a.stages) { stage = 0; phase ^= 1; }
       }
@@ -352,7 +372,35 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       const int n0 = nb * NCTA;
 #pragma unroll
       for (int j = 0; j < NCTA; ++j) v[j] += a.bias[n0 + j];
-      if (a.epi == TE_STORE) {
+      if (a.epi == TE_FOLD) {
+        if (valid) {
+          const int32_t *sp = a.fold_s + (int64_t)p * hw;
+          float nbv[9];
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            nbv[tap] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && step_of(yy, xx) < a.step)
+                           ? (float)sp[(int64_t)yy * a.W + xx]
+                           : 0.f;
+          }
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            const float4 *wr = reinterpret_cast<const float4 *>(a.fold_w + tap * NCTA);
+#pragma unroll
+            for (int j = 0; j < NCTA / 4; ++j) {
+              const float4 w4 = __ldg(wr + j);
+              v[4 * j] = fmaf(w4.x, nbv[tap], v[4 * j]);
+              v[4 * j + 1] = fmaf(w4.y, nbv[tap], v[4 * j + 1]);
+              v[4 * j + 2] = fmaf(w4.z, nbv[tap], v[4 * j + 2]);
+              v[4 * j + 3] = fmaf(w4.w, nbv[tap], v[4 * j + 3]);
+            }
+          }
+#pragma unroll
+          for (int g = 0; g < NCTA / 8; ++g)
+            store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (n0 >> 3) + g) * hw + pix) * 8,
+                         v + 8 * g);
+        }
+      } else if (a.epi == TE_STORE) {
         if (valid) {
 #pragma unroll
           for (int g = 0; g < NCTA / 8; ++g) {
@@ -427,22 +475,24 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
 // ---------------------------------------------------------------------------
 // SIMT helper kernels on the blocked BF16 layout.
 
-// X[:, 0:C] = conv3x3(1->C)(up(s_prev)) + be; X[:, C:2C] = up(h_prev)
-// (h_prev read from X2 groups [C/8, C/4) at the previous resolution).
+// ConvLSTM input, one thread per pixel: X[:, 0:C] = conv3x3(1->C)(up(s_prev))
+// + be and, when copy_h is set, X[:, C:2C] = up(h_prev) (h_prev: C channels
+// at the previous resolution). With copy_h = 0 the gates conv reads h_prev
+// from its own buffer instead.
 __global__ void k_lstm_in_bf16(const int32_t *__restrict__ s_prev,
-                               const __nv_bfloat16 *__restrict__ X2prev,
+                               const __nv_bfloat16 *__restrict__ hprev,
                                const float *__restrict__ we, const float *__restrict__ be,
                                __nv_bfloat16 *__restrict__ X, int P, int H, int W, int C, int up,
-                               int first) {
+                               int copy_h, int first) {
   const int G = C / 8;
-  const int64_t n = (int64_t)P * H * W * G;
+  const int64_t n = (int64_t)P * H * W;
   const int Hp = H >> up, Wp = W >> up;
+  const int64_t hw = (int64_t)H * W;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(e % W);
     const int y = (int)((e / W) % H);
-    const int g = (int)((e / ((int64_t)W * H)) % G);
-    const int p = (int)(e / ((int64_t)W * H * G));
+    const int p = (int)(e / hw);
     const int32_t *sp = s_prev + (int64_t)p * Hp * Wp;
     float nb[9];
 #pragma unroll
@@ -452,57 +502,27 @@ __global__ void k_lstm_in_bf16(const int32_t *__restrict__ s_prev,
                     ? (float)sp[(int64_t)(yy >> up) * Wp + (xx >> up)]
                     : 0.f;
     }
-    float v[8];
+    const int64_t pix = (int64_t)y * W + x;
+    for (int g = 0; g < G; ++g) {
+      float v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int c = 8 * g + k;
-      float s = be[c];
+      for (int k = 0; k < 8; ++k) {
+        const int c = 8 * g + k;
+        float s = __ldg(be + c);
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) s = fmaf(we[c * 9 + tap], nb[tap], s);
-      v[k] = s;
+        for (int tap = 0; tap < 9; ++tap) s = fmaf(__ldg(we + c * 9 + tap), nb[tap], s);
+        v[k] = s;
+      }
+      store_bf16x8(X + (((int64_t)p * 2 * G + g) * hw + pix) * 8, v);
+      if (copy_h) {
+        float hv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        if (!first)
+          load_bf16x8(hprev + (((int64_t)p * G + g) * ((int64_t)Hp * Wp) +
+                               (int64_t)(y >> up) * Wp + (x >> up)) * 8,
+                      hv);
+        store_bf16x8(X + (((int64_t)p * 2 * G + G + g) * hw + pix) * 8, hv);
+      }
     }
-    const int64_t hw = (int64_t)H * W;
-    store_bf16x8(X + (((int64_t)p * 2 * G + g) * hw + (int64_t)y * W + x) * 8, v);
-    float hv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    if (!first)
-      load_bf16x8(X2prev + (((int64_t)p * 2 * G + G + g) * ((int64_t)Hp * Wp) +
-                            (int64_t)(y >> up) * Wp + (x >> up)) * 8,
-                  hv);
-    store_bf16x8(X + (((int64_t)p * 2 * G + G + g) * hw + (int64_t)y * W + x) * 8, hv);
-  }
-}
-
-// X2[:, 0:C] = conv3x3(1->C)(m_<step * s) + ba
-__global__ void k_masked_in_bf16(const int32_t *__restrict__ s, const float *__restrict__ wa,
-                                 const float *__restrict__ ba, __nv_bfloat16 *__restrict__ X2,
-                                 int P, int H, int W, int C, int step) {
-  const int G = C / 8;
-  const int64_t n = (int64_t)P * H * W * G;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(e % W);
-    const int y = (int)((e / W) % H);
-    const int g = (int)((e / ((int64_t)W * H)) % G);
-    const int p = (int)(e / ((int64_t)W * H * G));
-    const int32_t *sp = s + (int64_t)p * H * W;
-    float nb[9];
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-      nb[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W && step_of(yy, xx) < step)
-                    ? (float)sp[(int64_t)yy * W + xx]
-                    : 0.f;
-    }
-    float v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int c = 8 * g + k;
-      float sum = ba[c];
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) sum = fmaf(wa[c * 9 + tap], nb[tap], sum);
-      v[k] = sum;
-    }
-    store_bf16x8(X2 + (((int64_t)p * 2 * G + g) * ((int64_t)H * W) + (int64_t)y * W + x) * 8, v);
   }
 }
 
@@ -577,8 +597,12 @@ static int make_map(CUtensorMap *map, const __nv_bfloat16 *base, int P, int G, i
 static int g_num_sms = 0;
 
 // Launch one tensor-core convolution.
+// in / in_G / in_goff: the input tensor of the first nkb0 K-blocks (all of
+// them when in1 is null); in1 / in1_G: the input of the remaining K-blocks.
 static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *in, int in_G,
-                   int in_goff, int P, int H, int W, TcConvArgs a, int *err) {
+                   int in_goff, int P, int H, int W, TcConvArgs a, int *err,
+                   const __nv_bfloat16 *in1 = nullptr, int in1_G = 0, int in1_goff = 0,
+                   int nkb0 = -1) {
   if (!g_num_sms) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -601,9 +625,17 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
   if (stages < 2) { set_last_error("tensor-core conv does not fit in shared memory"); return PW_EUNSUPPORTED; }
   a.stages = stages;
   const size_t smem = fixed + (size_t)stages * a.stage_bytes;
-  CUtensorMap map;
+  CUtensorMap map, map1;
   int s = make_map(&map, in, P, in_G, H, W, a.halo_x, a.halo_y, cv.kb / 8);
   if (s) return s;
+  a.nkb0 = a.nkb;
+  a.in1_goff = in1_goff;
+  if (in1) {
+    a.nkb0 = nkb0;
+    if ((s = make_map(&map1, in1, P, in1_G, H, W, a.halo_x, a.halo_y, cv.kb / 8))) return s;
+  } else {
+    map1 = map;
+  }
   int per_nb = g_num_sms / cv.nb;
   if (per_nb < 1) per_nb = 1;
   if (per_nb > a.tiles) per_nb = a.tiles;
@@ -617,7 +649,7 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
                            (int)maxsm);                                                     \
       attr = true;                                                                          \
     }                                                                                       \
-    k_conv_tc<N_><<<grid, 192, smem, st>>>(map, a);                                         \
+    k_conv_tc<N_><<<grid, 192, smem, st>>>(map, map1, a);                                   \
     ctx->launches += 1;                                                                     \
     return PW_OK;                                                                           \
   }
@@ -628,10 +660,14 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
 }
 
 // ---- weights -------------------------------------------------------------
+// kb: channels per K-block (0 = min(cin, 64)); the ConvLSTM gates use kb = C
+// so that every K-block is either all e channels or all h channels.
 static int pack_conv(TcWeights &tw, TcWeights::Conv &cv, const std::vector<float> &w,
-                     const std::vector<float> &b, int cout, int cin, int ks, int ncta) {
+                     const std::vector<float> &b, int cout, int cin, int ks, int ncta,
+                     int kb = 0) {
   // w: [cout][cin][ks*ks] (output order as the kernel's columns)
-  cv.cin = cin; cv.cout = cout; cv.ks = ks; cv.kb = cin >= 64 ? 64 : cin; cv.ncta = ncta;
+  cv.cin = cin; cv.cout = cout; cv.ks = ks; cv.kb = kb ? kb : (cin >= 64 ? 64 : cin);
+  cv.ncta = ncta;
   cv.nb = cout / ncta;
   const int taps = ks * ks, nkb = cin / cv.kb, gpb = cv.kb / 8;
   std::vector<__nv_bfloat16> h((size_t)cout * cin * taps);
@@ -665,7 +701,7 @@ int Model::ensure_tc() {
   std::unique_ptr<TcWeights> t(new TcWeights());
   int s;
   auto H = [&](const std::string &n) -> const std::vector<float> & { return host.at(n); };
-  if ((s = pack_conv(*t, t->gates, H("lstm.wg.perm"), H("lstm.bg.perm"), 4 * C, 2 * C, 3, 64)))
+  if ((s = pack_conv(*t, t->gates, H("lstm.wg.perm"), H("lstm.bg.perm"), 4 * C, 2 * C, 3, 64, C)))
     return s;
   auto set = [&](const std::string &ns, TcWeights::Conv &in_, TcWeights::Conv &w1,
                  TcWeights::Conv &w2, TcWeights::Conv &w3, TcWeights::Conv &w4,
@@ -688,6 +724,38 @@ int Model::ensure_tc() {
   if ((s = set("sb", t->s0_in, t->s0_w1, t->s0_w2, t->s0_w3, t->s0_w4, t->sk_z, t->sk_c1,
                t->sk_c2)))
     return s;
+  // Steps 2-4: z = Wz [a; l] + bz with a = Wa * (m s) + ba is linear in a,
+  // so z = Wz_l l + sum_tap (Wz_a Wa[:, tap]) (m s)(tap) + (Wz_a ba + bz):
+  // the tensor cores do the 1x1 over l, the epilogue the 9-tap term.
+  auto fold = [&](const std::string &ns, TcWeights::Conv *zf, float **fw) -> int {
+    for (int k = 1; k < 4; ++k) {
+      const std::string q = ns + ".s" + std::to_string(k) + ".";
+      const std::vector<float> &wz = H(q + "wz"), &bz = H(q + "bz"), &wa = H(q + "wa"),
+                               &ba = H(q + "ba");
+      std::vector<float> wl((size_t)C * C), bf(C), wf((size_t)9 * C);
+      for (int c = 0; c < C; ++c) {
+        double bacc = bz[c];
+        for (int j = 0; j < C; ++j) {
+          wl[(size_t)c * C + j] = wz[(size_t)c * 2 * C + C + j];
+          bacc += (double)wz[(size_t)c * 2 * C + j] * ba[j];
+        }
+        bf[c] = (float)bacc;
+        for (int tap = 0; tap < 9; ++tap) {
+          double acc = 0.0;
+          for (int j = 0; j < C; ++j) acc += (double)wz[(size_t)c * 2 * C + j] * wa[j * 9 + tap];
+          wf[(size_t)tap * C + c] = (float)acc;
+        }
+      }
+      int r;
+      if ((r = pack_conv(*t, zf[k - 1], wl, bf, C, C, 1, C))) return r;
+      if (cudaMalloc(&fw[k - 1], wf.size() * 4) != cudaSuccess) return PW_ENOMEM;
+      t->allocs.push_back(fw[k - 1]);
+      cudaMemcpy(fw[k - 1], wf.data(), wf.size() * 4, cudaMemcpyHostToDevice);
+    }
+    return PW_OK;
+  };
+  if ((s = fold("sb", t->sk_zf, t->sk_fw))) return s;
+  if (ll_mode == 0 && (s = fold("ll", t->lk_zf, t->lk_fw))) return s;
   if (ll_mode == 0 &&
       (s = set("ll", t->l0_in, t->l0_w1, t->l0_w2, t->l0_w3, t->l0_w4, t->lk_z, t->lk_c1,
                t->lk_c2)))
@@ -707,8 +775,9 @@ void Model::free_tc() {
 int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
   const int64_t big = (int64_t)ws->P * g.sh.back() * g.sw.back();
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
-  const int64_t sizes[6] = {big * 2 * C * 2, big * 2 * C * 2, big * C * 2,
-                            big * 2 * C * 2, big * C * 2,     big * C * 2};
+  // X (2C), L0 (C), L1 (C), Z (C), U (2C), V (C), Z2 (C); bf16
+  const int64_t sizes[7] = {big * 2 * C * 2, big * C * 2, big * C * 2, big * C * 2,
+                            big * 2 * C * 2, big * C * 2, big * C * 2};
   int64_t tot = 1024;
   for (int64_t v : sizes) tot += al(v);
   TcAct *t = new TcAct();
@@ -721,8 +790,8 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
   t->err = reinterpret_cast<int *>(b);
   cudaMemset(t->err, 0, 1024);
   int64_t o = 1024;
-  __nv_bfloat16 **dst[6] = {&t->X, &t->X2, &t->Z, &t->U, &t->V, &t->Z2};
-  for (int i = 0; i < 6; ++i) { *dst[i] = reinterpret_cast<__nv_bfloat16 *>(b + o); o += al(sizes[i]); }
+  __nv_bfloat16 **dst[7] = {&t->X, &t->L[0], &t->L[1], &t->Z, &t->U, &t->V, &t->Z2};
+  for (int i = 0; i < 7; ++i) { *dst[i] = reinterpret_cast<__nv_bfloat16 *>(b + o); o += al(sizes[i]); }
   ws->tc = t;
   return PW_OK;
 }
@@ -745,18 +814,27 @@ int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   TcAct &t = *static_cast<TcAct *>(ws.tc);
   const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P, G = C / 8;
   const double pix = (double)P * h * w;
+  __nv_bfloat16 *lprev = t.L[(sb - 1) & 1], *lout = t.L[sb & 1];
+  // h_{i-1} is copied into X only when it must be upsampled (or when a
+  // K-block would mix e and h channels); otherwise the gates conv reads it
+  // from lprev directly
+  const int copy_h = (up || m.tc->gates.kb != C) ? 1 : 0;
   {
-    ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 4.0 * C));
-    k_lstm_in_bf16<<<grid_for((int64_t)P * h * w * G), 256, 0, ctx->stream>>>(
-        sprev, t.X2, m.lstm_we, m.lstm_be, t.X, P, h, w, C, up, first);
+    ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 2.0 * C * (copy_h ? 3 : 1)));
+    k_lstm_in_bf16<<<grid_for((int64_t)P * h * w), 256, 0, ctx->stream>>>(
+        sprev, lprev, m.lstm_we, m.lstm_be, t.X, P, h, w, C, up, copy_h, first);
     ctx->launches += 1;
   }
   TcConvArgs a{};
   a.epi = TE_LSTM;
-  a.out = t.X2; a.out_G = 2 * G; a.out_goff = G;
+  a.out = lout; a.out_G = G; a.out_goff = 0;
   a.c_prev = ws.Cst[cur]; a.c_new = ws.Cst[cur ^ 1]; a.up = up; a.first = first; a.C = C;
-  ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * 2 * C * 4 * C, pix * (2.0 * 2 * C + 2.0 * C + 8.0 * C));
-  return conv_tc(ctx, m.tc->gates, t.X, 2 * G, 0, P, h, w, a, t.err);
+  ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * 2 * C * 4 * C,
+               pix * (2.0 * 2 * C + 2.0 * C + 8.0 * C));
+  if (copy_h) return conv_tc(ctx, m.tc->gates, t.X, 2 * G, 0, P, h, w, a, t.err);
+  // same resolution: e from X, h_{i-1} straight from the previous l buffer
+  // (for subband 2 that buffer holds the LL subband's l = 0)
+  return conv_tc(ctx, m.tc->gates, t.X, 2 * G, 0, P, h, w, a, t.err, lprev, G, 0, 1);
 }
 
 int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb, int step,
@@ -768,24 +846,25 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P, G = C / 8;
   cudaStream_t st = ctx->stream;
   const double pix = (double)P * h * w;
+  __nv_bfloat16 *l = t.L[sb & 1];
   auto conv = [&](const TcWeights::Conv &cv, const __nv_bfloat16 *in, int in_G, int in_goff,
-                  TcConvArgs a) {
+                  TcConvArgs a, double extra_flops) {
     ProfScope ps(ctx, cv.ks == 3 ? KC_CONV3 : KC_CONV1,
-                 2.0 * pix * cv.ks * cv.ks * cv.cin * cv.cout,
+                 2.0 * pix * cv.ks * cv.ks * cv.cin * cv.cout + extra_flops,
                  pix * 2.0 * (cv.cin + cv.cout + (a.res ? cv.cout : 0)));
     return conv_tc(ctx, cv, in, in_G, in_goff, P, h, w, a, t.err);
   };
   int s;
-  if (ll && step == 0) cudaMemsetAsync(t.X2, 0, (size_t)P * h * w * 2 * C * 2, st);
+  if (ll && step == 0) cudaMemsetAsync(l, 0, (size_t)P * h * w * C * 2, st);  // l = 0 for LL
   if (step == 0) {
     const TcWeights::Conv &cin_ = ll ? W.l0_in : W.s0_in, &c1 = ll ? W.l0_w1 : W.s0_w1,
                           &c2 = ll ? W.l0_w2 : W.s0_w2, &c3 = ll ? W.l0_w3 : W.s0_w3,
                           &c4 = ll ? W.l0_w4 : W.s0_w4;
     TcConvArgs a{};
     a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
-    if ((s = conv(cin_, t.X2, 2 * G, G, a))) return s;           // z = 1x1(l)
+    if ((s = conv(cin_, l, G, 0, a, 0))) return s;                 // z = 1x1(l)
     a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
-    if ((s = conv(c1, t.Z, G, 0, a))) return s;                  // u = lrelu(1x1 z)
+    if ((s = conv(c1, t.Z, G, 0, a, 0))) return s;                 // u = lrelu(1x1 z)
     {
       ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * 4.0 * C);
       k_dw3x3_bf16<<<grid_for((int64_t)P * h * w * G), 256, 0, st>>>(t.U, n.wdw, n.bdw, t.V, P, h,
@@ -793,32 +872,27 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
       ctx->launches += 1;
     }
     a = TcConvArgs{}; a.epi = TE_STORE; a.out = t.Z2; a.out_G = G; a.res = t.Z; a.res_G = G;
-    if ((s = conv(c2, t.V, G, 0, a))) return s;                  // z2 = z + 1x1(v)
+    if ((s = conv(c2, t.V, G, 0, a, 0))) return s;                 // z2 = z + 1x1(v)
     a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = 2 * G;
-    if ((s = conv(c3, t.Z2, G, 0, a))) return s;                 // u2 = lrelu(1x1 z2)
+    if ((s = conv(c3, t.Z2, G, 0, a, 0))) return s;                // u2 = lrelu(1x1 z2)
     a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z2; a.res_G = G;
     a.wh = n.wh; a.bh = n.bh; a.step = 0; a.idx = idx; a.idx_stride = nk;
     a.mu_out = mu; a.sg_out = sgp;
-    return conv(c4, t.U, 2 * G, 0, a);                           // head
+    return conv(c4, t.U, 2 * G, 0, a, 0);                          // head
   }
-  const TcWeights::Conv &cz = ll ? W.lk_z[step - 1] : W.sk_z[step - 1];
+  const TcWeights::Conv &zf = ll ? W.lk_zf[step - 1] : W.sk_zf[step - 1];
+  const float *fw = ll ? W.lk_fw[step - 1] : W.sk_fw[step - 1];
   const TcWeights::Conv &c1 = ll ? W.lk_c1[step - 1] : W.sk_c1[step - 1];
   const TcWeights::Conv &c2 = ll ? W.lk_c2[step - 1] : W.sk_c2[step - 1];
-  {
-    ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 2.0 * C));
-    k_masked_in_bf16<<<grid_for((int64_t)P * h * w * G), 256, 0, st>>>(Qi, n.wa, n.ba, t.X2, P,
-                                                                        h, w, C, step);
-    ctx->launches += 1;
-  }
   TcConvArgs a{};
-  a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
-  if ((s = conv(cz, t.X2, 2 * G, 0, a))) return s;               // z = 1x1[a, l]
+  a.epi = TE_FOLD; a.out = t.Z; a.out_G = G; a.fold_w = fw; a.fold_s = Qi; a.step = step;
+  if ((s = conv(zf, l, G, 0, a, 2.0 * pix * 9 * C))) return s;    // z = 1x1 l + mixed taps
   a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
-  if ((s = conv(c1, t.Z, G, 0, a))) return s;                    // u = lrelu(conv3x3 z)
+  if ((s = conv(c1, t.Z, G, 0, a, 0))) return s;                  // u = lrelu(conv3x3 z)
   a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z; a.res_G = G;
   a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
   a.mu_out = mu; a.sg_out = sgp;
-  return conv(c2, t.U, G, 0, a);                                // head
+  return conv(c2, t.U, G, 0, a, 0);                                // head
 }
 
 // Stage entry: one tensor-core convolution on host data (testing).

@@ -23,12 +23,29 @@ constexpr int L1 = LT + 4;        // layer-1 region (20)
 constexpr int L2 = LT + 2;        // layer-2 region (18)
 constexpr int LI = LT + 6;        // input region (22)
 
+// Shared memory of one tile. Weights are stored tap-major with the output
+// (or input) channel innermost so that 16 of them come in four broadcast
+// 128-bit loads: w1t[tap][c], w2t[tap][ci][c], w3t[tap][ci].
 struct LiftSmem {
-  float in[LI * LI];
-  float a1[L1 * L1 * LF];
-  float a2[L2 * L2 * LF];
-  float w1[LF * 9], b1[LF], w2[LF * LF * 9], b2[LF], w3[LF * 9], b3[1];
+  alignas(16) float in[LI * LI];
+  alignas(16) float a1[L1 * L1 * LF];
+  alignas(16) float a2[L2 * L2 * LF];
+  alignas(16) float w1t[9 * LF];
+  alignas(16) float w2t[9 * LF * LF];
+  alignas(16) float w3t[9 * LF];
+  alignas(16) float b1[LF];
+  alignas(16) float b2[LF];
+  alignas(16) float b3[4];
 };
+
+__device__ __forceinline__ void ld16(const float *p, float *v) {
+  const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float4 f = q[i];
+    v[4 * i] = f.x; v[4 * i + 1] = f.y; v[4 * i + 2] = f.z; v[4 * i + 3] = f.w;
+  }
+}
 
 __device__ __forceinline__ float acc_get(const PlaneAcc &a, int p, int y, int x) {
   return a.p[(int64_t)p * a.ps + (int64_t)y * a.rs + (int64_t)x * a.cs];
@@ -51,8 +68,15 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
     S.in[e] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? acc_get(a.src, p, yy, xx) : 0.f;
   }
   if (cnn) {
-    for (int e = t; e < LF * 9; e += 256) { S.w1[e] = a.net.w1[e]; S.w3[e] = a.net.w3[e]; }
-    for (int e = t; e < LF * LF * 9; e += 256) S.w2[e] = a.net.w2[e];
+    for (int e = t; e < LF * 9; e += 256) {
+      const int c = e / 9, tap = e % 9;  // source [c][tap]
+      S.w1t[tap * LF + c] = a.net.w1[e];
+      S.w3t[tap * LF + c] = a.net.w3[e];
+    }
+    for (int e = t; e < LF * LF * 9; e += 256) {
+      const int c = e / (LF * 9), ci = (e / 9) % LF, tap = e % 9;  // source [c][ci][tap]
+      S.w2t[(tap * LF + ci) * LF + c] = a.net.w2[e];
+    }
     if (t < LF) { S.b1[t] = a.net.b1[t]; S.b2[t] = a.net.b2[t]; }
     if (t == 0) S.b3[0] = a.net.b3[0];
   }
@@ -64,37 +88,61 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
       const int ly = e / L1, lx = e % L1;
       const int yy = y0 + ly - 2, xx = x0 + lx - 2;
       const bool inside = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-      float iv[9];
+      float acc[LF], w[LF];
+      ld16(S.b1, acc);
 #pragma unroll
-      for (int tap = 0; tap < 9; ++tap) iv[tap] = S.in[(ly + tap / 3) * LI + lx + tap % 3];
+      for (int tap = 0; tap < 9; ++tap) {
+        const float iv = S.in[(ly + tap / 3) * LI + lx + tap % 3];
+        ld16(S.w1t + tap * LF, w);
 #pragma unroll
-      for (int c = 0; c < LF; ++c) {
-        float v = S.b1[c];
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) v = fmaf(S.w1[c * 9 + tap], iv[tap], v);
-        S.a1[e * LF + c] = inside ? tanhf(v) : 0.f;
+        for (int c = 0; c < LF; ++c) acc[c] = fmaf(w[c], iv, acc[c]);
       }
+      float4 *dst = reinterpret_cast<float4 *>(S.a1 + e * LF);
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        dst[i] = inside ? make_float4(tanhf(acc[4 * i]), tanhf(acc[4 * i + 1]),
+                                      tanhf(acc[4 * i + 2]), tanhf(acc[4 * i + 3]))
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    // layer 2 on the 18 x 18 region (origin y0 - 1, x0 - 1)
-    for (int e = t; e < L2 * L2; e += 256) {
-      const int ly = e / L2, lx = e % L2;
-      const int yy = y0 + ly - 1, xx = x0 + lx - 1;
-      const bool inside = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-      float acc[LF];
-#pragma unroll
-      for (int c = 0; c < LF; ++c) acc[c] = S.b2[c];
+    // layer 2 on the 18 x 18 region (origin y0 - 1, x0 - 1): 324 positions,
+    // two per thread (threads 0..161) so that every weight load feeds 32 FMAs
+    constexpr int kHalf = L2 * L2 / 2;
+    if (t < kHalf) {
+      const int e0 = t, e1 = t + kHalf;
+      const int ly0 = e0 / L2, lx0 = e0 % L2, ly1 = e1 / L2, lx1 = e1 % L2;
+      float acc0[LF], acc1[LF];
+      ld16(S.b2, acc0);
+      ld16(S.b2, acc1);
       for (int tap = 0; tap < 9; ++tap) {
-        const float *src = &S.a1[((ly + tap / 3) * L1 + lx + tap % 3) * LF];
+        float in0v[LF], in1v[LF];
+        ld16(S.a1 + ((ly0 + tap / 3) * L1 + lx0 + tap % 3) * LF, in0v);
+        ld16(S.a1 + ((ly1 + tap / 3) * L1 + lx1 + tap % 3) * LF, in1v);
 #pragma unroll
         for (int ci = 0; ci < LF; ++ci) {
-          const float v = src[ci];
+          float w[LF];
+          ld16(S.w2t + (tap * LF + ci) * LF, w);
 #pragma unroll
-          for (int c = 0; c < LF; ++c) acc[c] = fmaf(S.w2[(c * LF + ci) * 9 + tap], v, acc[c]);
+          for (int c = 0; c < LF; ++c) {
+            acc0[c] = fmaf(w[c], in0v[ci], acc0[c]);
+            acc1[c] = fmaf(w[c], in1v[ci], acc1[c]);
+          }
         }
       }
+      const int yy0 = y0 + ly0 - 1, xx0 = x0 + lx0 - 1, yy1 = y0 + ly1 - 1, xx1 = x0 + lx1 - 1;
+      const bool in0 = yy0 >= 0 && yy0 < a.H && xx0 >= 0 && xx0 < a.W;
+      const bool in1 = yy1 >= 0 && yy1 < a.H && xx1 >= 0 && xx1 < a.W;
+      float4 *d0 = reinterpret_cast<float4 *>(S.a2 + e0 * LF);
+      float4 *d1 = reinterpret_cast<float4 *>(S.a2 + e1 * LF);
 #pragma unroll
-      for (int c = 0; c < LF; ++c) S.a2[e * LF + c] = inside ? tanhf(acc[c]) : 0.f;
+      for (int i = 0; i < 4; ++i) {
+        d0[i] = in0 ? make_float4(tanhf(acc0[4 * i]), tanhf(acc0[4 * i + 1]),
+                                  tanhf(acc0[4 * i + 2]), tanhf(acc0[4 * i + 3]))
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        d1[i] = in1 ? make_float4(tanhf(acc1[4 * i]), tanhf(acc1[4 * i + 1]),
+                                  tanhf(acc1[4 * i + 2]), tanhf(acc1[4 * i + 3]))
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
     __syncthreads();
     // layer 3 on the 16 x 16 outputs
@@ -102,9 +150,11 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
       const int ly = t / LT, lx = t % LT;
       float v = S.b3[0];
       for (int tap = 0; tap < 9; ++tap) {
-        const float *src = &S.a2[((ly + tap / 3) * L2 + lx + tap % 3) * LF];
+        float xv[LF], w[LF];
+        ld16(S.a2 + ((ly + tap / 3) * L2 + lx + tap % 3) * LF, xv);
+        ld16(S.w3t + tap * LF, w);
 #pragma unroll
-        for (int ci = 0; ci < LF; ++ci) v = fmaf(S.w3[ci * 9 + tap], src[ci], v);
+        for (int ci = 0; ci < LF; ++ci) v = fmaf(w[ci], xv[ci], v);
       }
       r_out = v;
     }

@@ -184,7 +184,7 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
       const std::string p = ns + ".s" + std::to_string(k) + ".";
       std::vector<float> w, bb;
       if (!get(p + "wa", {C, 1, 3, 3}, w) || !get(p + "ba", {C}, bb)) return false;
-      s.wa = up(w); s.ba = up(bb);
+      s.wa = up(w); s.ba = up(bb); keep(p + "wa", w); keep(p + "ba", bb);
       if (!get(p + "wz", {C, 2 * C}, w) || !get(p + "bz", {C}, bb)) return false;
       s.wz = up(transpose(w, C, 2 * C)); s.bz = up(bb); keep(p + "wz", w); keep(p + "bz", bb);
       if (!get(p + "w1", {C, C, 3, 3}, w) || !get(p + "b1", {C}, bb)) return false;
