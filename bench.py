@@ -51,10 +51,10 @@ def dist_info():
     return rank, world, local
 
 
-def make_inputs(seed_base: int):
+def make_inputs(seed_base: int, batch: int):
     import synthetic as S
-    imgs = [S.rgb_natural(H, W, seed=seed_base + i) for i in range(BATCH)]
-    qs = [QSTEPS[i % 4] for i in range(BATCH)]
+    imgs = [S.rgb_natural(H, W, seed=seed_base + i) for i in range(batch)]
+    qs = [QSTEPS[i % 4] for i in range(batch)]
     return imgs, qs
 
 
@@ -206,10 +206,13 @@ def run_gpu(args):
     codec = pw.Codec(local, args.precision, stream=stream.cuda_stream)
     blob = model_blob()
     model = codec.load_model(blob)
-    imgs, qs = make_inputs(1 + 1000 * rank)
+    BATCH = args.batch
+    imgs, qs = make_inputs(1 + 1000 * rank, BATCH)
     streams = []
     for q in QSTEPS:
         idx = [i for i in range(BATCH) if qs[i] == q]
+        if not idx:
+            continue
         enc = codec.encode_batch(model, [imgs[i] for i in idx], q=q)
         streams += list(zip(idx, enc))
     streams = [s for _, s in sorted(streams, key=lambda t: t[0])]
@@ -317,7 +320,8 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "global_batch": BATCH * world, "image": "768x512 RGB",
+        "config": {"workload": WORKLOAD if BATCH == 24 else WORKLOAD.replace("24", str(BATCH), 1),
+                   "global_batch": BATCH * world, "image": "768x512 RGB",
                    "context_channels": 64, "levels": 4, "ll_mode": "four-step",
                    "precision": args.precision, "parallelism": f"replicas x{world}",
                    "l2": "flushed (256 MB write) between timed steps",
@@ -352,6 +356,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=os.environ.get("PW_BENCH_PRECISION", "bf16"),
                     choices=["fp32", "bf16"])
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="images per step (24 = the benchmark workload; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

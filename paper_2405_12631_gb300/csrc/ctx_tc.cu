@@ -3,10 +3,10 @@
 // tensor memory, operand tiles brought in by TMA, fused epilogues.
 //
 // Activations are BF16 in a channel-group-blocked layout [P][G][H][W][8]
-// (G = channels / 8), so that a TMA box (8 channels, tile width + halo,
+// (G = channels / 8), so that a TMA box ((tile width + halo) x 8 channels,
 // tile height + halo, groups) lands in shared memory as one slab of 16-byte
-// rows per channel group: exactly the no-swizzle K-major core-matrix layout
-// of the MMA A operand. A 3x3 tap is then just a shifted start address into
+// pixel rows per channel group: exactly the no-swizzle K-major core-matrix
+// layout of the MMA A operand. A 3x3 tap is then just a shifted start address into
 // the halo tile, so every input pixel is loaded once per K-block.
 //
 // GEMM view: M = 128 output pixels (16 rows x 8 columns of one plane),
@@ -84,15 +84,28 @@ __device__ __forceinline__ bool mbar_try(uint64_t *bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// try_wait that may suspend the thread for up to ~hint_ns before failing,
+// so waiting warps do not compete for issue slots with working ones.
+__device__ __forceinline__ bool mbar_try_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
 // Bounded wait (about 2^31 clock cycles, ~1 s). Returns false on expiry or
 // when another role has already aborted.
 constexpr long long kWaitCycles = 1ll << 31;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort,
+                                          uint32_t hint_ns = 0) {
   if (mbar_try(bar, parity)) return true;
   const long long t0 = clock64();
   for (uint32_t i = 0;; ++i) {
-    if (mbar_try(bar, parity)) return true;
-    if ((i & 63) == 0) {
+    if (hint_ns ? mbar_try_sleep(bar, parity, hint_ns) : mbar_try(bar, parity)) return true;
+    if ((i & 15) == 0) {
       if (*abort) return false;
       if (clock64() - t0 > kWaitCycles) { *abort = 1; return false; }
     }
@@ -106,12 +119,12 @@ __device__ __forceinline__ bool mbar_wait_drain(uint64_t *bar, uint32_t parity) 
     if (clock64() - t0 > (1ll << 28)) return false;
   return true;
 }
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, uint64_t *bar,
-                                            int c0, int c1, int c2, int c3, int c4) {
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar,
+                                            int c0, int c1, int c2, int c3) {
   asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4, %5, %6, %7}], [%2];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4)
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
       : "memory");
 }
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
@@ -161,6 +174,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
 }
 
 __device__ __forceinline__ float sigm_f(float x) { return 1.f / (1.f + __expf(-x)); }
+// Hardware tanh (MUFU, ~2^-11 relative): the BF16 path's gate nonlinearities.
+__device__ __forceinline__ float tanh_fast(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float sigm_fast(float x) { return fmaf(0.5f, tanh_fast(0.5f * x), 0.5f); }
 __device__ __forceinline__ float lrelu_f(float x) { return x >= 0.f ? x : 0.01f * x; }
 
 // ---------------------------------------------------------------------------
@@ -219,16 +239,20 @@ __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *p, float *v) {
   }
 }
 
-template <int NCTA>
-__global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap,
+constexpr int kEpiWarps = 8;                    // two per TMEM lane quadrant
+constexpr int kConvThreads = 64 + 32 * kEpiWarps;
+constexpr int kAcc = 4;                         // TMEM accumulator buffers
+
+template <int KS, int KB, int NCTA, int EPI>
+__global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap,
                                                     const __grid_constant__ CUtensorMap tmap1,
                                                     const TcConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem);       // [8]
   uint64_t *empty = full + 8;                                // [8]
-  uint64_t *accf = empty + 8;                                // [2]
-  uint64_t *acce = accf + 2;                                 // [2]
-  uint64_t *wbar = acce + 2;                                 // [1]
+  uint64_t *accf = empty + 8;                                // [kAcc]
+  uint64_t *acce = accf + kAcc;                              // [kAcc]
+  uint64_t *wbar = acce + kAcc;                              // [1]
   volatile int *s_abort = reinterpret_cast<volatile int *>(wbar + 1);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 256);
   uint8_t *wsm = smem + 1024;
@@ -238,11 +262,11 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   const int nb = blockIdx.x % a.nb;
   const int cta = blockIdx.x / a.nb;
   const int nctas = gridDim.x / a.nb;
-  constexpr uint32_t kCols = NCTA * 2 <= 32 ? 32 : NCTA * 2;  // power of two
+  constexpr uint32_t kCols = NCTA * kAcc <= 32 ? 32 : NCTA * kAcc;  // power of two
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-    for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 4); }
+    for (int i = 0; i < kAcc; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], kEpiWarps); }
     mbar_init(wbar, 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -257,8 +281,9 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   __syncthreads();
   fence_after();
   const uint32_t tbase = *s_tmem;
-  const int taps = a.ks * a.ks;
-  const int R = a.ks / 2;
+  constexpr int taps = KS * KS;
+  constexpr int R = KS / 2;
+  constexpr int HX = kTileW + 2 * R, HY = kTileH + 2 * R;   // halo tile
 
   if (warp == 0 && lane == 0) {
     // ---- producer: weights once, then halo K-blocks ----------------------
@@ -274,17 +299,19 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     for (int t = cta; t < a.tiles && !*s_abort; t += nctas) {
       const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, p = t / (a.tiles_x * a.tiles_y);
       for (int kbi = 0; kbi < a.nkb; ++kbi) {
-        if (!mbar_wait(&empty[stage], phase ^ 1, s_abort)) break;
+        if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) break;
         mbar_expect_tx(&full[stage], a.stage_bytes);
         // K-blocks [0, nkb0) come through tmap (group offset in_goff), the
         // rest through tmap1 (groups counted from 0)
+        // innermost coordinate = pixel x * 8 channels (a multiple of 8
+        // elements = 16 bytes, also when negative at the left border)
         if (kbi < a.nkb0)
-          tma_load_5d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage], 0,
-                      tx * kTileW - R, ty * kTileH - R, a.in_goff + kbi * (a.kb / 8), p);
+          tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage],
+                      (tx * kTileW - R) * 8, ty * kTileH - R, a.in_goff + kbi * (KB / 8), p);
         else
-          tma_load_5d(stg + (size_t)stage * a.stage_bytes, &tmap1, &full[stage], 0,
-                      tx * kTileW - R, ty * kTileH - R, a.in1_goff + (kbi - a.nkb0) * (a.kb / 8),
-                      p);
+          tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap1, &full[stage],
+                      (tx * kTileW - R) * 8, ty * kTileH - R,
+                      a.in1_goff + (kbi - a.nkb0) * (KB / 8), p);
         ++issued;
         if (++stage == a.stages) { stage = 0; phase ^= 1; }
       }
@@ -301,32 +328,33 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer ---------------------------------------------------------
+    // All descriptor offsets are compile-time constants: one K-block is
+    // taps x KB/16 MMAs whose descriptors differ from the block's base
+    // descriptors by fixed amounts (addresses enter descriptors >> 4).
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCTA >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
-    const uint32_t slab = (uint32_t)a.halo_x * a.halo_y * 16u;
-    const uint32_t wblock = (uint32_t)taps * (a.kb / 8) * NCTA * 16u;  // bytes per K-block
+    constexpr uint32_t slab = (uint32_t)HX * HY * 16u;
+    constexpr uint32_t wblock = (uint32_t)taps * (KB / 8) * NCTA * 16u;  // bytes per K-block
     bool ok = mbar_wait(wbar, 0, s_abort);
     int stage = 0, acc = 0;
     uint32_t phase = 0, aphase = 0;
     for (int t = cta; ok && t < a.tiles; t += nctas) {
-      if (!mbar_wait(&acce[acc], aphase ^ 1, s_abort)) break;
+      if (!mbar_wait(&acce[acc], aphase ^ 1, s_abort, 200)) break;
       fence_after();
       const uint32_t d = tbase + (uint32_t)(acc * NCTA);
       uint32_t accum = 0;
       for (int kbi = 0; kbi < a.nkb; ++kbi) {
         if (!mbar_wait(&full[stage], phase, s_abort)) { ok = false; break; }
         fence_after();
-        const uint32_t abase = smem_u32(stg + (size_t)stage * a.stage_bytes);
-        const uint32_t bbase = smem_u32(wsm) + (uint32_t)kbi * wblock;
+        const uint64_t a0 = sdesc(smem_u32(stg + (size_t)stage * a.stage_bytes), slab, HX * 16u);
+        const uint64_t b0 = sdesc(smem_u32(wsm) + (uint32_t)kbi * wblock, NCTA * 16u, 128u);
+#pragma unroll
         for (int tap = 0; tap < taps; ++tap) {
-          const int dy = tap / a.ks, dx = tap % a.ks;
-          const uint32_t aoff = (uint32_t)(dy * a.halo_x + dx) * 16u;
-          for (int s = 0; s < a.kb / 16; ++s) {
-            const uint64_t ad = sdesc(abase + (uint32_t)(2 * s) * slab + aoff, slab,
-                                      (uint32_t)a.halo_x * 16u);
-            const uint64_t bd =
-                sdesc(bbase + (uint32_t)(tap * (a.kb / 8) + 2 * s) * (NCTA * 16u), NCTA * 16u, 128u);
-            mma_bf16(d, ad, bd, idesc, accum);
+#pragma unroll
+          for (int s = 0; s < KB / 16; ++s) {
+            const uint32_t aoff = ((uint32_t)(2 * s) * slab + (uint32_t)((tap / KS) * HX + tap % KS) * 16u) >> 4;
+            const uint32_t boff = ((uint32_t)(tap * (KB / 8) + 2 * s) * (NCTA * 16u)) >> 4;
+            mma_bf16(d, a0 + aoff, b0 + boff, idesc, accum);
             accum = 1;
           }
         }
@@ -335,11 +363,17 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       }
       if (!ok) break;
       mma_commit(&accf[acc]);
-      if (++acc == 2) { acc = 0; aphase ^= 1; }
+      if (++acc == kAcc) { acc = 0; aphase ^= 1; }
     }
   } else if (warp >= 2) {
-    // ---- epilogue -----------------------------------------------------------
+    // ---- epilogue: warps 2..9; warp w reads TMEM lanes 32 (w % 4) .. +31
+    // (output pixels), half (w - 2) / 4 of the columns (the head epilogue
+    // needs all columns of a pixel and runs on half 0 only) --------------
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    constexpr int NH = (EPI == TE_HEAD) ? NCTA : NCTA / 2;
+    const bool work = (EPI != TE_HEAD) || half == 0;
+    const int col0 = (EPI == TE_HEAD) ? 0 : half * NH;
     const int m = 32 * q + lane;
     const int r = m / kTileW, c = m % kTileW;
     int acc = 0;
@@ -347,104 +381,128 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     const int G = a.out_G;
     for (int t = cta; t < a.tiles; t += nctas) {
       const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, p = t / (a.tiles_x * a.tiles_y);
+      const int y = ty * kTileH + r, x = tx * kTileW + c;
+      const bool valid = y < a.H && x < a.W;
+      const int64_t hw = (int64_t)a.H * a.W;
+      const int64_t pix = (int64_t)y * a.W + x;
+      const int n0 = nb * NCTA + col0;   // first output column handled here
+      // Global operands of the epilogue do not depend on the accumulator:
+      // load them before waiting so their latency overlaps the MMAs.
+      constexpr int NPF = (EPI == TE_LSTM) ? NH / 4 : (EPI == TE_FOLD ? 9 : 1);
+      float pf[NPF];
+      uint4 pres[(EPI == TE_HEAD || EPI == TE_STORE) ? NH / 8 : 1];
+      if (work && valid) {
+        if (EPI == TE_LSTM) {
+          const int Hp = a.H >> a.up, Wp = a.W >> a.up;
+          const int64_t ppix = ((int64_t)p * Hp + (y >> a.up)) * Wp + (x >> a.up);
+#pragma unroll
+          for (int k = 0; k < NPF; k += 4) {
+            float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!a.first) c4 = __ldg(reinterpret_cast<const float4 *>(a.c_prev + ppix * a.C + n0 / 4 + k));
+            pf[k] = c4.x; pf[k + 1] = c4.y; pf[k + 2] = c4.z; pf[k + 3] = c4.w;
+          }
+        } else if (EPI == TE_FOLD) {
+          const int32_t *sp = a.fold_s + (int64_t)p * hw;
+#pragma unroll
+          for (int tap = 0; tap < 9; ++tap) {
+            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+            pf[tap] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && step_of(yy, xx) < a.step)
+                          ? (float)__ldg(sp + (int64_t)yy * a.W + xx)
+                          : 0.f;
+          }
+        } else if (EPI == TE_HEAD || (EPI == TE_STORE && a.res)) {
+          const bool need = (EPI == TE_STORE) || step_of(y, x) == a.step;
+          if (need) {
+#pragma unroll
+            for (int g = 0; g < NH / 8; ++g)
+              pres[g] = __ldg(reinterpret_cast<const uint4 *>(
+                  a.res + (((int64_t)p * a.res_G + a.res_goff + (n0 >> 3) + g) * hw + pix) * 8));
+          }
+        }
+      }
       // warp-uniform wait: lane 0 decides, the others then observe the
       // completed phase themselves (their try_wait succeeds at once)
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(&accf[acc], aphase, s_abort) ? 1 : 0;
+      if (lane == 0) ok = mbar_wait(&accf[acc], aphase, s_abort, 200) ? 1 : 0;
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) break;
       if (lane != 0) mbar_wait(&accf[acc], aphase, s_abort);
       __syncwarp();
       fence_after();
-      float v[NCTA];
-      const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NCTA);
+      float v[NH];
+      const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NCTA + col0);
+      if (work) {
 #pragma unroll
-      for (int ch = 0; ch < NCTA / 16; ++ch) tmem_ld16(taddr + 16 * ch, v + 16 * ch);
+        for (int ch = 0; ch < NH / 16; ++ch) tmem_ld16(taddr + 16 * ch, v + 16 * ch);
+      }
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce[acc]);
-      if (++acc == 2) { acc = 0; aphase ^= 1; }
+      if (++acc == kAcc) { acc = 0; aphase ^= 1; }
+      if (!work) continue;
 
-      const int y = ty * kTileH + r, x = tx * kTileW + c;
-      const bool valid = y < a.H && x < a.W;
-      const int64_t hw = (int64_t)a.H * a.W;
-      const int64_t pix = (int64_t)y * a.W + x;
-      const int n0 = nb * NCTA;
 #pragma unroll
-      for (int j = 0; j < NCTA; ++j) v[j] += a.bias[n0 + j];
-      if (a.epi == TE_FOLD) {
-        if (valid) {
-          const int32_t *sp = a.fold_s + (int64_t)p * hw;
-          float nbv[9];
+      for (int j = 0; j < NH; ++j) v[j] += a.bias[n0 + j];
+      if (!valid) continue;
+      if (EPI == TE_FOLD) {
+        const float *nbv = pf;
 #pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
-            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-            nbv[tap] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && step_of(yy, xx) < a.step)
-                           ? (float)sp[(int64_t)yy * a.W + xx]
-                           : 0.f;
-          }
+        for (int tap = 0; tap < 9; ++tap) {
+          const float4 *wr = reinterpret_cast<const float4 *>(a.fold_w + tap * NCTA + col0);
 #pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
-            const float4 *wr = reinterpret_cast<const float4 *>(a.fold_w + tap * NCTA);
-#pragma unroll
-            for (int j = 0; j < NCTA / 4; ++j) {
-              const float4 w4 = __ldg(wr + j);
-              v[4 * j] = fmaf(w4.x, nbv[tap], v[4 * j]);
-              v[4 * j + 1] = fmaf(w4.y, nbv[tap], v[4 * j + 1]);
-              v[4 * j + 2] = fmaf(w4.z, nbv[tap], v[4 * j + 2]);
-              v[4 * j + 3] = fmaf(w4.w, nbv[tap], v[4 * j + 3]);
-            }
-          }
-#pragma unroll
-          for (int g = 0; g < NCTA / 8; ++g)
-            store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (n0 >> 3) + g) * hw + pix) * 8,
-                         v + 8 * g);
-        }
-      } else if (a.epi == TE_STORE) {
-        if (valid) {
-#pragma unroll
-          for (int g = 0; g < NCTA / 8; ++g) {
-            const int gg = (n0 >> 3) + g;
-            if (a.res) {
-              float rv[8];
-              load_bf16x8(a.res + (((int64_t)p * a.res_G + a.res_goff + gg) * hw + pix) * 8, rv);
-#pragma unroll
-              for (int e = 0; e < 8; ++e) v[8 * g + e] += rv[e];
-            }
-            if (a.act) {
-#pragma unroll
-              for (int e = 0; e < 8; ++e) v[8 * g + e] = lrelu_f(v[8 * g + e]);
-            }
-            store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + gg) * hw + pix) * 8, v + 8 * g);
+          for (int j = 0; j < NH / 4; ++j) {
+            const float4 w4 = __ldg(wr + j);
+            v[4 * j] = fmaf(w4.x, nbv[tap], v[4 * j]);
+            v[4 * j + 1] = fmaf(w4.y, nbv[tap], v[4 * j + 1]);
+            v[4 * j + 2] = fmaf(w4.z, nbv[tap], v[4 * j + 2]);
+            v[4 * j + 3] = fmaf(w4.w, nbv[tap], v[4 * j + 3]);
           }
         }
-      } else if (a.epi == TE_LSTM) {
+#pragma unroll
+        for (int g = 0; g < NH / 8; ++g)
+          store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (n0 >> 3) + g) * hw + pix) * 8,
+                       v + 8 * g);
+      } else if (EPI == TE_STORE) {
+#pragma unroll
+        for (int g = 0; g < NH / 8; ++g) {
+          const int gg = (n0 >> 3) + g;
+          if (a.res) {
+            float rv[8];
+            load_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(&pres[g]), rv);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[8 * g + e] += rv[e];
+          }
+          if (a.act) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[8 * g + e] = lrelu_f(v[8 * g + e]);
+          }
+          store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + gg) * hw + pix) * 8, v + 8 * g);
+        }
+      } else if (EPI == TE_LSTM) {
         // column 4 * ch + gate (i, f, o, g) within the CTA's N block
-        if (valid) {
-          const int Hp = a.H >> a.up, Wp = a.W >> a.up;
-          const int64_t ppix = ((int64_t)p * Hp + (y >> a.up)) * Wp + (x >> a.up);
-          const int ch0 = n0 / 4;
-          float hv[NCTA / 4];
+        const int ch0 = n0 / 4;
+        const float *cp = pf;
+        float hv[NH / 4], cn[NH / 4];
 #pragma unroll
-          for (int k = 0; k < NCTA / 4; ++k) {
-            const int chn = ch0 + k;
-            const float cp = a.first ? 0.f : a.c_prev[ppix * a.C + chn];
-            const float cn = sigm_f(v[4 * k + 1]) * cp + sigm_f(v[4 * k]) * tanhf(v[4 * k + 3]);
-            hv[k] = sigm_f(v[4 * k + 2]) * tanhf(cn);
-            a.c_new[((int64_t)p * hw + pix) * a.C + chn] = cn;
-          }
-#pragma unroll
-          for (int g = 0; g < NCTA / 32; ++g)
-            store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (ch0 >> 3) + g) * hw + pix) * 8,
-                         hv + 8 * g);
+        for (int k = 0; k < NH / 4; ++k) {
+          cn[k] = sigm_fast(v[4 * k + 1]) * cp[k] + sigm_fast(v[4 * k]) * tanh_fast(v[4 * k + 3]);
+          hv[k] = sigm_fast(v[4 * k + 2]) * tanh_fast(cn[k]);
         }
+#pragma unroll
+        for (int k = 0; k < NH / 4; k += 4)
+          *reinterpret_cast<float4 *>(a.c_new + ((int64_t)p * hw + pix) * a.C + ch0 + k) =
+              make_float4(cn[k], cn[k + 1], cn[k + 2], cn[k + 3]);
+#pragma unroll
+        for (int g = 0; g < NH / 32; ++g)
+          store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (ch0 >> 3) + g) * hw + pix) * 8,
+                       hv + 8 * g);
       } else {  // TE_HEAD: z' = res + acc + b over all C columns, then 1x1(C->2)
-        if (valid && step_of(y, x) == a.step) {
+        if (step_of(y, x) == a.step) {
           float mu = a.bh[0], rho = a.bh[1];
 #pragma unroll
           for (int g = 0; g < NCTA / 8; ++g) {
             float rv[8];
-            load_bf16x8(a.res + (((int64_t)p * a.res_G + a.res_goff + g) * hw + pix) * 8, rv);
+            load_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(&pres[g]), rv);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const float z = v[8 * g + e] + rv[e];
@@ -573,18 +631,19 @@ static int get_encoder() {
   return PW_OK;
 }
 
-// Tensor map over a blocked BF16 tensor [P][G][H][W][8]; box = one K-block
-// halo tile.
+// Tensor map over a blocked BF16 tensor [P][G][H][W][8], viewed as 4-D
+// (W * 8 elements, H, G, P) so that each box row is one contiguous run of
+// box_x * 16 bytes; box = one K-block halo tile.
 static int make_map(CUtensorMap *map, const __nv_bfloat16 *base, int P, int G, int H, int W,
                     int box_x, int box_y, int box_g) {
   int s = get_encoder();
   if (s) return s;
-  cuuint64_t dims[5] = {8, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)G, (cuuint64_t)P};
-  cuuint64_t strides[4] = {16, (cuuint64_t)W * 16, (cuuint64_t)H * W * 16,
+  cuuint64_t dims[4] = {(cuuint64_t)W * 8, (cuuint64_t)H, (cuuint64_t)G, (cuuint64_t)P};
+  cuuint64_t strides[3] = {(cuuint64_t)W * 16, (cuuint64_t)H * W * 16,
                            (cuuint64_t)G * H * W * 16};
-  cuuint32_t box[5] = {8, (cuuint32_t)box_x, (cuuint32_t)box_y, (cuuint32_t)box_g, 1};
-  cuuint32_t es[5] = {1, 1, 1, 1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void *)base, dims, strides, box,
+  cuuint32_t box[4] = {(cuuint32_t)box_x * 8, (cuuint32_t)box_y, (cuuint32_t)box_g, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims, strides, box,
                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -641,21 +700,32 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
   if (per_nb > a.tiles) per_nb = a.tiles;
   const int grid = per_nb * cv.nb;
   cudaStream_t st = ctx->stream;
-#define PW_TC_CASE(N_)                                                                      \
-  if (cv.ncta == N_) {                                                                      \
+#define PW_TC_CASE(KS_, KB_, N_, E_)                                                        \
+  if (cv.ks == KS_ && cv.kb == KB_ && cv.ncta == N_ && a.epi == E_) {                       \
     static bool attr = false;                                                               \
     if (!attr) {                                                                            \
-      cudaFuncSetAttribute(k_conv_tc<N_>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                           (int)maxsm);                                                     \
+      cudaFuncSetAttribute(k_conv_tc<KS_, KB_, N_, E_>,                                     \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);        \
       attr = true;                                                                          \
     }                                                                                       \
-    k_conv_tc<N_><<<grid, 192, smem, st>>>(map, map1, a);                                   \
+    k_conv_tc<KS_, KB_, N_, E_><<<grid, kConvThreads, smem, st>>>(map, map1, a);            \
     ctx->launches += 1;                                                                     \
     return PW_OK;                                                                           \
   }
-  PW_TC_CASE(32) PW_TC_CASE(64) PW_TC_CASE(128)
+  // plain stores (all shapes the stage entry accepts)
+  PW_TC_CASE(1, 32, 32, TE_STORE) PW_TC_CASE(1, 32, 64, TE_STORE) PW_TC_CASE(1, 32, 128, TE_STORE)
+  PW_TC_CASE(1, 64, 32, TE_STORE) PW_TC_CASE(1, 64, 64, TE_STORE) PW_TC_CASE(1, 64, 128, TE_STORE)
+  PW_TC_CASE(3, 32, 32, TE_STORE) PW_TC_CASE(3, 32, 64, TE_STORE) PW_TC_CASE(3, 32, 128, TE_STORE)
+  PW_TC_CASE(3, 64, 32, TE_STORE) PW_TC_CASE(3, 64, 64, TE_STORE) PW_TC_CASE(3, 64, 128, TE_STORE)
+  // ConvLSTM gates (K-block = C channels)
+  PW_TC_CASE(3, 32, 64, TE_LSTM) PW_TC_CASE(3, 64, 64, TE_LSTM)
+  // residual + head: 3x3 C->C of steps 2-4, 1x1 2C->C of step 1
+  PW_TC_CASE(3, 32, 32, TE_HEAD) PW_TC_CASE(3, 64, 64, TE_HEAD)
+  PW_TC_CASE(1, 64, 32, TE_HEAD) PW_TC_CASE(1, 64, 64, TE_HEAD)
+  // 1x1 over l with the folded masked-input taps (steps 2-4)
+  PW_TC_CASE(1, 32, 32, TE_FOLD) PW_TC_CASE(1, 64, 64, TE_FOLD)
 #undef PW_TC_CASE
-  set_last_error("no tensor-core conv for this N");
+  set_last_error("no tensor-core conv for this shape");
   return PW_EUNSUPPORTED;
 }
 
