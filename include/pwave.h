@@ -113,6 +113,28 @@ int pw_decode_batch(pw_ctx *ctx, const pw_model *m, int count,
                     const uint8_t *const *bs, const size_t *n, int bs_on_device,
                     pw_image *out);
 
+/* ---- video GOPs (Section 3.3) -------------------------------------------- */
+
+/* Encode a group of nframes = 2^k frames: identity-motion temporal lifting
+ * (the MCTF-style predict / update steps of Section 3.3 with zero motion and
+ * the blob's temporal CNNs), then the lowpass band coded as an image with
+ * m_low and the nframes - 1 highpass bands (batched) with m_high. frames are
+ * 8-bit gray or RGB images of one size (host or device). *bs (host, free
+ * with pw_free) is a "PWGP" container: 36-byte header (magic, version,
+ * nframes, width, height, temporal levels, components, the two model
+ * hashes) then, per band, a u32 length and a "PWBS" stream. */
+int pw_encode_gop(pw_ctx *ctx, const pw_model *m_low, const pw_model *m_high, int nframes,
+                  const pw_image *frames, const pw_codec_opts *opts, uint8_t **bs, size_t *n);
+/* Inverse of pw_encode_gop into frames[0..nframes-1]. Errors: PW_EINVAL
+ * (models / sizes do not match the stream), PW_ECORRUPT. */
+int pw_decode_gop(pw_ctx *ctx, const pw_model *m_low, const pw_model *m_high, const uint8_t *bs,
+                  size_t n, int nframes, pw_image *frames);
+/* Temporal lifting alone on nframes host planes of H x W floats ([frame]
+ * [H][W]): forward writes the bands [L_T, H_T, H_{T-1}..., H_1] (the highs
+ * of a level in frame order), inverse reads them back (Section 3.3). */
+int pw_temporal_lift(pw_ctx *ctx, const pw_model *m, int nframes, int H, int W, int forward,
+                     const float *in, float *out);
+
 /* ---- stages of the decode path (for testing and composition) ----------- */
 
 /* Build the 2048 x 128 uint16 CDF table bank (table id (phi + 8) * 128 + j)

@@ -86,6 +86,11 @@ _sig = {
                                    C.POINTER(C.c_size_t)]),
     "pw_conv_bf16": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                C.c_int, _P, _P, _P, _P]),
+    "pw_encode_gop": (C.c_int, [_P, _P, _P, C.c_int, C.POINTER(pw_image),
+                                C.POINTER(pw_codec_opts), C.POINTER(_u8p),
+                                C.POINTER(C.c_size_t)]),
+    "pw_decode_gop": (C.c_int, [_P, _P, _P, _P, C.c_size_t, C.c_int, C.POINTER(pw_image)]),
+    "pw_temporal_lift": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
     "pw_ctx_profile": (C.c_int, [_P, C.c_int]),
     "pw_ctx_kernel_stats": (C.c_int, [_P, C.POINTER(pw_kernel_stat), C.c_int]),
     "pw_free": (None, [_P]),
@@ -237,6 +242,37 @@ class Codec:
         p = (C.c_void_p * B)(*ptrs)
         n = (C.c_size_t * B)(*lens)
         check(pw_decode_batch(self.ctx, model.handle, B, p, n, 1, ims))
+
+    # ---- video GOPs -------------------------------------------------------
+    def encode_gop(self, m_low: Model, m_high: Model, frames: np.ndarray, q: float = 8.0,
+                   chunk: int = 16384) -> bytes:
+        frames = np.ascontiguousarray(frames, dtype=np.uint8)
+        nf = frames.shape[0]
+        ims = (pw_image * nf)(*[_host_image(frames[f], 8)[0] for f in range(nf)])
+        o = _opts(q, False, chunk)
+        p = _u8p()
+        n = C.c_size_t()
+        check(pw_encode_gop(self.ctx, m_low.handle, m_high.handle, nf, ims, C.byref(o),
+                            C.byref(p), C.byref(n)))
+        return _take_bytes(p, n.value)
+
+    def decode_gop(self, m_low: Model, m_high: Model, gs: bytes, nframes: int, shape) -> np.ndarray:
+        out = np.zeros((nframes,) + tuple(shape), dtype=np.uint8)
+        h, w = shape[:2]
+        ch = 1 if len(shape) == 2 else shape[2]
+        item = out[0].nbytes
+        ims = (pw_image * nframes)(*[pw_image(w, h, ch, 8, 0, 0, out.ctypes.data + f * item, 0)
+                                     for f in range(nframes)])
+        check(pw_decode_gop(self.ctx, m_low.handle, m_high.handle, gs, len(gs), nframes, ims))
+        return out
+
+    def temporal_lift(self, model: Model, frames: np.ndarray, forward: bool = True) -> np.ndarray:
+        frames = np.ascontiguousarray(frames, dtype=np.float32)
+        nf, H, W = frames.shape
+        out = np.zeros_like(frames)
+        check(pw_temporal_lift(self.ctx, model.handle, nf, H, W, int(forward), _ptr(frames),
+                               _ptr(out)))
+        return out
 
     # ---- stages -----------------------------------------------------------
     def cdf_bank_device(self, dev_ptr: int):

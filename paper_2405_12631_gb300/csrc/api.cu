@@ -276,6 +276,33 @@ static int stage_streams(pw_ctx *ctx, Plan &pl, int B, const uint8_t *const *bs,
   return PW_OK;
 }
 
+// Decode B host streams (same geometry) to component planes; on success
+// *planes points into the plan's workspace ([B][nc][Hp][Wp] floats) and *geo
+// describes them. The planes stay valid until the next call on this plan.
+static int decode_to_planes(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs,
+                            const size_t *n, float **planes, Geometry *geo) {
+  StreamHeader h0;
+  int s = read_header(bs[0], n[0], 0, h0);
+  if (s || (s = check_header_model(ctx, m, h0))) return s;
+  Geometry g;
+  if ((s = build_geo(h0, g))) return s;
+  Plan *pl;
+  if ((s = get_plan(ctx, m, g, B, "dec", false, &pl))) return s;
+  std::vector<const uint8_t *> ptrs;
+  if ((s = stage_streams(ctx, *pl, B, bs, n, 0, ptrs))) return s;
+  if ((s = decode_symbols_dev(ctx, m, *pl, ptrs.data(), n, h0))) return s;
+  const int P = B * g.nc;
+  SbTable tb = make_sbtable(g, P);
+  launch_dequant_all(pl->ws.Q, pl->ws.Yf, (int64_t)P * g.plane_elems, tb, g.nc,
+                     reinterpret_cast<float *>(pl->d_deltas.p), ctx->stream);
+  bump(ctx);
+  if ((s = lift_inverse_planes(ctx, m, g, pl->ws, pl->ws.planes))) return s;
+  if ((s = check_status(ctx, &pl->ws))) return s;
+  *planes = pl->ws.planes;
+  *geo = g;
+  return PW_OK;
+}
+
 static int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,
                         int on_dev, pw_image *out) {
   if (B < 1 || !bs || !n || !out) { set_last_error("bad arguments"); return PW_EINVAL; }
@@ -467,6 +494,30 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
   return PW_OK;
 }
 
+// Encode B x nc device planes ([B][nc][Hp][Wp], colour code 3 = raw
+// planes) with model m.
+static int encode_planes_dev(pw_ctx *ctx, Model &m, int B, int nc, int H, int W,
+                             const float *planes, const pw_codec_opts *o, uint8_t **bs,
+                             size_t *n) {
+  const int lossless = o && o->lossless ? 1 : 0;
+  if (!lossless && !(o && o->q > 0.f)) { set_last_error("quantiser step must be > 0"); return PW_EINVAL; }
+  const int chunk = (o && o->chunk_symbols > 0) ? o->chunk_symbols : 16384;
+  Geometry g;
+  g.build(H, W, nc, m.levels, 3, 8, lossless, m.ll_mode, chunk);
+  Plan *pl;
+  int s;
+  if ((s = get_plan(ctx, m, g, B, "enc", false, &pl))) return s;
+  const int P = B * nc;
+  PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.planes, planes, (size_t)P * g.Hp * g.Wp * 4,
+                              cudaMemcpyDeviceToDevice, ctx->stream));
+  if ((s = lift_forward_planes(ctx, m, g, pl->ws, pl->ws.planes))) return s;
+  const float d = lossless ? 1.f : 1.f / o->q;
+  SbTable tb = make_sbtable(g, P);
+  launch_quant_all(pl->ws.Yf, pl->ws.Q, (int64_t)P * g.plane_elems, tb, d, d, ctx->stream);
+  bump(ctx);
+  return encode_from_latent(ctx, m, *pl, B, d, d, bs, n);
+}
+
 static int image_geo(pw_ctx *ctx, const Model &m, const pw_image &im, const pw_codec_opts *o,
                      Geometry &g) {
   if (im.width < 1 || im.height < 1 || (im.channels != 1 && im.channels != 3) || !im.data ||
@@ -646,6 +697,174 @@ int pw_decode_batch(pw_ctx *c, const pw_model *m, int count, const uint8_t *cons
 
 int pw_decode_image(pw_ctx *c, const pw_model *m, const uint8_t *bs, size_t n, pw_image *out) {
   return pw_decode_batch(c, m, 1, &bs, &n, 0, out);
+}
+
+// ---- video GOPs (Section 3.3) ----------------------------------------------
+#pragma pack(push, 1)
+struct GopHeader {
+  char magic[4];
+  uint16_t version, nframes;
+  uint32_t width, height;
+  uint8_t tlevels, ncomp;
+  uint16_t zero;
+  uint64_t hash_low, hash_high;
+};
+#pragma pack(pop)
+static_assert(sizeof(GopHeader) == 36, "GOP header is 36 bytes");
+
+int pw_encode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, int nframes,
+                  const pw_image *frames, const pw_codec_opts *o, uint8_t **bs, size_t *n) {
+  if (!c || !ml || !mh || !frames || !bs || !n || nframes < 2 || (nframes & (nframes - 1))) {
+    set_last_error("GOP: need 2^k frames, models and outputs"); return PW_EINVAL;
+  }
+  Model &L = const_cast<pw_model *>(ml)->m, &Hm = const_cast<pw_model *>(mh)->m;
+  if (L.levels != Hm.levels) { set_last_error("GOP models differ in levels"); return PW_EINVAL; }
+  if (o && o->lossless) { set_last_error("lossless GOPs are not supported"); return PW_EUNSUPPORTED; }
+  const pw_image &f0 = frames[0];
+  for (int f = 0; f < nframes; ++f)
+    if (frames[f].width != f0.width || frames[f].height != f0.height ||
+        frames[f].channels != f0.channels || frames[f].bitdepth != 8 || !frames[f].data) {
+      set_last_error("GOP frames must be 8-bit images of one size"); return PW_EINVAL;
+    }
+  const int nc = f0.channels, H = f0.height, W = f0.width;
+  const int mult = 1 << L.levels;
+  const int Hp = (H + mult - 1) / mult * mult, Wp = (W + mult - 1) / mult * mult;
+  const int64_t F = (int64_t)nc * Hp * Wp;
+  const int64_t row = (int64_t)W * nc, img = row * H;
+  DevBuf dimg, dframes, dbands, dt0, dt1;
+  int s;
+  if ((s = dimg.ensure((size_t)img * nframes)) || (s = dframes.ensure((size_t)F * nframes * 4)) ||
+      (s = dbands.ensure((size_t)F * nframes * 4)) || (s = dt0.ensure((size_t)F * nframes * 2)) ||
+      (s = dt1.ensure((size_t)F * nframes * 2)))
+    return s;
+  cudaStream_t st = c->stream;
+  for (int f = 0; f < nframes; ++f) {
+    const int64_t rs = frames[f].stride_bytes ? frames[f].stride_bytes : row;
+    PW_CUDA_TRY(cudaMemcpy2DAsync((uint8_t *)dimg.p + f * img, row, frames[f].data, rs, row, H,
+                                  frames[f].is_device ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyHostToDevice, st));
+  }
+  launch_colour_in(dimg.p, img, row, nframes, nc, H, W, Hp, Wp, 0, 8, (float *)dframes.p, st);
+  bump(c);
+  if ((s = temporal_planes(c, L, nframes, nc, Hp, Wp, (float *)dframes.p, (float *)dbands.p,
+                           (float *)dt0.p, (float *)dt1.p, true)))
+    return s;
+  std::vector<uint8_t *> sb(nframes, nullptr);
+  std::vector<size_t> sn(nframes, 0);
+  if ((s = encode_planes_dev(c, L, 1, nc, H, W, (float *)dbands.p, o, sb.data(), sn.data())))
+    return s;
+  if ((s = encode_planes_dev(c, Hm, nframes - 1, nc, H, W, (float *)dbands.p + F, o, sb.data() + 1,
+                             sn.data() + 1))) {
+    std::free(sb[0]);
+    return s;
+  }
+  GopHeader gh{};
+  std::memcpy(gh.magic, "PWGP", 4);
+  gh.version = 1; gh.nframes = (uint16_t)nframes; gh.width = W; gh.height = H;
+  int T = 0;
+  while ((1 << T) < nframes) ++T;
+  gh.tlevels = (uint8_t)T; gh.ncomp = (uint8_t)nc; gh.hash_low = L.hash; gh.hash_high = Hm.hash;
+  size_t total = sizeof(gh);
+  for (int f = 0; f < nframes; ++f) total += 4 + sn[f];
+  uint8_t *out = static_cast<uint8_t *>(std::malloc(total));
+  if (!out) { for (auto q : sb) std::free(q); return PW_ENOMEM; }
+  size_t pos = 0;
+  std::memcpy(out, &gh, sizeof(gh));
+  pos += sizeof(gh);
+  for (int f = 0; f < nframes; ++f) {
+    const uint32_t len = (uint32_t)sn[f];
+    std::memcpy(out + pos, &len, 4);
+    std::memcpy(out + pos + 4, sb[f], sn[f]);
+    pos += 4 + sn[f];
+    std::free(sb[f]);
+  }
+  *bs = out;
+  *n = total;
+  return PW_OK;
+}
+
+int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8_t *bs, size_t n,
+                  int nframes, pw_image *frames) {
+  if (!c || !ml || !mh || !bs || !frames || n < sizeof(GopHeader)) return PW_EINVAL;
+  Model &L = const_cast<pw_model *>(ml)->m, &Hm = const_cast<pw_model *>(mh)->m;
+  GopHeader gh;
+  std::memcpy(&gh, bs, sizeof(gh));
+  if (std::memcmp(gh.magic, "PWGP", 4) || gh.version != 1) { set_last_error("not a PWGP stream"); return PW_ECORRUPT; }
+  if (gh.hash_low != L.hash || gh.hash_high != Hm.hash) { set_last_error("GOP made with other models"); return PW_EINVAL; }
+  if ((int)gh.nframes != nframes || nframes < 2 || (1 << gh.tlevels) != nframes ||
+      (gh.ncomp != 1 && gh.ncomp != 3)) {
+    set_last_error("GOP frame count mismatch"); return PW_EINVAL;
+  }
+  const int nc = gh.ncomp, H = gh.height, W = gh.width;
+  for (int f = 0; f < nframes; ++f)
+    if (frames[f].width != W || frames[f].height != H || frames[f].channels != nc ||
+        frames[f].bitdepth != 8 || !frames[f].data) {
+      set_last_error("GOP output frames do not match the stream"); return PW_EINVAL;
+    }
+  std::vector<const uint8_t *> bp(nframes);
+  std::vector<size_t> bn(nframes);
+  size_t pos = sizeof(gh);
+  for (int f = 0; f < nframes; ++f) {
+    uint32_t len;
+    if (pos + 4 > n) { set_last_error("truncated GOP"); return PW_ECORRUPT; }
+    std::memcpy(&len, bs + pos, 4);
+    pos += 4;
+    if (pos + len > n) { set_last_error("truncated GOP"); return PW_ECORRUPT; }
+    bp[f] = bs + pos;
+    bn[f] = len;
+    pos += len;
+  }
+  const int mult = 1 << L.levels;
+  const int Hp = (H + mult - 1) / mult * mult, Wp = (W + mult - 1) / mult * mult;
+  const int64_t F = (int64_t)nc * Hp * Wp;
+  DevBuf dbands, dframes, dt0, dt1, dimg;
+  const int64_t row = (int64_t)W * nc, img = row * H;
+  int s;
+  if ((s = dbands.ensure((size_t)F * nframes * 4)) || (s = dframes.ensure((size_t)F * nframes * 4)) ||
+      (s = dt0.ensure((size_t)F * nframes * 2)) || (s = dt1.ensure((size_t)F * nframes * 2)) ||
+      (s = dimg.ensure((size_t)img * nframes)))
+    return s;
+  cudaStream_t st = c->stream;
+  float *planes;
+  Geometry g;
+  if ((s = decode_to_planes(c, L, 1, bp.data(), bn.data(), &planes, &g))) return s;
+  if (g.H != H || g.W != W || g.nc != nc || g.colour != 3) { set_last_error("GOP band geometry"); return PW_ECORRUPT; }
+  PW_CUDA_TRY(cudaMemcpyAsync(dbands.p, planes, (size_t)F * 4, cudaMemcpyDeviceToDevice, st));
+  if ((s = decode_to_planes(c, Hm, nframes - 1, bp.data() + 1, bn.data() + 1, &planes, &g))) return s;
+  if (g.H != H || g.W != W || g.nc != nc || g.colour != 3) { set_last_error("GOP band geometry"); return PW_ECORRUPT; }
+  PW_CUDA_TRY(cudaMemcpyAsync((float *)dbands.p + F, planes, (size_t)F * (nframes - 1) * 4,
+                              cudaMemcpyDeviceToDevice, st));
+  if ((s = temporal_planes(c, L, nframes, nc, Hp, Wp, (float *)dbands.p, (float *)dframes.p,
+                           (float *)dt0.p, (float *)dt1.p, false)))
+    return s;
+  launch_colour_out((float *)dframes.p, nframes, nc, Hp, Wp, H, W, nc == 3 ? 1 : 0, 8, dimg.p, img,
+                    row, st);
+  bump(c);
+  for (int f = 0; f < nframes; ++f) {
+    const int64_t rs = frames[f].stride_bytes ? frames[f].stride_bytes : row;
+    PW_CUDA_TRY(cudaMemcpy2DAsync(frames[f].data, rs, (uint8_t *)dimg.p + f * img, row, row, H,
+                                  frames[f].is_device ? cudaMemcpyDeviceToDevice
+                                                      : cudaMemcpyDeviceToHost, st));
+  }
+  return finish(c);
+}
+
+int pw_temporal_lift(pw_ctx *c, const pw_model *mm, int nframes, int H, int W, int forward,
+                     const float *in, float *out) {
+  if (!c || !mm || !in || !out || H < 1 || W < 1) return PW_EINVAL;
+  Model &m = const_cast<pw_model *>(mm)->m;
+  const int64_t F = (int64_t)H * W;
+  DevBuf din, dout, dt0, dt1;
+  int s;
+  if ((s = din.ensure((size_t)F * nframes * 4)) || (s = dout.ensure((size_t)F * nframes * 4)) ||
+      (s = dt0.ensure((size_t)F * nframes * 2)) || (s = dt1.ensure((size_t)F * nframes * 2)))
+    return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(din.p, in, (size_t)F * nframes * 4, cudaMemcpyHostToDevice, c->stream));
+  if ((s = temporal_planes(c, m, nframes, 1, H, W, (float *)din.p, (float *)dout.p, (float *)dt0.p,
+                           (float *)dt1.p, forward != 0)))
+    return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(out, dout.p, (size_t)F * nframes * 4, cudaMemcpyDeviceToHost, c->stream));
+  return finish(c);
 }
 
 // ---- stages ---------------------------------------------------------------

@@ -343,4 +343,62 @@ int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
   return PW_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Temporal lifting of a GOP (Section 3.3, identity motion): frames are
+// nf x nc planes [frame][comp][Hp][Wp]. Forward: per level, pairs (f_e, f_o)
+// -> H = f_o - (f_e + CNN_P(f_e)), L = f_e + (H / 2 + CNN_U(H)); bands are
+// written as [L_T, H_T, H_{T-1} ..., H_1] (highs of a level in frame order).
+// Inverse runs the same steps backwards. tmp holds nf / 2 frames.
+int temporal_planes(pw_ctx *ctx, Model &m, int nf, int nc, int Hp, int Wp, const float *in,
+                    float *out, float *tmp0, float *tmp1, bool forward) {
+  const int64_t HW = (int64_t)Hp * Wp;
+  const int64_t F = (int64_t)nc * HW;  // one frame
+  int T = 0;
+  while ((1 << T) < nf) ++T;
+  if ((1 << T) != nf || nf < 2) { set_last_error("GOP size must be a power of two >= 2"); return PW_EINVAL; }
+  auto step = [&](const float *src, int64_t ssrc, const float *oth, int64_t soth, float *dst,
+                  int64_t sdst, int P, int lin, int sign, const LiftNetDev &net) {
+    LiftStepParams a{};
+    a.P = P; a.H = Hp; a.W = Wp; a.dir = 0; a.lin = lin; a.sign = sign; a.round = 0; a.net = net;
+    a.src = acc(const_cast<float *>(src), ssrc, Wp);
+    a.other = acc(const_cast<float *>(oth), soth, Wp);
+    a.out = acc(dst, sdst, Wp);
+    a.copy = acc(nullptr, 0, 0);
+    lift_step(ctx, a);
+  };
+  if (forward) {
+    const float *cur = in;
+    float *bufs[2] = {tmp0, tmp1};
+    for (int lv = 1; lv <= T; ++lv) {
+      const int n = nf >> (lv - 1), h = n / 2;
+      float *L = (lv == T) ? out : bufs[lv & 1];
+      for (int c = 0; c < nc; ++c) {
+        const float *fe = cur + c * HW, *fo = cur + F + c * HW;
+        float *Hb = out + (int64_t)h * F + c * HW;
+        step(fe, 2 * F, fo, 2 * F, Hb, F, h, LIN_ID, -1, m.tlift[0]);
+        step(Hb, F, fe, 2 * F, L + c * HW, F, h, LIN_HALF, +1, m.tlift[1]);
+      }
+      ctx->launches += 2 * nc;
+      cur = L;
+    }
+  } else {
+    // bands in `in`; start from L_T, rebuild level by level
+    const float *cur = in;  // L of the current level: frame 0 of the bands
+    float *bufs[2] = {tmp0, tmp1};
+    for (int lv = T; lv >= 1; --lv) {
+      const int n = nf >> (lv - 1), h = n / 2;
+      float *dst = (lv == 1) ? out : bufs[lv & 1];
+      for (int c = 0; c < nc; ++c) {
+        const float *Hb = in + (int64_t)h * F + c * HW, *L = cur + c * HW;
+        float *fe = dst + c * HW, *fo = dst + F + c * HW;
+        step(Hb, F, L, F, fe, 2 * F, h, LIN_HALF, -1, m.tlift[1]);
+        step(fe, 2 * F, Hb, F, fo, 2 * F, h, LIN_ID, +1, m.tlift[0]);
+      }
+      ctx->launches += 2 * nc;
+      cur = dst;
+    }
+  }
+  return PW_OK;
+}
+
 }  // namespace pw

@@ -119,6 +119,8 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         float *dst_planes);
 int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         const float *src_planes);
+int temporal_planes(pw_ctx *ctx, Model &m, int nf, int nc, int Hp, int Wp, const float *in,
+                    float *out, float *tmp0, float *tmp1, bool forward);
 
 }  // namespace pw
 

@@ -296,3 +296,31 @@ def test_corrupt_and_foreign_streams_rejected(codec, model32, pw):
         codec.decode_image(gm, bs[: len(bs) - 7], shape=(48, 64), dtype=np.uint8)
     # the context still works afterwards
     assert np.array_equal(codec.decode_image(gm, bs), codec.decode_image(gm, bs))
+
+
+# ---------------------------------------------------------------------------
+# Video GOPs (Section 3.3): temporal lifting and the GOP container.
+def test_temporal_lifting_matches_oracle(codec, model32):
+    from oracle.lifting import temporal_forward, temporal_inverse
+    blob, gm, om = model32
+    rng = np.random.default_rng(50)
+    frames = rng.uniform(-128, 127, (8, 24, 40))
+    bands = temporal_forward(list(frames), om.tensors, 3)
+    got = codec.temporal_lift(gm, frames.astype(np.float32), forward=True)
+    assert np.max(np.abs(got - np.stack(bands))) < 2e-3
+    back = codec.temporal_lift(gm, np.stack(bands).astype(np.float32), forward=False)
+    ref = temporal_inverse(bands, om.tensors, 3)
+    assert np.max(np.abs(back - np.stack(ref))) < 2e-3
+    assert np.max(np.abs(back - frames)) < 2e-3
+
+
+def test_gop_roundtrip_psnr_matches_oracle(codec):
+    bl, bh = _blob(C=32, seed=2), _blob(C=32, seed=3)
+    ml, mh = codec.load_model(bl), codec.load_model(bh)
+    frames = S.video_gop(40, 56, 8, seed=7)
+    gs = codec.encode_gop(ml, mh, frames, q=8.0)
+    out = codec.decode_gop(ml, mh, gs, 8, frames.shape[1:])
+    ref = K.decode_gop(bl, bh, K.encode_gop(bl, bh, frames, q=8.0))
+    assert abs(_psnr(out, frames) - _psnr(ref, frames)) < 0.01
+    fine = codec.decode_gop(ml, mh, codec.encode_gop(ml, mh, frames, q=1 / 32.0), 8, frames.shape[1:])
+    assert np.max(np.abs(fine.astype(int) - frames.astype(int))) <= 1
