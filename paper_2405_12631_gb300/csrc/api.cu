@@ -7,6 +7,7 @@
 #include "codec.h"
 #include "ctx_tc.h"
 #include "driver.h"
+#include "ll_ar.h"
 #include "prof.h"
 
 namespace pw {
@@ -154,6 +155,10 @@ static int finish(pw_ctx *ctx) {
   return PW_OK;
 }
 
+static ArWeightsDev ar_weights(const Model &m) {
+  return ArWeightsDev{m.ar_w5, m.ar_b5, m.ar_w1, m.ar_b1, m.ar_wh, m.ar_bh};
+}
+
 static uint16_t prec_flags(pw_ctx *ctx) {
   return (uint16_t)((ctx->precision == PW_PREC_BF16 ? 1 : 0) << FLAG_PREC_SHIFT);
 }
@@ -195,8 +200,15 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *co
   bump(ctx, 2);
   for (int sb = 0; sb < g.nsb; ++sb) {
     if (sb == 0 && g.ll_ar) {
-      set_last_error("autoregressive LL decoding is not available in this build");
-      return PW_EUNSUPPORTED;
+      // autoregressive LL: one warp per plane walks the positions in raster
+      // order, decoding each symbol from the plane's single-state chunk
+      if (g.group_count[0] != 1) { set_last_error("bad LL chunk layout"); return PW_ECORRUPT; }
+      ProfScope ps(ctx, KC_RANS_DEC, 0.0, (double)P * g.sh[0] * g.sw[0] * 8.0);
+      int s = launch_ll_ar_decode(dch + pl.gbase[0], P, g.sh[0], g.sw[0], m.C, ar_weights(m),
+                                  ctx->bank, pl.ws.Q, ctx->status, st);
+      bump(ctx);
+      if (s) return s;
+      continue;
     }
     if (sb >= 1) {
       int s = run_lstm(ctx, m, g, pl.ws, sb);
@@ -379,22 +391,29 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
   launch_cdf_bank(ctx->bank, st);
   bump(ctx);
   for (int sb = 0; sb < g.nsb; ++sb) {
-    if (sb == 0 && g.ll_ar) {
-      set_last_error("autoregressive LL coding is not available in this build");
-      return PW_EUNSUPPORTED;
-    }
     int s;
+    if (sb == 0 && g.ll_ar) {
+      // all LL symbols are known: the AR model runs at every position at once
+      if ((s = launch_ll_ar_params(ws.Q, P, g.sh[0], g.sw[0], m.C, ar_weights(m), ws.idx, nullptr,
+                                   nullptr, st)))
+        return s;
+      bump(ctx);
+      continue;
+    }
     if (sb >= 1 && (s = run_lstm(ctx, m, g, ws, sb))) return s;
     for (int k = 0; k < 4; ++k)
       if ((s = run_context_pass(ctx, m, g, ws, sb, k, false))) return s;
   }
-  // gather values in step order (same layout as idx)
+  // gather values in coding order (same layout as idx): step order, or
+  // raster order for the autoregressive LL chunk
   int32_t *vals = reinterpret_cast<int32_t *>(ws.T0);
   for (int sb = 0; sb < g.nsb; ++sb)
     for (int k = 0; k < 4; ++k) {
-      const int64_t nk = step_count(g.sh[sb], g.sw[sb], k);
+      const bool ar = sb == 0 && g.ll_ar;
+      if (ar && k > 0) continue;
+      const int64_t nk = ar ? (int64_t)g.sh[0] * g.sw[0] : step_count(g.sh[sb], g.sw[sb], k);
       if (!nk) continue;
-      launch_gather_step(ws.Q + (int64_t)P * g.soff[sb], P, g.sh[sb], g.sw[sb], k,
+      launch_gather_step(ws.Q + (int64_t)P * g.soff[sb], P, g.sh[sb], g.sw[sb], ar ? -1 : k,
                          vals + (int64_t)P * g.ioff[sb * 4 + k], nk, st);
       bump(ctx);
     }
@@ -408,7 +427,8 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
         const ChunkTpl &t = g.chunks[j];
         const int p = b * g.nc + c;
         const int gi = t.sb * 4 + (t.step < 0 ? 0 : t.step);
-        const int64_t nk = step_count(g.sh[t.sb], g.sw[t.sb], t.step < 0 ? 0 : t.step);
+        const int64_t nk = t.step < 0 ? (int64_t)g.sh[t.sb] * g.sw[t.sb]
+                                      : step_count(g.sh[t.sb], g.sw[t.sb], t.step);
         EncChunk &e = ec[(b * g.nc + c) * nck + j];
         e.sym_base = (uint64_t)((int64_t)P * g.ioff[gi] + (int64_t)p * nk + t.first);
         e.count = t.count;
@@ -1014,7 +1034,6 @@ int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t
   if (H < mult || W < mult || H % mult || W % mult) {
     set_last_error("H and W must be positive multiples of 2^levels"); return PW_EINVAL;
   }
-  if (m.ll_mode) { set_last_error("autoregressive LL model not available"); return PW_EUNSUPPORTED; }
   Geometry g;
   g.build(H, W, 1, m.levels, 0, 8, 0, m.ll_mode, 16384);
   Plan *pl;
@@ -1024,6 +1043,13 @@ int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t
   PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.Q, q, g.plane_elems * 4, cudaMemcpyHostToDevice, st));
   if (c->precision == PW_PREC_BF16) tc_error_reset(pl->ws, st);
   for (int sb = 0; sb < g.nsb; ++sb) {
+    if (sb == 0 && m.ll_mode == 1) {
+      if ((s = launch_ll_ar_params(pl->ws.Q, 1, g.sh[0], g.sw[0], m.C, ar_weights(m), pl->ws.idx,
+                                   pl->ws.mu, pl->ws.sg, st)))
+        return s;
+      bump(c);
+      continue;
+    }
     if (sb >= 1 && (s = run_lstm(c, m, g, pl->ws, sb))) return s;
     for (int k = 0; k < 4; ++k)
       if ((s = run_context_pass(c, m, g, pl->ws, sb, k, false))) return s;

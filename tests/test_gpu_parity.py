@@ -324,3 +324,39 @@ def test_gop_roundtrip_psnr_matches_oracle(codec):
     assert abs(_psnr(out, frames) - _psnr(ref, frames)) < 0.01
     fine = codec.decode_gop(ml, mh, codec.encode_gop(ml, mh, frames, q=1 / 32.0), 8, frames.shape[1:])
     assert np.max(np.abs(fine.astype(int) - frames.astype(int))) <= 1
+
+
+# ---------------------------------------------------------------------------
+# Autoregressive LL mode (pWave++'s default, Table 1)
+def test_ar_ll_params_and_roundtrip(codec):
+    blob = _blob(C=32, ll_mode=1, seed=4)
+    gm, om = codec.load_model(blob), K.Model(blob)
+    img = S.gray_sinusoids(80, 112, seed=12)
+    qsb = _oracle_latent(om, img)[0]
+    mu_g, sg_g = codec.context_params(gm, 80, 112, _flat([qsb]))
+    params = K.context_params_all(om, qsb)
+    mu_o = np.concatenate([p[0].reshape(-1) for p in params])
+    sg_o = np.concatenate([p[1].reshape(-1) for p in params])
+    assert np.all(np.abs(mu_g - mu_o) <= 1e-3 * np.maximum(np.abs(mu_o), 1.0))
+    assert np.all(np.abs(sg_g - sg_o) <= 1e-3 * sg_o)
+    for im in (img, S.rgb_natural(72, 104, seed=13)):
+        bs = codec.encode_image(gm, im, q=4.0, chunk=300)
+        assert np.array_equal(codec.decode_symbols(gm, bs), codec.analyse(gm, im, q=4.0))
+
+
+def test_ar_ll_decodes_oracle_stream(codec):
+    blob = _blob(C=32, ll_mode=1, seed=4)
+    gm, om = codec.load_model(blob), K.Model(blob)
+    img = S.gray_sinusoids(48, 64, seed=14)
+    qsb = _oracle_latent(om, img)[0]
+    params = K.context_params_all(om, qsb)
+    mu_o = np.concatenate([p[0].reshape(-1) for p in params])
+    sg_o = np.concatenate([p[1].reshape(-1) for p in params])
+    mu_g, sg_g = codec.context_params(gm, 48, 64, _flat([qsb]))
+    a, b = E.index_decision(mu_g, sg_g), E.index_decision(mu_o, sg_o)
+    diff = (a[0] != b[0]) | (a[1] != b[1]) | (a[2] != b[2])
+    assert not np.any(diff & ~E.near_tie(mu_o, sg_o, TIE_EPS))
+    if np.any(diff):
+        pytest.skip(f"{int(diff.sum())} certified near-tie index differences in this input")
+    bs = K.encode_image(blob, img, q=8.0, chunk=256)
+    assert np.array_equal(codec.decode_symbols(gm, bs), _flat([qsb]))

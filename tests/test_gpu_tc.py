@@ -128,3 +128,11 @@ def test_precision_class_recorded_in_stream(tc, pw):
         tc.decode_image(tc.load_model(blob), bs)
     assert e.value.code == pw.PW_EINVAL
     fp.close()
+
+
+def test_bf16_ar_ll_roundtrip(tc):
+    cfg = S.ModelConfig(levels=4, C=64, ll_mode=1)
+    gm = tc.load_model(S.pack_blob(cfg, S.random_model(cfg, 5)))
+    for im in (S.gray_sinusoids(64, 96, seed=15), S.rgb_natural(48, 80, seed=16)):
+        bs = tc.encode_image(gm, im, q=8.0)
+        assert np.array_equal(tc.decode_symbols(gm, bs), tc.analyse(gm, im, q=8.0))
