@@ -234,6 +234,56 @@ int pw_encode_latent(pw_ctx *ctx, const pw_model *m, const int32_t *q, int width
 int pw_conv_bf16(pw_ctx *ctx, int P, int H, int W, int cin, int cout, int ks, int act,
                  const float *x, const float *w, const float *b, float *y);
 
+/* ---- decode server ------------------------------------------------------- */
+/* A decode server for a stream of requests of mixed sizes (the serving
+ * workload: images that arrive one at a time at random instants). The paper
+ * decodes one image per call; the server adds continuous batching around
+ * that same decode path and changes no result.
+ *
+ * pw_server_create starts `lanes` worker threads (1..16). Each lane owns a
+ * CUDA stream and a context of ctx's device and precision; all lanes share
+ * the model m (read only; m and ctx must outlive the server, and ctx itself
+ * is not used by the lanes). A lane repeatedly takes the oldest queued
+ * request together with every queued request of the same geometry (size,
+ * channels, bit depth, format; at most max_batch) and decodes them as one
+ * batch. A batch starts only when its device workspace fits in hbm_budget
+ * bytes next to the workspaces the other lanes hold; an idle lane frees its
+ * workspace. Lanes run concurrently, so different sizes overlap on the GPU.
+ * Each result is bit-identical to pw_decode_image of the same stream on a
+ * context of the same precision.
+ *
+ * pw_server_submit copies the host stream bs[0..n) and returns at once with
+ * a ticket. Errors: those of the header checks of pw_decode_image (PW_ECORRUPT
+ * not a stream, PW_EINVAL another model or precision class),
+ * PW_EAGAIN (one request alone exceeds hbm_budget, or 4096 requests are
+ * queued). pw_server_poll waits up to timeout_ms for a ticket (0: do not
+ * wait) and copies the decoded image into out (host or device, packed or
+ * strided, as pw_decode_image); the ticket is then released. It returns the
+ * decode's status (a failed batch is re-decoded one request at a time, so a
+ * corrupt stream fails only its own ticket), PW_EAGAIN (timeout_ms = 0, not
+ * done), PW_ETIMEOUT, or PW_EINVAL (unknown ticket, or out does not match
+ * the image; the ticket then stays valid).
+ * The submit / poll / stats calls are thread-safe. pw_server_destroy
+ * finishes the batches in flight, drops queued requests and frees all. */
+typedef struct pw_server pw_server;
+typedef struct {
+  uint64_t submitted, completed, failed, rejected, queued, batches;
+  uint64_t held_bytes;       /* workspace bytes the lanes hold now          */
+  double p50_ms, p99_ms;     /* submit -> result ready, completed requests  */
+  double mpix_per_s;         /* decoded pixels / (last result - first submit) */
+} pw_stats;
+/* Estimated device workspace bytes for decoding `count` streams of the
+ * geometry of host stream bs[0..n) in one batch on ctx (the figure the
+ * server's admission uses). Errors as pw_decode_image's header checks. */
+int pw_decode_footprint(pw_ctx *ctx, const pw_model *m, const uint8_t *bs, size_t n, int count,
+                        uint64_t *bytes);
+int pw_server_create(pw_ctx *ctx, const pw_model *m, size_t hbm_budget, int lanes,
+                     int max_batch, pw_server **out);
+int pw_server_submit(pw_server *s, const uint8_t *bs, size_t n, uint64_t *ticket);
+int pw_server_poll(pw_server *s, uint64_t ticket, pw_image *out, int timeout_ms);
+int pw_server_stats(pw_server *s, pw_stats *out);
+void pw_server_destroy(pw_server *s);
+
 /* ---- misc ---------------------------------------------------------------- */
 void pw_free(void *p);
 const char *pw_strerror(int status);

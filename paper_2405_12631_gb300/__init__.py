@@ -36,6 +36,13 @@ class pw_codec_opts(C.Structure):
     _fields_ = [("q", C.c_float), ("lossless", C.c_int32), ("chunk_symbols", C.c_int32)]
 
 
+class pw_stats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("rejected", C.c_uint64), ("queued", C.c_uint64), ("batches", C.c_uint64),
+                ("held_bytes", C.c_uint64), ("p50_ms", C.c_double), ("p99_ms", C.c_double),
+                ("mpix_per_s", C.c_double)]
+
+
 class pw_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 40), ("launches", C.c_uint64), ("ms", C.c_double),
                 ("flops", C.c_double), ("bytes", C.c_double)]
@@ -91,6 +98,13 @@ _sig = {
                                 C.POINTER(C.c_size_t)]),
     "pw_decode_gop": (C.c_int, [_P, _P, _P, _P, C.c_size_t, C.c_int, C.POINTER(pw_image)]),
     "pw_temporal_lift": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "pw_decode_footprint": (C.c_int, [_P, _P, _P, C.c_size_t, C.c_int,
+                                      C.POINTER(C.c_uint64)]),
+    "pw_server_create": (C.c_int, [_P, _P, C.c_size_t, C.c_int, C.c_int, C.POINTER(_P)]),
+    "pw_server_submit": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(C.c_uint64)]),
+    "pw_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(pw_image), C.c_int]),
+    "pw_server_stats": (C.c_int, [_P, C.POINTER(pw_stats)]),
+    "pw_server_destroy": (None, [_P]),
     "pw_ctx_profile": (C.c_int, [_P, C.c_int]),
     "pw_ctx_kernel_stats": (C.c_int, [_P, C.POINTER(pw_kernel_stat), C.c_int]),
     "pw_free": (None, [_P]),
@@ -149,6 +163,55 @@ class Model:
     def close(self):
         if self.handle:
             pw_model_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """A decode server (pw_server_*): continuous batching over worker lanes."""
+
+    def __init__(self, codec: "Codec", model: Model, hbm_budget: int, lanes: int = 2,
+                 max_batch: int = 8):
+        self.codec, self.model = codec, model
+        h = C.c_void_p()
+        check(pw_server_create(codec.ctx, model.handle, int(hbm_budget), int(lanes),
+                               int(max_batch), C.byref(h)))
+        self.handle = h
+        self._shapes = {}
+
+    def submit(self, bs: bytes) -> int:
+        t = C.c_uint64()
+        check(pw_server_submit(self.handle, bs, len(bs), C.byref(t)))
+        self._shapes[t.value] = stream_image_shape(bs)
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = 60000):
+        """Decoded image of a ticket (numpy), or None when not ready yet."""
+        shape, dtype = self._shapes[ticket]
+        out = np.zeros(shape, dtype=dtype)
+        h, w = shape[:2]
+        ch = 1 if len(shape) == 2 else shape[2]
+        im = pw_image(w, h, ch, 8 if out.dtype == np.uint8 else 16, 0, 0, out.ctypes.data, 0)
+        r = pw_server_poll(self.handle, ticket, C.byref(im), int(timeout_ms))
+        if r in (PW_EAGAIN, PW_ETIMEOUT):
+            return None
+        del self._shapes[ticket]
+        check(r)
+        return out
+
+    def stats(self) -> dict:
+        st = pw_stats()
+        check(pw_server_stats(self.handle, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in pw_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            pw_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -225,6 +288,12 @@ class Codec:
         lens = (C.c_size_t * B)(*[len(s) for s in streams])
         check(pw_decode_batch(self.ctx, model.handle, B, ptrs, lens, 0, ims))
         return out
+
+    def decode_footprint(self, model: Model, bs: bytes, count: int = 1) -> int:
+        """Estimated device workspace bytes to decode `count` streams like bs."""
+        b = C.c_uint64()
+        check(pw_decode_footprint(self.ctx, model.handle, bs, len(bs), int(count), C.byref(b)))
+        return int(b.value)
 
     def decode_batch_device(self, model: Model, ptrs, lens, out_ptr: int, shape,
                             bitdepth: int = 8):

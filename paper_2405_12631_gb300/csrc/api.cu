@@ -128,6 +128,12 @@ static int get_plan(pw_ctx *ctx, Model &m, const Geometry &g, int B, const char 
   return PW_OK;
 }
 
+// Release every cached workspace of the context (after its work finished).
+void drop_plans(pw_ctx *ctx) {
+  cudaStreamSynchronize(ctx->stream);
+  cache_of(ctx).plans.clear();
+}
+
 static int check_status(pw_ctx *ctx, Workspace *ws = nullptr) {
   if (launch_failed()) { launch_failed() = false; return PW_EUNSUPPORTED; }
   if (ws && ctx->precision == PW_PREC_BF16) {
@@ -268,6 +274,13 @@ static int build_geo(const StreamHeader &h, Geometry &g) {
   return PW_OK;
 }
 
+int stream_geometry(pw_ctx *ctx, const Model &m, const uint8_t *bs, size_t n, Geometry &g) {
+  StreamHeader h;
+  int s = read_header(bs, n, 0, h);
+  if (s || (s = check_header_model(ctx, m, h))) return s;
+  return build_geo(h, g);
+}
+
 // Stage host streams in device memory; fills ptrs.
 static int stage_streams(pw_ctx *ctx, Plan &pl, int B, const uint8_t *const *bs, const size_t *n,
                          int on_dev, std::vector<const uint8_t *> &ptrs) {
@@ -315,8 +328,8 @@ static int decode_to_planes(pw_ctx *ctx, Model &m, int B, const uint8_t *const *
   return PW_OK;
 }
 
-static int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,
-                        int on_dev, pw_image *out) {
+int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,
+                 int on_dev, pw_image *out) {
   if (B < 1 || !bs || !n || !out) { set_last_error("bad arguments"); return PW_EINVAL; }
   StreamHeader h0;
   int s = read_header(bs[0], n[0], on_dev, h0);

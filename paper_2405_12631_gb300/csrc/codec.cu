@@ -111,6 +111,17 @@ int Workspace::alloc(const Geometry &g, int P_, int C, bool params, bool bf16) {
   return PW_OK;
 }
 
+int64_t Workspace::estimate(const Geometry &g, int P, int C, bool params, bool bf16) {
+  const int64_t pe = (int64_t)P * g.Hp * g.Wp;
+  const int64_t big = (int64_t)P * g.sh.back() * g.sw.back();
+  auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
+  int64_t tot = 7 * al(pe * 4) + 2 * al(big * C * 4);
+  if (!bf16) tot += 3 * al(big * 2 * C * 4) + 3 * al(big * C * 4);
+  else tot += 1024 + 2 * al(big * 2 * C * 2) + 5 * al(big * C * 2);
+  if (params) tot += 2 * al(pe * 4);
+  return tot;
+}
+
 void Workspace::release() {
   if (tc) tc_workspace_free(this);
   if (base) cudaFree(base);

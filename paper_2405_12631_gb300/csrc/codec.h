@@ -107,6 +107,8 @@ struct Workspace {
   void *tc = nullptr;          // BF16 activations (tensor-core path)
   int lstm_cur = 0;            // which Cst holds the current cell state
   int alloc(const Geometry &g, int P, int C, bool params, bool bf16);
+  // upper bound of the device bytes alloc() takes for these arguments
+  static int64_t estimate(const Geometry &g, int P, int C, bool params, bool bf16);
   void release();
   ~Workspace() { release(); }
 };
@@ -121,6 +123,14 @@ int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         const float *src_planes);
 int temporal_planes(pw_ctx *ctx, Model &m, int nf, int nc, int Hp, int Wp, const float *in,
                     float *out, float *tmp0, float *tmp1, bool forward);
+// Batch decode of B streams of one geometry (api.cu) and release of a
+// context's cached workspaces; used by the decode server.
+int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,
+                 int on_dev, pw_image *out);
+void drop_plans(pw_ctx *ctx);
+// Validate a host stream's header against the model and the context's
+// precision and derive its geometry (api.cu).
+int stream_geometry(pw_ctx *ctx, const Model &m, const uint8_t *bs, size_t n, Geometry &g);
 
 }  // namespace pw
 

@@ -22,7 +22,9 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstring>
+#include <mutex>
 
 #include "ctx_tc.h"
 #include "prof.h"
@@ -615,10 +617,10 @@ __global__ void k_dw3x3_bf16(const __nv_bfloat16 *__restrict__ U, const float *_
 
 // ---------------------------------------------------------------------------
 // Host side.
-static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
 
 static int get_encoder() {
-  if (g_encode) return PW_OK;
+  if (g_encode.load()) return PW_OK;
   void *fn = nullptr;
   cudaDriverEntryPointQueryResult q;
   if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
@@ -627,7 +629,7 @@ static int get_encoder() {
     set_last_error("cuTensorMapEncodeTiled not available");
     return PW_ECUDA;
   }
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  g_encode.store(reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn));
   return PW_OK;
 }
 
@@ -643,7 +645,7 @@ static int make_map(CUtensorMap *map, const __nv_bfloat16 *base, int P, int G, i
                            (cuuint64_t)G * H * W * 16};
   cuuint32_t box[4] = {(cuuint32_t)box_x * 8, (cuuint32_t)box_y, (cuuint32_t)box_g, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims, strides, box,
+  CUresult r = g_encode.load()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims, strides, box,
                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -653,7 +655,7 @@ static int make_map(CUtensorMap *map, const __nv_bfloat16 *base, int P, int G, i
   return PW_OK;
 }
 
-static int g_num_sms = 0;
+static std::atomic<int> g_num_sms{0};
 
 // Launch one tensor-core convolution.
 // in / in_G / in_goff: the input tensor of the first nkb0 K-blocks (all of
@@ -662,11 +664,11 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
                    int in_goff, int P, int H, int W, TcConvArgs a, int *err,
                    const __nv_bfloat16 *in1 = nullptr, int in1_G = 0, int in1_goff = 0,
                    int nkb0 = -1) {
-  if (!g_num_sms) {
-    int dev = 0;
+  if (!g_num_sms.load()) {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 148;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    g_num_sms.store(n > 0 ? n : 148);
   }
   const int R = cv.ks / 2;
   a.P = P; a.H = H; a.W = W; a.ks = cv.ks; a.cin = cv.cin; a.kb = cv.kb; a.nkb = cv.cin / cv.kb;
@@ -695,19 +697,18 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
   } else {
     map1 = map;
   }
-  int per_nb = g_num_sms / cv.nb;
+  int per_nb = g_num_sms.load() / cv.nb;
   if (per_nb < 1) per_nb = 1;
   if (per_nb > a.tiles) per_nb = a.tiles;
   const int grid = per_nb * cv.nb;
   cudaStream_t st = ctx->stream;
 #define PW_TC_CASE(KS_, KB_, N_, E_)                                                        \
   if (cv.ks == KS_ && cv.kb == KB_ && cv.ncta == N_ && a.epi == E_) {                       \
-    static bool attr = false;                                                               \
-    if (!attr) {                                                                            \
+    static std::once_flag attr;                                                             \
+    std::call_once(attr, [&] {                                                              \
       cudaFuncSetAttribute(k_conv_tc<KS_, KB_, N_, E_>,                                     \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);        \
-      attr = true;                                                                          \
-    }                                                                                       \
+    });                                                                                     \
     k_conv_tc<KS_, KB_, N_, E_><<<grid, kConvThreads, smem, st>>>(map, map1, a);            \
     ctx->launches += 1;                                                                     \
     return PW_OK;                                                                           \

@@ -12,6 +12,8 @@
 // spatial transform; Haar (P = s, U = s / 2) for the temporal one. Integer
 // mode (lossless) rounds P with floor(v) and U with floor(v + 1/2), which
 // makes the transform the JPEG 2000 reversible 5/3 when the CNN is zero.
+#include <mutex>
+
 #include "pw_internal.cuh"
 #include "lift_kernels.cuh"
 
@@ -282,12 +284,11 @@ static int grid_for(int64_t n) {
 }
 
 void launch_lift_step(const LiftStepParams &a, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
+  static std::once_flag attr;
+  std::call_once(attr, [] {
     cudaFuncSetAttribute(k_lift_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(LiftSmem));
-    attr = true;
-  }
+  });
   const int tiles = ((a.H + LT - 1) / LT) * ((a.W + LT - 1) / LT);
   dim3 grid(tiles, 1, a.P);
   k_lift_step<<<grid, 256, sizeof(LiftSmem), st>>>(a);
