@@ -17,6 +17,12 @@ images, host wall clock around each call. roofline: the dominant kernel class
 from the library's own CUDA-event timing. cpu_baseline: the CPU oracle
 decoding a bounded sample (one 256x256 RGB crop of the workload).
 
+fp32_single_image: the plain FP32 GPU path decoding the same images one per
+call (its own FP32 streams, same q). serving: an open-loop run of the serving
+workload's first 200 requests (Poisson arrivals at 200/s, mixed sizes from
+256x256 to 2048x2048, gray/RGB) through the decode server, with p50/p99
+latency (submit -> decoded host image) and MPix/s.
+
 With --impl reference the CPU oracle is timed instead (each step decodes one
 128x128 RGB crop of the workload) and one JSON line with "impl": "reference"
 is printed. Multi-GPU (torchrun, N > 1): every rank decodes its own batch
@@ -191,6 +197,98 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def fp32_single_image(pw, local, imgs, qs, blob, stream_ptr):
+    """The plain FP32 path decoding the workload one image per call.
+
+    Its own FP32 streams (the precision class is part of the stream); the
+    same images and quantiser steps, so the rate is essentially equal (bpp
+    reported). Device streams -> device image, CUDA events around all calls.
+    """
+    import torch
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    c32 = pw.Codec(local, "fp32", stream=stream_ptr)
+    m32 = c32.load_model(blob)
+    enc = []
+    for img, q in zip(imgs, qs):
+        enc.append(c32.encode_image(m32, img, q=q))
+    bufs = [torch.from_numpy(np.frombuffer(b, dtype=np.uint8).copy()).to(dev) for b in enc]
+    out = torch.empty((H, W, 3), dtype=torch.uint8, device=dev)
+
+    def one(i):
+        c32.decode_batch_device(m32, [bufs[i].data_ptr()], [len(enc[i])], out.data_ptr(), (H, W, 3))
+
+    one(0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(len(enc)):
+        one(i)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    n = len(enc)
+    res = {"value": n * H * W / (ms / 1e3) / 1e6, "unit": "MPix/s", "images": n,
+           "ms_per_image": ms / n, "bpp": 8.0 * sum(len(b) for b in enc) / (n * H * W),
+           "path": "fp32 SIMT context model, one image per decode call"}
+    m32.close()
+    c32.close()
+    return res
+
+
+def serving_run(pw, codec, model, n_req: int, rate: float, lanes: int, max_batch: int,
+                budget: int):
+    """Open-loop serving: a Poisson stream of mixed-size decode requests.
+
+    The first n_req requests of the serving workload (Poisson arrivals at
+    `rate` per second, w and h log-uniform in [256, 2048] rounded down to a
+    multiple of 16, gray/RGB 50/50, q uniform over {4, 8, 16, 32}); every
+    image is a crop of a seeded synthetic canvas, pre-encoded by the GPU
+    encoder. Requests are submitted at their arrival instants; latency is
+    submit -> decoded image on the host (the server's own clock).
+    """
+    import synthetic as S
+    reqs = S.request_stream(n=n_req, rate=rate, seed=7)
+    rng = np.random.default_rng(7)
+    canvas = {1: S.gray_sinusoids(2048, 2048, seed=7), 3: S.rgb_natural(2048, 2048, seed=7)}
+    streams = []
+    for r in reqs:
+        y0 = int(rng.integers(0, 2048 - r["h"] + 1))
+        x0 = int(rng.integers(0, 2048 - r["w"] + 1))
+        img = np.ascontiguousarray(canvas[r["c"]][y0:y0 + r["h"], x0:x0 + r["w"]])
+        streams.append(codec.encode_image(model, img, q=r["q"]))
+    srv = pw.Server(codec, model, hbm_budget=budget, lanes=lanes, max_batch=max_batch)
+    done = {}
+
+    def collect():
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(0.0005)
+            done[i] = srv.poll(tickets[i], timeout_ms=600000) is not None
+
+    tickets = [None] * len(reqs)
+    th = threading.Thread(target=collect)
+    th.start()
+    t0 = time.perf_counter()
+    for i, r in enumerate(reqs):
+        dt = t0 + r["t"] - reqs[0]["t"] - time.perf_counter()
+        if dt > 0:
+            time.sleep(dt)
+        tickets[i] = srv.submit(streams[i])
+    th.join()
+    st = srv.stats()
+    srv.close()
+    mpix = sum(r["w"] * r["h"] for r in reqs) / 1e6
+    return {"requests": len(reqs), "rate_per_s": rate, "lanes": lanes, "max_batch": max_batch,
+            "hbm_budget_gb": budget / 2**30, "mean_mpix_per_request": mpix / len(reqs),
+            "completed": int(st["completed"]), "batches": int(st["batches"]),
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "mpix_per_s": st["mpix_per_s"],
+            "offered_mpix_per_s": mpix / max(reqs[-1]["t"] - reqs[0]["t"], 1e-9),
+            "all_ok": all(done.values())}
+
+
+# ---------------------------------------------------------------------------
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -296,22 +394,33 @@ def run_gpu(args):
     clocks = sampler.summary()
     roofline = None
     if dom:
-        tc = args.precision == "bf16" and dom["name"].startswith("ctx")
+        hbm = float(peaks.get("hbm_gbs", 6800.0))
         if dom["name"].startswith("ctx") or dom["name"] == "lift_step":
-            if tc:
-                peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-                bound, unit = "tensor", "TFLOP/s"
+            if args.precision == "bf16" and dom["name"].startswith("ctx"):
+                tpeak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+                cbound = "tensor"
             else:
                 # FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
-                peak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
-                bound, unit = "alu", "TFLOP/s"
-            achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+                tpeak = 152 * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+                cbound = "alu"
+            # the bound is whichever roof the kernel's arithmetic intensity
+            # (algorithmic FLOP per algorithmic HBM byte) hits first
+            ridge = tpeak * 1e12 / (hbm * 1e9)
+            ai = dom["flops"] / max(dom["bytes"], 1.0)
+            if ai >= ridge:
+                bound, unit, peak = cbound, "TFLOP/s", tpeak
+                achieved = dom["flops"] / (dom["ms"] / 1e3) / 1e12
+            else:
+                bound, unit, peak = "hbm", "GB/s", hbm
+                achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
         else:
-            peak = float(peaks.get("hbm_gbs", 6800.0))
+            ai, ridge = None, None
+            peak = hbm
             bound, unit = "hbm", "GB/s"
             achieved = dom["bytes"] / (dom["ms"] / 1e3) / 1e9
         roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                     "frac": achieved / peak, "traffic": None, "kernel": dom["name"],
+                    "flop_per_byte": ai, "ridge_flop_per_byte": ridge,
                     "peak_source": peak_kind + (" (derived: SMs x lanes x clock)"
                                                 if bound == "alu" else "")}
     total_kernel_ms = sum(k["ms"] for k in kern) or 1.0
@@ -340,6 +449,12 @@ def run_gpu(args):
                    "reasons": clocks["reasons"]},
         "wall_s_timed_region": t_wall,
     }
+    if not args.no_fp32 and world == 1:
+        line["fp32_single_image"] = fp32_single_image(pw, local, imgs, qs, blob,
+                                                      stream.cuda_stream)
+    if args.serve > 0 and world == 1:
+        line["serving"] = serving_run(pw, codec, model, args.serve, 200.0, lanes=4,
+                                      max_batch=8, budget=48 << 30)
     if not args.no_cpu and world == 1:
         px, dt = cpu_oracle_decode_sample(256)
         line["cpu_baseline"] = {"value": px / dt / 1e6, "unit": "MPix/s",
@@ -360,6 +475,10 @@ def main():
                     help="images per step (24 = the benchmark workload; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true",
+                    help="skip the FP32 single-image comparison")
+    ap.add_argument("--serve", type=int, default=200,
+                    help="requests of the open-loop serving run (0 = skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
