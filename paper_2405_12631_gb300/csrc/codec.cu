@@ -117,7 +117,7 @@ int64_t Workspace::estimate(const Geometry &g, int P, int C, bool params, bool b
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
   int64_t tot = 7 * al(pe * 4) + 2 * al(big * C * 4);
   if (!bf16) tot += 3 * al(big * 2 * C * 4) + 3 * al(big * C * 4);
-  else tot += 1024 + 2 * al(big * 2 * C * 2) + 5 * al(big * C * 2);
+  else tot += tc_workspace_bytes(g, P, C);
   if (params) tot += 2 * al(pe * 4);
   return tot;
 }

@@ -56,6 +56,11 @@ struct TcAct {  // BF16 activations in [P][G][H][W][8]
   // read h_{i-1} while its epilogue writes h_i); Z, V, Z2 (C); U (2C).
   __nv_bfloat16 *X = nullptr, *L[2] = {nullptr, nullptr}, *Z = nullptr, *U = nullptr,
                 *V = nullptr, *Z2 = nullptr;
+  // Step-1 tail on the step-1 positions only, in the compact layout
+  // [P][G][ceil(h/2)][n_even + n_odd][8] (row pair, index within the pair):
+  // Vc = dw3x3 output, Zc = block input (residual), Z2c = block output (C
+  // each), U2c = feed-forward hidden layer (2C).
+  __nv_bfloat16 *Vc = nullptr, *Zc = nullptr, *Z2c = nullptr, *U2c = nullptr;
   int *err = nullptr;
   void *base = nullptr;
 };
@@ -215,6 +220,10 @@ struct TcConvArgs {
   const int32_t *fold_s;        // quantised subband [P][H][W]
   int nkb0;                     // K-blocks read through the first tensor map
   int in1_goff;                 // group offset of the second tensor map
+  // TE_HEAD on a compact step layout (H x W = row pairs x positions per
+  // pair): compact_n = number of step positions (0: full-plane layout),
+  // full_W = width of the subband (for the mu / sigma planes)
+  int compact_n, full_W, full_H;
   int *err;
 };
 
@@ -413,7 +422,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
                           : 0.f;
           }
         } else if (EPI == TE_HEAD || (EPI == TE_STORE && a.res)) {
-          const bool need = (EPI == TE_STORE) || step_of(y, x) == a.step;
+          const bool need = (EPI == TE_STORE) ||
+                            (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step);
           if (need) {
 #pragma unroll
             for (int g = 0; g < NH / 8; ++g)
@@ -499,7 +509,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (ch0 >> 3) + g) * hw + pix) * 8,
                        hv + 8 * g);
       } else {  // TE_HEAD: z' = res + acc + b over all C columns, then 1x1(C->2)
-        if (step_of(y, x) == a.step) {
+        if (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step) {
           float mu = a.bh[0], rho = a.bh[1];
 #pragma unroll
           for (int g = 0; g < NCTA / 8; ++g) {
@@ -512,11 +522,23 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
               rho = fmaf(a.wh[NCTA + 8 * g + e], z, rho);
             }
           }
-          const int qi = step_index(a.W, a.step, y, x);
+          int qi;
+          int64_t fpix, fhw;
+          if (a.compact_n) {
+            qi = (int)pix;
+            int fy, fx;
+            step_pos(a.full_W, a.step, qi, fy, fx);
+            fpix = (int64_t)fy * a.full_W + fx;
+            fhw = (int64_t)a.full_H * a.full_W;
+          } else {
+            qi = step_index(a.W, a.step, y, x);
+            fpix = pix;
+            fhw = hw;
+          }
           a.idx[(int64_t)p * a.idx_stride + qi] = pack_index(mu, rho);
           if (a.mu_out) {
-            a.mu_out[(int64_t)p * hw + pix] = mu;
-            a.sg_out[(int64_t)p * hw + pix] = rho > 20.f ? rho : log1pf(expf(rho));
+            a.mu_out[(int64_t)p * fhw + fpix] = mu;
+            a.sg_out[(int64_t)p * fhw + fpix] = rho > 20.f ? rho : log1pf(expf(rho));
           }
         }
       }
@@ -612,6 +634,42 @@ __global__ void k_dw3x3_bf16(const __nv_bfloat16 *__restrict__ U, const float *_
       for (int k = 0; k < 8; ++k) v[k] = fmaf(w[(8 * g + k) * 9 + tap], u[k], v[k]);
     }
     store_bf16x8(V + (pg * hw + (int64_t)y * W + x) * 8, v);
+  }
+}
+
+// Compact step tail input: for the q-th position (y, x) of step `step`,
+// Vc[q] = dw3x3(U)(y, x) + b and Zc[q] = Z(y, x) (C channels each, blocked
+// layout; q indexes the compact plane of hc x wc positions).
+__global__ void k_dw3x3_compact(const __nv_bfloat16 *__restrict__ U,
+                                const __nv_bfloat16 *__restrict__ Z, const float *__restrict__ w,
+                                const float *__restrict__ b, __nv_bfloat16 *__restrict__ Vc,
+                                __nv_bfloat16 *__restrict__ Zc, int P, int H, int W, int C,
+                                int step, int n, int64_t chw) {
+  const int G = C / 8;
+  const int64_t tot = (int64_t)P * G * n;
+  const int64_t hw = (int64_t)H * W;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % n);
+    const int64_t pg = e / n;  // p * G + g
+    const int g = (int)(pg % G);
+    int y, x;
+    step_pos(W, step, q, y, x);
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = b[8 * g + k];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+      float u[8];
+      load_bf16x8(U + (pg * hw + (int64_t)yy * W + xx) * 8, u);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = fmaf(w[(8 * g + k) * 9 + tap], u[k], v[k]);
+    }
+    store_bf16x8(Vc + (pg * chw + q) * 8, v);
+    *reinterpret_cast<uint4 *>(Zc + (pg * chw + q) * 8) =
+        *reinterpret_cast<const uint4 *>(Z + (pg * hw + (int64_t)y * W + x) * 8);
   }
 }
 
@@ -843,12 +901,34 @@ void Model::free_tc() {
 }
 
 // ---- workspace -----------------------------------------------------------
+// Positions of the compact step-1 plane of an h x w subband (row pairs x
+// step-1 positions per pair).
+static int64_t compact_elems(int h, int w) {
+  return (int64_t)((h + 1) >> 1) * (row_count(w, step_phase(0, 0)) + row_count(w, step_phase(0, 1)));
+}
+
+int64_t tc_workspace_bytes(const Geometry &g, int P, int C) {
+  const int64_t big = (int64_t)P * g.sh.back() * g.sw.back();
+  int64_t cmax = 0;
+  for (int sb = 0; sb < g.nsb; ++sb) cmax = std::max(cmax, compact_elems(g.sh[sb], g.sw[sb]));
+  cmax *= P;
+  auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
+  return 1024 + al(big * 2 * C * 2) + 5 * al(big * C * 2) + al(big * 2 * C * 2) +
+         3 * al(cmax * C * 2) + al(cmax * 2 * C * 2);
+}
+
 int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
   const int64_t big = (int64_t)ws->P * g.sh.back() * g.sw.back();
+  int64_t cmax = 0;
+  for (int sb = 0; sb < g.nsb; ++sb) cmax = std::max(cmax, compact_elems(g.sh[sb], g.sw[sb]));
+  cmax *= ws->P;
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
-  // X (2C), L0 (C), L1 (C), Z (C), U (2C), V (C), Z2 (C); bf16
-  const int64_t sizes[7] = {big * 2 * C * 2, big * C * 2, big * C * 2, big * C * 2,
-                            big * 2 * C * 2, big * C * 2, big * C * 2};
+  // X (2C), L0 (C), L1 (C), Z (C), U (2C), V (C), Z2 (C); compact Vc, Zc,
+  // Z2c (C), U2c (2C); bf16
+  constexpr int kN = 11;
+  const int64_t sizes[kN] = {big * 2 * C * 2, big * C * 2,  big * C * 2,      big * C * 2,
+                             big * 2 * C * 2, big * C * 2,  big * C * 2,      cmax * C * 2,
+                             cmax * C * 2,    cmax * C * 2, cmax * 2 * C * 2};
   int64_t tot = 1024;
   for (int64_t v : sizes) tot += al(v);
   TcAct *t = new TcAct();
@@ -861,8 +941,9 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
   t->err = reinterpret_cast<int *>(b);
   cudaMemset(t->err, 0, 1024);
   int64_t o = 1024;
-  __nv_bfloat16 **dst[7] = {&t->X, &t->L[0], &t->L[1], &t->Z, &t->U, &t->V, &t->Z2};
-  for (int i = 0; i < 7; ++i) { *dst[i] = reinterpret_cast<__nv_bfloat16 *>(b + o); o += al(sizes[i]); }
+  __nv_bfloat16 **dst[kN] = {&t->X,  &t->L[0], &t->L[1], &t->Z,  &t->U,  &t->V,
+                             &t->Z2, &t->Vc,   &t->Zc,   &t->Z2c, &t->U2c};
+  for (int i = 0; i < kN; ++i) { *dst[i] = reinterpret_cast<__nv_bfloat16 *>(b + o); o += al(sizes[i]); }
   ws->tc = t;
   return PW_OK;
 }
@@ -936,20 +1017,35 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     if ((s = conv(cin_, l, G, 0, a, 0))) return s;                 // z = 1x1(l)
     a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
     if ((s = conv(c1, t.Z, G, 0, a, 0))) return s;                 // u = lrelu(1x1 z)
+    // Everything after the depthwise conv is per position and only the
+    // step-1 positions' parameters are used: run it on those alone, in the
+    // compact layout (hc row pairs x wc positions per pair).
+    const int hc = (h + 1) >> 1;
+    const int wc = row_count(w, step_phase(0, 0)) + row_count(w, step_phase(0, 1));
+    const int n0 = step_count(h, w, 0);
+    const int64_t chw = (int64_t)hc * wc;
+    const double cpix = (double)P * n0;
+    auto cconv = [&](const TcWeights::Conv &cv, const __nv_bfloat16 *in, int in_G,
+                     TcConvArgs a2) {
+      ProfScope ps(ctx, KC_CONV1, 2.0 * cpix * cv.cin * cv.cout,
+                   cpix * 2.0 * (cv.cin + cv.cout + (a2.res ? cv.cout : 0)));
+      return conv_tc(ctx, cv, in, in_G, 0, P, hc, wc, a2, t.err);
+    };
     {
-      ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * 4.0 * C);
-      k_dw3x3_bf16<<<grid_for((int64_t)P * h * w * G), 256, 0, st>>>(t.U, n.wdw, n.bdw, t.V, P, h,
-                                                                     w, C);
+      ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * cpix * 9 * C, cpix * 2.0 * C * 4);
+      k_dw3x3_compact<<<grid_for((int64_t)P * n0 * G), 256, 0, st>>>(
+          t.U, t.Z, n.wdw, n.bdw, t.Vc, t.Zc, P, h, w, C, 0, n0, chw);
       ctx->launches += 1;
     }
-    a = TcConvArgs{}; a.epi = TE_STORE; a.out = t.Z2; a.out_G = G; a.res = t.Z; a.res_G = G;
-    if ((s = conv(c2, t.V, G, 0, a, 0))) return s;                 // z2 = z + 1x1(v)
-    a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = 2 * G;
-    if ((s = conv(c3, t.Z2, G, 0, a, 0))) return s;                // u2 = lrelu(1x1 z2)
-    a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z2; a.res_G = G;
+    a = TcConvArgs{}; a.epi = TE_STORE; a.out = t.Z2c; a.out_G = G; a.res = t.Zc; a.res_G = G;
+    if ((s = cconv(c2, t.Vc, G, a))) return s;                     // z2 = z + 1x1(v)
+    a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U2c; a.out_G = 2 * G;
+    if ((s = cconv(c3, t.Z2c, G, a))) return s;                    // u2 = lrelu(1x1 z2)
+    a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z2c; a.res_G = G;
     a.wh = n.wh; a.bh = n.bh; a.step = 0; a.idx = idx; a.idx_stride = nk;
     a.mu_out = mu; a.sg_out = sgp;
-    return conv(c4, t.U, 2 * G, 0, a, 0);                          // head
+    a.compact_n = n0; a.full_W = w; a.full_H = h;
+    return cconv(c4, t.U2c, 2 * G, a);                             // head
   }
   const TcWeights::Conv &zf = ll ? W.lk_zf[step - 1] : W.sk_zf[step - 1];
   const float *fw = ll ? W.lk_fw[step - 1] : W.sk_fw[step - 1];

@@ -4,6 +4,8 @@
 
 namespace pw {
 int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C);
+// Device bytes tc_workspace_alloc takes for P planes of geometry g.
+int64_t tc_workspace_bytes(const Geometry &g, int P, int C);
 void tc_workspace_free(Workspace *ws);
 int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
                 const int32_t *sprev, int up, int first, int cur);
