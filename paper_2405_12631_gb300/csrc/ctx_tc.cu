@@ -43,10 +43,11 @@ struct TcWeights {
   Conv sk_z[3], sk_c1[3], sk_c2[3];             // sb set, steps 1..3
   Conv l0_in, l0_w1, l0_w2, l0_w3, l0_w4;       // ll set
   Conv lk_z[3], lk_c1[3], lk_c2[3];
-  // steps 2-4 with the masked input conv folded into z = 1x1(l) + mix:
-  // zf = 1x1 over l only (bias includes the folded bias), fw = [9][C] taps
-  Conv sk_zf[3], lk_zf[3];
-  float *sk_fw[3] = {nullptr, nullptr, nullptr}, *lk_fw[3] = {nullptr, nullptr, nullptr};
+  // steps 2-4 with the masked input conv folded into the 1x1: zt = 1x1 over
+  // [l (C channels), T (32 channels: the 9 masked neighbour values, each
+  // split into a BF16 high and low part, then zero padding)]; the bias
+  // includes the folded bias
+  Conv sk_zt[3], lk_zt[3];
   std::vector<void *> allocs;
 };
 
@@ -61,6 +62,8 @@ struct TcAct {  // BF16 activations in [P][G][H][W][8]
   // Vc = dw3x3 output, Zc = block input (residual), Z2c = block output (C
   // each), U2c = feed-forward hidden layer (2C).
   __nv_bfloat16 *Vc = nullptr, *Zc = nullptr, *Z2c = nullptr, *U2c = nullptr;
+  // T: masked neighbour values of steps 2-4 (32 channels, see TcWeights)
+  __nv_bfloat16 *T = nullptr;
   int *err = nullptr;
   void *base = nullptr;
 };
@@ -191,7 +194,7 @@ __device__ __forceinline__ float sigm_fast(float x) { return fmaf(0.5f, tanh_fas
 __device__ __forceinline__ float lrelu_f(float x) { return x >= 0.f ? x : 0.01f * x; }
 
 // ---------------------------------------------------------------------------
-enum { TE_STORE = 0, TE_LSTM = 1, TE_HEAD = 2, TE_FOLD = 3 };
+enum { TE_STORE = 0, TE_LSTM = 1, TE_HEAD = 2 };
 
 struct TcConvArgs {
   int P, H, W;
@@ -215,9 +218,6 @@ struct TcConvArgs {
   uint32_t *idx;
   int64_t idx_stride;
   float *mu_out, *sg_out;
-  // TE_FOLD: v += sum_tap fold_w[tap][c] * (m_<step s)(y+dy, x+dx), then store
-  const float *fold_w;          // [9][ncta] (already including the 1x1 mix)
-  const int32_t *fold_s;        // quantised subband [P][H][W]
   int nkb0;                     // K-blocks read through the first tensor map
   int in1_goff;                 // group offset of the second tensor map
   // TE_HEAD on a compact step layout (H x W = row pairs x positions per
@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const int n0 = nb * NCTA + col0;   // first output column handled here
       // Global operands of the epilogue do not depend on the accumulator:
       // load them before waiting so their latency overlaps the MMAs.
-      constexpr int NPF = (EPI == TE_LSTM) ? NH / 4 : (EPI == TE_FOLD ? 9 : 1);
+      constexpr int NPF = (EPI == TE_LSTM) ? NH / 4 : 1;
       float pf[NPF];
       uint4 pres[(EPI == TE_HEAD || EPI == TE_STORE) ? NH / 8 : 1];
       if (work && valid) {
@@ -411,15 +411,6 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
             float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
             if (!a.first) c4 = __ldg(reinterpret_cast<const float4 *>(a.c_prev + ppix * a.C + n0 / 4 + k));
             pf[k] = c4.x; pf[k + 1] = c4.y; pf[k + 2] = c4.z; pf[k + 3] = c4.w;
-          }
-        } else if (EPI == TE_FOLD) {
-          const int32_t *sp = a.fold_s + (int64_t)p * hw;
-#pragma unroll
-          for (int tap = 0; tap < 9; ++tap) {
-            const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-            pf[tap] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W && step_of(yy, xx) < a.step)
-                          ? (float)__ldg(sp + (int64_t)yy * a.W + xx)
-                          : 0.f;
           }
         } else if (EPI == TE_HEAD || (EPI == TE_STORE && a.res)) {
           const bool need = (EPI == TE_STORE) ||
@@ -456,25 +447,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 #pragma unroll
       for (int j = 0; j < NH; ++j) v[j] += a.bias[n0 + j];
       if (!valid) continue;
-      if (EPI == TE_FOLD) {
-        const float *nbv = pf;
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-          const float4 *wr = reinterpret_cast<const float4 *>(a.fold_w + tap * NCTA + col0);
-#pragma unroll
-          for (int j = 0; j < NH / 4; ++j) {
-            const float4 w4 = __ldg(wr + j);
-            v[4 * j] = fmaf(w4.x, nbv[tap], v[4 * j]);
-            v[4 * j + 1] = fmaf(w4.y, nbv[tap], v[4 * j + 1]);
-            v[4 * j + 2] = fmaf(w4.z, nbv[tap], v[4 * j + 2]);
-            v[4 * j + 3] = fmaf(w4.w, nbv[tap], v[4 * j + 3]);
-          }
-        }
-#pragma unroll
-        for (int g = 0; g < NH / 8; ++g)
-          store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (n0 >> 3) + g) * hw + pix) * 8,
-                       v + 8 * g);
-      } else if (EPI == TE_STORE) {
+      if (EPI == TE_STORE) {
 #pragma unroll
         for (int g = 0; g < NH / 8; ++g) {
           const int gg = (n0 >> 3) + g;
@@ -673,6 +646,41 @@ __global__ void k_dw3x3_compact(const __nv_bfloat16 *__restrict__ U,
   }
 }
 
+// T = the 9 masked neighbour values of every position for step `step`
+// (neighbours coded in an earlier step, else 0), channel 2 tap = BF16 value,
+// 2 tap + 1 = BF16 of the remainder, channels 18..31 = 0. One thread per
+// position; blocked layout [P][4][H][W][8].
+__global__ void k_masked_taps(const int32_t *__restrict__ s, __nv_bfloat16 *__restrict__ T,
+                              int P, int H, int W, int step) {
+  const int64_t hw = (int64_t)H * W;
+  const int64_t n = (int64_t)P * hw;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % W);
+    const int y = (int)((e / W) % H);
+    const int64_t p = e / hw;
+    const int32_t *sp = s + p * hw;
+    __align__(16) __nv_bfloat16 v[32];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      const float f = (yy >= 0 && yy < H && xx >= 0 && xx < W && step_of(yy, xx) < step)
+                          ? (float)__ldg(sp + (int64_t)yy * W + xx)
+                          : 0.f;
+      const __nv_bfloat16 hi = __float2bfloat16_rn(f);
+      v[2 * tap] = hi;
+      v[2 * tap + 1] = __float2bfloat16_rn(f - __bfloat162float(hi));
+    }
+#pragma unroll
+    for (int c = 18; c < 32; ++c) v[c] = __float2bfloat16_rn(0.f);
+    const int64_t pix = e - p * hw;
+#pragma unroll
+    for (int g = 0; g < 4; ++g)
+      *reinterpret_cast<uint4 *>(T + ((p * 4 + g) * hw + pix) * 8) =
+          *reinterpret_cast<const uint4 *>(v + 8 * g);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host side.
 static std::atomic<PFN_cuTensorMapEncodeTiled_v12000> g_encode{nullptr};
@@ -781,8 +789,6 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
   // residual + head: 3x3 C->C of steps 2-4, 1x1 2C->C of step 1
   PW_TC_CASE(3, 32, 32, TE_HEAD) PW_TC_CASE(3, 64, 64, TE_HEAD)
   PW_TC_CASE(1, 64, 32, TE_HEAD) PW_TC_CASE(1, 64, 64, TE_HEAD)
-  // 1x1 over l with the folded masked-input taps (steps 2-4)
-  PW_TC_CASE(1, 32, 32, TE_FOLD) PW_TC_CASE(1, 64, 64, TE_FOLD)
 #undef PW_TC_CASE
   set_last_error("no tensor-core conv for this shape");
   return PW_EUNSUPPORTED;
@@ -855,36 +861,37 @@ int Model::ensure_tc() {
     return s;
   // Steps 2-4: z = Wz [a; l] + bz with a = Wa * (m s) + ba is linear in a,
   // so z = Wz_l l + sum_tap (Wz_a Wa[:, tap]) (m s)(tap) + (Wz_a ba + bz):
-  // the tensor cores do the 1x1 over l, the epilogue the 9-tap term.
-  auto fold = [&](const std::string &ns, TcWeights::Conv *zf, float **fw) -> int {
+  // one 1x1 over l and the 9 masked neighbour values. Each value enters as
+  // two BF16 channels (high part, exact remainder) with the same weight, so
+  // integers below 2^16 reach the accumulator exactly.
+  auto fold = [&](const std::string &ns, TcWeights::Conv *zt) -> int {
     for (int k = 1; k < 4; ++k) {
       const std::string q = ns + ".s" + std::to_string(k) + ".";
       const std::vector<float> &wz = H(q + "wz"), &bz = H(q + "bz"), &wa = H(q + "wa"),
                                &ba = H(q + "ba");
-      std::vector<float> wl((size_t)C * C), bf(C), wf((size_t)9 * C);
+      const int K = C + 32;
+      std::vector<float> wk((size_t)C * K, 0.f), bf(C);
       for (int c = 0; c < C; ++c) {
         double bacc = bz[c];
         for (int j = 0; j < C; ++j) {
-          wl[(size_t)c * C + j] = wz[(size_t)c * 2 * C + C + j];
+          wk[(size_t)c * K + j] = wz[(size_t)c * 2 * C + C + j];
           bacc += (double)wz[(size_t)c * 2 * C + j] * ba[j];
         }
         bf[c] = (float)bacc;
         for (int tap = 0; tap < 9; ++tap) {
           double acc = 0.0;
           for (int j = 0; j < C; ++j) acc += (double)wz[(size_t)c * 2 * C + j] * wa[j * 9 + tap];
-          wf[(size_t)tap * C + c] = (float)acc;
+          wk[(size_t)c * K + C + 2 * tap] = (float)acc;
+          wk[(size_t)c * K + C + 2 * tap + 1] = (float)acc;
         }
       }
       int r;
-      if ((r = pack_conv(*t, zf[k - 1], wl, bf, C, C, 1, C))) return r;
-      if (cudaMalloc(&fw[k - 1], wf.size() * 4) != cudaSuccess) return PW_ENOMEM;
-      t->allocs.push_back(fw[k - 1]);
-      cudaMemcpy(fw[k - 1], wf.data(), wf.size() * 4, cudaMemcpyHostToDevice);
+      if ((r = pack_conv(*t, zt[k - 1], wk, bf, C, K, 1, C, 32))) return r;
     }
     return PW_OK;
   };
-  if ((s = fold("sb", t->sk_zf, t->sk_fw))) return s;
-  if (ll_mode == 0 && (s = fold("ll", t->lk_zf, t->lk_fw))) return s;
+  if ((s = fold("sb", t->sk_zt))) return s;
+  if (ll_mode == 0 && (s = fold("ll", t->lk_zt))) return s;
   if (ll_mode == 0 &&
       (s = set("ll", t->l0_in, t->l0_w1, t->l0_w2, t->l0_w3, t->l0_w4, t->lk_z, t->lk_c1,
                t->lk_c2)))
@@ -914,7 +921,7 @@ int64_t tc_workspace_bytes(const Geometry &g, int P, int C) {
   cmax *= P;
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
   return 1024 + al(big * 2 * C * 2) + 5 * al(big * C * 2) + al(big * 2 * C * 2) +
-         3 * al(cmax * C * 2) + al(cmax * 2 * C * 2);
+         3 * al(cmax * C * 2) + al(cmax * 2 * C * 2) + al(big * 32 * 2);
 }
 
 int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
@@ -924,11 +931,11 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
   cmax *= ws->P;
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
   // X (2C), L0 (C), L1 (C), Z (C), U (2C), V (C), Z2 (C); compact Vc, Zc,
-  // Z2c (C), U2c (2C); bf16
-  constexpr int kN = 11;
+  // Z2c (C), U2c (2C); T (32); bf16
+  constexpr int kN = 12;
   const int64_t sizes[kN] = {big * 2 * C * 2, big * C * 2,  big * C * 2,      big * C * 2,
                              big * 2 * C * 2, big * C * 2,  big * C * 2,      cmax * C * 2,
-                             cmax * C * 2,    cmax * C * 2, cmax * 2 * C * 2};
+                             cmax * C * 2,    cmax * C * 2, cmax * 2 * C * 2, big * 32 * 2};
   int64_t tot = 1024;
   for (int64_t v : sizes) tot += al(v);
   TcAct *t = new TcAct();
@@ -941,8 +948,8 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
   t->err = reinterpret_cast<int *>(b);
   cudaMemset(t->err, 0, 1024);
   int64_t o = 1024;
-  __nv_bfloat16 **dst[kN] = {&t->X,  &t->L[0], &t->L[1], &t->Z,  &t->U,  &t->V,
-                             &t->Z2, &t->Vc,   &t->Zc,   &t->Z2c, &t->U2c};
+  __nv_bfloat16 **dst[kN] = {&t->X,  &t->L[0], &t->L[1], &t->Z,   &t->U,  &t->V,
+                             &t->Z2, &t->Vc,   &t->Zc,   &t->Z2c, &t->U2c, &t->T};
   for (int i = 0; i < kN; ++i) { *dst[i] = reinterpret_cast<__nv_bfloat16 *>(b + o); o += al(sizes[i]); }
   ws->tc = t;
   return PW_OK;
@@ -1047,13 +1054,21 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     a.compact_n = n0; a.full_W = w; a.full_H = h;
     return cconv(c4, t.U2c, 2 * G, a);                             // head
   }
-  const TcWeights::Conv &zf = ll ? W.lk_zf[step - 1] : W.sk_zf[step - 1];
-  const float *fw = ll ? W.lk_fw[step - 1] : W.sk_fw[step - 1];
+  const TcWeights::Conv &zt = ll ? W.lk_zt[step - 1] : W.sk_zt[step - 1];
   const TcWeights::Conv &c1 = ll ? W.lk_c1[step - 1] : W.sk_c1[step - 1];
   const TcWeights::Conv &c2 = ll ? W.lk_c2[step - 1] : W.sk_c2[step - 1];
+  {
+    ProfScope ps(ctx, KC_SMALL_CTX, 0.0, pix * (4.0 + 64.0));
+    k_masked_taps<<<grid_for((int64_t)P * h * w), 256, 0, st>>>(Qi, t.T, P, h, w, step);
+    ctx->launches += 1;
+  }
   TcConvArgs a{};
-  a.epi = TE_FOLD; a.out = t.Z; a.out_G = G; a.fold_w = fw; a.fold_s = Qi; a.step = step;
-  if ((s = conv(zf, l, G, 0, a, 2.0 * pix * 9 * C))) return s;    // z = 1x1 l + mixed taps
+  a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
+  {
+    // z = 1x1 over [l, T]: K-blocks of 32 channels, the first C / 32 from l
+    ProfScope ps(ctx, KC_CONV1, 2.0 * pix * zt.cin * zt.cout, pix * 2.0 * (zt.cin + zt.cout));
+    if ((s = conv_tc(ctx, zt, l, G, 0, P, h, w, a, t.err, t.T, 4, 0, C / 32))) return s;
+  }
   a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
   if ((s = conv(c1, t.Z, G, 0, a, 0))) return s;                  // u = lrelu(conv3x3 z)
   a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z; a.res_G = G;
