@@ -149,6 +149,7 @@ static int check_status(pw_ctx *ctx, Workspace *ws = nullptr) {
   if (st & kStHeader) { set_last_error("stream header does not match (model, size or format)"); return PW_EINVAL; }
   if (st & kStCorrupt) { set_last_error("corrupt or truncated bitstream"); return PW_ECORRUPT; }
   if (st & kStRange) { set_last_error("value outside the coder's range"); return PW_EINVAL; }
+  if (st & kStTimeout) { set_last_error("a kernel's bounded wait expired"); return PW_ETIMEOUT; }
   return PW_OK;
 }
 
@@ -1092,6 +1093,7 @@ static int lift_stage(pw_ctx *c, const pw_model *mm, int H, int W, int lossless,
   if ((s = get_plan(c, m, g, 1, "lift", false, &pl))) return s;
   cudaStream_t st = c->stream;
   const size_t bytes = (size_t)g.plane_elems * 4;
+  PW_CUDA_TRY(cudaMemsetAsync(c->status, 0, 4, st));
   if (fwd) {
     PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.planes, in, bytes, cudaMemcpyHostToDevice, st));
     if ((s = lift_forward_planes(c, m, g, pl->ws, pl->ws.planes))) return s;
@@ -1101,7 +1103,7 @@ static int lift_stage(pw_ctx *c, const pw_model *mm, int H, int W, int lossless,
     if ((s = lift_inverse_planes(c, m, g, pl->ws, pl->ws.planes))) return s;
     PW_CUDA_TRY(cudaMemcpyAsync(out, pl->ws.planes, bytes, cudaMemcpyDeviceToHost, st));
   }
-  return finish(c);
+  return check_status(c);
 }
 
 int pw_lift_forward(pw_ctx *c, const pw_model *m, int H, int W, int lossless, const float *x,

@@ -267,6 +267,8 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
   const int P = ws.P, L = g.levels;
   cudaStream_t st = ctx->stream;
   const int rP = g.lossless ? 1 : 0, rU = g.lossless ? 2 : 0;
+  // BF16 precision class, lossy: the CNNs' middle layer on the tensor cores
+  const int tc = (ctx->precision == PW_PREC_BF16 && !g.lossless) ? 1 : 0;
   float *cur = ws.Yf;  // LL_L, plane stride h*w
   for (int lv = L; lv >= 1; --lv) {
     const int h = g.Hp >> lv, w = g.Wp >> lv;
@@ -279,7 +281,7 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
     float *X = (lv == 1) ? dst : ws.T2;
     auto colinv = [&](float *Lb, float *Hb, float *out) {
       LiftStepParams a{};
-      a.P = P; a.H = h; a.W = w; a.dir = 1;
+      a.P = P; a.H = h; a.W = w; a.dir = 1; a.tc = tc; a.status = ctx->status;
       a.src = acc(Hb, hw, w); a.other = acc(Lb, hw, w); a.out = acc(E, hw, w);
       a.copy = acc(nullptr, 0, 0); a.net = m.lift[1][1]; a.lin = LIN_U53; a.sign = -1;
       a.round = rU;
@@ -292,7 +294,7 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
     colinv(cur, LH, Lo);
     colinv(HL, HH, Hi);
     LiftStepParams a{};
-    a.P = P; a.H = 2 * h; a.W = w; a.dir = 0;
+    a.P = P; a.H = 2 * h; a.W = w; a.dir = 0; a.tc = tc; a.status = ctx->status;
     a.src = acc(Hi, 2 * hw, w); a.other = acc(Lo, 2 * hw, w); a.out = acc(E, 2 * hw, w);
     a.copy = acc(nullptr, 0, 0); a.net = m.lift[0][1]; a.lin = LIN_U53; a.sign = -1;
     a.round = rU;

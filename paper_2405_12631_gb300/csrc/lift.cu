@@ -12,10 +12,13 @@
 // spatial transform; Haar (P = s, U = s / 2) for the temporal one. Integer
 // mode (lossless) rounds P with floor(v) and U with floor(v + 1/2), which
 // makes the transform the JPEG 2000 reversible 5/3 when the CNN is zero.
+#include <cuda_bf16.h>
+
 #include <mutex>
 
 #include "pw_internal.cuh"
 #include "lift_kernels.cuh"
+#include "tc_ptx.cuh"
 
 namespace pw {
 
@@ -56,6 +59,52 @@ __device__ __forceinline__ void acc_set(const PlaneAcc &a, int p, int y, int x, 
   a.p[(int64_t)p * a.ps + (int64_t)y * a.rs + (int64_t)x * a.cs] = v;
 }
 
+// Layer 3 of the CNN (conv3x3 16 -> 1 over the 18 x 18 layer-2 region a2,
+// null when the step has no CNN), the linear part and the output of one
+// 16 x 16 tile; thread t handles output (t / 16, t % 16). in: the 22 x 22
+// input region (origin y0 - 3, x0 - 3).
+__device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int y0, int x0,
+                                            const float *in, const float *a2, const float *w3t,
+                                            const float *b3) {
+  const int t = threadIdx.x;
+  const int ly = t / LT, lx = t % LT;
+  float r_out = 0.f;
+  if (a2) {
+    float v = b3[0];
+    for (int tap = 0; tap < 9; ++tap) {
+      float xv[LF], w[LF];
+      ld16(a2 + ((ly + tap / 3) * L2 + lx + tap % 3) * LF, xv);
+      ld16(w3t + tap * LF, w);
+#pragma unroll
+      for (int ci = 0; ci < LF; ++ci) v = fmaf(w[ci], xv[ci], v);
+    }
+    r_out = v;
+  }
+  const int y = y0 + ly, x = x0 + lx;
+  if (y >= a.H || x >= a.W) return;
+  const float s0 = in[(ly + 3) * LI + lx + 3];
+  float lin;
+  if (a.lin == LIN_P53) {
+    const float s1 = a.dir == 0 ? (x + 1 < a.W ? in[(ly + 3) * LI + lx + 4] : s0)
+                                : (y + 1 < a.H ? in[(ly + 4) * LI + lx + 3] : s0);
+    lin = 0.5f * (s0 + s1);
+  } else if (a.lin == LIN_U53) {
+    const float sm = a.dir == 0 ? (x > 0 ? in[(ly + 3) * LI + lx + 2] : s0)
+                                : (y > 0 ? in[(ly + 2) * LI + lx + 3] : s0);
+    lin = 0.25f * (sm + s0);
+  } else if (a.lin == LIN_ID) {
+    lin = s0;
+  } else {  // LIN_HALF
+    lin = 0.5f * s0;
+  }
+  float v = lin + r_out;
+  if (a.round == 1) v = floorf(v);
+  else if (a.round == 2) v = floorf(v + 0.5f);
+  const float o = acc_get(a.other, p, y, x);
+  acc_set(a.out, p, y, x, a.sign > 0 ? o + v : o - v);
+  if (a.copy.p) acc_set(a.copy, p, y, x, s0);
+}
+
 __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
   extern __shared__ float smem_raw[];
   LiftSmem &S = *reinterpret_cast<LiftSmem *>(smem_raw);
@@ -83,7 +132,6 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
     if (t == 0) S.b3[0] = a.net.b3[0];
   }
   __syncthreads();
-  float r_out = 0.f;
   if (cnn) {
     // layer 1 on the 20 x 20 region (origin y0 - 2, x0 - 2)
     for (int e = t; e < L1 * L1; e += 256) {
@@ -147,44 +195,170 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
       }
     }
     __syncthreads();
-    // layer 3 on the 16 x 16 outputs
-    {
-      const int ly = t / LT, lx = t % LT;
-      float v = S.b3[0];
-      for (int tap = 0; tap < 9; ++tap) {
-        float xv[LF], w[LF];
-        ld16(S.a2 + ((ly + tap / 3) * L2 + lx + tap % 3) * LF, xv);
-        ld16(S.w3t + tap * LF, w);
+  }
+  lift_finish(a, p, y0, x0, S.in, cnn ? S.a2 : nullptr, S.w3t, S.b3);
+}
+
+// ---------------------------------------------------------------------------
+// Lifting step with the middle CNN layer (conv3x3 16 -> 16, 89 % of the
+// CNN's FLOPs) on the tensor cores: BF16 operands, FP32 accumulation in
+// tensor memory. Layers 1 and 3, the linear part and the output stay FP32.
+//
+// Layer-2 positions of the tile's 18 x 18 region are the GEMM rows, laid out
+// with a row stride of RS = 24 positions: output row m = r * RS + c. Layer 1
+// is stored with the same row stride, so tap (dy, dx) of row m reads layer-1
+// position m + dy * RS + dx: each tap is one MMA per 128-row block whose A
+// operand is the layer-1 slab shifted by a constant (columns c >= 18 are
+// padding and never read back). A: [2 channel groups][kA positions][8] BF16
+// (K-major core matrices, no swizzle); B: [tap][2][16 outputs][8].
+constexpr int kRS = 24;                   // row stride of the layer-1/2 regions
+constexpr int kMT = 4;                    // 128-row MMA blocks (18 * 24 = 432 rows)
+constexpr int kA = 576;                   // layer-1 positions kept (> 511 + 2 * 24 + 2)
+
+struct LiftTcSmem {
+  alignas(128) __nv_bfloat16 a1[2 * kA * 8];
+  alignas(128) __nv_bfloat16 w2[9 * 2 * LF * 8];
+  alignas(16) float in[LI * LI];
+  alignas(16) float a2[L2 * L2 * LF];
+  alignas(16) float w1t[9 * LF];
+  alignas(16) float w3t[9 * LF];
+  alignas(16) float b1[LF];
+  alignas(16) float b2[LF];
+  alignas(16) float b3[4];
+  alignas(8) uint64_t bar;
+  uint32_t tmem;
+};
+
+__global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
+  extern __shared__ __align__(1024) uint8_t lsm_raw[];
+  LiftTcSmem &S = *reinterpret_cast<LiftTcSmem *>(lsm_raw);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int p = blockIdx.z;
+  const int tiles_x = (a.W + LT - 1) / LT;
+  const int y0 = (blockIdx.x / tiles_x) * LT, x0 = (blockIdx.x % tiles_x) * LT;
+  constexpr uint32_t kCols = kMT * LF;    // 64 TMEM columns: 4 blocks x 16 outputs
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&S.tmem)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (t == 32) {
+    mbar_init(&S.bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int e = t; e < LI * LI; e += 256) {
+    const int yy = y0 + e / LI - 3, xx = x0 + e % LI - 3;
+    S.in[e] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? acc_get(a.src, p, yy, xx) : 0.f;
+  }
+  for (int e = t; e < LF * 9; e += 256) {
+    const int c = e / 9, tap = e % 9;  // source [c][tap]
+    S.w1t[tap * LF + c] = a.net.w1[e];
+    S.w3t[tap * LF + c] = a.net.w3[e];
+  }
+  for (int e = t; e < LF * LF * 9; e += 256) {
+    const int c = e / (LF * 9), ci = (e / 9) % LF, tap = e % 9;  // source [c][ci][tap]
+    S.w2[((tap * 2 + (ci >> 3)) * LF + c) * 8 + (ci & 7)] = __float2bfloat16_rn(a.net.w2[e]);
+  }
+  if (t < LF) { S.b1[t] = a.net.b1[t]; S.b2[t] = a.net.b2[t]; }
+  if (t == 0) S.b3[0] = a.net.b3[0];
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tbase = S.tmem;
+
+  // layer 1 on the 20 x 24 region (origin y0 - 2, x0 - 2), one position and
+  // one group of 8 channels per item; padding positions are written as 0
+  for (int it = t; it < 2 * kA; it += 256) {
+    const int pos = it >> 1, g = it & 1;
+    const int r = pos / kRS, c = pos % kRS;
+    const int yy = y0 - 2 + r, xx = x0 - 2 + c;
+    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r < L1 && c < L1 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
 #pragma unroll
-        for (int ci = 0; ci < LF; ++ci) v = fmaf(w[ci], xv[ci], v);
+      for (int k = 0; k < 8; ++k) v[k] = S.b1[8 * g + k];
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const float iv = S.in[(r + tap / 3) * LI + c + tap % 3];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = fmaf(S.w1t[tap * LF + 8 * g + k], iv, v[k]);
       }
-      r_out = v;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = tanh_fast(v[k]);
+    }
+    __align__(16) __nv_bfloat16 hb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) hb[k] = __float2bfloat16_rn(v[k]);
+    *reinterpret_cast<uint4 *>(S.a1 + ((size_t)g * kA + pos) * 8) =
+        *reinterpret_cast<const uint4 *>(hb);
+  }
+  fence_proxy_async();
+  __syncthreads();
+
+  // layer 2: 4 blocks x 9 taps MMAs (M = 128, N = 16, K = 16), one thread
+  if (t == 0) {
+    fence_after();
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(LF >> 3) << 17) |
+                           ((uint32_t)(128 >> 4) << 24);
+    const uint32_t abase = smem_u32(S.a1), bbase = smem_u32(S.w2);
+#pragma unroll
+    for (int i = 0; i < kMT; ++i) {
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const uint32_t arow = (uint32_t)(i * 128 + (tap / 3) * kRS + tap % 3);
+        const uint64_t ad = sdesc(abase + arow * 16u, kA * 16u, 128u);
+        const uint64_t bd = sdesc(bbase + (uint32_t)tap * (2 * LF * 16), LF * 16u, 128u);
+        mma_bf16(tbase + (uint32_t)(i * LF), ad, bd, idesc, tap > 0 ? 1u : 0u);
+      }
+    }
+    mma_commit(&S.bar);
+  }
+  // bounded wait for the MMAs (lane 0 of each warp, then the whole warp)
+  int ok = 1;
+  if (lane == 0) {
+    const long long t0 = clock64();
+    while (!mbar_try(&S.bar, 0))
+      if (clock64() - t0 > kWaitCycles) { ok = 0; break; }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok && lane != 0) while (!mbar_try(&S.bar, 0)) {}
+  __syncwarp();
+  fence_after();
+  if (!ok && lane == 0) atomicOr(a.status, kStTimeout);
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of blocks w / 4 and
+  // w / 4 + 2 -> tanh(acc + b2) into the 18 x 18 layer-2 region
+  if (ok) {
+    const int q = warp & 3;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = (warp >> 2) + 2 * h;
+      float v[LF];
+      tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(i * LF), v);
+      const int m = i * 128 + 32 * q + lane;
+      const int r2 = m / kRS, c2 = m % kRS;
+      if (r2 < L2 && c2 < L2) {
+        const int yy = y0 - 1 + r2, xx = x0 - 1 + c2;
+        const bool inside = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        float4 *dst = reinterpret_cast<float4 *>(S.a2 + (r2 * L2 + c2) * LF);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          dst[k] = inside ? make_float4(tanh_fast(v[4 * k] + S.b2[4 * k]),
+                                        tanh_fast(v[4 * k + 1] + S.b2[4 * k + 1]),
+                                        tanh_fast(v[4 * k + 2] + S.b2[4 * k + 2]),
+                                        tanh_fast(v[4 * k + 3] + S.b2[4 * k + 3]))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
     }
   }
-  const int ly = t / LT, lx = t % LT;
-  const int y = y0 + ly, x = x0 + lx;
-  if (y >= a.H || x >= a.W) return;
-  const float s0 = S.in[(ly + 3) * LI + lx + 3];
-  float lin;
-  if (a.lin == LIN_P53) {
-    const float s1 = a.dir == 0 ? (x + 1 < a.W ? S.in[(ly + 3) * LI + lx + 4] : s0)
-                                : (y + 1 < a.H ? S.in[(ly + 4) * LI + lx + 3] : s0);
-    lin = 0.5f * (s0 + s1);
-  } else if (a.lin == LIN_U53) {
-    const float sm = a.dir == 0 ? (x > 0 ? S.in[(ly + 3) * LI + lx + 2] : s0)
-                                : (y > 0 ? S.in[(ly + 2) * LI + lx + 3] : s0);
-    lin = 0.25f * (sm + s0);
-  } else if (a.lin == LIN_ID) {
-    lin = s0;
-  } else {  // LIN_HALF
-    lin = 0.5f * s0;
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) {
+    __syncwarp();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols));
   }
-  float v = lin + r_out;
-  if (a.round == 1) v = floorf(v);
-  else if (a.round == 2) v = floorf(v + 0.5f);
-  const float o = acc_get(a.other, p, y, x);
-  acc_set(a.out, p, y, x, a.sign > 0 ? o + v : o - v);
-  if (a.copy.p) acc_set(a.copy, p, y, x, s0);
+  if (ok) lift_finish(a, p, y0, x0, S.in, S.a2, S.w3t, S.b3);
 }
 
 // Component planes [B][nc][Hp][Wp] -> interleaved samples (crop, inverse
@@ -284,6 +458,17 @@ static int grid_for(int64_t n) {
 }
 
 void launch_lift_step(const LiftStepParams &a, cudaStream_t st) {
+  if (a.tc && a.net.w1 && a.round == 0) {
+    static std::once_flag attr_tc;
+    std::call_once(attr_tc, [] {
+      cudaFuncSetAttribute(k_lift_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)sizeof(LiftTcSmem) + 1024);
+    });
+    const int tiles = ((a.H + LT - 1) / LT) * ((a.W + LT - 1) / LT);
+    dim3 grid(tiles, 1, a.P);
+    k_lift_tc<<<grid, 256, sizeof(LiftTcSmem) + 1024, st>>>(a);
+    return;
+  }
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(k_lift_step, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -26,6 +26,9 @@ struct LiftStepParams {
   int lin, dir;                    // dir 0: along x (rows), 1: along y (columns)
   int sign;                        // out = other + sign * v
   int round;                       // 0 none, 1 floor(v), 2 floor(v + 1/2)
+  int tc;                          // 1: middle CNN layer on the tensor cores
+                                   // (BF16 operands; round must be 0)
+  uint32_t *status;                // kStTimeout is set here (tc only)
 };
 
 void launch_lift_step(const LiftStepParams &a, cudaStream_t st);

@@ -27,7 +27,8 @@ constexpr int kMaxEscBits = 30;        // Exp-Golomb prefix length limit
 enum : uint32_t {
   kStCorrupt = 1u,     // rANS stream inconsistent (overrun / bad final state)
   kStHeader = 2u,      // stream header does not match the decode plan
-  kStRange = 4u        // a value fell outside its representable range
+  kStRange = 4u,       // a value fell outside its representable range
+  kStTimeout = 8u      // a kernel's bounded wait expired
 };
 
 // ---------------------------------------------------------------------------
