@@ -396,8 +396,11 @@ def run_gpu(args):
     if dom:
         hbm = float(peaks.get("hbm_gbs", 6800.0))
         if dom["name"].startswith("ctx") or dom["name"] == "lift_step":
-            if args.precision == "bf16" and dom["name"].startswith("ctx"):
+            if args.precision in ("bf16", "fp8") and dom["name"].startswith("ctx"):
                 tpeak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+                if args.precision == "fp8" and dom["name"] in ("ctx_conv3x3",
+                                                               "ctx_lstm_gates_conv3x3"):
+                    tpeak *= 2.0   # E4M3 convs: bf16 peak x the nominal fp8/bf16 ratio (2)
                 cbound = "tensor"
             else:
                 # FP32 SIMT: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock
@@ -428,7 +431,8 @@ def run_gpu(args):
         "metric": "decoded MPix/s", "value": value, "unit": "MPix/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16" if args.precision == "bf16" else "f32", "data": "synthetic",
+        "dtype": {"bf16": "bf16", "fp8": "fp8-e4m3+bf16", "fp32": "f32"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": WORKLOAD if BATCH == 24 else WORKLOAD.replace("24", str(BATCH), 1),
                    "global_batch": BATCH * world, "image": "768x512 RGB",
                    "context_channels": 64, "levels": 4, "ll_mode": "four-step",
@@ -470,7 +474,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default=os.environ.get("PW_BENCH_PRECISION", "bf16"),
-                    choices=["fp32", "bf16"])
+                    choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="images per step (24 = the benchmark workload; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -91,7 +91,9 @@ static int get_plan(pw_ctx *ctx, Model &m, const Geometry &g, int B, const char 
   p->key = key;
   p->g = g;
   p->B = B;
-  int s = p->ws.alloc(g, B * g.nc, m.C, params, ctx->precision == PW_PREC_BF16);
+  int s = m.prepare(ctx->precision);
+  if (s != PW_OK) return s;
+  s = p->ws.alloc(g, B * g.nc, m.C, params, ctx->precision);
   if (s != PW_OK) return s;
   if (!strcmp(kind, "dec") || !strcmp(kind, "sym")) {
     // decode descriptor layout: group blocks of P x count
@@ -136,7 +138,7 @@ void drop_plans(pw_ctx *ctx) {
 
 static int check_status(pw_ctx *ctx, Workspace *ws = nullptr) {
   if (launch_failed()) { launch_failed() = false; return PW_EUNSUPPORTED; }
-  if (ws && ctx->precision == PW_PREC_BF16) {
+  if (ws && ctx->precision != PW_PREC_FP32) {
     cudaStreamSynchronize(ctx->stream);
     if (tc_error(*ws)) { set_last_error("a tensor-core kernel's bounded wait expired"); return PW_ETIMEOUT; }
   }
@@ -167,7 +169,7 @@ static ArWeightsDev ar_weights(const Model &m) {
 }
 
 static uint16_t prec_flags(pw_ctx *ctx) {
-  return (uint16_t)((ctx->precision == PW_PREC_BF16 ? 1 : 0) << FLAG_PREC_SHIFT);
+  return (uint16_t)(ctx->precision << FLAG_PREC_SHIFT);
 }
 
 // --------------------------------------------------------------------------
@@ -184,7 +186,7 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *co
   PW_CUDA_TRY(cudaMemcpyAsync(pl.d_ptrs.p, hs, B * 8, cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemcpyAsync(pl.d_lens.p, hs + B, B * 8, cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemsetAsync(ctx->status, 0, 4, st));
-  if (ctx->precision == PW_PREC_BF16) tc_error_reset(pl.ws, st);
+  if (ctx->precision != PW_PREC_FP32) tc_error_reset(pl.ws, st);
   ParseExpect ex{};
   ex.width = h0.width; ex.height = h0.height; ex.ncomp = g.nc; ex.levels = g.levels;
   ex.bitdepth = g.bitdepth; ex.colour = g.colour; ex.flags = h0.flags; ex.chunk = g.chunk;
@@ -256,7 +258,7 @@ static int check_header_model(pw_ctx *ctx, const Model &m, const StreamHeader &h
   if (h.levels != m.levels || ((h.flags & FLAG_LL_AR) ? 1 : 0) != m.ll_mode) {
     set_last_error("stream levels / LL mode do not match the model"); return PW_EINVAL;
   }
-  if (((h.flags >> FLAG_PREC_SHIFT) & 3) != (ctx->precision == PW_PREC_BF16 ? 1 : 0)) {
+  if (((h.flags >> FLAG_PREC_SHIFT) & 3) != ctx->precision) {
     set_last_error("stream was encoded with another precision class"); return PW_EINVAL;
   }
   if (h.T != kT || h.log2m != kLogM || h.lanes != kMaxLanes || h.chunk_symbols == 0 ||
@@ -401,7 +403,7 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
   const int P = B * g.nc;
   cudaStream_t st = ctx->stream;
   Workspace &ws = pl.ws;
-  if (ctx->precision == PW_PREC_BF16) tc_error_reset(ws, st);
+  if (ctx->precision != PW_PREC_FP32) tc_error_reset(ws, st);
   launch_cdf_bank(ctx->bank, st);
   bump(ctx);
   for (int sb = 0; sb < g.nsb; ++sb) {
@@ -631,7 +633,8 @@ const char *pw_last_error(void) { return g_last_error.c_str(); }
 void pw_free(void *p) { std::free(p); }
 
 int pw_ctx_create(int device, void *stream, int precision, pw_ctx **out) {
-  if (!out || (precision != PW_PREC_FP32 && precision != PW_PREC_BF16)) {
+  if (!out || (precision != PW_PREC_FP32 && precision != PW_PREC_BF16 &&
+               precision != PW_PREC_FP8)) {
     set_last_error("bad precision"); return PW_EINVAL;
   }
   int ndev = 0;
@@ -703,7 +706,7 @@ int pw_model_load(pw_ctx *c, const void *blob, size_t n, pw_model **out) {
   if (!c || !blob || !out) { set_last_error("bad arguments"); return PW_EINVAL; }
   pw_model *m = new pw_model();
   int s = m->m.load(c, blob, n);
-  if (s == PW_OK && c->precision == PW_PREC_BF16) s = m->m.ensure_tc();
+  if (s == PW_OK) s = m->m.prepare(c->precision);
   if (s != PW_OK) { delete m; return s; }
   *out = m;
   return PW_OK;
@@ -1055,7 +1058,7 @@ int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t
   if ((s = get_plan(c, m, g, 1, "par", true, &pl))) return s;
   cudaStream_t st = c->stream;
   PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.Q, q, g.plane_elems * 4, cudaMemcpyHostToDevice, st));
-  if (c->precision == PW_PREC_BF16) tc_error_reset(pl->ws, st);
+  if (c->precision != PW_PREC_FP32) tc_error_reset(pl->ws, st);
   for (int sb = 0; sb < g.nsb; ++sb) {
     if (sb == 0 && m.ll_mode == 1) {
       if ((s = launch_ll_ar_params(pl->ws.Q, 1, g.sh[0], g.sw[0], m.C, ar_weights(m), pl->ws.idx,
@@ -1071,7 +1074,7 @@ int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t
   PW_CUDA_TRY(cudaMemcpyAsync(mu, pl->ws.mu, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
   PW_CUDA_TRY(cudaMemcpyAsync(sigma, pl->ws.sg, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
   if ((s = finish(c))) return s;
-  if (c->precision == PW_PREC_BF16 && tc_error(pl->ws)) {
+  if (c->precision != PW_PREC_FP32 && tc_error(pl->ws)) {
     set_last_error("a tensor-core kernel's bounded wait expired");
     return PW_ETIMEOUT;
   }

@@ -69,7 +69,8 @@ void Geometry::build(int H_, int W_, int nc_, int levels_, int colour_, int bitd
 }
 
 // ---------------------------------------------------------------------------
-int Workspace::alloc(const Geometry &g, int P_, int C, bool params, bool bf16) {
+int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec) {
+  const bool bf16 = prec != PW_PREC_FP32;
   release();
   P = P_;
   const int64_t pe = (int64_t)P * g.Hp * g.Wp;
@@ -105,19 +106,20 @@ int Workspace::alloc(const Geometry &g, int P_, int C, bool params, bool bf16) {
   int64_t o = 0;
   for (auto &p : parts) { *p.first = base + o; o += p.second; }
   if (bf16) {
-    int s = tc_workspace_alloc(this, g, C);
+    int s = tc_workspace_alloc(this, g, C, prec == PW_PREC_FP8);
     if (s != PW_OK) return s;
   }
   return PW_OK;
 }
 
-int64_t Workspace::estimate(const Geometry &g, int P, int C, bool params, bool bf16) {
+int64_t Workspace::estimate(const Geometry &g, int P, int C, bool params, int prec) {
+  const bool bf16 = prec != PW_PREC_FP32;
   const int64_t pe = (int64_t)P * g.Hp * g.Wp;
   const int64_t big = (int64_t)P * g.sh.back() * g.sw.back();
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
   int64_t tot = 7 * al(pe * 4) + 2 * al(big * C * 4);
   if (!bf16) tot += 3 * al(big * 2 * C * 4) + 3 * al(big * C * 4);
-  else tot += tc_workspace_bytes(g, P, C);
+  else tot += tc_workspace_bytes(g, P, C, prec == PW_PREC_FP8);
   if (params) tot += 2 * al(pe * 4);
   return tot;
 }
@@ -140,7 +142,7 @@ int run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb) {
   if (first) ws.lstm_cur = 0;
   const int cur = ws.lstm_cur;
   const int32_t *sprev = ws.Q + (int64_t)P * g.soff[sb - 1];
-  if (ctx->precision == PW_PREC_BF16) {
+  if (ctx->precision != PW_PREC_FP32) {
     int s = tc_run_lstm(ctx, m, g, ws, sb, sprev, up, first, cur);
     ws.lstm_cur = cur ^ 1;
     return s;
@@ -176,7 +178,7 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
   const int64_t nk = step_count(h, w, step);
   float *mu = ws.mu ? ws.mu + (int64_t)P * g.soff[sb] : nullptr;
   float *sgp = ws.sg ? ws.sg + (int64_t)P * g.soff[sb] : nullptr;
-  if (ctx->precision == PW_PREC_BF16)
+  if (ctx->precision != PW_PREC_FP32)
     return tc_run_step(ctx, m, g, ws, sb, step, n, Qi, idx, nk, mu, sgp);
   cudaStream_t st = ctx->stream;
   if (sb == 0 && step == 0) {
@@ -267,8 +269,8 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
   const int P = ws.P, L = g.levels;
   cudaStream_t st = ctx->stream;
   const int rP = g.lossless ? 1 : 0, rU = g.lossless ? 2 : 0;
-  // BF16 precision class, lossy: the CNNs' middle layer on the tensor cores
-  const int tc = (ctx->precision == PW_PREC_BF16 && !g.lossless) ? 1 : 0;
+  // BF16 / FP8 precision class, lossy: the CNNs' middle layer on the tensor cores
+  const int tc = (ctx->precision != PW_PREC_FP32 && !g.lossless) ? 1 : 0;
   float *cur = ws.Yf;  // LL_L, plane stride h*w
   for (int lv = L; lv >= 1; --lv) {
     const int h = g.Hp >> lv, w = g.Wp >> lv;

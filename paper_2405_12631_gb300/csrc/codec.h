@@ -3,6 +3,7 @@
 
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -43,8 +44,12 @@ struct Model {
   float *ar_w5 = nullptr, *ar_b5 = nullptr, *ar_w1 = nullptr, *ar_b1 = nullptr,
         *ar_wh = nullptr, *ar_bh = nullptr;
   TcWeights *tc = nullptr;
+  std::mutex mu;     // guards the lazy tensor-core weight builds
   int load(pw_ctx *c, const void *blob, size_t n);
   int ensure_tc();   // builds tc on first use (BF16 contexts)
+  int ensure_fp8();  // adds the E4M3 convolutions to tc (FP8 contexts)
+  // weights a context of this precision needs (thread-safe)
+  int prepare(int precision);
   void free_tc();
   ~Model();
 };
@@ -104,11 +109,12 @@ struct Workspace {
   float *T0 = nullptr, *T1 = nullptr, *T2 = nullptr;  // lifting temporaries
   float *planes = nullptr;     // component planes [P][Hp][Wp]
   float *mu = nullptr, *sg = nullptr;  // optional parameter outputs [P][Hp*Wp]
-  void *tc = nullptr;          // BF16 activations (tensor-core path)
+  void *tc = nullptr;          // BF16 / FP8 activations (tensor-core path)
   int lstm_cur = 0;            // which Cst holds the current cell state
-  int alloc(const Geometry &g, int P, int C, bool params, bool bf16);
+  // prec: the context's pw_precision (tensor-core buffers unless FP32)
+  int alloc(const Geometry &g, int P, int C, bool params, int prec);
   // upper bound of the device bytes alloc() takes for these arguments
-  static int64_t estimate(const Geometry &g, int P, int C, bool params, bool bf16);
+  static int64_t estimate(const Geometry &g, int P, int C, bool params, int prec);
   void release();
   ~Workspace() { release(); }
 };

@@ -21,8 +21,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 
@@ -35,9 +37,11 @@ namespace pw {
 struct TcWeights {
   // per conv: packed BF16 weights [nb][kblock][tap][kb/8][ncta][8] + FP32 bias
   struct Conv {
-    __nv_bfloat16 *w = nullptr;
+    __nv_bfloat16 *w = nullptr;   // BF16 weights, or (f8) E4M3 bytes in the same order
     float *b = nullptr;
+    float *sw = nullptr;          // f8: per-output-column scale of the accumulator
     int cin = 0, cout = 0, ks = 1, kb = 64, ncta = 64, nb = 1;
+    bool f8 = false;
   };
   Conv gates;
   Conv s0_in, s0_w1, s0_w2, s0_w3, s0_w4;        // sb set, step 0
@@ -49,6 +53,15 @@ struct TcWeights {
   // split into a BF16 high and low part, then zero padding)]; the bias
   // includes the folded bias
   Conv sk_zt[3], lk_zt[3];
+  // FP8 precision: E4M3 copies of the 3x3 convolutions (gates, steps 2-4
+  // residual blocks) with the input channels' static scales folded in, and
+  // the scales (value * scale = stored E4M3 value) of the FP8 activations:
+  // e (ConvLSTM input conv), z (residual-block input, per step), u (hidden
+  // layer, per step) and h (l_i, fixed 256 since |h| < 1)
+  bool has_f8 = false;
+  Conv gates8, sk_c1_8[3], sk_c2_8[3], lk_c1_8[3], lk_c2_8[3];
+  float *e_scale = nullptr, *h_scale = nullptr;
+  float *sk_z_scale[3] = {}, *sk_u_scale[3] = {}, *lk_z_scale[3] = {}, *lk_u_scale[3] = {};
   std::vector<void *> allocs;
 };
 
@@ -65,6 +78,10 @@ struct TcAct {  // BF16 activations in [P][G][H][W][8]
   __nv_bfloat16 *Vc = nullptr, *Zc = nullptr, *Z2c = nullptr, *U2c = nullptr;
   // T: masked neighbour values of steps 2-4 (32 channels, see TcWeights)
   __nv_bfloat16 *T = nullptr;
+  // FP8 precision: E4M3 activations [P][G16][H][W][16]: X8 = [e, up(h)]
+  // (2C), L8[2] = l_i (C, ping-pong like L), Z8 / U8 = residual-block input
+  // and hidden layer (C)
+  uint8_t *X8 = nullptr, *L8[2] = {nullptr, nullptr}, *Z8 = nullptr, *U8 = nullptr;
   int *err = nullptr;
   void *base = nullptr;
 };
@@ -104,6 +121,13 @@ struct TcConvArgs {
   // pair): compact_n = number of step positions (0: full-plane layout),
   // full_W = width of the subband (for the mu / sigma planes)
   int compact_n, full_W, full_H;
+  // FP8 (E4M3) operands: per-output-column scale applied to the accumulator
+  // (acc * w_scale[n] + bias[n]); optional second output in FP8, blocked
+  // [P][G16][H][W][16], value = output * out8_scale[channel]
+  const float *w_scale;
+  uint8_t *out8;
+  int out8_G16;
+  const float *out8_scale;
   int *err;
 };
 
@@ -130,11 +154,35 @@ __device__ __forceinline__ void load_bf16x8(const __nv_bfloat16 *p, float *v) {
   }
 }
 
+// 16 floats -> 16 E4M3 bytes (round to nearest, saturating), one 16-byte store
+__device__ __forceinline__ void store_fp8x16(uint8_t *p, const float *v) {
+  uint32_t w[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i], v[4 * i + 1]),
+                                                 __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(v[4 * i + 2], v[4 * i + 3]),
+                                                 __NV_SATFINITE, __NV_E4M3);
+    w[i] = lo | (hi << 16);
+  }
+  *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+__device__ __forceinline__ void mma_fp8(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                        uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
 constexpr int kEpiWarps = 8;                    // two per TMEM lane quadrant
 constexpr int kConvThreads = 64 + 32 * kEpiWarps;
 constexpr int kAcc = 4;                         // TMEM accumulator buffers
 
-template <int KS, int KB, int NCTA, int EPI>
+// KB: input channels per K-block; F8: E4M3 operands (kind::f8f6f4, 16
+// channels per 16-byte core-matrix row) instead of BF16 (8 per row).
+template <int KS, int KB, int NCTA, int EPI, bool F8>
 __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap,
                                                     const __grid_constant__ CUtensorMap tmap1,
                                                     const TcConvArgs a) {
@@ -175,6 +223,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   constexpr int taps = KS * KS;
   constexpr int R = KS / 2;
   constexpr int HX = kTileW + 2 * R, HY = kTileH + 2 * R;   // halo tile
+  constexpr int EPG = F8 ? 16 : 8;          // channels per 16-byte group
+  constexpr int GPK = KB / EPG;             // groups per K-block
+  constexpr int KSTEPS = GPK / 2;           // MMAs per tap (32 bytes of K each)
 
   if (warp == 0 && lane == 0) {
     // ---- producer: weights once, then halo K-blocks ----------------------
@@ -198,11 +249,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         // elements = 16 bytes, also when negative at the left border)
         if (kbi < a.nkb0)
           tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage],
-                      (tx * kTileW - R) * 8, ty * kTileH - R, a.in_goff + kbi * (KB / 8), p);
+                      (tx * kTileW - R) * EPG, ty * kTileH - R, a.in_goff + kbi * GPK, p);
         else
           tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap1, &full[stage],
-                      (tx * kTileW - R) * 8, ty * kTileH - R,
-                      a.in1_goff + (kbi - a.nkb0) * (KB / 8), p);
+                      (tx * kTileW - R) * EPG, ty * kTileH - R,
+                      a.in1_goff + (kbi - a.nkb0) * GPK, p);
         ++issued;
         if (++stage == a.stages) { stage = 0; phase ^= 1; }
       }
@@ -222,10 +273,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     // All descriptor offsets are compile-time constants: one K-block is
     // taps x KB/16 MMAs whose descriptors differ from the block's base
     // descriptors by fixed amounts (addresses enter descriptors >> 4).
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NCTA >> 3) << 17) |
+    // instruction descriptor: FP32 accumulate; A/B format BF16 (1) for
+    // kind::f16, E4M3 (0) for kind::f8f6f4; K-major; N, M = 128
+    constexpr uint32_t fmt = F8 ? 0u : 1u;
+    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NCTA >> 3) << 17) |
                            ((uint32_t)(128 >> 4) << 24);
     constexpr uint32_t slab = (uint32_t)HX * HY * 16u;
-    constexpr uint32_t wblock = (uint32_t)taps * (KB / 8) * NCTA * 16u;  // bytes per K-block
+    constexpr uint32_t wblock = (uint32_t)taps * GPK * NCTA * 16u;  // bytes per K-block
     bool ok = mbar_wait(wbar, 0, s_abort);
     int stage = 0, acc = 0;
     uint32_t phase = 0, aphase = 0;
@@ -242,10 +296,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 #pragma unroll
         for (int tap = 0; tap < taps; ++tap) {
 #pragma unroll
-          for (int s = 0; s < KB / 16; ++s) {
+          for (int s = 0; s < KSTEPS; ++s) {
             const uint32_t aoff = ((uint32_t)(2 * s) * slab + (uint32_t)((tap / KS) * HX + tap % KS) * 16u) >> 4;
-            const uint32_t boff = ((uint32_t)(tap * (KB / 8) + 2 * s) * (NCTA * 16u)) >> 4;
-            mma_bf16(d, a0 + aoff, b0 + boff, idesc, accum);
+            const uint32_t boff = ((uint32_t)(tap * GPK + 2 * s) * (NCTA * 16u)) >> 4;
+            if (F8) mma_fp8(d, a0 + aoff, b0 + boff, idesc, accum);
+            else mma_bf16(d, a0 + aoff, b0 + boff, idesc, accum);
             accum = 1;
           }
         }
@@ -324,8 +379,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       if (++acc == kAcc) { acc = 0; aphase ^= 1; }
       if (!work) continue;
 
+      if (F8) {
 #pragma unroll
-      for (int j = 0; j < NH; ++j) v[j] += a.bias[n0 + j];
+        for (int j = 0; j < NH; ++j) v[j] = fmaf(v[j], a.w_scale[n0 + j], a.bias[n0 + j]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < NH; ++j) v[j] += a.bias[n0 + j];
+      }
       if (!valid) continue;
       if (EPI == TE_STORE) {
 #pragma unroll
@@ -341,7 +401,17 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[8 * g + e] = lrelu_f(v[8 * g + e]);
           }
-          store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + gg) * hw + pix) * 8, v + 8 * g);
+          if (a.out)
+            store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + gg) * hw + pix) * 8, v + 8 * g);
+        }
+        if (NH % 16 == 0 && a.out8) {
+#pragma unroll
+          for (int g = 0; g < NH / 16; ++g) {
+            float f[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) f[e] = v[16 * g + e] * a.out8_scale[n0 + 16 * g + e];
+            store_fp8x16(a.out8 + (((int64_t)p * a.out8_G16 + (n0 >> 4) + g) * hw + pix) * 16, f);
+          }
         }
       } else if (EPI == TE_LSTM) {
         // column 4 * ch + gate (i, f, o, g) within the CTA's N block
@@ -361,6 +431,15 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         for (int g = 0; g < NH / 32; ++g)
           store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (ch0 >> 3) + g) * hw + pix) * 8,
                        hv + 8 * g);
+        if (NH % 64 == 0 && a.out8) {
+#pragma unroll
+          for (int g = 0; g < NH / 64; ++g) {
+            float f[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) f[e] = hv[16 * g + e] * a.out8_scale[ch0 + 16 * g + e];
+            store_fp8x16(a.out8 + (((int64_t)p * a.out8_G16 + (ch0 >> 4) + g) * hw + pix) * 16, f);
+          }
+        }
       } else {  // TE_HEAD: z' = res + acc + b over all C columns, then 1x1(C->2)
         if (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step) {
           float mu = a.bh[0], rho = a.bh[1];
@@ -456,6 +535,57 @@ __global__ void k_lstm_in_bf16(const int32_t *__restrict__ s_prev,
                                (int64_t)(y >> up) * Wp + (x >> up)) * 8,
                       hv);
         store_bf16x8(X + (((int64_t)p * 2 * G + G + g) * hw + pix) * 8, hv);
+      }
+    }
+  }
+}
+
+// FP8 precision: X8[:, 0:C] = E4M3((conv3x3(1->C)(up(s_prev)) + be) *
+// e_scale) and, when copy_h is set, X8[:, C:2C] = up(h8_prev) (E4M3 l_i of
+// the previous subband, copied as bytes; zero when first). Layout
+// [P][G16][H][W][16].
+__global__ void k_lstm_in_fp8(const int32_t *__restrict__ s_prev,
+                              const uint8_t *__restrict__ h8prev, const float *__restrict__ we,
+                              const float *__restrict__ be, const float *__restrict__ e_scale,
+                              uint8_t *__restrict__ X8, int P, int H, int W, int C, int up,
+                              int copy_h, int first) {
+  const int G16 = C / 16;
+  const int64_t n = (int64_t)P * H * W;
+  const int Hp = H >> up, Wp = W >> up;
+  const int64_t hw = (int64_t)H * W;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(e % W);
+    const int y = (int)((e / W) % H);
+    const int p = (int)(e / hw);
+    const int32_t *sp = s_prev + (int64_t)p * Hp * Wp;
+    float nb[9];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      nb[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    ? (float)sp[(int64_t)(yy >> up) * Wp + (xx >> up)]
+                    : 0.f;
+    }
+    const int64_t pix = (int64_t)y * W + x;
+    for (int g = 0; g < G16; ++g) {
+      float v[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int c = 16 * g + k;
+        float s = __ldg(be + c);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) s = fmaf(__ldg(we + c * 9 + tap), nb[tap], s);
+        v[k] = s * __ldg(e_scale + c);
+      }
+      store_fp8x16(X8 + (((int64_t)p * 2 * G16 + g) * hw + pix) * 16, v);
+      if (copy_h) {
+        uint4 hv = make_uint4(0u, 0u, 0u, 0u);
+        if (!first)
+          hv = *reinterpret_cast<const uint4 *>(
+              h8prev + (((int64_t)p * G16 + g) * ((int64_t)Hp * Wp) +
+                        (int64_t)(y >> up) * Wp + (x >> up)) * 16);
+        *reinterpret_cast<uint4 *>(X8 + (((int64_t)p * 2 * G16 + G16 + g) * hw + pix) * 16) = hv;
       }
     }
   }
@@ -582,16 +712,20 @@ static int get_encoder() {
 // Tensor map over a blocked BF16 tensor [P][G][H][W][8], viewed as 4-D
 // (W * 8 elements, H, G, P) so that each box row is one contiguous run of
 // box_x * 16 bytes; box = one K-block halo tile.
-static int make_map(CUtensorMap *map, const __nv_bfloat16 *base, int P, int G, int H, int W,
-                    int box_x, int box_y, int box_g) {
+// With f8 the tensor holds E4M3 bytes [P][G][H][W][16] (G = channels / 16)
+// and the map's elements are bytes; the byte geometry is the same.
+static int make_map(CUtensorMap *map, const void *base, int P, int G, int H, int W,
+                    int box_x, int box_y, int box_g, bool f8 = false) {
   int s = get_encoder();
   if (s) return s;
-  cuuint64_t dims[4] = {(cuuint64_t)W * 8, (cuuint64_t)H, (cuuint64_t)G, (cuuint64_t)P};
+  const cuuint64_t epg = f8 ? 16 : 8;
+  cuuint64_t dims[4] = {(cuuint64_t)W * epg, (cuuint64_t)H, (cuuint64_t)G, (cuuint64_t)P};
   cuuint64_t strides[3] = {(cuuint64_t)W * 16, (cuuint64_t)H * W * 16,
                            (cuuint64_t)G * H * W * 16};
-  cuuint32_t box[4] = {(cuuint32_t)box_x * 8, (cuuint32_t)box_y, (cuuint32_t)box_g, 1};
+  cuuint32_t box[4] = {(cuuint32_t)(box_x * epg), (cuuint32_t)box_y, (cuuint32_t)box_g, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
-  CUresult r = g_encode.load()(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)base, dims, strides, box,
+  CUresult r = g_encode.load()(map, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                        4, (void *)base, dims, strides, box,
                         es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -606,9 +740,11 @@ static std::atomic<int> g_num_sms{0};
 // Launch one tensor-core convolution.
 // in / in_G / in_goff: the input tensor of the first nkb0 K-blocks (all of
 // them when in1 is null); in1 / in1_G: the input of the remaining K-blocks.
-static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *in, int in_G,
+// in_G / in1_G / goffs count 16-byte channel groups (8 BF16 or 16 E4M3
+// channels; cv.f8 selects the operand type).
+static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int in_G,
                    int in_goff, int P, int H, int W, TcConvArgs a, int *err,
-                   const __nv_bfloat16 *in1 = nullptr, int in1_G = 0, int in1_goff = 0,
+                   const void *in1 = nullptr, int in1_G = 0, int in1_goff = 0,
                    int nkb0 = -1) {
   if (!g_num_sms.load()) {
     int dev = 0, n = 0;
@@ -622,9 +758,10 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
   a.halo_x = kTileW + 2 * R; a.halo_y = kTileH + 2 * R;
   a.tiles_x = (W + kTileW - 1) / kTileW; a.tiles_y = (H + kTileH - 1) / kTileH;
   a.tiles = P * a.tiles_x * a.tiles_y;
-  a.stage_bytes = (uint32_t)a.halo_x * a.halo_y * cv.kb * 2;
-  a.w_bytes = (uint32_t)(cv.ks * cv.ks) * cv.cin * cv.ncta * 2;
-  a.wt = cv.w; a.bias = cv.b; a.err = err;
+  const int esz = cv.f8 ? 1 : 2, epg = cv.f8 ? 16 : 8;
+  a.stage_bytes = (uint32_t)a.halo_x * a.halo_y * cv.kb * esz;
+  a.w_bytes = (uint32_t)(cv.ks * cv.ks) * cv.cin * cv.ncta * esz;
+  a.wt = cv.w; a.bias = cv.b; a.w_scale = cv.sw; a.err = err;
   const size_t fixed = 1024 + (a.w_bytes + 1023) / 1024 * 1024;
   const size_t maxsm = 227 * 1024;
   int stages = (int)((maxsm - fixed) / a.stage_bytes);
@@ -633,13 +770,14 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
   a.stages = stages;
   const size_t smem = fixed + (size_t)stages * a.stage_bytes;
   CUtensorMap map, map1;
-  int s = make_map(&map, in, P, in_G, H, W, a.halo_x, a.halo_y, cv.kb / 8);
+  int s = make_map(&map, in, P, in_G, H, W, a.halo_x, a.halo_y, cv.kb / epg, cv.f8);
   if (s) return s;
   a.nkb0 = a.nkb;
   a.in1_goff = in1_goff;
   if (in1) {
     a.nkb0 = nkb0;
-    if ((s = make_map(&map1, in1, P, in1_G, H, W, a.halo_x, a.halo_y, cv.kb / 8))) return s;
+    if ((s = make_map(&map1, in1, P, in1_G, H, W, a.halo_x, a.halo_y, cv.kb / epg, cv.f8)))
+      return s;
   } else {
     map1 = map;
   }
@@ -648,27 +786,33 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const __nv_bfloat16 *
   if (per_nb > a.tiles) per_nb = a.tiles;
   const int grid = per_nb * cv.nb;
   cudaStream_t st = ctx->stream;
-#define PW_TC_CASE(KS_, KB_, N_, E_)                                                        \
-  if (cv.ks == KS_ && cv.kb == KB_ && cv.ncta == N_ && a.epi == E_) {                       \
+#define PW_TC_CASE(KS_, KB_, N_, E_, F8_)                                                   \
+  if (cv.ks == KS_ && cv.kb == KB_ && cv.ncta == N_ && a.epi == E_ && cv.f8 == F8_) {       \
     static std::once_flag attr;                                                             \
     std::call_once(attr, [&] {                                                              \
-      cudaFuncSetAttribute(k_conv_tc<KS_, KB_, N_, E_>,                                     \
+      cudaFuncSetAttribute(k_conv_tc<KS_, KB_, N_, E_, F8_>,                                \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);        \
     });                                                                                     \
-    k_conv_tc<KS_, KB_, N_, E_><<<grid, kConvThreads, smem, st>>>(map, map1, a);            \
+    k_conv_tc<KS_, KB_, N_, E_, F8_><<<grid, kConvThreads, smem, st>>>(map, map1, a);       \
     ctx->launches += 1;                                                                     \
     return PW_OK;                                                                           \
   }
-  // plain stores (all shapes the stage entry accepts)
-  PW_TC_CASE(1, 32, 32, TE_STORE) PW_TC_CASE(1, 32, 64, TE_STORE) PW_TC_CASE(1, 32, 128, TE_STORE)
-  PW_TC_CASE(1, 64, 32, TE_STORE) PW_TC_CASE(1, 64, 64, TE_STORE) PW_TC_CASE(1, 64, 128, TE_STORE)
-  PW_TC_CASE(3, 32, 32, TE_STORE) PW_TC_CASE(3, 32, 64, TE_STORE) PW_TC_CASE(3, 32, 128, TE_STORE)
-  PW_TC_CASE(3, 64, 32, TE_STORE) PW_TC_CASE(3, 64, 64, TE_STORE) PW_TC_CASE(3, 64, 128, TE_STORE)
+  // BF16 plain stores (all shapes the stage entry accepts)
+  PW_TC_CASE(1, 32, 32, TE_STORE, false) PW_TC_CASE(1, 32, 64, TE_STORE, false)
+  PW_TC_CASE(1, 32, 128, TE_STORE, false) PW_TC_CASE(1, 64, 32, TE_STORE, false)
+  PW_TC_CASE(1, 64, 64, TE_STORE, false) PW_TC_CASE(1, 64, 128, TE_STORE, false)
+  PW_TC_CASE(3, 32, 32, TE_STORE, false) PW_TC_CASE(3, 32, 64, TE_STORE, false)
+  PW_TC_CASE(3, 32, 128, TE_STORE, false) PW_TC_CASE(3, 64, 32, TE_STORE, false)
+  PW_TC_CASE(3, 64, 64, TE_STORE, false) PW_TC_CASE(3, 64, 128, TE_STORE, false)
   // ConvLSTM gates (K-block = C channels)
-  PW_TC_CASE(3, 32, 64, TE_LSTM) PW_TC_CASE(3, 64, 64, TE_LSTM)
+  PW_TC_CASE(3, 32, 64, TE_LSTM, false) PW_TC_CASE(3, 64, 64, TE_LSTM, false)
   // residual + head: 3x3 C->C of steps 2-4, 1x1 2C->C of step 1
-  PW_TC_CASE(3, 32, 32, TE_HEAD) PW_TC_CASE(3, 64, 64, TE_HEAD)
-  PW_TC_CASE(1, 64, 32, TE_HEAD) PW_TC_CASE(1, 64, 64, TE_HEAD)
+  PW_TC_CASE(3, 32, 32, TE_HEAD, false) PW_TC_CASE(3, 64, 64, TE_HEAD, false)
+  PW_TC_CASE(1, 64, 32, TE_HEAD, false) PW_TC_CASE(1, 64, 64, TE_HEAD, false)
+  // FP8: gates (N = 128 per CTA), residual-block convs of steps 2-4
+  PW_TC_CASE(3, 32, 128, TE_LSTM, true) PW_TC_CASE(3, 64, 128, TE_LSTM, true)
+  PW_TC_CASE(3, 32, 32, TE_STORE, true) PW_TC_CASE(3, 64, 64, TE_STORE, true)
+  PW_TC_CASE(3, 32, 32, TE_HEAD, true) PW_TC_CASE(3, 64, 64, TE_HEAD, true)
 #undef PW_TC_CASE
   set_last_error("no tensor-core conv for this shape");
   return PW_EUNSUPPORTED;
@@ -780,6 +924,137 @@ int Model::ensure_tc() {
   return PW_OK;
 }
 
+// E4M3 copy of a convolution whose input channel k is stored as value *
+// in_scale[k]: W'[n][k] = W[n][k] / in_scale[k], per output column
+// sw[n] = max |W'[n][.]| / 448, stored E4M3(W' / sw) in the BF16 packing
+// order with 16 channels per 16-byte group. The epilogue computes
+// acc * sw[n] + b[n].
+static int pack_conv_f8(TcWeights &tw, TcWeights::Conv &cv, const std::vector<float> &w,
+                        const std::vector<float> &b, const std::vector<float> &in_scale,
+                        int cout, int cin, int ks, int ncta, int kb) {
+  cv.cin = cin; cv.cout = cout; cv.ks = ks; cv.kb = kb; cv.ncta = ncta; cv.nb = cout / ncta;
+  cv.f8 = true;
+  const int taps = ks * ks, nkb = cin / kb, gpb = kb / 16;
+  std::vector<float> sw(cout, 1.f);
+  for (int n = 0; n < cout; ++n) {
+    double mx = 0.0;
+    for (int k = 0; k < cin; ++k)
+      for (int t = 0; t < taps; ++t)
+        mx = std::max(mx, std::fabs((double)w[((size_t)n * cin + k) * taps + t] / in_scale[k]));
+    if (mx > 0.0) sw[n] = (float)(mx / 448.0);
+  }
+  std::vector<uint8_t> h((size_t)cout * cin * taps);
+  size_t o = 0;
+  for (int nb = 0; nb < cv.nb; ++nb)
+    for (int kbi = 0; kbi < nkb; ++kbi)
+      for (int t = 0; t < taps; ++t)
+        for (int g = 0; g < gpb; ++g)
+          for (int n = 0; n < ncta; ++n)
+            for (int e = 0; e < 16; ++e) {
+              const int co = nb * ncta + n, ci = kbi * kb + g * 16 + e;
+              const float v = (float)((double)w[((size_t)co * cin + ci) * taps + t] /
+                                      in_scale[ci] / sw[co]);
+              h[o++] = (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+            }
+  if (cudaMalloc(&cv.w, h.size()) != cudaSuccess || cudaMalloc(&cv.b, cout * 4) != cudaSuccess ||
+      cudaMalloc(&cv.sw, cout * 4) != cudaSuccess) {
+    set_last_error("weight allocation failed");
+    return PW_ENOMEM;
+  }
+  tw.allocs.push_back(cv.w);
+  tw.allocs.push_back(cv.b);
+  tw.allocs.push_back(cv.sw);
+  cudaMemcpy(cv.w, h.data(), h.size(), cudaMemcpyHostToDevice);
+  cudaMemcpy(cv.b, b.data(), cout * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(cv.sw, sw.data(), cout * 4, cudaMemcpyHostToDevice);
+  return PW_OK;
+}
+
+// FP8 activation scales (stored E4M3 value = activation * scale), fixed per
+// model from the weights alone: a root-mean-square estimate of every
+// channel, propagated through the layers from assumed input magnitudes
+// (quantised symbols RMS 8, l_i RMS 0.5), is mapped to 16. E4M3 then holds
+// 28x that RMS before saturating and keeps full precision down to 1/1000 of
+// it. l_i = h is bounded by 1 and is stored * 256.
+int Model::ensure_fp8() {
+  int s = ensure_tc();
+  if (s) return s;
+  if (tc->has_f8) return PW_OK;
+  TcWeights &t = *tc;
+  auto H = [&](const std::string &n) -> const std::vector<float> & { return host.at(n); };
+  constexpr double kSigS = 8.0, kSigL = 0.5, kTarget = 16.0;
+  auto dev = [&](const std::vector<float> &v, float **out) -> int {
+    if (cudaMalloc(out, v.size() * 4) != cudaSuccess) return PW_ENOMEM;
+    t.allocs.push_back(*out);
+    cudaMemcpy(*out, v.data(), v.size() * 4, cudaMemcpyHostToDevice);
+    return PW_OK;
+  };
+  // ConvLSTM input conv e = we * s + be
+  const std::vector<float> &we = H("lstm.we"), &be = H("lstm.be");
+  std::vector<float> es(C), hs(C, 256.f);
+  for (int c = 0; c < C; ++c) {
+    double v = (double)be[c] * be[c];
+    for (int tap = 0; tap < 9; ++tap) v += (double)we[c * 9 + tap] * we[c * 9 + tap] * kSigS * kSigS;
+    es[c] = (float)(kTarget / std::sqrt(std::max(v, 1e-12)));
+  }
+  if ((s = dev(es, &t.e_scale)) || (s = dev(hs, &t.h_scale))) return s;
+  std::vector<float> gin(2 * C);
+  for (int c = 0; c < C; ++c) { gin[c] = es[c]; gin[C + c] = hs[c]; }
+  if ((s = pack_conv_f8(t, t.gates8, H("lstm.wg.perm"), H("lstm.bg.perm"), gin, 4 * C, 2 * C,
+                        3, 128, C)))
+    return s;
+  // steps 2-4: z = Wz [a; l] + bz (a = Wa (m s) + ba), u = lrelu(conv3x3 z)
+  auto steps = [&](const std::string &ns, TcWeights::Conv *c1, TcWeights::Conv *c2,
+                   float **zsc, float **usc) -> int {
+    for (int k = 1; k < 4; ++k) {
+      const std::string q = ns + ".s" + std::to_string(k) + ".";
+      const std::vector<float> &wz = H(q + "wz"), &bz = H(q + "bz"), &wa = H(q + "wa"),
+                               &ba = H(q + "ba"), &w1 = H(q + "w1"), &b1 = H(q + "b1");
+      std::vector<double> sa(C), sz(C);
+      for (int j = 0; j < C; ++j) {
+        double v = (double)ba[j] * ba[j];
+        for (int tap = 0; tap < 9; ++tap) v += (double)wa[j * 9 + tap] * wa[j * 9 + tap] * kSigS * kSigS;
+        sa[j] = v;
+      }
+      std::vector<float> zs(C), us(C);
+      for (int c = 0; c < C; ++c) {
+        double v = (double)bz[c] * bz[c];
+        for (int j = 0; j < C; ++j) {
+          const double wa_ = wz[(size_t)c * 2 * C + j], wl = wz[(size_t)c * 2 * C + C + j];
+          v += wa_ * wa_ * sa[j] + wl * wl * kSigL * kSigL;
+        }
+        sz[c] = v;
+        zs[c] = (float)(kTarget / std::sqrt(std::max(v, 1e-12)));
+      }
+      for (int c = 0; c < C; ++c) {
+        double v = (double)b1[c] * b1[c];
+        for (int j = 0; j < C; ++j)
+          for (int tap = 0; tap < 9; ++tap) {
+            const double ww = w1[((size_t)c * C + j) * 9 + tap];
+            v += ww * ww * sz[j];
+          }
+        us[c] = (float)(kTarget / std::sqrt(std::max(v, 1e-12)));
+      }
+      int r;
+      if ((r = dev(zs, &zsc[k - 1])) || (r = dev(us, &usc[k - 1]))) return r;
+      if ((r = pack_conv_f8(t, c1[k - 1], w1, b1, zs, C, C, 3, C, C))) return r;
+      if ((r = pack_conv_f8(t, c2[k - 1], H(q + "w2"), H(q + "b2"), us, C, C, 3, C, C))) return r;
+    }
+    return PW_OK;
+  };
+  if ((s = steps("sb", t.sk_c1_8, t.sk_c2_8, t.sk_z_scale, t.sk_u_scale))) return s;
+  if (ll_mode == 0 && (s = steps("ll", t.lk_c1_8, t.lk_c2_8, t.lk_z_scale, t.lk_u_scale)))
+    return s;
+  t.has_f8 = true;
+  return PW_OK;
+}
+
+int Model::prepare(int precision) {
+  if (precision == PW_PREC_FP32) return PW_OK;
+  std::lock_guard<std::mutex> lk(mu);
+  return precision == PW_PREC_FP8 ? ensure_fp8() : ensure_tc();
+}
+
 void Model::free_tc() {
   if (!tc) return;
   for (void *p : tc->allocs) cudaFree(p);
@@ -794,30 +1069,35 @@ static int64_t compact_elems(int h, int w) {
   return (int64_t)((h + 1) >> 1) * (row_count(w, step_phase(0, 0)) + row_count(w, step_phase(0, 1)));
 }
 
-int64_t tc_workspace_bytes(const Geometry &g, int P, int C) {
+int64_t tc_workspace_bytes(const Geometry &g, int P, int C, bool f8) {
   const int64_t big = (int64_t)P * g.sh.back() * g.sw.back();
   int64_t cmax = 0;
   for (int sb = 0; sb < g.nsb; ++sb) cmax = std::max(cmax, compact_elems(g.sh[sb], g.sw[sb]));
   cmax *= P;
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
-  return 1024 + al(big * 2 * C * 2) + 5 * al(big * C * 2) + al(big * 2 * C * 2) +
-         3 * al(cmax * C * 2) + al(cmax * 2 * C * 2) + al(big * 32 * 2);
+  int64_t tot = 1024 + al(big * 2 * C * 2) + 5 * al(big * C * 2) + al(big * 2 * C * 2) +
+                3 * al(cmax * C * 2) + al(cmax * 2 * C * 2) + al(big * 32 * 2);
+  if (f8) tot += al(big * 2 * C) + 4 * al(big * C);
+  return tot;
 }
 
-int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
+int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C, bool f8) {
   const int64_t big = (int64_t)ws->P * g.sh.back() * g.sw.back();
   int64_t cmax = 0;
   for (int sb = 0; sb < g.nsb; ++sb) cmax = std::max(cmax, compact_elems(g.sh[sb], g.sw[sb]));
   cmax *= ws->P;
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
   // X (2C), L0 (C), L1 (C), Z (C), U (2C), V (C), Z2 (C); compact Vc, Zc,
-  // Z2c (C), U2c (2C); T (32); bf16
-  constexpr int kN = 12;
+  // Z2c (C), U2c (2C); T (32); bf16. FP8: X8 (2C), L8 x 2, Z8, U8 (C) bytes
+  constexpr int kN = 12, kN8 = 5;
   const int64_t sizes[kN] = {big * 2 * C * 2, big * C * 2,  big * C * 2,      big * C * 2,
                              big * 2 * C * 2, big * C * 2,  big * C * 2,      cmax * C * 2,
                              cmax * C * 2,    cmax * C * 2, cmax * 2 * C * 2, big * 32 * 2};
+  const int64_t sizes8[kN8] = {big * 2 * C, big * C, big * C, big * C, big * C};
   int64_t tot = 1024;
   for (int64_t v : sizes) tot += al(v);
+  if (f8)
+    for (int64_t v : sizes8) tot += al(v);
   TcAct *t = new TcAct();
   if (cudaMalloc(&t->base, (size_t)tot) != cudaSuccess) {
     delete t;
@@ -831,6 +1111,10 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C) {
   __nv_bfloat16 **dst[kN] = {&t->X,  &t->L[0], &t->L[1], &t->Z,   &t->U,  &t->V,
                              &t->Z2, &t->Vc,   &t->Zc,   &t->Z2c, &t->U2c, &t->T};
   for (int i = 0; i < kN; ++i) { *dst[i] = reinterpret_cast<__nv_bfloat16 *>(b + o); o += al(sizes[i]); }
+  if (f8) {
+    uint8_t **dst8[kN8] = {&t->X8, &t->L8[0], &t->L8[1], &t->Z8, &t->U8};
+    for (int i = 0; i < kN8; ++i) { *dst8[i] = b + o; o += al(sizes8[i]); }
+  }
   ws->tc = t;
   return PW_OK;
 }
@@ -851,29 +1135,41 @@ static int grid_for(int64_t n) {
 int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
                 const int32_t *sprev, int up, int first, int cur) {
   TcAct &t = *static_cast<TcAct *>(ws.tc);
-  const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P, G = C / 8;
+  const bool f8 = ctx->precision == PW_PREC_FP8;
+  const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P, G = C / 8, G16 = C / 16;
   const double pix = (double)P * h * w;
   __nv_bfloat16 *lprev = t.L[(sb - 1) & 1], *lout = t.L[sb & 1];
-  // h_{i-1} is copied into X only when it must be upsampled (or when a
-  // K-block would mix e and h channels); otherwise the gates conv reads it
-  // from lprev directly
-  const int copy_h = (up || m.tc->gates.kb != C) ? 1 : 0;
+  const TcWeights::Conv &gates = f8 ? m.tc->gates8 : m.tc->gates;
+  // h_{i-1} is copied into X only when it must be upsampled, when a K-block
+  // would mix e and h channels, or for the first subband (h_{i-1} = 0);
+  // otherwise the gates conv reads it from the previous l buffer directly
+  const int copy_h = (up || first || gates.kb != C) ? 1 : 0;
   {
-    ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 2.0 * C * (copy_h ? 3 : 1)));
-    k_lstm_in_bf16<<<grid_for((int64_t)P * h * w), 256, 0, ctx->stream>>>(
-        sprev, lprev, m.lstm_we, m.lstm_be, t.X, P, h, w, C, up, copy_h, first);
+    ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C,
+                 pix * (4.0 + (f8 ? 1.0 : 2.0) * C * (copy_h ? 3 : 1)));
+    if (f8)
+      k_lstm_in_fp8<<<grid_for((int64_t)P * h * w), 256, 0, ctx->stream>>>(
+          sprev, t.L8[(sb - 1) & 1], m.lstm_we, m.lstm_be, m.tc->e_scale, t.X8, P, h, w, C, up,
+          copy_h, first);
+    else
+      k_lstm_in_bf16<<<grid_for((int64_t)P * h * w), 256, 0, ctx->stream>>>(
+          sprev, lprev, m.lstm_we, m.lstm_be, t.X, P, h, w, C, up, copy_h, first);
     ctx->launches += 1;
   }
   TcConvArgs a{};
   a.epi = TE_LSTM;
   a.out = lout; a.out_G = G; a.out_goff = 0;
   a.c_prev = ws.Cst[cur]; a.c_new = ws.Cst[cur ^ 1]; a.up = up; a.first = first; a.C = C;
+  if (f8) { a.out8 = t.L8[sb & 1]; a.out8_G16 = G16; a.out8_scale = m.tc->h_scale; }
   ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * 2 * C * 4 * C,
-               pix * (2.0 * 2 * C + 2.0 * C + 8.0 * C));
-  if (copy_h) return conv_tc(ctx, m.tc->gates, t.X, 2 * G, 0, P, h, w, a, t.err);
+               pix * ((f8 ? 2.0 : 4.0) * C + 2.0 * C + 8.0 * C + (f8 ? C : 0)));
+  if (f8) {
+    if (copy_h) return conv_tc(ctx, gates, t.X8, 2 * G16, 0, P, h, w, a, t.err);
+    return conv_tc(ctx, gates, t.X8, 2 * G16, 0, P, h, w, a, t.err, t.L8[(sb - 1) & 1], G16, 0, 1);
+  }
+  if (copy_h) return conv_tc(ctx, gates, t.X, 2 * G, 0, P, h, w, a, t.err);
   // same resolution: e from X, h_{i-1} straight from the previous l buffer
-  // (for subband 2 that buffer holds the LL subband's l = 0)
-  return conv_tc(ctx, m.tc->gates, t.X, 2 * G, 0, P, h, w, a, t.err, lprev, G, 0, 1);
+  return conv_tc(ctx, gates, t.X, 2 * G, 0, P, h, w, a, t.err, lprev, G, 0, 1);
 }
 
 int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb, int step,
@@ -894,7 +1190,10 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     return conv_tc(ctx, cv, in, in_G, in_goff, P, h, w, a, t.err);
   };
   int s;
-  if (ll && step == 0) cudaMemsetAsync(l, 0, (size_t)P * h * w * C * 2, st);  // l = 0 for LL
+  if (ll && step == 0) {  // l = 0 for LL
+    cudaMemsetAsync(l, 0, (size_t)P * h * w * C * 2, st);
+    if (ctx->precision == PW_PREC_FP8) cudaMemsetAsync(t.L8[sb & 1], 0, (size_t)P * h * w * C, st);
+  }
   if (step == 0) {
     const TcWeights::Conv &cin_ = ll ? W.l0_in : W.s0_in, &c1 = ll ? W.l0_w1 : W.s0_w1,
                           &c2 = ll ? W.l0_w2 : W.s0_w2, &c3 = ll ? W.l0_w3 : W.s0_w3,
@@ -935,8 +1234,14 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     return cconv(c4, t.U2c, 2 * G, a);                             // head
   }
   const TcWeights::Conv &zt = ll ? W.lk_zt[step - 1] : W.sk_zt[step - 1];
-  const TcWeights::Conv &c1 = ll ? W.lk_c1[step - 1] : W.sk_c1[step - 1];
-  const TcWeights::Conv &c2 = ll ? W.lk_c2[step - 1] : W.sk_c2[step - 1];
+  const bool f8 = ctx->precision == PW_PREC_FP8;
+  const TcWeights::Conv &c1 = f8 ? (ll ? W.lk_c1_8[step - 1] : W.sk_c1_8[step - 1])
+                                 : (ll ? W.lk_c1[step - 1] : W.sk_c1[step - 1]);
+  const TcWeights::Conv &c2 = f8 ? (ll ? W.lk_c2_8[step - 1] : W.sk_c2_8[step - 1])
+                                 : (ll ? W.lk_c2[step - 1] : W.sk_c2[step - 1]);
+  const float *zsc = ll ? W.lk_z_scale[step - 1] : W.sk_z_scale[step - 1];
+  const float *usc = ll ? W.lk_u_scale[step - 1] : W.sk_u_scale[step - 1];
+  const int G16 = C / 16;
   {
     ProfScope ps(ctx, KC_SMALL_CTX, 0.0, pix * (4.0 + 64.0));
     k_masked_taps<<<grid_for((int64_t)P * h * w), 256, 0, st>>>(Qi, t.T, P, h, w, step);
@@ -944,10 +1249,25 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   }
   TcConvArgs a{};
   a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
+  if (f8) { a.out8 = t.Z8; a.out8_G16 = G16; a.out8_scale = zsc; }
   {
     // z = 1x1 over [l, T]: K-blocks of 32 channels, the first C / 32 from l
-    ProfScope ps(ctx, KC_CONV1, 2.0 * pix * zt.cin * zt.cout, pix * 2.0 * (zt.cin + zt.cout));
+    ProfScope ps(ctx, KC_CONV1, 2.0 * pix * zt.cin * zt.cout,
+                 pix * (2.0 * (zt.cin + zt.cout) + (f8 ? C : 0)));
     if ((s = conv_tc(ctx, zt, l, G, 0, P, h, w, a, t.err, t.T, 4, 0, C / 32))) return s;
+  }
+  if (f8) {
+    a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = nullptr; a.out_G = G;
+    a.out8 = t.U8; a.out8_G16 = G16; a.out8_scale = usc;
+    {
+      ProfScope ps(ctx, KC_CONV3, 2.0 * pix * 9 * C * C, pix * 2.0 * C);
+      if ((s = conv_tc(ctx, c1, t.Z8, G16, 0, P, h, w, a, t.err))) return s;  // u = lrelu(3x3 z)
+    }
+    a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z; a.res_G = G;
+    a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
+    a.mu_out = mu; a.sg_out = sgp;
+    ProfScope ps(ctx, KC_CONV3, 2.0 * pix * 9 * C * C, pix * 3.0 * C);
+    return conv_tc(ctx, c2, t.U8, G16, 0, P, h, w, a, t.err);               // head
   }
   a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
   if ((s = conv(c1, t.Z, G, 0, a, 0))) return s;                  // u = lrelu(conv3x3 z)

@@ -1,11 +1,12 @@
-// Tensor-core (tcgen05, BF16) context-model path: declarations.
+// Tensor-core (tcgen05, BF16 / FP8) context-model path: declarations.
 #pragma once
 #include "codec.h"
 
 namespace pw {
-int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C);
+// f8: also the E4M3 activation buffers of the FP8 precision
+int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C, bool f8);
 // Device bytes tc_workspace_alloc takes for P planes of geometry g.
-int64_t tc_workspace_bytes(const Geometry &g, int P, int C);
+int64_t tc_workspace_bytes(const Geometry &g, int P, int C, bool f8);
 void tc_workspace_free(Workspace *ws);
 int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
                 const int32_t *sprev, int up, int first, int cur);

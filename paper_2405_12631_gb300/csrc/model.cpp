@@ -157,6 +157,8 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
     lstm_bg = up(bgp);
     keep("lstm.wg.perm", wgp);
     keep("lstm.bg.perm", bgp);
+    keep("lstm.we", we);
+    keep("lstm.be", be);
   }
   // four-step nets
   auto load_set = [&](const std::string &ns, StepNetDev *nets) -> bool {

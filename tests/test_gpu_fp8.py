@@ -1,0 +1,107 @@
+"""FP8 precision: the ConvLSTM gates and the residual-block convolutions of
+steps 2-4 in E4M3 (kind::f8f6f4 tensor-core MMAs) with static per-channel
+scales and FP32 accumulation.
+
+* Encoder and decoder run the same kernels, so the decoded symbols equal the
+  encoder's quantised coefficients exactly and results do not depend on the
+  batch.
+* Reconstruction does not involve the context model: PSNR within 0.01 dB of
+  the oracle's.
+* The entropy parameters against the FP64 oracle are reported per result
+  (E4M3 keeps 3 mantissa bits, so errors of a few percent are expected) and
+  bounded loosely; the rate cost against BF16 is reported and bounded.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import codec as K
+from tests._lib import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pw():
+    ensure_built()
+    import paper_2405_12631_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def f8(pw):
+    c = pw.Codec(0, "fp8")
+    yield c
+    c.close()
+
+
+def _blob(C, levels=4, seed=0, ll_mode=0):
+    cfg = S.ModelConfig(levels=levels, C=C, ll_mode=ll_mode)
+    return S.pack_blob(cfg, S.random_model(cfg, seed))
+
+
+@pytest.mark.parametrize("C", [32, 64])
+@pytest.mark.parametrize("rgb", [False, True])
+def test_fp8_roundtrip_symbols_exact(f8, C, rgb):
+    gm = f8.load_model(_blob(C))
+    img = S.rgb_natural(72, 104, seed=7) if rgb else S.gray_sinusoids(72, 104, seed=7)
+    bs = f8.encode_image(gm, img, q=8.0, chunk=300)
+    assert np.array_equal(f8.decode_symbols(gm, bs), f8.analyse(gm, img, q=8.0))
+
+
+def test_fp8_batch_invariance(f8):
+    gm = f8.load_model(_blob(64))
+    imgs = [S.rgb_natural(48, 80, seed=s) for s in (20, 21, 22)]
+    single = [f8.encode_image(gm, im, q=8.0) for im in imgs]
+    assert f8.encode_batch(gm, imgs, q=8.0) == single
+    dec = f8.decode_batch(gm, single)
+    for i, bs in enumerate(single):
+        assert np.array_equal(dec[i], f8.decode_image(gm, bs))
+
+
+def test_fp8_psnr_matches_oracle(f8):
+    blob = _blob(32)
+    gm = f8.load_model(blob)
+    img = S.rgb_natural(64, 96, seed=9)
+    out = f8.decode_image(gm, f8.encode_image(gm, img, q=8.0))
+    ref = K.decode_image(blob, K.encode_image(blob, img, q=8.0))
+
+    def psnr(a):
+        return 10 * np.log10(255.0 ** 2 / np.mean((a.astype(float) - img) ** 2))
+    assert abs(psnr(out) - psnr(ref)) < 0.01
+
+
+def test_fp8_entropy_params_error_and_rate(f8, pw):
+    blob = _blob(64)
+    gm = f8.load_model(blob)
+    om = K.Model(blob)
+    img = S.gray_sinusoids(80, 112, seed=5)
+    planes, _ = K.colour_forward(img, False, 8)
+    qsb = [K.quantise(s, np.float32(1 / 8.0))
+           for s in om.lift.forward(K.pad_plane(planes[0], 16), 4, False)]
+    mu, sg = f8.context_params(gm, 80, 112, np.concatenate([q.reshape(-1) for q in qsb]))
+    ref = K.context_params_all(om, qsb)
+    mu_o = np.concatenate([r[0].reshape(-1) for r in ref])
+    sg_o = np.concatenate([r[1].reshape(-1) for r in ref])
+    e_mu = np.abs(mu - mu_o) / np.maximum(np.abs(mu_o), 1.0)
+    e_sg = np.abs(sg - sg_o) / sg_o
+    bf = pw.Codec(0, "bf16")
+    gb = bf.load_model(blob)
+    rgb = S.rgb_natural(128, 192, seed=3)
+    n8 = len(f8.encode_image(gm, rgb, q=8.0))
+    n16 = len(bf.encode_image(gb, rgb, q=8.0))
+    print(f"FP8 vs FP64 oracle: mu rel err mean {e_mu.mean():.2e} max {e_mu.max():.2e}; "
+          f"sigma rel err mean {e_sg.mean():.2e} max {e_sg.max():.2e}; "
+          f"stream bytes FP8 {n8} vs BF16 {n16} ({100.0 * (n8 - n16) / n16:+.2f} %)")
+    gb.close()
+    bf.close()
+    assert np.all(np.isfinite(mu)) and np.all(np.isfinite(sg))
+    assert e_mu.mean() < 0.1 and e_sg.mean() < 0.1
+    assert abs(n8 - n16) / n16 < 0.05
+
+
+def test_fp8_ar_ll_roundtrip(f8):
+    gm = f8.load_model(_blob(32, ll_mode=1))
+    img = S.gray_sinusoids(64, 96, seed=4)
+    bs = f8.encode_image(gm, img, q=8.0)
+    assert np.array_equal(f8.decode_symbols(gm, bs), f8.analyse(gm, img, q=8.0))
