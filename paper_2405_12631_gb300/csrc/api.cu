@@ -204,7 +204,7 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *co
   }
   {
     ProfScope ps(ctx, KC_CDF, 0.0, (double)kNTables * (kNSym + 1) * 2);
-    launch_cdf_bank(ctx->bank, st);
+    launch_cdf_bank(ctx->bank, ctx->coarse, st);
   }
   bump(ctx, 2);
   for (int sb = 0; sb < g.nsb; ++sb) {
@@ -232,7 +232,7 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *co
       const int h = g.sh[sb], w = g.sw[sb];
       const double nsym = (double)P * step_count(h, w, k);
       ProfScope ps(ctx, KC_RANS_DEC, 0.0, nsym * 8.0 + stream_bytes * nsym / total_syms);
-      launch_rans_decode(dch + pl.gbase[gi], P * cnt, ctx->bank,
+      launch_rans_decode(dch + pl.gbase[gi], P * cnt, ctx->bank, ctx->coarse,
                          pl.ws.idx + (int64_t)P * g.ioff[gi], step_count(h, w, k),
                          pl.ws.Q + (int64_t)P * g.soff[sb], (int64_t)h * w, h, w, k,
                          ctx->status, st);
@@ -404,7 +404,7 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
   cudaStream_t st = ctx->stream;
   Workspace &ws = pl.ws;
   if (ctx->precision != PW_PREC_FP32) tc_error_reset(ws, st);
-  launch_cdf_bank(ctx->bank, st);
+  launch_cdf_bank(ctx->bank, ctx->coarse, st);
   bump(ctx);
   for (int sb = 0; sb < g.nsb; ++sb) {
     int s;
@@ -648,7 +648,7 @@ int pw_ctx_create(int device, void *stream, int precision, pw_ctx **out) {
   c->precision = precision;
   c->plan_cache = new PlanCache();
   c->prof = new Prof();
-  if (cudaMalloc(&c->bank, kNTables * (kNSym + 1) * 2) != cudaSuccess ||
+  if (cudaMalloc(&c->bank, kNTables * (kNSym + 1 + kCoarse) * 2) != cudaSuccess ||
       cudaMalloc(&c->status, 256) != cudaSuccess) {
     delete reinterpret_cast<PlanCache *>(c->plan_cache);
     delete reinterpret_cast<Prof *>(c->prof);
@@ -656,6 +656,7 @@ int pw_ctx_create(int device, void *stream, int precision, pw_ctx **out) {
     set_last_error("device allocation failed");
     return PW_ENOMEM;
   }
+  c->coarse = c->bank + (size_t)kNTables * (kNSym + 1);
   *out = c;
   return PW_OK;
 }
@@ -907,7 +908,7 @@ int pw_temporal_lift(pw_ctx *c, const pw_model *mm, int nframes, int H, int W, i
 // ---- stages ---------------------------------------------------------------
 int pw_cdf_bank(pw_ctx *c, uint16_t *dev_bank) {
   if (!c || !dev_bank) return PW_EINVAL;
-  launch_cdf_bank(dev_bank, c->stream);
+  launch_cdf_bank(dev_bank, nullptr, c->stream);
   bump(c);
   return finish(c);
 }
@@ -963,8 +964,8 @@ int pw_rans_decode(pw_ctx *c, const uint8_t *payload, size_t payload_bytes, int 
   if (nchunks)
     PW_CUDA_TRY(cudaMemcpyAsync(dch.p, ch.data(), nchunks * sizeof(DecChunk), cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemsetAsync(c->status, 0, 4, st));
-  launch_cdf_bank(c->bank, st);
-  launch_rans_decode((DecChunk *)dch.p, nchunks, c->bank, (uint32_t *)di.p, 0,
+  launch_cdf_bank(c->bank, c->coarse, st);
+  launch_rans_decode((DecChunk *)dch.p, nchunks, c->bank, c->coarse, (uint32_t *)di.p, 0,
                      (int32_t *)dout.p, 0, 0, 0, -1, c->status, st);
   bump(c, 2);
   if (nsym) PW_CUDA_TRY(cudaMemcpyAsync(out, dout.p, nsym * 4, cudaMemcpyDeviceToHost, st));
@@ -1000,7 +1001,7 @@ int pw_rans_encode(pw_ctx *c, int nchunks, const uint32_t *count, const uint32_t
   }
   if (nchunks)
     PW_CUDA_TRY(cudaMemcpyAsync(dec.p, ec.data(), nchunks * sizeof(EncChunk), cudaMemcpyHostToDevice, st));
-  launch_cdf_bank(c->bank, st);
+  launch_cdf_bank(c->bank, c->coarse, st);
   launch_rans_count_ops((EncChunk *)dec.p, nchunks, (uint32_t *)di.p, (int32_t *)dv.p,
                         (uint32_t *)dops.p, st);
   bump(c, 2);

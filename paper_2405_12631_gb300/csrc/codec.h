@@ -145,6 +145,7 @@ struct pw_ctx {
   cudaStream_t stream = nullptr;
   int precision = PW_PREC_FP32;
   uint16_t *bank = nullptr;        // CDF table bank (built by k_cdf_bank)
+  uint16_t *coarse = nullptr;      // its coarse level (same allocation, after the bank)
   uint32_t *status = nullptr;      // device status word
   uint64_t launches = 0;
   void *plan_cache = nullptr;      // cached workspaces per geometry (api.cu)

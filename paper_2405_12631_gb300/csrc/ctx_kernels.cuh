@@ -59,11 +59,12 @@ struct EncChunk {
   uint64_t scratch_end;  // word index one past the chunk's scratch region
   uint32_t count, lanes;
 };
-void launch_cdf_bank(uint16_t *bank, cudaStream_t st);
+// bank: 2048 x 128 CDF tables; coarse (may be null): every 8th entry, 2048 x 16
+void launch_cdf_bank(uint16_t *bank, uint16_t *coarse, cudaStream_t st);
 void launch_rans_decode(const DecChunk *chunks, int nchunks, const uint16_t *bank,
-                        const uint32_t *idx, int64_t idx_stride, int32_t *out,
-                        int64_t out_stride, int h, int w, int step, uint32_t *status,
-                        cudaStream_t st);
+                        const uint16_t *coarse, const uint32_t *idx, int64_t idx_stride,
+                        int32_t *out, int64_t out_stride, int h, int w, int step,
+                        uint32_t *status, cudaStream_t st);
 void launch_rans_count_ops(const EncChunk *chunks, int nchunks, const uint32_t *idx,
                            const int32_t *vals, uint32_t *ops, cudaStream_t st);
 void launch_rans_encode(const EncChunk *chunks, int nchunks, const uint16_t *bank,

@@ -15,6 +15,8 @@
 // exp() here is the library's own routine (Cody-Waite reduction by ln 2 and a
 // degree-6 Taylor polynomial in Horner order) written with explicitly
 // rounded intrinsics, so no contraction or library-specific rounding enters.
+#include <mutex>
+
 #include "pw_internal.cuh"
 #include "ctx_kernels.cuh"
 
@@ -44,7 +46,9 @@ __device__ __forceinline__ float exp32_spec(float z) {
 
 // One warp per table. Lane l owns symbols 4l .. 4l+3 (127 symbols) and the
 // CDF entries 4l .. 4l+3 (128 entries: cdf[0] = 0 .. cdf[127] = M).
-__global__ void k_cdf_bank(uint16_t *__restrict__ bank) {
+// coarse (optional): every 8th CDF entry of each table, [table][16], the
+// first level of the decoder's symbol search.
+__global__ void k_cdf_bank(uint16_t *__restrict__ bank, uint16_t *__restrict__ coarse) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (warp >= kNTables) return;
@@ -107,6 +111,7 @@ __global__ void k_cdf_bank(uint16_t *__restrict__ bank) {
   }
   int run = incl - local;
   uint16_t *row = bank + (size_t)warp * (kNSym + 1);
+  if (coarse && (lane & 1) == 0) coarse[(size_t)warp * kCoarse + (lane >> 1)] = (uint16_t)run;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     int s = 4 * lane + i;  // cdf index s = sum of f[0..s-1]
@@ -126,26 +131,68 @@ __global__ void k_cdf_bank(uint16_t *__restrict__ bank) {
 // DecChunk (ctx_kernels.cuh): data = nl u32 states then u16 words; count
 // symbols; first = index of its first symbol in the output list.
 
-__device__ __forceinline__ int cdf_find(const uint16_t *__restrict__ t, uint32_t slot) {
-  // largest s in [0, 126] with t[s] <= slot (t strictly increasing, t[0] = 0)
-  int lo = 0, hi = kNSym;  // invariant t[lo] <= slot < t[hi]
-#pragma unroll
-  for (int it = 0; it < 7; ++it) {
-    int mid = (lo + hi) >> 1;
-    if (mid > lo) {
-      if ((uint32_t)__ldg(t + mid) <= slot) lo = mid; else hi = mid;
-    }
-  }
-  return lo;
+// Number of the two u16 halves of w that are <= slot.
+__device__ __forceinline__ int cnt_le2(uint32_t w, uint32_t slot) {
+  return (int)((w & 0xFFFFu) <= slot) + (int)((w >> 16) <= slot);
+}
+__device__ __forceinline__ uint32_t u16_at(const uint4 &v, int i) {  // i in 0..7
+  const uint32_t w = (i >> 1) == 0 ? v.x : (i >> 1) == 1 ? v.y : (i >> 1) == 2 ? v.z : v.w;
+  return (i & 1) ? (w >> 16) : (w & 0xFFFFu);
+}
+// Two consecutive 16-bit words k, k + 1 of a chunk's word stream (0 past the
+// end), byte loads so that no alignment is assumed.
+__device__ __forceinline__ uint32_t ld_words2(const uint8_t *wp, uint32_t k, uint32_t nwords) {
+  uint32_t v = 0;
+  if (k < nwords) v = (uint32_t)__ldg(wp + 2 * k) | ((uint32_t)__ldg(wp + 2 * k + 1) << 8);
+  if (k + 1 < nwords)
+    v |= ((uint32_t)__ldg(wp + 2 * k + 2) << 16) | ((uint32_t)__ldg(wp + 2 * k + 3) << 24);
+  return v;
+}
+
+// Symbol search: the largest s in [0, 126] with t[s] <= slot, in two levels:
+// the table's 16 coarse entries (every 8th, shared memory) give the block
+// b = s / 8, one 16-byte load gives its 8 entries. The entries are strictly
+// increasing with t[0] = 0 and t[127] = M > slot, so the counts below are
+// exactly that s. Returns s; lo = t[s], hi = t[s + 1].
+__device__ __forceinline__ int cdf_search(const uint16_t *__restrict__ row,
+                                          const uint16_t *s_crow, uint32_t slot, uint32_t &lo,
+                                          uint32_t &hi) {
+  const uint4 c0 = *reinterpret_cast<const uint4 *>(s_crow);
+  const uint4 c1 = *reinterpret_cast<const uint4 *>(s_crow + 8);
+  const int b = cnt_le2(c0.x, slot) + cnt_le2(c0.y, slot) + cnt_le2(c0.z, slot) +
+                cnt_le2(c0.w, slot) + cnt_le2(c1.x, slot) + cnt_le2(c1.y, slot) +
+                cnt_le2(c1.z, slot) + cnt_le2(c1.w, slot) - 1;
+  const uint4 f = __ldg(reinterpret_cast<const uint4 *>(row + 8 * b));
+  const int i = cnt_le2(f.x, slot) + cnt_le2(f.y, slot) + cnt_le2(f.z, slot) +
+                cnt_le2(f.w, slot) - 1;
+  lo = u16_at(f, i);
+  // i == 7 implies b < 15 (t[127] = M > slot); the clamp keeps the read in
+  // the table either way
+  hi = (i < 7) ? u16_at(f, i + 1) : (uint32_t)s_crow[min(b + 1, kCoarse - 1)];
+  return 8 * b + i;
 }
 
 // Output modes: positions of a four-step subband plane (step >= 0), or a
 // linear array (step < 0, out[first + i]).
-__global__ void k_rans_decode(const DecChunk *__restrict__ chunks, int nchunks,
-                              const uint16_t *__restrict__ bank,
-                              const uint32_t *__restrict__ idx, int64_t idx_stride,
-                              int32_t *__restrict__ out, int64_t out_stride,
-                              int h, int w, int step, uint32_t *status) {
+//
+// The block first copies the coarse table bank (64 KB) into shared memory.
+// Per round each lane's packed table index was loaded one round earlier;
+// the renormalisation words come from a 128-word window that the warp keeps
+// in registers (lane l holds words wb + 2l, wb + 2l + 1 in cur and the same
+// 64 words later in nxt) and reads with shuffles; the window moves by 64
+// words once 64 are consumed, loading the next 64 one shift ahead.
+__global__ void __launch_bounds__(256) k_rans_decode(
+    const DecChunk *__restrict__ chunks, int nchunks, const uint16_t *__restrict__ bank,
+    const uint16_t *__restrict__ coarse, const uint32_t *__restrict__ idx, int64_t idx_stride,
+    int32_t *__restrict__ out, int64_t out_stride, int h, int w, int step,
+    uint32_t *status) {
+  extern __shared__ uint4 s_coarse4[];
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(coarse);
+    for (int i = threadIdx.x; i < kNTables * kCoarse / 8; i += blockDim.x) s_coarse4[i] = __ldg(src + i);
+  }
+  __syncthreads();
+  const uint16_t *s_coarse = reinterpret_cast<const uint16_t *>(s_coarse4);
   const int cw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (cw >= nchunks) return;
@@ -164,36 +211,73 @@ __global__ void k_rans_decode(const DecChunk *__restrict__ chunks, int nchunks,
         ((uint32_t)sp[3] << 24);
   }
   const uint8_t *wp = base + 4 * nl;
+  uint32_t wb = 0;
+  uint32_t wcur = ld_words2(wp, 2 * lane, nwords), wnxt = ld_words2(wp, 64 + 2 * lane, nwords);
   uint32_t ptr = 0;
   bool bad = false;
   const uint32_t lt = (1u << lane) - 1u;
+  // word k of the stream (k - wb in [0, 128) for every calling lane)
+  auto word = [&](uint32_t k) -> uint32_t {
+    const uint32_t r = k - wb;
+    const int src = (int)((r & 63u) >> 1);
+    const uint32_t a = __shfl_sync(0xffffffffu, wcur, src);
+    const uint32_t b = __shfl_sync(0xffffffffu, wnxt, src);
+    const uint32_t v = r < 64u ? a : b;
+    return (r & 1u) ? (v >> 16) : (v & 0xFFFFu);
+  };
+  auto advance = [&](uint32_t n) {
+    ptr += n;
+    if (ptr - wb >= 64u) {
+      wcur = wnxt;
+      wnxt = ld_words2(wp, wb + 128 + 2 * lane, nwords);
+      wb += 64;
+    }
+  };
   const uint32_t *idxp = idx + (int64_t)ch.plane * idx_stride + ch.first;
   int32_t *outp = out + (int64_t)ch.plane * out_stride;
-  const int niter = (ch.count + nl - 1) / nl;
+  const int count = (int)ch.count;
+  const int niter = (count + nl - 1) / nl;
+  // output position of symbol q = first + p (step layout): row pair y2,
+  // index r within the pair, advanced by nl per iteration
+  int ae = 0, ao = 0, ne = 1, pair = 1, y2 = 0, rr = 0;
+  if (step >= 0) {
+    ae = step_phase(step, 0); ao = step_phase(step, 1);
+    ne = row_count(w, ae);
+    pair = ne + row_count(w, ao);
+    if (pair == 0) {  // a step without positions has no chunks
+      if (lane == 0) atomicOr(status, kStCorrupt);
+      return;
+    }
+    const int q0 = (int)ch.first + lane;
+    y2 = q0 / pair; rr = q0 - y2 * pair;
+  }
+  uint32_t pk_next = (lane < nl && lane < count) ? __ldg(idxp + lane) : 0u;
   for (int it = 0; it < niter; ++it) {
     const int p = it * nl + lane;
-    const bool active = lane < nl && p < (int)ch.count;
+    const bool active = lane < nl && p < count;
+    const uint32_t pk = pk_next;
+    if (active && p + nl < count) pk_next = __ldg(idxp + p + nl);
     int ctr = 0, s = 1;
     if (active) {
       int tid;
-      unpack_index(__ldg(idxp + p), ctr, tid);
-      const uint16_t *t = bank + (size_t)tid * (kNSym + 1);
-      uint32_t slot = x & (kM - 1);
-      s = cdf_find(t, slot);
-      uint32_t c0 = __ldg(t + s), c1 = __ldg(t + s + 1);
-      x = (c1 - c0) * (x >> kLogM) + slot - c0;
+      unpack_index(pk, ctr, tid);
+      const uint32_t slot = x & (kM - 1);
+      uint32_t lo, hi;
+      s = cdf_search(bank + (size_t)tid * (kNSym + 1), s_coarse + tid * kCoarse, slot, lo, hi);
+      x = (hi - lo) * (x >> kLogM) + slot - lo;
     }
     {
-      bool need = active && x < kRansL;
-      uint32_t m = __ballot_sync(0xffffffffu, need);
-      if (need) {
-        uint32_t k = ptr + __popc(m & lt);
-        uint32_t wv = 0;
-        if (k < nwords) wv = (uint32_t)wp[2 * k] | ((uint32_t)wp[2 * k + 1] << 8);
-        else bad = true;
-        x = (x << 16) | wv;
+      const bool need = active && x < kRansL;
+      const uint32_t m = __ballot_sync(0xffffffffu, need);
+      if (m) {
+        const uint32_t k = ptr + __popc(m & lt);
+        const uint32_t wv = word(need ? k : ptr);
+        if (need) {
+          if (k >= nwords) bad = true;
+          x = (x << 16) | (k < nwords ? wv : 0u);
+        }
+        advance(__popc(m));
       }
-      ptr += __popc(m);
     }
     // escapes: phase 0 counts ones up to a zero, phase 1 reads k bits
     bool pend = active && (s == 0 || s == kNSym - 1);
@@ -202,8 +286,8 @@ __global__ void k_rans_decode(const DecChunk *__restrict__ chunks, int nchunks,
     for (int rnd = 0; rnd < 2 * kMaxEscBits + 2; ++rnd) {
       if (!__any_sync(0xffffffffu, pend)) break;
       if (pend) {
-        uint32_t slot = x & (kM - 1);
-        uint32_t bit = slot >> (kLogM - 1);
+        const uint32_t slot = x & (kM - 1);
+        const uint32_t bit = slot >> (kLogM - 1);
         x = (kM >> 1) * (x >> kLogM) + (slot & ((kM >> 1) - 1));
         if (phase == 0) {
           if (bit) { if (++kcnt > kMaxEscBits) { bad = true; } }
@@ -213,16 +297,17 @@ __global__ void k_rans_decode(const DecChunk *__restrict__ chunks, int nchunks,
           --kcnt;
         }
       }
-      bool need = pend && x < kRansL;
-      uint32_t m = __ballot_sync(0xffffffffu, need);
-      if (need) {
-        uint32_t k = ptr + __popc(m & lt);
-        uint32_t wv = 0;
-        if (k < nwords) wv = (uint32_t)wp[2 * k] | ((uint32_t)wp[2 * k + 1] << 8);
-        else bad = true;
-        x = (x << 16) | wv;
+      const bool need = pend && x < kRansL;
+      const uint32_t m = __ballot_sync(0xffffffffu, need);
+      if (m) {
+        const uint32_t k = ptr + __popc(m & lt);
+        const uint32_t wv = word(need ? k : ptr);
+        if (need) {
+          if (k >= nwords) bad = true;
+          x = (x << 16) | (k < nwords ? wv : 0u);
+        }
+        advance(__popc(m));
       }
-      ptr += __popc(m);
       if (pend && ((phase == 1 && kcnt == 0) || bad)) pend = false;
     }
     if (pend) bad = true;
@@ -231,15 +316,18 @@ __global__ void k_rans_decode(const DecChunk *__restrict__ chunks, int nchunks,
       if (s == 0) r = -(int)(v - 1) - kT - 1;
       else if (s == kNSym - 1) r = (int)(v - 1) + kT + 1;
       else r = s - kT - 1;
-      int val = ctr + r;
-      int q = ch.first + p;
+      const int val = ctr + r;
       if (step >= 0) {
-        int y, xx;
-        step_pos(w, step, q, y, xx);
-        outp[(int64_t)y * w + xx] = val;
+        const int yy = rr < ne ? 2 * y2 : 2 * y2 + 1;
+        const int xx = rr < ne ? ae + 4 * rr : ao + 4 * (rr - ne);
+        outp[(int64_t)yy * w + xx] = val;
       } else {
-        outp[q] = val;
+        outp[ch.first + p] = val;
       }
+    }
+    if (step >= 0) {
+      rr += nl;
+      while (rr >= pair) { rr -= pair; ++y2; }
     }
     if (__any_sync(0xffffffffu, bad)) break;
   }
@@ -400,17 +488,22 @@ __global__ void k_pack_index(const float *__restrict__ mu, const float *__restri
 
 // ---------------------------------------------------------------------------
 // Host launchers.
-void launch_cdf_bank(uint16_t *bank, cudaStream_t st) {
-  k_cdf_bank<<<kNTables * 32 / 256, 256, 0, st>>>(bank);
+void launch_cdf_bank(uint16_t *bank, uint16_t *coarse, cudaStream_t st) {
+  k_cdf_bank<<<kNTables * 32 / 256, 256, 0, st>>>(bank, coarse);
 }
 void launch_rans_decode(const DecChunk *chunks, int nchunks, const uint16_t *bank,
-                        const uint32_t *idx, int64_t idx_stride, int32_t *out,
-                        int64_t out_stride, int h, int w, int step, uint32_t *status,
-                        cudaStream_t st) {
+                        const uint16_t *coarse, const uint32_t *idx, int64_t idx_stride,
+                        int32_t *out, int64_t out_stride, int h, int w, int step,
+                        uint32_t *status, cudaStream_t st) {
   if (nchunks <= 0) return;
-  const int wpb = 4;
-  k_rans_decode<<<(nchunks + wpb - 1) / wpb, 32 * wpb, 0, st>>>(
-      chunks, nchunks, bank, idx, idx_stride, out, out_stride, h, w, step, status);
+  constexpr int smem = kNTables * kCoarse * 2;
+  static std::once_flag attr;
+  std::call_once(attr, [] {
+    cudaFuncSetAttribute(k_rans_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  });
+  const int wpb = 8;
+  k_rans_decode<<<(nchunks + wpb - 1) / wpb, 32 * wpb, smem, st>>>(
+      chunks, nchunks, bank, coarse, idx, idx_stride, out, out_stride, h, w, step, status);
 }
 void launch_rans_count_ops(const EncChunk *chunks, int nchunks, const uint32_t *idx,
                            const int32_t *vals, uint32_t *ops, cudaStream_t st) {

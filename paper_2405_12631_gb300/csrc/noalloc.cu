@@ -21,10 +21,11 @@
 namespace pw {
 
 // Scratch layout: [0, 256) status word, [256, 256 + 512 KiB) CDF table bank,
-// then kNoAllocMaxChunks decode descriptors.
+// its 64 KiB coarse level, then kNoAllocMaxChunks decode descriptors.
 constexpr int kNoAllocMaxChunks = 16384;
 constexpr size_t kBankBytes = (size_t)kNTables * (kNSym + 1) * sizeof(uint16_t);
-constexpr size_t kDescOff = 256 + kBankBytes;
+constexpr size_t kCoarseBytes = (size_t)kNTables * kCoarse * sizeof(uint16_t);
+constexpr size_t kDescOff = 256 + kBankBytes + kCoarseBytes;
 constexpr size_t kScratchBytes = kDescOff + (size_t)kNoAllocMaxChunks * sizeof(DecChunk);
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
@@ -115,15 +116,16 @@ extern "C" int pw_rans_decode_noalloc(void *cuda_stream, const uint8_t *payload,
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   uint32_t *status = reinterpret_cast<uint32_t *>(base);
   uint16_t *bank = reinterpret_cast<uint16_t *>(base + 256);
+  uint16_t *coarse = reinterpret_cast<uint16_t *>(base + 256 + kBankBytes);
   DecChunk *desc = reinterpret_cast<DecChunk *>(base + kDescOff);
   if (cudaMemsetAsync(status, 0, sizeof(uint32_t), st) != cudaSuccess) {
     set_last_error("pw_rans_decode_noalloc: cudaMemsetAsync failed");
     return PW_ECUDA;
   }
-  launch_cdf_bank(bank, st);
+  launch_cdf_bank(bank, coarse, st);
   k_noalloc_descs<<<1, 1024, 0, st>>>(payload, payload_bytes, nchunks, offset, nbytes, count,
                                       lanes, desc, status);
-  launch_rans_decode(desc, nchunks, bank, idx, 0, out, 0, 0, 0, -1, status, st);
+  launch_rans_decode(desc, nchunks, bank, coarse, idx, 0, out, 0, 0, 0, -1, status, st);
   uint32_t h = 0;
   cudaError_t e = cudaMemcpyAsync(&h, status, sizeof(h), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

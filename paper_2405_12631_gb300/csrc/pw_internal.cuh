@@ -20,6 +20,7 @@ constexpr uint32_t kM = 1u << kLogM;   // total frequency
 constexpr uint32_t kRansL = 1u << 16;  // lower end of the state interval
 constexpr int kNPhi = 16, kNJ = 128;
 constexpr int kNTables = kNPhi * kNJ;  // 2048 tables of kNSym + 1 entries
+constexpr int kCoarse = 16;            // coarse CDF entries per table (every 8th)
 constexpr int kMaxLanes = 32;
 constexpr int kMaxEscBits = 30;        // Exp-Golomb prefix length limit
 
