@@ -17,8 +17,10 @@ images, host wall clock around each call. roofline: the dominant kernel class
 from the library's own CUDA-event timing. cpu_baseline: the CPU oracle
 decoding a bounded sample (one 256x256 RGB crop of the workload).
 
-fp32_single_image: the plain FP32 GPU path decoding the same images one per
-call (its own FP32 streams, same q). serving: an open-loop run of the serving
+Precision: FP8 by default (E4M3 3x3 context convolutions, BF16 elsewhere);
+the other tensor-core class (BF16) is timed the same way under
+"bf16_batched". fp32_single_image: the plain FP32 GPU path decoding the same
+images one per call (its own FP32 streams, same q). serving: an open-loop run of the serving
 workload's first 200 requests (Poisson arrivals at 200/s, mixed sizes from
 256x256 to 2048x2048, gray/RGB) through the decode server, with p50/p99
 latency (submit -> decoded host image) and MPix/s.
@@ -234,6 +236,50 @@ def fp32_single_image(pw, local, imgs, qs, blob, stream_ptr):
            "path": "fp32 SIMT context model, one image per decode call"}
     m32.close()
     c32.close()
+    return res
+
+
+def batched_precision(pw, local, prec, imgs, qs, blob, stream_ptr, steps, warmup):
+    """The same batched, device-resident decode in another precision class
+    (its own streams; same images and q), timed the same way."""
+    import torch
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    c = pw.Codec(local, prec, stream=stream_ptr)
+    m = c.load_model(blob)
+    enc = [None] * len(imgs)
+    for q in QSTEPS:
+        idx = [i for i in range(len(imgs)) if qs[i] == q]
+        if idx:
+            for i, b in zip(idx, c.encode_batch(m, [imgs[i] for i in idx], q=q)):
+                enc[i] = b
+    lens = [len(b) for b in enc]
+    offs = np.cumsum([0] + [(n + 255) // 256 * 256 for n in lens])
+    host_all = np.zeros(int(offs[-1]), dtype=np.uint8)
+    for i, b in enumerate(enc):
+        host_all[offs[i]:offs[i] + lens[i]] = np.frombuffer(b, dtype=np.uint8)
+    dev_all = torch.from_numpy(host_all).to(dev)
+    ptrs = [dev_all.data_ptr() + int(offs[i]) for i in range(len(enc))]
+    out = torch.empty((len(enc), H, W, 3), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(warmup):
+        c.decode_batch_device(m, ptrs, lens, out.data_ptr(), (H, W, 3))
+    torch.cuda.synchronize()
+    times = []
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c.decode_batch_device(m, ptrs, lens, out.data_ptr(), (H, W, 3))
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = float(np.mean(times))
+    res = {"value": len(enc) * H * W / (ms / 1e3) / 1e6, "unit": "MPix/s", "ms_per_step": ms,
+           "bpp": 8.0 * sum(lens) / (len(enc) * H * W)}
+    m.close()
+    c.close()
     return res
 
 
@@ -453,6 +499,12 @@ def run_gpu(args):
                    "reasons": clocks["reasons"]},
         "wall_s_timed_region": t_wall,
     }
+    if world == 1 and not args.no_compare:
+        for p in ("fp8", "bf16"):
+            if p != args.precision:
+                line[f"{p}_batched"] = batched_precision(pw, local, p, imgs, qs, blob,
+                                                         stream.cuda_stream, args.steps,
+                                                         args.warmup)
     if not args.no_fp32 and world == 1:
         line["fp32_single_image"] = fp32_single_image(pw, local, imgs, qs, blob,
                                                       stream.cuda_stream)
@@ -473,12 +525,14 @@ def main():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=os.environ.get("PW_BENCH_PRECISION", "bf16"),
+    ap.add_argument("--precision", default=os.environ.get("PW_BENCH_PRECISION", "fp8"),
                     choices=["fp32", "bf16", "fp8"])
     ap.add_argument("--batch", type=int, default=BATCH,
                     help="images per step (24 = the benchmark workload; smaller for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip timing the other tensor-core precision class")
     ap.add_argument("--no-fp32", action="store_true",
                     help="skip the FP32 single-image comparison")
     ap.add_argument("--serve", type=int, default=200,
