@@ -19,7 +19,8 @@ decoding a bounded sample (one 256x256 RGB crop of the workload).
 
 Precision: FP8 by default (E4M3 3x3 context convolutions, BF16 elsewhere);
 the other tensor-core class (BF16) is timed the same way under
-"bf16_batched". fp32_single_image: the plain FP32 GPU path decoding the same
+"bf16_batched". gop: one 8-frame 1920x1080 GOP through pw_decode_gop (host in, host out).
+fp32_single_image: the plain FP32 GPU path decoding the same
 images one per call (its own FP32 streams, same q). serving: an open-loop run of the serving
 workload's first 200 requests (Poisson arrivals at 200/s, mixed sizes from
 256x256 to 2048x2048, gray/RGB) through the decode server, with p50/p99
@@ -283,6 +284,31 @@ def batched_precision(pw, local, prec, imgs, qs, blob, stream_ptr, steps, warmup
     return res
 
 
+def gop_run(pw, codec, blob_low, blob_high, reps: int):
+    """Video: one GOP of 8 synthetic 1920x1080 RGB frames (panned 1/f canvas +
+    sprites), identity-motion temporal lifting, 8 temporal bands coded as
+    images (low band with one model, the 7 high bands batched with another),
+    q = 8. Host stream in, host frames out; host wall clock per decode."""
+    import synthetic as S
+    frames = S.video_gop(1080, 1920, 8, seed=3)
+    ml, mh = codec.load_model(blob_low), codec.load_model(blob_high)
+    gs = codec.encode_gop(ml, mh, frames, q=8.0)
+    out = codec.decode_gop(ml, mh, gs, 8, (1080, 1920, 3))
+    mse = float(np.mean((out.astype(np.float64) - frames) ** 2))
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        codec.decode_gop(ml, mh, gs, 8, (1080, 1920, 3))
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.median(times))
+    ml.close()
+    mh.close()
+    return {"workload": "1 GOP x 8 frames 1920x1080 RGB, 3 temporal levels, q=8", "frames": 8,
+            "value": 8 * 1920 * 1080 / (ms / 1e3) / 1e6, "unit": "MPix/s",
+            "ms_per_gop": ms, "bpp": 8.0 * len(gs) / (8 * 1920 * 1080),
+            "psnr_db": 10 * np.log10(255.0 ** 2 / mse), "timing": "host wall clock, e2e"}
+
+
 def serving_run(pw, codec, model, n_req: int, rate: float, lanes: int, max_batch: int,
                 budget: int):
     """Open-loop serving: a Poisson stream of mixed-size decode requests.
@@ -508,6 +534,10 @@ def run_gpu(args):
     if not args.no_fp32 and world == 1:
         line["fp32_single_image"] = fp32_single_image(pw, local, imgs, qs, blob,
                                                       stream.cuda_stream)
+    if not args.no_gop and world == 1:
+        import synthetic as S
+        cfg = S.ModelConfig(levels=4, C=64, F=16, ll_mode=0)
+        line["gop"] = gop_run(pw, codec, blob, S.pack_blob(cfg, S.random_model(cfg, 1)), 3)
     if args.serve > 0 and world == 1:
         line["serving"] = serving_run(pw, codec, model, args.serve, 200.0, lanes=4,
                                       max_batch=8, budget=48 << 30)
@@ -533,6 +563,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip timing the other tensor-core precision class")
+    ap.add_argument("--no-gop", action="store_true", help="skip the video GOP leg")
     ap.add_argument("--no-fp32", action="store_true",
                     help="skip the FP32 single-image comparison")
     ap.add_argument("--serve", type=int, default=200,

@@ -105,3 +105,21 @@ def test_fp8_ar_ll_roundtrip(f8):
     img = S.gray_sinusoids(64, 96, seed=4)
     bs = f8.encode_image(gm, img, q=8.0)
     assert np.array_equal(f8.decode_symbols(gm, bs), f8.analyse(gm, img, q=8.0))
+
+
+def test_fp8_lossless_5_levels_12bit_exact(f8, pw):
+    """Lossless mode at the scale configuration's settings: 12-bit RGB,
+    integer lifting with 5 levels, RCT, FP8 context model. The GPU encode ->
+    decode is exact; a batch of two decodes like the single images; the
+    stream is smaller than the packed 12-bit samples (the weights are random,
+    so no particular compression ratio is expected)."""
+    cfg = S.ModelConfig(levels=5, C=64, ll_mode=0)
+    gm = f8.load_model(S.pack_blob(cfg, S.random_model(cfg, 2)))
+    imgs = [S.lossless_blobs(96, 160, seed=s) for s in (11, 12)]
+    streams = [f8.encode_image(gm, im, lossless=True, bitdepth=12) for im in imgs]
+    for im, bs in zip(imgs, streams):
+        assert np.array_equal(f8.decode_image(gm, bs), im)
+        assert len(bs) < im.size * 12 / 8
+    dec = f8.decode_batch(gm, streams)
+    for i, im in enumerate(imgs):
+        assert np.array_equal(dec[i], im)
