@@ -131,13 +131,13 @@ __global__ void k_cdf_bank(uint16_t *__restrict__ bank, uint16_t *__restrict__ c
 // DecChunk (ctx_kernels.cuh): data = nl u32 states then u16 words; count
 // symbols; first = index of its first symbol in the output list.
 
-// Number of the two u16 halves of w that are <= slot.
-__device__ __forceinline__ int cnt_le2(uint32_t w, uint32_t slot) {
-  return (int)((w & 0xFFFFu) <= slot) + (int)((w >> 16) <= slot);
-}
-__device__ __forceinline__ uint32_t u16_at(const uint4 &v, int i) {  // i in 0..7
-  const uint32_t w = (i >> 1) == 0 ? v.x : (i >> 1) == 1 ? v.y : (i >> 1) == 2 ? v.z : v.w;
-  return (i & 1) ? (w >> 16) : (w & 0xFFFFu);
+// SWAR compare of the two u16 entries of w against slot (< 2^15): with
+// s2 = (slot | 0x8000) in both halves, each half of s2 - w is
+// 0x8000 + slot - e, which lies in [0, 0xFFFF] for every entry e <= 2^15,
+// so no borrow crosses the halves and bit 15 of a half is set exactly when
+// e <= slot. Returns those two bits at positions 0 and 16.
+__device__ __forceinline__ uint32_t le2(uint32_t s2, uint32_t w) {
+  return ((s2 - w) >> 15) & 0x10001u;
 }
 // Two consecutive 16-bit words k, k + 1 of a chunk's word stream (0 past the
 // end), byte loads so that no alignment is assumed.
@@ -152,23 +152,30 @@ __device__ __forceinline__ uint32_t ld_words2(const uint8_t *wp, uint32_t k, uin
 // Symbol search: the largest s in [0, 126] with t[s] <= slot, in two levels:
 // the table's 16 coarse entries (every 8th, shared memory) give the block
 // b = s / 8, one 16-byte load gives its 8 entries. The entries are strictly
-// increasing with t[0] = 0 and t[127] = M > slot, so the counts below are
-// exactly that s. Returns s; lo = t[s], hi = t[s + 1].
+// increasing with t[0] = 0, t[127] = M = 2^15 > slot, and all are <= 2^15,
+// so the SWAR counts below are exactly that s. Returns s; lo = t[s],
+// hi = t[s + 1].
 __device__ __forceinline__ int cdf_search(const uint16_t *__restrict__ row,
                                           const uint16_t *s_crow, uint32_t slot, uint32_t &lo,
                                           uint32_t &hi) {
+  const uint32_t s2 = (slot | 0x8000u) * 0x10001u;
   const uint4 c0 = *reinterpret_cast<const uint4 *>(s_crow);
   const uint4 c1 = *reinterpret_cast<const uint4 *>(s_crow + 8);
-  const int b = cnt_le2(c0.x, slot) + cnt_le2(c0.y, slot) + cnt_le2(c0.z, slot) +
-                cnt_le2(c0.w, slot) + cnt_le2(c1.x, slot) + cnt_le2(c1.y, slot) +
-                cnt_le2(c1.z, slot) + cnt_le2(c1.w, slot) - 1;
+  uint32_t a = le2(s2, c0.x) + le2(s2, c0.y) + le2(s2, c0.z) + le2(s2, c0.w) + le2(s2, c1.x) +
+               le2(s2, c1.y) + le2(s2, c1.z) + le2(s2, c1.w);
+  const int b = (int)((a & 0xFFFFu) + (a >> 16)) - 1;
   const uint4 f = __ldg(reinterpret_cast<const uint4 *>(row + 8 * b));
-  const int i = cnt_le2(f.x, slot) + cnt_le2(f.y, slot) + cnt_le2(f.z, slot) +
-                cnt_le2(f.w, slot) - 1;
-  lo = u16_at(f, i);
-  // i == 7 implies b < 15 (t[127] = M > slot); the clamp keeps the read in
-  // the table either way
-  hi = (i < 7) ? u16_at(f, i + 1) : (uint32_t)s_crow[min(b + 1, kCoarse - 1)];
+  a = le2(s2, f.x) + le2(s2, f.y) + le2(s2, f.z) + le2(s2, f.w);
+  const int i = (int)((a & 0xFFFFu) + (a >> 16)) - 1;
+  // entries i and i + 1 of the block (entry 8 = next coarse entry; i == 7
+  // implies b < 15, the clamp keeps the read in the table either way)
+  const int wi = i >> 1;
+  const uint32_t nxt = s_crow[min(b + 1, kCoarse - 1)];
+  const uint32_t w0 = (wi & 2) ? ((wi & 1) ? f.w : f.z) : ((wi & 1) ? f.y : f.x);
+  const uint32_t w1 = (wi & 2) ? ((wi & 1) ? nxt : f.w) : ((wi & 1) ? f.z : f.y);
+  const uint32_t pair = (i & 1) ? __funnelshift_r(w0, w1, 16) : w0;
+  lo = pair & 0xFFFFu;
+  hi = pair >> 16;
   return 8 * b + i;
 }
 
@@ -329,7 +336,9 @@ __global__ void __launch_bounds__(256) k_rans_decode(
       rr += nl;
       while (rr >= pair) { rr -= pair; ++y2; }
     }
-    if (__any_sync(0xffffffffu, bad)) break;
+    // every loop is bounded, so a corrupt chunk only has to stop early
+    // eventually: vote every 32 iterations
+    if ((it & 31) == 31 && __any_sync(0xffffffffu, bad)) break;
   }
   if (lane < nl && x != kRansL) bad = true;
   if (lane == 0 && ptr != nwords) bad = true;
