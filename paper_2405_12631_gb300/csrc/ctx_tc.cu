@@ -176,6 +176,10 @@ __device__ __forceinline__ void mma_fp8(uint32_t d, uint64_t a, uint64_t b, uint
       "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 
+// shared memory: barriers [0, 1024), epilogue constants [1024, 4096)
+// (5 x NCTA floats), then the resident weights and the stages
+constexpr int kConvHeader = 4096;
+
 constexpr int kEpiWarps = 8;                    // two per TMEM lane quadrant
 constexpr int kConvThreads = 64 + 32 * kEpiWarps;
 constexpr int kAcc = 4;                         // TMEM accumulator buffers
@@ -194,7 +198,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   uint64_t *wbar = acce + kAcc;                              // [1]
   volatile int *s_abort = reinterpret_cast<volatile int *>(wbar + 1);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 256);
-  uint8_t *wsm = smem + 1024;
+  // per-column epilogue constants of this CTA's N block (loaded once):
+  // bias, accumulator scale (F8), FP8 output scale, head weights [2][NCTA]
+  float *s_bias = reinterpret_cast<float *>(smem + 1024);
+  float *s_wsc = s_bias + NCTA;
+  float *s_osc = s_wsc + NCTA;
+  float *s_wh = s_osc + NCTA;
+  uint8_t *wsm = smem + kConvHeader;
   uint8_t *stg = wsm + ((a.w_bytes + 1023) / 1024) * 1024;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -203,6 +213,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   const int nctas = gridDim.x / a.nb;
   constexpr uint32_t kCols = NCTA * kAcc <= 32 ? 32 : NCTA * kAcc;  // power of two
 
+  {
+    const int nb0 = (blockIdx.x % a.nb) * NCTA;
+    // FP8 output scale per output channel: the LSTM's outputs are channels
+    // (4 gate columns each), the other epilogues' outputs are columns
+    const int nosc = (EPI == TE_LSTM) ? NCTA / 4 : NCTA;
+    const int osc0 = (EPI == TE_LSTM) ? nb0 / 4 : nb0;
+    for (int j = threadIdx.x; j < NCTA; j += blockDim.x) {
+      s_bias[j] = a.bias[nb0 + j];
+      s_wsc[j] = F8 ? a.w_scale[nb0 + j] : 1.f;
+      s_osc[j] = (a.out8_scale && j < nosc) ? a.out8_scale[osc0 + j] : 0.f;
+      if (EPI == TE_HEAD) { s_wh[j] = a.wh[j]; s_wh[NCTA + j] = a.wh[NCTA + j]; }
+    }
+  }
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
     for (int i = 0; i < kAcc; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], kEpiWarps); }
@@ -381,10 +404,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 
       if (F8) {
 #pragma unroll
-        for (int j = 0; j < NH; ++j) v[j] = fmaf(v[j], a.w_scale[n0 + j], a.bias[n0 + j]);
+        for (int j = 0; j < NH; ++j) v[j] = fmaf(v[j], s_wsc[col0 + j], s_bias[col0 + j]);
       } else {
 #pragma unroll
-        for (int j = 0; j < NH; ++j) v[j] += a.bias[n0 + j];
+        for (int j = 0; j < NH; ++j) v[j] += s_bias[col0 + j];
       }
       if (!valid) continue;
       if (EPI == TE_STORE) {
@@ -409,7 +432,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           for (int g = 0; g < NH / 16; ++g) {
             float f[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) f[e] = v[16 * g + e] * a.out8_scale[n0 + 16 * g + e];
+            for (int e = 0; e < 16; ++e) f[e] = v[16 * g + e] * s_osc[col0 + 16 * g + e];
             store_fp8x16(a.out8 + (((int64_t)p * a.out8_G16 + (n0 >> 4) + g) * hw + pix) * 16, f);
           }
         }
@@ -436,7 +459,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           for (int g = 0; g < NH / 64; ++g) {
             float f[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) f[e] = hv[16 * g + e] * a.out8_scale[ch0 + 16 * g + e];
+            for (int e = 0; e < 16; ++e) f[e] = hv[16 * g + e] * s_osc[col0 / 4 + 16 * g + e];
             store_fp8x16(a.out8 + (((int64_t)p * a.out8_G16 + (ch0 >> 4) + g) * hw + pix) * 16, f);
           }
         }
@@ -450,8 +473,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const float z = v[8 * g + e] + rv[e];
-              mu = fmaf(a.wh[8 * g + e], z, mu);
-              rho = fmaf(a.wh[NCTA + 8 * g + e], z, rho);
+              mu = fmaf(s_wh[8 * g + e], z, mu);
+              rho = fmaf(s_wh[NCTA + 8 * g + e], z, rho);
             }
           }
           int qi;
@@ -762,7 +785,7 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   a.stage_bytes = (uint32_t)a.halo_x * a.halo_y * cv.kb * esz;
   a.w_bytes = (uint32_t)(cv.ks * cv.ks) * cv.cin * cv.ncta * esz;
   a.wt = cv.w; a.bias = cv.b; a.w_scale = cv.sw; a.err = err;
-  const size_t fixed = 1024 + (a.w_bytes + 1023) / 1024 * 1024;
+  const size_t fixed = kConvHeader + (a.w_bytes + 1023) / 1024 * 1024;
   const size_t maxsm = 227 * 1024;
   int stages = (int)((maxsm - fixed) / a.stage_bytes);
   stages = stages > 6 ? 6 : stages;
