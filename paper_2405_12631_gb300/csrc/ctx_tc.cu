@@ -392,10 +392,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       fence_after();
       float v[NH];
       const uint32_t taddr = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * NCTA + col0);
-      if (work) {
-#pragma unroll
-        for (int ch = 0; ch < NH / 16; ++ch) tmem_ld16(taddr + 16 * ch, v + 16 * ch);
-      }
+      if (work) tmem_ld<NH>(taddr, v);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce[acc]);
