@@ -63,13 +63,16 @@ __device__ __forceinline__ void acc_set(const PlaneAcc &a, int p, int y, int x, 
 // null when the step has no CNN), the linear part and the output of one
 // 16 x 16 tile; thread t handles output (t / 16, t % 16). in: the 22 x 22
 // input region (origin y0 - 3, x0 - 3).
+// rout (optional): the CNN residual of the tile's outputs, already computed.
 __device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int y0, int x0,
                                             const float *in, const float *a2, const float *w3t,
-                                            const float *b3) {
+                                            const float *b3, const float *rout = nullptr) {
   const int t = threadIdx.x;
   const int ly = t / LT, lx = t % LT;
   float r_out = 0.f;
-  if (a2) {
+  if (rout) {
+    r_out = rout[t];
+  } else if (a2) {
     float v = b3[0];
     for (int tap = 0; tap < 9; ++tap) {
       float xv[LF], w[LF];
@@ -200,34 +203,56 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
 }
 
 // ---------------------------------------------------------------------------
-// Lifting step with the middle CNN layer (conv3x3 16 -> 16, 89 % of the
-// CNN's FLOPs) on the tensor cores: BF16 operands, FP32 accumulation in
-// tensor memory. Layers 1 and 3, the linear part and the output stay FP32.
+// Lifting step with the CNN's second and third layers (conv3x3 16 -> 16 and
+// 16 -> 1, 95 % of its FLOPs) on the tensor cores: BF16 operands, FP32
+// accumulation in tensor memory. Layer 1, the linear part and the output
+// stay FP32.
 //
-// Layer-2 positions of the tile's 18 x 18 region are the GEMM rows, laid out
-// with a row stride of RS = 24 positions: output row m = r * RS + c. Layer 1
-// is stored with the same row stride, so tap (dy, dx) of row m reads layer-1
-// position m + dy * RS + dx: each tap is one MMA per 128-row block whose A
-// operand is the layer-1 slab shifted by a constant (columns c >= 18 are
-// padding and never read back). A: [2 channel groups][kA positions][8] BF16
-// (K-major core matrices, no swizzle); B: [tap][2][16 outputs][8].
-constexpr int kRS = 24;                   // row stride of the layer-1/2 regions
-constexpr int kMT = 4;                    // 128-row MMA blocks (18 * 24 = 432 rows)
+// Rows of every GEMM are positions of a region laid out with a row stride of
+// RS = 24 positions: row m = r * RS + c. Layer 1 (20 x 20 region) and layer 2
+// (18 x 18) are stored as BF16 slabs with that stride, so tap (dy, dx) of row
+// m reads position m + dy * RS + dx of the layer below: each tap is one MMA
+// per 128-row block whose A operand is the slab shifted by a constant
+// (columns c >= 18, resp. 16, are padding whose results are never used).
+// Slabs: [2 channel groups][positions][8] BF16 (K-major core matrices, no
+// swizzle); B: [tap][2][16 outputs][8] (layer 3: output 0 only, rest zero).
+constexpr int kRS = 24;                   // row stride of the regions
+constexpr int kMT = 4;                    // layer-2 blocks (18 * 24 = 432 rows)
+constexpr int kMT3 = 3;                   // layer-3 blocks (16 * 24 = 384 rows)
 constexpr int kA = 576;                   // layer-1 positions kept (> 511 + 2 * 24 + 2)
+constexpr int kA2 = 448;                  // layer-2 positions kept (> 383 + 2 * 24 + 2)
 
 struct LiftTcSmem {
   alignas(128) __nv_bfloat16 a1[2 * kA * 8];
+  alignas(128) __nv_bfloat16 a2[2 * kA2 * 8];
   alignas(128) __nv_bfloat16 w2[9 * 2 * LF * 8];
+  alignas(128) __nv_bfloat16 w3[9 * 2 * LF * 8];
   alignas(16) float in[LI * LI];
-  alignas(16) float a2[L2 * L2 * LF];
+  alignas(16) float rout[LT * LT];
   alignas(16) float w1t[9 * LF];
-  alignas(16) float w3t[9 * LF];
   alignas(16) float b1[LF];
   alignas(16) float b2[LF];
-  alignas(16) float b3[4];
   alignas(8) uint64_t bar;
   uint32_t tmem;
+  float b3;
 };
+
+// Bounded wait of every thread for completion phase `parity` of the MMA
+// barrier (lane 0 polls, the rest follow); false on expiry.
+__device__ __forceinline__ bool lift_mma_wait(uint64_t *bar, uint32_t parity) {
+  const int lane = threadIdx.x & 31;
+  int ok = 1;
+  if (lane == 0) {
+    const long long t0 = clock64();
+    while (!mbar_try(bar, parity))
+      if (clock64() - t0 > kWaitCycles) { ok = 0; break; }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok && lane != 0) while (!mbar_try(bar, parity)) {}
+  __syncwarp();
+  fence_after();
+  return ok != 0;
+}
 
 __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
   extern __shared__ __align__(1024) uint8_t lsm_raw[];
@@ -236,7 +261,8 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
   const int p = blockIdx.z;
   const int tiles_x = (a.W + LT - 1) / LT;
   const int y0 = (blockIdx.x / tiles_x) * LT, x0 = (blockIdx.x % tiles_x) * LT;
-  constexpr uint32_t kCols = kMT * LF;    // 64 TMEM columns: 4 blocks x 16 outputs
+  // TMEM columns: layer 2 in [0, 64) (4 blocks x 16), layer 3 in [64, 112)
+  constexpr uint32_t kCols = 128;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -255,18 +281,22 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
   for (int e = t; e < LF * 9; e += 256) {
     const int c = e / 9, tap = e % 9;  // source [c][tap]
     S.w1t[tap * LF + c] = a.net.w1[e];
-    S.w3t[tap * LF + c] = a.net.w3[e];
   }
   for (int e = t; e < LF * LF * 9; e += 256) {
     const int c = e / (LF * 9), ci = (e / 9) % LF, tap = e % 9;  // source [c][ci][tap]
-    S.w2[((tap * 2 + (ci >> 3)) * LF + c) * 8 + (ci & 7)] = __float2bfloat16_rn(a.net.w2[e]);
+    const int o = ((tap * 2 + (ci >> 3)) * LF + c) * 8 + (ci & 7);
+    S.w2[o] = __float2bfloat16_rn(a.net.w2[e]);
+    // layer 3: output 0 = the CNN's single output channel, ci = e / 9 here
+    S.w3[o] = __float2bfloat16_rn(c == 0 ? a.net.w3[(e / 9) % LF * 9 + tap] : 0.f);
   }
   if (t < LF) { S.b1[t] = a.net.b1[t]; S.b2[t] = a.net.b2[t]; }
-  if (t == 0) S.b3[0] = a.net.b3[0];
+  if (t == 0) S.b3 = a.net.b3[0];
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tbase = S.tmem;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(LF >> 3) << 17) |
+                         ((uint32_t)(128 >> 4) << 24);
 
   // layer 1 on the 20 x 24 region (origin y0 - 2, x0 - 2), one position and
   // one group of 8 channels per item; padding positions are written as 0
@@ -299,8 +329,6 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
   // layer 2: 4 blocks x 9 taps MMAs (M = 128, N = 16, K = 16), one thread
   if (t == 0) {
     fence_after();
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(LF >> 3) << 17) |
-                           ((uint32_t)(128 >> 4) << 24);
     const uint32_t abase = smem_u32(S.a1), bbase = smem_u32(S.w2);
 #pragma unroll
     for (int i = 0; i < kMT; ++i) {
@@ -314,20 +342,10 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
     }
     mma_commit(&S.bar);
   }
-  // bounded wait for the MMAs (lane 0 of each warp, then the whole warp)
-  int ok = 1;
-  if (lane == 0) {
-    const long long t0 = clock64();
-    while (!mbar_try(&S.bar, 0))
-      if (clock64() - t0 > kWaitCycles) { ok = 0; break; }
-  }
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  if (ok && lane != 0) while (!mbar_try(&S.bar, 0)) {}
-  __syncwarp();
-  fence_after();
-  if (!ok && lane == 0) atomicOr(a.status, kStTimeout);
-  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of blocks w / 4 and
-  // w / 4 + 2 -> tanh(acc + b2) into the 18 x 18 layer-2 region
+  bool ok = lift_mma_wait(&S.bar, 0);
+  // layer-2 epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 of blocks
+  // w / 4 and w / 4 + 2 -> tanh(acc + b2) (0 outside the image and in the
+  // padding rows / columns) into the layer-2 slab
   if (ok) {
     const int q = warp & 3;
 #pragma unroll
@@ -336,19 +354,51 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
       float v[LF];
       tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(i * LF), v);
       const int m = i * 128 + 32 * q + lane;
-      const int r2 = m / kRS, c2 = m % kRS;
-      if (r2 < L2 && c2 < L2) {
+      if (m < kA2) {
+        const int r2 = m / kRS, c2 = m % kRS;
         const int yy = y0 - 1 + r2, xx = x0 - 1 + c2;
-        const bool inside = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-        float4 *dst = reinterpret_cast<float4 *>(S.a2 + (r2 * L2 + c2) * LF);
+        const bool live = r2 < L2 && c2 < L2 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        __align__(16) __nv_bfloat16 hb[LF];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-          dst[k] = inside ? make_float4(tanh_fast(v[4 * k] + S.b2[4 * k]),
-                                        tanh_fast(v[4 * k + 1] + S.b2[4 * k + 1]),
-                                        tanh_fast(v[4 * k + 2] + S.b2[4 * k + 2]),
-                                        tanh_fast(v[4 * k + 3] + S.b2[4 * k + 3]))
-                          : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < LF; ++k)
+          hb[k] = __float2bfloat16_rn(live ? tanh_fast(v[k] + S.b2[k]) : 0.f);
+        *reinterpret_cast<uint4 *>(S.a2 + (size_t)m * 8) = *reinterpret_cast<const uint4 *>(hb);
+        *reinterpret_cast<uint4 *>(S.a2 + ((size_t)kA2 + m) * 8) =
+            *reinterpret_cast<const uint4 *>(hb + 8);
       }
+    }
+  }
+  fence_proxy_async();
+  fence_before();
+  __syncthreads();
+  fence_after();
+
+  // layer 3: 3 blocks x 9 taps MMAs into TMEM columns 64 + 16 i
+  if (t == 0 && ok) {
+    const uint32_t abase = smem_u32(S.a2), bbase = smem_u32(S.w3);
+#pragma unroll
+    for (int i = 0; i < kMT3; ++i) {
+#pragma unroll
+      for (int tap = 0; tap < 9; ++tap) {
+        const uint32_t arow = (uint32_t)(i * 128 + (tap / 3) * kRS + tap % 3);
+        const uint64_t ad = sdesc(abase + arow * 16u, kA2 * 16u, 128u);
+        const uint64_t bd = sdesc(bbase + (uint32_t)tap * (2 * LF * 16), LF * 16u, 128u);
+        mma_bf16(tbase + (uint32_t)(kMT * LF + i * LF), ad, bd, idesc, tap > 0 ? 1u : 0u);
+      }
+    }
+    mma_commit(&S.bar);
+  }
+  if (ok) ok = lift_mma_wait(&S.bar, 1);
+  if (!ok && lane == 0) atomicOr(a.status, kStTimeout);
+  // layer-3 epilogue: column 0 of each block -> residual of output (r, c)
+  if (ok) {
+    const int q = warp & 3;
+    for (int i = warp >> 2; i < kMT3; i += 2) {
+      float v[LF];
+      tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(kMT * LF + i * LF), v);
+      const int m = i * 128 + 32 * q + lane;
+      const int r = m / kRS, c = m % kRS;
+      if (r < LT && c < LT) S.rout[r * LT + c] = v[0] + S.b3;
     }
   }
   fence_before();
@@ -358,7 +408,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols));
   }
-  if (ok) lift_finish(a, p, y0, x0, S.in, S.a2, S.w3t, S.b3);
+  if (ok) lift_finish(a, p, y0, x0, S.in, nullptr, nullptr, nullptr, S.rout);
 }
 
 // Component planes [B][nc][Hp][Wp] -> interleaved samples (crop, inverse
