@@ -45,9 +45,12 @@ struct TcWeights {
   };
   Conv gates;
   Conv s0_in, s0_w1, s0_w2, s0_w3, s0_w4;        // sb set, step 0
-  Conv sk_z[3], sk_c1[3], sk_c2[3];             // sb set, steps 1..3
+  // step 1: in_ = 1x1 z = Win l + bin (run on the step-1 positions only),
+  // w1 = the composite 1x1 W1 Win, W1 bin + b1 (u = lrelu(w1 l), there is no
+  // nonlinearity between the two 1x1 layers)
+  Conv sk_c1[3], sk_c2[3];                      // sb set, steps 1..3
   Conv l0_in, l0_w1, l0_w2, l0_w3, l0_w4;       // ll set
-  Conv lk_z[3], lk_c1[3], lk_c2[3];
+  Conv lk_c1[3], lk_c2[3];
   // steps 2-4 with the masked input conv folded into the 1x1: zt = 1x1 over
   // [l (C channels), T (32 channels: the 9 masked neighbour values, each
   // split into a BF16 high and low part, then zero padding)]; the bias
@@ -884,24 +887,37 @@ int Model::ensure_tc() {
     return s;
   auto set = [&](const std::string &ns, TcWeights::Conv &in_, TcWeights::Conv &w1,
                  TcWeights::Conv &w2, TcWeights::Conv &w3, TcWeights::Conv &w4,
-                 TcWeights::Conv *kz, TcWeights::Conv *k1, TcWeights::Conv *k2) -> int {
+                 TcWeights::Conv *k1, TcWeights::Conv *k2) -> int {
     int r;
     const std::string p = ns + ".s0.";
-    if ((r = pack_conv(*t, in_, H(p + "win"), H(p + "bin"), C, C, 1, C))) return r;
-    if ((r = pack_conv(*t, w1, H(p + "w1"), H(p + "b1"), C, C, 1, C))) return r;
+    const std::vector<float> &win = H(p + "win"), &bin = H(p + "bin"), &wa = H(p + "w1"),
+                             &ba = H(p + "b1");
+    if ((r = pack_conv(*t, in_, win, bin, C, C, 1, C))) return r;
+    {
+      std::vector<float> wc((size_t)C * C), bc(C);
+      for (int c = 0; c < C; ++c) {
+        double bacc = ba[c];
+        for (int k = 0; k < C; ++k) bacc += (double)wa[(size_t)c * C + k] * bin[k];
+        bc[c] = (float)bacc;
+        for (int j = 0; j < C; ++j) {
+          double acc = 0.0;
+          for (int k = 0; k < C; ++k) acc += (double)wa[(size_t)c * C + k] * win[(size_t)k * C + j];
+          wc[(size_t)c * C + j] = (float)acc;
+        }
+      }
+      if ((r = pack_conv(*t, w1, wc, bc, C, C, 1, C))) return r;
+    }
     if ((r = pack_conv(*t, w2, H(p + "w2"), H(p + "b2"), C, C, 1, C))) return r;
     if ((r = pack_conv(*t, w3, H(p + "w3"), H(p + "b3"), 2 * C, C, 1, 2 * C))) return r;
     if ((r = pack_conv(*t, w4, H(p + "w4"), H(p + "b4"), C, 2 * C, 1, C))) return r;
     for (int k = 1; k < 4; ++k) {
       const std::string q = ns + ".s" + std::to_string(k) + ".";
-      if ((r = pack_conv(*t, kz[k - 1], H(q + "wz"), H(q + "bz"), C, 2 * C, 1, C))) return r;
       if ((r = pack_conv(*t, k1[k - 1], H(q + "w1"), H(q + "b1"), C, C, 3, C))) return r;
       if ((r = pack_conv(*t, k2[k - 1], H(q + "w2"), H(q + "b2"), C, C, 3, C))) return r;
     }
     return PW_OK;
   };
-  if ((s = set("sb", t->s0_in, t->s0_w1, t->s0_w2, t->s0_w3, t->s0_w4, t->sk_z, t->sk_c1,
-               t->sk_c2)))
+  if ((s = set("sb", t->s0_in, t->s0_w1, t->s0_w2, t->s0_w3, t->s0_w4, t->sk_c1, t->sk_c2)))
     return s;
   // Steps 2-4: z = Wz [a; l] + bz with a = Wa * (m s) + ba is linear in a,
   // so z = Wz_l l + sum_tap (Wz_a Wa[:, tap]) (m s)(tap) + (Wz_a ba + bz):
@@ -937,8 +953,7 @@ int Model::ensure_tc() {
   if ((s = fold("sb", t->sk_zt))) return s;
   if (ll_mode == 0 && (s = fold("ll", t->lk_zt))) return s;
   if (ll_mode == 0 &&
-      (s = set("ll", t->l0_in, t->l0_w1, t->l0_w2, t->l0_w3, t->l0_w4, t->lk_z, t->lk_c1,
-               t->lk_c2)))
+      (s = set("ll", t->l0_in, t->l0_w1, t->l0_w2, t->l0_w3, t->l0_w4, t->lk_c1, t->lk_c2)))
     return s;
   tc = t.release();
   return PW_OK;
@@ -1219,10 +1234,8 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
                           &c2 = ll ? W.l0_w2 : W.s0_w2, &c3 = ll ? W.l0_w3 : W.s0_w3,
                           &c4 = ll ? W.l0_w4 : W.s0_w4;
     TcConvArgs a{};
-    a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
-    if ((s = conv(cin_, l, G, 0, a, 0))) return s;                 // z = 1x1(l)
-    a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
-    if ((s = conv(c1, t.Z, G, 0, a, 0))) return s;                 // u = lrelu(1x1 z)
+    a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
+    if ((s = conv(c1, l, G, 0, a, 0))) return s;                   // u = lrelu(W1 Win l + .)
     // Everything after the depthwise conv is per position and only the
     // step-1 positions' parameters are used: run it on those alone, in the
     // compact layout (hc row pairs x wc positions per pair).
@@ -1240,10 +1253,13 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     {
       ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * cpix * 9 * C, cpix * 2.0 * C * 4);
       k_dw3x3_compact<<<grid_for((int64_t)P * n0 * G), 256, 0, st>>>(
-          t.U, t.Z, n.wdw, n.bdw, t.Vc, t.Zc, P, h, w, C, 0, n0, chw);
+          t.U, l, n.wdw, n.bdw, t.Vc, t.Zc, P, h, w, C, 0, n0, chw);  // Zc <- l gathered
       ctx->launches += 1;
     }
-    a = TcConvArgs{}; a.epi = TE_STORE; a.out = t.Z2c; a.out_G = G; a.res = t.Zc; a.res_G = G;
+    // the block input z = Win l + bin on the step-1 positions (compact, in Z)
+    a = TcConvArgs{}; a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
+    if ((s = cconv(cin_, t.Zc, G, a))) return s;
+    a = TcConvArgs{}; a.epi = TE_STORE; a.out = t.Z2c; a.out_G = G; a.res = t.Z; a.res_G = G;
     if ((s = cconv(c2, t.Vc, G, a))) return s;                     // z2 = z + 1x1(v)
     a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U2c; a.out_G = 2 * G;
     if ((s = cconv(c3, t.Z2c, G, a))) return s;                    // u2 = lrelu(1x1 z2)
@@ -1269,6 +1285,7 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   }
   TcConvArgs a{};
   a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
+  // FP8: the residual-block input also feeds conv 1 as E4M3
   if (f8) { a.out8 = t.Z8; a.out8_G16 = G16; a.out8_scale = zsc; }
   {
     // z = 1x1 over [l, T]: K-blocks of 32 channels, the first C / 32 from l
