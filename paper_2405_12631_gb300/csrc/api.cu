@@ -54,7 +54,7 @@ struct Plan {
   Workspace ws;
   // decode
   DevBuf d_chunks, d_tpl, d_deltas, d_ptrs, d_lens, d_stage, d_out;
-  HostBuf h_stage, h_small;
+  HostBuf h_stage, h_small, h_out;
   std::vector<int64_t> gbase;   // decode descriptor block of each group
   // encode
   DevBuf d_enc, d_ops, d_scratch, d_states, d_nwords, d_outoff, d_payload, d_img;
@@ -383,16 +383,37 @@ int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const s
                       img, row, st);
   }
   bump(ctx);
+  // host outputs: one copy into pinned staging, then host memcpy (pageable
+  // destinations would make the DMA go through the driver's bounce buffer)
+  bool any_host = false;
+  for (int b = 0; b < B; ++b) any_host = any_host || !out[b].is_device;
   if (!direct) {
     for (int b = 0; b < B; ++b) {
+      if (!out[b].is_device) continue;
       const int64_t rs = out[b].stride_bytes ? out[b].stride_bytes : row;
       PW_CUDA_TRY(cudaMemcpy2DAsync(out[b].data, rs, (uint8_t *)dst + b * img, row, row, g.H,
-                                    out[b].is_device ? cudaMemcpyDeviceToDevice
-                                                     : cudaMemcpyDeviceToHost,
-                                    st));
+                                    cudaMemcpyDeviceToDevice, st));
+    }
+    if (any_host) {
+      if ((s = pl->h_out.ensure((size_t)img * B))) return s;
+      PW_CUDA_TRY(cudaMemcpyAsync(pl->h_out.p, dst, (size_t)img * B, cudaMemcpyDeviceToHost, st));
     }
   }
-  return check_status(ctx, &pl->ws);
+  if ((s = check_status(ctx, &pl->ws))) return s;
+  if (!direct && any_host) {
+    const uint8_t *hp = static_cast<const uint8_t *>(pl->h_out.p);
+    for (int b = 0; b < B; ++b) {
+      if (out[b].is_device) continue;
+      const int64_t rs = out[b].stride_bytes ? out[b].stride_bytes : row;
+      if (rs == row) {
+        std::memcpy(out[b].data, hp + b * img, (size_t)img);
+      } else {
+        for (int y = 0; y < g.H; ++y)
+          std::memcpy((uint8_t *)out[b].data + y * rs, hp + b * img + y * row, (size_t)row);
+      }
+    }
+  }
+  return PW_OK;
 }
 
 // --------------------------------------------------------------------------
