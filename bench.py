@@ -539,7 +539,7 @@ def run_gpu(args):
         cfg = S.ModelConfig(levels=4, C=64, F=16, ll_mode=0)
         line["gop"] = gop_run(pw, codec, blob, S.pack_blob(cfg, S.random_model(cfg, 1)), 3)
     if args.serve > 0 and world == 1:
-        line["serving"] = serving_run(pw, codec, model, args.serve, 200.0, lanes=4,
+        line["serving"] = serving_run(pw, codec, model, args.serve, 200.0, lanes=16,
                                       max_batch=8, budget=48 << 30)
     if not args.no_cpu and world == 1:
         px, dt = cpu_oracle_decode_sample(256)

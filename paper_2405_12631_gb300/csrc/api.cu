@@ -17,6 +17,24 @@ void set_last_error(const std::string &s) { g_last_error = s; }
 
 static inline void bump(pw_ctx *ctx, int n = 1) { ctx->launches += (uint64_t)n; }
 
+// Device buffer of a plan that grows on demand, from the context's
+// stream-ordered pool.
+struct PoolBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  cudaStream_t st = nullptr;
+  int ensure(size_t n) {
+    if (n <= cap) return PW_OK;
+    pool_free(p, st);
+    p = nullptr;
+    cap = 0;
+    if (pool_alloc(&p, n ? n : 1, st) != PW_OK) return PW_ENOMEM;
+    cap = n;
+    return PW_OK;
+  }
+  ~PoolBuf() { pool_free(p, st); }
+};
+
 // Device buffer that grows on demand.
 struct DevBuf {
   void *p = nullptr;
@@ -53,11 +71,16 @@ struct Plan {
   int B = 0;
   Workspace ws;
   // decode
-  DevBuf d_chunks, d_tpl, d_deltas, d_ptrs, d_lens, d_stage, d_out;
+  PoolBuf d_chunks, d_tpl, d_deltas, d_ptrs, d_lens, d_stage, d_out;
   HostBuf h_stage, h_small, h_out;
   std::vector<int64_t> gbase;   // decode descriptor block of each group
   // encode
-  DevBuf d_enc, d_ops, d_scratch, d_states, d_nwords, d_outoff, d_payload, d_img;
+  PoolBuf d_enc, d_ops, d_scratch, d_states, d_nwords, d_outoff, d_payload, d_img;
+  void set_stream(cudaStream_t s) {
+    for (PoolBuf *b : {&d_chunks, &d_tpl, &d_deltas, &d_ptrs, &d_lens, &d_stage, &d_out, &d_enc,
+                       &d_ops, &d_scratch, &d_states, &d_nwords, &d_outoff, &d_payload, &d_img})
+      b->st = s;
+  }
 };
 
 struct PlanCache {
@@ -91,9 +114,10 @@ static int get_plan(pw_ctx *ctx, Model &m, const Geometry &g, int B, const char 
   p->key = key;
   p->g = g;
   p->B = B;
+  p->set_stream(ctx->stream);
   int s = m.prepare(ctx->precision);
   if (s != PW_OK) return s;
-  s = p->ws.alloc(g, B * g.nc, m.C, params, ctx->precision);
+  s = p->ws.alloc(g, B * g.nc, m.C, params, ctx->precision, ctx->stream);
   if (s != PW_OK) return s;
   if (!strcmp(kind, "dec") || !strcmp(kind, "sym")) {
     // decode descriptor layout: group blocks of P x count
@@ -119,7 +143,9 @@ static int get_plan(pw_ctx *ctx, Model &m, const Geometry &g, int B, const char 
       tpl[c].lanes = t.lanes;
     }
     if ((s = p->d_tpl.ensure(std::max(nck, 1) * sizeof(TplDev)))) return s;
-    if (nck) cudaMemcpy(p->d_tpl.p, tpl.data(), nck * sizeof(TplDev), cudaMemcpyHostToDevice);
+    if (nck)
+      cudaMemcpyAsync(p->d_tpl.p, tpl.data(), nck * sizeof(TplDev), cudaMemcpyHostToDevice,
+                      ctx->stream);
     if ((s = p->d_deltas.ensure(2 * B * sizeof(float)))) return s;
     if ((s = p->d_ptrs.ensure(B * sizeof(void *)))) return s;
     if ((s = p->d_lens.ensure(B * sizeof(uint64_t)))) return s;

@@ -9,6 +9,7 @@
 // on the fully known latent (each step's net masks the positions of later
 // steps, so it sees exactly what the decoder sees) and rANS-encodes.
 #include <algorithm>
+#include <mutex>
 #include <cstring>
 
 #include "codec.h"
@@ -69,9 +70,47 @@ void Geometry::build(int H_, int W_, int nc_, int levels_, int colour_, int bitd
 }
 
 // ---------------------------------------------------------------------------
-int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec) {
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pools[64] = {};
+
+static cudaMemPool_t device_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;  // keep freed memory in the pool
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
+int pool_alloc(void **p, size_t n, cudaStream_t st) {
+  *p = nullptr;
+  cudaMemPool_t pool = device_pool();
+  if (!pool || cudaMallocFromPoolAsync(p, n ? n : 1, pool, st) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    set_last_error("device allocation failed");
+    return PW_ENOMEM;
+  }
+  return PW_OK;
+}
+
+void pool_free(void *p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec, cudaStream_t st) {
   const bool bf16 = prec != PW_PREC_FP32;
   release();
+  stream = st;
   P = P_;
   const int64_t pe = (int64_t)P * g.Hp * g.Wp;
   const int64_t big = (int64_t)P * g.sh.back() * g.sw.back();  // largest subband
@@ -97,11 +136,13 @@ int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec) {
   }
   int64_t tot = 0;
   for (auto &p : parts) tot += p.second;
-  if (cudaMalloc(&base, (size_t)tot) != cudaSuccess) {
+  void *b = nullptr;
+  if (pool_alloc(&b, (size_t)tot, stream) != PW_OK) {
     base = nullptr;
     set_last_error("workspace allocation failed");
     return PW_ENOMEM;
   }
+  base = static_cast<uint8_t *>(b);
   bytes = (size_t)tot;
   int64_t o = 0;
   for (auto &p : parts) { *p.first = base + o; o += p.second; }
@@ -126,7 +167,7 @@ int64_t Workspace::estimate(const Geometry &g, int P, int C, bool params, int pr
 
 void Workspace::release() {
   if (tc) tc_workspace_free(this);
-  if (base) cudaFree(base);
+  pool_free(base, stream);
   base = nullptr;
   bytes = 0;
 }

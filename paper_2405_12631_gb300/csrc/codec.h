@@ -97,9 +97,16 @@ struct Geometry {
 };
 
 // Device buffers for a batch of planes of one geometry.
+// Stream-ordered device allocations from a per-device memory pool that keeps
+// freed memory for reuse: freeing never synchronises the device, so plans
+// of one context can come and go while other streams keep decoding.
+int pool_alloc(void **p, size_t n, cudaStream_t st);
+void pool_free(void *p, cudaStream_t st);
+
 struct Workspace {
   int P = 0;
   size_t bytes = 0;
+  cudaStream_t stream = nullptr;   // the stream alloc() ran on (frees go there)
   uint8_t *base = nullptr;
   int32_t *Q = nullptr;        // quantised latent, [sb][P][h][w]
   float *Yf = nullptr;         // float latent (dequantised / forward output)
@@ -112,7 +119,7 @@ struct Workspace {
   void *tc = nullptr;          // BF16 / FP8 activations (tensor-core path)
   int lstm_cur = 0;            // which Cst holds the current cell state
   // prec: the context's pw_precision (tensor-core buffers unless FP32)
-  int alloc(const Geometry &g, int P, int C, bool params, int prec);
+  int alloc(const Geometry &g, int P, int C, bool params, int prec, cudaStream_t st);
   // upper bound of the device bytes alloc() takes for these arguments
   static int64_t estimate(const Geometry &g, int P, int C, bool params, int prec);
   void release();

@@ -1134,14 +1134,14 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C, bool f8) {
   if (f8)
     for (int64_t v : sizes8) tot += al(v);
   TcAct *t = new TcAct();
-  if (cudaMalloc(&t->base, (size_t)tot) != cudaSuccess) {
+  if (pool_alloc(&t->base, (size_t)tot, ws->stream) != PW_OK) {
     delete t;
     set_last_error("tensor-core workspace allocation failed");
     return PW_ENOMEM;
   }
   uint8_t *b = static_cast<uint8_t *>(t->base);
   t->err = reinterpret_cast<int *>(b);
-  cudaMemset(t->err, 0, 1024);
+  cudaMemsetAsync(t->err, 0, 1024, ws->stream);
   int64_t o = 1024;
   __nv_bfloat16 **dst[kN] = {&t->X,  &t->L[0], &t->L[1], &t->Z,   &t->U,  &t->V,
                              &t->Z2, &t->Vc,   &t->Zc,   &t->Z2c, &t->U2c, &t->T};
@@ -1157,7 +1157,7 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C, bool f8) {
 void tc_workspace_free(Workspace *ws) {
   TcAct *t = static_cast<TcAct *>(ws->tc);
   if (!t) return;
-  cudaFree(t->base);
+  pool_free(t->base, ws->stream);
   delete t;
   ws->tc = nullptr;
 }
