@@ -516,49 +516,53 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 // + be and, when copy_h is set, X[:, C:2C] = up(h_prev) (h_prev: C channels
 // at the previous resolution). With copy_h = 0 the gates conv reads h_prev
 // from its own buffer instead.
-__global__ void k_lstm_in_bf16(const int32_t *__restrict__ s_prev,
-                               const __nv_bfloat16 *__restrict__ hprev,
-                               const float *__restrict__ we, const float *__restrict__ be,
-                               __nv_bfloat16 *__restrict__ X, int P, int H, int W, int C, int up,
-                               int copy_h, int first) {
+__global__ void __launch_bounds__(256) k_lstm_in_bf16(const int32_t *__restrict__ s_prev,
+                                                      const __nv_bfloat16 *__restrict__ hprev,
+                                                      const float *__restrict__ we,
+                                                      const float *__restrict__ be,
+                                                      __nv_bfloat16 *__restrict__ X, int P,
+                                                      int H, int W, int C, int up, int copy_h,
+                                                      int first) {
+  // one block per row (plane p, row y); item = group-major (g, x) so that a
+  // warp reads the same weights (shared-memory broadcast)
+  __shared__ float swe[9 * 128], sbe[128];
+  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) swe[i] = we[i];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sbe[i] = be[i];
+  __syncthreads();
   const int G = C / 8;
-  const int64_t n = (int64_t)P * H * W;
+  const int y = blockIdx.x % H;
+  const int64_t p = blockIdx.x / H;
   const int Hp = H >> up, Wp = W >> up;
   const int64_t hw = (int64_t)H * W;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(e % W);
-    const int y = (int)((e / W) % H);
-    const int p = (int)(e / hw);
-    const int32_t *sp = s_prev + (int64_t)p * Hp * Wp;
+  const int32_t *sp = s_prev + p * Hp * Wp;
+  for (int it = threadIdx.x; it < G * W; it += blockDim.x) {
+    const int g = it / W, x = it - g * W;
     float nb[9];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
       nb[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    ? (float)sp[(int64_t)(yy >> up) * Wp + (xx >> up)]
+                    ? (float)__ldg(sp + (int64_t)(yy >> up) * Wp + (xx >> up))
                     : 0.f;
     }
     const int64_t pix = (int64_t)y * W + x;
-    for (int g = 0; g < G; ++g) {
-      float v[8];
+    float v[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int c = 8 * g + k;
-        float s = __ldg(be + c);
+    for (int k = 0; k < 8; ++k) {
+      const int c = 8 * g + k;
+      float a = sbe[c];
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) s = fmaf(__ldg(we + c * 9 + tap), nb[tap], s);
-        v[k] = s;
-      }
-      store_bf16x8(X + (((int64_t)p * 2 * G + g) * hw + pix) * 8, v);
-      if (copy_h) {
-        float hv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        if (!first)
-          load_bf16x8(hprev + (((int64_t)p * G + g) * ((int64_t)Hp * Wp) +
-                               (int64_t)(y >> up) * Wp + (x >> up)) * 8,
-                      hv);
-        store_bf16x8(X + (((int64_t)p * 2 * G + G + g) * hw + pix) * 8, hv);
-      }
+      for (int tap = 0; tap < 9; ++tap) a = fmaf(swe[c * 9 + tap], nb[tap], a);
+      v[k] = a;
+    }
+    store_bf16x8(X + ((p * 2 * G + g) * hw + pix) * 8, v);
+    if (copy_h) {
+      float hv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      if (!first)
+        load_bf16x8(hprev + ((p * G + g) * ((int64_t)Hp * Wp) + (int64_t)(y >> up) * Wp +
+                             (x >> up)) * 8,
+                    hv);
+      store_bf16x8(X + ((p * 2 * G + G + g) * hw + pix) * 8, hv);
     }
   }
 }
@@ -567,103 +571,87 @@ __global__ void k_lstm_in_bf16(const int32_t *__restrict__ s_prev,
 // e_scale) and, when copy_h is set, X8[:, C:2C] = up(h8_prev) (E4M3 l_i of
 // the previous subband, copied as bytes; zero when first). Layout
 // [P][G16][H][W][16].
-__global__ void k_lstm_in_fp8(const int32_t *__restrict__ s_prev,
-                              const uint8_t *__restrict__ h8prev, const float *__restrict__ we,
-                              const float *__restrict__ be, const float *__restrict__ e_scale,
-                              uint8_t *__restrict__ X8, int P, int H, int W, int C, int up,
-                              int copy_h, int first) {
+__global__ void __launch_bounds__(256) k_lstm_in_fp8(const int32_t *__restrict__ s_prev,
+                                                     const uint8_t *__restrict__ h8prev,
+                                                     const float *__restrict__ we,
+                                                     const float *__restrict__ be,
+                                                     const float *__restrict__ e_scale,
+                                                     uint8_t *__restrict__ X8, int P, int H,
+                                                     int W, int C, int up, int copy_h,
+                                                     int first) {
+  // one block per row (plane p, row y); item = group-major (g, x)
+  __shared__ float swe[9 * 128], sbe[128], ssc[128];
+  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) swe[i] = we[i];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) { sbe[i] = be[i]; ssc[i] = e_scale[i]; }
+  __syncthreads();
   const int G16 = C / 16;
-  const int64_t n = (int64_t)P * H * W;
+  const int y = blockIdx.x % H;
+  const int64_t p = blockIdx.x / H;
   const int Hp = H >> up, Wp = W >> up;
   const int64_t hw = (int64_t)H * W;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(e % W);
-    const int y = (int)((e / W) % H);
-    const int p = (int)(e / hw);
-    const int32_t *sp = s_prev + (int64_t)p * Hp * Wp;
+  const int32_t *sp = s_prev + p * Hp * Wp;
+  for (int it = threadIdx.x; it < G16 * W; it += blockDim.x) {
+    const int g = it / W, x = it - g * W;
     float nb[9];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
       nb[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    ? (float)sp[(int64_t)(yy >> up) * Wp + (xx >> up)]
+                    ? (float)__ldg(sp + (int64_t)(yy >> up) * Wp + (xx >> up))
                     : 0.f;
     }
     const int64_t pix = (int64_t)y * W + x;
-    for (int g = 0; g < G16; ++g) {
-      float v[16];
+    float v[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int c = 16 * g + k;
-        float s = __ldg(be + c);
+    for (int k = 0; k < 16; ++k) {
+      const int c = 16 * g + k;
+      float a = sbe[c];
 #pragma unroll
-        for (int tap = 0; tap < 9; ++tap) s = fmaf(__ldg(we + c * 9 + tap), nb[tap], s);
-        v[k] = s * __ldg(e_scale + c);
-      }
-      store_fp8x16(X8 + (((int64_t)p * 2 * G16 + g) * hw + pix) * 16, v);
-      if (copy_h) {
-        uint4 hv = make_uint4(0u, 0u, 0u, 0u);
-        if (!first)
-          hv = *reinterpret_cast<const uint4 *>(
-              h8prev + (((int64_t)p * G16 + g) * ((int64_t)Hp * Wp) +
-                        (int64_t)(y >> up) * Wp + (x >> up)) * 16);
-        *reinterpret_cast<uint4 *>(X8 + (((int64_t)p * 2 * G16 + G16 + g) * hw + pix) * 16) = hv;
-      }
+      for (int tap = 0; tap < 9; ++tap) a = fmaf(swe[c * 9 + tap], nb[tap], a);
+      v[k] = a * ssc[c];
+    }
+    store_fp8x16(X8 + ((p * 2 * G16 + g) * hw + pix) * 16, v);
+    if (copy_h) {
+      uint4 hv = make_uint4(0u, 0u, 0u, 0u);
+      if (!first)
+        hv = *reinterpret_cast<const uint4 *>(
+            h8prev + ((p * G16 + g) * ((int64_t)Hp * Wp) + (int64_t)(y >> up) * Wp + (x >> up)) *
+                         16);
+      *reinterpret_cast<uint4 *>(X8 + ((p * 2 * G16 + G16 + g) * hw + pix) * 16) = hv;
     }
   }
 }
 
-// V = dw3x3(U) + b on C channels (blocked layout).
-__global__ void k_dw3x3_bf16(const __nv_bfloat16 *__restrict__ U, const float *__restrict__ w,
-                             const float *__restrict__ b, __nv_bfloat16 *__restrict__ V, int P,
-                             int H, int W, int C) {
-  const int G = C / 8;
-  const int64_t n = (int64_t)P * H * W * G;
-  const int64_t hw = (int64_t)H * W;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(e % W);
-    const int y = (int)((e / W) % H);
-    const int64_t pg = e / hw;  // p * G + g
-    const int g = (int)(pg % G);
-    float v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = b[8 * g + k];
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-      if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-      float u[8];
-      load_bf16x8(U + (pg * hw + (int64_t)yy * W + xx) * 8, u);
-#pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = fmaf(w[(8 * g + k) * 9 + tap], u[k], v[k]);
-    }
-    store_bf16x8(V + (pg * hw + (int64_t)y * W + x) * 8, v);
-  }
-}
 
 // Compact step tail input: for the q-th position (y, x) of step `step`,
 // Vc[q] = dw3x3(U)(y, x) + b and Zc[q] = Z(y, x) (C channels each, blocked
 // layout; q indexes the compact plane of hc x wc positions).
-__global__ void k_dw3x3_compact(const __nv_bfloat16 *__restrict__ U,
-                                const __nv_bfloat16 *__restrict__ Z, const float *__restrict__ w,
-                                const float *__restrict__ b, __nv_bfloat16 *__restrict__ Vc,
-                                __nv_bfloat16 *__restrict__ Zc, int P, int H, int W, int C,
-                                int step, int n, int64_t chw) {
+__global__ void __launch_bounds__(256) k_dw3x3_compact(
+    const __nv_bfloat16 *__restrict__ U, const __nv_bfloat16 *__restrict__ Z,
+    const float *__restrict__ w, const float *__restrict__ b, __nv_bfloat16 *__restrict__ Vc,
+    __nv_bfloat16 *__restrict__ Zc, int P, int H, int W, int C, int step, int n, int64_t chw) {
+  // one block per compact row (plane p, row pair yc); item = group-major
+  // (g, xc); xc < n_even lies on row 2 yc, the rest on row 2 yc + 1
+  __shared__ float sw[9 * 128], sb[128];
+  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) sw[i] = w[i];
+  for (int i = threadIdx.x; i < C; i += blockDim.x) sb[i] = b[i];
+  __syncthreads();
   const int G = C / 8;
-  const int64_t tot = (int64_t)P * G * n;
+  const int hc = (H + 1) >> 1;
+  const int yc = blockIdx.x % hc;
+  const int64_t p = blockIdx.x / hc;
+  const int ae = step_phase(step, 0), ao = step_phase(step, 1);
+  const int ne = row_count(W, ae), wc = ne + row_count(W, ao);
   const int64_t hw = (int64_t)H * W;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int q = (int)(e % n);
-    const int64_t pg = e / n;  // p * G + g
-    const int g = (int)(pg % G);
-    int y, x;
-    step_pos(W, step, q, y, x);
+  for (int it = threadIdx.x; it < G * wc; it += blockDim.x) {
+    const int g = it / wc, xc = it - g * wc;
+    const int y = xc < ne ? 2 * yc : 2 * yc + 1;
+    const int x = xc < ne ? ae + 4 * xc : ao + 4 * (xc - ne);
+    if (y >= H) continue;  // odd height: the last pair has no odd row
+    const int64_t pg = p * G + g;
     float v[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] = b[8 * g + k];
+    for (int k = 0; k < 8; ++k) v[k] = sb[8 * g + k];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
@@ -671,8 +659,9 @@ __global__ void k_dw3x3_compact(const __nv_bfloat16 *__restrict__ U,
       float u[8];
       load_bf16x8(U + (pg * hw + (int64_t)yy * W + xx) * 8, u);
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = fmaf(w[(8 * g + k) * 9 + tap], u[k], v[k]);
+      for (int k = 0; k < 8; ++k) v[k] = fmaf(sw[(8 * g + k) * 9 + tap], u[k], v[k]);
     }
+    const int64_t q = (int64_t)yc * wc + xc;
     store_bf16x8(Vc + (pg * chw + q) * 8, v);
     *reinterpret_cast<uint4 *>(Zc + (pg * chw + q) * 8) =
         *reinterpret_cast<const uint4 *>(Z + (pg * hw + (int64_t)y * W + x) * 8);
@@ -683,30 +672,43 @@ __global__ void k_dw3x3_compact(const __nv_bfloat16 *__restrict__ U,
 // (neighbours coded in an earlier step, else 0), channel 2 tap = BF16 value,
 // 2 tap + 1 = BF16 of the remainder, channels 18..31 = 0. One thread per
 // position; blocked layout [P][4][H][W][8].
-__global__ void k_masked_taps(const int32_t *__restrict__ s, __nv_bfloat16 *__restrict__ T,
-                              int P, int H, int W, int step) {
+// One block per row (plane p, row y), threads along x: no integer division
+// per element. Which of the 9 taps come from an earlier step depends only
+// on (y mod 2, x mod 4): a 9-bit mask per class, built once per block.
+__global__ void __launch_bounds__(128) k_masked_taps(const int32_t *__restrict__ s,
+                                                     __nv_bfloat16 *__restrict__ T, int P, int H,
+                                                     int W, int step) {
+  __shared__ uint32_t smask[8];
+  const int y = blockIdx.x % H;
+  const int64_t p = blockIdx.x / H;
+  if (threadIdx.x < 8) {
+    const int ry = threadIdx.x >> 2, rx = threadIdx.x & 3;
+    uint32_t m = 0;
+    for (int tap = 0; tap < 9; ++tap)
+      if (step_of(ry + 2 + tap / 3 - 1, rx + 4 + tap % 3 - 1) < step) m |= 1u << tap;
+    smask[threadIdx.x] = m;
+  }
+  __syncthreads();
   const int64_t hw = (int64_t)H * W;
-  const int64_t n = (int64_t)P * hw;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(e % W);
-    const int y = (int)((e / W) % H);
-    const int64_t p = e / hw;
-    const int32_t *sp = s + p * hw;
+  const int32_t *sp = s + p * hw;
+  const bool yin = y > 0 && y + 1 < H;
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    const uint32_t mask = smask[((y & 1) << 2) | (x & 3)];
+    const bool interior = yin && x > 0 && x + 1 < W;
     __align__(16) __nv_bfloat16 v[32];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-      const float f = (yy >= 0 && yy < H && xx >= 0 && xx < W && step_of(yy, xx) < step)
-                          ? (float)__ldg(sp + (int64_t)yy * W + xx)
-                          : 0.f;
+      const bool use = ((mask >> tap) & 1u) &&
+                       (interior || (yy >= 0 && yy < H && xx >= 0 && xx < W));
+      const float f = use ? (float)__ldg(sp + (int64_t)yy * W + xx) : 0.f;
       const __nv_bfloat16 hi = __float2bfloat16_rn(f);
       v[2 * tap] = hi;
       v[2 * tap + 1] = __float2bfloat16_rn(f - __bfloat162float(hi));
     }
 #pragma unroll
     for (int c = 18; c < 32; ++c) v[c] = __float2bfloat16_rn(0.f);
-    const int64_t pix = e - p * hw;
+    const int64_t pix = (int64_t)y * W + x;
 #pragma unroll
     for (int g = 0; g < 4; ++g)
       *reinterpret_cast<uint4 *>(T + ((p * 4 + g) * hw + pix) * 8) =
@@ -1183,11 +1185,11 @@ int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C,
                  pix * (4.0 + (f8 ? 1.0 : 2.0) * C * (copy_h ? 3 : 1)));
     if (f8)
-      k_lstm_in_fp8<<<grid_for((int64_t)P * h * w), 256, 0, ctx->stream>>>(
+      k_lstm_in_fp8<<<P * h, 256, 0, ctx->stream>>>(
           sprev, t.L8[(sb - 1) & 1], m.lstm_we, m.lstm_be, m.tc->e_scale, t.X8, P, h, w, C, up,
           copy_h, first);
     else
-      k_lstm_in_bf16<<<grid_for((int64_t)P * h * w), 256, 0, ctx->stream>>>(
+      k_lstm_in_bf16<<<P * h, 256, 0, ctx->stream>>>(
           sprev, lprev, m.lstm_we, m.lstm_be, t.X, P, h, w, C, up, copy_h, first);
     ctx->launches += 1;
   }
@@ -1252,7 +1254,7 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     };
     {
       ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * cpix * 9 * C, cpix * 2.0 * C * 4);
-      k_dw3x3_compact<<<grid_for((int64_t)P * n0 * G), 256, 0, st>>>(
+      k_dw3x3_compact<<<P * hc, 256, 0, st>>>(
           t.U, l, n.wdw, n.bdw, t.Vc, t.Zc, P, h, w, C, 0, n0, chw);  // Zc <- l gathered
       ctx->launches += 1;
     }
@@ -1280,7 +1282,7 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   const int G16 = C / 16;
   {
     ProfScope ps(ctx, KC_SMALL_CTX, 0.0, pix * (4.0 + 64.0));
-    k_masked_taps<<<grid_for((int64_t)P * h * w), 256, 0, st>>>(Qi, t.T, P, h, w, step);
+    k_masked_taps<<<P * h, 128, 0, st>>>(Qi, t.T, P, h, w, step);
     ctx->launches += 1;
   }
   TcConvArgs a{};
