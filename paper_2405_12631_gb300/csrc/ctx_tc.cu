@@ -101,6 +101,7 @@ struct TcConvArgs {
   int ks, cin, kb, nkb, in_goff;
   int ncta, nb;
   int tiles_x, tiles_y, tiles;  // tiles per N block
+  int step_dx, step_dy, step_dp;  // the CTA stride in (tiles_x, tiles_y) digits
   int stages, halo_x, halo_y;
   uint32_t stage_bytes, w_bytes;
   const __nv_bfloat16 *wt;      // [nb][kblock][tap][kb/8][ncta][8]
@@ -135,6 +136,26 @@ struct TcConvArgs {
 };
 
 constexpr int kTileH = 16, kTileW = 8;
+
+// Tile coordinates of a persistent CTA's tiles t = t0, t0 + step, ...:
+// (tx, ty, p) advanced like an odometer by the step's digits (dx, dy, dp)
+// in the (tiles_x, tiles_y) radix, which the host precomputes, so the loop
+// needs no division and holds three registers.
+struct TileIter {
+  int tx, ty, p;
+  __device__ __forceinline__ TileIter(int t0, int tiles_x, int tiles_y) {
+    tx = t0 % tiles_x; ty = (t0 / tiles_x) % tiles_y; p = t0 / (tiles_x * tiles_y);
+  }
+  __device__ __forceinline__ void next(int dx, int dy, int dp, int nx, int ny) {
+    tx += dx;
+    int cy = 0;
+    if (tx >= nx) { tx -= nx; cy = 1; }
+    ty += dy + cy;
+    int cp = 0;
+    if (ty >= ny) { ty -= ny; cp = 1; }
+    p += dp + cp;
+  }
+};
 
 __device__ __forceinline__ void store_bf16x8(__nv_bfloat16 *p, const float *v) {
   uint4 u;
@@ -216,6 +237,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   const int nctas = gridDim.x / a.nb;
   constexpr uint32_t kCols = NCTA * kAcc <= 32 ? 32 : NCTA * kAcc;  // power of two
 
+  // a plain store whose only output is FP8: the output scale is folded into
+  // the accumulator scale and bias (lrelu commutes with a positive scale)
+  const bool fold8 = EPI == TE_STORE && a.out8 && !a.out && !a.res;
   {
     const int nb0 = (blockIdx.x % a.nb) * NCTA;
     // FP8 output scale per output channel: the LSTM's outputs are channels
@@ -223,9 +247,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     const int nosc = (EPI == TE_LSTM) ? NCTA / 4 : NCTA;
     const int osc0 = (EPI == TE_LSTM) ? nb0 / 4 : nb0;
     for (int j = threadIdx.x; j < NCTA; j += blockDim.x) {
-      s_bias[j] = a.bias[nb0 + j];
-      s_wsc[j] = F8 ? a.w_scale[nb0 + j] : 1.f;
-      s_osc[j] = (a.out8_scale && j < nosc) ? a.out8_scale[osc0 + j] : 0.f;
+      const float os = (a.out8_scale && j < nosc) ? a.out8_scale[osc0 + j] : 0.f;
+      const float k = fold8 ? os : 1.f;
+      s_bias[j] = a.bias[nb0 + j] * k;
+      s_wsc[j] = (F8 ? a.w_scale[nb0 + j] : 1.f) * k;
+      s_osc[j] = os;
       if (EPI == TE_HEAD) { s_wh[j] = a.wh[j]; s_wh[NCTA + j] = a.wh[NCTA + j]; }
     }
   }
@@ -264,8 +290,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     int stage = 0;
     uint32_t phase = 0;
     int issued = 0;
-    for (int t = cta; t < a.tiles && !*s_abort; t += nctas) {
-      const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, p = t / (a.tiles_x * a.tiles_y);
+    TileIter ti(cta, a.tiles_x, a.tiles_y);
+    for (int t = cta; t < a.tiles && !*s_abort;
+         t += nctas, ti.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y)) {
+      const int tx = ti.tx, ty = ti.ty, p = ti.p;
       for (int kbi = 0; kbi < a.nkb; ++kbi) {
         if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) break;
         mbar_expect_tx(&full[stage], a.stage_bytes);
@@ -351,8 +379,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     int acc = 0;
     uint32_t aphase = 0;
     const int G = a.out_G;
-    for (int t = cta; t < a.tiles; t += nctas) {
-      const int tx = t % a.tiles_x, ty = (t / a.tiles_x) % a.tiles_y, p = t / (a.tiles_x * a.tiles_y);
+    TileIter ti(cta, a.tiles_x, a.tiles_y);
+    for (int t = cta; t < a.tiles;
+         t += nctas, ti.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y)) {
+      const int tx = ti.tx, ty = ti.ty, p = ti.p;
       const int y = ty * kTileH + r, x = tx * kTileW + c;
       const bool valid = y < a.H && x < a.W;
       const int64_t hw = (int64_t)a.H * a.W;
@@ -402,7 +432,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       if (++acc == kAcc) { acc = 0; aphase ^= 1; }
       if (!work) continue;
 
-      if (F8) {
+      if (F8 || (EPI == TE_STORE && fold8)) {
 #pragma unroll
         for (int j = 0; j < NH; ++j) v[j] = fmaf(v[j], s_wsc[col0 + j], s_bias[col0 + j]);
       } else {
@@ -432,7 +462,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           for (int g = 0; g < NH / 16; ++g) {
             float f[16];
 #pragma unroll
-            for (int e = 0; e < 16; ++e) f[e] = v[16 * g + e] * s_osc[col0 + 16 * g + e];
+            for (int e = 0; e < 16; ++e)
+              f[e] = fold8 ? v[16 * g + e] : v[16 * g + e] * s_osc[col0 + 16 * g + e];
             store_fp8x16(a.out8 + (((int64_t)p * a.out8_G16 + (n0 >> 4) + g) * hw + pix) * 16, f);
           }
         }
@@ -810,6 +841,9 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   if (per_nb < 1) per_nb = 1;
   if (per_nb > a.tiles) per_nb = a.tiles;
   const int grid = per_nb * cv.nb;
+  a.step_dx = per_nb % a.tiles_x;
+  a.step_dy = (per_nb / a.tiles_x) % a.tiles_y;
+  a.step_dp = per_nb / (a.tiles_x * a.tiles_y);
   cudaStream_t st = ctx->stream;
 #define PW_TC_CASE(KS_, KB_, N_, E_, F8_)                                                   \
   if (cv.ks == KS_ && cv.kb == KB_ && cv.ncta == N_ && a.epi == E_ && cv.f8 == F8_) {       \
