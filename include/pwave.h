@@ -42,8 +42,8 @@ typedef enum {
 
 /* Arithmetic of the context-model and lifting convolutions. FP32 is the
  * plain SIMT path; BF16 runs the convolutions on tcgen05 tensor cores with
- * FP32 accumulation (and, for lossy streams, the inverse lifting CNN's middle
- * layer); FP8 is BF16 with the three 3x3 context convolutions (ConvLSTM
+ * FP32 accumulation (and, for lossy streams, layers 2 and 3 of the inverse
+ * lifting CNN); FP8 is BF16 with the three 3x3 context convolutions (ConvLSTM
  * gates, residual blocks of steps 2-4) in E4M3 with per-channel scales and
  * FP32 accumulation. The entropy-parameter -> table decision and the CDF
  * tables are FP32/integer in every mode. A stream decodes only with the
