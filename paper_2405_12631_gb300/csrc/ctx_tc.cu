@@ -125,6 +125,11 @@ struct TcConvArgs {
   // pair): compact_n = number of step positions (0: full-plane layout),
   // full_W = width of the subband (for the mu / sigma planes)
   int compact_n, full_W, full_H;
+  // step-compact BF16 copy of a plain store's output: the positions of step
+  // `step` only, [P][G][n][8] in step order (outc_n = n positions per plane);
+  // a head reads its residual from such a copy when res_compact_n > 0
+  __nv_bfloat16 *outc;
+  int outc_n, res_compact_n;
   // FP8 (E4M3) operands: per-output-column scale applied to the accumulator
   // (acc * w_scale[n] + bias[n]); optional second output in FP8, blocked
   // [P][G16][H][W][16], value = output * out8_scale[channel]
@@ -201,8 +206,9 @@ __device__ __forceinline__ void mma_fp8(uint32_t d, uint64_t a, uint64_t b, uint
 }
 
 // shared memory: barriers [0, 1024), epilogue constants [1024, 4096)
-// (5 x NCTA floats), then the resident weights and the stages
-constexpr int kConvHeader = 4096;
+// (5 x NCTA floats), head partial sums [4096, 8192), then the resident
+// weights and the stages
+constexpr int kConvHeader = 8192;
 
 constexpr int kEpiWarps = 8;                    // two per TMEM lane quadrant
 constexpr int kConvThreads = 64 + 32 * kEpiWarps;
@@ -222,6 +228,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   uint64_t *wbar = acce + kAcc;                              // [1]
   volatile int *s_abort = reinterpret_cast<volatile int *>(wbar + 1);
   uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 256);
+  // TE_HEAD: the column halves of a lane quadrant exchange partial (mu, rho)
+  // sums through s_part[acc][quadrant][lane], signalled by hbar[acc][quadrant]
+  uint64_t *hbar = reinterpret_cast<uint64_t *>(smem + 512);        // [kAcc * 4]
+  float2 *s_part = reinterpret_cast<float2 *>(smem + 4096);          // [kAcc][4][32]
   // per-column epilogue constants of this CTA's N block (loaded once):
   // bias, accumulator scale (F8), FP8 output scale, head weights [2][NCTA]
   float *s_bias = reinterpret_cast<float *>(smem + 1024);
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 
   // a plain store whose only output is FP8: the output scale is folded into
   // the accumulator scale and bias (lrelu commutes with a positive scale)
-  const bool fold8 = EPI == TE_STORE && a.out8 && !a.out && !a.res;
+  const bool fold8 = EPI == TE_STORE && a.out8 && !a.out && !a.res && !a.outc;
   {
     const int nb0 = (blockIdx.x % a.nb) * NCTA;
     // FP8 output scale per output channel: the LSTM's outputs are channels
@@ -258,6 +268,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
     for (int i = 0; i < kAcc; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], kEpiWarps); }
+    if (EPI == TE_HEAD)
+      for (int i = 0; i < kAcc * 4; ++i) mbar_init(&hbar[i], 1);
     mbar_init(wbar, 1);
     *s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -371,9 +383,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     // needs all columns of a pixel and runs on half 0 only) --------------
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
-    constexpr int NH = (EPI == TE_HEAD) ? NCTA : NCTA / 2;
-    const bool work = (EPI != TE_HEAD) || half == 0;
-    const int col0 = (EPI == TE_HEAD) ? 0 : half * NH;
+    constexpr int NH = NCTA / 2;
+    const bool work = true;
+    const int col0 = half * NH;
     const int m = 32 * q + lane;
     const int r = m / kTileW, c = m % kTileW;
     int acc = 0;
@@ -407,10 +419,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           const bool need = (EPI == TE_STORE) ||
                             (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step);
           if (need) {
+            if (EPI == TE_HEAD && a.res_compact_n) {
+              const int64_t qn = step_index(a.W, a.step, y, x);
 #pragma unroll
-            for (int g = 0; g < NH / 8; ++g)
-              pres[g] = __ldg(reinterpret_cast<const uint4 *>(
-                  a.res + (((int64_t)p * a.res_G + a.res_goff + (n0 >> 3) + g) * hw + pix) * 8));
+              for (int g = 0; g < NH / 8; ++g)
+                pres[g] = __ldg(reinterpret_cast<const uint4 *>(
+                    a.res + (((int64_t)p * a.res_G + (n0 >> 3) + g) * a.res_compact_n + qn) * 8));
+            } else {
+#pragma unroll
+              for (int g = 0; g < NH / 8; ++g)
+                pres[g] = __ldg(reinterpret_cast<const uint4 *>(
+                    a.res + (((int64_t)p * a.res_G + a.res_goff + (n0 >> 3) + g) * hw + pix) * 8));
+            }
           }
         }
       }
@@ -428,7 +448,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       if (work) tmem_ld<NH>(taddr, v);
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&acce[acc]);
+      // the head's half 0 releases the accumulator only after it has read its
+      // partner's partial sums for this tile (which then cannot be overwritten)
+      const int cur_acc = acc;
+      const uint32_t cur_phase = aphase;
+      if (lane == 0 && !(EPI == TE_HEAD && half == 0)) mbar_arrive(&acce[acc]);
       if (++acc == kAcc) { acc = 0; aphase ^= 1; }
       if (!work) continue;
 
@@ -439,7 +463,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 #pragma unroll
         for (int j = 0; j < NH; ++j) v[j] += s_bias[col0 + j];
       }
-      if (!valid) continue;
+      // (the head's halves must both reach the partial-sum handoff, so
+      // invalid positions only skip the work inside it)
+      if (!valid && EPI != TE_HEAD) continue;
       if (EPI == TE_STORE) {
 #pragma unroll
         for (int g = 0; g < NH / 8; ++g) {
@@ -456,6 +482,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           }
           if (a.out)
             store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + gg) * hw + pix) * 8, v + 8 * g);
+        }
+        if (a.outc && step_of(y, x) == a.step) {
+          const int64_t qn = step_index(a.W, a.step, y, x);
+#pragma unroll
+          for (int g = 0; g < NH / 8; ++g)
+            store_bf16x8(a.outc + (((int64_t)p * G + (n0 >> 3) + g) * a.outc_n + qn) * 8, v + 8 * g);
         }
         if (NH % 16 == 0 && a.out8) {
 #pragma unroll
@@ -495,19 +527,41 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           }
         }
       } else {  // TE_HEAD: z' = res + acc + b over all C columns, then 1x1(C->2)
-        if (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step) {
-          float mu = a.bh[0], rho = a.bh[1];
+        const bool mine =
+            valid && (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step);
+        // partial sums of this half's columns (half 0 adds the head bias)
+        float mu = half == 0 ? a.bh[0] : 0.f, rho = half == 0 ? a.bh[1] : 0.f;
+        if (mine) {
 #pragma unroll
-          for (int g = 0; g < NCTA / 8; ++g) {
+          for (int g = 0; g < NH / 8; ++g) {
             float rv[8];
             load_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(&pres[g]), rv);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const float z = v[8 * g + e] + rv[e];
-              mu = fmaf(s_wh[8 * g + e], z, mu);
-              rho = fmaf(s_wh[NCTA + 8 * g + e], z, rho);
+              mu = fmaf(s_wh[col0 + 8 * g + e], z, mu);
+              rho = fmaf(s_wh[NCTA + col0 + 8 * g + e], z, rho);
             }
           }
+        }
+        float2 *slot = s_part + (cur_acc * 4 + q) * 32 + lane;
+        if (half == 1) {
+          *slot = make_float2(mu, rho);
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&hbar[cur_acc * 4 + q]);
+          continue;
+        }
+        int hok = 1;
+        if (lane == 0) hok = mbar_wait(&hbar[cur_acc * 4 + q], cur_phase, s_abort, 100) ? 1 : 0;
+        hok = __shfl_sync(0xffffffffu, hok, 0);
+        if (!hok) break;
+        if (lane != 0) mbar_wait(&hbar[cur_acc * 4 + q], cur_phase, s_abort);
+        const float2 other = *slot;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acce[cur_acc]);
+        mu += other.x;
+        rho += other.y;
+        if (mine) {
           int qi;
           int64_t fpix, fhw;
           if (a.compact_n) {
@@ -1321,8 +1375,12 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   }
   TcConvArgs a{};
   a.epi = TE_STORE; a.out = t.Z; a.out_G = G;
-  // FP8: the residual-block input also feeds conv 1 as E4M3
-  if (f8) { a.out8 = t.Z8; a.out8_G16 = G16; a.out8_scale = zsc; }
+  // FP8: the residual-block input feeds conv 1 as E4M3 and the head's
+  // residual as a dense BF16 copy of this step's positions (in Zc)
+  if (f8) {
+    a.out = nullptr; a.out8 = t.Z8; a.out8_G16 = G16; a.out8_scale = zsc;
+    a.outc = t.Zc; a.outc_n = (int)nk; a.step = step;
+  }
   {
     // z = 1x1 over [l, T]: K-blocks of 32 channels, the first C / 32 from l
     ProfScope ps(ctx, KC_CONV1, 2.0 * pix * zt.cin * zt.cout,
@@ -1336,10 +1394,10 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
       ProfScope ps(ctx, KC_CONV3, 2.0 * pix * 9 * C * C, pix * 2.0 * C);
       if ((s = conv_tc(ctx, c1, t.Z8, G16, 0, P, h, w, a, t.err))) return s;  // u = lrelu(3x3 z)
     }
-    a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z; a.res_G = G;
+    a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Zc; a.res_G = G; a.res_compact_n = (int)nk;
     a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
     a.mu_out = mu; a.sg_out = sgp;
-    ProfScope ps(ctx, KC_CONV3, 2.0 * pix * 9 * C * C, pix * 3.0 * C);
+    ProfScope ps(ctx, KC_CONV3, 2.0 * pix * 9 * C * C, pix * 1.5 * C);
     return conv_tc(ctx, c2, t.U8, G16, 0, P, h, w, a, t.err);               // head
   }
   a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
