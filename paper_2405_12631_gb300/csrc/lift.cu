@@ -282,12 +282,15 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
     const int c = e / 9, tap = e % 9;  // source [c][tap]
     S.w1t[tap * LF + c] = a.net.w1[e];
   }
-  for (int e = t; e < LF * LF * 9; e += 256) {
-    const int c = e / (LF * 9), ci = (e / 9) % LF, tap = e % 9;  // source [c][ci][tap]
-    const int o = ((tap * 2 + (ci >> 3)) * LF + c) * 8 + (ci & 7);
-    S.w2[o] = __float2bfloat16_rn(a.net.w2[e]);
-    // layer 3: output 0 = the CNN's single output channel, ci = e / 9 here
-    S.w3[o] = __float2bfloat16_rn(c == 0 ? a.net.w3[(e / 9) % LF * 9 + tap] : 0.f);
+  {
+    // the packed B operands of layers 2 and 3 (9 x 2 x 16 x 8 BF16 each)
+    constexpr int kB16 = 9 * 2 * LF * 8 * 2 / 16;
+    const uint4 *src2 = reinterpret_cast<const uint4 *>(a.net.w2b);
+    const uint4 *src3 = reinterpret_cast<const uint4 *>(a.net.w3b);
+    for (int i = t; i < kB16; i += 256) {
+      reinterpret_cast<uint4 *>(S.w2)[i] = __ldg(src2 + i);
+      reinterpret_cast<uint4 *>(S.w3)[i] = __ldg(src3 + i);
+    }
   }
   if (t < LF) { S.b1[t] = a.net.b1[t]; S.b2[t] = a.net.b2[t]; }
   if (t == 0) S.b3 = a.net.b3[0];

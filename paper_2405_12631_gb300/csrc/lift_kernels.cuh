@@ -15,6 +15,9 @@ struct PlaneAcc {
 
 struct LiftNetDev {
   const float *w1, *b1, *w2, *b2, *w3, *b3;  // [16][9], [16], [16][16][9], [16], [16][9], [1]
+  // BF16 MMA B operands of layers 2 and 3 for the tensor-core step, packed
+  // [tap][2 channel groups][16 outputs][8] (layer 3: output 0, rest zero)
+  const void *w2b, *w3b;
 };
 
 enum { LIN_P53 = 0, LIN_U53 = 1, LIN_ID = 2, LIN_HALF = 3 };

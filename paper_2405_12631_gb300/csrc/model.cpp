@@ -8,6 +8,8 @@
 #include <cstring>
 #include <map>
 
+#include <cuda_bf16.h>
+
 #include "codec.h"
 
 namespace pw {
@@ -124,6 +126,30 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
         !get(p + "w3", {1, 16, 3, 3}, w3) || !get(p + "b3", {1}, b3))
       return false;
     n.w1 = up(w1); n.b1 = up(b1); n.w2 = up(w2); n.b2 = up(b2); n.w3 = up(w3); n.b3 = up(b3);
+    {
+      // packed BF16 B operands: [tap][ci / 8][c][ci % 8]
+      std::vector<__nv_bfloat16> b2p(9 * 2 * 16 * 8), b3p(9 * 2 * 16 * 8, __float2bfloat16(0.f));
+      for (int c = 0; c < 16; ++c)
+        for (int ci = 0; ci < 16; ++ci)
+          for (int tap = 0; tap < 9; ++tap) {
+            const size_t o = ((size_t)(tap * 2 + ci / 8) * 16 + c) * 8 + ci % 8;
+            b2p[o] = __float2bfloat16(w2[((size_t)c * 16 + ci) * 9 + tap]);
+            if (c == 0) b3p[o] = __float2bfloat16(w3[(size_t)ci * 9 + tap]);
+          }
+      void *d2 = nullptr, *d3 = nullptr;
+      if (cudaMalloc(&d2, b2p.size() * 2) != cudaSuccess ||
+          cudaMalloc(&d3, b3p.size() * 2) != cudaSuccess) {
+        cudaFree(d2);
+        st = PW_ENOMEM;
+        return false;
+      }
+      allocs.push_back(static_cast<float *>(d2));
+      allocs.push_back(static_cast<float *>(d3));
+      cudaMemcpy(d2, b2p.data(), b2p.size() * 2, cudaMemcpyHostToDevice);
+      cudaMemcpy(d3, b3p.data(), b3p.size() * 2, cudaMemcpyHostToDevice);
+      n.w2b = d2;
+      n.w3b = d3;
+    }
     keep(p + "w2", w2); keep(p + "w1", w1); keep(p + "w3", w3);
     keep(p + "b1", b1); keep(p + "b2", b2); keep(p + "b3", b3);
     return true;
