@@ -349,15 +349,33 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     bool ok = mbar_wait(wbar, 0, s_abort);
     int stage = 0, acc = 0;
     uint32_t phase = 0, aphase = 0;
-    for (int t = cta; ok && t < a.tiles; t += nctas) {
+    // FP8 3x3 convs: two tiles per round (when both tiles' K-blocks fit in
+    // the stages), their MMAs interleaved into two accumulators so that
+    // consecutive MMAs never depend on each other's accumulator. (Measured:
+    // faster for these, slower for the HBM-bound 1x1 convs and BF16.)
+    const bool pairs = F8 && KS == 3 && a.stages >= 2 * a.nkb;
+    for (int t = cta; ok && t < a.tiles; t += (pairs ? 2 : 1) * nctas) {
+      const bool two = pairs && t + nctas < a.tiles;
+      const int acc1 = acc + 1 == kAcc ? 0 : acc + 1;
+      const uint32_t aphase1 = acc + 1 == kAcc ? aphase ^ 1 : aphase;
       if (!mbar_wait(&acce[acc], aphase ^ 1, s_abort, 200)) break;
+      if (two && !mbar_wait(&acce[acc1], aphase1 ^ 1, s_abort, 200)) break;
       fence_after();
-      const uint32_t d = tbase + (uint32_t)(acc * NCTA);
+      const uint32_t d0 = tbase + (uint32_t)(acc * NCTA), d1 = tbase + (uint32_t)(acc1 * NCTA);
       uint32_t accum = 0;
       for (int kbi = 0; kbi < a.nkb; ++kbi) {
-        if (!mbar_wait(&full[stage], phase, s_abort)) { ok = false; break; }
+        // stage of this K-block of tile 0 and (nkb stages later) of tile 1
+        int s0 = stage + kbi;
+        uint32_t p0 = phase;
+        if (s0 >= a.stages) { s0 -= a.stages; p0 ^= 1; }
+        int s1 = s0 + a.nkb;
+        uint32_t p1 = p0;
+        if (s1 >= a.stages) { s1 -= a.stages; p1 ^= 1; }
+        if (!mbar_wait(&full[s0], p0, s_abort)) { ok = false; break; }
+        if (two && !mbar_wait(&full[s1], p1, s_abort)) { ok = false; break; }
         fence_after();
-        const uint64_t a0 = sdesc(smem_u32(stg + (size_t)stage * a.stage_bytes), slab, HX * 16u);
+        const uint64_t a0 = sdesc(smem_u32(stg + (size_t)s0 * a.stage_bytes), slab, HX * 16u);
+        const uint64_t a1 = sdesc(smem_u32(stg + (size_t)s1 * a.stage_bytes), slab, HX * 16u);
         const uint64_t b0 = sdesc(smem_u32(wsm) + (uint32_t)kbi * wblock, NCTA * 16u, 128u);
 #pragma unroll
         for (int tap = 0; tap < taps; ++tap) {
@@ -365,17 +383,27 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           for (int s = 0; s < KSTEPS; ++s) {
             const uint32_t aoff = ((uint32_t)(2 * s) * slab + (uint32_t)((tap / KS) * HX + tap % KS) * 16u) >> 4;
             const uint32_t boff = ((uint32_t)(tap * GPK + 2 * s) * (NCTA * 16u)) >> 4;
-            if (F8) mma_fp8(d, a0 + aoff, b0 + boff, idesc, accum);
-            else mma_bf16(d, a0 + aoff, b0 + boff, idesc, accum);
+            if (F8) mma_fp8(d0, a0 + aoff, b0 + boff, idesc, accum);
+            else mma_bf16(d0, a0 + aoff, b0 + boff, idesc, accum);
+            if (two) {
+              if (F8) mma_fp8(d1, a1 + aoff, b0 + boff, idesc, accum);
+              else mma_bf16(d1, a1 + aoff, b0 + boff, idesc, accum);
+            }
             accum = 1;
           }
         }
-        mma_commit(&empty[stage]);
-        if (++stage == a.stages) { stage = 0; phase ^= 1; }
+        mma_commit(&empty[s0]);
+        if (two) mma_commit(&empty[s1]);
       }
       if (!ok) break;
       mma_commit(&accf[acc]);
-      if (++acc == kAcc) { acc = 0; aphase ^= 1; }
+      if (two) mma_commit(&accf[acc1]);
+      // advance past the consumed stages and accumulators
+      const int used = (two ? 2 : 1) * a.nkb;
+      stage += used;
+      while (stage >= a.stages) { stage -= a.stages; phase ^= 1; }
+      acc += two ? 2 : 1;
+      if (acc >= kAcc) { acc -= kAcc; aphase ^= 1; }
     }
   } else if (warp >= 2) {
     // ---- epilogue: warps 2..9; warp w reads TMEM lanes 32 (w % 4) .. +31
