@@ -295,6 +295,21 @@ const char *pw_last_error(void);
 /* Number of kernels this library launched on the context so far. */
 uint64_t pw_ctx_launch_count(const pw_ctx *ctx);
 
+/* Autotuner of the tensor-core convolutions. For every convolution variant
+ * and size class (log2 of its tile count) the MMA issue schedule (one tile
+ * or two interleaved tiles per round) is chosen by sampling both candidates
+ * round robin on the first real launches of the class in the process
+ * (CUDA events read back without synchronising, 3 samples each) and
+ * keeping the faster median; results never depend on the schedule.
+ * pw_autotune(0 / 1) disables / enables sampling of classes not tuned yet
+ * (default on; disabled classes use the default schedule) and returns the
+ * previous setting. pw_autotune_report writes one line per tuned class
+ * ("ks kb ncta epilogue fp8 log2tiles pairs t_single t_paired", median sample
+ * times in microseconds, -1 = no sample) into buf (NUL-terminated,
+ * truncated to n) and returns the full length. */
+int pw_autotune(int enable);
+int pw_autotune_report(char *buf, size_t n);
+
 /* Per-kernel-class timing. pw_ctx_profile(ctx, 1) resets the counters and
  * records a CUDA event pair on the context's stream around every launch that
  * follows (adds a few microseconds per launch); 0 stops recording.

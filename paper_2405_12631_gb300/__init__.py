@@ -105,6 +105,8 @@ _sig = {
     "pw_server_poll": (C.c_int, [_P, C.c_uint64, C.POINTER(pw_image), C.c_int]),
     "pw_server_stats": (C.c_int, [_P, C.POINTER(pw_stats)]),
     "pw_server_destroy": (None, [_P]),
+    "pw_autotune": (C.c_int, [C.c_int]),
+    "pw_autotune_report": (C.c_int, [C.c_char_p, C.c_size_t]),
     "pw_ctx_profile": (C.c_int, [_P, C.c_int]),
     "pw_ctx_kernel_stats": (C.c_int, [_P, C.POINTER(pw_kernel_stat), C.c_int]),
     "pw_free": (None, [_P]),
@@ -459,6 +461,21 @@ def parse_stream_header(bs: bytes) -> dict:
 def padded_elems(hd: dict) -> int:
     mult = 1 << hd["levels"]
     return (-(-hd["height"] // mult) * mult) * (-(-hd["width"] // mult) * mult)
+
+
+def autotune_report() -> list:
+    """Tuned convolution classes as dicts (see pw_autotune_report)."""
+    n = pw_autotune_report(None, 0)
+    buf = C.create_string_buffer(n + 1)
+    pw_autotune_report(buf, n + 1)
+    keys = ("ks", "kb", "ncta", "epi", "fp8", "log2tiles", "pairs")
+    out = []
+    for line in buf.value.decode().splitlines():
+        v = line.split()
+        d = {k: int(x) for k, x in zip(keys, v[:7])}
+        d["us"] = [float(x) for x in v[7:9]]
+        out.append(d)
+    return out
 
 
 def stream_image_shape(bs: bytes):

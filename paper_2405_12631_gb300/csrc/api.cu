@@ -750,6 +750,18 @@ int pw_ctx_kernel_stats(pw_ctx *c, pw_kernel_stat *out, int max) {
 }
 uint64_t pw_ctx_launch_count(const pw_ctx *c) { return c ? c->launches : 0; }
 
+int pw_autotune(int enable) { return tune_set_enabled(enable); }
+
+int pw_autotune_report(char *buf, size_t n) {
+  const std::string r = tune_report();
+  if (buf && n) {
+    const size_t k = r.size() < n - 1 ? r.size() : n - 1;
+    std::memcpy(buf, r.data(), k);
+    buf[k] = 0;
+  }
+  return (int)r.size();
+}
+
 int pw_model_load(pw_ctx *c, const void *blob, size_t n, pw_model **out) {
   if (!c || !blob || !out) { set_last_error("bad arguments"); return PW_EINVAL; }
   pw_model *m = new pw_model();

@@ -23,7 +23,9 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <atomic>
+#include <map>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -102,6 +104,7 @@ struct TcConvArgs {
   int ncta, nb;
   int tiles_x, tiles_y, tiles;  // tiles per N block
   int step_dx, step_dy, step_dp;  // the CTA stride in (tiles_x, tiles_y) digits
+  int pairs;                      // MMA issue of two tiles per round (see the issuer)
   int stages, halo_x, halo_y;
   uint32_t stage_bytes, w_bytes;
   const __nv_bfloat16 *wt;      // [nb][kblock][tap][kb/8][ncta][8]
@@ -349,11 +352,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     bool ok = mbar_wait(wbar, 0, s_abort);
     int stage = 0, acc = 0;
     uint32_t phase = 0, aphase = 0;
-    // FP8 3x3 convs: two tiles per round (when both tiles' K-blocks fit in
-    // the stages), their MMAs interleaved into two accumulators so that
-    // consecutive MMAs never depend on each other's accumulator. (Measured:
-    // faster for these, slower for the HBM-bound 1x1 convs and BF16.)
-    const bool pairs = F8 && KS == 3 && a.stages >= 2 * a.nkb;
+    // a.pairs: two tiles per round (when both tiles' K-blocks fit in the
+    // stages), their MMAs interleaved into two accumulators so that
+    // consecutive MMAs never depend on each other's accumulator (the
+    // autotuner decides per shape class: faster for the FP8 3x3 convs,
+    // slower for the HBM-bound 1x1 convs)
+    const bool pairs = a.pairs && a.stages >= 2 * a.nkb;
     for (int t = cta; ok && t < a.tiles; t += (pairs ? 2 : 1) * nctas) {
       const bool two = pairs && t + nctas < a.tiles;
       const int acc1 = acc + 1 == kAcc ? 0 : acc + 1;
@@ -875,6 +879,149 @@ static int make_map(CUtensorMap *map, const void *base, int P, int G, int H, int
 
 static std::atomic<int> g_num_sms{0};
 
+// ---- autotuner -------------------------------------------------------------
+// Per (kernel variant, size class = log2 of the tile count) the MMA issue
+// schedule: one or two tiles per round. The candidates are sampled in place,
+// round robin, on the real launches of the decode / encode pipeline (each
+// launch bracketed by events that are read back later without a
+// synchronisation), so that the choice reflects the caches and concurrency
+// the kernel really sees; after kSamples samples of every candidate the
+// fastest median wins (the median ignores a one-off outlier such as the
+// first launch of a kernel, which loads its module). Results do not depend
+// on the schedule.
+constexpr int kTuneCand = 2, kSamples = 3;
+struct TuneChoice {
+  int pairs = 0;
+};
+struct TuneEntry {
+  bool tuned = false;
+  TuneChoice choice;
+  int next = 0;                        // candidate of the next sample
+  int issued[kTuneCand] = {0, 0};      // samples launched
+  int n[kTuneCand] = {0, 0};           // samples read back
+  float us[kTuneCand][kSamples] = {};  // their times
+  double median(int c) const {
+    if (n[c] == 0) return -1.0;
+    float v[kSamples];
+    for (int i = 0; i < n[c]; ++i) v[i] = us[c][i];
+    std::sort(v, v + n[c]);
+    return v[n[c] / 2];
+  }
+};
+struct TunePending {
+  uint64_t key;
+  int cand;
+  cudaEvent_t e0, e1;
+};
+static std::mutex g_tune_mu;
+static std::map<uint64_t, TuneEntry> g_tune;
+static std::vector<TunePending> g_tune_pending;
+static std::atomic<int> g_tune_on{1};
+
+static uint64_t tune_key(const TcWeights::Conv &cv, int epi, int tiles) {
+  int cls = 0;
+  while ((1 << (cls + 1)) <= tiles && cls < 30) ++cls;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return ((uint64_t)dev << 40) | ((uint64_t)cv.ks << 32) | ((uint64_t)cv.kb << 24) |
+         ((uint64_t)cv.ncta << 14) | ((uint64_t)epi << 10) | ((uint64_t)cv.f8 << 9) |
+         (uint64_t)cls;
+}
+
+// Read back finished samples (lock held).
+static void tune_poll_locked() {
+  size_t w = 0;
+  for (size_t i = 0; i < g_tune_pending.size(); ++i) {
+    TunePending &q = g_tune_pending[i];
+    const cudaError_t e = cudaEventQuery(q.e1);
+    if (e == cudaErrorNotReady) { g_tune_pending[w++] = q; continue; }
+    float ms = 0.f;
+    if (e == cudaSuccess && cudaEventElapsedTime(&ms, q.e0, q.e1) == cudaSuccess) {
+      TuneEntry &t = g_tune[q.key];
+      if (t.n[q.cand] < kSamples) t.us[q.cand][t.n[q.cand]++] = 1e3f * ms;
+      bool done = !t.tuned;
+      for (int c = 0; c < kTuneCand; ++c) done = done && (t.issued[c] == 0 || t.n[c] >= kSamples);
+      if (done) {
+        double best = 1e30;
+        for (int c = 0; c < kTuneCand; ++c)
+          if (t.n[c] && t.median(c) < best) { best = t.median(c); t.choice.pairs = c; }
+        t.tuned = true;
+      }
+    } else {
+      cudaGetLastError();
+    }
+    cudaEventDestroy(q.e0);
+    cudaEventDestroy(q.e1);
+  }
+  g_tune_pending.resize(w);
+}
+
+// The schedule of the next launch of a class. While the class is being tuned
+// (sample = true) the launch is a sample of candidate `cand`.
+static TuneChoice tune_next(uint64_t key, bool can_pair, cudaStream_t st, bool &sample,
+                            int &cand) {
+  TuneChoice c;
+  c.pairs = ((key >> 32) & 0xFF) == 3 && ((key >> 9) & 1) && can_pair;  // default
+  sample = false;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_poll_locked();
+  TuneEntry &t = g_tune[key];
+  if (t.tuned) {
+    c.pairs = t.choice.pairs && can_pair;
+    return c;
+  }
+  if (!g_tune_on.load()) return c;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return c;
+  }
+  const int ncand = can_pair ? 2 : 1;
+  if (ncand == 1) {  // nothing to choose
+    t.tuned = true;
+    t.choice.pairs = 0;
+    return c;
+  }
+  cand = t.next;
+  if (t.issued[cand] >= kSamples) return c;  // enough in flight; wait for read-back
+  t.next = (t.next + 1) % ncand;
+  t.issued[cand] += 1;
+  c.pairs = cand;
+  sample = true;
+  return c;
+}
+
+static void tune_record(uint64_t key, int cand, cudaEvent_t e0, cudaEvent_t e1) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_pending.push_back(TunePending{key, cand, e0, e1});
+}
+
+int tune_set_enabled(int on) {
+  const int old = g_tune_on.load();
+  g_tune_on.store(on ? 1 : 0);
+  return old;
+}
+// One line per tuned class: "ks kb ncta epi f8 log2tiles pairs t0 t1"
+// (median sampled time in microseconds of single / paired issue, -1 = no
+// sample).
+std::string tune_report() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_poll_locked();
+  std::string out;
+  char line[256];
+  for (const auto &kv : g_tune) {
+    if (!kv.second.tuned) continue;
+    const uint64_t k = kv.first;
+    const TuneEntry &t = kv.second;
+    snprintf(line, sizeof(line), "%d %d %d %d %d %d %d %.1f %.1f\n", (int)((k >> 32) & 0xFF),
+             (int)((k >> 24) & 0xFF), (int)((k >> 14) & 0x3FF), (int)((k >> 10) & 0xF),
+             (int)((k >> 9) & 1), (int)(k & 0x1FF), t.choice.pairs,
+             t.median(0), t.median(1));
+    out += line;
+  }
+  return out;
+}
+
 // Launch one tensor-core convolution.
 // in / in_G / in_goff: the input tensor of the first nkb0 K-blocks (all of
 // them when in1 is null); in1 / in1_G: the input of the remaining K-blocks.
@@ -919,44 +1066,61 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   } else {
     map1 = map;
   }
-  int per_nb = g_num_sms.load() / cv.nb;
-  if (per_nb < 1) per_nb = 1;
-  if (per_nb > a.tiles) per_nb = a.tiles;
-  const int grid = per_nb * cv.nb;
-  a.step_dx = per_nb % a.tiles_x;
-  a.step_dy = (per_nb / a.tiles_x) % a.tiles_y;
-  a.step_dp = per_nb / (a.tiles_x * a.tiles_y);
   cudaStream_t st = ctx->stream;
+  // one launch with a persistent grid of SMs / frac CTAs per N block
+  auto launch = [&](TcConvArgs &la, int frac) -> int {
+    int per_nb = g_num_sms.load() / cv.nb / frac;
+    if (per_nb < 1) per_nb = 1;
+    if (per_nb > la.tiles) per_nb = la.tiles;
+    const int grid = per_nb * cv.nb;
+    la.step_dx = per_nb % la.tiles_x;
+    la.step_dy = (per_nb / la.tiles_x) % la.tiles_y;
+    la.step_dp = per_nb / (la.tiles_x * la.tiles_y);
 #define PW_TC_CASE(KS_, KB_, N_, E_, F8_)                                                   \
-  if (cv.ks == KS_ && cv.kb == KB_ && cv.ncta == N_ && a.epi == E_ && cv.f8 == F8_) {       \
-    static std::once_flag attr;                                                             \
-    std::call_once(attr, [&] {                                                              \
-      cudaFuncSetAttribute(k_conv_tc<KS_, KB_, N_, E_, F8_>,                                \
-                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);        \
-    });                                                                                     \
-    k_conv_tc<KS_, KB_, N_, E_, F8_><<<grid, kConvThreads, smem, st>>>(map, map1, a);       \
-    ctx->launches += 1;                                                                     \
-    return PW_OK;                                                                           \
-  }
-  // BF16 plain stores (all shapes the stage entry accepts)
-  PW_TC_CASE(1, 32, 32, TE_STORE, false) PW_TC_CASE(1, 32, 64, TE_STORE, false)
-  PW_TC_CASE(1, 32, 128, TE_STORE, false) PW_TC_CASE(1, 64, 32, TE_STORE, false)
-  PW_TC_CASE(1, 64, 64, TE_STORE, false) PW_TC_CASE(1, 64, 128, TE_STORE, false)
-  PW_TC_CASE(3, 32, 32, TE_STORE, false) PW_TC_CASE(3, 32, 64, TE_STORE, false)
-  PW_TC_CASE(3, 32, 128, TE_STORE, false) PW_TC_CASE(3, 64, 32, TE_STORE, false)
-  PW_TC_CASE(3, 64, 64, TE_STORE, false) PW_TC_CASE(3, 64, 128, TE_STORE, false)
-  // ConvLSTM gates (K-block = C channels)
-  PW_TC_CASE(3, 32, 64, TE_LSTM, false) PW_TC_CASE(3, 64, 64, TE_LSTM, false)
-  // residual + head: 3x3 C->C of steps 2-4, 1x1 2C->C of step 1
-  PW_TC_CASE(3, 32, 32, TE_HEAD, false) PW_TC_CASE(3, 64, 64, TE_HEAD, false)
-  PW_TC_CASE(1, 64, 32, TE_HEAD, false) PW_TC_CASE(1, 64, 64, TE_HEAD, false)
-  // FP8: gates (N = 128 per CTA), residual-block convs of steps 2-4
-  PW_TC_CASE(3, 32, 128, TE_LSTM, true) PW_TC_CASE(3, 64, 128, TE_LSTM, true)
-  PW_TC_CASE(3, 32, 32, TE_STORE, true) PW_TC_CASE(3, 64, 64, TE_STORE, true)
-  PW_TC_CASE(3, 32, 32, TE_HEAD, true) PW_TC_CASE(3, 64, 64, TE_HEAD, true)
+    if (cv.ks == KS_ && cv.kb == KB_ && cv.ncta == N_ && la.epi == E_ && cv.f8 == F8_) {    \
+      static std::once_flag attr;                                                           \
+      std::call_once(attr, [&] {                                                            \
+        cudaFuncSetAttribute(k_conv_tc<KS_, KB_, N_, E_, F8_>,                              \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);      \
+      });                                                                                   \
+      k_conv_tc<KS_, KB_, N_, E_, F8_><<<grid, kConvThreads, smem, st>>>(map, map1, la);    \
+      ctx->launches += 1;                                                                   \
+      return PW_OK;                                                                         \
+    }
+    // BF16 plain stores (all shapes the stage entry accepts)
+    PW_TC_CASE(1, 32, 32, TE_STORE, false) PW_TC_CASE(1, 32, 64, TE_STORE, false)
+    PW_TC_CASE(1, 32, 128, TE_STORE, false) PW_TC_CASE(1, 64, 32, TE_STORE, false)
+    PW_TC_CASE(1, 64, 64, TE_STORE, false) PW_TC_CASE(1, 64, 128, TE_STORE, false)
+    PW_TC_CASE(3, 32, 32, TE_STORE, false) PW_TC_CASE(3, 32, 64, TE_STORE, false)
+    PW_TC_CASE(3, 32, 128, TE_STORE, false) PW_TC_CASE(3, 64, 32, TE_STORE, false)
+    PW_TC_CASE(3, 64, 64, TE_STORE, false) PW_TC_CASE(3, 64, 128, TE_STORE, false)
+    // ConvLSTM gates (K-block = C channels)
+    PW_TC_CASE(3, 32, 64, TE_LSTM, false) PW_TC_CASE(3, 64, 64, TE_LSTM, false)
+    // residual + head: 3x3 C->C of steps 2-4, 1x1 2C->C of step 1
+    PW_TC_CASE(3, 32, 32, TE_HEAD, false) PW_TC_CASE(3, 64, 64, TE_HEAD, false)
+    PW_TC_CASE(1, 64, 32, TE_HEAD, false) PW_TC_CASE(1, 64, 64, TE_HEAD, false)
+    // FP8: gates (N = 128 per CTA), residual-block convs of steps 2-4
+    PW_TC_CASE(3, 32, 128, TE_LSTM, true) PW_TC_CASE(3, 64, 128, TE_LSTM, true)
+    PW_TC_CASE(3, 32, 32, TE_STORE, true) PW_TC_CASE(3, 64, 64, TE_STORE, true)
+    PW_TC_CASE(3, 32, 32, TE_HEAD, true) PW_TC_CASE(3, 64, 64, TE_HEAD, true)
 #undef PW_TC_CASE
-  set_last_error("no tensor-core conv for this shape");
-  return PW_EUNSUPPORTED;
+    set_last_error("no tensor-core conv for this shape");
+    return PW_EUNSUPPORTED;
+  };
+  const uint64_t key = tune_key(cv, a.epi, a.tiles);
+  bool sample = false;
+  int cand = 0;
+  const TuneChoice ch = tune_next(key, a.stages >= 2 * a.nkb, st, sample, cand);
+  a.pairs = ch.pairs;
+  if (!sample) return launch(a, 1);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  s = launch(a, 1);
+  cudaEventRecord(e1, st);
+  tune_record(key, cand, e0, e1);
+  return s;
 }
 
 // ---- weights -------------------------------------------------------------

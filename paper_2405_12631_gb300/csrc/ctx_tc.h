@@ -19,4 +19,8 @@ int tc_error(Workspace &ws);
 void tc_error_reset(Workspace &ws, cudaStream_t st);
 int tc_conv_host(pw_ctx *ctx, int P, int H, int W, int cin, int cout, int ks, int act,
                  const float *x, const float *w, const float *b, float *y);
+// Autotuner of the tensor-core convolutions (ctx_tc.cu): enable / disable
+// (returns the previous setting) and a text report of the tuned classes.
+int tune_set_enabled(int on);
+std::string tune_report();
 }  // namespace pw

@@ -1,0 +1,44 @@
+"""Autotuner of the tensor-core convolutions: encoding and decoding with
+tuning disabled (default schedules) and enabled (candidate schedules sampled
+on the real launches) give bit-identical streams and images, and every tuned
+class keeps the faster of its sampled candidates."""
+import numpy as np
+import pytest
+
+import synthetic as S
+from tests._lib import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pw():
+    ensure_built()
+    import paper_2405_12631_gb300 as m
+    return m
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_autotune_does_not_change_results(pw, prec):
+    codec = pw.Codec(0, prec)
+    cfg = S.ModelConfig(levels=4, C=64, ll_mode=0)
+    model = codec.load_model(S.pack_blob(cfg, S.random_model(cfg, 4)))
+    img = S.rgb_natural(200, 296, seed=13)
+    old = pw.pw_autotune(0)
+    bs0 = codec.encode_image(model, img, q=8.0)
+    out0 = codec.decode_image(model, bs0)
+    pw.pw_autotune(1)
+    # the tuning samples run on real launches: repeat until classes converge
+    bs1 = [codec.encode_image(model, img, q=8.0) for _ in range(4)]
+    outs = [codec.decode_image(model, bs0) for _ in range(4)]
+    pw.pw_autotune(old)
+    assert all(b == bs0 for b in bs1)
+    assert all(np.array_equal(out0, o) for o in outs)
+    rep = pw.autotune_report()
+    assert rep, "no convolution class was tuned"
+    for e in rep:
+        t = e["us"]
+        if t[0] >= 0 and t[1] >= 0:
+            assert t[e["pairs"]] == min(t)
+    model.close()
+    codec.close()
