@@ -96,7 +96,9 @@ __device__ __forceinline__ float sigm_fast(float x) { return fmaf(0.5f, tanh_fas
 __device__ __forceinline__ float lrelu_f(float x) { return x >= 0.f ? x : 0.01f * x; }
 
 // ---------------------------------------------------------------------------
-enum { TE_STORE = 0, TE_LSTM = 1, TE_HEAD = 2 };
+// TE_HEADC: the residual + head 3x3 conv of steps 2-4 evaluated at the
+// step's own positions only (see the compact head below)
+enum { TE_STORE = 0, TE_LSTM = 1, TE_HEAD = 2, TE_HEADC = 3 };
 
 struct TcConvArgs {
   int P, H, W;
@@ -140,6 +142,14 @@ struct TcConvArgs {
   uint8_t *out8;
   int out8_G16;
   const float *out8_scale;
+  // out / out8 in the compact head's input layout when set: pixel-major and
+  // split by column phase, [P][H][4][W4 / 4][channels] (x = 4 j + phase,
+  // W4 = W rounded up to a multiple of 4; columns W .. W4 - 1 are written
+  // with zeros)
+  int out_ps;
+  // TE_HEADC: tile = cR rows of one parity x cJ step positions per row
+  // (cR * cJ = 128, cJ = 1 << cJlog)
+  int cR, cJ, cJlog;
   int *err;
 };
 
@@ -208,6 +218,9 @@ __device__ __forceinline__ void mma_fp8(uint32_t d, uint64_t a, uint64_t b, uint
       "l"(a), "l"(b), "r"(idesc), "r"(accum));
 }
 
+// pipeline stages at most (the barrier arrays below hold this many)
+constexpr int kMaxStages = 24;
+
 // shared memory: barriers [0, 1024), epilogue constants [1024, 4096)
 // (5 x NCTA floats), head partial sums [4096, 8192), then the resident
 // weights and the stages
@@ -224,13 +237,16 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
                                                     const __grid_constant__ CUtensorMap tmap1,
                                                     const TcConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem);       // [8]
-  uint64_t *empty = full + 8;                                // [8]
-  uint64_t *accf = empty + 8;                                // [kAcc]
+  // [0, 384): stage barriers; [384, 456): accumulator and weight barriers;
+  // 456: abort flag; 464: TMEM base; [512, 640): head barriers
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem);       // [kMaxStages]
+  uint64_t *empty = full + kMaxStages;                       // [kMaxStages]
+  uint64_t *accf = empty + kMaxStages;                       // [kAcc]
   uint64_t *acce = accf + kAcc;                              // [kAcc]
   uint64_t *wbar = acce + kAcc;                              // [1]
   volatile int *s_abort = reinterpret_cast<volatile int *>(wbar + 1);
-  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 256);
+  uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + 464);
+  static_assert(2 * kMaxStages * 8 + (2 * kAcc + 1) * 8 + 4 <= 464, "barrier area");
   // TE_HEAD: the column halves of a lane quadrant exchange partial (mu, rho)
   // sums through s_part[acc][quadrant][lane], signalled by hbar[acc][quadrant]
   uint64_t *hbar = reinterpret_cast<uint64_t *>(smem + 512);        // [kAcc * 4]
@@ -244,6 +260,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   uint8_t *wsm = smem + kConvHeader;
   uint8_t *stg = wsm + ((a.w_bytes + 1023) / 1024) * 1024;
 
+  // the head epilogue (residual + 1x1 C->2) on full tiles or compact ones
+  constexpr bool HEADK = EPI == TE_HEAD || EPI == TE_HEADC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nb = blockIdx.x % a.nb;
   const int cta = blockIdx.x / a.nb;
@@ -265,16 +283,18 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       s_bias[j] = a.bias[nb0 + j] * k;
       s_wsc[j] = (F8 ? a.w_scale[nb0 + j] : 1.f) * k;
       s_osc[j] = os;
-      if (EPI == TE_HEAD) { s_wh[j] = a.wh[j]; s_wh[NCTA + j] = a.wh[NCTA + j]; }
+      if (HEADK) { s_wh[j] = a.wh[j]; s_wh[NCTA + j] = a.wh[NCTA + j]; }
     }
   }
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
     for (int i = 0; i < kAcc; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], kEpiWarps); }
-    if (EPI == TE_HEAD)
+    if (HEADK)
       for (int i = 0; i < kAcc * 4; ++i) mbar_init(&hbar[i], 1);
     mbar_init(wbar, 1);
-    *s_abort = 0;
+    // the compact head's swizzled stages must start on 1024-byte boundaries
+    // (the swizzle pattern's period), else the kernel reports an error
+    *s_abort = (EPI == TE_HEADC && (smem_u32(stg) & 1023u)) ? 1 : 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -309,6 +329,28 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     for (int t = cta; t < a.tiles && !*s_abort;
          t += nctas, ti.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y)) {
       const int tx = ti.tx, ty = ti.ty, p = ti.p;
+      if constexpr (EPI == TE_HEADC) {
+        // compact head: one stage per tap, one box of cR rows x cJ positions
+        // x all channels (one 128-row swizzled K-major slab). Output (row, j)
+        // of the tile is at y = 2 (i0 + row) + par, x = aph + 4 (j0 + j); tap
+        // (dy, dx) reads row 2 (i0 + row) + v, v = par + dy, through the map
+        // of rows of parity v & 1 (index i0 + row + (v >> 1)), and column
+        // 4 (j0 + j) + u, u = aph + dx, as phase u & 3 of position
+        // j0 + j + (u >> 2). Out-of-range boxes read zeros (the padding).
+        const int par = ty & 1, i0 = (ty >> 1) * a.cR, j0 = tx * a.cJ;
+        const int aph = step_phase(a.step, par);
+        for (int tap = 0; tap < 9; ++tap) {
+          if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) break;
+          mbar_expect_tx(&full[stage], a.stage_bytes);
+          const int v = par + tap / 3 - 1, u = aph + tap % 3 - 1;
+          const CUtensorMap *mp = (v & 1) ? &tmap1 : &tmap;
+          tma_load_5d(stg + (size_t)stage * a.stage_bytes, mp, &full[stage], 0, j0 + (u >> 2),
+                      u & 3, i0 + (v >> 1), p);
+          ++issued;
+          if (++stage == a.stages) { stage = 0; phase ^= 1; }
+        }
+        continue;
+      }
       for (int kbi = 0; kbi < a.nkb; ++kbi) {
         if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) break;
         mbar_expect_tx(&full[stage], a.stage_bytes);
@@ -367,6 +409,41 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       fence_after();
       const uint32_t d0 = tbase + (uint32_t)(acc * NCTA), d1 = tbase + (uint32_t)(acc1 * NCTA);
       uint32_t accum = 0;
+      if constexpr (EPI == TE_HEADC) {
+        // one stage per tap: A = 128 positions x KB channels, rows of
+        // KB * element bytes (32, 64 or 128) swizzled like the TMA wrote
+        // them; each MMA takes the next 32 bytes of K within the rows
+        constexpr uint32_t rowb = KB * (F8 ? 1 : 2);
+        constexpr uint32_t swz = rowb == 128 ? 2u : rowb == 64 ? 4u : 6u;
+        const uint64_t b0 = sdesc(smem_u32(wsm), NCTA * 16u, 128u);
+        for (int tap = 0; tap < 9; ++tap) {
+          int s0 = stage + tap;
+          uint32_t p0 = phase;
+          if (s0 >= a.stages) { s0 -= a.stages; p0 ^= 1; }
+          int s1 = s0 + 9;
+          uint32_t p1 = p0;
+          if (s1 >= a.stages) { s1 -= a.stages; p1 ^= 1; }
+          if (!mbar_wait(&full[s0], p0, s_abort)) { ok = false; break; }
+          if (two && !mbar_wait(&full[s1], p1, s_abort)) { ok = false; break; }
+          fence_after();
+          const uint64_t a0 = sdesc_sw(smem_u32(stg + (size_t)s0 * a.stage_bytes), 8u * rowb, swz);
+          const uint64_t a1 = sdesc_sw(smem_u32(stg + (size_t)s1 * a.stage_bytes), 8u * rowb, swz);
+#pragma unroll
+          for (int s = 0; s < KSTEPS; ++s) {
+            const uint32_t aoff = (32u * s) >> 4;
+            const uint32_t boff = ((uint32_t)(tap * GPK + 2 * s) * (NCTA * 16u)) >> 4;
+            if (F8) mma_fp8(d0, a0 + aoff, b0 + boff, idesc, accum);
+            else mma_bf16(d0, a0 + aoff, b0 + boff, idesc, accum);
+            if (two) {
+              if (F8) mma_fp8(d1, a1 + aoff, b0 + boff, idesc, accum);
+              else mma_bf16(d1, a1 + aoff, b0 + boff, idesc, accum);
+            }
+            accum = 1;
+          }
+          mma_commit(&empty[s0]);
+          if (two) mma_commit(&empty[s1]);
+        }
+      } else
       for (int kbi = 0; kbi < a.nkb; ++kbi) {
         // stage of this K-block of tile 0 and (nkb stages later) of tile 1
         int s0 = stage + kbi;
@@ -427,7 +504,15 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     for (int t = cta; t < a.tiles;
          t += nctas, ti.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y)) {
       const int tx = ti.tx, ty = ti.ty, p = ti.p;
-      const int y = ty * kTileH + r, x = tx * kTileW + c;
+      int y, x;
+      if constexpr (EPI == TE_HEADC) {
+        const int par = ty & 1;
+        y = 2 * ((ty >> 1) * a.cR + (m >> a.cJlog)) + par;
+        x = step_phase(a.step, par) + 4 * (tx * a.cJ + (m & (a.cJ - 1)));
+      } else {
+        y = ty * kTileH + r;
+        x = tx * kTileW + c;
+      }
       const bool valid = y < a.H && x < a.W;
       const int64_t hw = (int64_t)a.H * a.W;
       const int64_t pix = (int64_t)y * a.W + x;
@@ -436,7 +521,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       // load them before waiting so their latency overlaps the MMAs.
       constexpr int NPF = (EPI == TE_LSTM) ? NH / 4 : 1;
       float pf[NPF];
-      uint4 pres[(EPI == TE_HEAD || EPI == TE_STORE) ? NH / 8 : 1];
+      uint4 pres[(HEADK || EPI == TE_STORE) ? NH / 8 : 1];
       if (work && valid) {
         if (EPI == TE_LSTM) {
           const int Hp = a.H >> a.up, Wp = a.W >> a.up;
@@ -447,11 +532,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
             if (!a.first) c4 = __ldg(reinterpret_cast<const float4 *>(a.c_prev + ppix * a.C + n0 / 4 + k));
             pf[k] = c4.x; pf[k + 1] = c4.y; pf[k + 2] = c4.z; pf[k + 3] = c4.w;
           }
-        } else if (EPI == TE_HEAD || (EPI == TE_STORE && a.res)) {
+        } else if (HEADK || (EPI == TE_STORE && a.res)) {
           const bool need = (EPI == TE_STORE) ||
                             (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step);
           if (need) {
-            if (EPI == TE_HEAD && a.res_compact_n) {
+            if (HEADK && a.res_compact_n) {
               const int64_t qn = step_index(a.W, a.step, y, x);
 #pragma unroll
               for (int g = 0; g < NH / 8; ++g)
@@ -484,7 +569,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       // partner's partial sums for this tile (which then cannot be overwritten)
       const int cur_acc = acc;
       const uint32_t cur_phase = aphase;
-      if (lane == 0 && !(EPI == TE_HEAD && half == 0)) mbar_arrive(&acce[acc]);
+      if (lane == 0 && !(HEADK && half == 0)) mbar_arrive(&acce[acc]);
       if (++acc == kAcc) { acc = 0; aphase ^= 1; }
       if (!work) continue;
 
@@ -497,7 +582,34 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       }
       // (the head's halves must both reach the partial-sum handoff, so
       // invalid positions only skip the work inside it)
-      if (!valid && EPI != TE_HEAD) continue;
+      // element offsets of this thread's 16-byte chunk g in out (BF16) and
+      // out8 (bytes): blocked planes, or the phase-split pixel-major layout
+      const int64_t psix = (((int64_t)p * a.H + y) * 4 + (x & 3)) * (((a.W + 3) & ~3) >> 2) + (x >> 2);
+      auto off_out = [&](int g) -> int64_t {
+        return a.out_ps ? psix * (int64_t)(G * 8) + n0 + 8 * g
+                        : (((int64_t)p * G + a.out_goff + (n0 >> 3) + g) * hw + pix) * 8;
+      };
+      auto off_out8 = [&](int g) -> int64_t {
+        return a.out_ps ? psix * (int64_t)(a.out8_G16 * 16) + n0 + 16 * g
+                        : (((int64_t)p * a.out8_G16 + (n0 >> 4) + g) * hw + pix) * 16;
+      };
+      if (EPI == TE_STORE && !valid) {
+        // pad columns of the phase-split layout: zeros
+        if (a.out_ps && y < a.H && x < ((a.W + 3) & ~3)) {
+          if (a.out) {
+#pragma unroll
+            for (int g = 0; g < NH / 8; ++g)
+              *reinterpret_cast<uint4 *>(a.out + off_out(g)) = make_uint4(0u, 0u, 0u, 0u);
+          }
+          if (NH % 16 == 0 && a.out8) {
+#pragma unroll
+            for (int g = 0; g < NH / 16; ++g)
+              *reinterpret_cast<uint4 *>(a.out8 + off_out8(g)) = make_uint4(0u, 0u, 0u, 0u);
+          }
+        }
+        continue;
+      }
+      if (!valid && !HEADK) continue;
       if (EPI == TE_STORE) {
 #pragma unroll
         for (int g = 0; g < NH / 8; ++g) {
@@ -512,8 +624,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 #pragma unroll
             for (int e = 0; e < 8; ++e) v[8 * g + e] = lrelu_f(v[8 * g + e]);
           }
-          if (a.out)
-            store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + gg) * hw + pix) * 8, v + 8 * g);
+          if (a.out) store_bf16x8(a.out + off_out(g), v + 8 * g);
         }
         if (a.outc && step_of(y, x) == a.step) {
           const int64_t qn = step_index(a.W, a.step, y, x);
@@ -528,7 +639,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 #pragma unroll
             for (int e = 0; e < 16; ++e)
               f[e] = fold8 ? v[16 * g + e] : v[16 * g + e] * s_osc[col0 + 16 * g + e];
-            store_fp8x16(a.out8 + (((int64_t)p * a.out8_G16 + (n0 >> 4) + g) * hw + pix) * 16, f);
+            store_fp8x16(a.out8 + off_out8(g), f);
           }
         }
       } else if (EPI == TE_LSTM) {
@@ -877,6 +988,39 @@ static int make_map(CUtensorMap *map, const void *base, int P, int G, int H, int
   return PW_OK;
 }
 
+// Compact-head view of a phase-split pixel-major activation
+// [P][H][4][W4 / 4][C] (x = 4 j + phase): the rows of parity `par` as a 5-D
+// tensor (channels, j, phase, row / 2, plane); a box is R rows x J positions
+// of one phase with all C channels, landing as 128 rows of C elements in
+// the swizzled K-major layout of the row size (32, 64 or 128 bytes).
+static int make_map_hc(CUtensorMap *map, const void *base, int P, int C, int H, int W4, int par,
+                       int R, int J, bool f8) {
+  int s = get_encoder();
+  if (s) return s;
+  const cuuint64_t rowb = (cuuint64_t)C * (f8 ? 1 : 2);
+  cuuint64_t dims[5] = {(cuuint64_t)C, (cuuint64_t)W4 / 4, 4, (cuuint64_t)(H + 1 - par) / 2,
+                        (cuuint64_t)P};
+  cuuint64_t strides[4] = {rowb, rowb * (W4 / 4), rowb * W4 * 2, rowb * W4 * H};
+  cuuint32_t box[5] = {(cuuint32_t)C, (cuuint32_t)J, 1, (cuuint32_t)R, 1};
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapSwizzle sw = rowb == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : rowb == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_32B;
+  void *b = (void *)(static_cast<const uint8_t *>(base) + (size_t)par * W4 * rowb);
+  CUresult r = g_encode.load()(map, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                               5, b, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_error("cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return PW_ECUDA;
+  }
+  return PW_OK;
+}
+
+// The compact head applies to subbands of at least 4 rows and 8 columns.
+static bool headc_ok(int h, int w) { return h >= 4 && w >= 8; }
+
 static std::atomic<int> g_num_sms{0};
 
 // ---- autotuner -------------------------------------------------------------
@@ -1047,23 +1191,50 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   a.stage_bytes = (uint32_t)a.halo_x * a.halo_y * cv.kb * esz;
   a.w_bytes = (uint32_t)(cv.ks * cv.ks) * cv.cin * cv.ncta * esz;
   a.wt = cv.w; a.bias = cv.b; a.w_scale = cv.sw; a.err = err;
+  const bool hc = a.epi == TE_HEADC;
+  if (hc) {
+    // compact head: tiles of R rows of one parity x J step positions; the
+    // shape with the fewest tiles (ties: the wider one)
+    const int npos = std::max(row_count(W, step_phase(a.step, 0)), row_count(W, step_phase(a.step, 1)));
+    const int nrows = (H + 1) / 2;
+    int best = -1;
+    for (int lj = 3; lj <= 7; ++lj) {
+      const int J = 1 << lj, Rr = 128 / J;
+      const int n = ((npos + J - 1) / J) * ((nrows + Rr - 1) / Rr);
+      if (best < 0 || n <= best) { best = n; a.cJlog = lj; }
+    }
+    a.cJ = 1 << a.cJlog; a.cR = 128 / a.cJ;
+    a.tiles_x = (npos + a.cJ - 1) / a.cJ;
+    a.tiles_y = 2 * ((nrows + a.cR - 1) / a.cR);
+    a.tiles = P * a.tiles_x * a.tiles_y;
+    a.nkb = 9;                                   // stages per tile: the taps
+    a.stage_bytes = 128u * (uint32_t)cv.cin * esz;   // one tap: 128 rows x C channels
+  }
   const size_t fixed = kConvHeader + (a.w_bytes + 1023) / 1024 * 1024;
   const size_t maxsm = 227 * 1024;
   int stages = (int)((maxsm - fixed) / a.stage_bytes);
-  stages = stages > 6 ? 6 : stages;
+  const int smax = hc ? 18 : 6;
+  static_assert(18 <= kMaxStages, "stage barriers");
+  stages = stages > smax ? smax : stages;
   if (stages < 2) { set_last_error("tensor-core conv does not fit in shared memory"); return PW_EUNSUPPORTED; }
   a.stages = stages;
   const size_t smem = fixed + (size_t)stages * a.stage_bytes;
   CUtensorMap map, map1;
-  int s = make_map(&map, in, P, in_G, H, W, a.halo_x, a.halo_y, cv.kb / epg, cv.f8);
-  if (s) return s;
+  int s;
+  if (hc) {
+    const int W4 = (W + 3) & ~3;
+    if ((s = make_map_hc(&map, in, P, cv.cin, H, W4, 0, a.cR, a.cJ, cv.f8))) return s;
+    if ((s = make_map_hc(&map1, in, P, cv.cin, H, W4, 1, a.cR, a.cJ, cv.f8))) return s;
+  } else if ((s = make_map(&map, in, P, in_G, H, W, a.halo_x, a.halo_y, cv.kb / epg, cv.f8))) {
+    return s;
+  }
   a.nkb0 = a.nkb;
   a.in1_goff = in1_goff;
-  if (in1) {
+  if (in1 && !hc) {
     a.nkb0 = nkb0;
     if ((s = make_map(&map1, in1, P, in1_G, H, W, a.halo_x, a.halo_y, cv.kb / epg, cv.f8)))
       return s;
-  } else {
+  } else if (!hc) {
     map1 = map;
   }
   cudaStream_t st = ctx->stream;
@@ -1103,6 +1274,9 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     PW_TC_CASE(3, 32, 128, TE_LSTM, true) PW_TC_CASE(3, 64, 128, TE_LSTM, true)
     PW_TC_CASE(3, 32, 32, TE_STORE, true) PW_TC_CASE(3, 64, 64, TE_STORE, true)
     PW_TC_CASE(3, 32, 32, TE_HEAD, true) PW_TC_CASE(3, 64, 64, TE_HEAD, true)
+    // compact heads of steps 2-4
+    PW_TC_CASE(3, 32, 32, TE_HEADC, false) PW_TC_CASE(3, 64, 64, TE_HEADC, false)
+    PW_TC_CASE(3, 32, 32, TE_HEADC, true) PW_TC_CASE(3, 64, 64, TE_HEADC, true)
 #undef PW_TC_CASE
     set_last_error("no tensor-core conv for this shape");
     return PW_EUNSUPPORTED;
@@ -1386,31 +1560,45 @@ static int64_t compact_elems(int h, int w) {
   return (int64_t)((h + 1) >> 1) * (row_count(w, step_phase(0, 0)) + row_count(w, step_phase(0, 1)));
 }
 
+// Largest subband with its width rounded up to a multiple of 4 (the pitched
+// u of the compact head), at least the largest plain subband.
+static int64_t pitched_elems(const Geometry &g) {
+  int64_t m = 0;
+  for (int sb = 0; sb < g.nsb; ++sb)
+    m = std::max(m, (int64_t)g.sh[sb] * std::max((g.sw[sb] + 3) & ~3, g.sw[sb]));
+  return m;
+}
+
 int64_t tc_workspace_bytes(const Geometry &g, int P, int C, bool f8) {
   const int64_t big = (int64_t)P * g.sh.back() * g.sw.back();
+  const int64_t big4 = (int64_t)P * pitched_elems(g);
   int64_t cmax = 0;
   for (int sb = 0; sb < g.nsb; ++sb) cmax = std::max(cmax, compact_elems(g.sh[sb], g.sw[sb]));
   cmax *= P;
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
-  int64_t tot = 1024 + al(big * 2 * C * 2) + 5 * al(big * C * 2) + al(big * 2 * C * 2) +
+  int64_t tot = 1024 + al(big * 2 * C * 2) + 4 * al(big * C * 2) +
+                al(std::max(big * 2, big4) * C * 2) + al(big * C * 2) +
                 3 * al(cmax * C * 2) + al(cmax * 2 * C * 2) + al(big * 32 * 2);
-  if (f8) tot += al(big * 2 * C) + 4 * al(big * C);
+  if (f8) tot += al(big * 2 * C) + 3 * al(big * C) + al(big4 * C);
   return tot;
 }
 
 int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C, bool f8) {
   const int64_t big = (int64_t)ws->P * g.sh.back() * g.sw.back();
+  const int64_t big4 = (int64_t)ws->P * pitched_elems(g);
   int64_t cmax = 0;
   for (int sb = 0; sb < g.nsb; ++sb) cmax = std::max(cmax, compact_elems(g.sh[sb], g.sw[sb]));
   cmax *= ws->P;
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
   // X (2C), L0 (C), L1 (C), Z (C), U (2C), V (C), Z2 (C); compact Vc, Zc,
-  // Z2c (C), U2c (2C); T (32); bf16. FP8: X8 (2C), L8 x 2, Z8, U8 (C) bytes
+  // Z2c (C), U2c (2C); T (32); bf16. FP8: X8 (2C), L8 x 2, Z8, U8 (C) bytes.
+  // U and U8 also hold the pitched input of the compact head (big4)
   constexpr int kN = 12, kN8 = 5;
   const int64_t sizes[kN] = {big * 2 * C * 2, big * C * 2,  big * C * 2,      big * C * 2,
-                             big * 2 * C * 2, big * C * 2,  big * C * 2,      cmax * C * 2,
-                             cmax * C * 2,    cmax * C * 2, cmax * 2 * C * 2, big * 32 * 2};
-  const int64_t sizes8[kN8] = {big * 2 * C, big * C, big * C, big * C, big * C};
+                             std::max(big * 2, big4) * C * 2, big * C * 2,  big * C * 2,
+                             cmax * C * 2,    cmax * C * 2, cmax * C * 2, cmax * 2 * C * 2,
+                             big * 32 * 2};
+  const int64_t sizes8[kN8] = {big * 2 * C, big * C, big * C, big * C, big4 * C};
   int64_t tot = 1024;
   for (int64_t v : sizes) tot += al(v);
   if (f8)
@@ -1579,25 +1767,33 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
                  pix * (2.0 * (zt.cin + zt.cout) + (f8 ? C : 0)));
     if ((s = conv_tc(ctx, zt, l, G, 0, P, h, w, a, t.err, t.T, 4, 0, C / 32))) return s;
   }
+  // The head conv's outputs are used at this step's positions only (a
+  // quarter of the plane): where the subband is large enough it runs on
+  // those alone (TE_HEADC), reading u in the phase-split layout.
+  const bool hcm = headc_ok(h, w);
+  const int ups = hcm ? 1 : 0;
+  const double kpix = hcm ? (double)P * nk : pix;   // positions the head computes
   if (f8) {
     a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = nullptr; a.out_G = G;
-    a.out8 = t.U8; a.out8_G16 = G16; a.out8_scale = usc;
+    a.out8 = t.U8; a.out8_G16 = G16; a.out8_scale = usc; a.out_ps = ups;
     {
       ProfScope ps(ctx, KC_CONV3, 2.0 * pix * 9 * C * C, pix * 2.0 * C);
       if ((s = conv_tc(ctx, c1, t.Z8, G16, 0, P, h, w, a, t.err))) return s;  // u = lrelu(3x3 z)
     }
-    a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Zc; a.res_G = G; a.res_compact_n = (int)nk;
+    a = TcConvArgs{}; a.epi = hcm ? TE_HEADC : TE_HEAD; a.res = t.Zc; a.res_G = G;
+    a.res_compact_n = (int)nk;
     a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
     a.mu_out = mu; a.sg_out = sgp;
-    ProfScope ps(ctx, KC_CONV3, 2.0 * pix * 9 * C * C, pix * 1.5 * C);
+    ProfScope ps(ctx, KC_CONV3, 2.0 * kpix * 9 * C * C, pix * C + kpix * 2.0 * C);
     return conv_tc(ctx, c2, t.U8, G16, 0, P, h, w, a, t.err);               // head
   }
-  a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
+  a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G; a.out_ps = ups;
   if ((s = conv(c1, t.Z, G, 0, a, 0))) return s;                  // u = lrelu(conv3x3 z)
-  a = TcConvArgs{}; a.epi = TE_HEAD; a.res = t.Z; a.res_G = G;
+  a = TcConvArgs{}; a.epi = hcm ? TE_HEADC : TE_HEAD; a.res = t.Z; a.res_G = G;
   a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
   a.mu_out = mu; a.sg_out = sgp;
-  return conv(c2, t.U, G, 0, a, 0);                                // head
+  ProfScope ps(ctx, KC_CONV3, 2.0 * kpix * 9 * C * C, pix * 2.0 * C + kpix * 4.0 * C);
+  return conv_tc(ctx, c2, t.U, G, 0, P, h, w, a, t.err);          // head
 }
 
 // Stage entry: one tensor-core convolution on host data (testing).

@@ -161,3 +161,40 @@ def test_bf16_ar_ll_roundtrip(tc):
     for im in (S.gray_sinusoids(64, 96, seed=15), S.rgb_natural(48, 80, seed=16)):
         bs = tc.encode_image(gm, im, q=8.0)
         assert np.array_equal(tc.decode_symbols(gm, bs), tc.analyse(gm, im, q=8.0))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_compact_head_ragged_subbands_vs_oracle(pw, prec):
+    """The head convolution of steps 2-4 runs on the step's own positions
+    only (a quarter of the plane). Subbands whose width is not a multiple of
+    4 (18 and 9 columns here) and whose height is odd (7 rows) exercise its
+    border handling; the entropy parameters stay within the precision's
+    error against the FP64 oracle everywhere, including the last columns."""
+    codec = pw.Codec(0, prec)
+    blob = _blob(64)
+    gm = codec.load_model(blob)
+    om = K.Model(blob)
+    H, W = 112, 144       # subbands 56x72, 28x36, 14x18, 7x9
+    img = S.gray_sinusoids(H, W, seed=21)
+    planes, _ = K.colour_forward(img, False, 8)
+    qsb = [K.quantise(s, np.float32(1 / 8.0)) for s in om.lift.forward(K.pad_plane(planes[0], 16), 4, False)]
+    mu, sg = codec.context_params(gm, H, W, np.concatenate([q.reshape(-1) for q in qsb]))
+    ref = K.context_params_all(om, qsb)
+    o = 0
+    worst = 0.0
+    for q, (mo, so) in zip(qsb, ref):
+        n = q.size
+        m_g = mu[o:o + n].reshape(q.shape)
+        s_g = sg[o:o + n].reshape(q.shape)
+        o += n
+        e_mu = np.abs(m_g - mo) / np.maximum(np.abs(mo), 1.0)
+        e_sg = np.abs(s_g - so) / so
+        assert np.all(np.isfinite(m_g)) and np.all(np.isfinite(s_g))
+        worst = max(worst, float(e_mu[:, -2:].max()), float(e_sg[:, -2:].max()))
+        assert e_mu.mean() < 0.02 and e_sg.mean() < 0.02, (q.shape, e_mu.mean(), e_sg.mean())
+        assert e_mu.max() < 0.25 and e_sg.max() < 0.25, (q.shape, e_mu.max(), e_sg.max())
+    print(f"{prec}: worst relative error in the last two columns {worst:.2e}")
+    bs = codec.encode_image(gm, img, q=8.0)
+    assert np.array_equal(codec.decode_symbols(gm, bs), codec.analyse(gm, img, q=8.0))
+    gm.close()
+    codec.close()
