@@ -148,8 +148,9 @@ struct TcConvArgs {
   // with zeros)
   int out_ps;
   // TE_HEADC: tile = cR rows of one parity x cJ step positions per row
-  // (cR * cJ = 128, cJ = 1 << cJlog)
-  int cR, cJ, cJlog;
+  // (cR * cJ = 128, cJ = 1 << cJlog); tps = taps per pipeline stage (1, 3
+  // or 9)
+  int cR, cJ, cJlog, tps;
   int *err;
 };
 
@@ -330,8 +331,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
          t += nctas, ti.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y)) {
       const int tx = ti.tx, ty = ti.ty, p = ti.p;
       if constexpr (EPI == TE_HEADC) {
-        // compact head: one stage per tap, one box of cR rows x cJ positions
-        // x all channels (one 128-row swizzled K-major slab). Output (row, j)
+        // compact head: a stage holds a.tps taps (9 / a.tps stages per
+        // tile), one box per tap of cR rows x cJ positions x all channels
+        // (one 128-row swizzled K-major slab). Output (row, j)
         // of the tile is at y = 2 (i0 + row) + par, x = aph + 4 (j0 + j); tap
         // (dy, dx) reads row 2 (i0 + row) + v, v = par + dy, through the map
         // of rows of parity v & 1 (index i0 + row + (v >> 1)), and column
@@ -339,13 +341,17 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         // j0 + j + (u >> 2). Out-of-range boxes read zeros (the padding).
         const int par = ty & 1, i0 = (ty >> 1) * a.cR, j0 = tx * a.cJ;
         const int aph = step_phase(a.step, par);
-        for (int tap = 0; tap < 9; ++tap) {
+        const uint32_t box = a.stage_bytes / a.tps;
+        for (int k0 = 0; k0 < 9; k0 += a.tps) {
           if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) break;
           mbar_expect_tx(&full[stage], a.stage_bytes);
-          const int v = par + tap / 3 - 1, u = aph + tap % 3 - 1;
-          const CUtensorMap *mp = (v & 1) ? &tmap1 : &tmap;
-          tma_load_5d(stg + (size_t)stage * a.stage_bytes, mp, &full[stage], 0, j0 + (u >> 2),
-                      u & 3, i0 + (v >> 1), p);
+          for (int tt = 0; tt < a.tps; ++tt) {
+            const int tap = k0 + tt;
+            const int v = par + tap / 3 - 1, u = aph + tap % 3 - 1;
+            const CUtensorMap *mp = (v & 1) ? &tmap1 : &tmap;
+            tma_load_5d(stg + (size_t)stage * a.stage_bytes + tt * box, mp, &full[stage], 0,
+                        j0 + (u >> 2), u & 3, i0 + (v >> 1), p);
+          }
           ++issued;
           if (++stage == a.stages) { stage = 0; phase ^= 1; }
         }
@@ -410,17 +416,19 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const uint32_t d0 = tbase + (uint32_t)(acc * NCTA), d1 = tbase + (uint32_t)(acc1 * NCTA);
       uint32_t accum = 0;
       if constexpr (EPI == TE_HEADC) {
-        // one stage per tap: A = 128 positions x KB channels, rows of
-        // KB * element bytes (32, 64 or 128) swizzled like the TMA wrote
-        // them; each MMA takes the next 32 bytes of K within the rows
+        // a.nkb = 9 / a.tps stages per tile, a.tps taps per stage: A =
+        // 128 positions x KB channels per tap, rows of KB * element bytes
+        // (32, 64 or 128) swizzled like the TMA wrote them; each MMA takes
+        // the next 32 bytes of K within the rows
         constexpr uint32_t rowb = KB * (F8 ? 1 : 2);
         constexpr uint32_t swz = rowb == 128 ? 2u : rowb == 64 ? 4u : 6u;
         const uint64_t b0 = sdesc(smem_u32(wsm), NCTA * 16u, 128u);
-        for (int tap = 0; tap < 9; ++tap) {
-          int s0 = stage + tap;
+        const uint32_t boxd = (128u * rowb) >> 4;   // descriptor step per tap
+        for (int kbi = 0; kbi < a.nkb; ++kbi) {
+          int s0 = stage + kbi;
           uint32_t p0 = phase;
           if (s0 >= a.stages) { s0 -= a.stages; p0 ^= 1; }
-          int s1 = s0 + 9;
+          int s1 = s0 + a.nkb;
           uint32_t p1 = p0;
           if (s1 >= a.stages) { s1 -= a.stages; p1 ^= 1; }
           if (!mbar_wait(&full[s0], p0, s_abort)) { ok = false; break; }
@@ -428,17 +436,20 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           fence_after();
           const uint64_t a0 = sdesc_sw(smem_u32(stg + (size_t)s0 * a.stage_bytes), 8u * rowb, swz);
           const uint64_t a1 = sdesc_sw(smem_u32(stg + (size_t)s1 * a.stage_bytes), 8u * rowb, swz);
+          for (int tt = 0; tt < a.tps; ++tt) {
+            const int tap = kbi * a.tps + tt;
 #pragma unroll
-          for (int s = 0; s < KSTEPS; ++s) {
-            const uint32_t aoff = (32u * s) >> 4;
-            const uint32_t boff = ((uint32_t)(tap * GPK + 2 * s) * (NCTA * 16u)) >> 4;
-            if (F8) mma_fp8(d0, a0 + aoff, b0 + boff, idesc, accum);
-            else mma_bf16(d0, a0 + aoff, b0 + boff, idesc, accum);
-            if (two) {
-              if (F8) mma_fp8(d1, a1 + aoff, b0 + boff, idesc, accum);
-              else mma_bf16(d1, a1 + aoff, b0 + boff, idesc, accum);
+            for (int s = 0; s < KSTEPS; ++s) {
+              const uint32_t aoff = tt * boxd + ((32u * s) >> 4);
+              const uint32_t boff = ((uint32_t)(tap * GPK + 2 * s) * (NCTA * 16u)) >> 4;
+              if (F8) mma_fp8(d0, a0 + aoff, b0 + boff, idesc, accum);
+              else mma_bf16(d0, a0 + aoff, b0 + boff, idesc, accum);
+              if (two) {
+                if (F8) mma_fp8(d1, a1 + aoff, b0 + boff, idesc, accum);
+                else mma_bf16(d1, a1 + aoff, b0 + boff, idesc, accum);
+              }
+              accum = 1;
             }
-            accum = 1;
           }
           mma_commit(&empty[s0]);
           if (two) mma_commit(&empty[s1]);
@@ -1207,14 +1218,18 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     a.tiles_x = (npos + a.cJ - 1) / a.cJ;
     a.tiles_y = 2 * ((nrows + a.cR - 1) / a.cR);
     a.tiles = P * a.tiles_x * a.tiles_y;
-    a.nkb = 9;                                   // stages per tile: the taps
-    a.stage_bytes = 128u * (uint32_t)cv.cin * esz;   // one tap: 128 rows x C channels
+    // taps per stage: 3 (three commits per tile), or 1 where two tiles
+    // of 3-tap stages do not fit next to the weights
+    const uint32_t tapb = 128u * (uint32_t)cv.cin * esz;   // one tap: 128 rows x C
+    const size_t room = 227 * 1024 - kConvHeader - (a.w_bytes + 1023) / 1024 * 1024;
+    a.tps = room >= 6 * 3 * (size_t)tapb ? 3 : 1;
+    a.nkb = 9 / a.tps;                           // stages per tile
+    a.stage_bytes = (uint32_t)a.tps * tapb;
   }
   const size_t fixed = kConvHeader + (a.w_bytes + 1023) / 1024 * 1024;
   const size_t maxsm = 227 * 1024;
   int stages = (int)((maxsm - fixed) / a.stage_bytes);
-  const int smax = hc ? 18 : 6;
-  static_assert(18 <= kMaxStages, "stage barriers");
+  const int smax = hc ? std::min(kMaxStages, 2 * a.nkb + 2) : 6;
   stages = stages > smax ? smax : stages;
   if (stages < 2) { set_last_error("tensor-core conv does not fit in shared memory"); return PW_EUNSUPPORTED; }
   a.stages = stages;
