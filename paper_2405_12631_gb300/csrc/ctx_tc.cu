@@ -1229,7 +1229,8 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   const size_t fixed = kConvHeader + (a.w_bytes + 1023) / 1024 * 1024;
   const size_t maxsm = 227 * 1024;
   int stages = (int)((maxsm - fixed) / a.stage_bytes);
-  const int smax = hc ? std::min(kMaxStages, 2 * a.nkb + 2) : 6;
+  // deep pipelines keep enough bytes in flight for the HBM-bound 1x1 convs
+  const int smax = hc ? std::min(kMaxStages, 2 * a.nkb + 2) : (cv.ks == 1 ? 16 : 6);
   stages = stages > smax ? smax : stages;
   if (stages < 2) { set_last_error("tensor-core conv does not fit in shared memory"); return PW_EUNSUPPORTED; }
   a.stages = stages;
