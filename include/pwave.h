@@ -323,6 +323,12 @@ typedef struct {
 } pw_kernel_stat;
 int pw_ctx_profile(pw_ctx *ctx, int enable);
 int pw_ctx_kernel_stats(pw_ctx *ctx, pw_kernel_stat *out, int max);
+/* Like pw_ctx_profile, but records only the kernel classes whose bit is set
+ * in class_mask (bit k = class index k, see pw_kernel_class; 0 stops), so
+ * that one class can be timed with little perturbation of the others. */
+int pw_ctx_profile_classes(pw_ctx *ctx, uint32_t class_mask);
+/* Class index of a name that pw_ctx_kernel_stats reports, or -1. */
+int pw_kernel_class(const char *name);
 
 #ifdef __cplusplus
 }

@@ -109,6 +109,8 @@ _sig = {
     "pw_autotune_report": (C.c_int, [C.c_char_p, C.c_size_t]),
     "pw_ctx_profile": (C.c_int, [_P, C.c_int]),
     "pw_ctx_kernel_stats": (C.c_int, [_P, C.POINTER(pw_kernel_stat), C.c_int]),
+    "pw_ctx_profile_classes": (C.c_int, [_P, C.c_uint32]),
+    "pw_kernel_class": (C.c_int, [C.c_char_p]),
     "pw_free": (None, [_P]),
     "pw_strerror": (C.c_char_p, [C.c_int]),
     "pw_last_error": (C.c_char_p, []),

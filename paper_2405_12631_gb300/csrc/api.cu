@@ -726,7 +726,25 @@ int pw_ctx_profile(pw_ctx *c, int enable) {
   cudaStreamSynchronize(c->stream);
   p.reset();
   p.on = enable != 0;
+  p.mask = ~0u;
   return PW_OK;
+}
+
+int pw_ctx_profile_classes(pw_ctx *c, uint32_t class_mask) {
+  if (!c) return PW_EINVAL;
+  Prof &p = prof_of(c);
+  cudaStreamSynchronize(c->stream);
+  p.reset();
+  p.on = class_mask != 0;
+  p.mask = class_mask;
+  return PW_OK;
+}
+
+int pw_kernel_class(const char *name) {
+  if (!name) return -1;
+  for (int k = 0; k < KC_COUNT; ++k)
+    if (std::strcmp(name, kclass_name(k)) == 0) return k;
+  return -1;
 }
 
 int pw_ctx_kernel_stats(pw_ctx *c, pw_kernel_stat *out, int max) {

@@ -48,7 +48,7 @@ Prof::~Prof() {
 
 ProfScope::ProfScope(pw_ctx *c, int k, double f, double b) : ctx(c), cls(k), flops(f), bytes(b) {
   Prof &p = prof_of(ctx);
-  if (p.on) {
+  if (p.on && ((p.mask >> k) & 1u)) {
     a = p.get();
     cudaEventRecord(a, ctx->stream);
   }

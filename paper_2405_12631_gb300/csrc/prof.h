@@ -15,6 +15,7 @@ const char *kclass_name(int c);
 
 struct Prof {
   bool on = false;
+  uint32_t mask = ~0u;   // classes recorded while on (bit = KClass)
   struct Pending {
     int cls;
     cudaEvent_t a, b;
