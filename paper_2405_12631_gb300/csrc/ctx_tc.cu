@@ -326,53 +326,66 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     int stage = 0;
     uint32_t phase = 0;
     int issued = 0;
+    // Tiles come in rounds of one, or two (paired issue: the MMA warp
+    // interleaves two tiles into two accumulators) whose stages alternate:
+    // K-step k of the first tile, K-step k of the second, k + 1, ...
+    const bool pairs = a.pairs && a.stages >= 2;
     TileIter ti(cta, a.tiles_x, a.tiles_y);
-    for (int t = cta; t < a.tiles && !*s_abort;
-         t += nctas, ti.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y)) {
-      const int tx = ti.tx, ty = ti.ty, p = ti.p;
-      if constexpr (EPI == TE_HEADC) {
-        // compact head: a stage holds a.tps taps (9 / a.tps stages per
-        // tile), one box per tap of cR rows x cJ positions x all channels
-        // (one 128-row swizzled K-major slab). Output (row, j)
-        // of the tile is at y = 2 (i0 + row) + par, x = aph + 4 (j0 + j); tap
-        // (dy, dx) reads row 2 (i0 + row) + v, v = par + dy, through the map
-        // of rows of parity v & 1 (index i0 + row + (v >> 1)), and column
-        // 4 (j0 + j) + u, u = aph + dx, as phase u & 3 of position
-        // j0 + j + (u >> 2). Out-of-range boxes read zeros (the padding).
-        const int par = ty & 1, i0 = (ty >> 1) * a.cR, j0 = tx * a.cJ;
-        const int aph = step_phase(a.step, par);
-        const uint32_t box = a.stage_bytes / a.tps;
-        for (int k0 = 0; k0 < 9; k0 += a.tps) {
-          if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) break;
+    for (int t = cta; t < a.tiles && !*s_abort;) {
+      const bool two = pairs && t + nctas < a.tiles;
+      TileIter t1 = ti;
+      t1.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y);   // tile t + nctas
+      bool stop = false;
+      for (int kbi = 0; kbi < a.nkb && !stop; ++kbi) {
+        for (int u = 0; u < (two ? 2 : 1); ++u) {
+          const TileIter &tt = u ? t1 : ti;
+          const int tx = tt.tx, ty = tt.ty, p = tt.p;
+          if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) { stop = true; break; }
           mbar_expect_tx(&full[stage], a.stage_bytes);
-          for (int tt = 0; tt < a.tps; ++tt) {
-            const int tap = k0 + tt;
-            const int v = par + tap / 3 - 1, u = aph + tap % 3 - 1;
-            const CUtensorMap *mp = (v & 1) ? &tmap1 : &tmap;
-            tma_load_5d(stg + (size_t)stage * a.stage_bytes + tt * box, mp, &full[stage], 0,
-                        j0 + (u >> 2), u & 3, i0 + (v >> 1), p);
+          if constexpr (EPI == TE_HEADC) {
+            // compact head: K-step kbi = a.tps taps (9 / a.tps steps per
+            // tile), one box per tap of cR rows x cJ positions x all
+            // channels (one 128-row swizzled K-major slab). Output (row, j)
+            // of the tile is at y = 2 (i0 + row) + par, x = aph + 4 (j0 + j);
+            // tap (dy, dx) reads row 2 (i0 + row) + v, v = par + dy, through
+            // the map of rows of parity v & 1 (index i0 + row + (v >> 1)),
+            // and column 4 (j0 + j) + w, w = aph + dx, as phase w & 3 of
+            // position j0 + j + (w >> 2). Out-of-range boxes read zeros (the
+            // padding).
+            const int par = ty & 1, i0 = (ty >> 1) * a.cR, j0 = tx * a.cJ;
+            const int aph = step_phase(a.step, par);
+            const uint32_t box = a.stage_bytes / a.tps;
+            for (int k = 0; k < a.tps; ++k) {
+              const int tap = kbi * a.tps + k;
+              const int v = par + tap / 3 - 1, w = aph + tap % 3 - 1;
+              const CUtensorMap *mp = (v & 1) ? &tmap1 : &tmap;
+              tma_load_5d(stg + (size_t)stage * a.stage_bytes + k * box, mp, &full[stage], 0,
+                          j0 + (w >> 2), w & 3, i0 + (v >> 1), p);
+            }
+          } else {
+            // K-blocks [0, nkb0) come through tmap (group offset in_goff),
+            // the rest through tmap1 (groups counted from 0); innermost
+            // coordinate = pixel x * 8 channels (a multiple of 8 elements =
+            // 16 bytes, also when negative at the left border)
+            if (kbi < a.nkb0)
+              tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage],
+                          (tx * kTileW - R) * EPG, ty * kTileH - R, a.in_goff + kbi * GPK, p);
+            else
+              tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap1, &full[stage],
+                          (tx * kTileW - R) * EPG, ty * kTileH - R,
+                          a.in1_goff + (kbi - a.nkb0) * GPK, p);
           }
           ++issued;
           if (++stage == a.stages) { stage = 0; phase ^= 1; }
         }
-        continue;
       }
-      for (int kbi = 0; kbi < a.nkb; ++kbi) {
-        if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) break;
-        mbar_expect_tx(&full[stage], a.stage_bytes);
-        // K-blocks [0, nkb0) come through tmap (group offset in_goff), the
-        // rest through tmap1 (groups counted from 0)
-        // innermost coordinate = pixel x * 8 channels (a multiple of 8
-        // elements = 16 bytes, also when negative at the left border)
-        if (kbi < a.nkb0)
-          tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage],
-                      (tx * kTileW - R) * EPG, ty * kTileH - R, a.in_goff + kbi * GPK, p);
-        else
-          tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap1, &full[stage],
-                      (tx * kTileW - R) * EPG, ty * kTileH - R,
-                      a.in1_goff + (kbi - a.nkb0) * GPK, p);
-        ++issued;
-        if (++stage == a.stages) { stage = 0; phase ^= 1; }
+      if (stop) break;
+      t += (two ? 2 : 1) * nctas;
+      if (two) {
+        ti = t1;
+        ti.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y);
+      } else {
+        ti = t1;
       }
     }
     // let every copy this thread issued land before the CTA can exit
@@ -400,12 +413,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     bool ok = mbar_wait(wbar, 0, s_abort);
     int stage = 0, acc = 0;
     uint32_t phase = 0, aphase = 0;
-    // a.pairs: two tiles per round (when both tiles' K-blocks fit in the
-    // stages), their MMAs interleaved into two accumulators so that
+    // a.pairs: two tiles per round (the producer alternates their K-blocks,
+    // so two stages suffice), their MMAs interleaved into two accumulators so that
     // consecutive MMAs never depend on each other's accumulator (the
     // autotuner decides per shape class: faster for the FP8 3x3 convs,
     // slower for the HBM-bound 1x1 convs)
-    const bool pairs = a.pairs && a.stages >= 2 * a.nkb;
+    const bool pairs = a.pairs && a.stages >= 2;
     for (int t = cta; ok && t < a.tiles; t += (pairs ? 2 : 1) * nctas) {
       const bool two = pairs && t + nctas < a.tiles;
       const int acc1 = acc + 1 == kAcc ? 0 : acc + 1;
@@ -425,10 +438,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         const uint64_t b0 = sdesc(smem_u32(wsm), NCTA * 16u, 128u);
         const uint32_t boxd = (128u * rowb) >> 4;   // descriptor step per tap
         for (int kbi = 0; kbi < a.nkb; ++kbi) {
-          int s0 = stage + kbi;
+          // stages of K-step kbi: the first tile's, then (paired) the second's
+          int s0 = stage + (two ? 2 * kbi : kbi);
           uint32_t p0 = phase;
-          if (s0 >= a.stages) { s0 -= a.stages; p0 ^= 1; }
-          int s1 = s0 + a.nkb;
+          while (s0 >= a.stages) { s0 -= a.stages; p0 ^= 1; }
+          int s1 = s0 + 1;
           uint32_t p1 = p0;
           if (s1 >= a.stages) { s1 -= a.stages; p1 ^= 1; }
           if (!mbar_wait(&full[s0], p0, s_abort)) { ok = false; break; }
@@ -456,11 +470,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         }
       } else
       for (int kbi = 0; kbi < a.nkb; ++kbi) {
-        // stage of this K-block of tile 0 and (nkb stages later) of tile 1
-        int s0 = stage + kbi;
+        // stages of this K-block: the first tile's, then (paired) the second's
+        int s0 = stage + (two ? 2 * kbi : kbi);
         uint32_t p0 = phase;
-        if (s0 >= a.stages) { s0 -= a.stages; p0 ^= 1; }
-        int s1 = s0 + a.nkb;
+        while (s0 >= a.stages) { s0 -= a.stages; p0 ^= 1; }
+        int s1 = s0 + 1;
         uint32_t p1 = p0;
         if (s1 >= a.stages) { s1 -= a.stages; p1 ^= 1; }
         if (!mbar_wait(&full[s0], p0, s_abort)) { ok = false; break; }
@@ -1218,11 +1232,11 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     a.tiles_x = (npos + a.cJ - 1) / a.cJ;
     a.tiles_y = 2 * ((nrows + a.cR - 1) / a.cR);
     a.tiles = P * a.tiles_x * a.tiles_y;
-    // taps per stage: 3 (three commits per tile), or 1 where two tiles
-    // of 3-tap stages do not fit next to the weights
+    // taps per stage: 3 (three commits per tile), or 1 where three 3-tap
+    // stages do not fit next to the weights
     const uint32_t tapb = 128u * (uint32_t)cv.cin * esz;   // one tap: 128 rows x C
     const size_t room = 227 * 1024 - kConvHeader - (a.w_bytes + 1023) / 1024 * 1024;
-    a.tps = room >= 6 * 3 * (size_t)tapb ? 3 : 1;
+    a.tps = room >= 3 * 3 * (size_t)tapb ? 3 : 1;
     a.nkb = 9 / a.tps;                           // stages per tile
     a.stage_bytes = (uint32_t)a.tps * tapb;
   }
@@ -1300,7 +1314,7 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   const uint64_t key = tune_key(cv, a.epi, a.tiles);
   bool sample = false;
   int cand = 0;
-  const TuneChoice ch = tune_next(key, a.stages >= 2 * a.nkb, st, sample, cand);
+  const TuneChoice ch = tune_next(key, a.stages >= 2, st, sample, cand);
   a.pairs = ch.pairs;
   if (!sample) return launch(a, 1);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
