@@ -116,8 +116,10 @@ struct TcConvArgs {
   int out_G, out_goff;
   const __nv_bfloat16 *res;
   int res_G, res_goff;
-  const float *c_prev;
-  float *c_new;
+  // ConvLSTM cell state, BF16 [P][H][W][C] (previous subband's resolution
+  // for c_prev)
+  const __nv_bfloat16 *c_prev;
+  __nv_bfloat16 *c_new;
   int up, first, C;
   const float *wh, *bh;
   int step;
@@ -544,7 +546,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const int n0 = nb * NCTA + col0;   // first output column handled here
       // Global operands of the epilogue do not depend on the accumulator:
       // load them before waiting so their latency overlaps the MMAs.
-      constexpr int NPF = (EPI == TE_LSTM) ? NH / 4 : 1;
+      constexpr int NPF = (EPI == TE_LSTM) ? NH / 4 : 8;
+      static_assert(NPF % 8 == 0, "cell state in 8-channel groups");
       float pf[NPF];
       uint4 pres[(HEADK || EPI == TE_STORE) ? NH / 8 : 1];
       if (work && valid) {
@@ -552,10 +555,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           const int Hp = a.H >> a.up, Wp = a.W >> a.up;
           const int64_t ppix = ((int64_t)p * Hp + (y >> a.up)) * Wp + (x >> a.up);
 #pragma unroll
-          for (int k = 0; k < NPF; k += 4) {
-            float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (!a.first) c4 = __ldg(reinterpret_cast<const float4 *>(a.c_prev + ppix * a.C + n0 / 4 + k));
-            pf[k] = c4.x; pf[k + 1] = c4.y; pf[k + 2] = c4.z; pf[k + 3] = c4.w;
+          for (int k = 0; k < NPF; k += 8) {
+            if (a.first) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) pf[k + e] = 0.f;
+            } else {
+              const uint4 c8 = __ldg(reinterpret_cast<const uint4 *>(a.c_prev + ppix * a.C + n0 / 4 + k));
+              load_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(&c8), pf + k);
+            }
           }
         } else if (HEADK || (EPI == TE_STORE && a.res)) {
           const bool need = (EPI == TE_STORE) ||
@@ -678,9 +685,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           hv[k] = sigm_fast(v[4 * k + 2]) * tanh_fast(cn[k]);
         }
 #pragma unroll
-        for (int k = 0; k < NH / 4; k += 4)
-          *reinterpret_cast<float4 *>(a.c_new + ((int64_t)p * hw + pix) * a.C + ch0 + k) =
-              make_float4(cn[k], cn[k + 1], cn[k + 2], cn[k + 3]);
+        for (int k = 0; k < NH / 4; k += 8)
+          store_bf16x8(a.c_new + ((int64_t)p * hw + pix) * a.C + ch0 + k, cn + k);
 #pragma unroll
         for (int g = 0; g < NH / 32; ++g)
           store_bf16x8(a.out + (((int64_t)p * G + a.out_goff + (ch0 >> 3) + g) * hw + pix) * 8,
@@ -1694,7 +1700,11 @@ int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   TcConvArgs a{};
   a.epi = TE_LSTM;
   a.out = lout; a.out_G = G; a.out_goff = 0;
-  a.c_prev = ws.Cst[cur]; a.c_new = ws.Cst[cur ^ 1]; a.up = up; a.first = first; a.C = C;
+  // the cell state is BF16 on the tensor-core path (half the bytes of the
+  // FP32 buffers it lives in)
+  a.c_prev = reinterpret_cast<const __nv_bfloat16 *>(ws.Cst[cur]);
+  a.c_new = reinterpret_cast<__nv_bfloat16 *>(ws.Cst[cur ^ 1]);
+  a.up = up; a.first = first; a.C = C;
   if (f8) { a.out8 = t.L8[sb & 1]; a.out8_G16 = G16; a.out8_scale = m.tc->h_scale; }
   ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * 2 * C * 4 * C,
                pix * ((f8 ? 2.0 : 4.0) * C + 2.0 * C + 8.0 * C + (f8 ? C : 0)));
