@@ -243,8 +243,10 @@ __device__ __forceinline__ bool lift_mma_wait(uint64_t *bar, uint32_t parity) {
   const int lane = threadIdx.x & 31;
   int ok = 1;
   if (lane == 0) {
+    // suspended try_wait: the waiting warps leave the issue slots to the
+    // other CTAs' warps on the SM instead of spinning
     const long long t0 = clock64();
-    while (!mbar_try(bar, parity))
+    while (!mbar_try_sleep(bar, parity, 2000u))
       if (clock64() - t0 > kWaitCycles) { ok = 0; break; }
   }
   ok = __shfl_sync(0xffffffffu, ok, 0);
