@@ -42,6 +42,9 @@ struct TcWeights {
     __nv_bfloat16 *w = nullptr;   // BF16 weights, or (f8) E4M3 bytes in the same order
     float *b = nullptr;
     float *sw = nullptr;          // f8: per-output-column scale of the accumulator
+    // ConvLSTM gates: BF16 weights of the v block (K-block 0, see
+    // TcConvArgs::wtv); w then holds the h block only (cin = C)
+    __nv_bfloat16 *wv = nullptr;
     int cin = 0, cout = 0, ks = 1, kb = 64, ncta = 64, nb = 1;
     bool f8 = false;
   };
@@ -81,6 +84,9 @@ struct TcAct {  // BF16 activations in [P][G][H][W][8]
   // Vc = dw3x3 output, Zc = block input (residual), Z2c = block output (C
   // each), U2c = feed-forward hidden layer (2C).
   __nv_bfloat16 *Vc = nullptr, *Zc = nullptr, *Z2c = nullptr, *U2c = nullptr;
+  // V16: the ConvLSTM gates' v block [P][2][H][W][8] (9 neighbour values of
+  // the upsampled previous subband, an inside indicator, zeros)
+  __nv_bfloat16 *V16 = nullptr;
   // T: masked neighbour values of steps 2-4 (32 channels, see TcWeights)
   __nv_bfloat16 *T = nullptr;
   // FP8 precision: E4M3 activations [P][G16][H][W][16]: X8 = [e, up(h)]
@@ -110,6 +116,12 @@ struct TcConvArgs {
   int stages, halo_x, halo_y;
   uint32_t stage_bytes, w_bytes;
   const __nv_bfloat16 *wt;      // [nb][kblock][tap][kb/8][ncta][8]
+  // ConvLSTM gates: K-block 0 is the 16-channel BF16 "v" block (the 9
+  // neighbour values of the upsampled previous subband and an inside
+  // indicator, weights wtv [nb][tap][2][ncta][8], wv_bytes per N block,
+  // stages of vstage_bytes) in place of e; wt then holds the h block only
+  const __nv_bfloat16 *wtv;
+  uint32_t wv_bytes, vstage_bytes;
   const float *bias;            // [nb * ncta]
   int epi, act;
   __nv_bfloat16 *out;
@@ -261,7 +273,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   float *s_osc = s_wsc + NCTA;
   float *s_wh = s_osc + NCTA;
   uint8_t *wsm = smem + kConvHeader;
-  uint8_t *stg = wsm + ((a.w_bytes + 1023) / 1024) * 1024;
+  uint8_t *stg = wsm + ((a.wv_bytes + a.w_bytes + 1023) / 1024) * 1024;
 
   // the head epilogue (residual + 1x1 C->2) on full tiles or compact ones
   constexpr bool HEADK = EPI == TE_HEAD || EPI == TE_HEADC;
@@ -320,10 +332,15 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   if (warp == 0 && lane == 0) {
     // ---- producer: weights once, then halo K-blocks ----------------------
     const uint8_t *wsrc = reinterpret_cast<const uint8_t *>(a.wt) + (size_t)nb * a.w_bytes;
-    mbar_expect_tx(wbar, a.w_bytes);
+    mbar_expect_tx(wbar, a.wv_bytes + a.w_bytes);
+    if (a.wv_bytes) {   // v block first, then the rest
+      const uint8_t *vsrc = reinterpret_cast<const uint8_t *>(a.wtv) + (size_t)nb * a.wv_bytes;
+      for (uint32_t off = 0; off < a.wv_bytes; off += 32768u)
+        bulk_load(wsm + off, vsrc + off, min(32768u, a.wv_bytes - off), wbar);
+    }
     for (uint32_t off = 0; off < a.w_bytes; off += 32768u) {
       const uint32_t n = min(32768u, a.w_bytes - off);
-      bulk_load(wsm + off, wsrc + off, n, wbar);
+      bulk_load(wsm + a.wv_bytes + off, wsrc + off, n, wbar);
     }
     int stage = 0;
     uint32_t phase = 0;
@@ -343,7 +360,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           const TileIter &tt = u ? t1 : ti;
           const int tx = tt.tx, ty = tt.ty, p = tt.p;
           if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) { stop = true; break; }
-          mbar_expect_tx(&full[stage], a.stage_bytes);
+          const bool vk = a.wv_bytes && kbi == 0;   // the gates' BF16 v block
+          mbar_expect_tx(&full[stage], vk ? a.vstage_bytes : a.stage_bytes);
           if constexpr (EPI == TE_HEADC) {
             // compact head: K-step kbi = a.tps taps (9 / a.tps steps per
             // tile), one box per tap of cR rows x cJ positions x all
@@ -369,7 +387,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
             // the rest through tmap1 (groups counted from 0); innermost
             // coordinate = pixel x * 8 channels (a multiple of 8 elements =
             // 16 bytes, also when negative at the left border)
-            if (kbi < a.nkb0)
+            if (vk)
+              tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage],
+                          (tx * kTileW - R) * 8, ty * kTileH - R, 0, p);
+            else if (kbi < a.nkb0)
               tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage],
                           (tx * kTileW - R) * EPG, ty * kTileH - R, a.in_goff + kbi * GPK, p);
             else
@@ -484,7 +505,26 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         fence_after();
         const uint64_t a0 = sdesc(smem_u32(stg + (size_t)s0 * a.stage_bytes), slab, HX * 16u);
         const uint64_t a1 = sdesc(smem_u32(stg + (size_t)s1 * a.stage_bytes), slab, HX * 16u);
-        const uint64_t b0 = sdesc(smem_u32(wsm) + (uint32_t)kbi * wblock, NCTA * 16u, 128u);
+        if (EPI == TE_LSTM && a.wv_bytes && kbi == 0) {
+          // v block: one BF16 MMA (K = 16, the block's two 16-byte groups)
+          // per tap, accumulating with the h block's MMAs
+          const uint32_t idv = (1u << 4) | (1u << 7) | (1u << 10) |
+                               ((uint32_t)(NCTA >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+          const uint64_t bv = sdesc(smem_u32(wsm), NCTA * 16u, 128u);
+#pragma unroll
+          for (int tap = 0; tap < taps; ++tap) {
+            const uint32_t aoff = ((uint32_t)((tap / KS) * HX + tap % KS) * 16u) >> 4;
+            const uint32_t boff = ((uint32_t)(tap * 2) * (NCTA * 16u)) >> 4;
+            mma_bf16(d0, a0 + aoff, bv + boff, idv, accum);
+            if (two) mma_bf16(d1, a1 + aoff, bv + boff, idv, accum);
+            accum = 1;
+          }
+          mma_commit(&empty[s0]);
+          if (two) mma_commit(&empty[s1]);
+          continue;
+        }
+        const int kh = kbi - ((EPI == TE_LSTM && a.wv_bytes) ? 1 : 0);   // index in wt
+        const uint64_t b0 = sdesc(smem_u32(wsm) + a.wv_bytes + (uint32_t)kh * wblock, NCTA * 16u, 128u);
 #pragma unroll
         for (int tap = 0; tap < taps; ++tap) {
 #pragma unroll
@@ -882,6 +922,54 @@ __global__ void __launch_bounds__(256) k_lstm_in_fp8(const int32_t *__restrict__
 }
 
 
+// ConvLSTM gates input v (see pack_gates_v), one block per row (plane p,
+// row y): V16[p][g][y][x][8] = 16 BF16 channels: the previous subband s
+// (nearest-upsampled by `up` levels) at the 9 neighbours (0 outside the
+// plane), 1 (inside indicator), zeros.
+__global__ void __launch_bounds__(256) k_lstm_v(const int32_t *__restrict__ s_prev,
+                                                __nv_bfloat16 *__restrict__ V16, int P, int H,
+                                                int W, int up) {
+  const int y = blockIdx.x % H;
+  const int64_t p = blockIdx.x / H;
+  const int Hp = H >> up, Wp = W >> up;
+  const int64_t hw = (int64_t)H * W;
+  const int32_t *sp = s_prev + p * Hp * Wp;
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    float v[16];
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+      v[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                   ? (float)__ldg(sp + (int64_t)(yy >> up) * Wp + (xx >> up))
+                   : 0.f;
+    }
+    v[9] = 1.f;
+#pragma unroll
+    for (int k = 10; k < 16; ++k) v[k] = 0.f;
+    const int64_t pix = (int64_t)y * W + x;
+    store_bf16x8(V16 + ((p * 2 + 0) * hw + pix) * 8, v);
+    store_bf16x8(V16 + ((p * 2 + 1) * hw + pix) * 8, v + 8);
+  }
+}
+
+// 16-byte channel groups of a blocked plane set, nearest-upsampled by `up`
+// levels (zeros when zero is set): dst[p][dst_goff + g][y][x] =
+// src[p][g][y >> up][x >> up] for g < ng, one block per row (plane, row).
+__global__ void __launch_bounds__(256) k_copy_up16(const uint4 *__restrict__ src, int src_G,
+                                                   uint4 *__restrict__ dst, int dst_G,
+                                                   int dst_goff, int ng, int P, int H, int W,
+                                                   int up, int zero) {
+  const int y = blockIdx.x % H;
+  const int64_t p = blockIdx.x / H;
+  const int Hp = H >> up, Wp = W >> up;
+  for (int it = threadIdx.x; it < ng * W; it += blockDim.x) {
+    const int g = it / W, x = it - g * W;
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (!zero) v = src[((p * src_G + g) * Hp + (y >> up)) * (int64_t)Wp + (x >> up)];
+    dst[((p * dst_G + dst_goff + g) * H + y) * (int64_t)W + x] = v;
+  }
+}
+
 // Compact step tail input: for the q-th position (y, x) of step `step`,
 // Vc[q] = dw3x3(U)(y, x) + b and Zc[q] = Z(y, x) (C channels each, blocked
 // layout; q indexes the compact plane of hc x wc positions).
@@ -1222,6 +1310,14 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   a.stage_bytes = (uint32_t)a.halo_x * a.halo_y * cv.kb * esz;
   a.w_bytes = (uint32_t)(cv.ks * cv.ks) * cv.cin * cv.ncta * esz;
   a.wt = cv.w; a.bias = cv.b; a.w_scale = cv.sw; a.err = err;
+  if (cv.wv) {
+    // ConvLSTM gates: K-block 0 = the BF16 v block through `in` (2 groups),
+    // the h block (cin channels) through in1
+    a.wtv = cv.wv;
+    a.wv_bytes = (uint32_t)(cv.ks * cv.ks) * 2u * cv.ncta * 16u;
+    a.vstage_bytes = (uint32_t)a.halo_x * a.halo_y * 32u;
+    a.nkb = 1 + cv.cin / cv.kb;
+  }
   const bool hc = a.epi == TE_HEADC;
   if (hc) {
     // compact head: tiles of R rows of one parity x J step positions; the
@@ -1246,7 +1342,7 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     a.nkb = 9 / a.tps;                           // stages per tile
     a.stage_bytes = (uint32_t)a.tps * tapb;
   }
-  const size_t fixed = kConvHeader + (a.w_bytes + 1023) / 1024 * 1024;
+  const size_t fixed = kConvHeader + (a.wv_bytes + a.w_bytes + 1023) / 1024 * 1024;
   const size_t maxsm = 227 * 1024;
   int stages = (int)((maxsm - fixed) / a.stage_bytes);
   // deep pipelines keep enough bytes in flight for the HBM-bound 1x1 convs
@@ -1261,6 +1357,9 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     const int W4 = (W + 3) & ~3;
     if ((s = make_map_hc(&map, in, P, cv.cin, H, W4, 0, a.cR, a.cJ, cv.f8))) return s;
     if ((s = make_map_hc(&map1, in, P, cv.cin, H, W4, 1, a.cR, a.cJ, cv.f8))) return s;
+  } else if (cv.wv) {
+    if (!in1) { set_last_error("gates conv needs the h input"); return PW_EINVAL; }
+    if ((s = make_map(&map, in, P, 2, H, W, a.halo_x, a.halo_y, 2, false))) return s;
   } else if ((s = make_map(&map, in, P, in_G, H, W, a.halo_x, a.halo_y, cv.kb / epg, cv.f8))) {
     return s;
   }
@@ -1366,6 +1465,46 @@ static int pack_conv(TcWeights &tw, TcWeights::Conv &cv, const std::vector<float
   return PW_OK;
 }
 
+// ConvLSTM gates without the e channels (Section 3.2): e = we * u + be (a
+// 3x3 conv of the upsampled previous subband u) has no nonlinearity before
+// the gates conv, so We * e = sum over taps of (We[tap] [we | be]) v, with
+// v = the 9 neighbour values of u and an inside indicator (zero outside the
+// plane, like e under the gates conv's zero padding): 10 input channels
+// instead of C. Returns the h-only weights [4C][C][9] of wg ([4C][2C][9],
+// inputs e then h) in wh and packs the v block as BF16 [nb][tap][2][ncta][8]
+// (channels 10..15 zero), each output column divided by colscale[n] (the
+// FP8 accumulator scale; null = 1).
+static int pack_gates_v(TcWeights &tw, TcWeights::Conv &cv, const std::vector<float> &wg,
+                        const std::vector<float> &we, const std::vector<float> &be, int C,
+                        int ncta, const std::vector<float> *colscale, std::vector<float> &wh) {
+  const int cout = 4 * C, nb = cout / ncta;
+  wh.assign((size_t)cout * C * 9, 0.f);
+  for (int n = 0; n < cout; ++n)
+    for (int c = 0; c < C; ++c)
+      for (int t = 0; t < 9; ++t)
+        wh[((size_t)n * C + c) * 9 + t] = wg[((size_t)n * 2 * C + C + c) * 9 + t];
+  std::vector<__nv_bfloat16> h((size_t)nb * 9 * 2 * ncta * 8, __float2bfloat16(0.f));
+  for (int n = 0; n < cout; ++n) {
+    const int b = n / ncta, nn = n % ncta;
+    const double cs = colscale ? (double)(*colscale)[n] : 1.0;
+    for (int t = 0; t < 9; ++t)
+      for (int j = 0; j < 10; ++j) {
+        double acc = 0.0;
+        for (int c = 0; c < C; ++c)
+          acc += (double)wg[((size_t)n * 2 * C + c) * 9 + t] * (j < 9 ? we[c * 9 + j] : be[c]);
+        const int g = j / 8, e = j % 8;
+        h[((((size_t)b * 9 + t) * 2 + g) * ncta + nn) * 8 + e] = __float2bfloat16((float)(acc / cs));
+      }
+  }
+  if (cudaMalloc(&cv.wv, h.size() * 2) != cudaSuccess) {
+    set_last_error("weight allocation failed");
+    return PW_ENOMEM;
+  }
+  tw.allocs.push_back(cv.wv);
+  cudaMemcpy(cv.wv, h.data(), h.size() * 2, cudaMemcpyHostToDevice);
+  return PW_OK;
+}
+
 int Model::ensure_tc() {
   if (tc) return PW_OK;
   if (C != 32 && C != 64) {
@@ -1375,8 +1514,13 @@ int Model::ensure_tc() {
   std::unique_ptr<TcWeights> t(new TcWeights());
   int s;
   auto H = [&](const std::string &n) -> const std::vector<float> & { return host.at(n); };
-  if ((s = pack_conv(*t, t->gates, H("lstm.wg.perm"), H("lstm.bg.perm"), 4 * C, 2 * C, 3, 64, C)))
-    return s;
+  {
+    std::vector<float> wh;
+    if ((s = pack_gates_v(*t, t->gates, H("lstm.wg.perm"), H("lstm.we"), H("lstm.be"), C, 64,
+                          nullptr, wh)))
+      return s;
+    if ((s = pack_conv(*t, t->gates, wh, H("lstm.bg.perm"), 4 * C, C, 3, 64, C))) return s;
+  }
   auto set = [&](const std::string &ns, TcWeights::Conv &in_, TcWeights::Conv &w1,
                  TcWeights::Conv &w2, TcWeights::Conv &w3, TcWeights::Conv &w4,
                  TcWeights::Conv *k1, TcWeights::Conv *k2) -> int {
@@ -1458,7 +1602,8 @@ int Model::ensure_tc() {
 // acc * sw[n] + b[n].
 static int pack_conv_f8(TcWeights &tw, TcWeights::Conv &cv, const std::vector<float> &w,
                         const std::vector<float> &b, const std::vector<float> &in_scale,
-                        int cout, int cin, int ks, int ncta, int kb) {
+                        int cout, int cin, int ks, int ncta, int kb,
+                        std::vector<float> *sw_out = nullptr) {
   cv.cin = cin; cv.cout = cout; cv.ks = ks; cv.kb = kb; cv.ncta = ncta; cv.nb = cout / ncta;
   cv.f8 = true;
   const int taps = ks * ks, nkb = cin / kb, gpb = kb / 16;
@@ -1494,6 +1639,7 @@ static int pack_conv_f8(TcWeights &tw, TcWeights::Conv &cv, const std::vector<fl
   cudaMemcpy(cv.w, h.data(), h.size(), cudaMemcpyHostToDevice);
   cudaMemcpy(cv.b, b.data(), cout * 4, cudaMemcpyHostToDevice);
   cudaMemcpy(cv.sw, sw.data(), cout * 4, cudaMemcpyHostToDevice);
+  if (sw_out) *sw_out = sw;
   return PW_OK;
 }
 
@@ -1525,11 +1671,26 @@ int Model::ensure_fp8() {
     es[c] = (float)(kTarget / std::sqrt(std::max(v, 1e-12)));
   }
   if ((s = dev(es, &t.e_scale)) || (s = dev(hs, &t.h_scale))) return s;
-  std::vector<float> gin(2 * C);
-  for (int c = 0; c < C; ++c) { gin[c] = es[c]; gin[C + c] = hs[c]; }
-  if ((s = pack_conv_f8(t, t.gates8, H("lstm.wg.perm"), H("lstm.bg.perm"), gin, 4 * C, 2 * C,
-                        3, 128, C)))
-    return s;
+  {
+    // gates: E4M3 h block (input scale hs), BF16 v block divided by the
+    // h block's accumulator scale so that both accumulate on one scale
+    std::vector<float> wh, sw;
+    {
+      std::vector<float> tmp;
+      const std::vector<float> &wg = H("lstm.wg.perm");
+      wh.assign((size_t)4 * C * C * 9, 0.f);
+      for (int n = 0; n < 4 * C; ++n)
+        for (int c = 0; c < C; ++c)
+          for (int tp = 0; tp < 9; ++tp)
+            wh[((size_t)n * C + c) * 9 + tp] = wg[((size_t)n * 2 * C + C + c) * 9 + tp];
+    }
+    if ((s = pack_conv_f8(t, t.gates8, wh, H("lstm.bg.perm"), hs, 4 * C, C, 3, 128, C, &sw)))
+      return s;
+    std::vector<float> unused;
+    if ((s = pack_gates_v(t, t.gates8, H("lstm.wg.perm"), H("lstm.we"), H("lstm.be"), C, 128,
+                          &sw, unused)))
+      return s;
+  }
   // steps 2-4: z = Wz [a; l] + bz (a = Wa (m s) + ba), u = lrelu(conv3x3 z)
   auto steps = [&](const std::string &ns, TcWeights::Conv *c1, TcWeights::Conv *c2,
                    float **zsc, float **usc) -> int {
@@ -1614,7 +1775,7 @@ int64_t tc_workspace_bytes(const Geometry &g, int P, int C, bool f8) {
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
   int64_t tot = 1024 + al(big * 2 * C * 2) + 4 * al(big * C * 2) +
                 al(std::max(big * 2, big4) * C * 2) + al(big * C * 2) +
-                3 * al(cmax * C * 2) + al(cmax * 2 * C * 2) + al(big * 32 * 2);
+                3 * al(cmax * C * 2) + al(cmax * 2 * C * 2) + al(big * 32 * 2) + al(big * 32);
   if (f8) tot += al(big * 2 * C) + 3 * al(big * C) + al(big4 * C);
   return tot;
 }
@@ -1629,11 +1790,11 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C, bool f8) {
   // X (2C), L0 (C), L1 (C), Z (C), U (2C), V (C), Z2 (C); compact Vc, Zc,
   // Z2c (C), U2c (2C); T (32); bf16. FP8: X8 (2C), L8 x 2, Z8, U8 (C) bytes.
   // U and U8 also hold the pitched input of the compact head (big4)
-  constexpr int kN = 12, kN8 = 5;
+  constexpr int kN = 13, kN8 = 5;
   const int64_t sizes[kN] = {big * 2 * C * 2, big * C * 2,  big * C * 2,      big * C * 2,
                              std::max(big * 2, big4) * C * 2, big * C * 2,  big * C * 2,
                              cmax * C * 2,    cmax * C * 2, cmax * C * 2, cmax * 2 * C * 2,
-                             big * 32 * 2};
+                             big * 32 * 2,    big * 32};
   const int64_t sizes8[kN8] = {big * 2 * C, big * C, big * C, big * C, big4 * C};
   int64_t tot = 1024;
   for (int64_t v : sizes) tot += al(v);
@@ -1650,7 +1811,7 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C, bool f8) {
   cudaMemsetAsync(t->err, 0, 1024, ws->stream);
   int64_t o = 1024;
   __nv_bfloat16 **dst[kN] = {&t->X,  &t->L[0], &t->L[1], &t->Z,   &t->U,  &t->V,
-                             &t->Z2, &t->Vc,   &t->Zc,   &t->Z2c, &t->U2c, &t->T};
+                             &t->Z2, &t->Vc,   &t->Zc,   &t->Z2c, &t->U2c, &t->T, &t->V16};
   for (int i = 0; i < kN; ++i) { *dst[i] = reinterpret_cast<__nv_bfloat16 *>(b + o); o += al(sizes[i]); }
   if (f8) {
     uint8_t **dst8[kN8] = {&t->X8, &t->L8[0], &t->L8[1], &t->Z8, &t->U8};
@@ -1681,21 +1842,25 @@ int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   const double pix = (double)P * h * w;
   __nv_bfloat16 *lprev = t.L[(sb - 1) & 1], *lout = t.L[sb & 1];
   const TcWeights::Conv &gates = f8 ? m.tc->gates8 : m.tc->gates;
-  // h_{i-1} is copied into X only when it must be upsampled, when a K-block
-  // would mix e and h channels, or for the first subband (h_{i-1} = 0);
-  // otherwise the gates conv reads it from the previous l buffer directly
-  const int copy_h = (up || first || gates.kb != C) ? 1 : 0;
+  // h_{i-1} is copied (upsampled, or zeros for the first subband) into the
+  // second half of X / X8 when it is not at this resolution; otherwise the
+  // gates conv reads it from the previous l buffer directly
+  const int copy_h = (up || first) ? 1 : 0;
   {
-    ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C,
-                 pix * (4.0 + (f8 ? 1.0 : 2.0) * C * (copy_h ? 3 : 1)));
-    if (f8)
-      k_lstm_in_fp8<<<P * h, 256, 0, ctx->stream>>>(
-          sprev, t.L8[(sb - 1) & 1], m.lstm_we, m.lstm_be, m.tc->e_scale, t.X8, P, h, w, C, up,
-          copy_h, first);
-    else
-      k_lstm_in_bf16<<<P * h, 256, 0, ctx->stream>>>(
-          sprev, lprev, m.lstm_we, m.lstm_be, t.X, P, h, w, C, up, copy_h, first);
+    ProfScope ps(ctx, KC_SMALL_CTX, 0.0, pix * (4.0 + 32.0 + (copy_h ? (f8 ? 2.0 : 4.0) * C : 0)));
+    k_lstm_v<<<P * h, 256, 0, ctx->stream>>>(sprev, t.V16, P, h, w, up);
     ctx->launches += 1;
+    if (copy_h) {
+      if (f8)
+        k_copy_up16<<<P * h, 256, 0, ctx->stream>>>(
+            reinterpret_cast<const uint4 *>(t.L8[(sb - 1) & 1]), G16,
+            reinterpret_cast<uint4 *>(t.X8), 2 * G16, G16, G16, P, h, w, up, first);
+      else
+        k_copy_up16<<<P * h, 256, 0, ctx->stream>>>(
+            reinterpret_cast<const uint4 *>(lprev), G, reinterpret_cast<uint4 *>(t.X), 2 * G, G,
+            G, P, h, w, up, first);
+      ctx->launches += 1;
+    }
   }
   TcConvArgs a{};
   a.epi = TE_LSTM;
@@ -1706,15 +1871,15 @@ int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   a.c_new = reinterpret_cast<__nv_bfloat16 *>(ws.Cst[cur ^ 1]);
   a.up = up; a.first = first; a.C = C;
   if (f8) { a.out8 = t.L8[sb & 1]; a.out8_G16 = G16; a.out8_scale = m.tc->h_scale; }
-  ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * 2 * C * 4 * C,
-               pix * ((f8 ? 2.0 : 4.0) * C + 2.0 * C + 8.0 * C + (f8 ? C : 0)));
+  // MMA work: the 16-channel v block and the C h channels, 9 taps, 4C outputs
+  ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * (16 + C) * 4 * C,
+               pix * (32.0 + (f8 ? 1.0 : 2.0) * C + 2.0 * C + 4.0 * C + (f8 ? C : 0)));
   if (f8) {
-    if (copy_h) return conv_tc(ctx, gates, t.X8, 2 * G16, 0, P, h, w, a, t.err);
-    return conv_tc(ctx, gates, t.X8, 2 * G16, 0, P, h, w, a, t.err, t.L8[(sb - 1) & 1], G16, 0, 1);
+    if (copy_h) return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X8, 2 * G16, G16, 1);
+    return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.L8[(sb - 1) & 1], G16, 0, 1);
   }
-  if (copy_h) return conv_tc(ctx, gates, t.X, 2 * G, 0, P, h, w, a, t.err);
-  // same resolution: e from X, h_{i-1} straight from the previous l buffer
-  return conv_tc(ctx, gates, t.X, 2 * G, 0, P, h, w, a, t.err, lprev, G, 0, 1);
+  if (copy_h) return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X, 2 * G, G, 1);
+  return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, lprev, G, 0, 1);
 }
 
 int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb, int step,
