@@ -64,17 +64,18 @@ struct TcWeights {
   // FP8 precision: E4M3 copies of the 3x3 convolutions (gates, steps 2-4
   // residual blocks) with the input channels' static scales folded in, and
   // the scales (value * scale = stored E4M3 value) of the FP8 activations:
-  // e (ConvLSTM input conv), z (residual-block input, per step), u (hidden
-  // layer, per step) and h (l_i, fixed 256 since |h| < 1)
+  // z (residual-block input, per step), u (hidden layer, per step) and h
+  // (l_i, fixed 256 since |h| < 1); the gates' v block stays BF16
   bool has_f8 = false;
   Conv gates8, sk_c1_8[3], sk_c2_8[3], lk_c1_8[3], lk_c2_8[3];
-  float *e_scale = nullptr, *h_scale = nullptr;
+  float *h_scale = nullptr;
   float *sk_z_scale[3] = {}, *sk_u_scale[3] = {}, *lk_z_scale[3] = {}, *lk_u_scale[3] = {};
   std::vector<void *> allocs;
 };
 
 struct TcAct {  // BF16 activations in [P][G][H][W][8]
-  // X: ConvLSTM input [e, up(h)] (2C); L[2]: long-term context l_i of the
+  // X: (2C; channels C..2C-1 hold up(h) when h_{i-1} is at another
+  // resolution); L[2]: long-term context l_i of the
   // current and previous subband (C each, ping-pong so the gates conv can
   // read h_{i-1} while its epilogue writes h_i); Z, V, Z2 (C); U (2C).
   __nv_bfloat16 *X = nullptr, *L[2] = {nullptr, nullptr}, *Z = nullptr, *U = nullptr,
@@ -89,9 +90,9 @@ struct TcAct {  // BF16 activations in [P][G][H][W][8]
   __nv_bfloat16 *V16 = nullptr;
   // T: masked neighbour values of steps 2-4 (32 channels, see TcWeights)
   __nv_bfloat16 *T = nullptr;
-  // FP8 precision: E4M3 activations [P][G16][H][W][16]: X8 = [e, up(h)]
-  // (2C), L8[2] = l_i (C, ping-pong like L), Z8 / U8 = residual-block input
-  // and hidden layer (C)
+  // FP8 precision: E4M3 activations [P][G16][H][W][16]: X8 (2C; channels
+  // C..2C-1 hold up(h) when h_{i-1} is at another resolution), L8[2] = l_i
+  // (C, ping-pong like L), Z8 / U8 = residual-block input and hidden layer (C)
   uint8_t *X8 = nullptr, *L8[2] = {nullptr, nullptr}, *Z8 = nullptr, *U8 = nullptr;
   int *err = nullptr;
   void *base = nullptr;
@@ -810,117 +811,6 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 
 // ---------------------------------------------------------------------------
 // SIMT helper kernels on the blocked BF16 layout.
-
-// ConvLSTM input, one thread per pixel: X[:, 0:C] = conv3x3(1->C)(up(s_prev))
-// + be and, when copy_h is set, X[:, C:2C] = up(h_prev) (h_prev: C channels
-// at the previous resolution). With copy_h = 0 the gates conv reads h_prev
-// from its own buffer instead.
-__global__ void __launch_bounds__(256) k_lstm_in_bf16(const int32_t *__restrict__ s_prev,
-                                                      const __nv_bfloat16 *__restrict__ hprev,
-                                                      const float *__restrict__ we,
-                                                      const float *__restrict__ be,
-                                                      __nv_bfloat16 *__restrict__ X, int P,
-                                                      int H, int W, int C, int up, int copy_h,
-                                                      int first) {
-  // one block per row (plane p, row y); item = group-major (g, x) so that a
-  // warp reads the same weights (shared-memory broadcast)
-  __shared__ float swe[9 * 128], sbe[128];
-  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) swe[i] = we[i];
-  for (int i = threadIdx.x; i < C; i += blockDim.x) sbe[i] = be[i];
-  __syncthreads();
-  const int G = C / 8;
-  const int y = blockIdx.x % H;
-  const int64_t p = blockIdx.x / H;
-  const int Hp = H >> up, Wp = W >> up;
-  const int64_t hw = (int64_t)H * W;
-  const int32_t *sp = s_prev + p * Hp * Wp;
-  for (int it = threadIdx.x; it < G * W; it += blockDim.x) {
-    const int g = it / W, x = it - g * W;
-    float nb[9];
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-      nb[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    ? (float)__ldg(sp + (int64_t)(yy >> up) * Wp + (xx >> up))
-                    : 0.f;
-    }
-    const int64_t pix = (int64_t)y * W + x;
-    float v[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int c = 8 * g + k;
-      float a = sbe[c];
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) a = fmaf(swe[c * 9 + tap], nb[tap], a);
-      v[k] = a;
-    }
-    store_bf16x8(X + ((p * 2 * G + g) * hw + pix) * 8, v);
-    if (copy_h) {
-      float hv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-      if (!first)
-        load_bf16x8(hprev + ((p * G + g) * ((int64_t)Hp * Wp) + (int64_t)(y >> up) * Wp +
-                             (x >> up)) * 8,
-                    hv);
-      store_bf16x8(X + ((p * 2 * G + G + g) * hw + pix) * 8, hv);
-    }
-  }
-}
-
-// FP8 precision: X8[:, 0:C] = E4M3((conv3x3(1->C)(up(s_prev)) + be) *
-// e_scale) and, when copy_h is set, X8[:, C:2C] = up(h8_prev) (E4M3 l_i of
-// the previous subband, copied as bytes; zero when first). Layout
-// [P][G16][H][W][16].
-__global__ void __launch_bounds__(256) k_lstm_in_fp8(const int32_t *__restrict__ s_prev,
-                                                     const uint8_t *__restrict__ h8prev,
-                                                     const float *__restrict__ we,
-                                                     const float *__restrict__ be,
-                                                     const float *__restrict__ e_scale,
-                                                     uint8_t *__restrict__ X8, int P, int H,
-                                                     int W, int C, int up, int copy_h,
-                                                     int first) {
-  // one block per row (plane p, row y); item = group-major (g, x)
-  __shared__ float swe[9 * 128], sbe[128], ssc[128];
-  for (int i = threadIdx.x; i < 9 * C; i += blockDim.x) swe[i] = we[i];
-  for (int i = threadIdx.x; i < C; i += blockDim.x) { sbe[i] = be[i]; ssc[i] = e_scale[i]; }
-  __syncthreads();
-  const int G16 = C / 16;
-  const int y = blockIdx.x % H;
-  const int64_t p = blockIdx.x / H;
-  const int Hp = H >> up, Wp = W >> up;
-  const int64_t hw = (int64_t)H * W;
-  const int32_t *sp = s_prev + p * Hp * Wp;
-  for (int it = threadIdx.x; it < G16 * W; it += blockDim.x) {
-    const int g = it / W, x = it - g * W;
-    float nb[9];
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
-      nb[tap] = (yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    ? (float)__ldg(sp + (int64_t)(yy >> up) * Wp + (xx >> up))
-                    : 0.f;
-    }
-    const int64_t pix = (int64_t)y * W + x;
-    float v[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) {
-      const int c = 16 * g + k;
-      float a = sbe[c];
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) a = fmaf(swe[c * 9 + tap], nb[tap], a);
-      v[k] = a * ssc[c];
-    }
-    store_fp8x16(X8 + ((p * 2 * G16 + g) * hw + pix) * 16, v);
-    if (copy_h) {
-      uint4 hv = make_uint4(0u, 0u, 0u, 0u);
-      if (!first)
-        hv = *reinterpret_cast<const uint4 *>(
-            h8prev + ((p * G16 + g) * ((int64_t)Hp * Wp) + (int64_t)(y >> up) * Wp + (x >> up)) *
-                         16);
-      *reinterpret_cast<uint4 *>(X8 + ((p * 2 * G16 + G16 + g) * hw + pix) * 16) = hv;
-    }
-  }
-}
-
 
 // ConvLSTM gates input v (see pack_gates_v), one block per row (plane p,
 // row y): V16[p][g][y][x][8] = 16 BF16 channels: the previous subband s
@@ -1662,15 +1552,8 @@ int Model::ensure_fp8() {
     cudaMemcpy(*out, v.data(), v.size() * 4, cudaMemcpyHostToDevice);
     return PW_OK;
   };
-  // ConvLSTM input conv e = we * s + be
-  const std::vector<float> &we = H("lstm.we"), &be = H("lstm.be");
-  std::vector<float> es(C), hs(C, 256.f);
-  for (int c = 0; c < C; ++c) {
-    double v = (double)be[c] * be[c];
-    for (int tap = 0; tap < 9; ++tap) v += (double)we[c * 9 + tap] * we[c * 9 + tap] * kSigS * kSigS;
-    es[c] = (float)(kTarget / std::sqrt(std::max(v, 1e-12)));
-  }
-  if ((s = dev(es, &t.e_scale)) || (s = dev(hs, &t.h_scale))) return s;
+  std::vector<float> hs(C, 256.f);
+  if ((s = dev(hs, &t.h_scale))) return s;
   {
     // gates: E4M3 h block (input scale hs), BF16 v block divided by the
     // h block's accumulator scale so that both accumulate on one scale
