@@ -305,7 +305,8 @@ uint64_t pw_ctx_launch_count(const pw_ctx *ctx);
  * (default on; disabled classes use the default schedule) and returns the
  * previous setting. pw_autotune_report writes one line per tuned class
  * ("ks kb ncta epilogue fp8 log2tiles pairs t_single t_paired", median sample
- * times in microseconds, -1 = no sample) into buf (NUL-terminated,
+ * times in microseconds, -1 = no sample; epilogue 0 store, 1 ConvLSTM gates,
+ * 2 head, 3 compact head, 4 store with a 16-channel BF16 input block) into buf (NUL-terminated,
  * truncated to n) and returns the full length. */
 int pw_autotune(int enable);
 int pw_autotune_report(char *buf, size_t n);

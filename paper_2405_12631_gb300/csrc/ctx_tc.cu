@@ -57,9 +57,8 @@ struct TcWeights {
   Conv l0_in, l0_w1, l0_w2, l0_w3, l0_w4;       // ll set
   Conv lk_c1[3], lk_c2[3];
   // steps 2-4 with the masked input conv folded into the 1x1: zt = 1x1 over
-  // [l (C channels), T (32 channels: the 9 masked neighbour values, each
-  // split into a BF16 high and low part, then zero padding)]; the bias
-  // includes the folded bias
+  // [T (v block: the 9 masked neighbour values as BF16, zero padding),
+  // l (C channels)]; the bias includes the folded bias
   Conv sk_zt[3], lk_zt[3];
   // FP8 precision: E4M3 copies of the 3x3 convolutions (gates, steps 2-4
   // residual blocks) with the input channels' static scales folded in, and
@@ -88,7 +87,7 @@ struct TcAct {  // BF16 activations in [P][G][H][W][8]
   // V16: the ConvLSTM gates' v block [P][2][H][W][8] (9 neighbour values of
   // the upsampled previous subband, an inside indicator, zeros)
   __nv_bfloat16 *V16 = nullptr;
-  // T: masked neighbour values of steps 2-4 (32 channels, see TcWeights)
+  // T: masked neighbour values of steps 2-4 (16 channels, see TcWeights)
   __nv_bfloat16 *T = nullptr;
   // FP8 precision: E4M3 activations [P][G16][H][W][16]: X8 (2C; channels
   // C..2C-1 hold up(h) when h_{i-1} is at another resolution), L8[2] = l_i
@@ -117,10 +116,12 @@ struct TcConvArgs {
   int stages, halo_x, halo_y;
   uint32_t stage_bytes, w_bytes;
   const __nv_bfloat16 *wt;      // [nb][kblock][tap][kb/8][ncta][8]
-  // ConvLSTM gates: K-block 0 is the 16-channel BF16 "v" block (the 9
+  // K-block 0 may be a 16-channel BF16 "v" block with its own weights wtv
+  // [nb][tap][2][ncta][8] (wv_bytes per N block, stages of vstage_bytes),
+  // read through the first tensor map: for the ConvLSTM gates the 9
   // neighbour values of the upsampled previous subband and an inside
-  // indicator, weights wtv [nb][tap][2][ncta][8], wv_bytes per N block,
-  // stages of vstage_bytes) in place of e; wt then holds the h block only
+  // indicator (in place of e), for the steps 2-4 z conv the 9 masked
+  // neighbour values; wt then holds the remaining K-blocks
   const __nv_bfloat16 *wtv;
   uint32_t wv_bytes, vstage_bytes;
   const float *bias;            // [nb * ncta]
@@ -506,9 +507,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         fence_after();
         const uint64_t a0 = sdesc(smem_u32(stg + (size_t)s0 * a.stage_bytes), slab, HX * 16u);
         const uint64_t a1 = sdesc(smem_u32(stg + (size_t)s1 * a.stage_bytes), slab, HX * 16u);
-        if (EPI == TE_LSTM && a.wv_bytes && kbi == 0) {
+        if (EPI != TE_HEADC && a.wv_bytes && kbi == 0) {
           // v block: one BF16 MMA (K = 16, the block's two 16-byte groups)
-          // per tap, accumulating with the h block's MMAs
+          // per tap, accumulating with the other K-blocks' MMAs
           const uint32_t idv = (1u << 4) | (1u << 7) | (1u << 10) |
                                ((uint32_t)(NCTA >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
           const uint64_t bv = sdesc(smem_u32(wsm), NCTA * 16u, 128u);
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           if (two) mma_commit(&empty[s1]);
           continue;
         }
-        const int kh = kbi - ((EPI == TE_LSTM && a.wv_bytes) ? 1 : 0);   // index in wt
+        const int kh = kbi - (a.wv_bytes ? 1 : 0);   // index in wt
         const uint64_t b0 = sdesc(smem_u32(wsm) + a.wv_bytes + (uint32_t)kh * wblock, NCTA * 16u, 128u);
 #pragma unroll
         for (int tap = 0; tap < taps; ++tap) {
@@ -906,9 +907,9 @@ __global__ void __launch_bounds__(256) k_dw3x3_compact(
 }
 
 // T = the 9 masked neighbour values of every position for step `step`
-// (neighbours coded in an earlier step, else 0), channel 2 tap = BF16 value,
-// 2 tap + 1 = BF16 of the remainder, channels 18..31 = 0. One thread per
-// position; blocked layout [P][4][H][W][8].
+// (neighbours coded in an earlier step, else 0) as BF16 channels 0..8,
+// channels 9..15 = 0 (the z conv's v block). One thread per position;
+// blocked layout [P][2][H][W][8].
 // One block per row (plane p, row y), threads along x: no integer division
 // per element. Which of the 9 taps come from an earlier step depends only
 // on (y mod 2, x mod 4): a 9-bit mask per class, built once per block.
@@ -932,24 +933,19 @@ __global__ void __launch_bounds__(128) k_masked_taps(const int32_t *__restrict__
   for (int x = threadIdx.x; x < W; x += blockDim.x) {
     const uint32_t mask = smask[((y & 1) << 2) | (x & 3)];
     const bool interior = yin && x > 0 && x + 1 < W;
-    __align__(16) __nv_bfloat16 v[32];
+    float v[16];
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
       const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
       const bool use = ((mask >> tap) & 1u) &&
                        (interior || (yy >= 0 && yy < H && xx >= 0 && xx < W));
-      const float f = use ? (float)__ldg(sp + (int64_t)yy * W + xx) : 0.f;
-      const __nv_bfloat16 hi = __float2bfloat16_rn(f);
-      v[2 * tap] = hi;
-      v[2 * tap + 1] = __float2bfloat16_rn(f - __bfloat162float(hi));
+      v[tap] = use ? (float)__ldg(sp + (int64_t)yy * W + xx) : 0.f;
     }
 #pragma unroll
-    for (int c = 18; c < 32; ++c) v[c] = __float2bfloat16_rn(0.f);
+    for (int c = 9; c < 16; ++c) v[c] = 0.f;
     const int64_t pix = (int64_t)y * W + x;
-#pragma unroll
-    for (int g = 0; g < 4; ++g)
-      *reinterpret_cast<uint4 *>(T + ((p * 4 + g) * hw + pix) * 8) =
-          *reinterpret_cast<const uint4 *>(v + 8 * g);
+    store_bf16x8(T + ((p * 2 + 0) * hw + pix) * 8, v);
+    store_bf16x8(T + ((p * 2 + 1) * hw + pix) * 8, v + 8);
   }
 }
 
@@ -1306,7 +1302,9 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     set_last_error("no tensor-core conv for this shape");
     return PW_EUNSUPPORTED;
   };
-  const uint64_t key = tune_key(cv, a.epi, a.tiles);
+  // tuning class: the variant (epilogue 4 = a plain store with a v block,
+  // the steps 2-4 z conv) and the size
+  const uint64_t key = tune_key(cv, (cv.wv && a.epi == TE_STORE) ? 4 : a.epi, a.tiles);
   bool sample = false;
   int cand = 0;
   const TuneChoice ch = tune_next(key, a.stages >= 2, st, sample, cand);
@@ -1447,32 +1445,35 @@ int Model::ensure_tc() {
     return s;
   // Steps 2-4: z = Wz [a; l] + bz with a = Wa * (m s) + ba is linear in a,
   // so z = Wz_l l + sum_tap (Wz_a Wa[:, tap]) (m s)(tap) + (Wz_a ba + bz):
-  // one 1x1 over l and the 9 masked neighbour values. Each value enters as
-  // two BF16 channels (high part, exact remainder) with the same weight, so
-  // integers below 2^16 reach the accumulator exactly.
+  // one 1x1 over l and a v block of the 9 masked neighbour values (BF16).
   auto fold = [&](const std::string &ns, TcWeights::Conv *zt) -> int {
     for (int k = 1; k < 4; ++k) {
       const std::string q = ns + ".s" + std::to_string(k) + ".";
       const std::vector<float> &wz = H(q + "wz"), &bz = H(q + "bz"), &wa = H(q + "wa"),
                                &ba = H(q + "ba");
-      const int K = C + 32;
-      std::vector<float> wk((size_t)C * K, 0.f), bf(C);
+      std::vector<float> wk((size_t)C * C, 0.f), bf(C);
+      std::vector<__nv_bfloat16> wv((size_t)2 * C * 8, __float2bfloat16(0.f));  // [2][C][8]
       for (int c = 0; c < C; ++c) {
         double bacc = bz[c];
         for (int j = 0; j < C; ++j) {
-          wk[(size_t)c * K + j] = wz[(size_t)c * 2 * C + C + j];
+          wk[(size_t)c * C + j] = wz[(size_t)c * 2 * C + C + j];
           bacc += (double)wz[(size_t)c * 2 * C + j] * ba[j];
         }
         bf[c] = (float)bacc;
         for (int tap = 0; tap < 9; ++tap) {
           double acc = 0.0;
           for (int j = 0; j < C; ++j) acc += (double)wz[(size_t)c * 2 * C + j] * wa[j * 9 + tap];
-          wk[(size_t)c * K + C + 2 * tap] = (float)acc;
-          wk[(size_t)c * K + C + 2 * tap + 1] = (float)acc;
+          wv[((size_t)(tap / 8) * C + c) * 8 + tap % 8] = __float2bfloat16((float)acc);
         }
       }
       int r;
-      if ((r = pack_conv(*t, zt[k - 1], wk, bf, C, K, 1, C, 32))) return r;
+      if ((r = pack_conv(*t, zt[k - 1], wk, bf, C, C, 1, C))) return r;
+      if (cudaMalloc(&zt[k - 1].wv, wv.size() * 2) != cudaSuccess) {
+        set_last_error("weight allocation failed");
+        return PW_ENOMEM;
+      }
+      t->allocs.push_back(zt[k - 1].wv);
+      cudaMemcpy(zt[k - 1].wv, wv.data(), wv.size() * 2, cudaMemcpyHostToDevice);
     }
     return PW_OK;
   };
@@ -1658,7 +1659,7 @@ int64_t tc_workspace_bytes(const Geometry &g, int P, int C, bool f8) {
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
   int64_t tot = 1024 + al(big * 2 * C * 2) + 4 * al(big * C * 2) +
                 al(std::max(big * 2, big4) * C * 2) + al(big * C * 2) +
-                3 * al(cmax * C * 2) + al(cmax * 2 * C * 2) + al(big * 32 * 2) + al(big * 32);
+                3 * al(cmax * C * 2) + al(cmax * 2 * C * 2) + al(big * 32) + al(big * 32);
   if (f8) tot += al(big * 2 * C) + 3 * al(big * C) + al(big4 * C);
   return tot;
 }
@@ -1677,7 +1678,7 @@ int tc_workspace_alloc(Workspace *ws, const Geometry &g, int C, bool f8) {
   const int64_t sizes[kN] = {big * 2 * C * 2, big * C * 2,  big * C * 2,      big * C * 2,
                              std::max(big * 2, big4) * C * 2, big * C * 2,  big * C * 2,
                              cmax * C * 2,    cmax * C * 2, cmax * C * 2, cmax * 2 * C * 2,
-                             big * 32 * 2,    big * 32};
+                             big * 32,        big * 32};
   const int64_t sizes8[kN8] = {big * 2 * C, big * C, big * C, big * C, big4 * C};
   int64_t tot = 1024;
   for (int64_t v : sizes) tot += al(v);
@@ -1837,8 +1838,8 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   const float *usc = ll ? W.lk_u_scale[step - 1] : W.sk_u_scale[step - 1];
   const int G16 = C / 16;
   {
-    ProfScope ps(ctx, KC_SMALL_CTX, 0.0, pix * (4.0 + 64.0));
-    k_masked_taps<<<P * h, 128, 0, st>>>(Qi, t.T, P, h, w, step);
+    ProfScope ps(ctx, KC_SMALL_CTX, 0.0, pix * (4.0 + 32.0));
+    k_masked_taps<<<P * h, 128, 0, st>>>(Qi, t.T, P, h, w, step);   // T: 16 channels
     ctx->launches += 1;
   }
   TcConvArgs a{};
@@ -1850,10 +1851,10 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     a.outc = t.Zc; a.outc_n = (int)nk; a.step = step;
   }
   {
-    // z = 1x1 over [l, T]: K-blocks of 32 channels, the first C / 32 from l
-    ProfScope ps(ctx, KC_CONV1, 2.0 * pix * zt.cin * zt.cout,
-                 pix * (2.0 * (zt.cin + zt.cout) + (f8 ? C : 0)));
-    if ((s = conv_tc(ctx, zt, l, G, 0, P, h, w, a, t.err, t.T, 4, 0, C / 32))) return s;
+    // z = 1x1 over [T (v block, 16 BF16 channels), l (C channels)]
+    ProfScope ps(ctx, KC_CONV1, 2.0 * pix * (16 + zt.cin) * zt.cout,
+                 pix * (32.0 + 2.0 * zt.cin + (f8 ? C + C / 2 : 2.0 * zt.cout)));
+    if ((s = conv_tc(ctx, zt, t.T, 2, 0, P, h, w, a, t.err, l, G, 0, 1))) return s;
   }
   // The head conv's outputs are used at this step's positions only (a
   // quarter of the plane): where the subband is large enough it runs on
