@@ -155,22 +155,27 @@ __device__ __forceinline__ uint32_t ld_words2(const uint8_t *wp, uint32_t k, uin
 // increasing with t[0] = 0, t[127] = M = 2^15 > slot, and all are <= 2^15,
 // so the SWAR counts below are exactly that s. Returns s; lo = t[s],
 // hi = t[s + 1].
-__device__ __forceinline__ int cdf_search(const uint16_t *__restrict__ row,
-                                          const uint16_t *s_crow, uint32_t slot, uint32_t &lo,
-                                          uint32_t &hi) {
+// The table's coarse entries come in registers (c0 = entries 0..7, c1 =
+// 8..15, two per word, low half first), loaded one round ahead; the entry
+// after block b also comes from them.
+__device__ __forceinline__ int cdf_search_r(const uint16_t *__restrict__ row, const uint4 c0,
+                                            const uint4 c1, uint32_t slot, uint32_t &lo,
+                                            uint32_t &hi) {
   const uint32_t s2 = (slot | 0x8000u) * 0x10001u;
-  const uint4 c0 = *reinterpret_cast<const uint4 *>(s_crow);
-  const uint4 c1 = *reinterpret_cast<const uint4 *>(s_crow + 8);
   uint32_t a = le2(s2, c0.x) + le2(s2, c0.y) + le2(s2, c0.z) + le2(s2, c0.w) + le2(s2, c1.x) +
                le2(s2, c1.y) + le2(s2, c1.z) + le2(s2, c1.w);
   const int b = (int)((a & 0xFFFFu) + (a >> 16)) - 1;
   const uint4 f = __ldg(reinterpret_cast<const uint4 *>(row + 8 * b));
   a = le2(s2, f.x) + le2(s2, f.y) + le2(s2, f.z) + le2(s2, f.w);
   const int i = (int)((a & 0xFFFFu) + (a >> 16)) - 1;
-  // entries i and i + 1 of the block (entry 8 = next coarse entry; i == 7
-  // implies b < 15, the clamp keeps the read in the table either way)
+  // coarse entry b + 1 (clamped; its low 16 bits are what is used)
+  const int bn = min(b + 1, kCoarse - 1), wn = bn >> 1;
+  const uint32_t q0 = (wn & 1) ? c0.y : c0.x, q1 = (wn & 1) ? c0.w : c0.z;
+  const uint32_t q2 = (wn & 1) ? c1.y : c1.x, q3 = (wn & 1) ? c1.w : c1.z;
+  const uint32_t r0 = (wn & 2) ? q1 : q0, r1 = (wn & 2) ? q3 : q2;
+  const uint32_t wsel = (wn & 4) ? r1 : r0;
+  const uint32_t nxt = (bn & 1) ? (wsel >> 16) : wsel;
   const int wi = i >> 1;
-  const uint32_t nxt = s_crow[min(b + 1, kCoarse - 1)];
   const uint32_t w0 = (wi & 2) ? ((wi & 1) ? f.w : f.z) : ((wi & 1) ? f.y : f.x);
   const uint32_t w1 = (wi & 2) ? ((wi & 1) ? nxt : f.w) : ((wi & 1) ? f.z : f.y);
   const uint32_t pair = (i & 1) ? __funnelshift_r(w0, w1, 16) : w0;
@@ -258,19 +263,38 @@ __global__ void __launch_bounds__(256) k_rans_decode(
     const int q0 = (int)ch.first + lane;
     y2 = q0 / pair; rr = q0 - y2 * pair;
   }
-  uint32_t pk_next = (lane < nl && lane < count) ? __ldg(idxp + lane) : 0u;
+  // packed indices of this lane's next two symbols and the coarse row of
+  // the next one, fetched a round ahead so that neither load is on the
+  // round's dependent chain (every unpacked index is a valid table)
+  uint32_t pk_a = (lane < nl && lane < count) ? __ldg(idxp + lane) : 0u;
+  uint32_t pk_b = (lane < nl && lane + nl < count) ? __ldg(idxp + lane + nl) : 0u;
+  uint4 ca0, ca1;
+  {
+    int c, t;
+    unpack_index(pk_a, c, t);
+    const uint4 *cr = reinterpret_cast<const uint4 *>(s_coarse + t * kCoarse);
+    ca0 = cr[0]; ca1 = cr[1];
+  }
   for (int it = 0; it < niter; ++it) {
     const int p = it * nl + lane;
     const bool active = lane < nl && p < count;
-    const uint32_t pk = pk_next;
-    if (active && p + nl < count) pk_next = __ldg(idxp + p + nl);
+    const uint32_t pk = pk_a;
+    const uint4 c0 = ca0, c1 = ca1;
+    {
+      int c, t;
+      unpack_index(pk_b, c, t);
+      const uint4 *cr = reinterpret_cast<const uint4 *>(s_coarse + t * kCoarse);
+      ca0 = cr[0]; ca1 = cr[1];
+    }
+    pk_a = pk_b;
+    pk_b = (active && p + 2 * nl < count) ? __ldg(idxp + p + 2 * nl) : 0u;
     int ctr = 0, s = 1;
     if (active) {
       int tid;
       unpack_index(pk, ctr, tid);
       const uint32_t slot = x & (kM - 1);
       uint32_t lo, hi;
-      s = cdf_search(bank + (size_t)tid * (kNSym + 1), s_coarse + tid * kCoarse, slot, lo, hi);
+      s = cdf_search_r(bank + (size_t)tid * (kNSym + 1), c0, c1, slot, lo, hi);
       x = (hi - lo) * (x >> kLogM) + slot - lo;
     }
     {
