@@ -223,8 +223,9 @@ constexpr int kA = 576;                   // layer-1 positions kept (> 511 + 2 *
 constexpr int kA2 = 448;                  // layer-2 positions kept (> 383 + 2 * 24 + 2)
 
 struct LiftTcSmem {
+  // layer-1 slab; once the layer-2 MMAs have completed, the layer-2 slab
+  // (2 * kA2 * 8 elements) is written over it
   alignas(128) __nv_bfloat16 a1[2 * kA * 8];
-  alignas(128) __nv_bfloat16 a2[2 * kA2 * 8];
   alignas(128) __nv_bfloat16 w2[9 * 2 * LF * 8];
   alignas(128) __nv_bfloat16 w3[9 * 2 * LF * 8];
   alignas(16) float in[LI * LI];
@@ -259,12 +260,14 @@ __device__ __forceinline__ bool lift_mma_wait(uint64_t *bar, uint32_t parity) {
 __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
   extern __shared__ __align__(1024) uint8_t lsm_raw[];
   LiftTcSmem &S = *reinterpret_cast<LiftTcSmem *>(lsm_raw);
+  __nv_bfloat16 *const a2 = S.a1;   // layer-2 slab over the consumed layer-1 slab
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int p = blockIdx.z;
   const int tiles_x = (a.W + LT - 1) / LT;
   const int y0 = (blockIdx.x / tiles_x) * LT, x0 = (blockIdx.x % tiles_x) * LT;
-  // TMEM columns: layer 2 in [0, 64) (4 blocks x 16), layer 3 in [64, 112)
-  constexpr uint32_t kCols = 128;
+  // TMEM columns: layer 2 in [0, 64) (4 blocks x 16), then layer 3 in
+  // [0, 48) once the layer-2 epilogue has read them
+  constexpr uint32_t kCols = 64;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -367,8 +370,8 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
 #pragma unroll
         for (int k = 0; k < LF; ++k)
           hb[k] = __float2bfloat16_rn(live ? tanh_fast(v[k] + S.b2[k]) : 0.f);
-        *reinterpret_cast<uint4 *>(S.a2 + (size_t)m * 8) = *reinterpret_cast<const uint4 *>(hb);
-        *reinterpret_cast<uint4 *>(S.a2 + ((size_t)kA2 + m) * 8) =
+        *reinterpret_cast<uint4 *>(a2 + (size_t)m * 8) = *reinterpret_cast<const uint4 *>(hb);
+        *reinterpret_cast<uint4 *>(a2 + ((size_t)kA2 + m) * 8) =
             *reinterpret_cast<const uint4 *>(hb + 8);
       }
     }
@@ -380,7 +383,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
 
   // layer 3: 3 blocks x 9 taps MMAs into TMEM columns 64 + 16 i
   if (t == 0 && ok) {
-    const uint32_t abase = smem_u32(S.a2), bbase = smem_u32(S.w3);
+    const uint32_t abase = smem_u32(a2), bbase = smem_u32(S.w3);
 #pragma unroll
     for (int i = 0; i < kMT3; ++i) {
 #pragma unroll
@@ -388,7 +391,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
         const uint32_t arow = (uint32_t)(i * 128 + (tap / 3) * kRS + tap % 3);
         const uint64_t ad = sdesc(abase + arow * 16u, kA2 * 16u, 128u);
         const uint64_t bd = sdesc(bbase + (uint32_t)tap * (2 * LF * 16), LF * 16u, 128u);
-        mma_bf16(tbase + (uint32_t)(kMT * LF + i * LF), ad, bd, idesc, tap > 0 ? 1u : 0u);
+        mma_bf16(tbase + (uint32_t)(i * LF), ad, bd, idesc, tap > 0 ? 1u : 0u);
       }
     }
     mma_commit(&S.bar);
@@ -400,7 +403,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
     const int q = warp & 3;
     for (int i = warp >> 2; i < kMT3; i += 2) {
       float v[LF];
-      tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(kMT * LF + i * LF), v);
+      tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(i * LF), v);
       const int m = i * 128 + 32 * q + lane;
       const int r = m / kRS, c = m % kRS;
       if (r < LT && c < LT) S.rout[r * LT + c] = v[0] + S.b3;
