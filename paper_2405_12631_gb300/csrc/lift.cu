@@ -238,6 +238,22 @@ struct LiftTcSmem {
   float b3;
 };
 
+// Two FP32 values in one 64-bit register pair, and a packed FP32 FMA (two
+// fused multiply-adds, each rounded like fmaf).
+__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
 // Bounded wait of every thread for completion phase `parity` of the MMA
 // barrier (lane 0 polls, the rest follow); false on expiry.
 __device__ __forceinline__ bool lift_mma_wait(uint64_t *bar, uint32_t parity) {
@@ -314,14 +330,23 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
     const int yy = y0 - 2 + r, xx = x0 - 2 + c;
     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (r < L1 && c < L1 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+      // channel pairs in packed FP32 FMAs (the same rounding as fmaf)
+      uint64_t acc[4];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = S.b1[8 * g + k];
+      for (int k = 0; k < 4; ++k) acc[k] = f2pack(S.b1[8 * g + 2 * k], S.b1[8 * g + 2 * k + 1]);
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const float iv = S.in[(r + tap / 3) * LI + c + tap % 3];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = fmaf(S.w1t[tap * LF + 8 * g + k], iv, v[k]);
+        const uint64_t iv2 = f2pack(iv, iv);
+        const float4 wa = *reinterpret_cast<const float4 *>(S.w1t + tap * LF + 8 * g);
+        const float4 wb = *reinterpret_cast<const float4 *>(S.w1t + tap * LF + 8 * g + 4);
+        acc[0] = fma2(f2pack(wa.x, wa.y), iv2, acc[0]);
+        acc[1] = fma2(f2pack(wa.z, wa.w), iv2, acc[1]);
+        acc[2] = fma2(f2pack(wb.x, wb.y), iv2, acc[2]);
+        acc[3] = fma2(f2pack(wb.z, wb.w), iv2, acc[3]);
       }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) f2unpack(acc[k], v[2 * k], v[2 * k + 1]);
 #pragma unroll
       for (int k = 0; k < 8; ++k) v[k] = tanh_fast(v[k]);
     }
