@@ -32,7 +32,7 @@ def _requests(n, seed):
     return reqs, imgs
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
 def test_server_results_identical_to_single_decode(pw, prec):
     codec = pw.Codec(0, prec)
     cfg = S.ModelConfig(levels=4, C=32, ll_mode=0)
