@@ -15,10 +15,12 @@
 // exp() here is the library's own routine (Cody-Waite reduction by ln 2 and a
 // degree-6 Taylor polynomial in Horner order) written with explicitly
 // rounded intrinsics, so no contraction or library-specific rounding enters.
+#include <atomic>
 #include <mutex>
 
 #include "pw_internal.cuh"
 #include "ctx_kernels.cuh"
+#include "tc_ptx.cuh"
 
 namespace pw {
 
@@ -200,10 +202,27 @@ __global__ void __launch_bounds__(256) k_rans_decode(
     uint32_t *status) {
   extern __shared__ uint4 s_coarse4[];
   {
-    const uint4 *src = reinterpret_cast<const uint4 *>(coarse);
-    for (int i = threadIdx.x; i < kNTables * kCoarse / 8; i += blockDim.x) s_coarse4[i] = __ldg(src + i);
+    // the coarse level (64 KB) in one asynchronous bulk copy, whatever the
+    // block's size; an mbarrier after it counts the bytes
+    constexpr uint32_t kBytes = kNTables * kCoarse * 2;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(s_coarse4 + kBytes / 16);
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      mbar_expect_tx(bar, kBytes);
+      for (uint32_t off = 0; off < kBytes; off += 32768u)
+        bulk_load(reinterpret_cast<uint8_t *>(s_coarse4) + off,
+                  reinterpret_cast<const uint8_t *>(coarse) + off, min(32768u, kBytes - off),
+                  bar);
+    }
+    __syncthreads();
+    // bounded: on expiry the status says so and the block leaves after the
+    // copy has had ample time to land
+    if (!mbar_wait_drain(bar, 0)) {
+      if (threadIdx.x == 0) atomicOr(status, kStTimeout);
+      return;
+    }
   }
-  __syncthreads();
   const uint16_t *s_coarse = reinterpret_cast<const uint16_t *>(s_coarse4);
   const int cw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -529,12 +548,22 @@ void launch_rans_decode(const DecChunk *chunks, int nchunks, const uint16_t *ban
                         int32_t *out, int64_t out_stride, int h, int w, int step,
                         uint32_t *status, cudaStream_t st) {
   if (nchunks <= 0) return;
-  constexpr int smem = kNTables * kCoarse * 2;
+  constexpr int smem = kNTables * kCoarse * 2 + 16;   // coarse level + mbarrier
   static std::once_flag attr;
   std::call_once(attr, [] {
     cudaFuncSetAttribute(k_rans_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   });
-  const int wpb = 8;
+  // one warp per chunk; with few chunks, fewer warps per block so that the
+  // chunks spread over the SMs (one warp per scheduler)
+  static std::atomic<int> nsm{0};
+  if (!nsm.load()) {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    nsm.store(n > 0 ? n : 148);
+  }
+  int wpb = 8;
+  while (wpb > 1 && (nchunks + wpb - 1) / wpb < nsm.load()) wpb >>= 1;
   k_rans_decode<<<(nchunks + wpb - 1) / wpb, 32 * wpb, smem, st>>>(
       chunks, nchunks, bank, coarse, idx, idx_stride, out, out_stride, h, w, step, status);
 }
