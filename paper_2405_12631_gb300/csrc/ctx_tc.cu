@@ -103,8 +103,10 @@ __device__ __forceinline__ float lrelu_f(float x) { return x >= 0.f ? x : 0.01f 
 
 // ---------------------------------------------------------------------------
 // TE_HEADC: the residual + head 3x3 conv of steps 2-4 evaluated at the
-// step's own positions only (see the compact head below)
-enum { TE_STORE = 0, TE_LSTM = 1, TE_HEAD = 2, TE_HEADC = 3 };
+// step's own positions only (see the compact head below). TE_STOREV: a plain
+// store whose K-block 0 is a BF16 v block (the steps 2-4 z conv); TE_LSTM
+// always has one too. Convs without a v block compile without its code.
+enum { TE_STORE = 0, TE_LSTM = 1, TE_HEAD = 2, TE_HEADC = 3, TE_STOREV = 4 };
 
 struct TcConvArgs {
   int P, H, W;
@@ -117,13 +119,16 @@ struct TcConvArgs {
   uint32_t stage_bytes, w_bytes;
   const __nv_bfloat16 *wt;      // [nb][kblock][tap][kb/8][ncta][8]
   // K-block 0 may be a 16-channel BF16 "v" block with its own weights wtv
-  // [nb][tap][2][ncta][8] (wv_bytes per N block, stages of vstage_bytes),
-  // read through the first tensor map: for the ConvLSTM gates the 9
+  // [nb][tap][2][ncta][8] (wv_bytes per N block), read through the first
+  // tensor map (vstage_bytes), either into the first K-block's stage after
+  // its hstage_bytes of the other input (one barrier and one commit for
+  // both) or, when hstage_bytes is 0, as K-block 0 in a stage of its own:
+  // for the ConvLSTM gates the 9
   // neighbour values of the upsampled previous subband and an inside
   // indicator (in place of e), for the steps 2-4 z conv the 9 masked
   // neighbour values; wt then holds the remaining K-blocks
   const __nv_bfloat16 *wtv;
-  uint32_t wv_bytes, vstage_bytes;
+  uint32_t wv_bytes, vstage_bytes, hstage_bytes;
   const float *bias;            // [nb * ncta]
   int epi, act;
   __nv_bfloat16 *out;
@@ -279,6 +284,12 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 
   // the head epilogue (residual + 1x1 C->2) on full tiles or compact ones
   constexpr bool HEADK = EPI == TE_HEAD || EPI == TE_HEADC;
+  // plain stores; convs with a v block; the gates' v block shares the h
+  // block's stage (one wait and one commit per tile), the z conv's has a
+  // stage of its own (both measured the faster choice)
+  constexpr bool STORE = EPI == TE_STORE || EPI == TE_STOREV;
+  constexpr bool HV = EPI == TE_LSTM || EPI == TE_STOREV;
+  constexpr bool VMERGE = EPI == TE_LSTM;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nb = blockIdx.x % a.nb;
   const int cta = blockIdx.x / a.nb;
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
 
   // a plain store whose only output is FP8: the output scale is folded into
   // the accumulator scale and bias (lrelu commutes with a positive scale)
-  const bool fold8 = EPI == TE_STORE && a.out8 && !a.out && !a.res && !a.outc;
+  const bool fold8 = STORE && a.out8 && !a.out && !a.res && !a.outc;
   {
     const int nb0 = (blockIdx.x % a.nb) * NCTA;
     // FP8 output scale per output channel: the LSTM's outputs are channels
@@ -362,8 +373,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
           const TileIter &tt = u ? t1 : ti;
           const int tx = tt.tx, ty = tt.ty, p = tt.p;
           if (!mbar_wait(&empty[stage], phase ^ 1, s_abort, 500)) { stop = true; break; }
-          const bool vk = a.wv_bytes && kbi == 0;   // the gates' BF16 v block
-          mbar_expect_tx(&full[stage], vk ? a.vstage_bytes : a.stage_bytes);
+          const bool vk = HV && kbi == 0;    // the stage holds the v block
+          const bool vsep = vk && !VMERGE;   // ... and nothing else
+          const uint32_t hb = VMERGE ? a.hstage_bytes : a.stage_bytes;
+          mbar_expect_tx(&full[stage], vsep ? a.vstage_bytes : vk ? hb + a.vstage_bytes : hb);
           if constexpr (EPI == TE_HEADC) {
             // compact head: K-step kbi = a.tps taps (9 / a.tps steps per
             // tile), one box per tap of cR rows x cJ positions x all
@@ -390,9 +403,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
             // coordinate = pixel x * 8 channels (a multiple of 8 elements =
             // 16 bytes, also when negative at the left border)
             if (vk)
-              tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage],
-                          (tx * kTileW - R) * 8, ty * kTileH - R, 0, p);
-            else if (kbi < a.nkb0)
+              tma_load_4d(stg + (size_t)stage * a.stage_bytes + a.hstage_bytes, &tmap,
+                          &full[stage], (tx * kTileW - R) * 8, ty * kTileH - R, 0, p);
+            if (vsep) {
+            } else if (kbi < a.nkb0)
               tma_load_4d(stg + (size_t)stage * a.stage_bytes, &tmap, &full[stage],
                           (tx * kTileW - R) * EPG, ty * kTileH - R, a.in_goff + kbi * GPK, p);
             else
@@ -507,25 +521,29 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         fence_after();
         const uint64_t a0 = sdesc(smem_u32(stg + (size_t)s0 * a.stage_bytes), slab, HX * 16u);
         const uint64_t a1 = sdesc(smem_u32(stg + (size_t)s1 * a.stage_bytes), slab, HX * 16u);
-        if (EPI != TE_HEADC && a.wv_bytes && kbi == 0) {
-          // v block: one BF16 MMA (K = 16, the block's two 16-byte groups)
-          // per tap, accumulating with the other K-blocks' MMAs
+        if (HV && kbi == 0) {
+          // v block (after the first K-block in the same stage, or alone
+          // in its stage): one BF16 MMA (K = 16, the block's two 16-byte
+          // groups) per tap, accumulating with the K-blocks' MMAs
           const uint32_t idv = (1u << 4) | (1u << 7) | (1u << 10) |
                                ((uint32_t)(NCTA >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
           const uint64_t bv = sdesc(smem_u32(wsm), NCTA * 16u, 128u);
+          const uint32_t vo = VMERGE ? a.hstage_bytes >> 4 : 0u;
 #pragma unroll
           for (int tap = 0; tap < taps; ++tap) {
-            const uint32_t aoff = ((uint32_t)((tap / KS) * HX + tap % KS) * 16u) >> 4;
+            const uint32_t aoff = vo + (((uint32_t)((tap / KS) * HX + tap % KS) * 16u) >> 4);
             const uint32_t boff = ((uint32_t)(tap * 2) * (NCTA * 16u)) >> 4;
             mma_bf16(d0, a0 + aoff, bv + boff, idv, accum);
             if (two) mma_bf16(d1, a1 + aoff, bv + boff, idv, accum);
             accum = 1;
           }
-          mma_commit(&empty[s0]);
-          if (two) mma_commit(&empty[s1]);
-          continue;
+          if (!VMERGE) {
+            mma_commit(&empty[s0]);
+            if (two) mma_commit(&empty[s1]);
+            continue;
+          }
         }
-        const int kh = kbi - (a.wv_bytes ? 1 : 0);   // index in wt
+        const int kh = kbi - (HV && !VMERGE ? 1 : 0);   // index in wt
         const uint64_t b0 = sdesc(smem_u32(wsm) + a.wv_bytes + (uint32_t)kh * wblock, NCTA * 16u, 128u);
 #pragma unroll
         for (int tap = 0; tap < taps; ++tap) {
@@ -591,7 +609,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       constexpr int NPF = (EPI == TE_LSTM) ? NH / 4 : 8;
       static_assert(NPF % 8 == 0, "cell state in 8-channel groups");
       float pf[NPF];
-      uint4 pres[(HEADK || EPI == TE_STORE) ? NH / 8 : 1];
+      uint4 pres[(HEADK || STORE) ? NH / 8 : 1];
       if (work && valid) {
         if (EPI == TE_LSTM) {
           const int Hp = a.H >> a.up, Wp = a.W >> a.up;
@@ -606,8 +624,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
               load_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(&c8), pf + k);
             }
           }
-        } else if (HEADK || (EPI == TE_STORE && a.res)) {
-          const bool need = (EPI == TE_STORE) ||
+        } else if (HEADK || (STORE && a.res)) {
+          const bool need = STORE ||
                             (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step);
           if (need) {
             if (HEADK && a.res_compact_n) {
@@ -647,7 +665,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       if (++acc == kAcc) { acc = 0; aphase ^= 1; }
       if (!work) continue;
 
-      if (F8 || (EPI == TE_STORE && fold8)) {
+      if (F8 || (STORE && fold8)) {
 #pragma unroll
         for (int j = 0; j < NH; ++j) v[j] = fmaf(v[j], s_wsc[col0 + j], s_bias[col0 + j]);
       } else {
@@ -667,7 +685,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         return a.out_ps ? psix * (int64_t)(a.out8_G16 * 16) + n0 + 16 * g
                         : (((int64_t)p * a.out8_G16 + (n0 >> 4) + g) * hw + pix) * 16;
       };
-      if (EPI == TE_STORE && !valid) {
+      if (STORE && !valid) {
         // pad columns of the phase-split layout: zeros
         if (a.out_ps && y < a.H && x < ((a.W + 3) & ~3)) {
           if (a.out) {
@@ -684,7 +702,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         continue;
       }
       if (!valid && !HEADK) continue;
-      if (EPI == TE_STORE) {
+      if (STORE) {
 #pragma unroll
         for (int g = 0; g < NH / 8; ++g) {
           const int gg = (n0 >> 3) + g;
@@ -1174,6 +1192,8 @@ std::string tune_report() {
 // Launch one tensor-core convolution.
 // in / in_G / in_goff: the input tensor of the first nkb0 K-blocks (all of
 // them when in1 is null); in1 / in1_G: the input of the remaining K-blocks.
+// With a v block (cv.wv) `in` holds its two BF16 groups, the K-blocks come
+// through in1 and the nkb0 argument is not used.
 // in_G / in1_G / goffs count 16-byte channel groups (8 BF16 or 16 E4M3
 // channels; cv.f8 selects the operand type).
 static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int in_G,
@@ -1202,7 +1222,20 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     a.wtv = cv.wv;
     a.wv_bytes = (uint32_t)(cv.ks * cv.ks) * 2u * cv.ncta * 16u;
     a.vstage_bytes = (uint32_t)a.halo_x * a.halo_y * 32u;
-    a.nkb = 1 + cv.cin / cv.kb;
+    if (a.epi == TE_LSTM) {
+      // the gates: the v block follows the h block in its stage
+      a.hstage_bytes = a.stage_bytes;
+      a.stage_bytes += a.vstage_bytes;
+    } else {
+      // the z conv: the v block is K-block 0 in a stage of its own
+      if (a.epi == TE_STORE) a.epi = TE_STOREV;
+      a.hstage_bytes = 0;
+      a.nkb += 1;
+    }
+  }
+  if ((a.epi == TE_LSTM || a.epi == TE_STOREV) != (cv.wv != nullptr)) {
+    set_last_error("tensor-core conv: v block and epilogue do not match");
+    return PW_EUNSUPPORTED;
   }
   const bool hc = a.epi == TE_HEADC;
   if (hc) {
@@ -1252,7 +1285,7 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   a.nkb0 = a.nkb;
   a.in1_goff = in1_goff;
   if (in1 && !hc) {
-    a.nkb0 = nkb0;
+    a.nkb0 = cv.wv ? (a.epi == TE_LSTM ? 0 : 1) : nkb0;
     if ((s = make_map(&map1, in1, P, in1_G, H, W, a.halo_x, a.halo_y, cv.kb / epg, cv.f8)))
       return s;
   } else if (!hc) {
@@ -1286,6 +1319,8 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     PW_TC_CASE(3, 32, 32, TE_STORE, false) PW_TC_CASE(3, 32, 64, TE_STORE, false)
     PW_TC_CASE(3, 32, 128, TE_STORE, false) PW_TC_CASE(3, 64, 32, TE_STORE, false)
     PW_TC_CASE(3, 64, 64, TE_STORE, false) PW_TC_CASE(3, 64, 128, TE_STORE, false)
+    // z conv of steps 2-4 (v block + l)
+    PW_TC_CASE(1, 32, 32, TE_STOREV, false) PW_TC_CASE(1, 64, 64, TE_STOREV, false)
     // ConvLSTM gates (K-block = C channels)
     PW_TC_CASE(3, 32, 64, TE_LSTM, false) PW_TC_CASE(3, 64, 64, TE_LSTM, false)
     // residual + head: 3x3 C->C of steps 2-4, 1x1 2C->C of step 1
@@ -1304,7 +1339,7 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   };
   // tuning class: the variant (epilogue 4 = a plain store with a v block,
   // the steps 2-4 z conv) and the size
-  const uint64_t key = tune_key(cv, (cv.wv && a.epi == TE_STORE) ? 4 : a.epi, a.tiles);
+  const uint64_t key = tune_key(cv, a.epi, a.tiles);
   bool sample = false;
   int cand = 0;
   const TuneChoice ch = tune_next(key, a.stages >= 2, st, sample, cand);
@@ -1759,11 +1794,11 @@ int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * (16 + C) * 4 * C,
                pix * (32.0 + (f8 ? 1.0 : 2.0) * C + 2.0 * C + 4.0 * C + (f8 ? C : 0)));
   if (f8) {
-    if (copy_h) return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X8, 2 * G16, G16, 1);
-    return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.L8[(sb - 1) & 1], G16, 0, 1);
+    if (copy_h) return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X8, 2 * G16, G16, 0);
+    return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.L8[(sb - 1) & 1], G16, 0, 0);
   }
-  if (copy_h) return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X, 2 * G, G, 1);
-  return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, lprev, G, 0, 1);
+  if (copy_h) return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X, 2 * G, G, 0);
+  return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, lprev, G, 0, 0);
 }
 
 int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb, int step,
@@ -1854,7 +1889,7 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     // z = 1x1 over [T (v block, 16 BF16 channels), l (C channels)]
     ProfScope ps(ctx, KC_CONV1, 2.0 * pix * (16 + zt.cin) * zt.cout,
                  pix * (32.0 + 2.0 * zt.cin + (f8 ? C + C / 2 : 2.0 * zt.cout)));
-    if ((s = conv_tc(ctx, zt, t.T, 2, 0, P, h, w, a, t.err, l, G, 0, 1))) return s;
+    if ((s = conv_tc(ctx, zt, t.T, 2, 0, P, h, w, a, t.err, l, G, 0, 0))) return s;
   }
   // The head conv's outputs are used at this step's positions only (a
   // quarter of the plane): where the subband is large enough it runs on
