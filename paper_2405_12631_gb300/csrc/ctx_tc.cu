@@ -334,6 +334,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   fence_before();
   __syncthreads();
   fence_after();
+  // The set-up above reads constants only (model weights, scales), so under
+  // a programmatic dependent launch it overlaps the previous kernel's tail;
+  // activations are read and written only after griddep_wait. The producer
+  // starts its (constant) weight loads first.
+  if (threadIdx.x != 0) { griddep_wait(); griddep_launch(); }
   const uint32_t tbase = *s_tmem;
   constexpr int taps = KS * KS;
   constexpr int R = KS / 2;
@@ -355,6 +360,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       const uint32_t n = min(32768u, a.w_bytes - off);
       bulk_load(wsm + a.wv_bytes + off, wsrc + off, n, wbar);
     }
+    griddep_wait();
+    griddep_launch();
     int stage = 0;
     uint32_t phase = 0;
     int issued = 0;
@@ -1189,6 +1196,31 @@ std::string tune_report() {
   return out;
 }
 
+// Launch a tensor-core convolution with a programmatic dependency on the
+// previous kernel of the stream (its set-up overlaps that kernel's tail; it
+// touches activations only after griddep_wait).
+template <typename K>
+static int launch_pdl(pw_ctx *ctx, K kern, int grid, size_t smem, cudaStream_t st,
+                      const CUtensorMap &map, const CUtensorMap &map1, const TcConvArgs &la) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kConvThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, map, map1, la);
+  if (e != cudaSuccess) {
+    set_last_error(std::string("tensor-core conv launch: ") + cudaGetErrorString(e));
+    return PW_ECUDA;
+  }
+  ctx->launches += 1;
+  return PW_OK;
+}
+
 // Launch one tensor-core convolution.
 // in / in_G / in_goff: the input tensor of the first nkb0 K-blocks (all of
 // them when in1 is null); in1 / in1_G: the input of the remaining K-blocks.
@@ -1308,9 +1340,7 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
         cudaFuncSetAttribute(k_conv_tc<KS_, KB_, N_, E_, F8_>,                              \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);      \
       });                                                                                   \
-      k_conv_tc<KS_, KB_, N_, E_, F8_><<<grid, kConvThreads, smem, st>>>(map, map1, la);    \
-      ctx->launches += 1;                                                                   \
-      return PW_OK;                                                                         \
+      return launch_pdl(ctx, k_conv_tc<KS_, KB_, N_, E_, F8_>, grid, smem, st, map, map1, la); \
     }
     // BF16 plain stores (all shapes the stage entry accepts)
     PW_TC_CASE(1, 32, 32, TE_STORE, false) PW_TC_CASE(1, 32, 64, TE_STORE, false)
