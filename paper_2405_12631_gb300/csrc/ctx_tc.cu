@@ -1202,17 +1202,8 @@ std::string tune_report() {
 template <typename K>
 static int launch_pdl(pw_ctx *ctx, K kern, int grid, size_t smem, cudaStream_t st,
                       const CUtensorMap &map, const CUtensorMap &map1, const TcConvArgs &la) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3(kConvThreads);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, map, map1, la);
+  const cudaError_t e = launch_dep(kern, dim3((unsigned)grid), dim3(kConvThreads), smem, st,
+                                   map, map1, la);
   if (e != cudaSuccess) {
     set_last_error(std::string("tensor-core conv launch: ") + cudaGetErrorString(e));
     return PW_ECUDA;

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/pwave.h"
@@ -23,6 +24,37 @@ constexpr int kNTables = kNPhi * kNJ;  // 2048 tables of kNSym + 1 entries
 constexpr int kCoarse = 16;            // coarse CDF entries per table (every 8th)
 constexpr int kMaxLanes = 32;
 constexpr int kMaxEscBits = 30;        // Exp-Golomb prefix length limit
+
+// Programmatic dependent launch: wait until the grids this one depends on
+// have completed and their memory is visible (returns at once when the
+// launch carried no programmatic dependency); let the next kernel of the
+// stream be scheduled once every CTA of this grid has signalled or exited.
+__device__ __forceinline__ void griddep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void griddep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launch `k` with a programmatic dependency on the previous kernel of the
+// stream: it may be scheduled while that kernel finishes, so `k` must call
+// griddep_wait before it touches memory an earlier kernel writes. Errors
+// surface through cudaGetLastError as for a <<<>>> launch.
+template <typename... P, typename... A>
+inline cudaError_t launch_dep(void (*k)(P...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, A &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
 
 // Device status word bits (OR-ed by kernels, read by the host).
 enum : uint32_t {

@@ -10,16 +10,6 @@ namespace pw {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
-// Programmatic dependent launch: wait until the grids this one depends on
-// have completed and their memory is visible (returns at once when the
-// launch carried no programmatic dependency); let the next kernel of the
-// stream be scheduled once every CTA of this grid has signalled or exited.
-__device__ __forceinline__ void griddep_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-__device__ __forceinline__ void griddep_launch() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
