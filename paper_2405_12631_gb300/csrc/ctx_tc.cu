@@ -337,8 +337,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   // The set-up above reads constants only (model weights, scales), so under
   // a programmatic dependent launch it overlaps the previous kernel's tail;
   // activations are read and written only after griddep_wait. The producer
-  // starts its (constant) weight loads first.
-  if (threadIdx.x != 0) { griddep_wait(); griddep_launch(); }
+  // starts its (constant) weight loads first, and lets the next kernel be
+  // scheduled once it has issued its last load (measured faster than at
+  // the start, when the next kernel's blocks would wait beside this one).
+  if (threadIdx.x != 0) griddep_wait();
   const uint32_t tbase = *s_tmem;
   constexpr int taps = KS * KS;
   constexpr int R = KS / 2;
@@ -361,7 +363,6 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       bulk_load(wsm + a.wv_bytes + off, wsrc + off, n, wbar);
     }
     griddep_wait();
-    griddep_launch();
     int stage = 0;
     uint32_t phase = 0;
     int issued = 0;
@@ -434,6 +435,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
         ti = t1;
       }
     }
+    griddep_launch();
     // let every copy this thread issued land before the CTA can exit
     {
       int s = stage;
