@@ -304,6 +304,11 @@ __global__ void __launch_bounds__(256) k_rans_decode(
       unpack_index(pk_b, c, t);
       const uint4 *cr = reinterpret_cast<const uint4 *>(s_coarse + t * kCoarse);
       ca0 = cr[0]; ca1 = cr[1];
+      // and its fine level (256 bytes, two L1 lines) into L1, so that next
+      // round's dependent 16-byte load hits there
+      const uint16_t *frow = bank + (size_t)t * (kNSym + 1);
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(frow));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(frow + 64));
     }
     pk_a = pk_b;
     pk_b = (active && p + 2 * nl < count) ? __ldg(idxp + p + 2 * nl) : 0u;
