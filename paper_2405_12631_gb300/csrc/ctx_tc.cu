@@ -714,7 +714,6 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       if (STORE) {
 #pragma unroll
         for (int g = 0; g < NH / 8; ++g) {
-          const int gg = (n0 >> 3) + g;
           if (a.res) {
             float rv[8];
             load_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(&pres[g]), rv);
@@ -1769,11 +1768,6 @@ void tc_workspace_free(Workspace *ws) {
   pool_free(t->base, ws->stream);
   delete t;
   ws->tc = nullptr;
-}
-
-static int grid_for(int64_t n) {
-  int64_t g = (n + 255) / 256;
-  return (int)(g > 152 * 32 ? 152 * 32 : (g < 1 ? 1 : g));
 }
 
 int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
