@@ -308,7 +308,6 @@ static void lift_step(pw_ctx *ctx, const LiftStepParams &a) {
 int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         float *dst) {
   const int P = ws.P, L = g.levels;
-  cudaStream_t st = ctx->stream;
   const int rP = g.lossless ? 1 : 0, rU = g.lossless ? 2 : 0;
   // BF16 / FP8 precision class, lossy: the CNNs' middle layer on the tensor cores
   const int tc = (ctx->precision != PW_PREC_FP32 && !g.lossless) ? 1 : 0;
@@ -355,7 +354,6 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
 int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         const float *src) {
   const int P = ws.P, L = g.levels;
-  cudaStream_t st = ctx->stream;
   const int rP = g.lossless ? 1 : 0, rU = g.lossless ? 2 : 0;
   float *cur = const_cast<float *>(src);
   for (int lv = 1; lv <= L; ++lv) {

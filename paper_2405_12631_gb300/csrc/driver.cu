@@ -8,8 +8,6 @@
 
 namespace pw {
 
-static inline void bump(pw_ctx *ctx, int n = 1) { ctx->launches += (uint64_t)n; }
-
 // ---------------------------------------------------------------------------
 // Device kernels
 
