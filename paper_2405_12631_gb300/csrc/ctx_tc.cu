@@ -334,8 +334,9 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   fence_before();
   __syncthreads();
   fence_after();
-  // The set-up above reads constants only (model weights, scales), so under
-  // a programmatic dependent launch it overlaps the previous kernel's tail;
+  // The set-up above reads constants only (model weights and scales, which
+  // host copies write once at model load, never a kernel), so under a
+  // programmatic dependent launch it overlaps the previous kernel's tail;
   // activations are read and written only after griddep_wait. The producer
   // starts its (constant) weight loads first, and lets the next kernel be
   // scheduled once it has issued its last load (measured faster than at
