@@ -60,6 +60,23 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(vals, world: int, dev=None):
+    """Element-wise maximum of `vals` over the ranks (one all-reduce of a
+    float64 tensor on `dev`); the values themselves when world == 1."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_mpix_per_s(world: int, pixels_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each decoded
+    pixels_per_rank pixels, timed by the slowest of them (seconds)."""
+    return world * pixels_per_rank / seconds / 1e6
+
+
 def make_inputs(seed_base: int, batch: int):
     import synthetic as S
     imgs = [S.rgb_natural(H, W, seed=seed_base + i) for i in range(batch)]
@@ -448,12 +465,8 @@ def run_gpu(args):
     launches = codec.launches - l0
     kern = class_stats()     # the dominant class over the timed steps
     pw.pw_ctx_profile(codec.ctx, 0)
-    total_ms = float(sum(times))
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
-    value = world * pixels * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = max_over_ranks([sum(times)], world, dev)[0]
+    value = job_mpix_per_s(world, pixels * args.steps, total_ms / 1e3)
 
     # e2e: host streams -> host images through the C ABI
     e2e_times = []
@@ -466,10 +479,8 @@ def run_gpu(args):
             host_out = codec.decode_batch(model, streams)
             e2e_times.append(time.perf_counter() - t0)
         torch.cuda.synchronize()
-    et = torch.tensor([sum(e2e_times), len(e2e_times)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e_value = (world * pixels * et[1].item() / et[0].item() / 1e6) if e2e_times else None
+    e2e_s, e2e_n = max_over_ranks([sum(e2e_times), len(e2e_times)], world, dev)
+    e2e_value = job_mpix_per_s(world, pixels * e2e_n, e2e_s) if e2e_times else None
 
     if rank != 0:
         return
