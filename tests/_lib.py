@@ -25,3 +25,20 @@ def ensure_built():
         finally:
             sys.path.pop(0)
     return LIB
+
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def golden(name: str):
+    """A fixture of tests/golden: '#' lines are the citation; every other
+    line is a key followed by integers. Returns {key: [list of int lists]}."""
+    out = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            key, *vals = line.split()
+            out.setdefault(key, []).append([int(v) for v in vals])
+    return out

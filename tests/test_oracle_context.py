@@ -13,6 +13,7 @@ import pytest
 import synthetic as S
 from oracle import context as CX
 from oracle.context import ContextModel, step_map
+from tests._lib import golden
 
 
 def test_steps_tile_every_position_once_with_quarter_density():
@@ -27,15 +28,23 @@ def test_steps_tile_every_position_once_with_quarter_density():
     assert np.all((sm < 2) == (np.arange(8)[None, :] % 2 == 0))
 
 
-def test_neighbour_counts_0_2_6_8():
+def test_neighbour_counts_match_the_paper():
+    # tests/golden/four_step_neighbours.txt: the counts Sec. 3.2 prints
+    g = golden("four_step_neighbours.txt")
+    per_step = g["available_per_step"][0]
+    assert per_step == [0, 2, 6, 8]
     sm = step_map(16, 16)
-    for k, expect in enumerate([0, 2, 6, 8]):
+    seen = []
+    for k, expect in enumerate(per_step):
         ys, xs = np.nonzero(sm == k)
+        assert ys.size * g["positions_per_step_fraction_inverse"][0][0] == sm.size
         for y, x in zip(ys, xs):
             if 1 <= y < 15 and 1 <= x < 15:
                 win = sm[y - 1:y + 2, x - 1:x + 2]
                 avail = np.count_nonzero(win < k)
                 assert avail == expect, (k, y, x, avail)
+                seen.append(avail)
+    assert np.mean(seen) == g["mean_available"][0][0]
 
 
 def _cm(C=8, ll_mode=0, seed=0):

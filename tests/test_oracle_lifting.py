@@ -13,6 +13,7 @@ from scipy.signal import correlate2d
 
 import synthetic as S
 from oracle import lifting as LF
+from tests._lib import golden
 
 
 def _model(levels=4, seed=0):
@@ -129,6 +130,19 @@ def test_subband_impulse_responses_are_haar_basis_functions():
         col_kind = "H" if nm in ("LH", "HH") else "L"
         ref = 7.0 * np.outer(_haar_1d(col_kind, lv, 16), _haar_1d(row_kind, lv, 16))
         np.testing.assert_allclose(x, ref, atol=1e-12, err_msg=f"subband {i} {nm}{lv}")
+
+
+def test_subband_layout_matches_the_paper():
+    # tests/golden/subband_layout.txt: Secs. 3.1, 3.2 and 3.4
+    g = golden("subband_layout.txt")
+    shapes = LF.subband_shapes(16, 16, 4)
+    assert len(shapes) == g["subbands"][0][0]
+    for lv, count, h, w in g["level"]:
+        at = [s for s in shapes if s[2] == lv]
+        assert len(at) == count and all(s[:2] == (h, w) for s in at), (lv, at)
+    d = g["ll_divisor"][0][0]
+    for H, W in [(512, 768), (64, 32), (1024, 2048)]:
+        assert LF.subband_shapes(H, W, 4)[0][:2] == (H // d, W // d)
 
 
 def test_subband_geometry():
