@@ -163,6 +163,26 @@ def test_forward_coefficient_count_and_order():
     assert [s.shape for s in sb] == [(h, w) for h, w, _ in LF.subband_shapes(32, 48, 4)]
 
 
+def test_temporal_lifting_gop_closed_form_without_cnn():
+    # GOP size of the paper's video experiments (tests/golden/gop.txt). With
+    # the predict and update CNNs zeroed, the temporal lifting is the Haar
+    # transform along time: the last lowpass band is the mean of the GOP and
+    # the level-1 highpass bands (the last n/2, in frame order) are the
+    # differences of the frame pairs.
+    n = golden("gop.txt")["gop_size"][0][0]
+    T = int(round(np.log2(n)))
+    assert 2 ** T == n
+    t = {k: (np.zeros_like(v) if k.startswith("tlift.") else v)
+         for k, v in _model(4, seed=8).items()}
+    rng = np.random.default_rng(10)
+    frames = [rng.uniform(-128, 127, (8, 12)) for _ in range(n)]
+    bands = LF.temporal_forward(frames, t, T)
+    assert len(bands) == n
+    np.testing.assert_allclose(bands[0], np.mean(frames, axis=0), atol=1e-12)
+    for m, h in enumerate(bands[n - n // 2:]):
+        np.testing.assert_allclose(h, frames[2 * m + 1] - frames[2 * m], atol=1e-12)
+
+
 def test_temporal_lifting_perfect_reconstruction():
     t = _model(4, seed=8)
     rng = np.random.default_rng(9)
