@@ -89,6 +89,29 @@ void pw_model_free(pw_model *m);
 /* 64-bit hash of the blob; every stream records the hash of its model. */
 uint64_t pw_model_hash(const pw_model *m);
 
+/* Architecture of a random-init model: wavelet levels (1..6), context
+ * channels C (32, 64 or 128), lifting CNN channels F (16), LL mode (0: the
+ * four-step nets also for LL4, 1: the autoregressive LL model, Section 3.2). */
+typedef struct {
+  int32_t levels, C, F, ll_mode;
+} pw_model_cfg;
+
+/* Seeded random-init weights of that architecture as a weight blob: the
+ * stand-in for a trained lambda model (Section 4.1). Every tensor of the
+ * format, uniform in +-b with a Kaiming-style bound per tensor role (0.05
+ * for biases; head biases fixed at (0, softplus^-1(1.5))), drawn by
+ * SplitMix64 keyed by (seed, tensor index, element index); the same seed
+ * gives the same bytes on every host. Host-only: needs no device.
+ * buf == NULL: size query (*n = bytes). Otherwise writes *n bytes to the
+ * caller's buffer of cap bytes. Errors: PW_EINVAL (cfg NULL, cap too small),
+ * PW_EUNSUPPORTED (configuration the library does not load). */
+int pw_model_random_blob(const pw_model_cfg *cfg, uint64_t seed, void *buf, size_t cap,
+                         size_t *n);
+/* pw_model_random_blob followed by pw_model_load on ctx. Errors: those of
+ * both. */
+int pw_model_init_random(pw_ctx *ctx, const pw_model_cfg *cfg, uint64_t seed,
+                         pw_model **out);
+
 /* ---- images (Sections 3.1, 3.2) ----------------------------------------- */
 
 /* Encode one image (host or device samples) into a newly allocated host

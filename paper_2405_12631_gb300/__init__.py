@@ -43,6 +43,11 @@ class pw_stats(C.Structure):
                 ("mpix_per_s", C.c_double)]
 
 
+class pw_model_cfg(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("C", C.c_int32), ("F", C.c_int32),
+                ("ll_mode", C.c_int32)]
+
+
 class pw_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 40), ("launches", C.c_uint64), ("ms", C.c_double),
                 ("flops", C.c_double), ("bytes", C.c_double)]
@@ -68,6 +73,10 @@ _sig = {
     "pw_model_load": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(_P)]),
     "pw_model_free": (None, [_P]),
     "pw_model_hash": (C.c_uint64, [_P]),
+    "pw_model_random_blob": (C.c_int, [C.POINTER(pw_model_cfg), C.c_uint64, _P, C.c_size_t,
+                                       C.POINTER(C.c_size_t)]),
+    "pw_model_init_random": (C.c_int, [_P, C.POINTER(pw_model_cfg), C.c_uint64,
+                                       C.POINTER(_P)]),
     "pw_encode_image": (C.c_int, [_P, _P, C.POINTER(pw_image), C.POINTER(pw_codec_opts),
                                   C.POINTER(_u8p), C.POINTER(C.c_size_t)]),
     "pw_decode_image": (C.c_int, [_P, _P, _P, C.c_size_t, C.POINTER(pw_image)]),
@@ -129,6 +138,20 @@ def check(code: int):
         raise PwError(code, pw_strerror(code).decode())
 
 
+def random_model_blob(levels: int = 4, C: int = 64, F: int = 16, ll_mode: int = 0,
+                      seed: int = 0) -> bytes:
+    """pw_model_random_blob: seeded random-init weights of the architecture as
+    a weight blob (host only, no device needed)."""
+    import ctypes
+    cfg = pw_model_cfg(levels, C, F, ll_mode)
+    n = ctypes.c_size_t(0)
+    check(pw_model_random_blob(ctypes.byref(cfg), seed, None, 0, ctypes.byref(n)))
+    buf = (ctypes.c_uint8 * n.value)()
+    check(pw_model_random_blob(ctypes.byref(cfg), seed, ctypes.cast(buf, ctypes.c_void_p),
+                               n.value, ctypes.byref(n)))
+    return bytes(buf)
+
+
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(C.c_void_p)
 
@@ -153,11 +176,17 @@ def _host_image(img: np.ndarray, bitdepth: int | None):
 
 
 class Model:
-    def __init__(self, codec: "Codec", blob: bytes):
+    def __init__(self, codec: "Codec", blob: bytes = None, cfg: "pw_model_cfg" = None,
+                 seed: int = 0):
+        """A loaded model: from a weight blob (pw_model_load), or, with
+        blob None, random-init weights of `cfg` (pw_model_init_random)."""
         self.codec = codec
         self._blob = blob
         h = C.c_void_p()
-        check(pw_model_load(codec.ctx, blob, len(blob), C.byref(h)))
+        if blob is not None:
+            check(pw_model_load(codec.ctx, blob, len(blob), C.byref(h)))
+        else:
+            check(pw_model_init_random(codec.ctx, C.byref(cfg), seed, C.byref(h)))
         self.handle = h
 
     @property
@@ -253,6 +282,11 @@ class Codec:
 
     def load_model(self, blob: bytes) -> Model:
         return Model(self, blob)
+
+    def init_random_model(self, levels: int = 4, C: int = 64, F: int = 16, ll_mode: int = 0,
+                          seed: int = 0) -> Model:
+        """pw_model_init_random: the model of random_model_blob(same arguments)."""
+        return Model(self, None, pw_model_cfg(levels, C, F, ll_mode), seed)
 
     # ---- images -----------------------------------------------------------
     def encode_image(self, model: Model, img: np.ndarray, q: float = 8.0,
