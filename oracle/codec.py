@@ -44,7 +44,10 @@ subband a u32 length and a "PWBS" stream with colour 3.
 
 Pins: decode(encode(x)) reproduces the quantised coefficients exactly and
 the image to within the quantiser's reconstruction error, and exactly in
-lossless mode (tests/test_oracle_codec.py).
+lossless mode (tests/test_oracle_codec.py); the YCbCr transform against the
+BT.601 full-range matrices as JFIF prints them, the RCT against the JPEG
+2000 definition, and the padding against an explicit whole-sample mirror
+index table (tests/test_oracle_layer_pins.py).
 """
 from __future__ import annotations
 

@@ -35,9 +35,14 @@ so the layer structure below is a reading of the text:
 
 Pins: the step partition (tiling, densities, 0/2/6/8 neighbour counts) and
 causality by brute force, and the LSTM cell against its defining equations
-(tests/test_oracle_context.py). The layer arithmetic beyond those checks is
-parity unpinned: the paper does not print the architecture, so this module
-is its own specification.
+(tests/test_oracle_context.py); the layer composition of both fusion nets
+against closed forms for special weights - each skip connection, the [a, l]
+order of the steps 2-4 fusion, the LeakyReLU slope, the orientation of the
+spatial taps, the head and softplus - and the autoregressive LL model against
+a single-tap closed form (tests/test_oracle_layer_pins.py). What stays
+parity unpinned is the architecture itself (layer counts, widths, which
+activation): the paper's figures that specify it are not available, so the
+reading above is the specification.
 """
 from __future__ import annotations
 
