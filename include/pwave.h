@@ -205,8 +205,15 @@ int pw_rans_encode(pw_ctx *ctx, int nchunks, const uint32_t *count,
  * device array of about 1 MiB that every GPU loading the library holds until
  * the process exits; at most 16384 chunks per call (PW_EINVAL beyond).
  * The first call on a device looks the array's address up (make it before
- * any stream capture). Every call reuses the array, so calls that overlap on
- * the GPU race: serialise them. Errors: PW_EINVAL, PW_ECORRUPT, PW_ECUDA. */
+ * any stream capture) and keeps it for the life of the process, so a
+ * cudaDeviceReset while the library is loaded is not supported. Every call
+ * reuses the array, so calls that overlap on the GPU race: serialise them.
+ * Errors: PW_EINVAL (chunk limit, null pointer, value out of range),
+ * PW_ECORRUPT (a corrupt or truncated chunk, and also a chunk whose offset +
+ * nbytes exceeds payload_bytes or whose lane count is not 1..32: the checks
+ * run on the device, where pw_rans_decode reports those two as PW_EINVAL),
+ * PW_ETIMEOUT (the decoder's bounded wait for its table copy expired),
+ * PW_EUNSUPPORTED, PW_ECUDA. */
 int pw_rans_decode_noalloc(void *cuda_stream, const uint8_t *payload, size_t payload_bytes,
                            int nchunks, const uint32_t *offset, const uint32_t *nbytes,
                            const uint32_t *count, const uint32_t *lanes, const uint32_t *idx,

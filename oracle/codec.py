@@ -241,10 +241,15 @@ def encode_planes(model: Model, planes: list, *, width: int, height: int,
 
 
 def _encode_symbols(model, qcomp, shapes, *, width, height, bitdepth, colour,
-                    d32, lossless, chunk):
+                    d32, lossless, chunk, params=None):
+    """Entropy-code quantised subbands. params, if given, replaces the
+    context model: params[comp][subband] = (mu, sigma) arrays of the
+    subband's shape (index injection: the coder alone is then exercised on
+    another implementation's entropy parameters)."""
     bank = E.cdf_bank().astype(np.int64)
     ll_ar = model.ll_mode == 1
-    params = [context_params_all(model, qsb) for qsb in qcomp]
+    if params is None:
+        params = [context_params_all(model, qsb) for qsb in qcomp]
     layout = chunk_layout(shapes, len(qcomp), ll_ar, chunk)
     payload = []
     offsets = [0]
@@ -304,8 +309,28 @@ def parse_header(bs: bytes) -> dict:
                 payload_base=base)
 
 
-def decode_symbols(model: Model, bs: bytes):
-    """Decode the quantised subbands of every component (list of lists)."""
+def encode_symbols_with_params(model: Model, qcomp: list, params: list, *, width: int,
+                               height: int, bitdepth: int, colour: int, q: float = 8.0,
+                               lossless: bool = False, chunk: int = DEFAULT_CHUNK) -> bytes:
+    """A PWBS stream of the given quantised subbands (per component, coding
+    order) coded with the given entropy parameters instead of the context
+    model's (four-step subbands only)."""
+    L = model.levels
+    mult = 1 << L
+    Hp = -(-height // mult) * mult
+    Wp = -(-width // mult) * mult
+    d32 = f32(1.0) if lossless else f32(1.0 / q)
+    return _encode_symbols(model, qcomp, subband_shapes(Hp, Wp, L), width=width,
+                           height=height, bitdepth=bitdepth, colour=colour, d32=d32,
+                           lossless=lossless, chunk=chunk, params=params)
+
+
+def decode_symbols(model: Model, bs: bytes, params: list | None = None):
+    """Decode the quantised subbands of every component (list of lists).
+
+    params, if given, replaces the context model of the four-step subbands
+    (params[comp][subband] = (mu, sigma) over the whole subband; only the
+    values at each step's positions are read)."""
     hd = parse_header(bs)
     if hd["model_hash"] != model.hash:
         raise ValueError("stream was made with another model")
@@ -350,7 +375,9 @@ def decode_symbols(model: Model, bs: bytes):
                     _, used, xf = R.decode_chunk(st, words, n, nl, table_of, on_symbol)
                     _check_chunk(used, len(words), xf)
                 continue
-            if i == 0:
+            if params is not None:
+                l = ns = None
+            elif i == 0:
                 l, ns = np.zeros((H, W, model.C)), "ll"
             else:
                 up = shapes[i - 1][0] < H
@@ -358,7 +385,10 @@ def decode_symbols(model: Model, bs: bytes):
                                            h_state, c_state, up)
                 l, ns = h_state, "sb"
             for k in range(4):
-                mu, sg = cm.step_params(k, s.astype(np.float64), l, ns)
+                if params is not None:
+                    mu, sg = params[comp][i]
+                else:
+                    mu, sg = cm.step_params(k, s.astype(np.float64), l, ns)
                 ys, xs = step_positions(H, W, k)
                 ctr, phi, j = E.index_decision(mu[ys, xs], sg[ys, xs])
                 tid = E.table_id(phi, j)

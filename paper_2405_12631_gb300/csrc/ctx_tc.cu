@@ -1053,7 +1053,6 @@ static int make_map_hc(CUtensorMap *map, const void *base, int P, int C, int H, 
 // The compact head applies to subbands of at least 4 rows and 8 columns.
 static bool headc_ok(int h, int w) { return h >= 4 && w >= 8; }
 
-static std::atomic<int> g_num_sms{0};
 
 // ---- autotuner -------------------------------------------------------------
 // Per (kernel variant, size class = log2 of the tile count) the MMA issue
@@ -1225,12 +1224,6 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
                    int in_goff, int P, int H, int W, TcConvArgs a, int *err,
                    const void *in1 = nullptr, int in1_G = 0, int in1_goff = 0,
                    int nkb0 = -1) {
-  if (!g_num_sms.load()) {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    g_num_sms.store(n > 0 ? n : 148);
-  }
   const int R = cv.ks / 2;
   a.P = P; a.H = H; a.W = W; a.ks = cv.ks; a.cin = cv.cin; a.kb = cv.kb; a.nkb = cv.cin / cv.kb;
   a.in_goff = in_goff; a.ncta = cv.ncta; a.nb = cv.nb;
@@ -1319,7 +1312,7 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
   cudaStream_t st = ctx->stream;
   // one launch with a persistent grid of SMs / frac CTAs per N block
   auto launch = [&](TcConvArgs &la, int frac) -> int {
-    int per_nb = g_num_sms.load() / cv.nb / frac;
+    int per_nb = sm_count() / cv.nb / frac;
     if (per_nb < 1) per_nb = 1;
     if (per_nb > la.tiles) per_nb = la.tiles;
     const int grid = per_nb * cv.nb;
@@ -1328,8 +1321,8 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     la.step_dp = per_nb / (la.tiles_x * la.tiles_y);
 #define PW_TC_CASE(KS_, KB_, N_, E_, F8_)                                                   \
     if (cv.ks == KS_ && cv.kb == KB_ && cv.ncta == N_ && la.epi == E_ && cv.f8 == F8_) {    \
-      static std::once_flag attr;                                                           \
-      std::call_once(attr, [&] {                                                            \
+      static std::atomic<uint64_t> attr{0};                                                 \
+      once_per_device(attr, [&] {                                                           \
         cudaFuncSetAttribute(k_conv_tc<KS_, KB_, N_, E_, F8_>,                              \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);      \
       });                                                                                   \

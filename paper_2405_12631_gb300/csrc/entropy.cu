@@ -20,31 +20,10 @@
 
 #include "pw_internal.cuh"
 #include "ctx_kernels.cuh"
+#include "spec_math.cuh"
 #include "tc_ptx.cuh"
 
 namespace pw {
-
-// --- FP32 exponential for z <= 0 (exact op sequence, see header comment) ---
-__device__ __forceinline__ float exp32_spec(float z) {
-  if (z < -80.f) return 0.f;
-  const float kLog2e = 0x1.715476p+0f;     // float nearest 1/ln 2
-  const float kLn2Hi = 0x1.62e4p-1f;       // 0.693145751953125
-  const float kLn2Lo = 0x1.7f7d1cp-20f;    // float nearest ln 2 - kLn2Hi
-  const float c6 = 0x1.6c16c2p-10f, c5 = 0x1.111112p-7f, c4 = 0x1.555556p-5f,
-              c3 = 0x1.555556p-3f, c2 = 0.5f, c1 = 1.f, c0 = 1.f;
-  float k = rintf(__fmul_rn(z, kLog2e));
-  float r = __fsub_rn(z, __fmul_rn(k, kLn2Hi));
-  r = __fsub_rn(r, __fmul_rn(k, kLn2Lo));
-  float p = c6;
-  p = __fadd_rn(__fmul_rn(p, r), c5);
-  p = __fadd_rn(__fmul_rn(p, r), c4);
-  p = __fadd_rn(__fmul_rn(p, r), c3);
-  p = __fadd_rn(__fmul_rn(p, r), c2);
-  p = __fadd_rn(__fmul_rn(p, r), c1);
-  p = __fadd_rn(__fmul_rn(p, r), c0);
-  float scale = __int_as_float(((int)k + 127) << 23);
-  return __fmul_rn(p, scale);
-}
 
 // One warp per table. Lane l owns symbols 4l .. 4l+3 (127 symbols) and the
 // CDF entries 4l .. 4l+3 (128 entries: cdf[0] = 0 .. cdf[127] = M).
@@ -554,21 +533,15 @@ void launch_rans_decode(const DecChunk *chunks, int nchunks, const uint16_t *ban
                         uint32_t *status, cudaStream_t st) {
   if (nchunks <= 0) return;
   constexpr int smem = kNTables * kCoarse * 2 + 16;   // coarse level + mbarrier
-  static std::once_flag attr;
-  std::call_once(attr, [] {
+  static std::atomic<uint64_t> attr{0};
+  once_per_device(attr, [] {
     cudaFuncSetAttribute(k_rans_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   });
   // one warp per chunk; with few chunks, fewer warps per block so that the
   // chunks spread over the SMs (one warp per scheduler)
-  static std::atomic<int> nsm{0};
-  if (!nsm.load()) {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    nsm.store(n > 0 ? n : 148);
-  }
+  const int nsm = sm_count();
   int wpb = 8;
-  while (wpb > 1 && (nchunks + wpb - 1) / wpb < nsm.load()) wpb >>= 1;
+  while (wpb > 1 && (nchunks + wpb - 1) / wpb < nsm) wpb >>= 1;
   k_rans_decode<<<(nchunks + wpb - 1) / wpb, 32 * wpb, smem, st>>>(
       chunks, nchunks, bank, coarse, idx, idx_stride, out, out_stride, h, w, step, status);
 }

@@ -542,8 +542,8 @@ static int grid_for(int64_t n) {
 
 void launch_lift_step(const LiftStepParams &a, cudaStream_t st) {
   if (a.tc && a.net.w1 && a.round == 0) {
-    static std::once_flag attr_tc;
-    std::call_once(attr_tc, [] {
+    static std::atomic<uint64_t> attr_tc{0};
+    once_per_device(attr_tc, [] {
       cudaFuncSetAttribute(k_lift_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)sizeof(LiftTcSmem) + 1024);
     });
@@ -552,8 +552,8 @@ void launch_lift_step(const LiftStepParams &a, cudaStream_t st) {
     k_lift_tc<<<grid, 256, sizeof(LiftTcSmem) + 1024, st>>>(a);
     return;
   }
-  static std::once_flag attr;
-  std::call_once(attr, [] {
+  static std::atomic<uint64_t> attr{0};
+  once_per_device(attr, [] {
     cudaFuncSetAttribute(k_lift_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(LiftSmem));
   });

@@ -68,7 +68,10 @@ __global__ void k_noalloc_descs(const uint8_t *payload, uint64_t payload_bytes, 
   }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array, looked up once per device (with that
+// device current) and kept for the life of the process. A cudaDeviceReset
+// while the library is loaded would leave a stale address here: this entry
+// point does not support one.
 static std::mutex g_mu;
 static uint8_t *g_addr[64] = {};
 
@@ -113,6 +116,7 @@ extern "C" int pw_rans_decode_noalloc(void *cuda_stream, const uint8_t *payload,
   uint8_t *base = nullptr;
   int s = scratch_address(&base);
   if (s) return s;
+  launch_failed() = false;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   uint32_t *status = reinterpret_cast<uint32_t *>(base);
   uint16_t *bank = reinterpret_cast<uint16_t *>(base + 256);
@@ -134,9 +138,26 @@ extern "C" int pw_rans_decode_noalloc(void *cuda_stream, const uint8_t *payload,
     set_last_error(std::string("CUDA: ") + cudaGetErrorString(e));
     return PW_ECUDA;
   }
+  if (launch_failed()) {
+    launch_failed() = false;
+    return PW_EUNSUPPORTED;
+  }
+  // every bit the decoder can set, as the context entry points report them
   if (h & kStCorrupt) {
-    set_last_error("corrupt or truncated rANS chunk");
+    set_last_error("corrupt or truncated rANS chunk (or a chunk outside the payload)");
     return PW_ECORRUPT;
+  }
+  if (h & kStRange) {
+    set_last_error("value outside the coder's range");
+    return PW_EINVAL;
+  }
+  if (h & kStTimeout) {
+    set_last_error("the decoder's bounded wait for its table copy expired");
+    return PW_ETIMEOUT;
+  }
+  if (h) {
+    set_last_error("unexpected decoder status");
+    return PW_ECUDA;
   }
   return PW_OK;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <utility>
 #include <vector>
@@ -54,6 +55,39 @@ inline cudaError_t launch_dep(void (*k)(P...), dim3 grid, dim3 block, size_t sme
   cfg.attrs = at;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+}
+
+// Kernel attributes and device properties belong to one device, so the
+// launchers' one-time set-up is kept per device ordinal (0..63; others redo
+// it every time). once_per_device runs f the first time it is reached with
+// the current device active; two threads racing there may both run f, which
+// is why f must be idempotent (setting a kernel attribute is).
+inline int current_device() {
+  int d = 0;
+  return cudaGetDevice(&d) == cudaSuccess ? d : -1;
+}
+template <typename F>
+inline void once_per_device(std::atomic<uint64_t> &done, F &&f) {
+  const int d = current_device();
+  const uint64_t bit = (d >= 0 && d < 64) ? (1ull << d) : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+  f();
+  if (bit) done.fetch_or(bit, std::memory_order_release);
+}
+// Number of SMs of the current device (cached per device).
+inline int sm_count() {
+  static std::atomic<int> cache[64];
+  const int d = current_device();
+  if (d >= 0 && d < 64) {
+    const int n = cache[d].load(std::memory_order_relaxed);
+    if (n) return n;
+  }
+  int n = 0;
+  if (d < 0 || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess ||
+      n <= 0)
+    n = 148;
+  if (d >= 0 && d < 64) cache[d].store(n, std::memory_order_relaxed);
+  return n;
 }
 
 // Device status word bits (OR-ed by kernels, read by the host).

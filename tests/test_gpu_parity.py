@@ -9,8 +9,12 @@ Bars (see the oracle module headers for the definitions):
   magnitude up to ~300 (FP32 vs FP64 through three tanh layers per step and
   four levels);
 * table-index decisions taken on FP32 parameters agree with the oracle's
-  FP64 parameters except at certified near-ties (oracle value within 1e-4
-  relative of a decision boundary), which are counted;
+  FP64 parameters except at certified near-ties (oracle value within 1e-5
+  relative of a decision boundary), which are counted and printed. 1e-5 is
+  above the FP32 path's largest measured deviation of the two decided
+  quantities (16 mu relative to max(|16 mu|, 1): 6.0e-6; sigma relative:
+  2.8e-7, over the 393,216 parameters of a 768x512 plane at C = 64,
+  test_gpu_fullsize_params.py);
 * decoded image PSNR within 0.01 dB of the oracle's.
 """
 import numpy as np
@@ -25,7 +29,7 @@ from tests._lib import ensure_built
 
 pytestmark = pytest.mark.gpu
 
-TIE_EPS = 1e-4
+TIE_EPS = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -186,6 +190,8 @@ def test_context_params_match_oracle(codec, model32):
     co, po, jo = E.index_decision(mu_o, sg_o)
     diff = (cg != co) | (pg != po) | (jg != jo)
     ties = E.near_tie(mu_o, sg_o, TIE_EPS)
+    print(f"\nFP32 index decisions differing from the oracle: {int(diff.sum())} of "
+          f"{diff.size}; near-ties at {TIE_EPS:g}: {int(ties.sum())}")
     assert not np.any(diff & ~ties), int(np.sum(diff & ~ties))
 
 
