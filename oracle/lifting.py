@@ -20,10 +20,19 @@ Readings (the paper defers the filter details to its references):
   shared by all levels;
 * integer mode takes floor(P) and floor(U + 1/2), decided in FP32, so
   that with the CNN residuals at zero it is exactly the reversible 5/3
-  lifting of JPEG 2000.
+  lifting of JPEG 2000;
+* integer mode evaluates the CNN residual as a fixed sequence of FP32
+  operations (lift_cnn_fp32, tanh32), because an integer lifting step
+  reconstructs exactly only where encoder and decoder round the same value:
+  the Fig. 2 caption's guarantee of perfect reconstruction then holds
+  between any two implementations, not just within one. Each layer starts
+  from its bias and adds, tap by tap in raster order and within a tap input
+  channel by input channel, the product w * x, product and sum each rounded
+  to FP32 (no fused multiply-add); v = P_lin + CNN is one FP32 addition.
 
 Pins: perfect reconstruction for random weights, the exact integer round
-trip, the LeGall 5/3 integer lifting of JPEG 2000 (CNN residual zero) checked
+trip, tanh32 within a few FP32 ulps of FP64 tanh and lift_cnn_fp32 within
+FP32 rounding of the FP64 CNN, the LeGall 5/3 integer lifting of JPEG 2000 (CNN residual zero) checked
 against a direct textbook formula, and the 2-D Haar basis functions for the
 Haar special case (tests/test_oracle_lifting.py).
 
@@ -36,6 +45,9 @@ from __future__ import annotations
 
 import numpy as np
 
+from .entropy import exp32
+
+f32 = np.float32
 
 def conv2d(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
     """Cross-correlation with zero padding ('same' size).
@@ -64,6 +76,68 @@ def lift_cnn(v: np.ndarray, net: dict) -> np.ndarray:
     return conv2d(t, net["w3"], net["b3"])[:, :, 0]
 
 
+# float32 nearest 1/n!, n = 3..11 (each written as its bit pattern's value)
+_INV_FACT32 = {n: f32(float.fromhex(h)) for n, h in
+               ((3, "0x1.555556p-3"), (4, "0x1.555556p-5"), (5, "0x1.111112p-7"),
+                (6, "0x1.6c16c2p-10"), (7, "0x1.a01a02p-13"), (8, "0x1.a01a02p-16"),
+                (9, "0x1.71de3ap-19"), (10, "0x1.27e4fcp-22"), (11, "0x1.ae6456p-26"))}
+
+
+def tanh32(x: np.ndarray) -> np.ndarray:
+    """tanh as a fixed sequence of correctly rounded FP32 operations.
+
+    With a = |x| and z = -2a (exact), m = e^z - 1 is the degree-11 Taylor
+    polynomial z + z^2/2! + ... + z^11/11! in Horner order (coefficients the
+    float32 nearest 1/n!) when z >= -1, else exp32(z) - 1 (e^z <= 1/e there,
+    so the subtraction does not cancel); then tanh(a) = -m / (2 + m), given
+    the sign of x.
+    """
+    x = np.asarray(x, dtype=f32)
+    a = np.abs(x)
+    z = (f32(-2.0) * a).astype(f32)
+    p = np.full_like(z, _INV_FACT32[11])
+    for n in (10, 9, 8, 7, 6, 5, 4, 3):
+        p = (p * z).astype(f32)
+        p = (p + _INV_FACT32[n]).astype(f32)
+    p = (p * z).astype(f32)
+    p = (p + f32(0.5)).astype(f32)
+    p = (p * z).astype(f32)
+    p = (p + f32(1.0)).astype(f32)
+    m_series = (p * z).astype(f32)
+    m_exp = (exp32(np.minimum(z, f32(0.0))) - f32(1.0)).astype(f32)
+    m = np.where(z >= f32(-1.0), m_series, m_exp).astype(f32)
+    t = ((-m).astype(f32) / (f32(2.0) + m).astype(f32)).astype(f32)
+    return np.copysign(t, x).astype(f32)
+
+
+def conv3x3_fp32(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Zero-padded 3x3 cross-correlation (as conv2d) in FP32 with a fixed
+    order of separately rounded operations: acc = b, then for each tap (dy,
+    dx) in raster order and each input channel i in ascending order
+    acc = acc + w[o, i, dy, dx] * x[y + dy - 1, x + dx - 1, i]."""
+    H, W, Cin = x.shape
+    Cout = w.shape[0]
+    w32 = np.asarray(w, dtype=f32)
+    xp = np.zeros((H + 2, W + 2, Cin), dtype=f32)
+    xp[1:H + 1, 1:W + 1, :] = x
+    acc = np.empty((H, W, Cout), dtype=f32)
+    acc[...] = np.asarray(b, dtype=f32)
+    for dy in range(3):
+        for dx in range(3):
+            for i in range(Cin):
+                prod = (xp[dy:dy + H, dx:dx + W, i:i + 1] * w32[:, i, dy, dx]).astype(f32)
+                acc = (acc + prod).astype(f32)
+    return acc
+
+
+def lift_cnn_fp32(v: np.ndarray, net: dict) -> np.ndarray:
+    """The CNN residual of lift_cnn evaluated as the integer-mode FP32
+    operation sequence (float32 result)."""
+    t = tanh32(conv3x3_fp32(np.asarray(v, dtype=f32)[:, :, None], net["w1"], net["b1"]))
+    t = tanh32(conv3x3_fp32(t, net["w2"], net["b2"]))
+    return conv3x3_fp32(t, net["w3"], net["b3"])[:, :, 0]
+
+
 def net_of(tensors: dict, prefix: str) -> dict:
     return {k: tensors[prefix + k] for k in ("w1", "b1", "w2", "b2", "w3", "b3")}
 
@@ -89,7 +163,9 @@ def predict(e: np.ndarray, axis: int, net: dict | None, lossless: bool,
     linear="haar" replaces the linear part by P_lin(e)[n] = e[n].
     """
     v = e.copy() if linear == "haar" else 0.5 * (e + _shift(e, axis, +1))
-    if net is not None:
+    if net is not None and lossless:
+        v = (v.astype(f32) + lift_cnn_fp32(e, net)).astype(f32).astype(np.float64)
+    elif net is not None:
         v = v + lift_cnn(e, net)
     return round_int(v, 0.0) if lossless else v
 
@@ -101,7 +177,9 @@ def update(h: np.ndarray, axis: int, net: dict | None, lossless: bool,
     linear="haar" replaces the linear part by U_lin(h)[n] = h[n] / 2.
     """
     v = 0.5 * h if linear == "haar" else 0.25 * (_shift(h, axis, -1) + h)
-    if net is not None:
+    if net is not None and lossless:
+        v = (v.astype(f32) + lift_cnn_fp32(h, net)).astype(f32).astype(np.float64)
+    elif net is not None:
         v = v + lift_cnn(h, net)
     return round_int(v, 0.5) if lossless else v
 

@@ -12,12 +12,23 @@
 // spatial transform; Haar (P = s, U = s / 2) for the temporal one. Integer
 // mode (lossless) rounds P with floor(v) and U with floor(v + 1/2), which
 // makes the transform the JPEG 2000 reversible 5/3 when the CNN is zero.
+//
+// An integer lifting step reconstructs exactly only if encoder and decoder
+// round the same P and U values, so in integer mode the CNN is evaluated as
+// a fixed sequence of FP32 operations that any IEEE implementation
+// reproduces bit for bit: every layer starts from its bias and adds, tap by
+// tap in raster order (dy, dx) and within a tap input channel by input
+// channel in ascending order, the product w * x (product and sum each
+// rounded to nearest even, never fused), the activation is tanh32_spec, and
+// v = lin + CNN is one rounded addition before the floor. The lossy steps
+// keep fused multiply-adds and the CUDA tanh.
 #include <cuda_bf16.h>
 
 #include <mutex>
 
 #include "pw_internal.cuh"
 #include "lift_kernels.cuh"
+#include "spec_math.cuh"
 #include "tc_ptx.cuh"
 
 namespace pw {
@@ -52,6 +63,17 @@ __device__ __forceinline__ void ld16(const float *p, float *v) {
   }
 }
 
+// acc + w * x: one fused multiply-add, or (kExact) a rounded product and a
+// rounded sum; the activation: CUDA's tanhf, or (kExact) tanh32_spec.
+template <bool kExact>
+__device__ __forceinline__ float mac(float acc, float w, float x) {
+  return kExact ? __fadd_rn(acc, __fmul_rn(w, x)) : fmaf(w, x, acc);
+}
+template <bool kExact>
+__device__ __forceinline__ float act(float v) {
+  return kExact ? tanh32_spec(v) : tanhf(v);
+}
+
 __device__ __forceinline__ float acc_get(const PlaneAcc &a, int p, int y, int x) {
   return a.p[(int64_t)p * a.ps + (int64_t)y * a.rs + (int64_t)x * a.cs];
 }
@@ -64,6 +86,7 @@ __device__ __forceinline__ void acc_set(const PlaneAcc &a, int p, int y, int x, 
 // 16 x 16 tile; thread t handles output (t / 16, t % 16). in: the 22 x 22
 // input region (origin y0 - 3, x0 - 3).
 // rout (optional): the CNN residual of the tile's outputs, already computed.
+template <bool kExact>
 __device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int y0, int x0,
                                             const float *in, const float *a2, const float *w3t,
                                             const float *b3, const float *rout = nullptr) {
@@ -79,7 +102,7 @@ __device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int 
       ld16(a2 + ((ly + tap / 3) * L2 + lx + tap % 3) * LF, xv);
       ld16(w3t + tap * LF, w);
 #pragma unroll
-      for (int ci = 0; ci < LF; ++ci) v = fmaf(w[ci], xv[ci], v);
+      for (int ci = 0; ci < LF; ++ci) v = mac<kExact>(v, w[ci], xv[ci]);
     }
     r_out = v;
   }
@@ -100,7 +123,7 @@ __device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int 
   } else {  // LIN_HALF
     lin = 0.5f * s0;
   }
-  float v = lin + r_out;
+  float v = kExact ? __fadd_rn(lin, r_out) : lin + r_out;
   if (a.round == 1) v = floorf(v);
   else if (a.round == 2) v = floorf(v + 0.5f);
   const float o = acc_get(a.other, p, y, x);
@@ -108,6 +131,7 @@ __device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int 
   if (a.copy.p) acc_set(a.copy, p, y, x, s0);
 }
 
+template <bool kExact>
 __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
   extern __shared__ float smem_raw[];
   LiftSmem &S = *reinterpret_cast<LiftSmem *>(smem_raw);
@@ -148,13 +172,13 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
         const float iv = S.in[(ly + tap / 3) * LI + lx + tap % 3];
         ld16(S.w1t + tap * LF, w);
 #pragma unroll
-        for (int c = 0; c < LF; ++c) acc[c] = fmaf(w[c], iv, acc[c]);
+        for (int c = 0; c < LF; ++c) acc[c] = mac<kExact>(acc[c], w[c], iv);
       }
       float4 *dst = reinterpret_cast<float4 *>(S.a1 + e * LF);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        dst[i] = inside ? make_float4(tanhf(acc[4 * i]), tanhf(acc[4 * i + 1]),
-                                      tanhf(acc[4 * i + 2]), tanhf(acc[4 * i + 3]))
+        dst[i] = inside ? make_float4(act<kExact>(acc[4 * i]), act<kExact>(acc[4 * i + 1]),
+                                      act<kExact>(acc[4 * i + 2]), act<kExact>(acc[4 * i + 3]))
                         : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
@@ -177,8 +201,8 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
           ld16(S.w2t + (tap * LF + ci) * LF, w);
 #pragma unroll
           for (int c = 0; c < LF; ++c) {
-            acc0[c] = fmaf(w[c], in0v[ci], acc0[c]);
-            acc1[c] = fmaf(w[c], in1v[ci], acc1[c]);
+            acc0[c] = mac<kExact>(acc0[c], w[c], in0v[ci]);
+            acc1[c] = mac<kExact>(acc1[c], w[c], in1v[ci]);
           }
         }
       }
@@ -189,17 +213,17 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
       float4 *d1 = reinterpret_cast<float4 *>(S.a2 + e1 * LF);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        d0[i] = in0 ? make_float4(tanhf(acc0[4 * i]), tanhf(acc0[4 * i + 1]),
-                                  tanhf(acc0[4 * i + 2]), tanhf(acc0[4 * i + 3]))
+        d0[i] = in0 ? make_float4(act<kExact>(acc0[4 * i]), act<kExact>(acc0[4 * i + 1]),
+                                  act<kExact>(acc0[4 * i + 2]), act<kExact>(acc0[4 * i + 3]))
                     : make_float4(0.f, 0.f, 0.f, 0.f);
-        d1[i] = in1 ? make_float4(tanhf(acc1[4 * i]), tanhf(acc1[4 * i + 1]),
-                                  tanhf(acc1[4 * i + 2]), tanhf(acc1[4 * i + 3]))
+        d1[i] = in1 ? make_float4(act<kExact>(acc1[4 * i]), act<kExact>(acc1[4 * i + 1]),
+                                  act<kExact>(acc1[4 * i + 2]), act<kExact>(acc1[4 * i + 3]))
                     : make_float4(0.f, 0.f, 0.f, 0.f);
       }
     }
     __syncthreads();
   }
-  lift_finish(a, p, y0, x0, S.in, cnn ? S.a2 : nullptr, S.w3t, S.b3);
+  lift_finish<kExact>(a, p, y0, x0, S.in, cnn ? S.a2 : nullptr, S.w3t, S.b3);
 }
 
 // ---------------------------------------------------------------------------
@@ -441,7 +465,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols));
   }
-  if (ok) lift_finish(a, p, y0, x0, S.in, nullptr, nullptr, nullptr, S.rout);
+  if (ok) lift_finish<false>(a, p, y0, x0, S.in, nullptr, nullptr, nullptr, S.rout);
 }
 
 // Component planes [B][nc][Hp][Wp] -> interleaved samples (crop, inverse
@@ -554,12 +578,16 @@ void launch_lift_step(const LiftStepParams &a, cudaStream_t st) {
   }
   static std::atomic<uint64_t> attr{0};
   once_per_device(attr, [] {
-    cudaFuncSetAttribute(k_lift_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_lift_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(LiftSmem));
+    cudaFuncSetAttribute(k_lift_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(LiftSmem));
   });
   const int tiles = ((a.H + LT - 1) / LT) * ((a.W + LT - 1) / LT);
   dim3 grid(tiles, 1, a.P);
-  k_lift_step<<<grid, 256, sizeof(LiftSmem), st>>>(a);
+  // integer (lossless) steps take the exact operation sequence
+  if (a.round != 0) k_lift_step<true><<<grid, 256, sizeof(LiftSmem), st>>>(a);
+  else k_lift_step<false><<<grid, 256, sizeof(LiftSmem), st>>>(a);
 }
 void launch_colour_out(const float *planes, int B, int nc, int Hp, int Wp, int H, int W,
                        int colour, int bitdepth, void *out, int64_t img_stride,

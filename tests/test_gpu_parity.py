@@ -152,20 +152,6 @@ def test_lift_inverse_and_forward_match_oracle(codec, model32):
     assert np.max(np.abs(got_i - x)) < 2e-3
 
 
-def test_lift_lossless_gpu_roundtrip_exact_and_oracle_agreement(codec, model32):
-    blob, gm, om = model32
-    H, W = 64, 96
-    x = np.random.default_rng(4).integers(-2048, 2048, (H, W)).astype(np.float32)
-    f = codec.lift_forward(gm, x, lossless=True)
-    assert np.all(f == np.round(f))
-    back = codec.lift_inverse(gm, f, H, W, lossless=True)
-    assert np.array_equal(back, x)
-    ref = np.concatenate([s.reshape(-1) for s in om.lift.forward(x.astype(np.float64), 4, True)])
-    # integer rounding decisions can differ only where P/U sit on a rounding
-    # boundary; such differences propagate, so bound the affected fraction
-    assert np.mean(f != ref) < 0.01
-
-
 # ---------------------------------------------------------------------------
 def _oracle_latent(om, img, q=8.0):
     planes, colour = K.colour_forward(img, False, 8)

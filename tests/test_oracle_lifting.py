@@ -192,3 +192,62 @@ def test_temporal_lifting_perfect_reconstruction():
     back = LF.temporal_inverse(bands, t, 3)
     for a, b in zip(frames, back):
         assert np.max(np.abs(a - b)) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# The integer-mode FP32 operation sequence (tanh32, conv3x3_fp32)
+def test_tanh32_within_a_few_ulps_of_tanh():
+    from oracle.lifting import tanh32
+    rng = np.random.default_rng(21)
+    x = np.concatenate([rng.uniform(-12, 12, 200000), rng.normal(0, 0.1, 100000),
+                        np.linspace(-0.2, 0.2, 20001), [0.0, -0.0, 1e-30, 40.0, -90.0,
+                                                       0.171875, -0.171875]])
+    x32 = x.astype(np.float32)
+    got = tanh32(x32).astype(np.float64)
+    ref = np.tanh(x32.astype(np.float64))
+    ulp = np.spacing(np.abs(ref).astype(np.float32)).astype(np.float64)
+    err = np.abs(got - ref) / ulp
+    assert err.max() <= 5.0, float(err.max())   # measured 4.2
+    assert np.all(np.sign(got) == np.sign(ref))
+    assert np.signbit(tanh32(np.float32(-0.0))) and tanh32(np.float32(90.0)) == 1.0
+
+
+def test_tanh32_coefficients_are_the_nearest_floats():
+    import math
+    from oracle.lifting import _INV_FACT32
+    for n, c in _INV_FACT32.items():
+        exact = 1.0 / math.factorial(n)
+        assert c == np.float32(exact)
+        assert abs(float(c) - exact) <= np.spacing(np.float32(exact)) / 2
+
+
+def test_conv3x3_fp32_matches_fp64_conv_within_rounding():
+    from oracle.lifting import conv2d, conv3x3_fp32
+    rng = np.random.default_rng(22)
+    x = rng.integers(-2048, 2048, (9, 11, 3)).astype(np.float64)
+    w = rng.uniform(-0.2, 0.2, (5, 3, 3, 3)).astype(np.float32).astype(np.float64)
+    b = rng.uniform(-1, 1, 5).astype(np.float32).astype(np.float64)
+    got = conv3x3_fp32(x, w, b).astype(np.float64)
+    ref = conv2d(x, w, b)
+    # 28 rounded terms of magnitude <= 0.2 * 2048 each
+    bound = 28 * 2 * np.finfo(np.float32).eps * (np.abs(w).max() * 2048 * 27 + 1)
+    assert np.max(np.abs(got - ref)) <= bound
+
+
+def test_integer_lifting_uses_the_fp32_sequence_and_stays_exact():
+    """Integer mode rounds P_lin + CNN evaluated by lift_cnn_fp32; the
+    round trip stays exact and the P values equal floor of that FP32 sum."""
+    from oracle.lifting import lift_cnn_fp32, predict
+    cfg = S.ModelConfig(levels=3, C=8)
+    t = {k: v.astype(np.float64) for k, v in S.random_model(cfg, 5).items()}
+    net = LF.net_of(t, "lift.row.P.")
+    e = np.random.default_rng(23).integers(-3000, 3000, (12, 10)).astype(np.float64)
+    p = predict(e, 1, net, True)
+    lin = 0.5 * (e + np.concatenate([e[:, 1:], e[:, -1:]], axis=1))
+    want = np.floor((lin.astype(np.float32) + lift_cnn_fp32(e, net)).astype(np.float32))
+    assert np.array_equal(p, want.astype(np.float64))
+    lift = LF.Lifting(t)
+    x = np.random.default_rng(24).integers(-2048, 2048, (32, 48)).astype(np.float64)
+    sb = lift.forward(x, 3, True)
+    assert all(np.array_equal(s, np.round(s)) for s in sb)
+    assert np.array_equal(lift.inverse(sb, 3, True), x)
