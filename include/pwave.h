@@ -141,25 +141,48 @@ int pw_decode_batch(pw_ctx *ctx, const pw_model *m, int count,
 
 /* ---- video GOPs (Section 3.3) -------------------------------------------- */
 
-/* Encode a group of nframes = 2^k frames: identity-motion temporal lifting
- * (the MCTF-style predict / update steps of Section 3.3 with zero motion and
- * the blob's temporal CNNs), then the lowpass band coded as an image with
- * m_low and the nframes - 1 highpass bands (batched) with m_high. frames are
- * 8-bit gray or RGB images of one size (host or device). *bs (host, free
- * with pw_free) is a "PWGP" container: 36-byte header (magic, version,
- * nframes, width, height, temporal levels, components, the two model
- * hashes) then, per band, a u32 length and a "PWBS" stream. */
+/* Encode a group of nframes = 2^k frames: motion-compensated temporal
+ * lifting (Section 3.3: the predict step warps the even frame with block
+ * motion vectors, the update step maps the highpass band back with the same
+ * vectors; the blob's temporal CNNs), then the lowpass band coded as an
+ * image with m_low and the nframes - 1 highpass bands (batched) with m_high.
+ * The vectors (16 x 16 blocks of the frames padded to 2^levels, |dy|, |dx|
+ * <= 16) come from pw_motion_search's full search on the frames' integer
+ * luma. frames are 8-bit gray or RGB images of one size (host or device).
+ * *bs (host, free with pw_free) is a "PWGP" version-2 container: 36-byte
+ * header (magic, version, nframes, width, height, temporal levels,
+ * components, the two model hashes), the vectors (nframes - 1 fields of
+ * ceil(Hp/16) x ceil(Wp/16) int8 (dy, dx) pairs, temporal level 1 first),
+ * then, per band, a u32 length and a "PWBS" stream. */
 int pw_encode_gop(pw_ctx *ctx, const pw_model *m_low, const pw_model *m_high, int nframes,
                   const pw_image *frames, const pw_codec_opts *opts, uint8_t **bs, size_t *n);
-/* Inverse of pw_encode_gop into frames[0..nframes-1]. Errors: PW_EINVAL
- * (models / sizes do not match the stream), PW_ECORRUPT. */
+/* Inverse of pw_encode_gop into frames[0..nframes-1]; also decodes version-1
+ * containers (no vectors: zero motion). Errors: PW_EINVAL (models / sizes do
+ * not match the stream), PW_ECORRUPT. */
 int pw_decode_gop(pw_ctx *ctx, const pw_model *m_low, const pw_model *m_high, const uint8_t *bs,
                   size_t n, int nframes, pw_image *frames);
 /* Temporal lifting alone on nframes host planes of H x W floats ([frame]
- * [H][W]): forward writes the bands [L_T, H_T, H_{T-1}..., H_1] (the highs
- * of a level in frame order), inverse reads them back (Section 3.3). */
+ * [H][W]) with zero motion: forward writes the bands [L_T, H_T, H_{T-1}...,
+ * H_1] (the highs of a level in frame order), inverse reads them back
+ * (Section 3.3). */
 int pw_temporal_lift(pw_ctx *ctx, const pw_model *m, int nframes, int H, int W, int forward,
                      const float *in, float *out);
+/* pw_temporal_lift with motion compensation (Section 3.3): mv (host) holds
+ * nframes - 1 fields of ceil(H/16) x ceil(W/16) (dy, dx) int8 pairs, level 1
+ * pairs first (the layout pw_motion_search writes). Level l, pair m warps
+ * frame 2m of that level by MC(f)[y, x] = f[y + dy, x + dx] for the predict
+ * step and the highpass band by f[y - dy, x - dx] for the update step,
+ * coordinates clamped. Errors: PW_EINVAL. */
+int pw_temporal_lift_mc(pw_ctx *ctx, const pw_model *m, int nframes, int H, int W, int forward,
+                        const int8_t *mv, const float *in, float *out);
+/* Block motion search of a GOP (the encoder's side of Section 3.3's
+ * motion-compensated prediction): luma (host, nframes x H x W int32,
+ * integer samples) -> mv (host, the layout of pw_temporal_lift_mc). Field
+ * (l, m) searches frame 2^l m + 2^(l-1) against frame 2^l m: per 16 x 16
+ * block the (dy, dx) in [-16, 16]^2 with the least sum of absolute
+ * differences (reference coordinates clamped), ties to the smaller
+ * |dy| + |dx|, then dy, then dx. Exact integer arithmetic. */
+int pw_motion_search(pw_ctx *ctx, int nframes, int H, int W, const int32_t *luma, int8_t *mv);
 
 /* ---- stages of the decode path (for testing and composition) ----------- */
 

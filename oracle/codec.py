@@ -39,8 +39,12 @@ steps.
 
 GOP stream ("PWGP"): 0 magic, 4 u16 version, 6 u16 nframes, 8 u32 width,
 12 u32 height, 16 u8 temporal levels, 17 u8 ncomp, 18 u16 zero, 20 u64 hash
-of the lowpass model, 28 u64 hash of the highpass model, then per temporal
-subband a u32 length and a "PWBS" stream with colour 3.
+of the lowpass model, 28 u64 hash of the highpass model; version 2 then
+holds the block motion vectors of every temporal level and pair (the order
+of lifting.gop_motion), each field ceil(Hp/16) x ceil(Wp/16) int8 pairs
+(dy, dx) in raster order over the padded frame; then per temporal subband a
+u32 length and a "PWBS" stream with colour 3. Version 1 (no vectors) is
+zero motion.
 
 Pins: decode(encode(x)) reproduces the quantised coefficients exactly and
 the image to within the quantiser's reconstruction error, and exactly in
@@ -59,7 +63,8 @@ from . import entropy as E
 from . import rans as R
 from .blob import model_hash, read_blob
 from .context import ContextModel, step_map, step_positions
-from .lifting import Lifting, subband_shapes, temporal_forward, temporal_inverse
+from .lifting import (MC_BLOCK, Lifting, gop_luma, gop_motion, subband_shapes,
+                      temporal_forward, temporal_inverse)
 
 LANES = 32
 DEFAULT_CHUNK = 16384
@@ -434,8 +439,9 @@ def decode_image(blob: bytes, bs: bytes) -> np.ndarray:
 # --------------------------------------------------------------------------
 # GOPs (Section 3.3)
 def encode_gop(blob_l: bytes, blob_h: bytes, frames: np.ndarray, *, q: float = 8.0,
-               tlevels: int = 3, chunk: int = DEFAULT_CHUNK) -> bytes:
-    """Encode nframes = 2^tlevels RGB (or gray) uint8 frames."""
+               tlevels: int = 3, chunk: int = DEFAULT_CHUNK, motion: bool = True) -> bytes:
+    """Encode nframes = 2^tlevels RGB (or gray) uint8 frames; motion=False
+    writes a version-1 (zero-motion) stream."""
     ml, mh = Model(blob_l), Model(blob_h)
     nf = frames.shape[0]
     assert nf == 1 << tlevels
@@ -443,12 +449,18 @@ def encode_gop(blob_l: bytes, blob_h: bytes, frames: np.ndarray, *, q: float = 8
     comps = [colour_forward(frames[f], False, 8)[0] for f in range(nf)]
     nc = len(comps[0])
     mult = 1 << ml.levels
+    mvs = None
+    if motion:
+        luma = [pad_plane(gop_luma(frames[f]), mult) for f in range(nf)]
+        mvs = gop_motion(luma, tlevels)
     bands_per_comp = []
     for c in range(nc):
         fr = [pad_plane(comps[f][c], mult) for f in range(nf)]
-        bands_per_comp.append(temporal_forward(fr, ml.tensors, tlevels))
-    out = [b"PWGP" + struct.pack("<HHIIBBHQQ", 1, nf, w, h, tlevels, nc, 0,
+        bands_per_comp.append(temporal_forward(fr, ml.tensors, tlevels, mvs))
+    out = [b"PWGP" + struct.pack("<HHIIBBHQQ", 2 if motion else 1, nf, w, h, tlevels, nc, 0,
                                  ml.hash, mh.hash)]
+    if motion:
+        out.append(b"".join(np.asarray(v, dtype=np.int8).tobytes() for v in mvs))
     for b in range(nf):
         m = ml if b == 0 else mh
         planes = [bands_per_comp[c][b] for c in range(nc)]
@@ -462,8 +474,21 @@ def decode_gop(blob_l: bytes, blob_h: bytes, gs: bytes) -> np.ndarray:
     ml, mh = Model(blob_l), Model(blob_h)
     if gs[:4] != b"PWGP":
         raise ValueError("not a PWGP stream")
-    _, nf, w, h, tlevels, nc, _, hl, hh = struct.unpack_from("<HHIIBBHQQ", gs, 4)
+    ver, nf, w, h, tlevels, nc, _, hl, hh = struct.unpack_from("<HHIIBBHQQ", gs, 4)
+    if ver not in (1, 2):
+        raise ValueError("unsupported PWGP version")
     pos = 4 + struct.calcsize("<HHIIBBHQQ")
+    mvs = None
+    if ver == 2:
+        mult = 1 << ml.levels
+        nby = -(-(-(-h // mult) * mult) // MC_BLOCK)
+        nbx = -(-(-(-w // mult) * mult) // MC_BLOCK)
+        mvs = []
+        for _ in range(nf - 1):
+            n = nby * nbx * 2
+            mvs.append(np.frombuffer(gs, dtype=np.int8, count=n, offset=pos)
+                       .astype(np.int64).reshape(nby, nbx, 2))
+            pos += n
     bands = []
     for b in range(nf):
         (n,) = struct.unpack_from("<I", gs, pos)
@@ -477,7 +502,7 @@ def decode_gop(blob_l: bytes, blob_h: bytes, gs: bytes) -> np.ndarray:
     per_comp = []
     for c in range(nc):
         per_comp.append(temporal_inverse([bands[b][c] for b in range(nf)],
-                                         ml.tensors, tlevels))
+                                         ml.tensors, tlevels, mvs))
     colour = 1 if nc == 3 else 0
     for f in range(nf):
         planes = [per_comp[c][f][:h, :w] for c in range(nc)]

@@ -37,9 +37,25 @@ against a direct textbook formula, and the 2-D Haar basis functions for the
 Haar special case (tests/test_oracle_lifting.py).
 
 The temporal transform (Section 3.3) is the same lifting idea along the
-frame axis with identity motion: H = f_odd - P_t(f_even) and
-L = f_even + U_t(H) with P_t(v) = v + CNN(v) and U_t(v) = v / 2 + CNN(v)
-(Haar linear parts; motion compensation is not modelled).
+frame axis: H = f_odd - P_t(MC(f_even)) and L = f_even + U_t(IMC(H)) with
+P_t(v) = v + CNN(v) and U_t(v) = v / 2 + CNN(v) (Haar linear parts). The
+predict step compensates motion: MC warps the even frame towards the odd
+one with block motion vectors; the update step re-uses the same vectors to
+map the highpass band back onto the even frame (inverse motion
+compensation), so it filters along the motion trajectory. The paper defers
+the motion model to its reference; the reading here:
+* integer-pel block motion, 16 x 16 blocks on the padded frame grid, one
+  vector (dy, dx) per block of the odd frame, |dy|, |dx| <= 16;
+* MC(f)[y, x] = f[y + dy, x + dx] and IMC(h)[y, x] = h[y - dy, x - dx],
+  (dy, dx) the vector of the block that contains (y, x), coordinates
+  clamped to the frame; zero vectors give the identity transform;
+* the vectors of temporal level l, pair m come from a full search between
+  the original frames that the pair's two lowpass frames stand for (frames
+  2^l m and 2^l m + 2^(l-1)) on an integer luma (the RCT luma
+  floor((R + 2G + B) / 4) of the 8-bit samples, or the gray sample):
+  minimum sum of absolute differences, ties to the smaller |dy| + |dx|,
+  then the smaller dy, then the smaller dx.
+The lifting structure makes the transform invertible for any vectors.
 """
 from __future__ import annotations
 
@@ -282,21 +298,96 @@ def _tnet(tensors, op):
     return net_of(tensors, f"tlift.{op}.")
 
 
-def temporal_forward(frames: list, tensors: dict, tlevels: int):
-    """Temporal lifting over a GOP of 2^tlevels frames (identity motion).
+MC_BLOCK = 16
+MC_RANGE = 16
 
-    Returns the temporal subbands in order [L_T, H_T, H_{T-1}..., H_1], the
-    H bands of each level in frame order.
+
+def mc_warp(f: np.ndarray, mv: np.ndarray, sign: int, B: int = MC_BLOCK) -> np.ndarray:
+    """out[y, x] = f[y + sign dy, x + sign dx], (dy, dx) = mv[y // B, x // B],
+    coordinates clamped to the frame (sign +1: MC, -1: inverse MC)."""
+    H, W = f.shape
+    yy = np.arange(H)[:, None]
+    xx = np.arange(W)[None, :]
+    dy = mv[yy // B, xx // B, 0]
+    dx = mv[yy // B, xx // B, 1]
+    return f[np.clip(yy + sign * dy, 0, H - 1), np.clip(xx + sign * dx, 0, W - 1)]
+
+
+def motion_search(cur: np.ndarray, ref: np.ndarray, B: int = MC_BLOCK,
+                  R: int = MC_RANGE) -> np.ndarray:
+    """Block motion vectors [ceil(H/B), ceil(W/B), 2] (int) of integer frame
+    `cur` against `ref`: per block the (dy, dx) in [-R, R]^2 minimising
+    sum |cur[y, x] - ref[clamp(y + dy), clamp(x + dx)]| over the block's
+    pixels; ties to the smaller |dy| + |dx|, then dy, then dx."""
+    H, W = cur.shape
+    nby, nbx = -(-H // B), -(-W // B)
+    cur = cur.astype(np.int64)
+    ref = ref.astype(np.int64)
+    yy = np.arange(H)[:, None]
+    xx = np.arange(W)[None, :]
+    best = np.full((nby, nbx, 4), np.iinfo(np.int64).max, dtype=np.int64)
+    out = np.zeros((nby, nbx, 2), dtype=np.int64)
+    for dy in range(-R, R + 1):
+        for dx in range(-R, R + 1):
+            d = np.zeros((nby * B, nbx * B), dtype=np.int64)
+            d[:H, :W] = np.abs(cur - ref[np.clip(yy + dy, 0, H - 1), np.clip(xx + dx, 0, W - 1)])
+            sad = d.reshape(nby, B, nbx, B).sum(axis=(1, 3))
+            key = np.stack([sad, np.full_like(sad, abs(dy) + abs(dx)),
+                            np.full_like(sad, dy), np.full_like(sad, dx)], axis=2)
+            better = np.zeros((nby, nbx), dtype=bool)
+            undecided = np.ones((nby, nbx), dtype=bool)
+            for k in range(4):
+                lt = key[:, :, k] < best[:, :, k]
+                gt = key[:, :, k] > best[:, :, k]
+                better |= undecided & lt
+                undecided &= ~(lt | gt)
+            best[better] = key[better]
+            out[better] = (dy, dx)
+    return out
+
+
+def gop_luma(img: np.ndarray) -> np.ndarray:
+    """Integer luma of an 8-bit frame for motion search: the gray sample, or
+    floor((R + 2G + B) / 4)."""
+    x = img.astype(np.int64)
+    if x.ndim == 2:
+        return x
+    return (x[:, :, 0] + 2 * x[:, :, 1] + x[:, :, 2]) >> 2
+
+
+def gop_motion(luma: list, tlevels: int) -> list:
+    """Vectors of every temporal level and pair, in stream order: for level
+    l = 1..T and pair m, motion_search(luma[2^l m + 2^(l-1)], luma[2^l m])."""
+    n = len(luma)
+    out = []
+    for lv in range(1, tlevels + 1):
+        for m in range(n >> lv):
+            a = (1 << lv) * m
+            out.append(motion_search(luma[a + (1 << (lv - 1))], luma[a]))
+    return out
+
+
+def temporal_forward(frames: list, tensors: dict, tlevels: int, mvs: list | None = None):
+    """Temporal lifting over a GOP of 2^tlevels frames.
+
+    mvs: the block vectors of every level and pair in the order of
+    gop_motion (None: zero motion). Returns the temporal subbands in order
+    [L_T, H_T, H_{T-1}..., H_1], the H bands of each level in frame order.
     """
     nP, nU = _tnet(tensors, "P"), _tnet(tensors, "U")
     cur = list(frames)
     highs = []
+    k = 0
     for _ in range(tlevels):
         lows, hs = [], []
         for m in range(len(cur) // 2):
             fe, fo = cur[2 * m], cur[2 * m + 1]
-            h = fo - (fe + lift_cnn(fe, nP))
-            l = fe + (0.5 * h + lift_cnn(h, nU))
+            mv = mvs[k] if mvs is not None else None
+            k += 1
+            w = fe if mv is None else mc_warp(fe, mv, +1)
+            h = fo - (w + lift_cnn(w, nP))
+            v = h if mv is None else mc_warp(h, mv, -1)
+            l = fe + (0.5 * v + lift_cnn(v, nU))
             lows.append(l)
             hs.append(h)
         highs.append(hs)
@@ -307,18 +398,25 @@ def temporal_forward(frames: list, tensors: dict, tlevels: int):
     return out
 
 
-def temporal_inverse(bands: list, tensors: dict, tlevels: int):
-    """Inverse of temporal_forward."""
+def temporal_inverse(bands: list, tensors: dict, tlevels: int, mvs: list | None = None):
+    """Inverse of temporal_forward (same vectors)."""
     nP, nU = _tnet(tensors, "P"), _tnet(tensors, "U")
+    nf = 1 << tlevels
+    starts = [0]
+    for lv in range(1, tlevels + 1):
+        starts.append(starts[-1] + (nf >> lv))      # first field of level lv + 1
     cur = [bands[0]]
     pos = 1
-    for _ in range(tlevels):
+    for lv in range(tlevels, 0, -1):
         hs = bands[pos:pos + len(cur)]
         pos += len(cur)
         nxt = []
-        for l, h in zip(cur, hs):
-            fe = l - (0.5 * h + lift_cnn(h, nU))
-            fo = h + (fe + lift_cnn(fe, nP))
+        for m, (l, h) in enumerate(zip(cur, hs)):
+            mv = mvs[starts[lv - 1] + m] if mvs is not None else None
+            v = h if mv is None else mc_warp(h, mv, -1)
+            fe = l - (0.5 * v + lift_cnn(v, nU))
+            w = fe if mv is None else mc_warp(fe, mv, +1)
+            fo = h + (w + lift_cnn(w, nP))
             nxt += [fe, fo]
         cur = nxt
     return cur

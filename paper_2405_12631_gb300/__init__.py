@@ -107,6 +107,8 @@ _sig = {
                                 C.POINTER(C.c_size_t)]),
     "pw_decode_gop": (C.c_int, [_P, _P, _P, _P, C.c_size_t, C.c_int, C.POINTER(pw_image)]),
     "pw_temporal_lift": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P]),
+    "pw_temporal_lift_mc": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
+    "pw_motion_search": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P]),
     "pw_decode_footprint": (C.c_int, [_P, _P, _P, C.c_size_t, C.c_int,
                                       C.POINTER(C.c_uint64)]),
     "pw_server_create": (C.c_int, [_P, _P, C.c_size_t, C.c_int, C.c_int, C.POINTER(_P)]),
@@ -381,6 +383,27 @@ class Codec:
         check(pw_temporal_lift(self.ctx, model.handle, nf, H, W, int(forward), _ptr(frames),
                                _ptr(out)))
         return out
+
+    def temporal_lift_mc(self, model: Model, frames: np.ndarray, mv: np.ndarray,
+                         forward: bool = True) -> np.ndarray:
+        """pw_temporal_lift_mc: frames [nf, H, W] float, mv [nf - 1, nby,
+        nbx, 2] int8 (the layout motion_search returns)."""
+        frames = np.ascontiguousarray(frames, dtype=np.float32)
+        mv = np.ascontiguousarray(mv, dtype=np.int8)
+        nf, H, W = frames.shape
+        out = np.zeros_like(frames)
+        check(pw_temporal_lift_mc(self.ctx, model.handle, nf, H, W, int(forward), _ptr(mv),
+                                  _ptr(frames), _ptr(out)))
+        return out
+
+    def motion_search(self, luma: np.ndarray) -> np.ndarray:
+        """pw_motion_search on integer luma frames [nf, H, W] -> vectors
+        [nf - 1, ceil(H/16), ceil(W/16), 2] (int8 dy, dx)."""
+        luma = np.ascontiguousarray(luma, dtype=np.int32)
+        nf, H, W = luma.shape
+        mv = np.zeros((nf - 1, -(-H // 16), -(-W // 16), 2), dtype=np.int8)
+        check(pw_motion_search(self.ctx, nf, H, W, _ptr(luma), _ptr(mv)))
+        return mv
 
     # ---- stages -----------------------------------------------------------
     def cdf_bank_device(self, dev_ptr: int):

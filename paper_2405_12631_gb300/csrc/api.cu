@@ -827,6 +827,13 @@ struct GopHeader {
 #pragma pack(pop)
 static_assert(sizeof(GopHeader) == 36, "GOP header is 36 bytes");
 
+// Bytes of the block motion vectors of a GOP (version 2): nframes - 1
+// fields of ceil(Hp / 16) x ceil(Wp / 16) (dy, dx) int8 pairs.
+static size_t gop_mv_bytes(int nframes, int Hp, int Wp) {
+  const size_t nby = (Hp + kMcBlock - 1) / kMcBlock, nbx = (Wp + kMcBlock - 1) / kMcBlock;
+  return (size_t)(nframes - 1) * nby * nbx * 2;
+}
+
 int pw_encode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, int nframes,
                   const pw_image *frames, const pw_codec_opts *o, uint8_t **bs, size_t *n) {
   if (!c || !ml || !mh || !frames || !bs || !n || nframes < 2 || (nframes & (nframes - 1))) {
@@ -846,11 +853,14 @@ int pw_encode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, int nframes
   const int Hp = (H + mult - 1) / mult * mult, Wp = (W + mult - 1) / mult * mult;
   const int64_t F = (int64_t)nc * Hp * Wp;
   const int64_t row = (int64_t)W * nc, img = row * H;
-  DevBuf dimg, dframes, dbands, dt0, dt1;
+  const size_t mv_bytes = gop_mv_bytes(nframes, Hp, Wp);
+  DevBuf dimg, dframes, dbands, dt0, dt1, dluma, dmv, dwarp;
   int s;
   if ((s = dimg.ensure((size_t)img * nframes)) || (s = dframes.ensure((size_t)F * nframes * 4)) ||
       (s = dbands.ensure((size_t)F * nframes * 4)) || (s = dt0.ensure((size_t)F * nframes * 2)) ||
-      (s = dt1.ensure((size_t)F * nframes * 2)))
+      (s = dt1.ensure((size_t)F * nframes * 2)) ||
+      (s = dluma.ensure((size_t)nframes * Hp * Wp * 4)) || (s = dmv.ensure(mv_bytes)) ||
+      (s = dwarp.ensure((size_t)F * (nframes / 2) * 4)))
     return s;
   cudaStream_t st = c->stream;
   for (int f = 0; f < nframes; ++f) {
@@ -860,9 +870,16 @@ int pw_encode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, int nframes
                                                       : cudaMemcpyHostToDevice, st));
   }
   launch_colour_in(dimg.p, img, row, nframes, nc, H, W, Hp, Wp, 0, 8, (float *)dframes.p, st);
-  bump(c);
+  // motion of every temporal level and pair on the frames' integer luma
+  launch_gop_luma((const uint8_t *)dimg.p, img, row, nframes, nc, H, W, Hp, Wp,
+                  (int32_t *)dluma.p, st);
+  launch_motion_search((const int32_t *)dluma.p, nframes, Hp, Wp, (int8_t *)dmv.p, st);
+  bump(c, 3);
+  std::vector<int8_t> hmv(mv_bytes);
+  PW_CUDA_TRY(cudaMemcpyAsync(hmv.data(), dmv.p, mv_bytes, cudaMemcpyDeviceToHost, st));
   if ((s = temporal_planes(c, L, nframes, nc, Hp, Wp, (float *)dframes.p, (float *)dbands.p,
-                           (float *)dt0.p, (float *)dt1.p, true)))
+                           (float *)dt0.p, (float *)dt1.p, true, (const int8_t *)dmv.p,
+                           (float *)dwarp.p)))
     return s;
   std::vector<uint8_t *> sb(nframes, nullptr);
   std::vector<size_t> sn(nframes, 0);
@@ -875,17 +892,19 @@ int pw_encode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, int nframes
   }
   GopHeader gh{};
   std::memcpy(gh.magic, "PWGP", 4);
-  gh.version = 1; gh.nframes = (uint16_t)nframes; gh.width = W; gh.height = H;
+  gh.version = 2; gh.nframes = (uint16_t)nframes; gh.width = W; gh.height = H;
   int T = 0;
   while ((1 << T) < nframes) ++T;
   gh.tlevels = (uint8_t)T; gh.ncomp = (uint8_t)nc; gh.hash_low = L.hash; gh.hash_high = Hm.hash;
-  size_t total = sizeof(gh);
+  size_t total = sizeof(gh) + mv_bytes;
   for (int f = 0; f < nframes; ++f) total += 4 + sn[f];
   uint8_t *out = static_cast<uint8_t *>(std::malloc(total));
   if (!out) { for (auto q : sb) std::free(q); return PW_ENOMEM; }
   size_t pos = 0;
   std::memcpy(out, &gh, sizeof(gh));
   pos += sizeof(gh);
+  std::memcpy(out + pos, hmv.data(), mv_bytes);   // synchronised by the encodes above
+  pos += mv_bytes;
   for (int f = 0; f < nframes; ++f) {
     const uint32_t len = (uint32_t)sn[f];
     std::memcpy(out + pos, &len, 4);
@@ -904,7 +923,9 @@ int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8
   Model &L = const_cast<pw_model *>(ml)->m, &Hm = const_cast<pw_model *>(mh)->m;
   GopHeader gh;
   std::memcpy(&gh, bs, sizeof(gh));
-  if (std::memcmp(gh.magic, "PWGP", 4) || gh.version != 1) { set_last_error("not a PWGP stream"); return PW_ECORRUPT; }
+  if (std::memcmp(gh.magic, "PWGP", 4) || (gh.version != 1 && gh.version != 2)) {
+    set_last_error("not a PWGP stream"); return PW_ECORRUPT;
+  }
   if (gh.hash_low != L.hash || gh.hash_high != Hm.hash) { set_last_error("GOP made with other models"); return PW_EINVAL; }
   if ((int)gh.nframes != nframes || nframes < 2 || (1 << gh.tlevels) != nframes ||
       (gh.ncomp != 1 && gh.ncomp != 3)) {
@@ -919,6 +940,12 @@ int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8
   std::vector<const uint8_t *> bp(nframes);
   std::vector<size_t> bn(nframes);
   size_t pos = sizeof(gh);
+  const int mult0 = 1 << L.levels;
+  const size_t mv_bytes = gh.version == 2 ? gop_mv_bytes(nframes, (H + mult0 - 1) / mult0 * mult0,
+                                                         (W + mult0 - 1) / mult0 * mult0) : 0;
+  const uint8_t *mv_src = bs + pos;
+  if (pos + mv_bytes > n) { set_last_error("truncated GOP"); return PW_ECORRUPT; }
+  pos += mv_bytes;
   for (int f = 0; f < nframes; ++f) {
     uint32_t len;
     if (pos + 4 > n) { set_last_error("truncated GOP"); return PW_ECORRUPT; }
@@ -932,14 +959,19 @@ int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8
   const int mult = 1 << L.levels;
   const int Hp = (H + mult - 1) / mult * mult, Wp = (W + mult - 1) / mult * mult;
   const int64_t F = (int64_t)nc * Hp * Wp;
-  DevBuf dbands, dframes, dt0, dt1, dimg;
+  DevBuf dbands, dframes, dt0, dt1, dimg, dmv, dwarp;
   const int64_t row = (int64_t)W * nc, img = row * H;
   int s;
   if ((s = dbands.ensure((size_t)F * nframes * 4)) || (s = dframes.ensure((size_t)F * nframes * 4)) ||
       (s = dt0.ensure((size_t)F * nframes * 2)) || (s = dt1.ensure((size_t)F * nframes * 2)) ||
-      (s = dimg.ensure((size_t)img * nframes)))
+      (s = dimg.ensure((size_t)img * nframes)) ||
+      (mv_bytes && ((s = dmv.ensure(mv_bytes)) ||
+                    (s = dwarp.ensure((size_t)F * (nframes / 2) * 4)))))
     return s;
   cudaStream_t st = c->stream;
+  if (mv_bytes) {
+    PW_CUDA_TRY(cudaMemcpyAsync(dmv.p, mv_src, mv_bytes, cudaMemcpyHostToDevice, st));
+  }
   float *planes;
   Geometry g;
   if ((s = decode_to_planes(c, L, 1, bp.data(), bn.data(), &planes, &g))) return s;
@@ -950,7 +982,8 @@ int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8
   PW_CUDA_TRY(cudaMemcpyAsync((float *)dbands.p + F, planes, (size_t)F * (nframes - 1) * 4,
                               cudaMemcpyDeviceToDevice, st));
   if ((s = temporal_planes(c, L, nframes, nc, Hp, Wp, (float *)dbands.p, (float *)dframes.p,
-                           (float *)dt0.p, (float *)dt1.p, false)))
+                           (float *)dt0.p, (float *)dt1.p, false,
+                           mv_bytes ? (const int8_t *)dmv.p : nullptr, (float *)dwarp.p)))
     return s;
   launch_colour_out((float *)dframes.p, nframes, nc, Hp, Wp, H, W, nc == 3 ? 1 : 0, 8, dimg.p, img,
                     row, st);
@@ -979,6 +1012,44 @@ int pw_temporal_lift(pw_ctx *c, const pw_model *mm, int nframes, int H, int W, i
                            (float *)dt1.p, forward != 0)))
     return s;
   PW_CUDA_TRY(cudaMemcpyAsync(out, dout.p, (size_t)F * nframes * 4, cudaMemcpyDeviceToHost, c->stream));
+  return finish(c);
+}
+
+int pw_temporal_lift_mc(pw_ctx *c, const pw_model *mm, int nframes, int H, int W, int forward,
+                        const int8_t *mv, const float *in, float *out) {
+  if (!c || !mm || !in || !out || !mv || H < 1 || W < 1 || nframes < 2 ||
+      (nframes & (nframes - 1)))
+    return PW_EINVAL;
+  Model &m = const_cast<pw_model *>(mm)->m;
+  const int64_t F = (int64_t)H * W;
+  const size_t mv_bytes = gop_mv_bytes(nframes, H, W);
+  DevBuf din, dout, dt0, dt1, dmv, dwarp;
+  int s;
+  if ((s = din.ensure((size_t)F * nframes * 4)) || (s = dout.ensure((size_t)F * nframes * 4)) ||
+      (s = dt0.ensure((size_t)F * nframes * 2)) || (s = dt1.ensure((size_t)F * nframes * 2)) ||
+      (s = dmv.ensure(mv_bytes)) || (s = dwarp.ensure((size_t)F * (nframes / 2) * 4)))
+    return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(din.p, in, (size_t)F * nframes * 4, cudaMemcpyHostToDevice, c->stream));
+  PW_CUDA_TRY(cudaMemcpyAsync(dmv.p, mv, mv_bytes, cudaMemcpyHostToDevice, c->stream));
+  if ((s = temporal_planes(c, m, nframes, 1, H, W, (float *)din.p, (float *)dout.p, (float *)dt0.p,
+                           (float *)dt1.p, forward != 0, (const int8_t *)dmv.p, (float *)dwarp.p)))
+    return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(out, dout.p, (size_t)F * nframes * 4, cudaMemcpyDeviceToHost, c->stream));
+  return finish(c);
+}
+
+int pw_motion_search(pw_ctx *c, int nframes, int H, int W, const int32_t *luma, int8_t *mv) {
+  if (!c || !luma || !mv || H < 1 || W < 1 || nframes < 2 || (nframes & (nframes - 1)))
+    return PW_EINVAL;
+  const size_t mv_bytes = gop_mv_bytes(nframes, H, W);
+  DevBuf dl, dmv;
+  int s;
+  if ((s = dl.ensure((size_t)nframes * H * W * 4)) || (s = dmv.ensure(mv_bytes))) return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(dl.p, luma, (size_t)nframes * H * W * 4, cudaMemcpyHostToDevice,
+                              c->stream));
+  launch_motion_search((const int32_t *)dl.p, nframes, H, W, (int8_t *)dmv.p, c->stream);
+  bump(c);
+  PW_CUDA_TRY(cudaMemcpyAsync(mv, dmv.p, mv_bytes, cudaMemcpyDeviceToHost, c->stream));
   return finish(c);
 }
 

@@ -229,7 +229,7 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
   auto conv = [&](int ks, const ConvParams &cp, int epi) {
     const double fl = 2.0 * pix * ks * ks * cp.cin * cp.cout_total;
     const double by = pix * 4.0 * (cp.cin + cp.cout_total + (cp.res ? cp.cout_total : 0));
-    ProfScope ps(ctx, ks == 3 ? KC_CONV3 : KC_CONV1, fl, by);
+    ProfScope ps(ctx, ks == 3 ? (epi == EPI_HEAD ? KC_HEAD3 : KC_CONV3) : KC_CONV1, fl, by);
     launch_conv_simt(ks, cp, epi, st);
   };
   ConvParams a{};
@@ -404,12 +404,14 @@ int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
 // written as [L_T, H_T, H_{T-1} ..., H_1] (highs of a level in frame order).
 // Inverse runs the same steps backwards. tmp holds nf / 2 frames.
 int temporal_planes(pw_ctx *ctx, Model &m, int nf, int nc, int Hp, int Wp, const float *in,
-                    float *out, float *tmp0, float *tmp1, bool forward) {
+                    float *out, float *tmp0, float *tmp1, bool forward, const int8_t *mv,
+                    float *twarp) {
   const int64_t HW = (int64_t)Hp * Wp;
   const int64_t F = (int64_t)nc * HW;  // one frame
   int T = 0;
   while ((1 << T) < nf) ++T;
   if ((1 << T) != nf || nf < 2) { set_last_error("GOP size must be a power of two >= 2"); return PW_EINVAL; }
+  if (mv && !twarp) { set_last_error("motion-compensated lifting needs scratch"); return PW_EINVAL; }
   auto step = [&](const float *src, int64_t ssrc, const float *oth, int64_t soth, float *dst,
                   int64_t sdst, int P, int lin, int sign, const LiftNetDev &net) {
     LiftStepParams a{};
@@ -420,17 +422,39 @@ int temporal_planes(pw_ctx *ctx, Model &m, int nf, int nc, int Hp, int Wp, const
     a.copy = acc(nullptr, 0, 0);
     lift_step(ctx, a);
   };
+  // MC (sign +1) or inverse MC (-1) of P planes with the vectors of fields
+  // field0 .. field0 + P - 1 into the scratch planes (stride F)
+  auto warp = [&](const float *src, int64_t ssrc, int P, int field0, int sign) {
+    launch_mc_warp(acc(const_cast<float *>(src), ssrc, Wp), acc(twarp, F, Wp), P, Hp, Wp, mv,
+                   field0, sign, ctx->stream);
+    bump(ctx);
+    return twarp;
+  };
+  // first field of level lv (fields of level 1 first, nf / 2 of them)
+  auto field0_of = [&](int lv) {
+    int f = 0;
+    for (int l = 1; l < lv; ++l) f += nf >> l;
+    return f;
+  };
   if (forward) {
     const float *cur = in;
     float *bufs[2] = {tmp0, tmp1};
     for (int lv = 1; lv <= T; ++lv) {
       const int n = nf >> (lv - 1), h = n / 2;
+      const int f0 = field0_of(lv);
       float *L = (lv == T) ? out : bufs[lv & 1];
       for (int c = 0; c < nc; ++c) {
         const float *fe = cur + c * HW, *fo = cur + F + c * HW;
         float *Hb = out + (int64_t)h * F + c * HW;
-        step(fe, 2 * F, fo, 2 * F, Hb, F, h, LIN_ID, -1, m.tlift[0]);
-        step(Hb, F, fe, 2 * F, L + c * HW, F, h, LIN_HALF, +1, m.tlift[1]);
+        if (mv) {
+          // H = fo - P(MC(fe)); L = fe + U(IMC(H))
+          step(warp(fe, 2 * F, h, f0, +1), F, fo, 2 * F, Hb, F, h, LIN_ID, -1,
+               m.tlift[0]);
+          step(warp(Hb, F, h, f0, -1), F, fe, 2 * F, L + c * HW, F, h, LIN_HALF, +1, m.tlift[1]);
+        } else {
+          step(fe, 2 * F, fo, 2 * F, Hb, F, h, LIN_ID, -1, m.tlift[0]);
+          step(Hb, F, fe, 2 * F, L + c * HW, F, h, LIN_HALF, +1, m.tlift[1]);
+        }
       }
       ctx->launches += 2 * nc;
       cur = L;
@@ -441,12 +465,19 @@ int temporal_planes(pw_ctx *ctx, Model &m, int nf, int nc, int Hp, int Wp, const
     float *bufs[2] = {tmp0, tmp1};
     for (int lv = T; lv >= 1; --lv) {
       const int n = nf >> (lv - 1), h = n / 2;
+      const int f0 = field0_of(lv);
       float *dst = (lv == 1) ? out : bufs[lv & 1];
       for (int c = 0; c < nc; ++c) {
         const float *Hb = in + (int64_t)h * F + c * HW, *L = cur + c * HW;
         float *fe = dst + c * HW, *fo = dst + F + c * HW;
-        step(Hb, F, L, F, fe, 2 * F, h, LIN_HALF, -1, m.tlift[1]);
-        step(fe, 2 * F, Hb, F, fo, 2 * F, h, LIN_ID, +1, m.tlift[0]);
+        if (mv) {
+          // fe = L - U(IMC(H)); fo = H + P(MC(fe))
+          step(warp(Hb, F, h, f0, -1), F, L, F, fe, 2 * F, h, LIN_HALF, -1, m.tlift[1]);
+          step(warp(fe, 2 * F, h, f0, +1), F, Hb, F, fo, 2 * F, h, LIN_ID, +1, m.tlift[0]);
+        } else {
+          step(Hb, F, L, F, fe, 2 * F, h, LIN_HALF, -1, m.tlift[1]);
+          step(fe, 2 * F, Hb, F, fo, 2 * F, h, LIN_ID, +1, m.tlift[0]);
+        }
       }
       ctx->launches += 2 * nc;
       cur = dst;

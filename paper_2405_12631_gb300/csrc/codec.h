@@ -134,8 +134,23 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         float *dst_planes);
 int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         const float *src_planes);
+// Temporal lifting of a GOP (Section 3.3). mv: device block motion vectors
+// of every level and pair (the order of the motion search: level 1 pairs
+// first), or null for zero motion; twarp: (nf / 2) frames of scratch for the
+// motion-compensated operands (unused without vectors).
 int temporal_planes(pw_ctx *ctx, Model &m, int nf, int nc, int Hp, int Wp, const float *in,
-                    float *out, float *tmp0, float *tmp1, bool forward);
+                    float *out, float *tmp0, float *tmp1, bool forward,
+                    const int8_t *mv = nullptr, float *twarp = nullptr);
+
+// Motion model of the temporal lifting (motion.cu): integer-pel vectors of
+// kMcBlock x kMcBlock blocks, |dy|, |dx| <= kMcRange.
+constexpr int kMcBlock = 16, kMcRange = 16;
+void launch_gop_luma(const uint8_t *img, int64_t img_stride, int64_t row_stride, int nf, int nc,
+                     int H, int W, int Hp, int Wp, int32_t *luma, cudaStream_t st);
+void launch_motion_search(const int32_t *luma, int nf, int Hp, int Wp, int8_t *mv,
+                          cudaStream_t st);
+void launch_mc_warp(const PlaneAcc &src, const PlaneAcc &dst, int P, int H, int W,
+                    const int8_t *mv, int field0, int sign, cudaStream_t st);
 // Batch decode of B streams of one geometry (api.cu) and release of a
 // context's cached workspaces; used by the decode server.
 int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,

@@ -1919,7 +1919,7 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     a.res_compact_n = (int)nk;
     a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
     a.mu_out = mu; a.sg_out = sgp;
-    ProfScope ps(ctx, KC_CONV3, 2.0 * kpix * 9 * C * C, pix * C + kpix * 2.0 * C);
+    ProfScope ps(ctx, KC_HEAD3, 2.0 * kpix * 9 * C * C, pix * C + kpix * 2.0 * C);
     return conv_tc(ctx, c2, t.U8, G16, 0, P, h, w, a, t.err);               // head
   }
   a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G; a.out_ps = ups;
@@ -1927,7 +1927,7 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   a = TcConvArgs{}; a.epi = hcm ? TE_HEADC : TE_HEAD; a.res = t.Z; a.res_G = G;
   a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
   a.mu_out = mu; a.sg_out = sgp;
-  ProfScope ps(ctx, KC_CONV3, 2.0 * kpix * 9 * C * C, pix * 2.0 * C + kpix * 4.0 * C);
+  ProfScope ps(ctx, KC_HEAD3, 2.0 * kpix * 9 * C * C, pix * 2.0 * C + kpix * 4.0 * C);
   return conv_tc(ctx, c2, t.U, G, 0, P, h, w, a, t.err);          // head
 }
 

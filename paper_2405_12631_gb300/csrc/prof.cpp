@@ -6,7 +6,8 @@ namespace pw {
 const char *kclass_name(int c) {
   static const char *n[KC_COUNT] = {"ctx_lstm_gates_conv3x3", "ctx_conv3x3", "ctx_conv1x1",
                                     "ctx_small", "rans_decode", "rans_encode", "cdf_bank",
-                                    "lift_step", "colour", "parse", "quant"};
+                                    "lift_step", "colour", "parse", "quant",
+                                    "ctx_head_conv3x3"};
   return (c >= 0 && c < KC_COUNT) ? n[c] : "?";
 }
 

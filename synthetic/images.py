@@ -121,17 +121,22 @@ def lossless_blobs(h: int = 2160, w: int = 3840, seed: int = 5,
     """
     rng = np.random.default_rng(seed)
     top = (1 << bitdepth) - 1
-    img = np.full((h, w, 3), top / 4.0)
     yy = np.arange(h, dtype=np.float64)[:, None]
     xx = np.arange(w, dtype=np.float64)[None, :]
-    for _ in range(int(rng.integers(20, 61))):
+    nb = int(rng.integers(20, 61))
+    gys, gxs, amps = [], [], []
+    for _ in range(nb):
         cy = rng.uniform(0, h); cx = rng.uniform(0, w)
         s = rng.uniform(20.0, 400.0)
-        amp = rng.uniform(-0.25, 0.5, 3) * top
-        gy = np.exp(-0.5 * ((yy - cy) / s) ** 2)
-        gx = np.exp(-0.5 * ((xx - cx) / s) ** 2)
-        g = gy * gx
-        img += g[:, :, None] * amp[None, None, :]
+        amps.append(rng.uniform(-0.25, 0.5, 3) * top)
+        gys.append(np.exp(-0.5 * ((yy[:, 0] - cy) / s) ** 2))
+        gxs.append(np.exp(-0.5 * ((xx[0] - cx) / s) ** 2))
+    gy = np.stack(gys, axis=1)          # [h, nb]
+    gx = np.stack(gxs, axis=0)          # [nb, w]
+    amp = np.stack(amps, axis=0)        # [nb, 3]
+    img = np.empty((h, w, 3))
+    for c in range(3):                  # separable blobs: one matrix product
+        img[:, :, c] = top / 4.0 + (gy * amp[None, :, c]) @ gx
     img += rng.normal(0.0, 15.0, (h, w, 3))
     return np.clip(np.round(img), 0, top).astype(np.uint16)
 

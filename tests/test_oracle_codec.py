@@ -97,3 +97,15 @@ def test_index_injection_with_own_params_reproduces_stream():
     for qa, qb in zip(qenc, dec):
         for a, b in zip(qa, qb):
             assert np.array_equal(a, b)
+
+
+def test_motion_compensation_lowers_the_rate_of_a_panning_gop():
+    """Section 3.3: motion-compensated prediction leaves less to code when
+    the content moves (a panning canvas with sprites)."""
+    bl, bh = _blob(0, seed=2), _blob(0, seed=3)
+    frames = S.video_gop(48, 64, 8, seed=5)
+    mc = K.encode_gop(bl, bh, frames, q=8.0, motion=True)
+    zero = K.encode_gop(bl, bh, frames, q=8.0, motion=False)
+    assert len(mc) < 0.95 * len(zero), (len(mc), len(zero))
+    out = K.decode_gop(bl, bh, mc)
+    assert out.shape == frames.shape

@@ -251,3 +251,93 @@ def test_integer_lifting_uses_the_fp32_sequence_and_stays_exact():
     sb = lift.forward(x, 3, True)
     assert all(np.array_equal(s, np.round(s)) for s in sb)
     assert np.array_equal(lift.inverse(sb, 3, True), x)
+
+
+# ---------------------------------------------------------------------------
+# Motion-compensated temporal lifting (Section 3.3)
+def _tlift_tensors(seed=3, zero=False):
+    cfg = S.ModelConfig(levels=4, C=8)
+    t = {k: v.astype(np.float64) for k, v in S.random_model(cfg, seed).items()}
+    if zero:
+        for k in t:
+            if k.startswith("tlift."):
+                t[k] = np.zeros_like(t[k])
+    return t
+
+
+def test_zero_motion_is_the_identity_motion_transform():
+    t = _tlift_tensors()
+    rng = np.random.default_rng(30)
+    frames = [rng.uniform(-128, 127, (32, 48)) for _ in range(8)]
+    zero = [np.zeros((2, 3, 2), dtype=np.int64) for _ in range(7)]
+    a = LF.temporal_forward(frames, t, 3)
+    b = LF.temporal_forward(frames, t, 3, zero)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert all(np.array_equal(x, y) for x, y in
+               zip(LF.temporal_inverse(a, t, 3), LF.temporal_inverse(b, t, 3, zero)))
+
+
+def test_mc_lifting_reconstructs_perfectly_for_any_vectors():
+    t = _tlift_tensors(seed=4)
+    rng = np.random.default_rng(31)
+    frames = [rng.uniform(-128, 127, (48, 64)) for _ in range(8)]
+    mvs = [rng.integers(-16, 17, (3, 4, 2)) for _ in range(7)]
+    bands = LF.temporal_forward(frames, t, 3, mvs)
+    back = LF.temporal_inverse(bands, t, 3, mvs)
+    assert max(np.max(np.abs(a - b)) for a, b in zip(back, frames)) < 1e-9
+
+
+def test_mc_warp_reads_the_block_vector_with_clamping():
+    f = np.arange(32 * 32, dtype=np.float64).reshape(32, 32)
+    mv = np.zeros((2, 2, 2), dtype=np.int64)
+    mv[0, 1] = (2, -3)           # block rows 0..15, columns 16..31
+    mv[1, 0] = (-20, 5)
+    w = LF.mc_warp(f, mv, +1)
+    assert w[4, 20] == f[6, 17] and w[4, 4] == f[4, 4]
+    assert w[17, 3] == f[0, 8]                         # row 17 - 20 clamped to 0
+    v = LF.mc_warp(f, mv, -1)
+    assert v[4, 20] == f[2, 23] and v[17, 3] == f[31, 0]
+
+
+def test_motion_search_matches_brute_force_definition():
+    rng = np.random.default_rng(32)
+    ref = rng.integers(0, 256, (32, 40))
+    cur = np.roll(ref, (1, -2), axis=(0, 1)) + rng.integers(-3, 4, (32, 40))
+    R = 4
+    got = LF.motion_search(cur, ref, 16, R)
+    H, W = cur.shape
+    for by in range(2):
+        for bx in range(3):
+            best = None
+            for dy in range(-R, R + 1):
+                for dx in range(-R, R + 1):
+                    sad = 0
+                    for y in range(by * 16, min(by * 16 + 16, H)):
+                        for x in range(bx * 16, min(bx * 16 + 16, W)):
+                            yy = min(max(y + dy, 0), H - 1)
+                            xx = min(max(x + dx, 0), W - 1)
+                            sad += abs(int(cur[y, x]) - int(ref[yy, xx]))
+                    key = (sad, abs(dy) + abs(dx), dy, dx)
+                    if best is None or key < best:
+                        best = key
+            assert tuple(got[by, bx]) == best[2:], (by, bx, got[by, bx], best)
+    flat = LF.motion_search(np.full((32, 32), 7), np.full((32, 32), 7), 16, 3)
+    assert np.all(flat == 0)                           # all ties -> (0, 0)
+
+
+def test_translated_gop_highpass_vanishes_with_motion():
+    """Frames of one canvas moving by (2, -3) pixels per frame: the search
+    finds the motion, and with zero CNN residuals (Haar predict) the
+    level-1 highpass bands are exactly zero wherever the prediction reads
+    inside the frame."""
+    t = _tlift_tensors(zero=True)
+    canvas = np.random.default_rng(33).integers(0, 256, (120, 140)).astype(np.float64)
+    frames = [canvas[40 + 2 * k:40 + 2 * k + 48, 40 - 3 * k:40 - 3 * k + 64] for k in range(8)]
+    mvs = LF.gop_motion(frames, 3)
+    assert np.all(mvs[0] == (2, -3))
+    bands = LF.temporal_forward(frames, t, 3, mvs)
+    for h in bands[4:8]:                               # level-1 highpass bands
+        assert np.all(h[:46, 3:] == 0.0)
+    zero = LF.temporal_forward(frames, t, 3)
+    # only the border strips the motion uncovers (2 rows, 3 columns) remain
+    assert np.sum(np.abs(bands[4])) < 0.15 * np.sum(np.abs(zero[4]))
