@@ -649,6 +649,36 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
     return res
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) of
+# the kernel classes of one decode step of this workload (batch 24, FP8),
+# from one ncu capture of `bench.py --nvtx-step` at full size (its summary
+# is kept under profiles/); valid only while the sources
+# of the convolution kernels hash to "src" (the capture's), else reported
+# as null.
+TRAFFIC = {"src": "81a51db34ed5659f", "precision": "fp8", "batch": 24,
+           "bytes_per_launch": {"ctx_conv1x1": 345.43e6, "ctx_lstm_gates_conv3x3": 1150.36e6,
+                                "ctx_conv3x3": 246.46e6, "ctx_head_conv3x3": 210.80e6,
+                                "rans_decode": 5.89e6, "lift_step": 31.10e6,
+                                "ctx_small": 173.88e6}}
+
+
+def conv_src_hash() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_2405_12631_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("ctx_tc.cu", "tc_ptx.cuh", "pw_internal.cuh"):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(name: str, precision: str, batch: int):
+    if (precision != TRAFFIC["precision"] or batch != TRAFFIC["batch"]
+            or conv_src_hash() != TRAFFIC["src"]):
+        return None
+    return TRAFFIC["bytes_per_launch"].get(name)
+
+
 PAPER = {"hardware": "NVIDIA RTX A6000 (Ampere)", "precision": "not stated",
          "scope": "luma only, averaged (Kodak 768x512; UVG centre crops 768x512, GOP 8)",
          "image_decode_speedup_vs_autoregressive": 354,
@@ -749,6 +779,17 @@ def run_gpu(args):
 
     for _ in range(max(args.warmup - 1, 0)):
         step()
+    if args.nvtx_step:
+        # one more decode step inside the NVTX range "pw_step" (for ncu
+        # --nvtx --nvtx-include "pw_step/"), then stop
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("pw_step")
+        step()
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"nvtx_step": "done", "batch": BATCH, "launches": codec.launches}))
+        return
     # the last warm-up step records every kernel class (the per-class
     # breakdown); the timed steps then record only the dominant class, whose
     # CUDA-event time gives the roofline figure without perturbing the rest
@@ -814,7 +855,11 @@ def run_gpu(args):
     if dom:
         r = class_roofline(dom, args.precision, peaks, peak_kind)
         roofline = {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
-                    "unit": r["unit"], "frac": r["frac"], "traffic": None, "kernel": dom["name"],
+                    "unit": r["unit"], "frac": r["frac"],
+                    "traffic": traffic_of(dom["name"], args.precision, BATCH),
+                    "traffic_unit": "bytes per launch (ncu, one step at this batch)",
+                    "algorithmic_bytes_per_launch": dom["bytes"] / max(dom["launches"], 1),
+                    "kernel": dom["name"],
                     "timing": "CUDA events around this class's launches over the timed steps "
                               "(the only class recorded there)",
                     "flop_per_byte": r["flop_per_byte"],
@@ -914,6 +959,9 @@ def main():
                     help="requests of the open-loop serving run (0 = skip)")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the single-image, video and lossless workloads")
+    ap.add_argument("--nvtx-step", action="store_true",
+                    help="after the warm-up, run one decode step inside the NVTX range "
+                         "'pw_step' and exit (for ncu captures of exactly one step)")
     ap.add_argument("--cpu-samples", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--single-thread", action="store_true", help=argparse.SUPPRESS)
     args = ap.parse_args()
