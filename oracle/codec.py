@@ -24,13 +24,17 @@ Readings where the paper is silent:
 Bitstream ("PWBS", little endian): 64-byte header, then n_chunks + 1 u32
 payload offsets, then the payload of rANS chunks in the order component,
 subband (coding order), step; each step's positions (raster order) are split
-into chunks of at most `chunk_symbols` symbols; a chunk of n symbols is coded
+into chunks of at most `chunk_symbols` symbols (see chunk_layout); a chunk of
+n symbols is coded
 with min(32, max(1, n >> 7)) interleaved states. In autoregressive-LL mode
 the LL subband is one single-state chunk in raster order instead of four
 steps.
 
   0 magic "PWBS"        4 u16 version (1)      6 u16 flags (1 lossless,
-  8 u32 width          12 u32 height             2 autoregressive LL)
+  8 u32 width          12 u32 height             2 autoregressive LL,
+                                                 16 balanced chunks; the
+                                                 library also records its
+                                                 precision class in bits 2-3)
  16 u8 ncomp           17 u8 levels            18 u8 bitdepth
  19 u8 colour (0 gray, 1 YCbCr, 2 RCT, 3 raw planes)
  20 f32 Delta_L        24 f32 Delta_H          28 u16 T   30 u8 log2 M
@@ -192,10 +196,15 @@ def context_params_all(model: Model, qsb: list):
 
 # --------------------------------------------------------------------------
 # chunk layout
-def chunk_layout(shapes, ncomp: int, ll_ar: bool, S: int):
+def chunk_layout(shapes, ncomp: int, ll_ar: bool, S: int, balanced: bool = True):
     """List of (comp, subband, step, first, count, lanes) in stream order.
 
-    step is -1 for the single-state autoregressive LL chunk.
+    step is -1 for the single-state autoregressive LL chunk. A step's n
+    symbols (raster order) form ceil(n / S) chunks: balanced (flag 16 of
+    the stream header), the first n mod k of the k chunks hold
+    floor(n / k) + 1 symbols and the rest floor(n / k), so that no chunk's
+    serial decode is longer than it needs to be; otherwise chunks of S
+    symbols and a shorter last one.
     """
     out = []
     for comp in range(ncomp):
@@ -207,9 +216,17 @@ def chunk_layout(shapes, ncomp: int, ll_ar: bool, S: int):
             sm = step_map(h, w)
             for k in range(4):
                 n = int(np.count_nonzero(sm == k))
-                for first in range(0, n, S):
-                    cnt = min(S, n - first)
-                    out.append((comp, i, k, first, cnt, chunk_lanes(cnt)))
+                if balanced:
+                    nch = -(-n // S)
+                    first = 0
+                    for j in range(nch):
+                        cnt = n // nch + (1 if j < n % nch else 0)
+                        out.append((comp, i, k, first, cnt, chunk_lanes(cnt)))
+                        first += cnt
+                else:
+                    for first in range(0, n, S):
+                        cnt = min(S, n - first)
+                        out.append((comp, i, k, first, cnt, chunk_lanes(cnt)))
     return out
 
 
@@ -271,7 +288,7 @@ def _encode_symbols(model, qcomp, shapes, *, width, height, bitdepth, colour,
         b = R.pack_chunk(st, words)
         payload.append(b)
         offsets.append(offsets[-1] + len(b))
-    flags = (1 if lossless else 0) | (2 if ll_ar else 0)
+    flags = (1 if lossless else 0) | (2 if ll_ar else 0) | 16
     head = (b"PWBS" + struct.pack("<HHIIBBBBffHBBIIQI", 1, flags, width, height,
                                   len(qcomp), model.levels, bitdepth, colour,
                                   float(d32), float(d32), E.T, E.LOG2M, LANES,
@@ -307,6 +324,7 @@ def parse_header(bs: bytes) -> dict:
     offs = np.frombuffer(bs, dtype="<u4", count=nch + 1, offset=64).astype(np.int64)
     base = 64 + 4 * (nch + 1)
     return dict(version=ver, lossless=bool(flags & 1), ll_ar=bool(flags & 2),
+                balanced=bool(flags & 16),
                 width=width, height=height, ncomp=ncomp, levels=levels,
                 bitdepth=bitdepth, colour=colour, delta_l=f32(dl), delta_h=f32(dh),
                 T=T, log2m=log2m, lanes=lanes, chunk=chunk, n_chunks=nch,
@@ -344,7 +362,7 @@ def decode_symbols(model: Model, bs: bytes, params: list | None = None):
     Hp = -(-hd["height"] // mult) * mult
     Wp = -(-hd["width"] // mult) * mult
     shapes = subband_shapes(Hp, Wp, L)
-    layout = chunk_layout(shapes, hd["ncomp"], hd["ll_ar"], hd["chunk"])
+    layout = chunk_layout(shapes, hd["ncomp"], hd["ll_ar"], hd["chunk"], hd["balanced"])
     if len(layout) != hd["n_chunks"]:
         raise ValueError("chunk count mismatch")
     bank = E.cdf_bank().astype(np.int64)

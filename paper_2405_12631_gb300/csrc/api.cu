@@ -298,7 +298,7 @@ static int check_header_model(pw_ctx *ctx, const Model &m, const StreamHeader &h
 static int build_geo(const StreamHeader &h, Geometry &g) {
   g.build((int)h.height, (int)h.width, h.ncomp, h.levels, h.colour, h.bitdepth,
           (h.flags & FLAG_LOSSLESS) ? 1 : 0, (h.flags & FLAG_LL_AR) ? 1 : 0,
-          (int)h.chunk_symbols);
+          (int)h.chunk_symbols, (h.flags & FLAG_BALANCED) ? 1 : 0);
   if ((uint64_t)g.chunks.size() * g.nc != h.n_chunks) { set_last_error("chunk count mismatch"); return PW_ECORRUPT; }
   return PW_OK;
 }
@@ -555,7 +555,7 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
     std::memcpy(h.magic, "PWBS", 4);
     h.version = 1;
     h.flags = (uint16_t)((g.lossless ? FLAG_LOSSLESS : 0) | (g.ll_ar ? FLAG_LL_AR : 0) |
-                         prec_flags(ctx));
+                         (g.balanced ? FLAG_BALANCED : 0) | prec_flags(ctx));
     h.width = g.W; h.height = g.H; h.ncomp = (uint8_t)g.nc; h.levels = (uint8_t)g.levels;
     h.bitdepth = (uint8_t)g.bitdepth; h.colour = (uint8_t)g.colour;
     h.delta_l = dl; h.delta_h = dh; h.T = kT; h.log2m = kLogM; h.lanes = kMaxLanes;

@@ -22,9 +22,9 @@ static inline void bump(pw_ctx *ctx, int n = 1) { ctx->launches += (uint64_t)n; 
 
 // ---------------------------------------------------------------------------
 void Geometry::build(int H_, int W_, int nc_, int levels_, int colour_, int bitdepth_,
-                     int lossless_, int ll_ar_, int chunk_) {
+                     int lossless_, int ll_ar_, int chunk_, int balanced_) {
   H = H_; W = W_; nc = nc_; levels = levels_; colour = colour_; bitdepth = bitdepth_;
-  lossless = lossless_; ll_ar = ll_ar_; chunk = chunk_;
+  lossless = lossless_; ll_ar = ll_ar_; chunk = chunk_; balanced = balanced_;
   const int mult = 1 << levels;
   Hp = (H + mult - 1) / mult * mult;
   Wp = (W + mult - 1) / mult * mult;
@@ -60,9 +60,19 @@ void Geometry::build(int H_, int W_, int nc_, int levels_, int colour_, int bitd
     for (int k = 0; k < 4; ++k) {
       const int n = step_count(sh[i], sw[i], k);
       group_first[i * 4 + k] = (int)chunks.size();
-      for (int f = 0; f < n; f += chunk) {
-        const int cnt = std::min(chunk, n - f);
-        chunks.push_back({i, k, (uint32_t)f, (uint32_t)cnt, (uint16_t)chunk_lanes(cnt)});
+      if (balanced) {
+        // ceil(n / chunk) chunks; the first n % nch get one symbol more
+        const int nch = (n + chunk - 1) / chunk;
+        for (int j = 0, f = 0; j < nch; ++j) {
+          const int cnt = n / nch + (j < n % nch ? 1 : 0);
+          chunks.push_back({i, k, (uint32_t)f, (uint32_t)cnt, (uint16_t)chunk_lanes(cnt)});
+          f += cnt;
+        }
+      } else {
+        for (int f = 0; f < n; f += chunk) {
+          const int cnt = std::min(chunk, n - f);
+          chunks.push_back({i, k, (uint32_t)f, (uint32_t)cnt, (uint16_t)chunk_lanes(cnt)});
+        }
       }
       group_count[i * 4 + k] = (int)chunks.size() - group_first[i * 4 + k];
     }

@@ -71,7 +71,7 @@ struct StreamHeader {
 #pragma pack(pop)
 static_assert(sizeof(StreamHeader) == 64, "stream header is 64 bytes");
 
-enum : uint16_t { FLAG_LOSSLESS = 1, FLAG_LL_AR = 2, FLAG_PREC_SHIFT = 2 };
+enum : uint16_t { FLAG_LOSSLESS = 1, FLAG_LL_AR = 2, FLAG_PREC_SHIFT = 2, FLAG_BALANCED = 16 };
 
 // One chunk of the per-component layout (same for every image of a class).
 struct ChunkTpl {
@@ -84,6 +84,10 @@ struct ChunkTpl {
 struct Geometry {
   int H = 0, W = 0, Hp = 0, Wp = 0, nc = 1, levels = 4, colour = 0, bitdepth = 8;
   int lossless = 0, ll_ar = 0, chunk = 16384;
+  // chunk layout of a step's symbols: 0 = chunks of `chunk` symbols and a
+  // shorter last one; 1 (balanced, header flag FLAG_BALANCED) = the fewest
+  // chunks of at most `chunk` symbols, of equal length to within one
+  int balanced = 1;
   int nsb = 13;
   std::vector<int> sh, sw;          // subband sizes in coding order
   std::vector<int64_t> soff;        // per-plane element offset of subband i
@@ -93,7 +97,7 @@ struct Geometry {
   std::vector<int> group_first;     // [sb * 4 + step] first chunk index, or -1
   std::vector<int> group_count;     // [sb * 4 + step]
   void build(int H, int W, int nc, int levels, int colour, int bitdepth, int lossless,
-             int ll_ar, int chunk);
+             int ll_ar, int chunk, int balanced = 1);
 };
 
 // Device buffers for a batch of planes of one geometry.

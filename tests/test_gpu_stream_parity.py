@@ -93,7 +93,7 @@ def test_index_injection_stream_identical(pw, blob, prec, kind, q):
                                        colour=hd["colour"], q=q, chunk=hd["chunk"])
     assert len(ref) == len(bs), (len(ref), len(bs))
     head_gpu = bytearray(bs[:64])
-    head_gpu[6] &= 0x3                                # precision-class bits
+    head_gpu[6] &= ~0x0C & 0xFF                       # precision-class bits (2-3)
     assert bytes(head_gpu) == ref[:64]
     assert bs[64:] == ref[64:], "payload or offset table differs"
 

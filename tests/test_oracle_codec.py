@@ -109,3 +109,31 @@ def test_motion_compensation_lowers_the_rate_of_a_panning_gop():
     assert len(mc) < 0.95 * len(zero), (len(mc), len(zero))
     out = K.decode_gop(bl, bh, mc)
     assert out.shape == frames.shape
+
+
+def test_balanced_chunk_layout():
+    """Balanced layout: ceil(n / S) chunks of equal length to within one,
+    covering the step's symbols in order; the plain layout (flag clear) is
+    S-symbol chunks and a remainder, and streams of both kinds decode."""
+    shapes = [(16, 24, 1)]
+    lay = K.chunk_layout(shapes, 1, False, 40, balanced=True)
+    for k in range(4):
+        ch = [c for c in lay if c[2] == k]
+        n = sum(c[4] for c in ch)
+        assert n == 96 and len(ch) == 3 and [c[4] for c in ch] == [32, 32, 32]
+        assert [c[3] for c in ch] == [0, 32, 64]
+    plain = K.chunk_layout(shapes, 1, False, 40, balanced=False)
+    assert [c[4] for c in plain if c[2] == 0] == [40, 40, 16]
+    for S_ in (7, 9, 11):
+        lay = K.chunk_layout([(10, 12, 1)], 1, False, S_)
+        for k in range(4):
+            cnt = [c[4] for c in lay if c[2] == k]
+            assert sum(cnt) == 30 and len(cnt) == -(-30 // S_)
+            assert max(cnt) <= S_ and max(cnt) - min(cnt) <= 1
+            assert cnt == sorted(cnt, reverse=True)
+    blob = _blob(0)
+    img = S.gray_sinusoids(32, 48, seed=9)
+    bs = K.encode_image(blob, img, q=8.0, chunk=50)
+    assert K.parse_header(bs)["balanced"]
+    out = K.decode_image(blob, bs)
+    assert out.shape == img.shape
