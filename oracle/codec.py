@@ -18,8 +18,12 @@ Readings where the paper is silent:
 * images whose sides are not multiples of 2^levels are padded by whole-sample
   mirroring and cropped after decoding; output samples are floor(v + 1/2)
   (FP32), clipped to the bit depth;
-* the post-processing network after the inverse transform is not part of
-  this path.
+* post-processing after the inverse transform (Section 3.1 names the module
+  but not its layers): when the weight blob carries one ("post.*"), each
+  reconstructed (padded, level-shifted) component plane x of a lossy image
+  becomes x + CNN_post(x), CNN_post with the structure of the lifting CNN
+  (conv3x3 1->F, tanh, conv3x3 F->F, tanh, conv3x3 F->1, zero padding);
+  lossless images and the temporal bands of a GOP are not post-processed.
 
 Bitstream ("PWBS", little endian): 64-byte header, then n_chunks + 1 u32
 payload offsets, then the payload of rANS chunks in the order component,
@@ -67,8 +71,8 @@ from . import entropy as E
 from . import rans as R
 from .blob import model_hash, read_blob
 from .context import ContextModel, step_map, step_positions
-from .lifting import (MC_BLOCK, Lifting, gop_luma, gop_motion, subband_shapes,
-                      temporal_forward, temporal_inverse)
+from .lifting import (MC_BLOCK, Lifting, gop_luma, gop_motion, lift_cnn, net_of,
+                      subband_shapes, temporal_forward, temporal_inverse)
 
 LANES = 32
 DEFAULT_CHUNK = 16384
@@ -89,6 +93,7 @@ class Model:
         self.ll_mode = cfg["ll_mode"]
         self.tensors = t
         self.lift = Lifting(t)
+        self.post = net_of(t, "post.") if "post.w1" in t else None
         self.ctx = ContextModel(t, cfg["C"], cfg["ll_mode"])
         self.hash = model_hash(blob)
 
@@ -443,11 +448,19 @@ def reconstruct_planes(model: Model, hd: dict, qcomp: list):
     return out
 
 
+def post_process(model: Model, hd: dict, planes: list) -> list:
+    """x + CNN_post(x) per padded component plane (lossy images of a model
+    with a post-processing net); the planes themselves otherwise."""
+    if model.post is None or hd["lossless"]:
+        return planes
+    return [p + lift_cnn(p, model.post) for p in planes]
+
+
 def decode_image(blob: bytes, bs: bytes) -> np.ndarray:
     """Decode a PWBS image stream to uint8/uint16 samples."""
     model = Model(blob)
     hd, qcomp = decode_symbols(model, bs)
-    planes = reconstruct_planes(model, hd, qcomp)
+    planes = post_process(model, hd, reconstruct_planes(model, hd, qcomp))
     h, w = hd["height"], hd["width"]
     planes = [p[:h, :w] for p in planes]
     v = colour_inverse(planes, hd["colour"], hd["bitdepth"])

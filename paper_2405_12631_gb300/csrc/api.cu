@@ -389,6 +389,13 @@ int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const s
   }
   bump(ctx);
   if ((s = lift_inverse_planes(ctx, m, g, pl->ws, pl->ws.planes))) return s;
+  // post-processing (Section 3.1) of lossy images, into the dequantised
+  // subbands' buffer, which the inverse transform has consumed
+  const float *recon = pl->ws.planes;
+  if (m.has_post && !g.lossless) {
+    if ((s = post_process_planes(ctx, m, g, P, pl->ws.planes, pl->ws.Yf))) return s;
+    recon = pl->ws.Yf;
+  }
   // output: direct when the batch is one contiguous packed device buffer
   const int64_t row = (int64_t)g.W * g.nc * bps, img = row * g.H;
   bool direct = true;
@@ -405,7 +412,7 @@ int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const s
   }
   {
     ProfScope ps(ctx, KC_COLOUR, 0.0, (double)P * g.H * g.W * 4.0 + (double)img * B);
-    launch_colour_out(pl->ws.planes, B, g.nc, g.Hp, g.Wp, g.H, g.W, g.colour, g.bitdepth, dst,
+    launch_colour_out(recon, B, g.nc, g.Hp, g.Wp, g.H, g.W, g.colour, g.bitdepth, dst,
                       img, row, st);
   }
   bump(ctx);

@@ -315,6 +315,22 @@ static void lift_step(pw_ctx *ctx, const LiftStepParams &a) {
   launch_lift_step(a, ctx->stream);
 }
 
+int post_process_planes(pw_ctx *ctx, Model &m, const Geometry &g, int P, const float *src,
+                        float *dst) {
+  LiftStepParams a{};
+  a.P = P; a.H = g.Hp; a.W = g.Wp; a.dir = 0; a.lin = LIN_ZERO; a.sign = +1; a.round = 0;
+  a.net = m.post; a.status = ctx->status;
+  a.tc = ctx->precision != PW_PREC_FP32 ? 1 : 0;
+  const int64_t hw = (int64_t)g.Hp * g.Wp;
+  a.src = acc(const_cast<float *>(src), hw, g.Wp);
+  a.other = acc(const_cast<float *>(src), hw, g.Wp);
+  a.out = acc(dst, hw, g.Wp);
+  a.copy = acc(nullptr, 0, 0);
+  lift_step(ctx, a);
+  bump(ctx);
+  return PW_OK;
+}
+
 int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         float *dst) {
   const int P = ws.P, L = g.levels;

@@ -39,6 +39,10 @@ struct Model {
   std::map<std::string, std::vector<float>> host;
   LiftNetDev lift[2][2];   // [row, col][P, U]
   LiftNetDev tlift[2];     // [P, U]
+  // post-processing CNN after the inverse transform (present when the blob
+  // carries "post.*" tensors; lossy images only)
+  LiftNetDev post{};
+  bool has_post = false;
   float *lstm_we = nullptr, *lstm_be = nullptr, *lstm_wg = nullptr, *lstm_bg = nullptr;
   StepNetDev sb[4], ll[4];
   float *ar_w5 = nullptr, *ar_b5 = nullptr, *ar_w1 = nullptr, *ar_b1 = nullptr,
@@ -138,6 +142,10 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         float *dst_planes);
 int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         const float *src_planes);
+// Post-processing of the reconstructed component planes ([P][Hp][Wp]):
+// dst = src + CNN_post(src) (dst != src).
+int post_process_planes(pw_ctx *ctx, Model &m, const Geometry &g, int P, const float *src,
+                        float *dst);
 // Temporal lifting of a GOP (Section 3.3). mv: device block motion vectors
 // of every level and pair (the order of the motion search: level 1 pairs
 // first), or null for zero motion; twarp: (nf / 2) frames of scratch for the

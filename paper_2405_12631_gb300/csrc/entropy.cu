@@ -291,32 +291,29 @@ __global__ void __launch_bounds__(256) k_rans_decode(
     }
     pk_a = pk_b;
     pk_b = (active && p + 2 * nl < count) ? __ldg(idxp + p + 2 * nl) : 0u;
-    int ctr = 0, s = 1;
-    if (active) {
-      int tid;
-      unpack_index(pk, ctr, tid);
-      const uint32_t slot = x & (kM - 1);
-      uint32_t lo, hi;
-      s = cdf_search_r(bank + (size_t)tid * (kNSym + 1), c0, c1, slot, lo, hi);
-      x = (hi - lo) * (x >> kLogM) + slot - lo;
-    }
+    // every lane runs the search (inactive lanes on a valid table, their
+    // state kept), so the round has no branch around it
+    int ctr, tid;
+    unpack_index(pk, ctr, tid);
+    const uint32_t slot = x & (kM - 1);
+    uint32_t lo, hi;
+    const int s = cdf_search_r(bank + (size_t)tid * (kNSym + 1), c0, c1, slot, lo, hi);
     {
+      const uint32_t xn = (hi - lo) * (x >> kLogM) + slot - lo;
+      x = active ? xn : x;
       const bool need = active && x < kRansL;
       const uint32_t m = __ballot_sync(0xffffffffu, need);
-      if (m) {
-        const uint32_t k = ptr + __popc(m & lt);
-        const uint32_t wv = word(need ? k : ptr);
-        if (need) {
-          if (k >= nwords) bad = true;
-          x = (x << 16) | (k < nwords ? wv : 0u);
-        }
-        advance(__popc(m));
-      }
+      const uint32_t k = ptr + __popc(m & lt);
+      const uint32_t wv = word(need ? k : ptr);
+      bad = bad || (need && k >= nwords);
+      x = need ? ((x << 16) | (k < nwords ? wv : 0u)) : x;
+      advance(__popc(m));
     }
     // escapes: phase 0 counts ones up to a zero, phase 1 reads k bits
     bool pend = active && (s == 0 || s == kNSym - 1);
     int phase = 0, kcnt = 0;
     uint32_t v = 0;
+    if (__builtin_expect(__any_sync(0xffffffffu, pend), 0))
     for (int rnd = 0; rnd < 2 * kMaxEscBits + 2; ++rnd) {
       if (!__any_sync(0xffffffffu, pend)) break;
       if (pend) {
@@ -361,7 +358,13 @@ __global__ void __launch_bounds__(256) k_rans_decode(
     }
     if (step >= 0) {
       rr += nl;
-      while (rr >= pair) { rr -= pair; ++y2; }
+      if (nl <= pair) {
+        const bool wrap = rr >= pair;
+        rr -= wrap ? pair : 0;
+        y2 += wrap ? 1 : 0;
+      } else {
+        while (rr >= pair) { rr -= pair; ++y2; }
+      }
     }
     // every loop is bounded, so a corrupt chunk only has to stop early
     // eventually: vote every 32 iterations

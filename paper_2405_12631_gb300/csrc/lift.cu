@@ -120,8 +120,10 @@ __device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int 
     lin = 0.25f * (sm + s0);
   } else if (a.lin == LIN_ID) {
     lin = s0;
-  } else {  // LIN_HALF
+  } else if (a.lin == LIN_HALF) {
     lin = 0.5f * s0;
+  } else {  // LIN_ZERO: the CNN alone (post-processing)
+    lin = 0.f;
   }
   float v = kExact ? __fadd_rn(lin, r_out) : lin + r_out;
   if (a.round == 1) v = floorf(v);

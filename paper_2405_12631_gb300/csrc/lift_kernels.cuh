@@ -20,7 +20,7 @@ struct LiftNetDev {
   const void *w2b, *w3b;
 };
 
-enum { LIN_P53 = 0, LIN_U53 = 1, LIN_ID = 2, LIN_HALF = 3 };
+enum { LIN_P53 = 0, LIN_U53 = 1, LIN_ID = 2, LIN_HALF = 3, LIN_ZERO = 4 };
 
 struct LiftStepParams {
   PlaneAcc src, other, out, copy;  // copy.p may be null

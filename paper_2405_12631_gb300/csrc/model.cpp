@@ -162,6 +162,12 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
         return PW_EINVAL;
   for (int o = 0; o < 2; ++o)
     if (!load_lift(std::string("tlift.") + ops[o] + ".", tlift[o])) return PW_EINVAL;
+  // optional post-processing net (same structure as the lifting nets)
+  has_post = false;
+  if (ts.count("post.w1")) {
+    if (!load_lift("post.", post)) return PW_EINVAL;
+    has_post = true;
+  }
 
   // ConvLSTM
   {

@@ -38,6 +38,7 @@ class ModelConfig:
     C: int = 32
     F: int = 16
     ll_mode: int = 0  # 0 four-step LL, 1 autoregressive LL
+    post: int = 0     # 1: the blob carries a post-processing CNN ("post.*")
 
 
 def tensor_specs(cfg: ModelConfig):
@@ -46,6 +47,7 @@ def tensor_specs(cfg: ModelConfig):
     Lifting predict/update CNNs (shared by all levels), one per direction
     (row, col) and operator (P, U): conv3x3 1->F, conv3x3 F->F, conv3x3 F->1;
     the same structure for the temporal lifting of GOPs ("tlift", P and U).
+    With cfg.post, a post-processing CNN ("post", same structure) follows.
     Context prediction: ConvLSTM input conv (1->C, 3x3) and gate conv
     (2C->4C, 3x3, gate order i, f, o, g). Context fusion nets for subbands
     2..13 ("sb"), and either four-step nets for LL ("ll", ll_mode 0) or the
@@ -64,6 +66,11 @@ def tensor_specs(cfg: ModelConfig):
         s += [(p + "w1", (F, 1, 3, 3)), (p + "b1", (F,)),
               (p + "w2", (F, F, 3, 3)), (p + "b2", (F,)),
               (p + "w3", (1, F, 3, 3)), (p + "b3", (1,))]
+    if cfg.post:
+        # post-processing CNN after the inverse transform (same structure)
+        s += [("post.w1", (F, 1, 3, 3)), ("post.b1", (F,)),
+              ("post.w2", (F, F, 3, 3)), ("post.b2", (F,)),
+              ("post.w3", (1, F, 3, 3)), ("post.b3", (1,))]
     s += [("lstm.we", (C, 1, 3, 3)), ("lstm.be", (C,)),
           ("lstm.wg", (4 * C, 2 * C, 3, 3)), ("lstm.bg", (4 * C,))]
     sets = ["sb", "ll"] if cfg.ll_mode == 0 else ["sb"]
@@ -98,7 +105,7 @@ def _init_scale(name: str, shape, cfg: ModelConfig) -> float:
         return 0.05
     fan_in = int(np.prod(shape[1:])) if len(shape) > 1 else 1
     base = np.sqrt(3.0 / max(fan_in, 1))
-    if name.startswith("lift.") or name.startswith("tlift."):
+    if name.startswith("lift.") or name.startswith("tlift.") or name.startswith("post."):
         if leaf == "w1":          # input samples are of order +-128
             return base * (5.0 / 3.0) / 64.0
         if leaf == "w2":

@@ -137,3 +137,52 @@ def test_balanced_chunk_layout():
     assert K.parse_header(bs)["balanced"]
     out = K.decode_image(blob, bs)
     assert out.shape == img.shape
+
+
+# ---------------------------------------------------------------------------
+# Post-processing after the inverse transform (Section 3.1)
+def _post_model(seed=4, zero=False, post_t=None):
+    cfg = S.ModelConfig(levels=4, C=8, post=1)
+    t = S.random_model(cfg, seed)
+    if zero:
+        for k in t:
+            if k.startswith("post."):
+                t[k] = np.zeros_like(t[k])
+    if post_t:
+        t.update(post_t)
+    return S.pack_blob(cfg, t)
+
+
+def test_post_processing_zero_net_is_identity_and_skipped_when_lossless():
+    blob = _post_model(zero=True)
+    m = K.Model(blob)
+    assert m.post is not None
+    planes = [np.random.default_rng(1).normal(0, 40, (16, 32))]
+    assert np.array_equal(K.post_process(m, {"lossless": False}, planes)[0], planes[0])
+    m2 = K.Model(_post_model())
+    assert K.post_process(m2, {"lossless": True}, planes)[0] is planes[0]
+    assert not np.array_equal(K.post_process(m2, {"lossless": False}, planes)[0], planes[0])
+
+
+def test_post_processing_single_tap_closed_form():
+    """CNN_post with one tap per layer: layer 1 reads the left neighbour
+    (tap (1, 0)) scaled by a, layer 2 the centre, layer 3 the centre scaled
+    by c: x + c tanh(tanh(a x[y, x - 1] + b1) + b2) + b3, zero left of the
+    plane."""
+    F = 16
+    a, c, b1, b2, b3 = 0.015625, 3.0, 0.25, -0.125, 0.5   # exact in float32
+    w1 = np.zeros((F, 1, 3, 3), np.float32); w1[0, 0, 1, 0] = a
+    w2 = np.zeros((F, F, 3, 3), np.float32); w2[0, 0, 1, 1] = 1.0
+    w3 = np.zeros((1, F, 3, 3), np.float32); w3[0, 0, 1, 1] = c
+    bb1 = np.zeros(F, np.float32); bb1[0] = b1
+    bb2 = np.zeros(F, np.float32); bb2[0] = b2
+    blob = _post_model(post_t={"post.w1": w1, "post.w2": w2, "post.w3": w3, "post.b1": bb1,
+                               "post.b2": bb2, "post.b3": np.array([b3], np.float32)})
+    m = K.Model(blob)
+    x = np.random.default_rng(2).normal(0, 60, (8, 12))
+    got = K.post_process(m, {"lossless": False}, [x])[0]
+    for yy in range(8):
+        for xx in range(12):
+            left = x[yy, xx - 1] if xx >= 1 else 0.0
+            want = x[yy, xx] + c * np.tanh(np.tanh(a * left + b1) + b2) + b3
+            assert abs(got[yy, xx] - want) < 1e-9
