@@ -342,19 +342,23 @@ def fp32_single_image(pw, local, imgs, qs, blob, stream_ptr):
     return res
 
 
-def batched_precision(pw, local, prec, imgs, qs, blob, stream_ptr, steps, warmup):
+def batched_precision(pw, local, prec, imgs, qs, blob, stream_ptr, steps, warmup,
+                      lane_shift: int = 7, chunk: int = 16384):
     """The same batched, device-resident decode in another precision class
-    (its own streams; same images and q), timed the same way."""
+    or stream format (its own streams; same images and q), timed the same
+    way. lane_shift / chunk: the coder's symbols per interleaved state
+    (2^lane_shift) and symbols per chunk."""
     import torch
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     c = pw.Codec(local, prec, stream=stream_ptr)
+    c.set_lane_rule(lane_shift)
     m = c.load_model(blob)
     enc = [None] * len(imgs)
     for q in QSTEPS:
         idx = [i for i in range(len(imgs)) if qs[i] == q]
         if idx:
-            for i, b in zip(idx, c.encode_batch(m, [imgs[i] for i in idx], q=q)):
+            for i, b in zip(idx, c.encode_batch(m, [imgs[i] for i in idx], q=q, chunk=chunk)):
                 enc[i] = b
     lens = [len(b) for b in enc]
     offs = np.cumsum([0] + [(n + 255) // 256 * 256 for n in lens])
@@ -384,6 +388,37 @@ def batched_precision(pw, local, prec, imgs, qs, blob, stream_ptr, steps, warmup
     m.close()
     c.close()
     return res
+
+
+def single_image_latency(pw, local, stream_ptr, blob, prec: str, lane_shift: int, chunk: int,
+                         reps: int = 10):
+    """Decode latency of one RGB image at 256x256, 1024x768 and 2048x2048
+    (crops of the batched workload's generator, q = 8), device stream in,
+    device image out, median CUDA-event time of `reps` decodes."""
+    import torch
+    import synthetic as S
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    c = pw.Codec(local, prec, stream=stream_ptr)
+    c.set_lane_rule(lane_shift)
+    m = c.load_model(blob)
+    out = {}
+    for hh, ww in ((256, 256), (768, 1024), (2048, 2048)):
+        img = S.rgb_natural(hh, ww, seed=5)
+        bs = c.encode_image(m, img, q=8.0, chunk=chunk)
+        d_bs = torch.from_numpy(np.frombuffer(bs, dtype=np.uint8).copy()).to(dev)
+        o = torch.empty((hh, ww, 3), dtype=torch.uint8, device=dev)
+
+        def one():
+            c.decode_batch_device(m, [d_bs.data_ptr()], [len(bs)], o.data_ptr(), (hh, ww, 3))
+        for _ in range(3):
+            one()
+        torch.cuda.synchronize()
+        t = _events_ms(stream, one, reps)
+        out[f"{ww}x{hh}"] = {"ms": float(np.median(t)), "bpp": 8.0 * len(bs) / (hh * ww)}
+    m.close()
+    c.close()
+    return out
 
 
 def _events_ms(stream, fn, reps: int):
@@ -476,7 +511,8 @@ def video_run(pw, local, stream_ptr, blob_low, blob_high, n_gop: int = 4, reps: 
             "timing": "host wall clock, e2e (host stream in, host frames out)"}
 
 
-def encode_requests(pw, local, blob, reqs, precision: str, threads: int = 8):
+def encode_requests(pw, local, blob, reqs, precision: str, threads: int = 8,
+                    lane_shift: int = 7, chunk: int = 16384):
     """Pre-encode the serving workload's requests: every image is a crop of
     a seeded synthetic 2048x2048 canvas (gray or RGB) at the request's size,
     coded with its quantiser step by the library's encoder (one context and
@@ -495,12 +531,13 @@ def encode_requests(pw, local, blob, reqs, precision: str, threads: int = 8):
     def work(tid):
         st = torch.cuda.Stream(device=local)
         c = pw.Codec(local, precision, stream=st.cuda_stream)
+        c.set_lane_rule(lane_shift)
         m = c.load_model(blob)
         for i in range(tid, len(reqs), threads):
             r = reqs[i]
             y0, x0 = crops[i]
             img = np.ascontiguousarray(canvas[r["c"]][y0:y0 + r["h"], x0:x0 + r["w"]])
-            streams[i] = c.encode_image(m, img, q=r["q"])
+            streams[i] = c.encode_image(m, img, q=r["q"], chunk=chunk)
         m.close()
         c.close()
 
@@ -547,7 +584,7 @@ def serve(pw, codec, model, reqs, streams, lanes: int, max_batch: int, budget: i
 
 
 def serving_run(pw, local, codec, model, blob, n_req: int, sweep_n: int = 2000,
-                sweep=(2.0, 4.0, 8.0), lanes: int = 16, max_batch: int = 8,
+                sweep=(1.0, 2.0, 4.0, 8.0), lanes: int = 16, max_batch: int = 8,
                 budget: int = 48 << 30):
     """The serving workload: n_req requests (Poisson arrivals at 200/s, w and
     h log-uniform in [256, 2048] rounded down to a multiple of 16, gray/RGB
@@ -581,6 +618,17 @@ def serving_run(pw, local, codec, model, blob, n_req: int, sweep_n: int = 2000,
     main["saturation_sweep"] = pts
     main["max_sustained_mpix_per_s"] = max(ok) if ok else None
     main["capacity_mpix_per_s"] = max([p["mpix_per_s"] for p in pts] + [main["mpix_per_s"]])
+    # the same first sweep_n requests in the faster coder format (one rANS
+    # state per 32 symbols, 6144-symbol chunks): at 200/s and at 8x
+    fs = encode_requests(pw, local, blob, reqs[:n],
+                         {0: "fp32", 1: "bf16", 2: "fp8"}[codec.precision], lane_shift=5,
+                         chunk=6144)
+    fo = {"format": "lane rule 5, 6144-symbol chunks",
+          "bytes_vs_default": sum(len(x) for x in fs) / sum(len(x) for x in streams[:n])}
+    for f in (1.0, 8.0):
+        fo[f"rate_{int(200 * f)}"] = serve(pw, codec, model, reqs[:n], fs, lanes, max_batch,
+                                           budget, f)
+    main["fast_format"] = fo
     return main
 
 
@@ -917,6 +965,21 @@ def run_gpu(args):
     if not args.no_fp32 and world == 1:
         line["fp32_single_image"] = fp32_single_image(pw, local, imgs, qs, blob,
                                                       stream.cuda_stream)
+    if world == 1 and not args.no_compare:
+        # the coder's rate / latency option: one rANS state per 32 symbols
+        # (default 128), and also 6144-symbol chunks (default 16384)
+        opts = {}
+        for name, ls, ch in (("lane_rule_5", 5, 16384), ("lane_rule_5_chunk_6144", 5, 6144)):
+            r = batched_precision(pw, local, args.precision, imgs, qs, blob, stream.cuda_stream,
+                                  max(args.steps // 2, 3), args.warmup, ls, ch)
+            r["bpp_vs_default"] = r["bpp"] / (8.0 * stream_bytes / pixels)
+            opts[name] = r
+        lat = {"default": single_image_latency(pw, local, stream.cuda_stream, blob,
+                                               args.precision, 7, 16384)}
+        lat["lane_rule_5_chunk_6144"] = single_image_latency(pw, local, stream.cuda_stream, blob,
+                                                             args.precision, 5, 6144)
+        opts["single_image_latency"] = lat
+        line["coder_format_options"] = opts
     wl = {}
     if world == 1 and not args.no_workloads:
         wl["single_gray_256"] = single_gray_run(pw, local, stream.cuda_stream, args.steps,

@@ -79,6 +79,15 @@ int pw_ctx_create(int device, void *cuda_stream, int precision, pw_ctx **out);
 void pw_ctx_destroy(pw_ctx *ctx);
 /* Precision the context was created with. */
 int pw_ctx_precision(const pw_ctx *ctx);
+/* Stream-format option of the streams this context encodes (the coder
+ * stands in for the paper's arithmetic coder, Section 3.1; the paper has no
+ * such parameter): a chunk of n symbols is coded with min(32, max(1,
+ * n >> s)) interleaved rANS states, s = log2_symbols_per_state in 5..7
+ * (default 7). Every state costs a 4-byte flush in the stream, and a chunk
+ * decodes in ceil(n / states) serial rounds, so a smaller s trades rate for
+ * decode latency on small subbands. The stream header records s (byte 52);
+ * decoders read any of them. Errors: PW_EINVAL (s outside 5..7). */
+int pw_ctx_set_lane_rule(pw_ctx *ctx, int log2_symbols_per_state);
 
 /* Load a weight blob ("PWMB" format: lifting nets, ConvLSTM, four-step
  * context nets; one blob per lambda model, Section 4.1). The blob is a host

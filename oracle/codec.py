@@ -30,7 +30,8 @@ payload offsets, then the payload of rANS chunks in the order component,
 subband (coding order), step; each step's positions (raster order) are split
 into chunks of at most `chunk_symbols` symbols (see chunk_layout); a chunk of
 n symbols is coded
-with min(32, max(1, n >> 7)) interleaved states. In autoregressive-LL mode
+with min(32, max(1, n >> s)) interleaved states (s = 7 unless header byte 52
+says otherwise). In autoregressive-LL mode
 the LL subband is one single-state chunk in raster order instead of four
 steps.
 
@@ -43,7 +44,8 @@ steps.
  19 u8 colour (0 gray, 1 YCbCr, 2 RCT, 3 raw planes)
  20 f32 Delta_L        24 f32 Delta_H          28 u16 T   30 u8 log2 M
  31 u8 lanes           32 u32 chunk_symbols    36 u32 n_chunks
- 40 u64 model hash     48 u32 payload bytes    52..63 zero
+ 40 u64 model hash     48 u32 payload bytes    52 u8 lane shift s: one
+ interleaved state per 2^s symbols (0 = the default 7)      53..63 zero
 
 GOP stream ("PWGP"): 0 magic, 4 u16 version, 6 u16 nframes, 8 u32 width,
 12 u32 height, 16 u8 temporal levels, 17 u8 ncomp, 18 u16 zero, 20 u64 hash
@@ -201,7 +203,8 @@ def context_params_all(model: Model, qsb: list):
 
 # --------------------------------------------------------------------------
 # chunk layout
-def chunk_layout(shapes, ncomp: int, ll_ar: bool, S: int, balanced: bool = True):
+def chunk_layout(shapes, ncomp: int, ll_ar: bool, S: int, balanced: bool = True,
+                 lane_shift: int = 7):
     """List of (comp, subband, step, first, count, lanes) in stream order.
 
     step is -1 for the single-state autoregressive LL chunk. A step's n
@@ -226,19 +229,20 @@ def chunk_layout(shapes, ncomp: int, ll_ar: bool, S: int, balanced: bool = True)
                     first = 0
                     for j in range(nch):
                         cnt = n // nch + (1 if j < n % nch else 0)
-                        out.append((comp, i, k, first, cnt, chunk_lanes(cnt)))
+                        out.append((comp, i, k, first, cnt, chunk_lanes(cnt, lane_shift)))
                         first += cnt
                 else:
                     for first in range(0, n, S):
                         cnt = min(S, n - first)
-                        out.append((comp, i, k, first, cnt, chunk_lanes(cnt)))
+                        out.append((comp, i, k, first, cnt, chunk_lanes(cnt, lane_shift)))
     return out
 
 
-def chunk_lanes(n: int) -> int:
-    """Interleaved states of a chunk of n symbols: one per 128 symbols,
-    between 1 and 32 (each state costs 4 bytes of flush)."""
-    return min(LANES, max(1, n >> 7))
+def chunk_lanes(n: int, lane_shift: int = 7) -> int:
+    """Interleaved states of a chunk of n symbols: one per 2^lane_shift
+    symbols (128 by default; header byte 52 holds another choice), between 1
+    and 32 (each state costs 4 bytes of flush)."""
+    return min(LANES, max(1, n >> lane_shift))
 
 
 def _sym_positions(h, w, step):
@@ -252,7 +256,7 @@ def _sym_positions(h, w, step):
 # encode
 def encode_planes(model: Model, planes: list, *, width: int, height: int,
                   bitdepth: int, colour: int, q: float = 8.0,
-                  lossless: bool = False, chunk: int = DEFAULT_CHUNK):
+                  lossless: bool = False, chunk: int = DEFAULT_CHUNK, lane_shift: int = 7):
     """Encode level-shifted component planes (already padded)."""
     L = model.levels
     Hp, Wp = planes[0].shape
@@ -264,11 +268,11 @@ def encode_planes(model: Model, planes: list, *, width: int, height: int,
         qcomp.append([quantise(s, d32) for s in sb])
     return _encode_symbols(model, qcomp, shapes, width=width, height=height,
                            bitdepth=bitdepth, colour=colour, d32=d32,
-                           lossless=lossless, chunk=chunk), qcomp
+                           lossless=lossless, chunk=chunk, lane_shift=lane_shift), qcomp
 
 
 def _encode_symbols(model, qcomp, shapes, *, width, height, bitdepth, colour,
-                    d32, lossless, chunk, params=None):
+                    d32, lossless, chunk, params=None, lane_shift=7):
     """Entropy-code quantised subbands. params, if given, replaces the
     context model: params[comp][subband] = (mu, sigma) arrays of the
     subband's shape (index injection: the coder alone is then exercised on
@@ -277,7 +281,7 @@ def _encode_symbols(model, qcomp, shapes, *, width, height, bitdepth, colour,
     ll_ar = model.ll_mode == 1
     if params is None:
         params = [context_params_all(model, qsb) for qsb in qcomp]
-    layout = chunk_layout(shapes, len(qcomp), ll_ar, chunk)
+    layout = chunk_layout(shapes, len(qcomp), ll_ar, chunk, True, lane_shift)
     payload = []
     offsets = [0]
     for comp, i, k, first, n, nl in layout:
@@ -298,13 +302,13 @@ def _encode_symbols(model, qcomp, shapes, *, width, height, bitdepth, colour,
                                   len(qcomp), model.levels, bitdepth, colour,
                                   float(d32), float(d32), E.T, E.LOG2M, LANES,
                                   chunk, len(layout), model.hash, offsets[-1]))
-    head = head.ljust(64, b"\0")
+    head = (head + bytes([0 if lane_shift == 7 else lane_shift])).ljust(64, b"\0")
     return head + np.asarray(offsets, dtype="<u4").tobytes() + b"".join(payload)
 
 
 def encode_image(blob: bytes, img: np.ndarray, *, q: float = 8.0,
                  lossless: bool = False, bitdepth: int | None = None,
-                 chunk: int = DEFAULT_CHUNK) -> bytes:
+                 chunk: int = DEFAULT_CHUNK, lane_shift: int = 7) -> bytes:
     """Encode an (h, w) or (h, w, 3) uint8/uint16 image."""
     model = Model(blob)
     if bitdepth is None:
@@ -314,7 +318,7 @@ def encode_image(blob: bytes, img: np.ndarray, *, q: float = 8.0,
     planes = [pad_plane(p, mult) for p in planes]
     bs, _ = encode_planes(model, planes, width=img.shape[1], height=img.shape[0],
                           bitdepth=bitdepth, colour=colour, q=q,
-                          lossless=lossless, chunk=chunk)
+                          lossless=lossless, chunk=chunk, lane_shift=lane_shift)
     return bs
 
 
@@ -329,7 +333,7 @@ def parse_header(bs: bytes) -> dict:
     offs = np.frombuffer(bs, dtype="<u4", count=nch + 1, offset=64).astype(np.int64)
     base = 64 + 4 * (nch + 1)
     return dict(version=ver, lossless=bool(flags & 1), ll_ar=bool(flags & 2),
-                balanced=bool(flags & 16),
+                balanced=bool(flags & 16), lane_shift=bs[52] or 7,
                 width=width, height=height, ncomp=ncomp, levels=levels,
                 bitdepth=bitdepth, colour=colour, delta_l=f32(dl), delta_h=f32(dh),
                 T=T, log2m=log2m, lanes=lanes, chunk=chunk, n_chunks=nch,
@@ -339,7 +343,8 @@ def parse_header(bs: bytes) -> dict:
 
 def encode_symbols_with_params(model: Model, qcomp: list, params: list, *, width: int,
                                height: int, bitdepth: int, colour: int, q: float = 8.0,
-                               lossless: bool = False, chunk: int = DEFAULT_CHUNK) -> bytes:
+                               lossless: bool = False, chunk: int = DEFAULT_CHUNK,
+                               lane_shift: int = 7) -> bytes:
     """A PWBS stream of the given quantised subbands (per component, coding
     order) coded with the given entropy parameters instead of the context
     model's (four-step subbands only)."""
@@ -350,7 +355,8 @@ def encode_symbols_with_params(model: Model, qcomp: list, params: list, *, width
     d32 = f32(1.0) if lossless else f32(1.0 / q)
     return _encode_symbols(model, qcomp, subband_shapes(Hp, Wp, L), width=width,
                            height=height, bitdepth=bitdepth, colour=colour, d32=d32,
-                           lossless=lossless, chunk=chunk, params=params)
+                           lossless=lossless, chunk=chunk, params=params,
+                           lane_shift=lane_shift)
 
 
 def decode_symbols(model: Model, bs: bytes, params: list | None = None):
@@ -367,7 +373,8 @@ def decode_symbols(model: Model, bs: bytes, params: list | None = None):
     Hp = -(-hd["height"] // mult) * mult
     Wp = -(-hd["width"] // mult) * mult
     shapes = subband_shapes(Hp, Wp, L)
-    layout = chunk_layout(shapes, hd["ncomp"], hd["ll_ar"], hd["chunk"], hd["balanced"])
+    layout = chunk_layout(shapes, hd["ncomp"], hd["ll_ar"], hd["chunk"], hd["balanced"],
+                          hd["lane_shift"])
     if len(layout) != hd["n_chunks"]:
         raise ValueError("chunk count mismatch")
     bank = E.cdf_bank().astype(np.int64)

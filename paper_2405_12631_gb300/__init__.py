@@ -69,6 +69,7 @@ _sig = {
     "pw_ctx_create": (C.c_int, [C.c_int, _P, C.c_int, C.POINTER(_P)]),
     "pw_ctx_destroy": (None, [_P]),
     "pw_ctx_precision": (C.c_int, [_P]),
+    "pw_ctx_set_lane_rule": (C.c_int, [_P, C.c_int]),
     "pw_ctx_launch_count": (C.c_uint64, [_P]),
     "pw_model_load": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(_P)]),
     "pw_model_free": (None, [_P]),
@@ -266,6 +267,11 @@ class Codec:
         check(pw_ctx_create(int(device), C.c_void_p(stream or None), int(prec), C.byref(h)))
         self.ctx = h
         self.precision = prec
+
+    def set_lane_rule(self, log2_symbols_per_state: int):
+        """pw_ctx_set_lane_rule: streams this context encodes use one rANS
+        state per 2^s symbols (s in 5..7; default 7)."""
+        check(pw_ctx_set_lane_rule(self.ctx, int(log2_symbols_per_state)))
 
     def close(self):
         if self.ctx:

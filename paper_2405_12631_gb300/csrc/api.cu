@@ -216,6 +216,7 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *co
   ParseExpect ex{};
   ex.width = h0.width; ex.height = h0.height; ex.ncomp = g.nc; ex.levels = g.levels;
   ex.bitdepth = g.bitdepth; ex.colour = g.colour; ex.flags = h0.flags; ex.chunk = g.chunk;
+  ex.lane_byte = h0.lane_shift;
   ex.hash = m.hash;
   DecChunk *dch = reinterpret_cast<DecChunk *>(pl.d_chunks.p);
   double stream_bytes = 0;
@@ -288,6 +289,7 @@ static int check_header_model(pw_ctx *ctx, const Model &m, const StreamHeader &h
     set_last_error("stream was encoded with another precision class"); return PW_EINVAL;
   }
   if (h.T != kT || h.log2m != kLogM || h.lanes != kMaxLanes || h.chunk_symbols == 0 ||
+      (h.lane_shift != 0 && (h.lane_shift < 5 || h.lane_shift > 7)) ||
       (h.ncomp != 1 && h.ncomp != 3) || h.width == 0 || h.height == 0 || h.bitdepth < 1 ||
       h.bitdepth > 16 || h.colour > 3) {
     set_last_error("unsupported stream parameters"); return PW_EUNSUPPORTED;
@@ -298,7 +300,8 @@ static int check_header_model(pw_ctx *ctx, const Model &m, const StreamHeader &h
 static int build_geo(const StreamHeader &h, Geometry &g) {
   g.build((int)h.height, (int)h.width, h.ncomp, h.levels, h.colour, h.bitdepth,
           (h.flags & FLAG_LOSSLESS) ? 1 : 0, (h.flags & FLAG_LL_AR) ? 1 : 0,
-          (int)h.chunk_symbols, (h.flags & FLAG_BALANCED) ? 1 : 0);
+          (int)h.chunk_symbols, (h.flags & FLAG_BALANCED) ? 1 : 0,
+          h.lane_shift ? h.lane_shift : kLaneShift);
   if ((uint64_t)g.chunks.size() * g.nc != h.n_chunks) { set_last_error("chunk count mismatch"); return PW_ECORRUPT; }
   return PW_OK;
 }
@@ -567,6 +570,7 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
     h.bitdepth = (uint8_t)g.bitdepth; h.colour = (uint8_t)g.colour;
     h.delta_l = dl; h.delta_h = dh; h.T = kT; h.log2m = kLogM; h.lanes = kMaxLanes;
     h.chunk_symbols = g.chunk; h.n_chunks = nch; h.model_hash = m.hash;
+    h.lane_shift = (uint8_t)(g.lane_shift == kLaneShift ? 0 : g.lane_shift);
     const uint64_t pb = img_start[b + 1] - img_start[b];
     h.payload_bytes = (uint32_t)pb;
     const size_t total = 64 + 4 * (size_t)(nch + 1) + pb;
@@ -593,7 +597,7 @@ static int encode_planes_dev(pw_ctx *ctx, Model &m, int B, int nc, int H, int W,
   if (!lossless && !(o && o->q > 0.f)) { set_last_error("quantiser step must be > 0"); return PW_EINVAL; }
   const int chunk = (o && o->chunk_symbols > 0) ? o->chunk_symbols : 16384;
   Geometry g;
-  g.build(H, W, nc, m.levels, 3, 8, lossless, m.ll_mode, chunk);
+  g.build(H, W, nc, m.levels, 3, 8, lossless, m.ll_mode, chunk, 1, ctx->lane_shift);
   Plan *pl;
   int s;
   if ((s = get_plan(ctx, m, g, B, "enc", false, &pl))) return s;
@@ -618,8 +622,7 @@ static int image_geo(pw_ctx *ctx, const Model &m, const pw_image &im, const pw_c
   const int colour = im.channels == 1 ? 0 : (lossless ? 2 : 1);
   const int chunk = (o && o->chunk_symbols > 0) ? o->chunk_symbols : 16384;
   g.build(im.height, im.width, im.channels, m.levels, colour, im.bitdepth, lossless, m.ll_mode,
-          chunk);
-  (void)ctx;
+          chunk, 1, ctx->lane_shift);
   return PW_OK;
 }
 
@@ -726,6 +729,15 @@ void pw_ctx_destroy(pw_ctx *c) {
 }
 
 int pw_ctx_precision(const pw_ctx *c) { return c ? c->precision : -1; }
+
+int pw_ctx_set_lane_rule(pw_ctx *c, int log2_symbols_per_state) {
+  if (!c || log2_symbols_per_state < 5 || log2_symbols_per_state > 7) {
+    set_last_error("lane rule: 2^5 .. 2^7 symbols per state");
+    return PW_EINVAL;
+  }
+  c->lane_shift = log2_symbols_per_state;
+  return PW_OK;
+}
 
 int pw_ctx_profile(pw_ctx *c, int enable) {
   if (!c) return PW_EINVAL;
@@ -1340,7 +1352,8 @@ int pw_encode_latent(pw_ctx *c, const pw_model *mm, const int32_t *q, int width,
   if (!lossless && !(o && o->q > 0.f)) { set_last_error("quantiser step must be > 0"); return PW_EINVAL; }
   const int chunk = (o && o->chunk_symbols > 0) ? o->chunk_symbols : 16384;
   Geometry g;
-  g.build(height, width, channels, m.levels, colour, bitdepth, lossless, m.ll_mode, chunk);
+  g.build(height, width, channels, m.levels, colour, bitdepth, lossless, m.ll_mode, chunk, 1,
+          c->lane_shift);
   Plan *pl;
   int s;
   if ((s = get_plan(c, m, g, 1, "lat", false, &pl))) return s;

@@ -22,9 +22,11 @@ static inline void bump(pw_ctx *ctx, int n = 1) { ctx->launches += (uint64_t)n; 
 
 // ---------------------------------------------------------------------------
 void Geometry::build(int H_, int W_, int nc_, int levels_, int colour_, int bitdepth_,
-                     int lossless_, int ll_ar_, int chunk_, int balanced_) {
+                     int lossless_, int ll_ar_, int chunk_, int balanced_,
+                     int lane_shift_) {
   H = H_; W = W_; nc = nc_; levels = levels_; colour = colour_; bitdepth = bitdepth_;
   lossless = lossless_; ll_ar = ll_ar_; chunk = chunk_; balanced = balanced_;
+  lane_shift = lane_shift_;
   const int mult = 1 << levels;
   Hp = (H + mult - 1) / mult * mult;
   Wp = (W + mult - 1) / mult * mult;
@@ -65,13 +67,15 @@ void Geometry::build(int H_, int W_, int nc_, int levels_, int colour_, int bitd
         const int nch = (n + chunk - 1) / chunk;
         for (int j = 0, f = 0; j < nch; ++j) {
           const int cnt = n / nch + (j < n % nch ? 1 : 0);
-          chunks.push_back({i, k, (uint32_t)f, (uint32_t)cnt, (uint16_t)chunk_lanes(cnt)});
+          chunks.push_back({i, k, (uint32_t)f, (uint32_t)cnt,
+                            (uint16_t)chunk_lanes(cnt, lane_shift)});
           f += cnt;
         }
       } else {
         for (int f = 0; f < n; f += chunk) {
           const int cnt = std::min(chunk, n - f);
-          chunks.push_back({i, k, (uint32_t)f, (uint32_t)cnt, (uint16_t)chunk_lanes(cnt)});
+          chunks.push_back({i, k, (uint32_t)f, (uint32_t)cnt,
+                            (uint16_t)chunk_lanes(cnt, lane_shift)});
         }
       }
       group_count[i * 4 + k] = (int)chunks.size() - group_first[i * 4 + k];

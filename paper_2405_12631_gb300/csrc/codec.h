@@ -70,7 +70,8 @@ struct StreamHeader {
   uint32_t chunk_symbols, n_chunks;
   uint64_t model_hash;
   uint32_t payload_bytes;
-  uint8_t reserved[12];
+  uint8_t lane_shift;          // 0: the default 2^7 symbols per state
+  uint8_t reserved[11];
 };
 #pragma pack(pop)
 static_assert(sizeof(StreamHeader) == 64, "stream header is 64 bytes");
@@ -92,6 +93,9 @@ struct Geometry {
   // shorter last one; 1 (balanced, header flag FLAG_BALANCED) = the fewest
   // chunks of at most `chunk` symbols, of equal length to within one
   int balanced = 1;
+  // symbols per interleaved rANS state: 2^lane_shift (5..7; header byte 52,
+  // where 0 stands for the default 7)
+  int lane_shift = kLaneShift;
   int nsb = 13;
   std::vector<int> sh, sw;          // subband sizes in coding order
   std::vector<int64_t> soff;        // per-plane element offset of subband i
@@ -101,7 +105,7 @@ struct Geometry {
   std::vector<int> group_first;     // [sb * 4 + step] first chunk index, or -1
   std::vector<int> group_count;     // [sb * 4 + step]
   void build(int H, int W, int nc, int levels, int colour, int bitdepth, int lossless,
-             int ll_ar, int chunk, int balanced = 1);
+             int ll_ar, int chunk, int balanced = 1, int lane_shift = kLaneShift);
 };
 
 // Device buffers for a batch of planes of one geometry.
@@ -184,6 +188,7 @@ struct pw_ctx {
   uint64_t launches = 0;
   void *plan_cache = nullptr;      // cached workspaces per geometry (api.cu)
   void *prof = nullptr;            // per-kernel-class event timing (prof.cpp)
+  int lane_shift = 7;              // encoders: 2^lane_shift symbols per rANS state
 };
 
 struct pw_model {

@@ -41,7 +41,8 @@ __global__ void k_parse_streams(const uint8_t *const *streams, const uint64_t *l
            s[16] == ex.ncomp && s[17] == ex.levels && s[18] == ex.bitdepth &&
            s[19] == ex.colour && rd16(s + 28) == kT && s[30] == kLogM && s[31] == kMaxLanes &&
            rd32(s + 32) == ex.chunk && rd32(s + 36) == nch &&
-           rd32(s + 40) == (uint32_t)ex.hash && rd32(s + 44) == (uint32_t)(ex.hash >> 32);
+           rd32(s + 40) == (uint32_t)ex.hash && rd32(s + 44) == (uint32_t)(ex.hash >> 32) &&
+           s[52] == ex.lane_byte;
     }
     uint32_t pb = ok ? rd32(s + 48) : 0;
     ok = ok && base + pb <= len;

@@ -9,6 +9,7 @@ struct ParseExpect {
   uint32_t ncomp, levels, bitdepth, colour;
   uint32_t flags, chunk;
   uint64_t hash;
+  uint32_t lane_byte;   // header byte 52 (lane rule) of the batch's streams
 };
 
 // Per-component chunk template on the device: where the chunk's decode

@@ -161,9 +161,11 @@ __host__ __device__ __forceinline__ int step_index(int w, int k, int y, int x) {
   return (y >> 1) * (ne + no) + ((y & 1) ? ne + ((x - ao) >> 2) : ((x - ae) >> 2));
 }
 
-// Interleaved states of a chunk of n symbols (one per 128 symbols, 1..32).
-__host__ __device__ __forceinline__ int chunk_lanes(int n) {
-  int l = n >> 7;
+// Interleaved states of a chunk of n symbols: one per 2^shift symbols
+// (shift 7 by default; the stream header records it), 1..32.
+constexpr int kLaneShift = 7;
+__host__ __device__ __forceinline__ int chunk_lanes(int n, int shift = kLaneShift) {
+  int l = n >> shift;
   return l < 1 ? 1 : (l > kMaxLanes ? kMaxLanes : l);
 }
 

@@ -69,8 +69,8 @@ namespace pw {
 
 static std::string req_key(const Geometry &g) {
   char b[160];
-  snprintf(b, sizeof(b), "%d:%d:%d:%d:%d:%d:%d:%d:%d:%d", g.H, g.W, g.nc, g.levels, g.colour,
-           g.bitdepth, g.lossless, g.ll_ar, g.chunk, g.balanced);
+  snprintf(b, sizeof(b), "%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d", g.H, g.W, g.nc, g.levels, g.colour,
+           g.bitdepth, g.lossless, g.ll_ar, g.chunk, g.balanced, g.lane_shift);
   return b;
 }
 

@@ -229,6 +229,26 @@ def test_decode_oracle_stream(codec, model32):
     assert np.max(np.abs(out.astype(int) - ref.astype(int))) <= 1
 
 
+def test_decode_oracle_stream_with_lane_rule_5(codec, model32):
+    """An oracle stream with one rANS state per 32 symbols (header byte 52)
+    decodes exactly on the GPU when the GPU's indices match the oracle's."""
+    blob, gm, om = model32
+    img = S.gray_sinusoids(48, 64, seed=18)
+    bs = K.encode_image(blob, img, q=8.0, lane_shift=5)
+    assert bs[52] == 5
+    qsb = _oracle_latent(om, img)[0]
+    params = K.context_params_all(om, qsb)
+    mu_o = np.concatenate([p[0].reshape(-1) for p in params])
+    sg_o = np.concatenate([p[1].reshape(-1) for p in params])
+    mu_g, sg_g = codec.context_params(gm, 48, 64, _flat([qsb]))
+    a, b = E.index_decision(mu_g, sg_g), E.index_decision(mu_o, sg_o)
+    diff = (a[0] != b[0]) | (a[1] != b[1]) | (a[2] != b[2])
+    assert not np.any(diff & ~E.near_tie(mu_o, sg_o, TIE_EPS))
+    if np.any(diff):
+        pytest.skip(f"{int(diff.sum())} certified near-tie index differences in this input")
+    assert np.array_equal(codec.decode_symbols(gm, bs), _flat([qsb]))
+
+
 def test_psnr_matches_oracle(codec, model32):
     blob, gm, om = model32
     img = S.rgb_natural(64, 96, seed=9)

@@ -70,13 +70,16 @@ def _gpu_params(codec, model, qsb, shapes):
     return out
 
 
-@pytest.mark.parametrize("prec,kind,q", [("fp8", "rgb", 4.0), ("bf16", "rgb", 8.0),
-                                         ("fp8", "gray", 16.0), ("bf16", "gray", 32.0)])
-def test_index_injection_stream_identical(pw, blob, prec, kind, q):
+@pytest.mark.parametrize("prec,kind,q,ls", [("fp8", "rgb", 4.0, 7), ("bf16", "rgb", 8.0, 7),
+                                            ("fp8", "gray", 16.0, 7), ("bf16", "gray", 32.0, 7),
+                                            ("fp8", "rgb", 8.0, 5)])
+def test_index_injection_stream_identical(pw, blob, prec, kind, q, ls):
+    """ls: log2 of the symbols per interleaved rANS state (7 = default)."""
     img = (S.rgb_natural(H, W, seed=1) if kind == "rgb" else
            S.gray_sinusoids(H, W, seed=3))
     nc = 3 if kind == "rgb" else 1
     codec = pw.Codec(0, prec)
+    codec.set_lane_rule(ls)
     model = codec.load_model(blob)
     bs = codec.encode_image(model, img, q=q)
     shapes = subband_shapes(H, W, 4)
@@ -89,8 +92,10 @@ def test_index_injection_stream_identical(pw, blob, prec, kind, q):
 
     om = K.Model(blob)
     hd = K.parse_header(bs)
+    assert hd["lane_shift"] == ls
     ref = K.encode_symbols_with_params(om, qcomp, params, width=W, height=H, bitdepth=8,
-                                       colour=hd["colour"], q=q, chunk=hd["chunk"])
+                                       colour=hd["colour"], q=q, chunk=hd["chunk"],
+                                       lane_shift=ls)
     assert len(ref) == len(bs), (len(ref), len(bs))
     head_gpu = bytearray(bs[:64])
     head_gpu[6] &= ~0x0C & 0xFF                       # precision-class bits (2-3)
@@ -101,5 +106,5 @@ def test_index_injection_stream_identical(pw, blob, prec, kind, q):
     for c in range(nc):
         for i in range(len(shapes)):
             assert np.array_equal(dec[c][i], qcomp[c][i]), (c, i)
-    print(f"\n{prec} {kind} q={q:g}: {len(bs)} bytes, {hd['n_chunks']} chunks, "
+    print(f"\n{prec} {kind} q={q:g} lane shift {ls}: {len(bs)} bytes, {hd['n_chunks']} chunks, "
           f"byte-identical to the oracle coder")

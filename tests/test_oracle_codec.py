@@ -186,3 +186,23 @@ def test_post_processing_single_tap_closed_form():
             left = x[yy, xx - 1] if xx >= 1 else 0.0
             want = x[yy, xx] + c * np.tanh(np.tanh(a * left + b1) + b2) + b3
             assert abs(got[yy, xx] - want) < 1e-9
+
+
+def test_lane_rule_option_round_trips_and_costs_rate():
+    """One rANS state per 32 symbols instead of 128 (header byte 52 = 5):
+    more states per small chunk (each a 4-byte flush), same symbols."""
+    blob = _blob(0)
+    model = K.Model(blob)
+    img = S.gray_sinusoids(64, 96, seed=10)
+    planes, colour = K.colour_forward(img, False, 8)
+    b7, q7 = K.encode_planes(model, planes, width=96, height=64, bitdepth=8, colour=colour, q=8.0)
+    b5, q5 = K.encode_planes(model, planes, width=96, height=64, bitdepth=8, colour=colour, q=8.0,
+                             lane_shift=5)
+    assert b7[52] == 0 and b5[52] == 5 and K.parse_header(b5)["lane_shift"] == 5
+    hd, dec = K.decode_symbols(model, b5)
+    for a, b in zip(q5[0], dec[0]):
+        assert np.array_equal(a, b)
+    lay7 = K.chunk_layout([(32, 48, 1)], 1, False, 16384)
+    lay5 = K.chunk_layout([(32, 48, 1)], 1, False, 16384, True, 5)
+    assert [c[5] for c in lay7] == [3] * 4 and [c[5] for c in lay5] == [12] * 4
+    assert len(b5) > len(b7)
