@@ -597,61 +597,86 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
     int acc = 0;
     uint32_t aphase = 0;
     const int G = a.out_G;
-    TileIter ti(cta, a.tiles_x, a.tiles_y);
-    for (int t = cta; t < a.tiles;
-         t += nctas, ti.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y)) {
-      const int tx = ti.tx, ty = ti.ty, p = ti.p;
-      int y, x;
+    const int n0 = nb * NCTA + col0;   // first output column handled here
+    const int64_t hw = (int64_t)a.H * a.W;
+    // output position of this thread in tile tt
+    auto tile_pos = [&](const TileIter &tt, int &y, int &x) {
       if constexpr (EPI == TE_HEADC) {
-        const int par = ty & 1;
-        y = 2 * ((ty >> 1) * a.cR + (m >> a.cJlog)) + par;
-        x = step_phase(a.step, par) + 4 * (tx * a.cJ + (m & (a.cJ - 1)));
+        const int par = tt.ty & 1;
+        y = 2 * ((tt.ty >> 1) * a.cR + (m >> a.cJlog)) + par;
+        x = step_phase(a.step, par) + 4 * (tt.tx * a.cJ + (m & (a.cJ - 1)));
       } else {
-        y = ty * kTileH + r;
-        x = tx * kTileW + c;
+        y = tt.ty * kTileH + r;
+        x = tt.tx * kTileW + c;
       }
-      const bool valid = y < a.H && x < a.W;
-      const int64_t hw = (int64_t)a.H * a.W;
+    };
+    // Global operands of the epilogue (cell state, residual) do not depend
+    // on the accumulator: they are loaded one tile ahead, so that their
+    // latency overlaps the processing of the tile before (the epilogue, not
+    // the MMAs, is the slower side of these kernels).
+    constexpr int NPF = (EPI == TE_LSTM) ? NH / 4 : 8;
+    static_assert(NPF % 8 == 0, "cell state in 8-channel groups");
+    constexpr int NRES = (HEADK || STORE) ? NH / 8 : 1;
+    // (the cell state stays packed BF16 until it is used: registers are
+    // scarce in the ConvLSTM epilogue)
+    constexpr int NCP = NPF / 8;
+    auto load_ops = [&](const TileIter &tt, uint4 *cpo, uint4 *preso) {
+      int y, x;
+      tile_pos(tt, y, x);
+      if (!(work && y < a.H && x < a.W)) return;
+      const int p = tt.p;
       const int64_t pix = (int64_t)y * a.W + x;
-      const int n0 = nb * NCTA + col0;   // first output column handled here
-      // Global operands of the epilogue do not depend on the accumulator:
-      // load them before waiting so their latency overlaps the MMAs.
-      constexpr int NPF = (EPI == TE_LSTM) ? NH / 4 : 8;
-      static_assert(NPF % 8 == 0, "cell state in 8-channel groups");
-      float pf[NPF];
-      uint4 pres[(HEADK || STORE) ? NH / 8 : 1];
-      if (work && valid) {
-        if (EPI == TE_LSTM) {
-          const int Hp = a.H >> a.up, Wp = a.W >> a.up;
-          const int64_t ppix = ((int64_t)p * Hp + (y >> a.up)) * Wp + (x >> a.up);
+      if (EPI == TE_LSTM) {
+        const int Hp = a.H >> a.up, Wp = a.W >> a.up;
+        const int64_t ppix = ((int64_t)p * Hp + (y >> a.up)) * Wp + (x >> a.up);
 #pragma unroll
-          for (int k = 0; k < NPF; k += 8) {
-            if (a.first) {
+        for (int k = 0; k < NCP; ++k)
+          cpo[k] = a.first ? make_uint4(0u, 0u, 0u, 0u)
+                           : __ldg(reinterpret_cast<const uint4 *>(a.c_prev + ppix * a.C + n0 / 4 + 8 * k));
+      } else if (HEADK || (STORE && a.res)) {
+        const bool need = STORE ||
+                          (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step);
+        if (need) {
+          if (HEADK && a.res_compact_n) {
+            const int64_t qn = step_index(a.W, a.step, y, x);
 #pragma unroll
-              for (int e = 0; e < 8; ++e) pf[k + e] = 0.f;
-            } else {
-              const uint4 c8 = __ldg(reinterpret_cast<const uint4 *>(a.c_prev + ppix * a.C + n0 / 4 + k));
-              load_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(&c8), pf + k);
-            }
-          }
-        } else if (HEADK || (STORE && a.res)) {
-          const bool need = STORE ||
-                            (a.compact_n ? pix < a.compact_n : step_of(y, x) == a.step);
-          if (need) {
-            if (HEADK && a.res_compact_n) {
-              const int64_t qn = step_index(a.W, a.step, y, x);
+            for (int g = 0; g < NRES; ++g)
+              preso[g] = __ldg(reinterpret_cast<const uint4 *>(
+                  a.res + (((int64_t)p * a.res_G + (n0 >> 3) + g) * a.res_compact_n + qn) * 8));
+          } else {
 #pragma unroll
-              for (int g = 0; g < NH / 8; ++g)
-                pres[g] = __ldg(reinterpret_cast<const uint4 *>(
-                    a.res + (((int64_t)p * a.res_G + (n0 >> 3) + g) * a.res_compact_n + qn) * 8));
-            } else {
-#pragma unroll
-              for (int g = 0; g < NH / 8; ++g)
-                pres[g] = __ldg(reinterpret_cast<const uint4 *>(
-                    a.res + (((int64_t)p * a.res_G + a.res_goff + (n0 >> 3) + g) * hw + pix) * 8));
-            }
+            for (int g = 0; g < NRES; ++g)
+              preso[g] = __ldg(reinterpret_cast<const uint4 *>(
+                  a.res + (((int64_t)p * a.res_G + a.res_goff + (n0 >> 3) + g) * hw + pix) * 8));
           }
         }
+      }
+    };
+    TileIter ti(cta, a.tiles_x, a.tiles_y);
+    uint4 cpq[NCP];      // operands of the next tile to process
+    uint4 presq[NRES];
+    // only the epilogues that read such operands pay for the lookahead (the
+    // z conv never has a residual, conv 1 and most plain stores neither)
+    constexpr bool PREF = EPI == TE_LSTM || HEADK || EPI == TE_STORE;
+    const bool has_ops = PREF && (EPI != TE_STORE || a.res != nullptr);
+    if (has_ops && cta < a.tiles) load_ops(ti, cpq, presq);
+    for (int t = cta; t < a.tiles;
+         t += nctas, ti.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y)) {
+      const int p = ti.p;
+      int y, x;
+      tile_pos(ti, y, x);
+      const bool valid = y < a.H && x < a.W;
+      const int64_t pix = (int64_t)y * a.W + x;
+      uint4 cpk[NCP];
+      uint4 pres[NRES];
+#pragma unroll
+      for (int k = 0; k < NCP; ++k) cpk[k] = cpq[k];
+#pragma unroll
+      for (int g = 0; g < NRES; ++g) pres[g] = presq[g];
+      if (has_ops && t + nctas < a.tiles) {
+        TileIter tn = ti;
+        tn.next(a.step_dx, a.step_dy, a.step_dp, a.tiles_x, a.tiles_y);
+        load_ops(tn, cpq, presq);
       }
       // warp-uniform wait: lane 0 decides, the others then observe the
       // completed phase themselves (their try_wait succeeds at once)
@@ -746,7 +771,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       } else if (EPI == TE_LSTM) {
         // column 4 * ch + gate (i, f, o, g) within the CTA's N block
         const int ch0 = n0 / 4;
-        const float *cp = pf;
+        float cp[NPF];
+#pragma unroll
+        for (int k = 0; k < NCP; ++k)
+          load_bf16x8(reinterpret_cast<const __nv_bfloat16 *>(&cpk[k]), cp + 8 * k);
         float hv[NH / 4], cn[NH / 4];
 #pragma unroll
         for (int k = 0; k < NH / 4; ++k) {
