@@ -358,18 +358,22 @@ const char *pw_last_error(void);
 uint64_t pw_ctx_launch_count(const pw_ctx *ctx);
 
 /* Autotuner of the tensor-core convolutions. For every convolution variant
- * and size class (log2 of its tile count) the MMA issue schedule (one tile
- * or two interleaved tiles per round) is chosen by sampling both candidates
- * round robin on the first real launches of the class in the process
- * (CUDA events read back without synchronising, 3 samples each) and
- * keeping the faster median; results never depend on the schedule.
+ * and size class (log2 of its tile count) it picks, among up to four
+ * candidates, the MMA issue schedule (one tile or two interleaved tiles per
+ * round) crossed with the pipeline shape (the default or a shallower
+ * pipeline for the plain convolutions; for the compact head, the tile shape
+ * with the fewest or the second-fewest tiles), by sampling the candidates
+ * round robin on the first real launches of the class in the process (CUDA
+ * events read back without synchronising, 3 samples each) and keeping the
+ * fastest median; results never depend on the choice.
  * pw_autotune(0 / 1) disables / enables sampling of classes not tuned yet
  * (default on; disabled classes use the default schedule) and returns the
  * previous setting. pw_autotune_report writes one line per tuned class
- * ("ks kb ncta epilogue fp8 log2tiles pairs t_single t_paired", median sample
- * times in microseconds, -1 = no sample; epilogue 0 store, 1 ConvLSTM gates,
- * 2 head, 3 compact head, 4 store with a 16-channel BF16 input block) into buf (NUL-terminated,
- * truncated to n) and returns the full length. */
+ * ("ks kb ncta epilogue fp8 log2tiles choice t0 t1 t2 t3": choice bit 0 =
+ * paired issue, bit 1 = alternative shape; t = median sample time of each
+ * candidate in microseconds, -1 = not sampled; epilogue 0 store, 1 ConvLSTM
+ * gates, 2 head, 3 compact head, 4 store with a 16-channel BF16 input block)
+ * into buf (NUL-terminated, truncated to n) and returns the full length. */
 int pw_autotune(int enable);
 int pw_autotune_report(char *buf, size_t n);
 

@@ -533,12 +533,14 @@ def autotune_report() -> list:
     n = pw_autotune_report(None, 0)
     buf = C.create_string_buffer(n + 1)
     pw_autotune_report(buf, n + 1)
-    keys = ("ks", "kb", "ncta", "epi", "fp8", "log2tiles", "pairs")
+    keys = ("ks", "kb", "ncta", "epi", "fp8", "log2tiles", "choice")
     out = []
     for line in buf.value.decode().splitlines():
         v = line.split()
         d = {k: int(x) for k, x in zip(keys, v[:7])}
-        d["us"] = [float(x) for x in v[7:9]]
+        d["pairs"] = d["choice"] & 1
+        d["shape"] = d["choice"] >> 1
+        d["us"] = [float(x) for x in v[7:11]]
         out.append(d)
     return out
 

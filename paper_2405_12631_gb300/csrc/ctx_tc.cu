@@ -1092,16 +1092,21 @@ static bool headc_ok(int h, int w) { return h >= 4 && w >= 8; }
 // fastest median wins (the median ignores a one-off outlier such as the
 // first launch of a kernel, which loads its module). Results do not depend
 // on the schedule.
-constexpr int kTuneCand = 2, kSamples = 3;
+// Candidates: bit 0 = paired MMA issue, bit 1 = the alternative pipeline
+// shape (a shallower pipeline for the plain convolutions, the second-best
+// tile shape for the compact head).
+constexpr int kTuneCand = 4, kSamples = 3;
 struct TuneChoice {
   int pairs = 0;
+  int shape = 0;
+  int cand() const { return pairs | (shape << 1); }
 };
 struct TuneEntry {
   bool tuned = false;
   TuneChoice choice;
   int next = 0;                        // candidate of the next sample
-  int issued[kTuneCand] = {0, 0};      // samples launched
-  int n[kTuneCand] = {0, 0};           // samples read back
+  int issued[kTuneCand] = {};          // samples launched
+  int n[kTuneCand] = {};               // samples read back
   float us[kTuneCand][kSamples] = {};  // their times
   double median(int c) const {
     if (n[c] == 0) return -1.0;
@@ -1147,7 +1152,11 @@ static void tune_poll_locked() {
       if (done) {
         double best = 1e30;
         for (int c = 0; c < kTuneCand; ++c)
-          if (t.n[c] && t.median(c) < best) { best = t.median(c); t.choice.pairs = c; }
+          if (t.n[c] && t.median(c) < best) {
+            best = t.median(c);
+            t.choice.pairs = c & 1;
+            t.choice.shape = c >> 1;
+          }
         t.tuned = true;
       }
     } else {
@@ -1161,8 +1170,8 @@ static void tune_poll_locked() {
 
 // The schedule of the next launch of a class. While the class is being tuned
 // (sample = true) the launch is a sample of candidate `cand`.
-static TuneChoice tune_next(uint64_t key, bool can_pair, cudaStream_t st, bool &sample,
-                            int &cand) {
+static TuneChoice tune_next(uint64_t key, bool can_pair, bool has_alt, cudaStream_t st,
+                            bool &sample, int &cand) {
   TuneChoice c;
   c.pairs = ((key >> 32) & 0xFF) == 3 && ((key >> 9) & 1) && can_pair;  // default
   sample = false;
@@ -1171,6 +1180,7 @@ static TuneChoice tune_next(uint64_t key, bool can_pair, cudaStream_t st, bool &
   TuneEntry &t = g_tune[key];
   if (t.tuned) {
     c.pairs = t.choice.pairs && can_pair;
+    c.shape = t.choice.shape && has_alt;
     return c;
   }
   if (!g_tune_on.load()) return c;
@@ -1179,17 +1189,21 @@ static TuneChoice tune_next(uint64_t key, bool can_pair, cudaStream_t st, bool &
     cudaGetLastError();
     return c;
   }
-  const int ncand = can_pair ? 2 : 1;
-  if (ncand == 1) {  // nothing to choose
+  auto valid = [&](int k) { return (!(k & 1) || can_pair) && (!(k & 2) || has_alt); };
+  int nvalid = 0;
+  for (int k = 0; k < kTuneCand; ++k) nvalid += valid(k) ? 1 : 0;
+  if (nvalid == 1) {  // nothing to choose
     t.tuned = true;
-    t.choice.pairs = 0;
+    t.choice = TuneChoice{};
     return c;
   }
+  while (!valid(t.next)) t.next = (t.next + 1) % kTuneCand;
   cand = t.next;
   if (t.issued[cand] >= kSamples) return c;  // enough in flight; wait for read-back
-  t.next = (t.next + 1) % ncand;
+  do { t.next = (t.next + 1) % kTuneCand; } while (!valid(t.next));
   t.issued[cand] += 1;
-  c.pairs = cand;
+  c.pairs = cand & 1;
+  c.shape = cand >> 1;
   sample = true;
   return c;
 }
@@ -1204,9 +1218,10 @@ int tune_set_enabled(int on) {
   g_tune_on.store(on ? 1 : 0);
   return old;
 }
-// One line per tuned class: "ks kb ncta epi f8 log2tiles pairs t0 t1"
-// (median sampled time in microseconds of single / paired issue, -1 = no
-// sample).
+// One line per tuned class: "ks kb ncta epi f8 log2tiles choice t0 t1 t2 t3"
+// (choice = the kept candidate, bit 0 paired issue, bit 1 alternative
+// pipeline shape; t = median sampled time of each candidate in microseconds,
+// -1 = not sampled).
 std::string tune_report() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_poll_locked();
@@ -1216,10 +1231,10 @@ std::string tune_report() {
     if (!kv.second.tuned) continue;
     const uint64_t k = kv.first;
     const TuneEntry &t = kv.second;
-    snprintf(line, sizeof(line), "%d %d %d %d %d %d %d %.1f %.1f\n", (int)((k >> 32) & 0xFF),
-             (int)((k >> 24) & 0xFF), (int)((k >> 14) & 0x3FF), (int)((k >> 10) & 0xF),
-             (int)((k >> 9) & 1), (int)(k & 0x1FF), t.choice.pairs,
-             t.median(0), t.median(1));
+    snprintf(line, sizeof(line), "%d %d %d %d %d %d %d %.1f %.1f %.1f %.1f\n",
+             (int)((k >> 32) & 0xFF), (int)((k >> 24) & 0xFF), (int)((k >> 14) & 0x3FF),
+             (int)((k >> 10) & 0xF), (int)((k >> 9) & 1), (int)(k & 0x1FF), t.choice.cand(),
+             t.median(0), t.median(1), t.median(2), t.median(3));
     out += line;
   }
   return out;
@@ -1284,17 +1299,28 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     return PW_EUNSUPPORTED;
   }
   const bool hc = a.epi == TE_HEADC;
+  // compact head: tiles of R rows of one parity x J step positions. The
+  // shapes with the fewest and the second-fewest tiles (ties: the wider one)
+  // are the tuner's two shape candidates.
+  int lj_best = -1, lj_alt = -1;
+  int npos = 0, nrows = 0;
   if (hc) {
-    // compact head: tiles of R rows of one parity x J step positions; the
-    // shape with the fewest tiles (ties: the wider one)
-    const int npos = std::max(row_count(W, step_phase(a.step, 0)), row_count(W, step_phase(a.step, 1)));
-    const int nrows = (H + 1) / 2;
-    int best = -1;
+    npos = std::max(row_count(W, step_phase(a.step, 0)), row_count(W, step_phase(a.step, 1)));
+    nrows = (H + 1) / 2;
+    int best = -1, second = -1;
     for (int lj = 3; lj <= 7; ++lj) {
       const int J = 1 << lj, Rr = 128 / J;
       const int n = ((npos + J - 1) / J) * ((nrows + Rr - 1) / Rr);
-      if (best < 0 || n <= best) { best = n; a.cJlog = lj; }
+      if (best < 0 || n <= best) {
+        second = best; lj_alt = lj_best;
+        best = n; lj_best = lj;
+      } else if (second < 0 || n <= second) {
+        second = n; lj_alt = lj;
+      }
     }
+  }
+  auto set_hc_shape = [&](int lj) {
+    a.cJlog = lj;
     a.cJ = 1 << a.cJlog; a.cR = 128 / a.cJ;
     a.tiles_x = (npos + a.cJ - 1) / a.cJ;
     a.tiles_y = 2 * ((nrows + a.cR - 1) / a.cR);
@@ -1306,16 +1332,34 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     a.tps = room >= 3 * 3 * (size_t)tapb ? 3 : 1;
     a.nkb = 9 / a.tps;                           // stages per tile
     a.stage_bytes = (uint32_t)a.tps * tapb;
-  }
+  };
+  if (hc) set_hc_shape(lj_best);
   const size_t fixed = kConvHeader + (a.wv_bytes + a.w_bytes + 1023) / 1024 * 1024;
   const size_t maxsm = 227 * 1024;
-  int stages = (int)((maxsm - fixed) / a.stage_bytes);
-  // deep pipelines keep enough bytes in flight for the HBM-bound 1x1 convs
-  const int smax = hc ? std::min(kMaxStages, 2 * a.nkb + 2) : (cv.ks == 1 ? 16 : 6);
-  stages = stages > smax ? smax : stages;
-  if (stages < 2) { set_last_error("tensor-core conv does not fit in shared memory"); return PW_EUNSUPPORTED; }
-  a.stages = stages;
-  const size_t smem = fixed + (size_t)stages * a.stage_bytes;
+  auto depth = [&](int cap) {
+    const int n = (int)((maxsm - fixed) / a.stage_bytes);
+    return n > cap ? cap : n;
+  };
+  // deep pipelines keep enough bytes in flight for the HBM-bound 1x1 convs;
+  // the alternative shape of the plain convs is a shallower pipeline
+  const int st_def = depth(hc ? std::min(kMaxStages, 2 * a.nkb + 2) : (cv.ks == 1 ? 16 : 6));
+  if (st_def < 2) { set_last_error("tensor-core conv does not fit in shared memory"); return PW_EUNSUPPORTED; }
+  int st_alt = -1;
+  if (!hc) {
+    const int v = depth(cv.ks == 1 ? 8 : 4);
+    if (v >= 2 && v != st_def) st_alt = v;
+  }
+  const bool has_alt = hc ? lj_alt >= 0 : st_alt >= 0;
+  // tuning class: the variant (epilogue 4 = a plain store with a v block,
+  // the steps 2-4 z conv) and the size (tiles of the default shape)
+  const uint64_t key = tune_key(cv, a.epi, a.tiles);
+  bool sample = false;
+  int cand = 0;
+  const TuneChoice ch = tune_next(key, true, has_alt, ctx->stream, sample, cand);
+  a.pairs = ch.pairs;
+  if (ch.shape && hc) set_hc_shape(lj_alt);
+  a.stages = (ch.shape && !hc) ? st_alt : st_def;
+  const size_t smem = fixed + (size_t)a.stages * a.stage_bytes;
   CUtensorMap map, map1;
   int s;
   if (hc) {
@@ -1381,13 +1425,6 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
     set_last_error("no tensor-core conv for this shape");
     return PW_EUNSUPPORTED;
   };
-  // tuning class: the variant (epilogue 4 = a plain store with a v block,
-  // the steps 2-4 z conv) and the size
-  const uint64_t key = tune_key(cv, a.epi, a.tiles);
-  bool sample = false;
-  int cand = 0;
-  const TuneChoice ch = tune_next(key, a.stages >= 2, st, sample, cand);
-  a.pairs = ch.pairs;
   if (!sample) return launch(a, 1);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);

@@ -1,7 +1,8 @@
 """Autotuner of the tensor-core convolutions: encoding and decoding with
 tuning disabled (default schedules) and enabled (candidate schedules sampled
-on the real launches) give bit-identical streams and images, and every tuned
-class keeps the faster of its sampled candidates."""
+on the real launches: one or two tiles per MMA round, default or
+alternative pipeline shape) give bit-identical streams and images, and
+every tuned class keeps the fastest of its sampled candidates."""
 import numpy as np
 import pytest
 
@@ -37,8 +38,10 @@ def test_autotune_does_not_change_results(pw, prec):
     rep = pw.autotune_report()
     assert rep, "no convolution class was tuned"
     for e in rep:
-        t = e["us"]
-        if t[0] >= 0 and t[1] >= 0:
-            assert t[e["pairs"]] == min(t)
+        sampled = [v for v in e["us"] if v >= 0]
+        if len(sampled) >= 2:
+            assert e["us"][e["choice"]] == min(sampled)
+    print("\n" + "\n".join(f"{e['ks']}x{e['ks']} epi {e['epi']} fp8 {e['fp8']} 2^{e['log2tiles']} "
+                             f"tiles: choice {e['choice']} us {e['us']}" for e in rep))
     model.close()
     codec.close()
