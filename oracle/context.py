@@ -119,14 +119,10 @@ class ContextModel:
         return h, c
 
     # --- context fusion ----------------------------------------------------
-    def step_params(self, k: int, s: np.ndarray, l: np.ndarray, ns: str):
-        """Entropy parameters (mu, sigma) of step k over the whole subband.
-
-        s is the current subband (only positions of steps < k are read: the
-        rest is masked to zero here); l the long-term context [H, W, C];
-        ns selects the net set ("sb" for subbands 2..13, "ll" for the
-        four-step LL model). Returns two [H, W] arrays.
-        """
+    def step_head(self, k: int, s: np.ndarray, l: np.ndarray, ns: str):
+        """Raw head outputs of step k over the whole subband, [H, W, nh]
+        (nh = 2: Laplace mean and scale pre-activation; 9: the logistic
+        mixture's 3 weight logits, 3 means, 3 scale pre-activations)."""
         t = self.t
         p = f"{ns}.s{k}."
         if k == 0:
@@ -143,7 +139,17 @@ class ContextModel:
             z = conv1x1(np.concatenate([a, l], axis=2), t[p + "wz"], t[p + "bz"])
             u = lrelu(conv2d(z, t[p + "w1"], t[p + "b1"]))
             z = z + conv2d(u, t[p + "w2"], t[p + "b2"])
-        out = conv1x1(z, t[p + "wh"], t[p + "bh"])
+        return conv1x1(z, t[p + "wh"], t[p + "bh"])
+
+    def step_params(self, k: int, s: np.ndarray, l: np.ndarray, ns: str):
+        """Entropy parameters (mu, sigma) of step k over the whole subband.
+
+        s is the current subband (only positions of steps < k are read: the
+        rest is masked to zero here); l the long-term context [H, W, C];
+        ns selects the net set ("sb" for subbands 2..13, "ll" for the
+        four-step LL model). Returns two [H, W] arrays.
+        """
+        out = self.step_head(k, s, l, ns)
         return out[:, :, 0], softplus(out[:, :, 1])
 
     # --- autoregressive LL ---------------------------------------------------

@@ -187,3 +187,128 @@ def laplace_probs64(phi: int, j: int) -> np.ndarray:
     p[1:-1] = np.diff(F)
     p[-1] = 1.0 - F[-1]
     return p
+
+
+# ---------------------------------------------------------------------------
+# Logistic mixture with K = 3 components (the probability model the batched
+# single-image configuration names; the paper's own model is the Laplace
+# above). The head gives per position 9 values: weight logits w_k, means
+# mu_k and scale pre-activations rho_k (scale softplus(rho_k)). As for the
+# Laplace model, the parameters are first reduced to integers by an FP32
+# decision, and the symbol's table is a function of those integers alone:
+#   a    = the first k with the largest w_k, ctr = rint(mu_a) (|t| <= 2^23),
+#   q_k  = clamp(rint(8 (mu_k - ctr)), -255, 255)   mean offset in 1/8,
+#   j_k  = the scale bin of softplus(rho_k)          (as sigma_bin),
+#   g_k  = clamp(rint(4 (w_k - w_a)), -31, 0)       log-weight in 1/4.
+# Table (FP32, exact IEEE operations in this order): m_k = q_k / 8,
+# 1/b_k with b_k = sigma_of_bin(j_k), weights om_k = exp32(g_k / 4),
+# W = (om_0 + om_1) + om_2; at the 126 symbol edges u (as for the Laplace
+# tables) F(u) = ((om_0 s_0 + om_1 s_1) + om_2 s_2) / W with
+# s_k = sigmoid((u - m_k) / b_k) = 1 / (1 + exp32(-z)) for z >= 0 and
+# exp32(z) / (1 + exp32(z)) for z < 0; then the probabilities, frequencies
+# and remainder exactly as cdf_table does.
+MIX_K = 3
+
+
+def mix_decision(head):
+    """(ctr, q, j, g) from head outputs [..., 9]: ctr [...] int, q, j, g
+    [..., 3] int; decided in FP32 (head values rounded to float32 first)."""
+    h = np.asarray(head, dtype=np.float64)
+    h32 = h.astype(f32)
+    w, mu = h32[..., 0:3], h32[..., 3:6]
+    a = np.argmax(w, axis=-1)
+    wa = np.take_along_axis(w, a[..., None], -1)
+    mua = np.take_along_axis(mu, a[..., None], -1)[..., 0]
+    t = np.rint(mua).astype(np.float64)
+    ctr = np.clip(t, -(1 << 23), 1 << 23).astype(np.int64)
+    d = (mu - ctr.astype(f32)[..., None]).astype(f32)
+    q = np.clip(np.rint((d * f32(8.0)).astype(f32)), -255, 255).astype(np.int64)
+    dw = (w - wa).astype(f32)
+    g = np.clip(np.rint((dw * f32(4.0)).astype(f32)), -31, 0).astype(np.int64)
+    rho = h[..., 6:9]
+    sg = np.where(rho > 20.0, rho, np.log1p(np.exp(np.minimum(rho, 20.0))))
+    j = sigma_bin(sg.astype(f32))
+    return ctr, q, j, g
+
+
+def _sigmoid32(z):
+    z = np.asarray(z, dtype=f32)
+    e_pos = exp32(np.where(z >= 0, -z, f32(0.0)).astype(f32))
+    e_neg = exp32(np.where(z < 0, z, f32(0.0)).astype(f32))
+    s_pos = (f32(1.0) / (f32(1.0) + e_pos).astype(f32)).astype(f32)
+    s_neg = (e_neg / (f32(1.0) + e_neg).astype(f32)).astype(f32)
+    return np.where(z >= 0, s_pos, s_neg).astype(f32)
+
+
+def mix_tables(q, j, g) -> np.ndarray:
+    """Cumulative frequencies [N, NSYM + 1] (uint32) of N mixture keys
+    (q, j, g: [N, 3] ints), each built as the header describes."""
+    q = np.asarray(q, dtype=np.int64).reshape(-1, MIX_K)
+    j = np.asarray(j, dtype=np.int64).reshape(-1, MIX_K)
+    g = np.asarray(g, dtype=np.int64).reshape(-1, MIX_K)
+    N = q.shape[0]
+    m = (q.astype(f32) / f32(8.0)).astype(f32)                       # [N, K]
+    inv_b = (f32(1.0) / sigma_of_bin(j)).astype(f32)                 # [N, K]
+    om = exp32((g.astype(f32) * f32(0.25)).astype(f32))              # [N, K]
+    W = ((om[:, 0] + om[:, 1]).astype(f32) + om[:, 2]).astype(f32)  # [N]
+    u = (np.arange(NSYM - 1, dtype=f32) - f32(T + 0.5)).astype(f32)  # [E]
+    acc = None
+    for k in range(MIX_K):
+        z = ((u[None, :] - m[:, k:k + 1]).astype(f32) * inv_b[:, k:k + 1]).astype(f32)
+        term = (om[:, k:k + 1] * _sigmoid32(z)).astype(f32)
+        acc = term if acc is None else (acc + term).astype(f32)
+    F = (acc / W[:, None]).astype(f32)                               # [N, E]
+    p = np.empty((N, NSYM), dtype=f32)
+    p[:, 0] = F[:, 0]
+    p[:, 1:NSYM - 1] = (F[:, 1:] - F[:, :-1]).astype(f32)
+    p[:, NSYM - 1] = (f32(1.0) - F[:, -1]).astype(f32)
+    p = np.maximum(p, f32(0.0))
+    f = 1 + np.floor((p * f32(M - NSYM)).astype(f32)).astype(np.int64)
+    rem = M - f.sum(axis=1)
+    f[np.arange(N), np.argmax(f, axis=1)] += rem
+    cdf = np.zeros((N, NSYM + 1), dtype=np.int64)
+    cdf[:, 1:] = np.cumsum(f, axis=1)
+    assert np.all(cdf[:, -1] == M)
+    return cdf.astype(np.uint32)
+
+
+def mix_table(q, j, g) -> np.ndarray:
+    """The table of one key (three ints each)."""
+    return mix_tables([q], [j], [g])[0]
+
+
+def mix_probs64(q, j, g) -> np.ndarray:
+    """FP64 symbol probabilities of one mixture key (for the pins)."""
+    om = np.exp(np.asarray(g, dtype=np.float64) / 4.0)
+    om = om / om.sum()
+    edges = np.arange(NSYM - 1) - (T + 0.5)
+    F = np.zeros(NSYM - 1)
+    for k in range(MIX_K):
+        b = float(sigma_of_bin(int(j[k])))
+        F += om[k] / (1.0 + np.exp(-(edges - q[k] / 8.0) / b))
+    p = np.empty(NSYM)
+    p[0] = F[0]
+    p[1:-1] = np.diff(F)
+    p[-1] = 1.0 - F[-1]
+    return p
+
+
+def mix_near_tie(head, eps: float):
+    """True where an FP64 head output lies within relative eps of one of the
+    mixture decision's boundaries (the argmax, rint of mu_a, of 8 (mu_k -
+    ctr) and of 4 (w_k - w_a), or a scale-bin edge)."""
+    h = np.asarray(head, dtype=np.float64)
+    w, mu, rho = h[..., 0:3], h[..., 3:6], h[..., 6:9]
+    srt = np.sort(w, axis=-1)
+    tie = np.abs(srt[..., 2] - srt[..., 1]) <= eps * np.maximum(np.abs(srt[..., 2]), 1.0)
+    a = np.argmax(w, axis=-1)
+    mua = np.take_along_axis(mu, a[..., None], -1)[..., 0]
+    wa = np.take_along_axis(w, a[..., None], -1)
+    half = lambda v: np.abs(v - (np.floor(v) + 0.5)) <= eps * np.maximum(np.abs(v), 1.0)
+    tie |= half(mua)
+    ctr = np.rint(mua)
+    tie |= np.any(half(8.0 * (mu - ctr[..., None])), axis=-1)
+    tie |= np.any(half(4.0 * (w - wa)), axis=-1)
+    sg = np.where(rho > 20.0, rho, np.log1p(np.exp(np.minimum(rho, 20.0))))
+    tie |= np.any(near_tie(np.zeros_like(sg), sg, eps), axis=-1)   # scale-bin edges
+    return tie

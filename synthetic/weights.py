@@ -39,6 +39,7 @@ class ModelConfig:
     F: int = 16
     ll_mode: int = 0  # 0 four-step LL, 1 autoregressive LL
     post: int = 0     # 1: the blob carries a post-processing CNN ("post.*")
+    prob: int = 0     # 0: Laplace heads (2 outputs), 1: logistic mixture K = 3 (9)
 
 
 def tensor_specs(cfg: ModelConfig):
@@ -52,8 +53,13 @@ def tensor_specs(cfg: ModelConfig):
     (2C->4C, 3x3, gate order i, f, o, g). Context fusion nets for subbands
     2..13 ("sb"), and either four-step nets for LL ("ll", ll_mode 0) or the
     autoregressive LL model ("ar", ll_mode 1). 1x1 weights are [Cout, Cin].
+    Heads have 2 outputs (Laplace mean, scale pre-activation) or, with
+    cfg.prob = 1 (four-step LL only), 9 (logistic mixture: 3 weight logits,
+    3 means, 3 scale pre-activations).
     """
     C, F = cfg.C, cfg.F
+    NH = 9 if cfg.prob else 2
+    assert not (cfg.prob and cfg.ll_mode), "mixture heads need the four-step LL model"
     s = []
     for d in ("row", "col"):
         for op in ("P", "U"):
@@ -82,14 +88,14 @@ def tensor_specs(cfg: ModelConfig):
               (p + "w2", (C, C)), (p + "b2", (C,)),
               (p + "w3", (2 * C, C)), (p + "b3", (2 * C,)),
               (p + "w4", (C, 2 * C)), (p + "b4", (C,)),
-              (p + "wh", (2, C)), (p + "bh", (2,))]
+              (p + "wh", (NH, C)), (p + "bh", (NH,))]
         for k in (1, 2, 3):
             p = f"{ns}.s{k}."
             s += [(p + "wa", (C, 1, 3, 3)), (p + "ba", (C,)),
                   (p + "wz", (C, 2 * C)), (p + "bz", (C,)),
                   (p + "w1", (C, C, 3, 3)), (p + "b1", (C,)),
                   (p + "w2", (C, C, 3, 3)), (p + "b2", (C,)),
-                  (p + "wh", (2, C)), (p + "bh", (2,))]
+                  (p + "wh", (NH, C)), (p + "bh", (NH,))]
     if cfg.ll_mode == 1:
         s += [("ar.w5", (C, 1, 5, 5)), ("ar.b5", (C,)),
               ("ar.w1", (C, C)), ("ar.b1", (C,)),
@@ -125,15 +131,18 @@ def random_model(cfg: ModelConfig, seed: int = 0) -> dict:
 
     Heads get bias (0, softplus^-1(1.5)) so that initial scales are near 1.5
     quantisation steps (rates of a few bits per sample, as for a trained
-    model at moderate quality); everything else is uniform in +-bound.
+    model at moderate quality), mixture heads equal weights, means 0 and
+    scales 1; everything else is uniform in +-bound.
     """
     rng = np.random.default_rng(seed)
     out = {}
     for name, shape in tensor_specs(cfg):
         b = _init_scale(name, shape, cfg)
         t = rng.uniform(-b, b, shape).astype(np.float32)
-        if name.endswith(".bh"):
+        if name.endswith(".bh") and shape[0] == 2:
             t = np.array([0.0, np.log(np.expm1(1.5))], dtype=np.float32)
+        elif name.endswith(".bh"):   # mixture: equal weights, mean 0, scale 1
+            t = np.array([0.0] * 6 + [np.log(np.expm1(1.0))] * 3, dtype=np.float32)
         out[name] = t
     return out
 
