@@ -37,7 +37,9 @@ steps.
 
   0 magic "PWBS"        4 u16 version (1)      6 u16 flags (1 lossless,
   8 u32 width          12 u32 height             2 autoregressive LL,
-                                                 16 balanced chunks; the
+                                                 16 balanced chunks,
+                                                 32 logistic-mixture
+                                                 probability model; the
                                                  library also records its
                                                  precision class in bits 2-3)
  16 u8 ncomp           17 u8 levels            18 u8 bitdepth
@@ -97,6 +99,8 @@ class Model:
         self.lift = Lifting(t)
         self.post = net_of(t, "post.") if "post.w1" in t else None
         self.ctx = ContextModel(t, cfg["C"], cfg["ll_mode"])
+        # logistic-mixture heads (9 outputs) instead of Laplace ones (2)
+        self.mixture = cfg["ll_mode"] == 0 and t["sb.s0.wh"].shape[0] == 9
         self.hash = model_hash(blob)
 
 
@@ -170,7 +174,9 @@ def dequantise(q: np.ndarray, delta32: np.float32) -> np.ndarray:
 # --------------------------------------------------------------------------
 # context parameters
 def context_params_all(model: Model, qsb: list):
-    """(mu, sigma) at every position of every subband, all symbols known.
+    """Entropy parameters at every position of every subband, all symbols
+    known: (mu, sigma) arrays, or for a mixture model [h, w, 9] arrays of
+    (w_k, mu_k, sigma_k).
 
     Equivalent to what the decoder computes step by step, because each step
     only reads positions of earlier steps (the nets mask the rest).
@@ -190,9 +196,15 @@ def context_params_all(model: Model, qsb: list):
             up = qsb[i - 1].shape[0] < H
             h, c = cm.lstm(qsb[i - 1].astype(np.float64), h, c, up)
             l, ns = h, "sb"
+        sm = step_map(H, W)
+        if model.mixture:
+            hd = np.zeros((H, W, E.MIX_K * 3))
+            for k in range(4):
+                hd = np.where((sm == k)[:, :, None], cm.step_head(k, s, l, ns), hd)
+            out.append(E.mix_params(hd))
+            continue
         mu = np.zeros((H, W))
         sg = np.zeros((H, W))
-        sm = step_map(H, W)
         for k in range(4):
             m, g = cm.step_params(k, s, l, ns)
             mu = np.where(sm == k, m, mu)
@@ -245,6 +257,18 @@ def chunk_lanes(n: int, lane_shift: int = 7) -> int:
     return min(LANES, max(1, n >> lane_shift))
 
 
+def coding_tables(model: Model, par, ys, xs, bank):
+    """Centres (ctr) and CDF tables ([n, NSYM + 1]) of the symbols at
+    (ys, xs) of one subband; par is the subband's (mu, sigma), or its
+    mixture parameters [h, w, 9] (w_k, mu_k, sigma_k)."""
+    if model.mixture:
+        ctr, q, j, g = E.mix_decision(par[ys, xs])
+        return ctr, E.mix_tables(q, j, g).astype(np.int64)
+    mu, sg = par
+    ctr, phi, j = E.index_decision(mu[ys, xs], sg[ys, xs])
+    return ctr, bank[E.table_id(phi, j)]
+
+
 def _sym_positions(h, w, step):
     if step < 0:
         ys, xs = np.nonzero(np.ones((h, w), dtype=bool))
@@ -276,7 +300,8 @@ def _encode_symbols(model, qcomp, shapes, *, width, height, bitdepth, colour,
     """Entropy-code quantised subbands. params, if given, replaces the
     context model: params[comp][subband] = (mu, sigma) arrays of the
     subband's shape (index injection: the coder alone is then exercised on
-    another implementation's entropy parameters)."""
+    another implementation's entropy parameters; a mixture model's params
+    are [h, w, 9] arrays of (w_k, mu_k, sigma_k) instead)."""
     bank = E.cdf_bank().astype(np.int64)
     ll_ar = model.ll_mode == 1
     if params is None:
@@ -288,16 +313,14 @@ def _encode_symbols(model, qcomp, shapes, *, width, height, bitdepth, colour,
         h, w, _ = shapes[i]
         ys, xs = _sym_positions(h, w, k)
         ys, xs = ys[first:first + n], xs[first:first + n]
-        mu, sg = params[comp][i]
-        ctr, phi, j = E.index_decision(mu[ys, xs], sg[ys, xs])
-        tid = E.table_id(phi, j)
+        ctr, tabs = coding_tables(model, params[comp][i], ys, xs, bank)
         vals = qcomp[comp][i][ys, xs]
-        ops = [R.symbol_ops(int(vals[p] - ctr[p]), bank[tid[p]]) for p in range(n)]
+        ops = [R.symbol_ops(int(vals[p] - ctr[p]), tabs[p]) for p in range(n)]
         st, words = R.encode_chunk(ops, nl)
         b = R.pack_chunk(st, words)
         payload.append(b)
         offsets.append(offsets[-1] + len(b))
-    flags = (1 if lossless else 0) | (2 if ll_ar else 0) | 16
+    flags = (1 if lossless else 0) | (2 if ll_ar else 0) | 16 | (32 if model.mixture else 0)
     head = (b"PWBS" + struct.pack("<HHIIBBBBffHBBIIQI", 1, flags, width, height,
                                   len(qcomp), model.levels, bitdepth, colour,
                                   float(d32), float(d32), E.T, E.LOG2M, LANES,
@@ -333,7 +356,8 @@ def parse_header(bs: bytes) -> dict:
     offs = np.frombuffer(bs, dtype="<u4", count=nch + 1, offset=64).astype(np.int64)
     base = 64 + 4 * (nch + 1)
     return dict(version=ver, lossless=bool(flags & 1), ll_ar=bool(flags & 2),
-                balanced=bool(flags & 16), lane_shift=bs[52] or 7,
+                balanced=bool(flags & 16), mixture=bool(flags & 32),
+                lane_shift=bs[52] or 7,
                 width=width, height=height, ncomp=ncomp, levels=levels,
                 bitdepth=bitdepth, colour=colour, delta_l=f32(dl), delta_h=f32(dh),
                 T=T, log2m=log2m, lanes=lanes, chunk=chunk, n_chunks=nch,
@@ -363,11 +387,14 @@ def decode_symbols(model: Model, bs: bytes, params: list | None = None):
     """Decode the quantised subbands of every component (list of lists).
 
     params, if given, replaces the context model of the four-step subbands
-    (params[comp][subband] = (mu, sigma) over the whole subband; only the
-    values at each step's positions are read)."""
+    (params[comp][subband] = (mu, sigma) over the whole subband, or the
+    mixture's [h, w, 9] (w_k, mu_k, sigma_k); only the values at each step's
+    positions are read)."""
     hd = parse_header(bs)
     if hd["model_hash"] != model.hash:
         raise ValueError("stream was made with another model")
+    if hd["mixture"] != model.mixture:
+        raise ValueError("probability model of the stream and the model differ")
     L = hd["levels"]
     mult = 1 << L
     Hp = -(-hd["height"] // mult) * mult
@@ -421,17 +448,18 @@ def decode_symbols(model: Model, bs: bytes, params: list | None = None):
                 l, ns = h_state, "sb"
             for k in range(4):
                 if params is not None:
-                    mu, sg = params[comp][i]
+                    par = params[comp][i]
+                elif model.mixture:
+                    par = E.mix_params(cm.step_head(k, s.astype(np.float64), l, ns))
                 else:
-                    mu, sg = cm.step_params(k, s.astype(np.float64), l, ns)
+                    par = cm.step_params(k, s.astype(np.float64), l, ns)
                 ys, xs = step_positions(H, W, k)
-                ctr, phi, j = E.index_decision(mu[ys, xs], sg[ys, xs])
-                tid = E.table_id(phi, j)
+                ctr, tabs = coding_tables(model, par, ys, xs, bank)
                 for ci, first, n, nl in chunks.get((comp, i, k), []):
                     buf = bs[base + offs[ci]: base + offs[ci + 1]]
                     st, words = R.unpack_chunk(buf, nl)
                     r, used, xf = R.decode_chunk(
-                        st, words, n, nl, lambda p, f=first: bank[tid[f + p]])
+                        st, words, n, nl, lambda p, f=first: tabs[f + p])
                     _check_chunk(used, len(words), xf)
                     sl = slice(first, first + n)
                     s[ys[sl], xs[sl]] = ctr[sl] + np.asarray(r, dtype=np.int64)

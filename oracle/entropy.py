@@ -27,11 +27,33 @@ degree-6 Taylor polynomial, Horner order), so both sides evaluate the same
 sequence of correctly rounded FP32 operations. numpy float32 array
 arithmetic performs exactly those single operations (no fused multiply-add).
 
+Logistic mixture (K = 3), the alternative probability model that Section
+4 compares with the Laplace one (the paper gives no layer or coding details;
+this is the reading). The head has 9 outputs per position: weight logits
+w_k, means mu_k and scale pre-activations rho_k, sigma_k = softplus(rho_k).
+Decision (FP32, from (w, mu, sigma) rounded to float32): a = the first k of largest w_k;
+ctr = rint(mu_a) (|ctr| <= 2^23); q_k = clamp(rint(8 (mu_k - ctr)),
+-255, 255) (eighth-step mean offsets); g_k = clamp(rint(4 (w_k - w_a)),
+-31, 0) (quarter-step log-weights, 0 for the reference component);
+j_k = the scale bin of sigma_k as above. Table of a key (q, j, g)
+for r = y - ctr, edges u_e = e - 62.5 (e = 0..125): m_k = q_k / 8,
+inv_k = 1 / b_{j_k}, om_k = exp32(g_k / 4), W = (om_0 + om_1) + om_2,
+z = (u_e - m_k) inv_k, S(z) = 1 / (1 + exp32(-z)) for z >= 0 and
+e / (1 + e), e = exp32(z), otherwise, F(u_e) = ((om_0 S_0 + om_1 S_1) +
+om_2 S_2) / W, then p, f and the remainder exactly as for the Laplace
+tables (same escapes, M and minimum frequency). Every operation is one
+correctly rounded FP32 operation, so encoder and decoder build the same
+table for every symbol.
+
 Pins (tests/test_oracle_entropy.py): every table is strictly increasing,
 starts at 0, ends at M, has every frequency >= 1, and is within (127+1)/M of
 the FP64 Laplace probabilities; the FP32 exponential is within 2 ulp of
 numpy's FP64 exp; the index decision matches its definition on hand-picked
-boundary values.
+boundary values. Mixture pins (tests/test_oracle_mixture.py): valid CDFs
+within (127+1)/M of the FP64 mixture; three equal components give the
+closed-form logistic; a component of weight e^(-31/4) barely moves the
+table and one of full weight moves it by the FP64 amount; hand-worked
+decisions at the rounding, argmax and clamping boundaries.
 """
 from __future__ import annotations
 
@@ -210,12 +232,21 @@ def laplace_probs64(phi: int, j: int) -> np.ndarray:
 MIX_K = 3
 
 
-def mix_decision(head):
-    """(ctr, q, j, g) from head outputs [..., 9]: ctr [...] int, q, j, g
-    [..., 3] int; decided in FP32 (head values rounded to float32 first)."""
-    h = np.asarray(head, dtype=np.float64)
-    h32 = h.astype(f32)
-    w, mu = h32[..., 0:3], h32[..., 3:6]
+def mix_params(head):
+    """Raw head outputs [..., 9] (w, mu, rho) -> entropy parameters
+    (w, mu, sigma), sigma = softplus(rho) (FP64)."""
+    h = np.array(head, dtype=np.float64)
+    rho = h[..., 6:9]
+    h[..., 6:9] = np.where(rho > 20.0, rho, np.log1p(np.exp(np.minimum(rho, 20.0))))
+    return h
+
+
+def mix_decision(par):
+    """(ctr, q, j, g) from mixture parameters [..., 9] (weight logits w,
+    means mu, scales sigma): ctr [...] int, q, j, g [..., 3] int; decided in
+    FP32 (parameters rounded to float32 first)."""
+    h32 = np.asarray(par, dtype=np.float64).astype(f32)
+    w, mu, sg = h32[..., 0:3], h32[..., 3:6], h32[..., 6:9]
     a = np.argmax(w, axis=-1)
     wa = np.take_along_axis(w, a[..., None], -1)
     mua = np.take_along_axis(mu, a[..., None], -1)[..., 0]
@@ -225,9 +256,7 @@ def mix_decision(head):
     q = np.clip(np.rint((d * f32(8.0)).astype(f32)), -255, 255).astype(np.int64)
     dw = (w - wa).astype(f32)
     g = np.clip(np.rint((dw * f32(4.0)).astype(f32)), -31, 0).astype(np.int64)
-    rho = h[..., 6:9]
-    sg = np.where(rho > 20.0, rho, np.log1p(np.exp(np.minimum(rho, 20.0))))
-    j = sigma_bin(sg.astype(f32))
+    j = sigma_bin(sg)
     return ctr, q, j, g
 
 
@@ -293,12 +322,12 @@ def mix_probs64(q, j, g) -> np.ndarray:
     return p
 
 
-def mix_near_tie(head, eps: float):
-    """True where an FP64 head output lies within relative eps of one of the
-    mixture decision's boundaries (the argmax, rint of mu_a, of 8 (mu_k -
-    ctr) and of 4 (w_k - w_a), or a scale-bin edge)."""
-    h = np.asarray(head, dtype=np.float64)
-    w, mu, rho = h[..., 0:3], h[..., 3:6], h[..., 6:9]
+def mix_near_tie(par, eps: float):
+    """True where an FP64 mixture parameter (w, mu, sigma) lies within
+    relative eps of one of the decision's boundaries (the argmax, rint of
+    mu_a, of 8 (mu_k - ctr) and of 4 (w_k - w_a), or a scale-bin edge)."""
+    h = np.asarray(par, dtype=np.float64)
+    w, mu, sg = h[..., 0:3], h[..., 3:6], h[..., 6:9]
     srt = np.sort(w, axis=-1)
     tie = np.abs(srt[..., 2] - srt[..., 1]) <= eps * np.maximum(np.abs(srt[..., 2]), 1.0)
     a = np.argmax(w, axis=-1)
@@ -309,6 +338,5 @@ def mix_near_tie(head, eps: float):
     ctr = np.rint(mua)
     tie |= np.any(half(8.0 * (mu - ctr[..., None])), axis=-1)
     tie |= np.any(half(4.0 * (w - wa)), axis=-1)
-    sg = np.where(rho > 20.0, rho, np.log1p(np.exp(np.minimum(rho, 20.0))))
     tie |= np.any(near_tie(np.zeros_like(sg), sg, eps), axis=-1)   # scale-bin edges
     return tie

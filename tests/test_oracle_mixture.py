@@ -70,7 +70,7 @@ def test_mixture_decision_hand_worked_values():
     head = np.array([0.1, 0.3, 0.3,  # w
                      -4.0, 2.5, 7.9,  # mu
                      0.0, 30.0, -30.0])  # rho
-    ctr, q, j, g = E.mix_decision(head)
+    ctr, q, j, g = E.mix_decision(E.mix_params(head))
     assert ctr == 2                              # rint(2.5) = 2 (half to even)
     assert list(q) == [-48, 4, 47]               # rint(8 (mu - 2)): -48, 4, 47.2 -> 47
     assert list(g) == [-1, 0, 0]                 # rint(4 (w - 0.3)) = rint(-0.8) = -1
@@ -79,14 +79,26 @@ def test_mixture_decision_hand_worked_values():
     assert j[1] == 63 == E.sigma_bin(np.float32(30.0)) and j[2] == 0
     # reference component 2 (largest w): ctr = -400; offsets and log-weights clamp
     far = np.array([0.0, -20.0, 1.0, 0.0, 400.0, -400.0, 1.0, 1.0, 1.0])
-    ctr, q, j, g = E.mix_decision(far)
+    ctr, q, j, g = E.mix_decision(E.mix_params(far))
     assert ctr == -400 and list(q) == [255, 255, 0] and list(g) == [-4, -31, 0]
 
 
+def test_mixture_params_softplus():
+    p = E.mix_params([1.0, 2.0, 3.0, 4.0, 5.0, 6.0, 0.0, 25.0, -40.0])
+    assert list(p[:6]) == [1.0, 2.0, 3.0, 4.0, 5.0, 6.0]
+    assert p[6] == np.log(2.0) and p[7] == 25.0
+    assert abs(p[8] / np.exp(-40.0) - 1.0) < 1e-12
+
+
 def test_mixture_near_tie_flags_boundaries():
-    h = np.array([0.0, 0.0, -1.0, 0.0, 0.0, 0.0, 1.0, 1.0, 1.0])
+    # parameters (w, mu, sigma); sigma 1.3 lies inside a scale bin
+    h = np.array([0.0, 0.0, -1.0, 0.0, 0.0, 0.0, 1.3, 1.3, 1.3])
     assert E.mix_near_tie(h, 1e-6)                     # argmax tie
-    h = np.array([1.0, 0.0, -1.0, 0.5 + 1e-9, 0.0, 0.0, 1.0, 1.0, 1.0])
+    h = np.array([1.0, 0.0, -1.0, 0.5 + 1e-9, 0.0, 0.0, 1.3, 1.3, 1.3])
     assert E.mix_near_tie(h, 1e-6)                     # mu_a at a half
-    h = np.array([1.0, 0.0, -1.0, 0.3, 0.0, 0.0, 1.0, 1.0, 1.0])
+    h = np.array([1.0, 0.0, -1.0, 0.3, 0.0, 0.0, 1.3, 1.3, 1.3])
     assert not E.mix_near_tie(h, 1e-6)
+    h = np.array([1.0, 0.0, -1.0, 0.3, 0.0, 0.0, 1.3, 1.0, 1.3])
+    assert E.mix_near_tie(h, 1e-6)                     # sigma 1.0 on a bin edge
+    h = np.array([1.0, 0.0, -1.0, 0.3, 0.0625 * (1 + 1e-9), 0.0, 1.3, 1.3, 1.3])
+    assert E.mix_near_tie(h, 1e-6)                     # 8 (mu_1 - ctr) at a half
