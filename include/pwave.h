@@ -97,6 +97,15 @@ int pw_model_load(pw_ctx *ctx, const void *blob, size_t n, pw_model **out);
 void pw_model_free(pw_model *m);
 /* 64-bit hash of the blob; every stream records the hash of its model. */
 uint64_t pw_model_hash(const pw_model *m);
+/* 1 when the model's probability model is the logistic mixture of three
+ * components (heads of 9 outputs in the blob: weight logits, means, scale
+ * pre-activations), 0 for the Laplace model (heads of 2). The paper's
+ * experiments compare both (Section 4). Mixture models are four-step LL
+ * models and run in the FP32 precision class only (pw_model_load returns
+ * PW_EUNSUPPORTED in a BF16 or FP8 context); their streams record the model
+ * in header flag 32, and each symbol is coded with its own CDF table built
+ * from its key (see pw_mix_tables). */
+int pw_model_mixture(const pw_model *m);
 
 /* Architecture of a random-init model: wavelet levels (1..6), context
  * channels C (32, 64 or 128), lifting CNN channels F (16), LL mode (0: the
@@ -258,6 +267,31 @@ int pw_rans_decode_noalloc(void *cuda_stream, const uint8_t *payload, size_t pay
  * step by step. H and W must be multiples of 2^levels. */
 int pw_context_params(pw_ctx *ctx, const pw_model *m, int H, int W,
                       const int32_t *q, float *mu, float *sigma);
+
+/* Logistic-mixture counterpart of pw_context_params: par (host float,
+ * 9 per position, positions in the layout of pw_context_params) receives
+ * (w_0, w_1, w_2, mu_0, mu_1, mu_2, sigma_0, sigma_1, sigma_2) of every
+ * position as the decoder computes them, sigma_k = softplus of the head's
+ * scale outputs. Errors: PW_EUNSUPPORTED for a Laplace model (and
+ * pw_context_params returns PW_EUNSUPPORTED for a mixture model). */
+int pw_context_mixture(pw_ctx *ctx, const pw_model *m, int H, int W,
+                       const int32_t *q, float *par);
+
+/* CDF tables of n logistic-mixture keys. key9 (host int32, 9 per key):
+ * q_0 q_1 q_2 (mean offsets from the centre in 1/8 steps, -255..255),
+ * j_0 j_1 j_2 (scale bins 0..127, the Laplace tables' bins), g_0 g_1 g_2
+ * (log-weights in 1/4 steps, -31..0), each clamped to its range. cdf (host
+ * uint16, 128 per key) receives cdf[0] = 0 .. cdf[127] = 2^15 of the 127
+ * symbols (escape, residuals -62..62 around the centre, escape): the
+ * mixture sum_k exp(g_k / 4) S((u - q_k / 8) / b_{j_k}) / sum_k exp(g_k / 4),
+ * S the logistic function, at the 126 symbol edges u, quantised like the
+ * Laplace tables, every step one correctly rounded FP32 operation (the
+ * exponential the library's own), so encoders and decoders on any GPU build
+ * identical tables. The decision of a key from the mixture parameters
+ * (w, mu, sigma): a = the first component of largest w, centre
+ * rint(mu_a), q_k = rint(8 (mu_k - centre)), g_k = rint(4 (w_k - w_a)),
+ * j_k = the bin of sigma_k, all in FP32. */
+int pw_mix_tables(pw_ctx *ctx, int64_t n, const int32_t *key9, uint16_t *cdf);
 
 /* Forward / inverse learned lifting DWT of one plane (Section 3.1, Fig. 2)
  * on host float arrays: x is H x W; sb holds the subbands in coding order

@@ -74,6 +74,7 @@ _sig = {
     "pw_model_load": (C.c_int, [_P, _P, C.c_size_t, C.POINTER(_P)]),
     "pw_model_free": (None, [_P]),
     "pw_model_hash": (C.c_uint64, [_P]),
+    "pw_model_mixture": (C.c_int, [_P]),
     "pw_model_random_blob": (C.c_int, [C.POINTER(pw_model_cfg), C.c_uint64, _P, C.c_size_t,
                                        C.POINTER(C.c_size_t)]),
     "pw_model_init_random": (C.c_int, [_P, C.POINTER(pw_model_cfg), C.c_uint64,
@@ -94,6 +95,8 @@ _sig = {
     "pw_rans_decode_noalloc": (C.c_int, [_P, _P, C.c_size_t, C.c_int, _P, _P, _P, _P, _P,
                                          _P]),
     "pw_context_params": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P, _P]),
+    "pw_context_mixture": (C.c_int, [_P, _P, C.c_int, C.c_int, _P, _P]),
+    "pw_mix_tables": (C.c_int, [_P, C.c_int64, _P, _P]),
     "pw_lift_forward": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
     "pw_lift_inverse": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, _P, _P]),
     "pw_decode_symbols": (C.c_int, [_P, _P, _P, C.c_size_t, _P]),
@@ -195,6 +198,11 @@ class Model:
     @property
     def hash(self) -> int:
         return int(pw_model_hash(self.handle))
+
+    @property
+    def mixture(self) -> bool:
+        """Logistic-mixture probability model (else Laplace)."""
+        return bool(pw_model_mixture(self.handle))
 
     def close(self):
         if self.handle:
@@ -454,6 +462,20 @@ class Codec:
         sg = np.zeros(q.size, dtype=np.float32)
         check(pw_context_params(self.ctx, model.handle, H, W, _ptr(q), _ptr(mu), _ptr(sg)))
         return mu, sg
+
+    def context_mixture(self, model: Model, H: int, W: int, q: np.ndarray) -> np.ndarray:
+        """Mixture parameters (w, mu, sigma) [n, 9] of every position."""
+        q = np.ascontiguousarray(q, dtype=np.int32)
+        par = np.zeros((q.size, 9), dtype=np.float32)
+        check(pw_context_mixture(self.ctx, model.handle, H, W, _ptr(q), _ptr(par)))
+        return par
+
+    def mix_tables(self, keys: np.ndarray) -> np.ndarray:
+        """CDF tables [n, 128] (uint16) of mixture keys [n, 9] (q, j, g)."""
+        keys = np.ascontiguousarray(keys, dtype=np.int32).reshape(-1, 9)
+        out = np.zeros((keys.shape[0], 128), dtype=np.uint16)
+        check(pw_mix_tables(self.ctx, keys.shape[0], _ptr(keys), _ptr(out)))
+        return out
 
     def lift_forward(self, model: Model, x: np.ndarray, lossless: bool = False) -> np.ndarray:
         x = np.ascontiguousarray(x, dtype=np.float32)

@@ -117,7 +117,7 @@ static int get_plan(pw_ctx *ctx, Model &m, const Geometry &g, int B, const char 
   p->set_stream(ctx->stream);
   int s = m.prepare(ctx->precision);
   if (s != PW_OK) return s;
-  s = p->ws.alloc(g, B * g.nc, m.C, params, ctx->precision, ctx->stream);
+  s = p->ws.alloc(g, B * g.nc, m.C, params, ctx->precision, ctx->stream, m.mix);
   if (s != PW_OK) return s;
   if (!strcmp(kind, "dec") || !strcmp(kind, "sym")) {
     // decode descriptor layout: group blocks of P x count
@@ -259,10 +259,11 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *co
       const int h = g.sh[sb], w = g.sw[sb];
       const double nsym = (double)P * step_count(h, w, k);
       ProfScope ps(ctx, KC_RANS_DEC, 0.0, nsym * 8.0 + stream_bytes * nsym / total_syms);
-      launch_rans_decode(dch + pl.gbase[gi], P * cnt, ctx->bank, ctx->coarse,
-                         pl.ws.idx + (int64_t)P * g.ioff[gi], step_count(h, w, k),
+      // logistic mixture: the step's own table rows instead of the bank
+      launch_rans_decode(dch + pl.gbase[gi], P * cnt, m.mix ? pl.ws.mrows : ctx->bank,
+                         ctx->coarse, pl.ws.idx + (int64_t)P * g.ioff[gi], step_count(h, w, k),
                          pl.ws.Q + (int64_t)P * g.soff[sb], (int64_t)h * w, h, w, k,
-                         ctx->status, st);
+                         ctx->status, st, m.mix);
       bump(ctx);
     }
   }
@@ -284,6 +285,9 @@ static int check_header_model(pw_ctx *ctx, const Model &m, const StreamHeader &h
   if (h.model_hash != m.hash) { set_last_error("stream was made with another model"); return PW_EINVAL; }
   if (h.levels != m.levels || ((h.flags & FLAG_LL_AR) ? 1 : 0) != m.ll_mode) {
     set_last_error("stream levels / LL mode do not match the model"); return PW_EINVAL;
+  }
+  if (((h.flags & FLAG_MIX) ? true : false) != m.mix) {
+    set_last_error("stream and model use different probability models"); return PW_EINVAL;
   }
   if (((h.flags >> FLAG_PREC_SHIFT) & 3) != ctx->precision) {
     set_last_error("stream was encoded with another precision class"); return PW_EINVAL;
@@ -518,7 +522,8 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
   EncChunk *d_ec = reinterpret_cast<EncChunk *>(pl.d_enc.p);
   PW_CUDA_TRY(cudaMemcpyAsync(d_ec, ec.data(), nall * sizeof(EncChunk), cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemsetAsync(ctx->status, 0, 4, st));
-  launch_rans_count_ops(d_ec, nall, ws.idx, vals, reinterpret_cast<uint32_t *>(pl.d_ops.p), st);
+  launch_rans_count_ops(d_ec, nall, ws.idx, vals, reinterpret_cast<uint32_t *>(pl.d_ops.p), st,
+                        m.mix);
   bump(ctx);
   std::vector<uint32_t> ops(nall);
   PW_CUDA_TRY(cudaMemcpyAsync(ops.data(), pl.d_ops.p, nall * 4, cudaMemcpyDeviceToHost, st));
@@ -530,7 +535,8 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
   launch_rans_encode(d_ec, nall, ctx->bank, ws.idx, vals,
                      reinterpret_cast<uint16_t *>(pl.d_scratch.p),
                      reinterpret_cast<uint32_t *>(pl.d_states.p),
-                     reinterpret_cast<uint32_t *>(pl.d_nwords.p), ctx->status, st);
+                     reinterpret_cast<uint32_t *>(pl.d_nwords.p), ctx->status, st,
+                     m.mix ? ws.mcf : nullptr);
   bump(ctx);
   std::vector<uint32_t> nw(nall);
   PW_CUDA_TRY(cudaMemcpyAsync(nw.data(), pl.d_nwords.p, nall * 4, cudaMemcpyDeviceToHost, st));
@@ -565,7 +571,8 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
     std::memcpy(h.magic, "PWBS", 4);
     h.version = 1;
     h.flags = (uint16_t)((g.lossless ? FLAG_LOSSLESS : 0) | (g.ll_ar ? FLAG_LL_AR : 0) |
-                         (g.balanced ? FLAG_BALANCED : 0) | prec_flags(ctx));
+                         (g.balanced ? FLAG_BALANCED : 0) | (m.mix ? FLAG_MIX : 0) |
+                         prec_flags(ctx));
     h.width = g.W; h.height = g.H; h.ncomp = (uint8_t)g.nc; h.levels = (uint8_t)g.levels;
     h.bitdepth = (uint8_t)g.bitdepth; h.colour = (uint8_t)g.colour;
     h.delta_l = dl; h.delta_h = dh; h.T = kT; h.log2m = kLogM; h.lanes = kMaxLanes;
@@ -1211,19 +1218,19 @@ int pw_rans_encode(pw_ctx *c, int nchunks, const uint32_t *count, const uint32_t
   return PW_OK;
 }
 
-int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t *q, float *mu,
-                      float *sigma) {
-  if (!c || !mm || !q || !mu || !sigma) return PW_EINVAL;
-  Model &m = const_cast<pw_model *>(mm)->m;
+// The context model over a fully known latent (every step at once); the
+// plan's workspace then holds the entropy parameters.
+static int context_all(pw_ctx *c, Model &m, int H, int W, const int32_t *q, Plan **plo,
+                       Geometry &g) {
   const int mult = 1 << m.levels;
   if (H < mult || W < mult || H % mult || W % mult) {
     set_last_error("H and W must be positive multiples of 2^levels"); return PW_EINVAL;
   }
-  Geometry g;
   g.build(H, W, 1, m.levels, 0, 8, 0, m.ll_mode, 16384);
   Plan *pl;
   int s;
   if ((s = get_plan(c, m, g, 1, "par", true, &pl))) return s;
+  *plo = pl;
   cudaStream_t st = c->stream;
   PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.Q, q, g.plane_elems * 4, cudaMemcpyHostToDevice, st));
   if (c->precision != PW_PREC_FP32) tc_error_reset(pl->ws, st);
@@ -1239,6 +1246,22 @@ int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t
     for (int k = 0; k < 4; ++k)
       if ((s = run_context_pass(c, m, g, pl->ws, sb, k, false))) return s;
   }
+  return PW_OK;
+}
+
+int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t *q, float *mu,
+                      float *sigma) {
+  if (!c || !mm || !q || !mu || !sigma) return PW_EINVAL;
+  Model &m = const_cast<pw_model *>(mm)->m;
+  if (m.mix) {
+    set_last_error("a mixture model's parameters come from pw_context_mixture");
+    return PW_EUNSUPPORTED;
+  }
+  Plan *pl;
+  Geometry g;
+  int s = context_all(c, m, H, W, q, &pl, g);
+  if (s) return s;
+  cudaStream_t st = c->stream;
   PW_CUDA_TRY(cudaMemcpyAsync(mu, pl->ws.mu, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
   PW_CUDA_TRY(cudaMemcpyAsync(sigma, pl->ws.sg, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
   if ((s = finish(c))) return s;
@@ -1248,6 +1271,40 @@ int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t
   }
   return PW_OK;
 }
+
+int pw_context_mixture(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t *q,
+                       float *par) {
+  if (!c || !mm || !q || !par) return PW_EINVAL;
+  Model &m = const_cast<pw_model *>(mm)->m;
+  if (!m.mix) {
+    set_last_error("not a mixture model (pw_context_params gives its parameters)");
+    return PW_EUNSUPPORTED;
+  }
+  Plan *pl;
+  Geometry g;
+  int s = context_all(c, m, H, W, q, &pl, g);
+  if (s) return s;
+  PW_CUDA_TRY(cudaMemcpyAsync(par, pl->ws.mpar, g.plane_elems * 9 * 4, cudaMemcpyDeviceToHost,
+                              c->stream));
+  return finish(c);
+}
+
+int pw_mix_tables(pw_ctx *c, int64_t n, const int32_t *key9, uint16_t *cdf) {
+  if (!c || n < 0 || (n && (!key9 || !cdf))) return PW_EINVAL;
+  if (!n) return PW_OK;
+  DevBuf dk, dr;
+  int s;
+  if ((s = dk.ensure((size_t)n * 9 * 4)) || (s = dr.ensure((size_t)n * kMixRow * 2))) return s;
+  cudaStream_t st = c->stream;
+  PW_CUDA_TRY(cudaMemcpyAsync(dk.p, key9, (size_t)n * 9 * 4, cudaMemcpyHostToDevice, st));
+  launch_mix_tables((const int32_t *)dk.p, n, (uint16_t *)dr.p, st);
+  bump(c);
+  PW_CUDA_TRY(cudaMemcpy2DAsync(cdf, (kNSym + 1) * 2, dr.p, kMixRow * 2, (kNSym + 1) * 2,
+                                (size_t)n, cudaMemcpyDeviceToHost, st));
+  return finish(c);
+}
+
+int pw_model_mixture(const pw_model *m) { return m && m->m.mix ? 1 : 0; }
 
 static int lift_stage(pw_ctx *c, const pw_model *mm, int H, int W, int lossless, const float *in,
                       float *out, bool fwd) {

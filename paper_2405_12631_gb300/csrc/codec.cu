@@ -121,7 +121,16 @@ void pool_free(void *p, cudaStream_t st) {
   if (p) cudaFreeAsync(p, st);
 }
 
-int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec, cudaStream_t st) {
+// Symbols of the largest coding step of one plane.
+static int64_t max_step_symbols(const Geometry &g) {
+  int64_t m = 0;
+  for (int sb = 0; sb < g.nsb; ++sb)
+    for (int k = 0; k < 4; ++k) m = std::max(m, (int64_t)step_count(g.sh[sb], g.sw[sb], k));
+  return m;
+}
+
+int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec, cudaStream_t st,
+                     bool mix) {
   const bool bf16 = prec != PW_PREC_FP32;
   release();
   stream = st;
@@ -148,6 +157,11 @@ int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec, cu
     parts.push_back({(void **)&mu, al(pe * 4)});
     parts.push_back({(void **)&sg, al(pe * 4)});
   }
+  if (mix) {
+    parts.push_back({(void **)&mrows, al((int64_t)P * max_step_symbols(g) * kMixRow * 2)});
+    parts.push_back({(void **)&mcf, al(pe * 4)});
+    if (params) parts.push_back({(void **)&mpar, al(pe * 9 * 4)});
+  }
   int64_t tot = 0;
   for (auto &p : parts) tot += p.second;
   void *b = nullptr;
@@ -167,7 +181,7 @@ int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec, cu
   return PW_OK;
 }
 
-int64_t Workspace::estimate(const Geometry &g, int P, int C, bool params, int prec) {
+int64_t Workspace::estimate(const Geometry &g, int P, int C, bool params, int prec, bool mix) {
   const bool bf16 = prec != PW_PREC_FP32;
   const int64_t pe = (int64_t)P * g.Hp * g.Wp;
   const int64_t big = (int64_t)P * g.sh.back() * g.sw.back();
@@ -176,6 +190,9 @@ int64_t Workspace::estimate(const Geometry &g, int P, int C, bool params, int pr
   if (!bf16) tot += 3 * al(big * 2 * C * 4) + 3 * al(big * C * 4);
   else tot += tc_workspace_bytes(g, P, C, prec == PW_PREC_FP8);
   if (params) tot += 2 * al(pe * 4);
+  if (mix)
+    tot += al((int64_t)P * max_step_symbols(g) * kMixRow * 2) + al(pe * 4) +
+           (params ? al(pe * 9 * 4) : 0);
   return tot;
 }
 
@@ -223,9 +240,11 @@ int run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb) {
   return PW_OK;
 }
 
-// One coding step's context fusion net -> packed table indices.
+// One coding step's context fusion net -> packed table indices (Laplace),
+// or centres plus table rows (decoding) / per-symbol (cdf, frequency)
+// pairs (encoding) of the logistic mixture.
 int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
-                     int step, bool /*decoding*/) {
+                     int step, bool decoding) {
   const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P;
   StepNetDev &n = (sb == 0) ? m.ll[step] : m.sb[step];
   const int32_t *Qi = ws.Q + (int64_t)P * g.soff[sb];
@@ -239,6 +258,25 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
   if (sb == 0 && step == 0) {
     cudaMemsetAsync(ws.X2, 0, (size_t)P * h * w * 2 * C * 4, st);  // l = 0 for LL
   }
+  // logistic mixture: the last convolution stores z' (in place over its
+  // residual input), then the mixture head runs on the step's symbols
+  auto mix_head = [&](const float *zp) {
+    MixHeadParams mp{};
+    mp.z = zp; mp.wh = n.wh; mp.bh = n.bh; mp.C = C; mp.P = P; mp.H = h; mp.W = w;
+    mp.step = step; mp.nk = nk;
+    mp.ctr = reinterpret_cast<int32_t *>(idx);
+    if (decoding) {
+      mp.rows = ws.mrows;
+    } else {
+      mp.q = Qi;
+      mp.cf = ws.mcf + (int64_t)P * g.ioff[sb * 4 + step];
+      mp.par = ws.mpar ? ws.mpar + (int64_t)P * g.soff[sb] * 9 : nullptr;
+    }
+    const double ns = (double)P * nk;
+    ProfScope ps(ctx, KC_MIX, ns * (2.0 * 9 * C + 3.0 * 126 * 8),
+                 ns * (4.0 * C + 4.0 + (decoding ? 2.0 * kMixRow : 8.0)));
+    launch_mix_head(mp, st);
+  };
   const double pix = (double)P * h * w;
   auto conv = [&](int ks, const ConvParams &cp, int epi) {
     const double fl = 2.0 * pix * ks * ks * cp.cin * cp.cout_total;
@@ -278,6 +316,13 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
     a = base();  // z3 = z2 + 1x1(2C->C) u2; head
     a.in = ws.U; a.in_cs = 2 * C; a.cin = 2 * C; a.w = n.w4; a.b = n.b4; a.cout_total = C;
     a.res = ws.Z2; a.res_cs = C;
+    if (m.mix) {
+      a.out = ws.Z2; a.out_cs = C;
+      conv(1, a, EPI_STORE);
+      mix_head(ws.Z2);
+      bump(ctx, 7);
+      return PW_OK;
+    }
     a.wh = n.wh; a.bh = n.bh; a.step = 0; a.idx = idx; a.idx_stride = nk;
     a.mu_out = mu; a.sg_out = sgp;
     conv(1, a, EPI_HEAD);
@@ -298,6 +343,13 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
     a = base();  // z' = z + conv3x3 u; head
     a.in = ws.U; a.in_cs = C; a.cin = C; a.w = n.c2w; a.b = n.c2b; a.cout_total = C;
     a.res = ws.Z; a.res_cs = C;
+    if (m.mix) {
+      a.out = ws.Z; a.out_cs = C;
+      conv(3, a, EPI_STORE);
+      mix_head(ws.Z);
+      bump(ctx, 5);
+      return PW_OK;
+    }
     a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
     a.mu_out = mu; a.sg_out = sgp;
     conv(3, a, EPI_HEAD);

@@ -33,6 +33,10 @@ struct TcWeights;
 struct Model {
   pw_ctx *ctx = nullptr;
   int levels = 4, C = 32, F = 16, ll_mode = 0;
+  // probability model: Laplace (heads of 2 outputs) or the logistic mixture
+  // of 3 (9 outputs; FP32 precision class and four-step LL only)
+  int nh = 2;
+  bool mix = false;
   uint64_t hash = 0;
   uint64_t uid = 0;          // unique per loaded model (keys cached workspaces)
   std::vector<float *> allocs;
@@ -76,7 +80,10 @@ struct StreamHeader {
 #pragma pack(pop)
 static_assert(sizeof(StreamHeader) == 64, "stream header is 64 bytes");
 
-enum : uint16_t { FLAG_LOSSLESS = 1, FLAG_LL_AR = 2, FLAG_PREC_SHIFT = 2, FLAG_BALANCED = 16 };
+enum : uint16_t {
+  FLAG_LOSSLESS = 1, FLAG_LL_AR = 2, FLAG_PREC_SHIFT = 2, FLAG_BALANCED = 16,
+  FLAG_MIX = 32   // logistic-mixture probability model
+};
 
 // One chunk of the per-component layout (same for every image of a class).
 struct ChunkTpl {
@@ -128,12 +135,21 @@ struct Workspace {
   float *T0 = nullptr, *T1 = nullptr, *T2 = nullptr;  // lifting temporaries
   float *planes = nullptr;     // component planes [P][Hp][Wp]
   float *mu = nullptr, *sg = nullptr;  // optional parameter outputs [P][Hp*Wp]
+  // logistic-mixture models: table rows of the current step ([P * largest
+  // step][kMixRow], decoding), (cdf | frequency << 16) of every symbol in the
+  // idx layout (encoding), optional parameters [P][Hp*Wp][9]
+  uint16_t *mrows = nullptr;
+  uint32_t *mcf = nullptr;
+  float *mpar = nullptr;
   void *tc = nullptr;          // BF16 / FP8 activations (tensor-core path)
   int lstm_cur = 0;            // which Cst holds the current cell state
   // prec: the context's pw_precision (tensor-core buffers unless FP32)
-  int alloc(const Geometry &g, int P, int C, bool params, int prec, cudaStream_t st);
+  // mix: buffers of the logistic-mixture model
+  int alloc(const Geometry &g, int P, int C, bool params, int prec, cudaStream_t st,
+            bool mix = false);
   // upper bound of the device bytes alloc() takes for these arguments
-  static int64_t estimate(const Geometry &g, int P, int C, bool params, int prec);
+  static int64_t estimate(const Geometry &g, int P, int C, bool params, int prec,
+                          bool mix = false);
   void release();
   ~Workspace() { release(); }
 };

@@ -34,6 +34,24 @@ struct ConvParams {
 };
 
 void launch_conv_simt(int ks, const ConvParams &a, int epi, cudaStream_t st);
+
+// Logistic-mixture head of one coding step (mixture.cu): one warp per
+// symbol of the step ([P][nk] in step order).
+struct MixHeadParams {
+  const float *z;       // z' [P, H, W, C]
+  const float *wh;      // [9][C]
+  const float *bh;      // [9]
+  int C, P, H, W, step;
+  int64_t nk;           // symbols of the step per plane
+  int32_t *ctr;         // [P][nk] centres (written)
+  uint16_t *rows;       // decoding: [P * nk][kMixRow] table rows, or null
+  const int32_t *q;     // encoding: quantised subband [P, H, W] ...
+  uint32_t *cf;         // ... and [P][nk] (cdf | frequency << 16) of each symbol, or null
+  float *par;           // optional [P, H, W, 9] (w, mu, sigma) at the step's positions
+};
+void launch_mix_head(const MixHeadParams &a, cudaStream_t st);
+// Stage entry: rows of n keys given as int32 (q0 q1 q2 j0 j1 j2 g0 g1 g2).
+void launch_mix_tables(const int32_t *key9, int64_t n, uint16_t *rows, cudaStream_t st);
 // Set when a launcher found no kernel for its arguments (checked and cleared
 // by the host drivers).
 bool &launch_failed();
@@ -61,16 +79,22 @@ struct EncChunk {
 };
 // bank: 2048 x 128 CDF tables; coarse (may be null): every 8th entry, 2048 x 16
 void launch_cdf_bank(uint16_t *bank, uint16_t *coarse, cudaStream_t st);
+// mix: per-symbol tables (logistic mixture) - bank is then the step's
+// [P * idx_stride][kMixRow] rows (row of symbol plane * idx_stride + first
+// + i), coarse is unused and idx holds the symbols' centres (int32).
 void launch_rans_decode(const DecChunk *chunks, int nchunks, const uint16_t *bank,
                         const uint16_t *coarse, const uint32_t *idx, int64_t idx_stride,
                         int32_t *out, int64_t out_stride, int h, int w, int step,
-                        uint32_t *status, cudaStream_t st);
+                        uint32_t *status, cudaStream_t st, bool mix = false);
+// cf (logistic mixture, else null): per symbol (cdf | frequency << 16) of its
+// coded symbol; idx then holds the centres (int32) and bank is unused.
 void launch_rans_count_ops(const EncChunk *chunks, int nchunks, const uint32_t *idx,
-                           const int32_t *vals, uint32_t *ops, cudaStream_t st);
+                           const int32_t *vals, uint32_t *ops, cudaStream_t st,
+                           bool mix = false);
 void launch_rans_encode(const EncChunk *chunks, int nchunks, const uint16_t *bank,
                         const uint32_t *idx, const int32_t *vals, uint16_t *scratch,
                         uint32_t *states, uint32_t *nwords, uint32_t *status,
-                        cudaStream_t st);
+                        cudaStream_t st, const uint32_t *cf = nullptr);
 void launch_rans_pack(const EncChunk *chunks, int nchunks, const uint16_t *scratch,
                       const uint32_t *states, const uint32_t *nwords,
                       const uint64_t *out_off, uint8_t *payload, cudaStream_t st);

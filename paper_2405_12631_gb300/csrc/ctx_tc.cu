@@ -1738,6 +1738,10 @@ int Model::ensure_fp8() {
 }
 
 int Model::prepare(int precision) {
+  if (mix && precision != PW_PREC_FP32) {
+    set_last_error("logistic-mixture models run in the FP32 precision class only");
+    return PW_EUNSUPPORTED;
+  }
   if (precision == PW_PREC_FP32) return PW_OK;
   std::lock_guard<std::mutex> lk(mu);
   return precision == PW_PREC_FP8 ? ensure_fp8() : ensure_tc();

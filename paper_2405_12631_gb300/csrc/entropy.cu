@@ -21,6 +21,7 @@
 #include "pw_internal.cuh"
 #include "ctx_kernels.cuh"
 #include "spec_math.cuh"
+#include "cdf_warp.cuh"
 #include "tc_ptx.cuh"
 
 namespace pw {
@@ -50,47 +51,8 @@ __global__ void k_cdf_bank(uint16_t *__restrict__ bank, uint16_t *__restrict__ c
     else v = __fsub_rn(1.f, __fmul_rn(0.5f, exp32_spec(-z)));
     F[i] = (e < kNSym - 1) ? v : 1.f;
   }
-  // p_s = F[s] - F[s-1], F[-1] = 0, F[126] = 1 (edge 126 does not exist)
-  float prevF = __shfl_up_sync(0xffffffffu, F[3], 1);
-  if (lane == 0) prevF = 0.f;
   int f[4];
-  int sum = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    int s = 4 * lane + i;
-    float lo = (i == 0) ? prevF : F[i - 1];
-    float hi = (s == kNSym - 1) ? 1.f : F[i];
-    float p = (s == 0) ? F[0] : __fsub_rn(hi, lo);
-    p = fmaxf(p, 0.f);
-    int q = (int)floorf(__fmul_rn(p, (float)(kM - kNSym)));
-    f[i] = (s < kNSym) ? 1 + q : 0;
-    sum += f[i];
-  }
-  // warp sum and first argmax
-  int best = -1, bidx = 0;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (f[i] > best) { best = f[i]; bidx = 4 * lane + i; }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    int ob = __shfl_xor_sync(0xffffffffu, best, o);
-    int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-    if (ob > best || (ob == best && oi < bidx)) { best = ob; bidx = oi; }
-  }
-  int rem = (int)kM - sum;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-    if (4 * lane + i == bidx) f[i] += rem;
-  // exclusive scan -> cdf[s] = sum of f[< s]
-  int local = f[0] + f[1] + f[2] + f[3];
-  int incl = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += t;
-  }
-  int run = incl - local;
+  int run = warp_cdf(F, lane, f);
   uint16_t *row = bank + (size_t)warp * (kNSym + 1);
   if (coarse && (lane & 1) == 0) coarse[(size_t)warp * kCoarse + (lane >> 1)] = (uint16_t)run;
 #pragma unroll
@@ -174,13 +136,20 @@ __device__ __forceinline__ int cdf_search_r(const uint16_t *__restrict__ row, co
 // in registers (lane l holds words wb + 2l, wb + 2l + 1 in cur and the same
 // 64 words later in nxt) and reads with shuffles; the window moves by 64
 // words once 64 are consumed, loading the next 64 one shift ahead.
+//
+// kMix (logistic mixture): every symbol has its own table row in global
+// memory (bank = the step's rows, kMixRow entries each, the coarse level in
+// the row's last 16), written just before by the mixture head; idx holds
+// the centres. The coarse entries of a lane's symbol are loaded two rounds
+// ahead, its fine row prefetched into L1 two rounds ahead.
+template <bool kMix>
 __global__ void __launch_bounds__(256) k_rans_decode(
     const DecChunk *__restrict__ chunks, int nchunks, const uint16_t *__restrict__ bank,
     const uint16_t *__restrict__ coarse, const uint32_t *__restrict__ idx, int64_t idx_stride,
     int32_t *__restrict__ out, int64_t out_stride, int h, int w, int step,
     uint32_t *status) {
   extern __shared__ uint4 s_coarse4[];
-  {
+  if constexpr (!kMix) {
     // the coarse level (64 KB) in one asynchronous bulk copy, whatever the
     // block's size; an mbarrier after it counts the bytes
     constexpr uint32_t kBytes = kNTables * kCoarse * 2;
@@ -246,6 +215,10 @@ __global__ void __launch_bounds__(256) k_rans_decode(
   const uint32_t *idxp = idx + (int64_t)ch.plane * idx_stride + ch.first;
   int32_t *outp = out + (int64_t)ch.plane * out_stride;
   const int count = (int)ch.count;
+  if (kMix && count == 0) {  // chunk layouts hold no empty chunks
+    if (lane == 0) atomicOr(status, kStCorrupt);
+    return;
+  }
   const int niter = (count + nl - 1) / nl;
   // output position of symbol q = first + p (step layout): row pair y2,
   // index r within the pair, advanced by nl per iteration
@@ -266,8 +239,16 @@ __global__ void __launch_bounds__(256) k_rans_decode(
   // round's dependent chain (every unpacked index is a valid table)
   uint32_t pk_a = (lane < nl && lane < count) ? __ldg(idxp + lane) : 0u;
   uint32_t pk_b = (lane < nl && lane + nl < count) ? __ldg(idxp + lane + nl) : 0u;
-  uint4 ca0, ca1;
-  {
+  uint4 ca0, ca1, cb0, cb1;
+  // kMix: row of the chunk's symbol i (inactive lanes use the first one)
+  const uint16_t *mrows = bank + ((int64_t)ch.plane * idx_stride + ch.first) * kMixRow;
+  auto mix_row = [&](int i) { return mrows + (int64_t)(i < count ? i : 0) * kMixRow; };
+  if constexpr (kMix) {
+    const uint4 *ra = reinterpret_cast<const uint4 *>(mix_row(lane) + kNSym + 1);
+    const uint4 *rb = reinterpret_cast<const uint4 *>(mix_row(lane + nl) + kNSym + 1);
+    ca0 = __ldg(ra); ca1 = __ldg(ra + 1);
+    cb0 = __ldg(rb); cb1 = __ldg(rb + 1);
+  } else {
     int c, t;
     unpack_index(pk_a, c, t);
     const uint4 *cr = reinterpret_cast<const uint4 *>(s_coarse + t * kCoarse);
@@ -278,7 +259,14 @@ __global__ void __launch_bounds__(256) k_rans_decode(
     const bool active = lane < nl && p < count;
     const uint32_t pk = pk_a;
     const uint4 c0 = ca0, c1 = ca1;
-    {
+    if constexpr (kMix) {
+      ca0 = cb0; ca1 = cb1;
+      const uint16_t *frow = mix_row(p + 2 * nl);
+      const uint4 *cr = reinterpret_cast<const uint4 *>(frow + kNSym + 1);
+      cb0 = __ldg(cr); cb1 = __ldg(cr + 1);
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(frow));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(frow + 64));
+    } else {
       int c, t;
       unpack_index(pk_b, c, t);
       const uint4 *cr = reinterpret_cast<const uint4 *>(s_coarse + t * kCoarse);
@@ -293,11 +281,19 @@ __global__ void __launch_bounds__(256) k_rans_decode(
     pk_b = (active && p + 2 * nl < count) ? __ldg(idxp + p + 2 * nl) : 0u;
     // every lane runs the search (inactive lanes on a valid table, their
     // state kept), so the round has no branch around it
-    int ctr, tid;
-    unpack_index(pk, ctr, tid);
+    int ctr;
+    const uint16_t *trow;
+    if constexpr (kMix) {
+      ctr = (int)pk;
+      trow = mix_row(active ? p : 0);
+    } else {
+      int tid;
+      unpack_index(pk, ctr, tid);
+      trow = bank + (size_t)tid * (kNSym + 1);
+    }
     const uint32_t slot = x & (kM - 1);
     uint32_t lo, hi;
-    const int s = cdf_search_r(bank + (size_t)tid * (kNSym + 1), c0, c1, slot, lo, hi);
+    const int s = cdf_search_r(trow, c0, c1, slot, lo, hi);
     {
       const uint32_t xn = (hi - lo) * (x >> kLogM) + slot - lo;
       x = active ? xn : x;
@@ -393,10 +389,11 @@ __device__ __forceinline__ void esc_code(int r, int &s, uint32_t &v, int &k) {
 }
 
 // ops of a symbol: 1 main + (2k + 1) bypass bits for an escape
+// (mix: idx holds the centres)
 __global__ void k_rans_count_ops(const EncChunk *__restrict__ chunks, int nchunks,
                                  const uint32_t *__restrict__ idx,
                                  const int32_t *__restrict__ vals,
-                                 uint32_t *__restrict__ ops) {
+                                 uint32_t *__restrict__ ops, int mix) {
   const int cw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (cw >= nchunks) return;
@@ -405,7 +402,8 @@ __global__ void k_rans_count_ops(const EncChunk *__restrict__ chunks, int nchunk
   for (uint32_t i = lane; i < ch.count; i += 32) {
     const int64_t q = (int64_t)ch.sym_base + i;
     int ctr, tid;
-    unpack_index(idx[q], ctr, tid);
+    if (mix) ctr = (int)idx[q];
+    else unpack_index(idx[q], ctr, tid);
     int s, k;
     uint32_t v;
     esc_code(vals[q] - ctr, s, v, k);
@@ -422,7 +420,8 @@ __global__ void k_rans_encode(const EncChunk *__restrict__ chunks, int nchunks,
                               const int32_t *__restrict__ vals,
                               uint16_t *__restrict__ scratch,
                               uint32_t *__restrict__ states_out,  // 32 per chunk
-                              uint32_t *__restrict__ nwords_out, uint32_t *status) {
+                              uint32_t *__restrict__ nwords_out, uint32_t *status,
+                              const uint32_t *__restrict__ cf) {
   const int cw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (cw >= nchunks) return;
@@ -441,12 +440,20 @@ __global__ void k_rans_encode(const EncChunk *__restrict__ chunks, int nchunks,
     if (active) {
       const int64_t q = (int64_t)ch.sym_base + p;
       int ctr, tid;
-      unpack_index(idx[q], ctr, tid);
-      esc_code(vals[q] - ctr, s, v, k);
+      if (cf) {
+        // logistic mixture: the symbol's own (cdf, frequency), centre in idx
+        ctr = (int)idx[q];
+        esc_code(vals[q] - ctr, s, v, k);
+        c0 = cf[q] & 0xFFFFu;
+        f0 = cf[q] >> 16;
+      } else {
+        unpack_index(idx[q], ctr, tid);
+        esc_code(vals[q] - ctr, s, v, k);
+        const uint16_t *t = bank + (size_t)tid * (kNSym + 1);
+        c0 = t[s];
+        f0 = (uint32_t)t[s + 1] - c0;
+      }
       if (k > kMaxEscBits) bad = true;
-      const uint16_t *t = bank + (size_t)tid * (kNSym + 1);
-      c0 = t[s];
-      f0 = (uint32_t)t[s + 1] - c0;
     }
     const int nops = active ? 1 + (k >= 0 ? 2 * k + 1 : 0) : 0;
     int rounds = nops;
@@ -533,33 +540,42 @@ void launch_cdf_bank(uint16_t *bank, uint16_t *coarse, cudaStream_t st) {
 void launch_rans_decode(const DecChunk *chunks, int nchunks, const uint16_t *bank,
                         const uint16_t *coarse, const uint32_t *idx, int64_t idx_stride,
                         int32_t *out, int64_t out_stride, int h, int w, int step,
-                        uint32_t *status, cudaStream_t st) {
+                        uint32_t *status, cudaStream_t st, bool mix) {
   if (nchunks <= 0) return;
+  const int nsm = sm_count();
+  if (mix) {
+    int wpb = 8;
+    while (wpb > 1 && (nchunks + wpb - 1) / wpb < nsm) wpb >>= 1;
+    k_rans_decode<true><<<(nchunks + wpb - 1) / wpb, 32 * wpb, 0, st>>>(
+        chunks, nchunks, bank, nullptr, idx, idx_stride, out, out_stride, h, w, step, status);
+    return;
+  }
   constexpr int smem = kNTables * kCoarse * 2 + 16;   // coarse level + mbarrier
   static std::atomic<uint64_t> attr{0};
   once_per_device(attr, [] {
-    cudaFuncSetAttribute(k_rans_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_rans_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
   });
   // one warp per chunk; with few chunks, fewer warps per block so that the
   // chunks spread over the SMs (one warp per scheduler)
-  const int nsm = sm_count();
   int wpb = 8;
   while (wpb > 1 && (nchunks + wpb - 1) / wpb < nsm) wpb >>= 1;
-  k_rans_decode<<<(nchunks + wpb - 1) / wpb, 32 * wpb, smem, st>>>(
+  k_rans_decode<false><<<(nchunks + wpb - 1) / wpb, 32 * wpb, smem, st>>>(
       chunks, nchunks, bank, coarse, idx, idx_stride, out, out_stride, h, w, step, status);
 }
 void launch_rans_count_ops(const EncChunk *chunks, int nchunks, const uint32_t *idx,
-                           const int32_t *vals, uint32_t *ops, cudaStream_t st) {
+                           const int32_t *vals, uint32_t *ops, cudaStream_t st, bool mix) {
   if (nchunks <= 0) return;
-  k_rans_count_ops<<<(nchunks + 3) / 4, 128, 0, st>>>(chunks, nchunks, idx, vals, ops);
+  k_rans_count_ops<<<(nchunks + 3) / 4, 128, 0, st>>>(chunks, nchunks, idx, vals, ops,
+                                                      mix ? 1 : 0);
 }
 void launch_rans_encode(const EncChunk *chunks, int nchunks, const uint16_t *bank,
                         const uint32_t *idx, const int32_t *vals, uint16_t *scratch,
                         uint32_t *states, uint32_t *nwords, uint32_t *status,
-                        cudaStream_t st) {
+                        cudaStream_t st, const uint32_t *cf) {
   if (nchunks <= 0) return;
   k_rans_encode<<<(nchunks + 3) / 4, 128, 0, st>>>(chunks, nchunks, bank, idx, vals, scratch,
-                                                   states, nwords, status);
+                                                   states, nwords, status, cf);
 }
 void launch_rans_pack(const EncChunk *chunks, int nchunks, const uint16_t *scratch,
                       const uint32_t *states, const uint32_t *nwords,

@@ -192,6 +192,14 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
     keep("lstm.we", we);
     keep("lstm.be", be);
   }
+  // heads: 2 outputs (Laplace mean and scale) or, four-step LL models only,
+  // 9 (logistic mixture of 3: weight logits, means, scale pre-activations)
+  {
+    auto it = ts.find("sb.s0.wh");
+    nh = (ll_mode == 0 && it != ts.end() && !it->second.shape.empty() &&
+          it->second.shape[0] == 9) ? 9 : 2;
+    mix = nh == 9;
+  }
   // four-step nets
   auto load_set = [&](const std::string &ns, StepNetDev *nets) -> bool {
     {
@@ -210,7 +218,7 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
       s.w3 = up(transpose(w, 2 * C, C)); s.b3 = up(bb); keep(p + "w3", w); keep(p + "b3", bb);
       if (!get(p + "w4", {C, 2 * C}, w) || !get(p + "b4", {C}, bb)) return false;
       s.w4 = up(transpose(w, C, 2 * C)); s.b4 = up(bb); keep(p + "w4", w); keep(p + "b4", bb);
-      if (!get(p + "wh", {2, C}, w) || !get(p + "bh", {2}, bb)) return false;
+      if (!get(p + "wh", {nh, C}, w) || !get(p + "bh", {nh}, bb)) return false;
       s.wh = up(w); s.bh = up(bb); keep(p + "wh", w); keep(p + "bh", bb);
     }
     for (int k = 1; k < 4; ++k) {
@@ -225,7 +233,7 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
       s.c1w = up(conv_tap_major(w, C, C, 3)); s.c1b = up(bb); keep(p + "w1", w); keep(p + "b1", bb);
       if (!get(p + "w2", {C, C, 3, 3}, w) || !get(p + "b2", {C}, bb)) return false;
       s.c2w = up(conv_tap_major(w, C, C, 3)); s.c2b = up(bb); keep(p + "w2", w); keep(p + "b2", bb);
-      if (!get(p + "wh", {2, C}, w) || !get(p + "bh", {2}, bb)) return false;
+      if (!get(p + "wh", {nh, C}, w) || !get(p + "bh", {nh}, bb)) return false;
       s.wh = up(w); s.bh = up(bb); keep(p + "wh", w); keep(p + "bh", bb);
     }
     return true;

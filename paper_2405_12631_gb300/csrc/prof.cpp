@@ -7,7 +7,7 @@ const char *kclass_name(int c) {
   static const char *n[KC_COUNT] = {"ctx_lstm_gates_conv3x3", "ctx_conv3x3", "ctx_conv1x1",
                                     "ctx_small", "rans_decode", "rans_encode", "cdf_bank",
                                     "lift_step", "colour", "parse", "quant",
-                                    "ctx_head_conv3x3"};
+                                    "ctx_head_conv3x3", "mix_head"};
   return (c >= 0 && c < KC_COUNT) ? n[c] : "?";
 }
 

@@ -11,6 +11,7 @@ enum KClass {
   KC_LSTM_GATES = 0, KC_CONV3, KC_CONV1, KC_SMALL_CTX, KC_RANS_DEC, KC_RANS_ENC, KC_CDF,
   KC_LIFT, KC_COLOUR, KC_PARSE, KC_QUANT,
   KC_HEAD3,  // steps 2-4 second residual conv fused with the head (3x3)
+  KC_MIX,    // logistic-mixture head, decision and per-symbol tables
   KC_COUNT
 };
 const char *kclass_name(int c);

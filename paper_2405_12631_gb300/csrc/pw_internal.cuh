@@ -23,6 +23,7 @@ constexpr uint32_t kRansL = 1u << 16;  // lower end of the state interval
 constexpr int kNPhi = 16, kNJ = 128;
 constexpr int kNTables = kNPhi * kNJ;  // 2048 tables of kNSym + 1 entries
 constexpr int kCoarse = 16;            // coarse CDF entries per table (every 8th)
+constexpr int kMixRow = kNSym + 1 + kCoarse;  // per-symbol table row: 128 entries + coarse
 constexpr int kMaxLanes = 32;
 constexpr int kMaxEscBits = 30;        // Exp-Golomb prefix length limit
 

@@ -103,7 +103,8 @@ static void lane_main(pw_server *s, int li) {
     const int64_t others = s->held - s->lane_bytes[li];
     int64_t need = 0;
     for (;;) {
-      need = Workspace::estimate(r0->g, (int)batch.size() * r0->g.nc, s->m->C, false, prec);
+      need = Workspace::estimate(r0->g, (int)batch.size() * r0->g.nc, s->m->C, false, prec,
+                                  s->m->mix);
       if (others + need <= s->budget || batch.size() == 1) break;
       batch.pop_back();
     }
@@ -226,7 +227,7 @@ int pw_server_submit(pw_server *s, const uint8_t *bs, size_t n, uint64_t *ticket
     return st;
   }
   r->key = req_key(r->g);
-  r->need = Workspace::estimate(r->g, r->g.nc, s->m->C, false, s->ctx->precision);
+  r->need = Workspace::estimate(r->g, r->g.nc, s->m->C, false, s->ctx->precision, s->m->mix);
   std::lock_guard<std::mutex> lk(s->mu);
   if (r->need > s->budget || s->queue.size() >= 4096) {
     ++s->rejected;
@@ -287,7 +288,8 @@ int pw_decode_footprint(pw_ctx *ctx, const pw_model *m, const uint8_t *bs, size_
   Geometry g;
   const int st = stream_geometry(ctx, m->m, bs, n, g);
   if (st != PW_OK) return st;
-  *bytes = (uint64_t)Workspace::estimate(g, count * g.nc, m->m.C, false, ctx->precision);
+  *bytes = (uint64_t)Workspace::estimate(g, count * g.nc, m->m.C, false, ctx->precision,
+                                         m->m.mix);
   return PW_OK;
 }
 

@@ -48,7 +48,7 @@ def test_status_strings(pw):
 def test_kernel_class_names_round_trip(pw):
     names = ["ctx_lstm_gates_conv3x3", "ctx_conv3x3", "ctx_conv1x1", "ctx_small",
              "rans_decode", "rans_encode", "cdf_bank", "lift_step", "colour", "parse", "quant",
-             "ctx_head_conv3x3"]
+             "ctx_head_conv3x3", "mix_head"]
     assert [pw.pw_kernel_class(n.encode()) for n in names] == list(range(len(names)))
     assert pw.pw_kernel_class(b"no_such_class") == -1
 
