@@ -23,7 +23,8 @@ convolutions, BF16 elsewhere); the BF16 class is timed the same way under
 The other workloads, each under "workloads" with its own key:
 * single_gray_256: one 256x256 grayscale image (sum of 8 sinusoids plus
   noise), q = 8, C = 32, FP32 class, batch 1, in both LL modes (four-step
-  and autoregressive), device-resident stream, CUDA events;
+  and autoregressive) and with the logistic-mixture (K = 3) probability
+  model (four-step LL), device-resident stream, CUDA events;
 * video_4gop_1080p: 4 GOPs x 8 frames of 1920x1080 RGB (panned 1/f canvas
   and sprites), 3 temporal levels, BF16 class, pw_decode_gop host in / host
   out, wall clock;
@@ -212,8 +213,8 @@ def cpu_baseline_samples(single_thread: bool) -> dict:
     import synthetic as S
     from oracle import codec as K
 
-    def blob_of(levels, C, ll_mode, seed=0):
-        cfg = S.ModelConfig(levels=levels, C=C, F=16, ll_mode=ll_mode)
+    def blob_of(levels, C, ll_mode, seed=0, prob=0):
+        cfg = S.ModelConfig(levels=levels, C=C, F=16, ll_mode=ll_mode, prob=prob)
         return S.pack_blob(cfg, S.random_model(cfg, seed))
 
     out = {}
@@ -225,6 +226,11 @@ def cpu_baseline_samples(single_thread: bool) -> dict:
                      "sample": "the whole 256x256 gray image, q=8, C=32"}
         if single_thread:
             return out
+    b = blob_of(4, 32, 0, prob=1)
+    bs = K.encode_image(b, gray[:128, :128], q=8.0)
+    out["single_gray_256_four_step_ll_logistic_mixture"] = {
+        "pixels": 128 * 128, "s": _time_oracle_decode(b, bs, K.decode_image),
+        "sample": "128x128 crop of the 256x256 gray image, q=8, C=32, mixture model"}
     b = blob_of(4, 64, 0)
     crop = S.rgb_natural(H, W, seed=1)[:256, :256]
     bs = K.encode_image(b, crop, q=8.0)
@@ -439,7 +445,9 @@ def _events_ms(stream, fn, reps: int):
 def single_gray_run(pw, local, stream_ptr, steps: int, warmup: int):
     """One 256x256 grayscale image (128 + 8 random sinusoids + N(0, 8^2),
     seed 0), q = 8, C = 32 context model, FP32 class, batch 1, in both LL
-    modes; device-resident stream -> device image, CUDA events per decode."""
+    modes, and with the logistic-mixture (K = 3) probability model in place
+    of the Laplace one (four-step LL); device-resident stream -> device
+    image, CUDA events per decode."""
     import torch
     import synthetic as S
     dev = torch.device("cuda", local)
@@ -447,8 +455,9 @@ def single_gray_run(pw, local, stream_ptr, steps: int, warmup: int):
     img = S.gray_sinusoids(256, 256, seed=0)
     res = {"workload": "single 256x256 grayscale image, 4-level lifting, C=32, q=8, FP32, batch 1",
            "timing": "CUDA events per decode, device stream in, device image out"}
-    for mode, name in ((0, "four_step_ll"), (1, "autoregressive_ll")):
-        cfg = S.ModelConfig(levels=4, C=32, F=16, ll_mode=mode)
+    for mode, name, prob in ((0, "four_step_ll", 0), (1, "autoregressive_ll", 0),
+                             (0, "four_step_ll_logistic_mixture", 1)):
+        cfg = S.ModelConfig(levels=4, C=32, F=16, ll_mode=mode, prob=prob)
         c = pw.Codec(local, "fp32", stream=stream_ptr)
         m = c.load_model(S.pack_blob(cfg, S.random_model(cfg, 0)))
         bs = c.encode_image(m, img, q=8.0)
