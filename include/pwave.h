@@ -130,6 +130,21 @@ int pw_model_random_blob(const pw_model_cfg *cfg, uint64_t seed, void *buf, size
 int pw_model_init_random(pw_ctx *ctx, const pw_model_cfg *cfg, uint64_t seed,
                          pw_model **out);
 
+/* Graph replay of image decodes (on by default). The device work of a
+ * batch image decode - stream parsing, every context-model pass, the rANS
+ * passes, dequantisation, inverse lifting and post-processing - depends only
+ * on the cached plan (image size, channels, batch, model, chunk layout), so
+ * after one direct run of a plan, and once the convolution autotuner has
+ * settled, the context captures that chain into a CUDA graph (on a private
+ * stream, so any user stream works, including the legacy default stream)
+ * and replays it for later decodes of the plan: one launch instead of
+ * hundreds. While per-kernel profiling is on, decodes run directly.
+ * Results are identical either way. pw_ctx_set_graphs returns the previous
+ * setting (or a negative pw_status); pw_ctx_graph_replays counts the
+ * decodes served by a replayed graph. */
+int pw_ctx_set_graphs(pw_ctx *ctx, int enable);
+uint64_t pw_ctx_graph_replays(const pw_ctx *ctx);
+
 /* ---- images (Sections 3.1, 3.2) ----------------------------------------- */
 
 /* Encode one image (host or device samples) into a newly allocated host

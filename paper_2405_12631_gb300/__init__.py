@@ -75,6 +75,8 @@ _sig = {
     "pw_model_free": (None, [_P]),
     "pw_model_hash": (C.c_uint64, [_P]),
     "pw_model_mixture": (C.c_int, [_P]),
+    "pw_ctx_set_graphs": (C.c_int, [_P, C.c_int]),
+    "pw_ctx_graph_replays": (C.c_uint64, [_P]),
     "pw_model_random_blob": (C.c_int, [C.POINTER(pw_model_cfg), C.c_uint64, _P, C.c_size_t,
                                        C.POINTER(C.c_size_t)]),
     "pw_model_init_random": (C.c_int, [_P, C.POINTER(pw_model_cfg), C.c_uint64,
@@ -280,6 +282,19 @@ class Codec:
         """pw_ctx_set_lane_rule: streams this context encodes use one rANS
         state per 2^s symbols (s in 5..7; default 7)."""
         check(pw_ctx_set_lane_rule(self.ctx, int(log2_symbols_per_state)))
+
+    def set_graphs(self, enable: bool) -> bool:
+        """pw_ctx_set_graphs: replay image decodes from captured CUDA graphs
+        (default on); returns the previous setting."""
+        old = pw_ctx_set_graphs(self.ctx, int(bool(enable)))
+        if old < 0:
+            check(-old)
+        return bool(old)
+
+    @property
+    def graph_replays(self) -> int:
+        """Decodes served by a replayed CUDA graph (pw_ctx_graph_replays)."""
+        return int(pw_ctx_graph_replays(self.ctx))
 
     def close(self):
         if self.ctx:

@@ -76,7 +76,21 @@ struct Plan {
   std::vector<int64_t> gbase;   // decode descriptor block of each group
   // encode
   PoolBuf d_enc, d_ops, d_scratch, d_states, d_nwords, d_outoff, d_payload, d_img;
+  // the decode chain as a CUDA graph (captured after one direct run)
+  cudaStream_t stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const float *graph_recon = nullptr;   // its reconstructed planes
+  uint64_t graph_launches = 0;          // kernel launches it holds
+  int direct_runs = 0;
+  bool graph_bad = false;               // capture failed: stay direct
+  ~Plan() {
+    if (gexec) {
+      cudaStreamSynchronize(stream);
+      cudaGraphExecDestroy(gexec);
+    }
+  }
   void set_stream(cudaStream_t s) {
+    stream = s;
     for (PoolBuf *b : {&d_chunks, &d_tpl, &d_deltas, &d_ptrs, &d_lens, &d_stage, &d_out, &d_enc,
                        &d_ops, &d_scratch, &d_states, &d_nwords, &d_outoff, &d_payload, &d_img})
       b->st = s;
@@ -95,10 +109,11 @@ static PlanCache &cache_of(pw_ctx *ctx) {
 
 static std::string geo_key(const char *kind, const Geometry &g, int B, const Model &m, int params) {
   char buf[256];
-  // the model's unique id and channel count: a workspace is sized by both
-  snprintf(buf, sizeof(buf), "%s:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%llu:%d:%d", kind, g.H, g.W, g.nc,
-           g.levels, g.colour, g.bitdepth, g.lossless, g.ll_ar, g.chunk, B,
-           (unsigned long long)m.uid, m.C, params);
+  // the model's unique id and channel count: a workspace is sized by both;
+  // the chunk layout (balanced flag, lane rule) shapes the plan's chunk tables
+  snprintf(buf, sizeof(buf), "%s:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%llu:%d:%d", kind, g.H, g.W,
+           g.nc, g.levels, g.colour, g.bitdepth, g.lossless, g.ll_ar, g.chunk, g.balanced,
+           g.lane_shift, B, (unsigned long long)m.uid, m.C, params);
   return buf;
 }
 
@@ -201,14 +216,24 @@ static uint16_t prec_flags(pw_ctx *ctx) {
 // --------------------------------------------------------------------------
 // Symbol decoding of a batch (context model + rANS), shared by decode and
 // pw_decode_symbols. Streams are device pointers in ptrs (host array).
-static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *const *ptrs,
-                              const size_t *lens, const StreamHeader &h0) {
+// Host half of a batch decode's stream table: the streams' device pointers
+// and lengths into the plan's pinned staging, which the device work below
+// copies to the device (so that a captured chain reads the current table).
+static void fill_stream_table(Plan &pl, const uint8_t *const *ptrs, const size_t *lens) {
+  uint64_t *hs = reinterpret_cast<uint64_t *>(pl.h_small.p);
+  for (int b = 0; b < pl.B; ++b) { hs[b] = (uint64_t)(uintptr_t)ptrs[b]; hs[pl.B + b] = lens[b]; }
+}
+
+// Device work of a batch decode up to the quantised latent (stream table
+// filled by fill_stream_table). Every size and flag it uses is fixed by the
+// plan (geometry, batch, model, chunk layout), so it can be captured once
+// and replayed for other streams of the plan.
+static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader &h0) {
   const Geometry &g = pl.g;
   const int B = pl.B, P = B * g.nc;
   cudaStream_t st = ctx->stream;
   // pointer / length tables -> device
-  uint64_t *hs = reinterpret_cast<uint64_t *>(pl.h_small.p);
-  for (int b = 0; b < B; ++b) { hs[b] = (uint64_t)(uintptr_t)ptrs[b]; hs[B + b] = lens[b]; }
+  const uint64_t *hs = reinterpret_cast<const uint64_t *>(pl.h_small.p);
   PW_CUDA_TRY(cudaMemcpyAsync(pl.d_ptrs.p, hs, B * 8, cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemcpyAsync(pl.d_lens.p, hs + B, B * 8, cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemsetAsync(ctx->status, 0, 4, st));
@@ -220,7 +245,7 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const uint8_t *co
   ex.hash = m.hash;
   DecChunk *dch = reinterpret_cast<DecChunk *>(pl.d_chunks.p);
   double stream_bytes = 0;
-  for (int b = 0; b < B; ++b) stream_bytes += (double)lens[b];
+  for (int b = 0; b < B; ++b) stream_bytes += (double)hs[B + b];
   const double total_syms = (double)P * g.plane_elems;
   {
   ProfScope ps(ctx, KC_PARSE, 0.0, (double)B * g.nc * g.chunks.size() * (8 + sizeof(DecChunk)));
@@ -351,7 +376,8 @@ static int decode_to_planes(pw_ctx *ctx, Model &m, int B, const uint8_t *const *
   if ((s = get_plan(ctx, m, g, B, "dec", false, &pl))) return s;
   std::vector<const uint8_t *> ptrs;
   if ((s = stage_streams(ctx, *pl, B, bs, n, 0, ptrs))) return s;
-  if ((s = decode_symbols_dev(ctx, m, *pl, ptrs.data(), n, h0))) return s;
+  fill_stream_table(*pl, ptrs.data(), n);
+  if ((s = decode_symbols_dev(ctx, m, *pl, h0))) return s;
   const int P = B * g.nc;
   SbTable tb = make_sbtable(g, P);
   launch_dequant_all(pl->ws.Q, pl->ws.Yf, (int64_t)P * g.plane_elems, tb, g.nc,
@@ -362,6 +388,86 @@ static int decode_to_planes(pw_ctx *ctx, Model &m, int B, const uint8_t *const *
   *planes = pl->ws.planes;
   *geo = g;
   return PW_OK;
+}
+
+// Device work of an image decode after the stream table: symbols,
+// dequantisation, inverse transform and post-processing (Section 3.1, of
+// lossy images, into the dequantised subbands' buffer, which the inverse
+// transform has consumed). *recon: the reconstructed planes (plan-owned).
+static int decode_chain(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader &h0,
+                        const float **recon) {
+  const Geometry &g = pl.g;
+  const int P = pl.B * g.nc;
+  int s;
+  if ((s = decode_symbols_dev(ctx, m, pl, h0))) return s;
+  SbTable tb = make_sbtable(g, P);
+  {
+    ProfScope ps(ctx, KC_QUANT, 0.0, (double)P * g.plane_elems * 8.0);
+    launch_dequant_all(pl.ws.Q, pl.ws.Yf, (int64_t)P * g.plane_elems, tb, g.nc,
+                       reinterpret_cast<float *>(pl.d_deltas.p), ctx->stream);
+  }
+  bump(ctx);
+  if ((s = lift_inverse_planes(ctx, m, g, pl.ws, pl.ws.planes))) return s;
+  *recon = pl.ws.planes;
+  if (m.has_post && !g.lossless) {
+    if ((s = post_process_planes(ctx, m, g, P, pl.ws.planes, pl.ws.Yf))) return s;
+    *recon = pl.ws.Yf;
+  }
+  return PW_OK;
+}
+
+// Capture the plan's decode chain on the context's private stream into a
+// CUDA graph. On any failure the plan stays on direct launches.
+static void capture_chain(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader &h0) {
+  if (!ctx->cap_stream &&
+      cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    pl.graph_bad = true;
+    return;
+  }
+  cudaStream_t user = ctx->stream;
+  ctx->stream = ctx->cap_stream;
+  const uint64_t l0 = ctx->launches;
+  cudaGraph_t graph = nullptr;
+  const float *recon = nullptr;
+  int s = PW_ECUDA;
+  if (cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+    s = decode_chain(ctx, m, pl, h0, &recon);
+    if (cudaStreamEndCapture(ctx->cap_stream, &graph) != cudaSuccess) s = PW_ECUDA;
+  }
+  ctx->stream = user;
+  const uint64_t nl = ctx->launches - l0;
+  ctx->launches = l0;
+  if (launch_failed()) { launch_failed() = false; s = PW_EUNSUPPORTED; }
+  if (s == PW_OK && graph && cudaGraphInstantiate(&pl.gexec, graph, 0) == cudaSuccess) {
+    pl.graph_launches = nl;
+    pl.graph_recon = recon;
+  } else {
+    pl.gexec = nullptr;
+    pl.graph_bad = true;
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();
+}
+
+// decode_chain, replayed from the plan's graph once the plan has run
+// directly (kernel attributes set, buffers in place) and no convolution
+// class is still being tuned; direct while the context profiles kernels.
+static int run_decode_chain(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader &h0,
+                            const float **recon) {
+  const bool eligible = ctx->graphs && !prof_of(ctx).on && !pl.graph_bad &&
+                        pl.direct_runs > 0 && tune_settled();
+  if (eligible && !pl.gexec) capture_chain(ctx, m, pl, h0);
+  if (eligible && pl.gexec) {
+    PW_CUDA_TRY(cudaGraphLaunch(pl.gexec, ctx->stream));
+    ctx->launches += pl.graph_launches;
+    ctx->graph_replays += 1;
+    *recon = pl.graph_recon;
+    return PW_OK;
+  }
+  const int s = decode_chain(ctx, m, pl, h0, recon);
+  if (s == PW_OK) pl.direct_runs += 1;
+  return s;
 }
 
 int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,
@@ -385,24 +491,11 @@ int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const s
   if ((s = get_plan(ctx, m, g, B, "dec", false, &pl))) return s;
   std::vector<const uint8_t *> ptrs;
   if ((s = stage_streams(ctx, *pl, B, bs, n, on_dev, ptrs))) return s;
-  if ((s = decode_symbols_dev(ctx, m, *pl, ptrs.data(), n, h0))) return s;
+  fill_stream_table(*pl, ptrs.data(), n);
+  const float *recon = nullptr;
+  if ((s = run_decode_chain(ctx, m, *pl, h0, &recon))) return s;
   cudaStream_t st = ctx->stream;
   const int P = B * g.nc;
-  SbTable tb = make_sbtable(g, P);
-  {
-    ProfScope ps(ctx, KC_QUANT, 0.0, (double)P * g.plane_elems * 8.0);
-    launch_dequant_all(pl->ws.Q, pl->ws.Yf, (int64_t)P * g.plane_elems, tb, g.nc,
-                       reinterpret_cast<float *>(pl->d_deltas.p), st);
-  }
-  bump(ctx);
-  if ((s = lift_inverse_planes(ctx, m, g, pl->ws, pl->ws.planes))) return s;
-  // post-processing (Section 3.1) of lossy images, into the dequantised
-  // subbands' buffer, which the inverse transform has consumed
-  const float *recon = pl->ws.planes;
-  if (m.has_post && !g.lossless) {
-    if ((s = post_process_planes(ctx, m, g, P, pl->ws.planes, pl->ws.Yf))) return s;
-    recon = pl->ws.Yf;
-  }
   // output: direct when the batch is one contiguous packed device buffer
   const int64_t row = (int64_t)g.W * g.nc * bps, img = row * g.H;
   bool direct = true;
@@ -730,6 +823,7 @@ void pw_ctx_destroy(pw_ctx *c) {
   cudaStreamSynchronize(c->stream);
   delete reinterpret_cast<PlanCache *>(c->plan_cache);
   delete reinterpret_cast<Prof *>(c->prof);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   cudaFree(c->bank);
   cudaFree(c->status);
   delete c;
@@ -1306,6 +1400,15 @@ int pw_mix_tables(pw_ctx *c, int64_t n, const int32_t *key9, uint16_t *cdf) {
 
 int pw_model_mixture(const pw_model *m) { return m && m->m.mix ? 1 : 0; }
 
+int pw_ctx_set_graphs(pw_ctx *c, int enable) {
+  if (!c) return -PW_EINVAL;
+  const int old = c->graphs;
+  c->graphs = enable ? 1 : 0;
+  return old;
+}
+
+uint64_t pw_ctx_graph_replays(const pw_ctx *c) { return c ? c->graph_replays : 0; }
+
 static int lift_stage(pw_ctx *c, const pw_model *mm, int H, int W, int lossless, const float *in,
                       float *out, bool fwd) {
   if (!c || !mm || !in || !out) return PW_EINVAL;
@@ -1362,7 +1465,8 @@ int pw_decode_symbols(pw_ctx *c, const pw_model *mm, const uint8_t *bs, size_t n
   std::vector<const uint8_t *> ptrs;
   const uint8_t *const bsp[1] = {bs};
   if ((s = stage_streams(c, *pl, 1, bsp, &n, 0, ptrs))) return s;
-  if ((s = decode_symbols_dev(c, m, *pl, ptrs.data(), &n, h0))) return s;
+  fill_stream_table(*pl, ptrs.data(), &n);
+  if ((s = decode_symbols_dev(c, m, *pl, h0))) return s;
   PW_CUDA_TRY(cudaMemcpyAsync(q, pl->ws.Q, (size_t)g.nc * g.plane_elems * 4,
                               cudaMemcpyDeviceToHost, c->stream));
   return check_status(c, &pl->ws);

@@ -1213,6 +1213,15 @@ static void tune_record(uint64_t key, int cand, cudaEvent_t e0, cudaEvent_t e1) 
   g_tune_pending.push_back(TunePending{key, cand, e0, e1});
 }
 
+bool tune_settled() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  tune_poll_locked();
+  if (!g_tune_on.load()) return true;
+  for (const auto &kv : g_tune)
+    if (!kv.second.tuned) return false;
+  return g_tune_pending.empty();
+}
+
 int tune_set_enabled(int on) {
   const int old = g_tune_on.load();
   g_tune_on.store(on ? 1 : 0);

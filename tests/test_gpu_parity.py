@@ -372,3 +372,24 @@ def test_ar_ll_decodes_oracle_stream(codec):
         pytest.skip(f"{int(diff.sum())} certified near-tie index differences in this input")
     bs = K.encode_image(blob, img, q=8.0, chunk=256)
     assert np.array_equal(codec.decode_symbols(gm, bs), _flat([qsb]))
+
+
+def test_lane_rules_share_one_context(codec, model32):
+    """Streams of one geometry with different chunk layouts (lane rule,
+    balanced flag) coded and decoded on one context: each plan follows its
+    own stream's layout."""
+    blob, gm, om = model32
+    img = S.gray_sinusoids(96, 128, seed=19)
+    q_ref = codec.analyse(gm, img, q=8.0)
+    streams = []
+    for ls in (7, 5, 7):
+        codec.set_lane_rule(ls)
+        bs = codec.encode_image(gm, img, q=8.0, chunk=512)
+        assert (bs[52] or 7) == ls
+        streams.append(bs)
+    codec.set_lane_rule(7)
+    assert streams[0] == streams[2] and streams[0] != streams[1]
+    lay = K.encode_image(blob, img, q=8.0, chunk=512, lane_shift=5)
+    for bs in streams + streams[::-1]:
+        assert np.array_equal(codec.decode_symbols(gm, bs), q_ref)
+    assert K.parse_header(lay)["n_chunks"] == K.parse_header(streams[1])["n_chunks"]
