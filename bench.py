@@ -466,17 +466,20 @@ def single_gray_run(pw, local, stream_ptr, steps: int, warmup: int):
 
         def one():
             c.decode_batch_device(m, [d_bs.data_ptr()], [len(bs)], out.data_ptr(), (256, 256))
-        for _ in range(warmup):
+        for _ in range(max(warmup, 3)):
             one()
         torch.cuda.synchronize()
+        r0 = c.graph_replays
         t = _events_ms(stream, one, steps)
+        replays = c.graph_replays - r0
         dec = out.cpu().numpy()
         mse = float(np.mean((dec.astype(np.float64) - img) ** 2))
         ms = float(np.median(t))
         res[name] = {"value": 256 * 256 / (ms / 1e3) / 1e6, "unit": "MPix/s",
                      "p50_ms": ms, "p99_ms": float(np.percentile(t, 99)),
                      "bpp": 8.0 * len(bs) / (256 * 256),
-                     "psnr_db": 10 * np.log10(255.0 ** 2 / mse)}
+                     "psnr_db": 10 * np.log10(255.0 ** 2 / mse),
+                     "graph_replays": replays}
         m.close()
         c.close()
     return res
