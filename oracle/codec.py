@@ -39,9 +39,12 @@ steps.
   8 u32 width          12 u32 height             2 autoregressive LL,
                                                  16 balanced chunks,
                                                  32 logistic-mixture
-                                                 probability model; the
-                                                 library also records its
-                                                 precision class in bits 2-3)
+                                                 probability model; bits 2-3:
+                                                 the precision class, which
+                                                 the library records; 3 =
+                                                 the integer-network context
+                                                 model, which the oracle
+                                                 writes and follows too)
  16 u8 ncomp           17 u8 levels            18 u8 bitdepth
  19 u8 colour (0 gray, 1 YCbCr, 2 RCT, 3 raw planes)
  20 f32 Delta_L        24 f32 Delta_H          28 u16 T   30 u8 log2 M
@@ -72,6 +75,7 @@ import struct
 import numpy as np
 
 from . import entropy as E
+from . import intnet as I
 from . import rans as R
 from .blob import model_hash, read_blob
 from .context import ContextModel, step_map, step_positions
@@ -87,9 +91,11 @@ KG = 1.0 - KR - KB
 
 
 class Model:
-    """A parsed weight blob: lifting nets, context model, hash."""
+    """A parsed weight blob: lifting nets, context model, hash. integer:
+    encode with the integer-network context model (oracle.intnet; streams
+    say so in header bits 2-3 = 3, and decoding follows the stream)."""
 
-    def __init__(self, blob: bytes):
+    def __init__(self, blob: bytes, integer: bool = False):
         cfg, t = read_blob(blob)
         self.cfg = cfg
         self.levels = cfg["levels"]
@@ -102,6 +108,15 @@ class Model:
         # logistic-mixture heads (9 outputs) instead of Laplace ones (2)
         self.mixture = cfg["ll_mode"] == 0 and t["sb.s0.wh"].shape[0] == 9
         self.hash = model_hash(blob)
+        self.integer = integer
+        self._intctx = None
+        if integer and (self.mixture or self.ll_mode):
+            raise ValueError("the integer context model is four-step LL with Laplace heads")
+
+    def int_context(self) -> I.IntContextModel:
+        if self._intctx is None:
+            self._intctx = I.IntContextModel(self.tensors, self.C)
+        return self._intctx
 
 
 # --------------------------------------------------------------------------
@@ -173,6 +188,13 @@ def dequantise(q: np.ndarray, delta32: np.float32) -> np.ndarray:
 
 # --------------------------------------------------------------------------
 # context parameters
+def int_params(t, j):
+    """(mu, sigma) that the index decision maps exactly to (t, j): t / 16
+    and the middle of scale bin j."""
+    return (np.asarray(t, dtype=np.float64) / 16.0,
+            E.sigma_of_bin(np.asarray(j)).astype(np.float64))
+
+
 def context_params_all(model: Model, qsb: list):
     """Entropy parameters at every position of every subband, all symbols
     known: (mu, sigma) arrays, or for a mixture model [h, w, 9] arrays of
@@ -181,6 +203,8 @@ def context_params_all(model: Model, qsb: list):
     Equivalent to what the decoder computes step by step, because each step
     only reads positions of earlier steps (the nets mask the rest).
     """
+    if model.integer:
+        return [int_params(t, j) for t, j in I.context_tj_all(model.int_context(), qsb)]
     cm = model.ctx
     out = []
     h = c = None
@@ -320,7 +344,8 @@ def _encode_symbols(model, qcomp, shapes, *, width, height, bitdepth, colour,
         b = R.pack_chunk(st, words)
         payload.append(b)
         offsets.append(offsets[-1] + len(b))
-    flags = (1 if lossless else 0) | (2 if ll_ar else 0) | 16 | (32 if model.mixture else 0)
+    flags = ((1 if lossless else 0) | (2 if ll_ar else 0) | 16 | (32 if model.mixture else 0) |
+             (12 if model.integer else 0))
     head = (b"PWBS" + struct.pack("<HHIIBBBBffHBBIIQI", 1, flags, width, height,
                                   len(qcomp), model.levels, bitdepth, colour,
                                   float(d32), float(d32), E.T, E.LOG2M, LANES,
@@ -331,9 +356,11 @@ def _encode_symbols(model, qcomp, shapes, *, width, height, bitdepth, colour,
 
 def encode_image(blob: bytes, img: np.ndarray, *, q: float = 8.0,
                  lossless: bool = False, bitdepth: int | None = None,
-                 chunk: int = DEFAULT_CHUNK, lane_shift: int = 7) -> bytes:
-    """Encode an (h, w) or (h, w, 3) uint8/uint16 image."""
-    model = Model(blob)
+                 chunk: int = DEFAULT_CHUNK, lane_shift: int = 7,
+                 integer: bool = False) -> bytes:
+    """Encode an (h, w) or (h, w, 3) uint8/uint16 image (integer: with the
+    integer-network context model)."""
+    model = Model(blob, integer=integer)
     if bitdepth is None:
         bitdepth = 8 if img.dtype == np.uint8 else 16
     planes, colour = colour_forward(img, lossless, bitdepth)
@@ -357,6 +384,7 @@ def parse_header(bs: bytes) -> dict:
     base = 64 + 4 * (nch + 1)
     return dict(version=ver, lossless=bool(flags & 1), ll_ar=bool(flags & 2),
                 balanced=bool(flags & 16), mixture=bool(flags & 32),
+                integer=((flags >> 2) & 3) == 3,
                 lane_shift=bs[52] or 7,
                 width=width, height=height, ncomp=ncomp, levels=levels,
                 bitdepth=bitdepth, colour=colour, delta_l=f32(dl), delta_h=f32(dh),
@@ -395,6 +423,10 @@ def decode_symbols(model: Model, bs: bytes, params: list | None = None):
         raise ValueError("stream was made with another model")
     if hd["mixture"] != model.mixture:
         raise ValueError("probability model of the stream and the model differ")
+    integer = hd["integer"]
+    if integer and (hd["mixture"] or hd["ll_ar"]):
+        raise ValueError("integer context model streams are four-step LL, Laplace")
+    ic = model.int_context() if integer else None
     L = hd["levels"]
     mult = 1 << L
     Hp = -(-hd["height"] // mult) * mult
@@ -439,6 +471,12 @@ def decode_symbols(model: Model, bs: bytes, params: list | None = None):
                 continue
             if params is not None:
                 l = ns = None
+            elif integer and i == 0:
+                l, ns = np.zeros((H, W, model.C), dtype=np.int64), "ll"
+            elif integer:
+                up = shapes[i - 1][0] < H
+                h_state, c_state = ic.lstm(qsb[i - 1], h_state, c_state, up)
+                l, ns = h_state, "sb"
             elif i == 0:
                 l, ns = np.zeros((H, W, model.C)), "ll"
             else:
@@ -449,6 +487,8 @@ def decode_symbols(model: Model, bs: bytes, params: list | None = None):
             for k in range(4):
                 if params is not None:
                     par = params[comp][i]
+                elif integer:
+                    par = int_params(*ic.step_tj(k, s, l, ns))
                 elif model.mixture:
                     par = E.mix_params(cm.step_head(k, s.astype(np.float64), l, ns))
                 else:
