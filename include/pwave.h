@@ -41,14 +41,22 @@ typedef enum {
 } pw_status;
 
 /* Arithmetic of the context-model and lifting convolutions. FP32 is the
- * plain SIMT path; BF16 runs the convolutions on tcgen05 tensor cores with
+ * plain SIMT path; INT8 is the integer-network context model (int8 weights
+ * with one power-of-two scale per tensor, int8 activations at fixed binary
+ * points, round-half-up requantisation, hard sigmoid / tanh ConvLSTM, a head
+ * whose outputs are the table indices: every operation exact integer
+ * arithmetic, so any two implementations derive identical tables; four-step
+ * LL Laplace models, loaded in an INT8 context; lifting as FP32);
+ * BF16 runs the convolutions on tcgen05 tensor cores with
  * FP32 accumulation (and, for lossy streams, layers 2 and 3 of the inverse
  * lifting CNN); FP8 is BF16 with the three 3x3 context convolutions (ConvLSTM
  * gates, residual blocks of steps 2-4) in E4M3 with per-channel scales and
  * FP32 accumulation. The entropy-parameter -> table decision and the CDF
  * tables are FP32/integer in every mode. A stream decodes only with the
  * precision class that encoded it (recorded in the stream header). */
-typedef enum { PW_PREC_FP32 = 0, PW_PREC_BF16 = 1, PW_PREC_FP8 = 2 } pw_precision;
+typedef enum {
+  PW_PREC_FP32 = 0, PW_PREC_BF16 = 1, PW_PREC_FP8 = 2, PW_PREC_INT8 = 3
+} pw_precision;
 
 typedef struct pw_ctx pw_ctx;
 typedef struct pw_model pw_model;

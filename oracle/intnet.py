@@ -130,20 +130,24 @@ def htanh(x):
 # integer layers (exact int64)
 def conv_i(x: np.ndarray, wq: np.ndarray, bq: np.ndarray) -> np.ndarray:
     """acc = b_q + conv(x, w_q), zero padding. x [H, W, Cin] int, w_q
-    [Cout, Cin, k, k] (or [Cout, Cin] for 1x1) -> [H, W, Cout] int64."""
-    x = np.asarray(x, dtype=np.int64)
+    [Cout, Cin, k, k] (or [Cout, Cin] for 1x1) -> [H, W, Cout] int64.
+
+    The products and sums are integers far below 2^53, so they are formed
+    exactly in FP64 (numpy's matrix product) and returned as int64."""
+    x = np.asarray(x, dtype=np.float64)
+    wf = np.asarray(wq, dtype=np.float64)
     if wq.ndim == 2:
-        return x @ wq.T + bq
+        return np.rint(x @ wf.T + bq).astype(np.int64)
     H, W, _ = x.shape
     k = wq.shape[2]
     r = k // 2
-    xp = np.zeros((H + 2 * r, W + 2 * r, x.shape[2]), dtype=np.int64)
+    xp = np.zeros((H + 2 * r, W + 2 * r, x.shape[2]))
     xp[r:r + H, r:r + W] = x
-    out = np.zeros((H, W, wq.shape[0]), dtype=np.int64) + bq
+    out = np.zeros((H, W, wq.shape[0])) + bq
     for dy in range(k):
         for dx in range(k):
-            out += xp[dy:dy + H, dx:dx + W, :] @ wq[:, :, dy, dx].T
-    return out
+            out += xp[dy:dy + H, dx:dx + W, :] @ wf[:, :, dy, dx].T
+    return np.rint(out).astype(np.int64)
 
 
 def dw_i(x: np.ndarray, wq: np.ndarray, bq: np.ndarray) -> np.ndarray:

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpwave.so")
 
 PW_OK, PW_EINVAL, PW_ENOMEM, PW_ECORRUPT, PW_EUNSUPPORTED, PW_ETIMEOUT, PW_EAGAIN, PW_ECUDA = range(8)
-PW_PREC_FP32, PW_PREC_BF16, PW_PREC_FP8 = 0, 1, 2
+PW_PREC_FP32, PW_PREC_BF16, PW_PREC_FP8, PW_PREC_INT8 = 0, 1, 2, 3
 
 
 class PwError(RuntimeError):
@@ -271,8 +271,8 @@ class Codec:
     """A libpwave context (one CUDA device, one stream, one precision)."""
 
     def __init__(self, device: int = 0, precision: str | int = "fp32", stream: int = 0):
-        prec = {"fp32": PW_PREC_FP32, "bf16": PW_PREC_BF16, "fp8": PW_PREC_FP8}.get(precision,
-                                                                                precision)
+        prec = {"fp32": PW_PREC_FP32, "bf16": PW_PREC_BF16, "fp8": PW_PREC_FP8,
+                "int8": PW_PREC_INT8}.get(precision, precision)
         h = C.c_void_p()
         check(pw_ctx_create(int(device), C.c_void_p(stream or None), int(prec), C.byref(h)))
         self.ctx = h

@@ -179,7 +179,7 @@ void drop_plans(pw_ctx *ctx) {
 
 static int check_status(pw_ctx *ctx, Workspace *ws = nullptr) {
   if (launch_failed()) { launch_failed() = false; return PW_EUNSUPPORTED; }
-  if (ws && ctx->precision != PW_PREC_FP32) {
+  if (ws && tc_precision(ctx->precision)) {
     cudaStreamSynchronize(ctx->stream);
     if (tc_error(*ws)) { set_last_error("a tensor-core kernel's bounded wait expired"); return PW_ETIMEOUT; }
   }
@@ -237,7 +237,7 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeade
   PW_CUDA_TRY(cudaMemcpyAsync(pl.d_ptrs.p, hs, B * 8, cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemcpyAsync(pl.d_lens.p, hs + B, B * 8, cudaMemcpyHostToDevice, st));
   PW_CUDA_TRY(cudaMemsetAsync(ctx->status, 0, 4, st));
-  if (ctx->precision != PW_PREC_FP32) tc_error_reset(pl.ws, st);
+  if (tc_precision(ctx->precision)) tc_error_reset(pl.ws, st);
   ParseExpect ex{};
   ex.width = h0.width; ex.height = h0.height; ex.ncomp = g.nc; ex.levels = g.levels;
   ex.bitdepth = g.bitdepth; ex.colour = g.colour; ex.flags = h0.flags; ex.chunk = g.chunk;
@@ -557,7 +557,7 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
   const int P = B * g.nc;
   cudaStream_t st = ctx->stream;
   Workspace &ws = pl.ws;
-  if (ctx->precision != PW_PREC_FP32) tc_error_reset(ws, st);
+  if (tc_precision(ctx->precision)) tc_error_reset(ws, st);
   launch_cdf_bank(ctx->bank, ctx->coarse, st);
   bump(ctx);
   for (int sb = 0; sb < g.nsb; ++sb) {
@@ -791,7 +791,7 @@ void pw_free(void *p) { std::free(p); }
 
 int pw_ctx_create(int device, void *stream, int precision, pw_ctx **out) {
   if (!out || (precision != PW_PREC_FP32 && precision != PW_PREC_BF16 &&
-               precision != PW_PREC_FP8)) {
+               precision != PW_PREC_FP8 && precision != PW_PREC_INT8)) {
     set_last_error("bad precision"); return PW_EINVAL;
   }
   int ndev = 0;
@@ -1327,7 +1327,7 @@ static int context_all(pw_ctx *c, Model &m, int H, int W, const int32_t *q, Plan
   *plo = pl;
   cudaStream_t st = c->stream;
   PW_CUDA_TRY(cudaMemcpyAsync(pl->ws.Q, q, g.plane_elems * 4, cudaMemcpyHostToDevice, st));
-  if (c->precision != PW_PREC_FP32) tc_error_reset(pl->ws, st);
+  if (tc_precision(c->precision)) tc_error_reset(pl->ws, st);
   for (int sb = 0; sb < g.nsb; ++sb) {
     if (sb == 0 && m.ll_mode == 1) {
       if ((s = launch_ll_ar_params(pl->ws.Q, 1, g.sh[0], g.sw[0], m.C, ar_weights(m), pl->ws.idx,
@@ -1359,7 +1359,7 @@ int pw_context_params(pw_ctx *c, const pw_model *mm, int H, int W, const int32_t
   PW_CUDA_TRY(cudaMemcpyAsync(mu, pl->ws.mu, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
   PW_CUDA_TRY(cudaMemcpyAsync(sigma, pl->ws.sg, g.plane_elems * 4, cudaMemcpyDeviceToHost, st));
   if ((s = finish(c))) return s;
-  if (c->precision != PW_PREC_FP32 && tc_error(pl->ws)) {
+  if (tc_precision(c->precision) && tc_error(pl->ws)) {
     set_last_error("a tensor-core kernel's bounded wait expired");
     return PW_ETIMEOUT;
   }

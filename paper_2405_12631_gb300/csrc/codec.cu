@@ -131,7 +131,7 @@ static int64_t max_step_symbols(const Geometry &g) {
 
 int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec, cudaStream_t st,
                      bool mix) {
-  const bool bf16 = prec != PW_PREC_FP32;
+  const bool bf16 = tc_precision(prec);
   release();
   stream = st;
   P = P_;
@@ -182,7 +182,7 @@ int Workspace::alloc(const Geometry &g, int P_, int C, bool params, int prec, cu
 }
 
 int64_t Workspace::estimate(const Geometry &g, int P, int C, bool params, int prec, bool mix) {
-  const bool bf16 = prec != PW_PREC_FP32;
+  const bool bf16 = tc_precision(prec);
   const int64_t pe = (int64_t)P * g.Hp * g.Wp;
   const int64_t big = (int64_t)P * g.sh.back() * g.sw.back();
   auto al = [](int64_t b) { return (b + 1023) / 1024 * 1024; };
@@ -214,20 +214,23 @@ int run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb) {
   if (first) ws.lstm_cur = 0;
   const int cur = ws.lstm_cur;
   const int32_t *sprev = ws.Q + (int64_t)P * g.soff[sb - 1];
-  if (ctx->precision != PW_PREC_FP32) {
+  if (tc_precision(ctx->precision)) {
     int s = tc_run_lstm(ctx, m, g, ws, sb, sprev, up, first, cur);
     ws.lstm_cur = cur ^ 1;
     return s;
   }
   const double pix = (double)P * h * w;
+  // integer-network class: the quantised weights and requantisation shifts
+  const IntNets *in = ctx->precision == PW_PREC_INT8 ? m.intn : nullptr;
   {
     ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 3.0 * C * 4));
-    launch_lstm_in(sprev, ws.X2, 2 * C, C, m.lstm_we, m.lstm_be, ws.X, P, h, w, C, up, first,
-                   ctx->stream);
+    launch_lstm_in(sprev, ws.X2, 2 * C, C, in ? in->we : m.lstm_we, in ? in->be : m.lstm_be,
+                   ws.X, P, h, w, C, up, first, ctx->stream, in ? in->n_e : kRqFloat);
   }
   ConvParams a{};
   a.in = ws.X; a.in_cs = 2 * C; a.in_co = 0; a.cin = 2 * C;
-  a.w = m.lstm_wg; a.b = m.lstm_bg; a.cout_total = 4 * C;
+  a.w = in ? in->wg : m.lstm_wg; a.b = in ? in->bg : m.lstm_bg; a.cout_total = 4 * C;
+  a.iq = in ? 1 : 0; a.rq = in ? in->n_g : 0;
   a.P = P; a.H = h; a.W = w;
   a.out = ws.X2; a.out_cs = 2 * C; a.out_co = C;
   a.c_prev = ws.Cst[cur]; a.c_new = ws.Cst[cur ^ 1]; a.up = up; a.first = first; a.C = C;
@@ -246,13 +249,18 @@ int run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb) {
 int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
                      int step, bool decoding) {
   const int h = g.sh[sb], w = g.sw[sb], C = m.C, P = ws.P;
-  StepNetDev &n = (sb == 0) ? m.ll[step] : m.sb[step];
+  // integer-network class: the quantised nets and their requantisation
+  // shifts (iq marks every convolution of the pass)
+  IntStepNet *in = nullptr;
+  if (ctx->precision == PW_PREC_INT8) in = sb == 0 ? &m.intn->ll[step] : &m.intn->sb[step];
+  const int iq = in ? 1 : 0;
+  StepNetDev &n = in ? in->d : ((sb == 0) ? m.ll[step] : m.sb[step]);
   const int32_t *Qi = ws.Q + (int64_t)P * g.soff[sb];
   uint32_t *idx = ws.idx + (int64_t)P * g.ioff[sb * 4 + step];
   const int64_t nk = step_count(h, w, step);
   float *mu = ws.mu ? ws.mu + (int64_t)P * g.soff[sb] : nullptr;
   float *sgp = ws.sg ? ws.sg + (int64_t)P * g.soff[sb] : nullptr;
-  if (ctx->precision != PW_PREC_FP32)
+  if (tc_precision(ctx->precision))
     return tc_run_step(ctx, m, g, ws, sb, step, n, Qi, idx, nk, mu, sgp);
   cudaStream_t st = ctx->stream;
   if (sb == 0 && step == 0) {
@@ -296,26 +304,32 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
     a.in = ws.X2; a.in_cs = 2 * C; a.in_co = C; a.cin = C;
     a.w = n.win; a.b = n.bin; a.cout_total = C;
     a.out = ws.Z; a.out_cs = C;
+    a.iq = iq; a.rq = iq ? in->n_win : 0;
     conv(1, a, EPI_STORE);
     a = base();  // u = lrelu(1x1 z)
     a.in = ws.Z; a.in_cs = C; a.cin = C; a.w = n.w1; a.b = n.b1; a.cout_total = C;
     a.out = ws.U; a.out_cs = C; a.act = 1;
+    a.iq = iq; a.rq = iq ? in->n_w1 : 0;
     conv(1, a, EPI_STORE);
     {
       ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * 8.0 * C);
-      launch_dw3x3(ws.U, n.wdw, n.bdw, ws.V, P, h, w, C, st);
+      launch_dw3x3(ws.U, n.wdw, n.bdw, ws.V, P, h, w, C, st, iq ? in->n_dw : kRqFloat);
     }
     a = base();  // z2 = z + 1x1(v)
     a.in = ws.V; a.in_cs = C; a.cin = C; a.w = n.w2; a.b = n.b2; a.cout_total = C;
     a.out = ws.Z2; a.out_cs = C; a.res = ws.Z; a.res_cs = C;
+    a.iq = iq; a.rq = iq ? in->n_w2 : 0;
     conv(1, a, EPI_STORE);
     a = base();  // u2 = lrelu(1x1(C->2C) z2)
     a.in = ws.Z2; a.in_cs = C; a.cin = C; a.w = n.w3; a.b = n.b3; a.cout_total = 2 * C;
     a.out = ws.U; a.out_cs = 2 * C; a.act = 1;
+    a.iq = iq; a.rq = iq ? in->n_w3 : 0;
     conv(1, a, EPI_STORE);
     a = base();  // z3 = z2 + 1x1(2C->C) u2; head
     a.in = ws.U; a.in_cs = 2 * C; a.cin = 2 * C; a.w = n.w4; a.b = n.b4; a.cout_total = C;
     a.res = ws.Z2; a.res_cs = C;
+    a.iq = iq; a.rq = iq ? in->n_w4 : 0;
+    a.rq_mu = iq ? in->n_mu : 0; a.rq_rho = iq ? in->n_rho : 0;
     if (m.mix) {
       a.out = ws.Z2; a.out_cs = C;
       conv(1, a, EPI_STORE);
@@ -330,19 +344,24 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
   } else {
     {
       ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * (4.0 + 4.0 * C));
-      launch_masked_in(Qi, n.wa, n.ba, ws.X2, 2 * C, P, h, w, C, step, st);
+      launch_masked_in(Qi, n.wa, n.ba, ws.X2, 2 * C, P, h, w, C, step, st,
+                       iq ? in->n_wa : kRqFloat);
     }
     a = base();  // z = 1x1(2C->C)[a, l]
     a.in = ws.X2; a.in_cs = 2 * C; a.cin = 2 * C; a.w = n.wz; a.b = n.bz; a.cout_total = C;
     a.out = ws.Z; a.out_cs = C;
+    a.iq = iq; a.rq = iq ? in->n_wz : 0;
     conv(1, a, EPI_STORE);
     a = base();  // u = lrelu(conv3x3 z)
     a.in = ws.Z; a.in_cs = C; a.cin = C; a.w = n.c1w; a.b = n.c1b; a.cout_total = C;
     a.out = ws.U; a.out_cs = C; a.act = 1;
+    a.iq = iq; a.rq = iq ? in->n_c1 : 0;
     conv(3, a, EPI_STORE);
     a = base();  // z' = z + conv3x3 u; head
     a.in = ws.U; a.in_cs = C; a.cin = C; a.w = n.c2w; a.b = n.c2b; a.cout_total = C;
     a.res = ws.Z; a.res_cs = C;
+    a.iq = iq; a.rq = iq ? in->n_c2 : 0;
+    a.rq_mu = iq ? in->n_mu : 0; a.rq_rho = iq ? in->n_rho : 0;
     if (m.mix) {
       a.out = ws.Z; a.out_cs = C;
       conv(3, a, EPI_STORE);
@@ -376,7 +395,7 @@ int post_process_planes(pw_ctx *ctx, Model &m, const Geometry &g, int P, const f
   LiftStepParams a{};
   a.P = P; a.H = g.Hp; a.W = g.Wp; a.dir = 0; a.lin = LIN_ZERO; a.sign = +1; a.round = 0;
   a.net = m.post; a.status = ctx->status;
-  a.tc = ctx->precision != PW_PREC_FP32 ? 1 : 0;
+  a.tc = tc_precision(ctx->precision) ? 1 : 0;
   const int64_t hw = (int64_t)g.Hp * g.Wp;
   a.src = acc(const_cast<float *>(src), hw, g.Wp);
   a.other = acc(const_cast<float *>(src), hw, g.Wp);
@@ -392,7 +411,7 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
   const int P = ws.P, L = g.levels;
   const int rP = g.lossless ? 1 : 0, rU = g.lossless ? 2 : 0;
   // BF16 / FP8 precision class, lossy: the CNNs' middle layer on the tensor cores
-  const int tc = (ctx->precision != PW_PREC_FP32 && !g.lossless) ? 1 : 0;
+  const int tc = (tc_precision(ctx->precision) && !g.lossless) ? 1 : 0;
   float *cur = ws.Yf;  // LL_L, plane stride h*w
   for (int lv = L; lv >= 1; --lv) {
     const int h = g.Hp >> lv, w = g.Wp >> lv;

@@ -15,6 +15,9 @@ struct pw_ctx;
 
 namespace pw {
 
+// Precision classes whose context convolutions run on the tensor cores.
+inline bool tc_precision(int p) { return p == PW_PREC_BF16 || p == PW_PREC_FP8; }
+
 struct StepNetDev {
   // step 1 (DepthConvBlock net)
   float *win = nullptr, *bin = nullptr, *w1 = nullptr, *b1 = nullptr, *wdw = nullptr,
@@ -27,6 +30,21 @@ struct StepNetDev {
   float *wh = nullptr, *bh = nullptr;
 };
 
+// Integer-network class (PW_PREC_INT8): the context model's weights and
+// biases quantised to integers (held exactly as floats, in the FP32 path's
+// layouts) and the requantisation shift of every layer's output.
+struct IntStepNet {
+  StepNetDev d;
+  int n_win = 0, n_w1 = 0, n_dw = 0, n_w2 = 0, n_w3 = 0, n_w4 = 0;  // step 1
+  int n_wa = 0, n_wz = 0, n_c1 = 0, n_c2 = 0;                       // steps 2-4
+  int n_mu = 0, n_rho = 0;                                          // head
+};
+struct IntNets {
+  float *we = nullptr, *be = nullptr, *wg = nullptr, *bg = nullptr;  // ConvLSTM
+  int n_e = 0, n_g = 0;
+  IntStepNet sb[4], ll[4];
+};
+
 // Tensor-core (BF16) copies of the context-model weights, see ctx_tc.cu.
 struct TcWeights;
 
@@ -37,6 +55,7 @@ struct Model {
   // of 3 (9 outputs; FP32 precision class and four-step LL only)
   int nh = 2;
   bool mix = false;
+  IntNets *intn = nullptr;   // built when loaded in an INT8 context
   uint64_t hash = 0;
   uint64_t uid = 0;          // unique per loaded model (keys cached workspaces)
   std::vector<float *> allocs;

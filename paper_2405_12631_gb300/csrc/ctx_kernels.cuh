@@ -31,7 +31,15 @@ struct ConvParams {
   uint32_t *idx;        // packed indices, [P][idx_stride] in step order
   int64_t idx_stride;
   float *mu_out, *sg_out;  // optional [P, H, W]
+  // integer-network class: inputs, weights and biases are integers held
+  // exactly in floats; the output is requantised by rq bits (round half
+  // up) and clamped (EPI_STORE: residual added after; EPI_LSTM: the gates;
+  // EPI_HEAD: z'), the head by rq_mu / rq_rho bits (see the launchers)
+  int iq, rq, rq_mu, rq_rho;
 };
+// Integer class of the SIMT producers below: rqn = kRqFloat selects the
+// float definition, otherwise their outputs are requantised by rqn bits.
+constexpr int kRqFloat = -1000;
 
 void launch_conv_simt(int ks, const ConvParams &a, int epi, cudaStream_t st);
 
@@ -57,11 +65,12 @@ void launch_mix_tables(const int32_t *key9, int64_t n, uint16_t *rows, cudaStrea
 bool &launch_failed();
 void launch_lstm_in(const int32_t *s_prev, const float *h_prev, int h_cs, int h_co,
                     const float *we, const float *be, float *X, int P, int H, int W, int C,
-                    int up, int first, cudaStream_t st);
+                    int up, int first, cudaStream_t st, int rqn = kRqFloat);
 void launch_masked_in(const int32_t *s, const float *wa, const float *ba, float *out,
-                      int out_cs, int P, int H, int W, int C, int step, cudaStream_t st);
+                      int out_cs, int P, int H, int W, int C, int step, cudaStream_t st,
+                      int rqn = kRqFloat);
 void launch_dw3x3(const float *in, const float *w, const float *b, float *out, int P, int H,
-                  int W, int C, cudaStream_t st);
+                  int W, int C, cudaStream_t st, int rqn = kRqFloat);
 
 // entropy.cu
 struct DecChunk {

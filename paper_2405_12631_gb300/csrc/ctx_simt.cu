@@ -11,6 +11,9 @@
 //            (mu, rho) = 1x1(C->2) z.
 //  steps 2-4: a = conv3x3(1->C)(m_<k s); z = 1x1(2C->C)[a, l];
 //            z += conv3x3(lrelu(conv3x3 z)); (mu, rho) = 1x1(C->2) z.
+// The integer-network class runs the same kernels on integers held exactly
+// in floats, with integer epilogues (requantisation, clamps, LeakyReLU
+// slope 1/128, hard sigmoid / tanh cell, log-scale head): see rq_ll below.
 #include "pw_internal.cuh"
 #include "ctx_kernels.cuh"
 
@@ -18,6 +21,32 @@ namespace pw {
 
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
 __device__ __forceinline__ float lrelu(float x) { return x >= 0.f ? x : 0.01f * x; }
+
+// Integer-network class. Every sum is of integers below 2^24 in magnitude
+// (at most 2304 products of weights |w| <= 56 and activations |a| <= 127,
+// plus a bias |b| <= 2^18), so FP32 FMAs compute it exactly in any order;
+// these helpers then work on the exact integer: requantisation by n bits
+// (round half up: floor((x + 2^(n-1)) / 2^n); n <= 0 shifts left),
+// clamping, LeakyReLU with slope 1/128 (floor division), hard sigmoid
+// clamp(2x + 64, 0, 128) and hard tanh clamp(8x, -128, 128) (7 fractional
+// bits).
+__device__ __forceinline__ long long rq_ll(long long x, int n) {
+  return n > 0 ? ((x + (1LL << (n - 1))) >> n) : (x << (-n));
+}
+__device__ __forceinline__ long long clamp_ll(long long x, long long lim) {
+  return x > lim ? lim : (x < -lim ? -lim : x);
+}
+__device__ __forceinline__ float rq_f(float v, int n, long long lim) {
+  return (float)clamp_ll(rq_ll((long long)v, n), lim);
+}
+__device__ __forceinline__ float lrelu_i(float v) {
+  const long long x = (long long)v;
+  return (float)(x >= 0 ? x : (x >> 7));
+}
+__device__ __forceinline__ long long hsig_i(long long x) {
+  return x * 2 + 64 < 0 ? 0 : (x * 2 + 64 > 128 ? 128 : x * 2 + 64);
+}
+__device__ __forceinline__ long long htanh_i(long long x) { return clamp_ll(8 * x, 128); }
 
 // Generic NHWC convolution, KS x KS (KS = 1 or 3, zero padding), output
 // channels [blockIdx.y * CO_T, +CO_T). Tile: 8 rows x 16 columns of one
@@ -96,6 +125,15 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
         const int co = co0 + cg * NC + j;
         if (co >= a.cout_total) continue;
         float v = acc[i][j] + a.b[co];
+        if (a.iq) {
+          // integer class: act on the accumulator, requantise, then the
+          // residual (an activation at the same binary point)
+          if (a.act) v = lrelu_i(v);
+          v = rq_f(v, a.rq, 127);
+          if (a.res) v = (float)clamp_ll((long long)v + (long long)a.res[pix * a.res_cs + a.res_co + co], 127);
+          a.out[pix * a.out_cs + a.out_co + co] = v;
+          continue;
+        }
         if (a.res) v += a.res[pix * a.res_cs + a.res_co + co];
         if (a.act) v = lrelu(v);
         a.out[pix * a.out_cs + a.out_co + co] = v;
@@ -117,6 +155,19 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
         float gi = acc[i][j] + a.b[o], gf = acc[i][j + 1] + a.b[o + 1];
         float go = acc[i][j + 2] + a.b[o + 2], gg = acc[i][j + 3] + a.b[o + 3];
         float cp = a.first ? 0.f : a.c_prev[ppix * a.C + ch];
+        if (a.iq) {
+          // integer cell: gates requantised to 4 fractional bits, hard
+          // sigmoid / tanh, c and h with 7
+          const long long si = hsig_i((long long)rq_f(gi, a.rq, 127));
+          const long long sf = hsig_i((long long)rq_f(gf, a.rq, 127));
+          const long long so = hsig_i((long long)rq_f(go, a.rq, 127));
+          const long long tg = htanh_i((long long)rq_f(gg, a.rq, 127));
+          const long long c = clamp_ll(rq_ll(sf * (long long)cp + si * tg, 7), 32767);
+          const long long hq = clamp_ll(rq_ll(so * clamp_ll(c, 128), 7), 127);
+          a.c_new[pix * a.C + ch] = (float)c;
+          a.out[pix * a.out_cs + a.out_co + ch] = (float)hq;
+          continue;
+        }
         float cn = sigm(gf) * cp + sigm(gi) * tanhf(gg);
         float hn = sigm(go) * tanhf(cn);
         a.c_new[pix * a.C + ch] = cn;
@@ -136,7 +187,12 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
       for (int j = 0; j < NC; ++j) {
         const int co = cg * NC + j;
         float v = acc[i][j] + a.b[co];
-        if (in) v += a.res[pix * a.res_cs + a.res_co + co];
+        if (a.iq) {
+          v = rq_f(v, a.rq, 127);
+          if (in) v = (float)clamp_ll((long long)v + (long long)a.res[pix * a.res_cs + a.res_co + co], 127);
+        } else if (in) {
+          v += a.res[pix * a.res_cs + a.res_co + co];
+        }
         pm[i] = fmaf(a.wh[co], v, pm[i]);
         pr[i] = fmaf(a.wh[a.cout_total + co], v, pr[i]);
       }
@@ -154,11 +210,25 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
 #pragma unroll
         for (int g = 0; g < 8; ++g) { mu += s_head[g][t][0]; rho += s_head[g][t][1]; }
         const int q = step_index(a.W, a.step, yy, xx);
-        a.idx[(int64_t)p * a.idx_stride + q] = pack_index(mu, rho);
-        if (a.mu_out) {
-          const int64_t o = (int64_t)p * a.H * a.W + (int64_t)yy * a.W + xx;
-          a.mu_out[o] = mu;
-          a.sg_out[o] = rho > 20.f ? rho : log1pf(expf(rho));
+        if (a.iq) {
+          // integer head: t = 16 mu and the scale bin j directly
+          const long long ti = clamp_ll(rq_ll((long long)mu, a.rq_mu), 1LL << 23);
+          long long j = rq_ll((long long)rho, a.rq_rho) + 24;
+          j = j < 0 ? 0 : (j > kNJ - 1 ? kNJ - 1 : j);
+          a.idx[(int64_t)p * a.idx_stride + q] =
+              ((uint32_t)(ti + (1 << 23)) << 7) | (uint32_t)j;
+          if (a.mu_out) {
+            const int64_t o = (int64_t)p * a.H * a.W + (int64_t)yy * a.W + xx;
+            a.mu_out[o] = (float)ti * 0.0625f;
+            a.sg_out[o] = __int_as_float(0x3E000000 + ((int)j << 20) + (1 << 19));
+          }
+        } else {
+          a.idx[(int64_t)p * a.idx_stride + q] = pack_index(mu, rho);
+          if (a.mu_out) {
+            const int64_t o = (int64_t)p * a.H * a.W + (int64_t)yy * a.W + xx;
+            a.mu_out[o] = mu;
+            a.sg_out[o] = rho > 20.f ? rho : log1pf(expf(rho));
+          }
         }
       }
     }
@@ -170,7 +240,7 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
 __global__ void k_lstm_in(const int32_t *__restrict__ s_prev, const float *__restrict__ h_prev,
                           int h_cs, int h_co, const float *__restrict__ we,
                           const float *__restrict__ be, float *__restrict__ X, int P, int H,
-                          int W, int C, int up, int first) {
+                          int W, int C, int up, int first, int rqn) {
   const int64_t n = (int64_t)P * H * W * C;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -186,9 +256,11 @@ __global__ void k_lstm_in(const int32_t *__restrict__ s_prev, const float *__res
     for (int tap = 0; tap < 9; ++tap) {
       const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
       if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-      v = fmaf(we[c * 9 + tap], (float)sp[(int64_t)(yy >> up) * Wp + (xx >> up)], v);
+      int32_t sv = sp[(int64_t)(yy >> up) * Wp + (xx >> up)];
+      if (rqn != kRqFloat) sv = min(max(sv, -127), 127);   // integer class input
+      v = fmaf(we[c * 9 + tap], (float)sv, v);
     }
-    X[pix * 2 * C + c] = v;
+    X[pix * 2 * C + c] = rqn != kRqFloat ? rq_f(v, rqn, 127) : v;
     float hv = 0.f;
     if (!first) {
       const int64_t pp = ((int64_t)p * Hp + (y >> up)) * Wp + (x >> up);
@@ -201,7 +273,7 @@ __global__ void k_lstm_in(const int32_t *__restrict__ s_prev, const float *__res
 // Masked spatial input of steps 2-4: out[..., 0:C] = conv3x3(1->C)(m_<k s) + b.
 __global__ void k_masked_in(const int32_t *__restrict__ s, const float *__restrict__ wa,
                             const float *__restrict__ ba, float *__restrict__ out, int out_cs,
-                            int P, int H, int W, int C, int step) {
+                            int P, int H, int W, int C, int step, int rqn) {
   const int64_t n = (int64_t)P * H * W * C;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -217,16 +289,18 @@ __global__ void k_masked_in(const int32_t *__restrict__ s, const float *__restri
       const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
       if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
       if (step_of(yy, xx) >= step) continue;
-      v = fmaf(wa[c * 9 + tap], (float)sp[(int64_t)yy * W + xx], v);
+      int32_t sv = sp[(int64_t)yy * W + xx];
+      if (rqn != kRqFloat) sv = min(max(sv, -127), 127);   // integer class input
+      v = fmaf(wa[c * 9 + tap], (float)sv, v);
     }
-    out[pix * out_cs + c] = v;
+    out[pix * out_cs + c] = rqn != kRqFloat ? rq_f(v, rqn, 127) : v;
   }
 }
 
 // Depthwise 3x3 (zero padding): out = dw(in) + b, NHWC with C channels.
 __global__ void k_dw3x3(const float *__restrict__ in, const float *__restrict__ w,
                         const float *__restrict__ b, float *__restrict__ out, int P, int H,
-                        int W, int C) {
+                        int W, int C, int rqn) {
   const int64_t n = (int64_t)P * H * W * C;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -242,7 +316,7 @@ __global__ void k_dw3x3(const float *__restrict__ in, const float *__restrict__ 
       if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
       v = fmaf(w[c * 9 + tap], in[(pbase + (int64_t)yy * W + xx) * C + c], v);
     }
-    out[pix * C + c] = v;
+    out[pix * C + c] = rqn != kRqFloat ? rq_f(v, rqn, 127) : v;
   }
 }
 
@@ -278,20 +352,21 @@ void launch_conv_simt(int ks, const ConvParams &a, int epi, cudaStream_t st) {
 
 void launch_lstm_in(const int32_t *s_prev, const float *h_prev, int h_cs, int h_co,
                     const float *we, const float *be, float *X, int P, int H, int W, int C,
-                    int up, int first, cudaStream_t st) {
+                    int up, int first, cudaStream_t st, int rqn) {
   int64_t n = (int64_t)P * H * W * C;
   k_lstm_in<<<grid_for(n), 256, 0, st>>>(s_prev, h_prev, h_cs, h_co, we, be, X, P, H, W, C,
-                                          up, first);
+                                          up, first, rqn);
 }
 void launch_masked_in(const int32_t *s, const float *wa, const float *ba, float *out,
-                      int out_cs, int P, int H, int W, int C, int step, cudaStream_t st) {
+                      int out_cs, int P, int H, int W, int C, int step, cudaStream_t st,
+                      int rqn) {
   int64_t n = (int64_t)P * H * W * C;
-  k_masked_in<<<grid_for(n), 256, 0, st>>>(s, wa, ba, out, out_cs, P, H, W, C, step);
+  k_masked_in<<<grid_for(n), 256, 0, st>>>(s, wa, ba, out, out_cs, P, H, W, C, step, rqn);
 }
 void launch_dw3x3(const float *in, const float *w, const float *b, float *out, int P, int H,
-                  int W, int C, cudaStream_t st) {
+                  int W, int C, cudaStream_t st, int rqn) {
   int64_t n = (int64_t)P * H * W * C;
-  k_dw3x3<<<grid_for(n), 256, 0, st>>>(in, w, b, out, P, H, W, C);
+  k_dw3x3<<<grid_for(n), 256, 0, st>>>(in, w, b, out, P, H, W, C, rqn);
 }
 
 }  // namespace pw

@@ -1751,6 +1751,14 @@ int Model::prepare(int precision) {
     set_last_error("logistic-mixture models run in the FP32 precision class only");
     return PW_EUNSUPPORTED;
   }
+  if (precision == PW_PREC_INT8) {
+    if (!intn) {
+      set_last_error("the integer-network class needs a four-step LL Laplace model loaded in an "
+                     "INT8 context");
+      return PW_EUNSUPPORTED;
+    }
+    return PW_OK;
+  }
   if (precision == PW_PREC_FP32) return PW_OK;
   std::lock_guard<std::mutex> lk(mu);
   return precision == PW_PREC_FP8 ? ensure_fp8() : ensure_tc();

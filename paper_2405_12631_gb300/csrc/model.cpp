@@ -5,7 +5,9 @@
 // 3.3), the ConvLSTM context prediction module and the four-step context
 // fusion nets (Section 3.2). Tensors are found by name; their shapes are
 // checked against the configuration in the blob header.
+#include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 
 #include <cuda_bf16.h>
@@ -32,6 +34,59 @@ uint64_t poly_hash(const uint8_t *p, size_t n) {
     h += ((uint64_t)w + 1ull) * pw;
   }
   return h;
+}
+
+// ---- integer-network weights ----------------------------------------------
+// Largest integer k with m 2^k <= lim (m > 0), found exactly.
+int max_shift(double m, double lim) {
+  int k = (int)std::floor(std::log2(lim / m));
+  while (std::ldexp(m, k + 1) <= lim) ++k;
+  while (std::ldexp(m, k) > lim) --k;
+  return k;
+}
+
+struct QGroup {
+  int c0, n, fa;  // input channels [c0, c0 + n) carrying fa fractional bits
+};
+constexpr double kWMax = 56.0, kBMax = 262144.0;  // |w_q| <= 56, |b_q| <= 2^18
+
+// Quantise a convolution's weights w ([cout][cin][kk], the blob's layout)
+// and bias b: k_g = the largest k with max|w_g| 2^k <= 56 per input group,
+// S = min_g (k_g + fa_g), lowered so that max|b| 2^S <= 2^18; w_q =
+// rint(w 2^(S - fa_g)), b_q = rint(b 2^S) (round half to even), kept as
+// exact float integers in the same layout. Returns S.
+int quantise(const std::vector<float> &w, const std::vector<float> &b, int cout, int cin, int kk,
+             std::initializer_list<QGroup> groups, std::vector<float> &wq,
+             std::vector<float> &bq) {
+  int S = 0;
+  bool any = false;
+  for (const QGroup &g : groups) {
+    double m = 0.0;
+    for (int o = 0; o < cout; ++o)
+      for (int ci = g.c0; ci < g.c0 + g.n; ++ci)
+        for (int t = 0; t < kk; ++t)
+          m = std::max(m, std::fabs((double)w[((size_t)o * cin + ci) * kk + t]));
+    if (m > 0.0) {
+      const int k = max_shift(m, kWMax) + g.fa;
+      S = any ? std::min(S, k) : k;
+      any = true;
+    }
+  }
+  if (!any) S = 30;
+  double mb = 0.0;
+  for (float v : b) mb = std::max(mb, std::fabs((double)v));
+  if (mb > 0.0) S = std::min(S, max_shift(mb, kBMax));
+  wq.assign(w.size(), 0.f);
+  for (const QGroup &g : groups)
+    for (int o = 0; o < cout; ++o)
+      for (int ci = g.c0; ci < g.c0 + g.n; ++ci)
+        for (int t = 0; t < kk; ++t) {
+          const size_t i = ((size_t)o * cin + ci) * kk + t;
+          wq[i] = (float)std::nearbyint(std::ldexp((double)w[i], S - g.fa));
+        }
+  bq.resize(b.size());
+  for (size_t i = 0; i < b.size(); ++i) bq[i] = (float)std::nearbyint(std::ldexp((double)b[i], S));
+  return S;
 }
 
 }  // namespace
@@ -250,6 +305,86 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
     if (!get("ar.wh", {2, C}, w) || !get("ar.bh", {2}, bb)) return PW_EINVAL;
     ar_wh = up(w); ar_bh = up(bb);
   }
+  // integer-network class: quantised copies of the context model
+  delete intn;
+  intn = nullptr;
+  if (c->precision == PW_PREC_INT8 && ll_mode == 0 && !mix && st == PW_OK) {
+    const int FA = 4, FH = 7;
+    IntNets *in = new IntNets();
+    std::vector<float> w, bb, wq, bq;
+    bool ok = true;
+    // shifts of layer outputs with 4 fractional bits (head: 4 for 16 mu, 3
+    // for the 8-per-octave scale bins)
+    auto shift_ok = [&](int n) { ok = ok && n >= -30 && n <= 62; return n; };
+    if (!get("lstm.we", {C, 1, 3, 3}, w) || !get("lstm.be", {C}, bb)) ok = false;
+    if (ok) {
+      in->n_e = shift_ok(quantise(w, bb, C, 1, 9, {{0, 1, 0}}, wq, bq) - FA);
+      in->we = up(wq); in->be = up(bq);
+    }
+    if (ok && get("lstm.wg", {4 * C, 2 * C, 3, 3}, w) && get("lstm.bg", {4 * C}, bb)) {
+      in->n_g = shift_ok(quantise(w, bb, 4 * C, 2 * C, 9, {{0, C, FA}, {C, C, FH}}, wq, bq) - FA);
+      std::vector<float> wp(wq.size()), bp(bq.size());
+      for (int g = 0; g < 4; ++g)
+        for (int ch = 0; ch < C; ++ch) {
+          const int o = g * C + ch, o2 = 4 * ch + g;  // gate-interleaved outputs
+          bp[o2] = bq[o];
+          std::memcpy(&wp[(size_t)o2 * 2 * C * 9], &wq[(size_t)o * 2 * C * 9], 2 * C * 9 * 4);
+        }
+      in->wg = up(conv_tap_major(wp, 4 * C, 2 * C, 3));
+      in->bg = up(bp);
+    } else {
+      ok = false;
+    }
+    for (int set = 0; set < 2 && ok; ++set) {
+      const std::string ns = set ? "ll" : "sb";
+      IntStepNet *nets = set ? in->ll : in->sb;
+      auto q1 = [&](const std::string &name, int co, int ci, int kk,
+                    std::initializer_list<QGroup> g, float *&dw, float *&db, bool tap_major,
+                    bool transp) -> int {
+        std::vector<int> shp = kk == 9 ? std::vector<int>{co, ci, 3, 3} : std::vector<int>{co, ci};
+        if (name.find("wdw") != std::string::npos) shp = {co, 3, 3};
+        if (!get(name, shp, w)) { ok = false; return 0; }
+        // its bias: "w..." -> "b..." in the last name component
+        const std::string bn = name.substr(0, name.rfind('.') + 1) + "b" +
+                               name.substr(name.rfind('.') + 2);
+        if (!get(bn, {co}, bb)) { ok = false; return 0; }
+        const int S = quantise(w, bb, co, ci, kk, g, wq, bq);
+        dw = up(tap_major ? conv_tap_major(wq, co, ci, 3) : transp ? transpose(wq, co, ci) : wq);
+        db = up(bq);
+        return S;
+      };
+      {
+        IntStepNet &s0 = nets[0];
+        const std::string p = ns + ".s0.";
+        s0.n_win = shift_ok(q1(p + "win", C, C, 1, {{0, C, FH}}, s0.d.win, s0.d.bin, false, true) - FA);
+        s0.n_w1 = shift_ok(q1(p + "w1", C, C, 1, {{0, C, FA}}, s0.d.w1, s0.d.b1, false, true) - FA);
+        s0.n_dw = shift_ok(q1(p + "wdw", C, 1, 9, {{0, 1, FA}}, s0.d.wdw, s0.d.bdw, false, false) - FA);
+        s0.n_w2 = shift_ok(q1(p + "w2", C, C, 1, {{0, C, FA}}, s0.d.w2, s0.d.b2, false, true) - FA);
+        s0.n_w3 = shift_ok(q1(p + "w3", 2 * C, C, 1, {{0, C, FA}}, s0.d.w3, s0.d.b3, false, true) - FA);
+        s0.n_w4 = shift_ok(q1(p + "w4", C, 2 * C, 1, {{0, 2 * C, FA}}, s0.d.w4, s0.d.b4, false, true) - FA);
+        const int Sh = q1(p + "wh", 2, C, 1, {{0, C, FA}}, s0.d.wh, s0.d.bh, false, false);
+        s0.n_mu = shift_ok(Sh - 4);
+        s0.n_rho = shift_ok(Sh - 3);
+      }
+      for (int k = 1; k < 4 && ok; ++k) {
+        IntStepNet &sk = nets[k];
+        const std::string p = ns + ".s" + std::to_string(k) + ".";
+        sk.n_wa = shift_ok(q1(p + "wa", C, 1, 9, {{0, 1, 0}}, sk.d.wa, sk.d.ba, false, false) - FA);
+        sk.n_wz = shift_ok(q1(p + "wz", C, 2 * C, 1, {{0, C, FA}, {C, C, FH}}, sk.d.wz, sk.d.bz, false, true) - FA);
+        sk.n_c1 = shift_ok(q1(p + "w1", C, C, 9, {{0, C, FA}}, sk.d.c1w, sk.d.c1b, true, false) - FA);
+        sk.n_c2 = shift_ok(q1(p + "w2", C, C, 9, {{0, C, FA}}, sk.d.c2w, sk.d.c2b, true, false) - FA);
+        const int Sh = q1(p + "wh", 2, C, 1, {{0, C, FA}}, sk.d.wh, sk.d.bh, false, false);
+        sk.n_mu = shift_ok(Sh - 4);
+        sk.n_rho = shift_ok(Sh - 3);
+      }
+    }
+    if (ok && st == PW_OK) {
+      intn = in;
+    } else {
+      delete in;
+      if (!ok) set_last_error("integer-network weights: a tensor is missing or out of range");
+    }
+  }
   cudaDeviceSynchronize();
   return st;
 }
@@ -257,6 +392,7 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
 Model::~Model() {
   for (float *p : allocs) cudaFree(p);
   free_tc();
+  delete intn;
 }
 
 }  // namespace pw

@@ -1,0 +1,126 @@
+"""GPU parity of the integer-network context model (precision class INT8)
+against the oracle's integer model (oracle/intnet.py).
+
+The class's arithmetic is exact integer arithmetic, so the bar is equality
+everywhere, with no near-tie certificate: the entropy parameters (t = 16 mu
+and the scale bin j) at every position, and the streams themselves - the
+GPU encoder writes the oracle encoder's stream byte for byte, header
+included, and each decodes the other's streams to the same symbols. The
+inverse transform stays FP32, so images agree with the oracle's to one
+grey level.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from oracle import codec as K
+from oracle import intnet as I
+from tests._lib import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pw():
+    ensure_built()
+    import paper_2405_12631_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def codec(pw):
+    c = pw.Codec(0, "int8")
+    yield c
+    c.close()
+
+
+def _blob(C=32, seed=0, ll_mode=0):
+    cfg = S.ModelConfig(levels=4, C=C, ll_mode=ll_mode)
+    return S.pack_blob(cfg, S.random_model(cfg, seed))
+
+
+def _latent(om, img):
+    planes, _ = K.colour_forward(img, False, 8)
+    planes = [K.pad_plane(p, 1 << om.levels) for p in planes]
+    d32 = np.float32(1.0 / 8.0)
+    return [[K.quantise(s, d32) for s in om.lift.forward(p, om.levels, False)] for p in planes]
+
+
+def _flat(qsb_list):
+    nsb = len(qsb_list[0])
+    return np.concatenate([np.stack([qc[i] for qc in qsb_list]).reshape(-1)
+                           for i in range(nsb)]).astype(np.int64)
+
+
+@pytest.mark.parametrize("C,H,W", [(32, 80, 112), (64, 512, 768)])
+def test_integer_parameters_equal_the_oracle_everywhere(codec, C, H, W):
+    blob = _blob(C=C, seed=1)
+    gm = codec.load_model(blob)
+    om = K.Model(blob, integer=True)
+    img = S.gray_sinusoids(H, W, seed=5)
+    qsb = _latent(om, img)[0]
+    mu_g, sg_g = codec.context_params(gm, H, W, _flat([qsb]))
+    tj = I.context_tj_all(om.int_context(), qsb)
+    t_o = np.concatenate([t.reshape(-1) for t, _ in tj])
+    j_o = np.concatenate([j.reshape(-1) for _, j in tj])
+    t_g = np.rint(mu_g.astype(np.float64) * 16).astype(np.int64)
+    j_g = ((sg_g.view(np.uint32).astype(np.int64) - 0x3E000000) >> 20)
+    assert np.array_equal(t_g, t_o), int(np.sum(t_g != t_o))
+    assert np.array_equal(j_g, j_o), int(np.sum(j_g != j_o))
+    print(f"\nINT8 C={C} {H}x{W}: {t_o.size} positions, t and j identical; "
+          f"t range [{t_o.min()}, {t_o.max()}], j range [{j_o.min()}, {j_o.max()}]")
+    gm.close()
+
+
+@pytest.mark.parametrize("kind", ["gray", "rgb"])
+def test_gpu_stream_equals_oracle_stream(codec, kind):
+    blob = _blob(seed=2)
+    gm = codec.load_model(blob)
+    img = S.gray_sinusoids(96, 128, seed=6) if kind == "gray" else S.rgb_natural(64, 96, seed=6)
+    bs_g = codec.encode_image(gm, img, q=8.0, chunk=500)
+    bs_o = K.encode_image(blob, img, q=8.0, chunk=500, integer=True)
+    assert bs_g == bs_o, "the integer class's stream differs from the oracle's"
+    # each side decodes the other's stream
+    om = K.Model(blob)
+    _, q_o = K.decode_symbols(om, bs_g)
+    assert np.array_equal(codec.decode_symbols(gm, bs_o), _flat(q_o))
+    out = codec.decode_image(gm, bs_o)
+    ref = K.decode_image(blob, bs_o)
+    assert np.max(np.abs(out.astype(int) - ref.astype(int))) <= 1
+    gm.close()
+
+
+def test_gpu_stream_equals_oracle_stream_fullsize(codec):
+    """768 x 512 gray, C = 64: the GPU encoder's stream is the oracle
+    encoder's, byte for byte."""
+    blob = _blob(C=64, seed=0)
+    gm = codec.load_model(blob)
+    img = S.gray_sinusoids(512, 768, seed=3)
+    bs_g = codec.encode_image(gm, img, q=8.0)
+    bs_o = K.encode_image(blob, img, q=8.0, integer=True)
+    assert len(bs_g) == len(bs_o) and bs_g == bs_o
+    assert np.array_equal(codec.decode_symbols(gm, bs_o), codec.analyse(gm, img, q=8.0))
+    print(f"\nINT8 768x512 gray: {len(bs_g)} bytes identical to the oracle's")
+    gm.close()
+
+
+def test_integer_class_limits(pw, codec):
+    with pytest.raises(pw.PwError) as e:            # AR LL: no integer model
+        codec.load_model(_blob(ll_mode=1))
+    assert e.value.code == pw.PW_EUNSUPPORTED
+    blob = _blob(seed=3)
+    gm = codec.load_model(blob)
+    img = S.gray_sinusoids(64, 64, seed=7)
+    bs = codec.encode_image(gm, img, q=8.0)
+    f32 = pw.Codec(0, "fp32")
+    m32 = f32.load_model(blob)
+    with pytest.raises(pw.PwError) as e:            # another class's decoder refuses it
+        f32.decode_image(m32, bs)
+    assert e.value.code == pw.PW_EINVAL
+    # the same images through the float class reconstruct identically
+    # (the probability model changes only the rate)
+    assert np.array_equal(f32.decode_image(m32, f32.encode_image(m32, img, q=8.0)),
+                          codec.decode_image(gm, bs))
+    m32.close()
+    f32.close()
+    gm.close()
