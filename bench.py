@@ -23,8 +23,9 @@ convolutions, BF16 elsewhere); the BF16 class is timed the same way under
 The other workloads, each under "workloads" with its own key:
 * single_gray_256: one 256x256 grayscale image (sum of 8 sinusoids plus
   noise), q = 8, C = 32, FP32 class, batch 1, in both LL modes (four-step
-  and autoregressive) and with the logistic-mixture (K = 3) probability
-  model (four-step LL), device-resident stream, CUDA events;
+  and autoregressive), with the logistic-mixture (K = 3) probability
+  model (four-step LL) and with the integer-network context model (INT8
+  class), device-resident stream, CUDA events;
 * video_4gop_1080p: 4 GOPs x 8 frames of 1920x1080 RGB (panned 1/f canvas
   and sprites), 3 temporal levels, BF16 class, pw_decode_gop host in / host
   out, wall clock;
@@ -445,8 +446,9 @@ def _events_ms(stream, fn, reps: int):
 def single_gray_run(pw, local, stream_ptr, steps: int, warmup: int):
     """One 256x256 grayscale image (128 + 8 random sinusoids + N(0, 8^2),
     seed 0), q = 8, C = 32 context model, FP32 class, batch 1, in both LL
-    modes, and with the logistic-mixture (K = 3) probability model in place
-    of the Laplace one (four-step LL); device-resident stream -> device
+    modes, with the logistic-mixture (K = 3) probability model in place
+    of the Laplace one (four-step LL), and with the integer-network context
+    model (INT8 class, four-step LL); device-resident stream -> device
     image, CUDA events per decode."""
     import torch
     import synthetic as S
@@ -455,10 +457,12 @@ def single_gray_run(pw, local, stream_ptr, steps: int, warmup: int):
     img = S.gray_sinusoids(256, 256, seed=0)
     res = {"workload": "single 256x256 grayscale image, 4-level lifting, C=32, q=8, FP32, batch 1",
            "timing": "CUDA events per decode, device stream in, device image out"}
-    for mode, name, prob in ((0, "four_step_ll", 0), (1, "autoregressive_ll", 0),
-                             (0, "four_step_ll_logistic_mixture", 1)):
+    for mode, name, prob, prec in ((0, "four_step_ll", 0, "fp32"),
+                                   (1, "autoregressive_ll", 0, "fp32"),
+                                   (0, "four_step_ll_logistic_mixture", 1, "fp32"),
+                                   (0, "four_step_ll_integer_network", 0, "int8")):
         cfg = S.ModelConfig(levels=4, C=32, F=16, ll_mode=mode, prob=prob)
-        c = pw.Codec(local, "fp32", stream=stream_ptr)
+        c = pw.Codec(local, prec, stream=stream_ptr)
         m = c.load_model(S.pack_blob(cfg, S.random_model(cfg, 0)))
         bs = c.encode_image(m, img, q=8.0)
         d_bs = torch.from_numpy(np.frombuffer(bs, dtype=np.uint8).copy()).to(dev)

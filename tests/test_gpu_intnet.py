@@ -34,9 +34,17 @@ def codec(pw):
     c.close()
 
 
-def _blob(C=32, seed=0, ll_mode=0):
+def _blob(C=32, seed=0, ll_mode=0, gain=1.0):
+    """gain > 1 scales the context model's weights (not the heads' biases)
+    so that clamps, the LeakyReLU's negative branch and the saturating
+    hard sigmoid / tanh are exercised."""
     cfg = S.ModelConfig(levels=4, C=C, ll_mode=ll_mode)
-    return S.pack_blob(cfg, S.random_model(cfg, seed))
+    t = S.random_model(cfg, seed)
+    if gain != 1.0:
+        for name in list(t):
+            if name.startswith(("lstm.", "sb.", "ll.")) and not name.endswith(".bh"):
+                t[name] = (t[name] * gain).astype(np.float32)
+    return S.pack_blob(cfg, t)
 
 
 def _latent(om, img):
@@ -52,9 +60,10 @@ def _flat(qsb_list):
                            for i in range(nsb)]).astype(np.int64)
 
 
-@pytest.mark.parametrize("C,H,W", [(32, 80, 112), (64, 512, 768)])
-def test_integer_parameters_equal_the_oracle_everywhere(codec, C, H, W):
-    blob = _blob(C=C, seed=1)
+@pytest.mark.parametrize("C,H,W,gain", [(32, 80, 112, 1.0), (32, 80, 112, 4.0),
+                                        (64, 512, 768, 1.0)])
+def test_integer_parameters_equal_the_oracle_everywhere(codec, C, H, W, gain):
+    blob = _blob(C=C, seed=1, gain=gain)
     gm = codec.load_model(blob)
     om = K.Model(blob, integer=True)
     img = S.gray_sinusoids(H, W, seed=5)
@@ -67,14 +76,14 @@ def test_integer_parameters_equal_the_oracle_everywhere(codec, C, H, W):
     j_g = ((sg_g.view(np.uint32).astype(np.int64) - 0x3E000000) >> 20)
     assert np.array_equal(t_g, t_o), int(np.sum(t_g != t_o))
     assert np.array_equal(j_g, j_o), int(np.sum(j_g != j_o))
-    print(f"\nINT8 C={C} {H}x{W}: {t_o.size} positions, t and j identical; "
+    print(f"\nINT8 C={C} {H}x{W} gain {gain:g}: {t_o.size} positions, t and j identical; "
           f"t range [{t_o.min()}, {t_o.max()}], j range [{j_o.min()}, {j_o.max()}]")
     gm.close()
 
 
-@pytest.mark.parametrize("kind", ["gray", "rgb"])
-def test_gpu_stream_equals_oracle_stream(codec, kind):
-    blob = _blob(seed=2)
+@pytest.mark.parametrize("kind,gain", [("gray", 1.0), ("rgb", 1.0), ("rgb", 4.0)])
+def test_gpu_stream_equals_oracle_stream(codec, kind, gain):
+    blob = _blob(seed=2, gain=gain)
     gm = codec.load_model(blob)
     img = S.gray_sinusoids(96, 128, seed=6) if kind == "gray" else S.rgb_natural(64, 96, seed=6)
     bs_g = codec.encode_image(gm, img, q=8.0, chunk=500)
