@@ -287,7 +287,9 @@ int pw_rans_decode_noalloc(void *cuda_stream, const uint8_t *payload, size_t pay
  * (Section 3.2): q holds the 3*levels+1 subbands in coding order, each
  * (H >> lv) x (W >> lv) int32, concatenated (host). Writes mu and sigma
  * (host float, same layout) of every position as the decoder computes them
- * step by step. H and W must be multiples of 2^levels. */
+ * step by step. H and W must be multiples of 2^levels. In the INT8 class
+ * mu = t / 16 and sigma = the middle of scale bin j, (t, j) the integer
+ * head's outputs (exact). */
 int pw_context_params(pw_ctx *ctx, const pw_model *m, int H, int W,
                       const int32_t *q, float *mu, float *sigma);
 
