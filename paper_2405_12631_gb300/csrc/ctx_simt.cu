@@ -57,7 +57,10 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
   constexpr int TH = 8, TW = 16, CI = (CO_T >= 128 ? 4 : 8), R = KS / 2;
   constexpr int HH = TH + KS - 1, HW = TW + KS - 1;
   constexpr int NC = CO_T / 8;
-  __shared__ float s_in[CI][HH][HW];
+  // input tile, one plane per channel; the plane stride avoids shared-memory
+  // bank conflicts of the channel-fastest fill below
+  constexpr int PS = HH * HW + ((HH * HW) % 32 == 0 ? 4 : 0);
+  __shared__ float s_in[CI * PS];
   __shared__ float s_w[KS * KS][CI][CO_T];
   __shared__ float s_head[EPI == EPI_HEAD ? 8 : 1][TH * TW][2];
 
@@ -78,13 +81,15 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
 
   for (int c0 = 0; c0 < a.cin; c0 += CI) {
     __syncthreads();
+    // channel fastest: consecutive threads read a pixel's consecutive
+    // channels (one 32-byte sector per pixel for CI = 8)
     for (int e = t; e < CI * HH * HW; e += 256) {
-      int c = e / (HH * HW), r = e % (HH * HW);
-      int yy = y0 + r / HW - R, xx = x0 + r % HW - R;
+      const int c = e % CI, r = e / CI;
+      const int yy = y0 + r / HW - R, xx = x0 + r % HW - R;
       float v = 0.f;
       if (c0 + c < a.cin && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W)
         v = inp[((int64_t)yy * a.W + xx) * a.in_cs + c0 + c];
-      s_in[c][r / HW][r % HW] = v;
+      s_in[c * PS + r] = v;
     }
     for (int e = t; e < KS * KS * CI * CO_T; e += 256) {
       int tap = e / (CI * CO_T), r = e % (CI * CO_T);
@@ -102,7 +107,7 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
       for (int c = 0; c < CI; ++c) {
         float xv[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) xv[i] = s_in[c][prow + dy][pcol + i + dx];
+        for (int i = 0; i < 4; ++i) xv[i] = s_in[c * PS + (prow + dy) * HW + pcol + i + dx];
 #pragma unroll
         for (int j = 0; j < NC; ++j) {
           float wv = s_w[tap][c][cg * NC + j];
@@ -115,28 +120,40 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
 
   const int y = y0 + prow;
   if (EPI == EPI_STORE) {
+    // four channels per 16-byte access (channel counts are multiples of
+    // 32, channel offsets and row strides multiples of 4 floats)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int x = x0 + pcol + i;
       if (y >= a.H || x >= a.W) continue;
       const int64_t pix = ((int64_t)p * a.H + y) * a.W + x;
 #pragma unroll
-      for (int j = 0; j < NC; ++j) {
+      for (int j = 0; j < NC; j += 4) {
         const int co = co0 + cg * NC + j;
         if (co >= a.cout_total) continue;
-        float v = acc[i][j] + a.b[co];
-        if (a.iq) {
-          // integer class: act on the accumulator, requantise, then the
-          // residual (an activation at the same binary point)
-          if (a.act) v = lrelu_i(v);
-          v = rq_f(v, a.rq, 127);
-          if (a.res) v = (float)clamp_ll((long long)v + (long long)a.res[pix * a.res_cs + a.res_co + co], 127);
-          a.out[pix * a.out_cs + a.out_co + co] = v;
-          continue;
+        const float4 bb = *reinterpret_cast<const float4 *>(a.b + co);
+        float v[4] = {acc[i][j] + bb.x, acc[i][j + 1] + bb.y, acc[i][j + 2] + bb.z,
+                      acc[i][j + 3] + bb.w};
+        float r[4] = {0.f, 0.f, 0.f, 0.f};
+        if (a.res) {
+          const float4 rr = *reinterpret_cast<const float4 *>(a.res + pix * a.res_cs + a.res_co + co);
+          r[0] = rr.x; r[1] = rr.y; r[2] = rr.z; r[3] = rr.w;
         }
-        if (a.res) v += a.res[pix * a.res_cs + a.res_co + co];
-        if (a.act) v = lrelu(v);
-        a.out[pix * a.out_cs + a.out_co + co] = v;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (a.iq) {
+            // integer class: act on the accumulator, requantise, then the
+            // residual (an activation at the same binary point)
+            if (a.act) v[k] = lrelu_i(v[k]);
+            v[k] = rq_f(v[k], a.rq, 127);
+            if (a.res) v[k] = (float)clamp_ll((long long)v[k] + (long long)r[k], 127);
+          } else {
+            if (a.res) v[k] += r[k];
+            if (a.act) v[k] = lrelu(v[k]);
+          }
+        }
+        *reinterpret_cast<float4 *>(a.out + pix * a.out_cs + a.out_co + co) =
+            make_float4(v[0], v[1], v[2], v[3]);
       }
     }
   } else if (EPI == EPI_LSTM) {
@@ -183,15 +200,22 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
       const int x = x0 + pcol + i;
       const bool in = y < a.H && x < a.W;
       const int64_t pix = ((int64_t)p * a.H + min(y, a.H - 1)) * a.W + min(x, a.W - 1);
+      float rv[NC];
+#pragma unroll
+      for (int j = 0; j < NC; j += 4) {  // the residual, 16 bytes at a time
+        float4 r4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (in) r4 = *reinterpret_cast<const float4 *>(a.res + pix * a.res_cs + a.res_co + cg * NC + j);
+        rv[j] = r4.x; rv[j + 1] = r4.y; rv[j + 2] = r4.z; rv[j + 3] = r4.w;
+      }
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
         const int co = cg * NC + j;
         float v = acc[i][j] + a.b[co];
         if (a.iq) {
           v = rq_f(v, a.rq, 127);
-          if (in) v = (float)clamp_ll((long long)v + (long long)a.res[pix * a.res_cs + a.res_co + co], 127);
+          if (in) v = (float)clamp_ll((long long)v + (long long)rv[j], 127);
         } else if (in) {
-          v += a.res[pix * a.res_cs + a.res_co + co];
+          v += rv[j];
         }
         pm[i] = fmaf(a.wh[co], v, pm[i]);
         pr[i] = fmaf(a.wh[a.cout_total + co], v, pr[i]);
