@@ -719,11 +719,11 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
 # is kept under profiles/); valid only while the sources
 # of the convolution kernels hash to "src" (the capture's), else reported
 # as null.
-TRAFFIC = {"src": "81a51db34ed5659f", "precision": "fp8", "batch": 24,
-           "bytes_per_launch": {"ctx_conv1x1": 345.43e6, "ctx_lstm_gates_conv3x3": 1150.36e6,
-                                "ctx_conv3x3": 246.46e6, "ctx_head_conv3x3": 210.80e6,
-                                "rans_decode": 5.89e6, "lift_step": 31.10e6,
-                                "ctx_small": 173.88e6}}
+TRAFFIC = {"src": "5b4c3e4b54ccb221", "precision": "fp8", "batch": 24,
+           "bytes_per_launch": {"ctx_conv1x1": 346.45e6, "ctx_lstm_gates_conv3x3": 1160.93e6,
+                                "ctx_conv3x3": 247.12e6, "ctx_head_conv3x3": 210.79e6,
+                                "rans_decode": 5.87e6, "lift_step": 31.08e6,
+                                "ctx_small": 173.85e6}}
 
 
 def conv_src_hash() -> str:
