@@ -25,7 +25,7 @@ The other workloads, each under "workloads" with its own key:
   noise), q = 8, C = 32, FP32 class, batch 1, in both LL modes (four-step
   and autoregressive), with the logistic-mixture (K = 3) probability
   model (four-step LL) and with the integer-network context model (INT8
-  class), device-resident stream, CUDA events;
+  class, both LL modes), device-resident stream, CUDA events;
 * video_4gop_1080p: 4 GOPs x 8 frames of 1920x1080 RGB (panned 1/f canvas
   and sprites), 3 temporal levels, BF16 class, pw_decode_gop host in / host
   out, wall clock;
@@ -448,7 +448,7 @@ def single_gray_run(pw, local, stream_ptr, steps: int, warmup: int):
     seed 0), q = 8, C = 32 context model, FP32 class, batch 1, in both LL
     modes, with the logistic-mixture (K = 3) probability model in place
     of the Laplace one (four-step LL), and with the integer-network context
-    model (INT8 class, four-step LL); device-resident stream -> device
+    model (INT8 class, both LL modes); device-resident stream -> device
     image, CUDA events per decode."""
     import torch
     import synthetic as S
@@ -460,7 +460,8 @@ def single_gray_run(pw, local, stream_ptr, steps: int, warmup: int):
     for mode, name, prob, prec in ((0, "four_step_ll", 0, "fp32"),
                                    (1, "autoregressive_ll", 0, "fp32"),
                                    (0, "four_step_ll_logistic_mixture", 1, "fp32"),
-                                   (0, "four_step_ll_integer_network", 0, "int8")):
+                                   (0, "four_step_ll_integer_network", 0, "int8"),
+                                   (1, "autoregressive_ll_integer_network", 0, "int8")):
         cfg = S.ModelConfig(levels=4, C=32, F=16, ll_mode=mode, prob=prob)
         c = pw.Codec(local, prec, stream=stream_ptr)
         m = c.load_model(S.pack_blob(cfg, S.random_model(cfg, 0)))

@@ -110,12 +110,12 @@ class Model:
         self.hash = model_hash(blob)
         self.integer = integer
         self._intctx = None
-        if integer and (self.mixture or self.ll_mode):
-            raise ValueError("the integer context model is four-step LL with Laplace heads")
+        if integer and self.mixture:
+            raise ValueError("the integer context model has Laplace heads")
 
     def int_context(self) -> I.IntContextModel:
         if self._intctx is None:
-            self._intctx = I.IntContextModel(self.tensors, self.C)
+            self._intctx = I.IntContextModel(self.tensors, self.C, self.ll_mode)
         return self._intctx
 
 
@@ -424,8 +424,8 @@ def decode_symbols(model: Model, bs: bytes, params: list | None = None):
     if hd["mixture"] != model.mixture:
         raise ValueError("probability model of the stream and the model differ")
     integer = hd["integer"]
-    if integer and (hd["mixture"] or hd["ll_ar"]):
-        raise ValueError("integer context model streams are four-step LL, Laplace")
+    if integer and hd["mixture"]:
+        raise ValueError("integer context model streams use Laplace tables")
     ic = model.int_context() if integer else None
     L = hd["levels"]
     mult = 1 << L
@@ -457,7 +457,10 @@ def decode_symbols(model: Model, bs: bytes, params: list | None = None):
 
                     def table_of(p, s=s, cur=cur, W=W):
                         y, x = divmod(p, W)
-                        mu, sg = cm.ar_params_at(s.astype(np.float64), y, x)
+                        if integer:
+                            mu, sg = int_params(*ic.ar_tj_at(s, y, x))
+                        else:
+                            mu, sg = cm.ar_params_at(s.astype(np.float64), y, x)
                         ctr, phi, j = E.index_decision(mu, sg)
                         cur[p] = int(ctr)
                         return bank[int(E.table_id(phi, j))]

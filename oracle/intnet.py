@@ -8,8 +8,8 @@ for data compression with latent-variable models", ICLR 2019) remove the
 problem by construction: every operation of the network is integer
 arithmetic with a fixed rounding rule, so encoder and decoder compute
 identical parameters on any hardware. This module states that arithmetic
-for the four-step context model (ConvLSTM and the fusion nets of steps
-1-4, Laplace heads, four-step LL). The layer structure is the float
+for the context model (ConvLSTM, the fusion nets of steps 1-4, the
+autoregressive LL model, Laplace heads). The layer structure is the float
 model's; this is the reading of how each layer is made integer:
 
 * activations are integers with a fixed binary point: z, u, e, a (the
@@ -183,16 +183,29 @@ class IntConv:
         return clampa(rq(v, self.S - fa_out))
 
 
-class IntContextModel:
-    """The integer context model of a float weight set (four-step LL)."""
+AR_MASK = np.array([[1, 1, 1, 1, 1], [1, 1, 1, 1, 1], [1, 1, 0, 0, 0],
+                    [0, 0, 0, 0, 0], [0, 0, 0, 0, 0]], dtype=np.float64)
 
-    def __init__(self, tensors: dict, C: int):
+
+class IntContextModel:
+    """The integer context model of a float weight set: four-step nets for
+    subbands 2..13 and either four-step nets (ll_mode 0) or the
+    autoregressive model (ll_mode 1) for LL. The autoregressive model's
+    layers in integer form: f1 = rq(lrelu(masked 5x5 conv of clamp(s))),
+    f2 = rq(lrelu(1x1 f1)) (4 fractional bits each), head as the steps'."""
+
+    def __init__(self, tensors: dict, C: int, ll_mode: int = 0):
         t = tensors
         self.C = C
+        self.ll_mode = ll_mode
         self.we = IntConv(t["lstm.we"], t["lstm.be"], [(0, 1, 0)])
         self.wg = IntConv(t["lstm.wg"], t["lstm.bg"], [(0, C, FA), (C, C, FH)])
         self.nets = {}
-        for ns in ("sb", "ll"):
+        if ll_mode == 1:
+            self.ar5 = IntConv(t["ar.w5"] * AR_MASK, t["ar.b5"], [(0, 1, 0)])
+            self.ar1 = IntConv(t["ar.w1"], t["ar.b1"], [(0, C, FA)])
+            self.arh = IntConv(t["ar.wh"], t["ar.bh"], [(0, C, FA)])
+        for ns in (("sb", "ll") if ll_mode == 0 else ("sb",)):
             p = f"{ns}.s0."
             n0 = dict(
                 win=IntConv(t[p + "win"], t[p + "bin"], [(0, C, FH)]),
@@ -236,6 +249,36 @@ class IntContextModel:
         h = clampa(rq(hsig(go) * np.clip(c, -128, 128), FH))
         return h, c
 
+    # --- autoregressive LL ---------------------------------------------------
+    def head_tj(self, hd: IntConv, acc):
+        t = np.clip(rq(acc[..., 0], hd.S - 4), -(1 << 23), 1 << 23)
+        j = np.clip(rq(acc[..., 1], hd.S - 3) + J0, 0, 127)
+        return t, j
+
+    def ar_tj_all(self, s: np.ndarray):
+        """(t, j) of the autoregressive LL model at every position, all
+        symbols known (only causal neighbours enter through the mask)."""
+        sc = clampa(np.asarray(s, dtype=np.int64))
+        f = self.ar5.out(sc[:, :, None], act=True)
+        f = self.ar1.out(f, act=True)
+        return self.head_tj(self.arh, self.arh.acc(f))
+
+    def ar_tj_at(self, s: np.ndarray, y: int, x: int):
+        """(t, j) at (y, x) from the causal neighbourhood only."""
+        H, W = s.shape
+        acc = self.ar5.bq.copy()
+        for dy in range(3):
+            for dx in range(5):
+                if dy == 2 and dx >= 2:
+                    continue
+                yy, xx = y + dy - 2, x + dx - 2
+                if 0 <= yy < H and 0 <= xx < W:
+                    acc = acc + self.ar5.wq[:, 0, dy, dx] * int(np.clip(s[yy, xx], -AMAX, AMAX))
+        f = clampa(rq(lrelu_i(acc), self.ar5.S - FA))
+        f = clampa(rq(lrelu_i(self.ar1.wq @ f + self.ar1.bq), self.ar1.S - FA))
+        t, j = self.head_tj(self.arh, self.arh.wq @ f + self.arh.bq)
+        return int(t), int(j)
+
     # --- context fusion ------------------------------------------------------
     def step_tj(self, k: int, s: np.ndarray, l: np.ndarray, ns: str):
         """(t, j) of step k over the whole subband: t = 16 mu, j the scale
@@ -257,11 +300,7 @@ class IntContextModel:
             z = n["wz"].out(np.concatenate([a, l], axis=2))
             u = n["w1"].out(z, act=True)
             z = clampa(z + n["w2"].out(u))
-        acc = n["wh"].acc(z)
-        S = n["wh"].S
-        t = np.clip(rq(acc[..., 0], S - 4), -(1 << 23), 1 << 23)
-        j = np.clip(rq(acc[..., 1], S - 3) + J0, 0, 127)
-        return t, j
+        return self.head_tj(n["wh"], n["wh"].acc(z))
 
 
 def index_of(t, j):
@@ -279,6 +318,9 @@ def context_tj_all(model: IntContextModel, qsb: list):
     C = model.C
     for i, s in enumerate(qsb):
         H, W = s.shape
+        if i == 0 and model.ll_mode == 1:
+            out.append(model.ar_tj_all(s))
+            continue
         if i == 0:
             l, ns = np.zeros((H, W, C), dtype=np.int64), "ll"
         else:

@@ -205,7 +205,15 @@ static int finish(pw_ctx *ctx) {
   return PW_OK;
 }
 
-static ArWeightsDev ar_weights(const Model &m) {
+// The autoregressive LL model's weights for this context's class (the
+// integer-network class uses the quantised copy).
+static ArWeightsDev ar_weights(const pw_ctx *ctx, const Model &m) {
+  if (ctx->precision == PW_PREC_INT8 && m.intn) {
+    const IntNets &n = *m.intn;
+    ArWeightsDev w{n.ar_w5, n.ar_b5, n.ar_w1, n.ar_b1, n.ar_wh, n.ar_bh};
+    w.iq = 1; w.n5 = n.ar_n5; w.n1 = n.ar_n1; w.n_mu = n.ar_nmu; w.n_rho = n.ar_nrho;
+    return w;
+  }
   return ArWeightsDev{m.ar_w5, m.ar_b5, m.ar_w1, m.ar_b1, m.ar_wh, m.ar_bh};
 }
 
@@ -265,7 +273,7 @@ static int decode_symbols_dev(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeade
       // order, decoding each symbol from the plane's single-state chunk
       if (g.group_count[0] != 1) { set_last_error("bad LL chunk layout"); return PW_ECORRUPT; }
       ProfScope ps(ctx, KC_RANS_DEC, 0.0, (double)P * g.sh[0] * g.sw[0] * 8.0);
-      int s = launch_ll_ar_decode(dch + pl.gbase[0], P, g.sh[0], g.sw[0], m.C, ar_weights(m),
+      int s = launch_ll_ar_decode(dch + pl.gbase[0], P, g.sh[0], g.sw[0], m.C, ar_weights(ctx, m),
                                   ctx->bank, pl.ws.Q, ctx->status, st);
       bump(ctx);
       if (s) return s;
@@ -564,7 +572,7 @@ static int encode_from_latent(pw_ctx *ctx, Model &m, Plan &pl, int B, float dl, 
     int s;
     if (sb == 0 && g.ll_ar) {
       // all LL symbols are known: the AR model runs at every position at once
-      if ((s = launch_ll_ar_params(ws.Q, P, g.sh[0], g.sw[0], m.C, ar_weights(m), ws.idx, nullptr,
+      if ((s = launch_ll_ar_params(ws.Q, P, g.sh[0], g.sw[0], m.C, ar_weights(ctx, m), ws.idx, nullptr,
                                    nullptr, st)))
         return s;
       bump(ctx);
@@ -1330,7 +1338,7 @@ static int context_all(pw_ctx *c, Model &m, int H, int W, const int32_t *q, Plan
   if (tc_precision(c->precision)) tc_error_reset(pl->ws, st);
   for (int sb = 0; sb < g.nsb; ++sb) {
     if (sb == 0 && m.ll_mode == 1) {
-      if ((s = launch_ll_ar_params(pl->ws.Q, 1, g.sh[0], g.sw[0], m.C, ar_weights(m), pl->ws.idx,
+      if ((s = launch_ll_ar_params(pl->ws.Q, 1, g.sh[0], g.sw[0], m.C, ar_weights(c, m), pl->ws.idx,
                                    pl->ws.mu, pl->ws.sg, st)))
         return s;
       bump(c);

@@ -43,6 +43,10 @@ struct IntNets {
   float *we = nullptr, *be = nullptr, *wg = nullptr, *bg = nullptr;  // ConvLSTM
   int n_e = 0, n_g = 0;
   IntStepNet sb[4], ll[4];
+  // autoregressive LL model (ll_mode 1): masked 5x5 conv, 1x1, head
+  float *ar_w5 = nullptr, *ar_b5 = nullptr, *ar_w1 = nullptr, *ar_b1 = nullptr,
+        *ar_wh = nullptr, *ar_bh = nullptr;
+  int ar_n5 = 0, ar_n1 = 0, ar_nmu = 0, ar_nrho = 0;
 };
 
 // Tensor-core (BF16) copies of the context-model weights, see ctx_tc.cu.
@@ -55,7 +59,7 @@ struct Model {
   // of 3 (9 outputs; FP32 precision class and four-step LL only)
   int nh = 2;
   bool mix = false;
-  IntNets *intn = nullptr;   // built when loaded in an INT8 context
+  IntNets *intn = nullptr;   // built when loaded in an INT8 context (Laplace models)
   uint64_t hash = 0;
   uint64_t uid = 0;          // unique per loaded model (keys cached workspaces)
   std::vector<float *> allocs;

@@ -1753,8 +1753,8 @@ int Model::prepare(int precision) {
   }
   if (precision == PW_PREC_INT8) {
     if (!intn) {
-      set_last_error("the integer-network class needs a four-step LL Laplace model loaded in an "
-                     "INT8 context");
+      set_last_error("the integer-network class needs a Laplace model loaded in an INT8 "
+                     "context");
       return PW_EUNSUPPORTED;
     }
     return PW_OK;

@@ -5,7 +5,9 @@
 // Model (a reading of the text; the architecture is in a missing figure):
 // a 5x5 mask-A convolution (taps strictly before the centre in raster order:
 // 12 taps) 1 -> C, LeakyReLU, 1x1 C -> C, LeakyReLU, 1x1 C -> 2 giving the
-// Laplace mean and softplus^-1 scale. The decoder runs one warp per plane
+// Laplace mean and softplus^-1 scale (in the integer-network class: the
+// same layers in integer arithmetic, the head giving 16 mu and the scale
+// bin directly). The decoder runs one warp per plane
 // over the LL positions in raster order: the warp evaluates the model at the
 // next position from symbols already decoded, lane 0 decodes that symbol
 // from the plane's single-state rANS chunk and the warp moves on. The
@@ -29,19 +31,36 @@ struct ArSmem {
 __device__ __forceinline__ int ar_tap_dy(int t) { return t < 10 ? t / 5 : 2; }
 __device__ __forceinline__ int ar_tap_dx(int t) { return t < 10 ? t % 5 : t - 10; }
 
-// Parameters (mu, rho) at (y, x) of one plane from its symbols s (int32 plane
-// of h x w, read through `get`). Executed by a full warp; returns the same
+// Integer-network class helpers: the sums below are exact integers in FP32
+// (|sum| < 2^24); requantisation by n bits rounds half up, LeakyReLU has
+// slope 1/128 (floor division), activations are clamped to +-127.
+__device__ __forceinline__ long long ar_rq(long long x, int n) {
+  return n > 0 ? ((x + (1LL << (n - 1))) >> n) : (x << (-n));
+}
+__device__ __forceinline__ float ar_act_i(float v, int n) {
+  long long x = (long long)v;
+  x = x >= 0 ? x : (x >> 7);
+  x = ar_rq(x, n);
+  return (float)(x > 127 ? 127 : (x < -127 ? -127 : x));
+}
+
+// Parameters at (y, x) of one plane from its symbols s (int32 plane of
+// h x w, read through `get`): the packed table index, and mu and sigma for
+// the optional parameter outputs. Executed by a full warp; returns the same
 // values in every lane. C in {32, 64, 128}: lane owns channels lane + 32 i.
 template <int C, class Get>
-__device__ __forceinline__ void ar_params(const ArSmem &S, int h, int w, int y, int x, Get get,
-                                          float &mu, float &rho) {
+__device__ __forceinline__ void ar_params(const ArSmem &S, const ArWeightsDev &wd, int h, int w,
+                                          int y, int x, Get get, uint32_t &pk, float &mu,
+                                          float &sg) {
   const int lane = threadIdx.x & 31;
   constexpr int NPL = C / 32;
   float nb[kArTaps];
 #pragma unroll
   for (int t = 0; t < kArTaps; ++t) {
     const int yy = y + ar_tap_dy(t) - 2, xx = x + ar_tap_dx(t) - 2;
-    nb[t] = (yy >= 0 && yy < h && xx >= 0 && xx < w) ? (float)get(yy * w + xx) : 0.f;
+    int32_t v = (yy >= 0 && yy < h && xx >= 0 && xx < w) ? get(yy * w + xx) : 0;
+    if (wd.iq) v = min(max(v, -127), 127);   // integer class input
+    nb[t] = (float)v;
   }
   float f[NPL];
 #pragma unroll
@@ -50,7 +69,7 @@ __device__ __forceinline__ void ar_params(const ArSmem &S, int h, int w, int y, 
     float v = S.b5[c];
 #pragma unroll
     for (int t = 0; t < kArTaps; ++t) v = fmaf(S.w5t[t * C + c], nb[t], v);
-    v = v >= 0.f ? v : 0.01f * v;
+    v = wd.iq ? ar_act_i(v, wd.n5) : (v >= 0.f ? v : 0.01f * v);
     f[i] = v;
     S.f[(threadIdx.x >> 5) * C + c] = v;
   }
@@ -68,7 +87,7 @@ __device__ __forceinline__ void ar_params(const ArSmem &S, int h, int w, int y, 
 #pragma unroll
   for (int i = 0; i < NPL; ++i) {
     const int c = lane + 32 * i;
-    const float hv = hsum[i] >= 0.f ? hsum[i] : 0.01f * hsum[i];
+    const float hv = wd.iq ? ar_act_i(hsum[i], wd.n1) : (hsum[i] >= 0.f ? hsum[i] : 0.01f * hsum[i]);
     pm = fmaf(S.wh[c], hv, pm);
     pr = fmaf(S.wh[C + c], hv, pr);
   }
@@ -78,8 +97,21 @@ __device__ __forceinline__ void ar_params(const ArSmem &S, int h, int w, int y, 
     pr += __shfl_xor_sync(0xffffffffu, pr, o);
   }
   __syncwarp();  // f is rewritten at the next position
-  mu = pm + S.bh[0];
-  rho = pr + S.bh[1];
+  const float m = pm + S.bh[0], rho = pr + S.bh[1];
+  if (wd.iq) {
+    // integer head: t = 16 mu and the scale bin j directly
+    long long t = ar_rq((long long)m, wd.n_mu);
+    t = t > (1LL << 23) ? (1LL << 23) : (t < -(1LL << 23) ? -(1LL << 23) : t);
+    long long j = ar_rq((long long)rho, wd.n_rho) + 24;
+    j = j < 0 ? 0 : (j > kNJ - 1 ? kNJ - 1 : j);
+    pk = ((uint32_t)(t + (1 << 23)) << 7) | (uint32_t)j;
+    mu = (float)t * 0.0625f;
+    sg = __int_as_float(0x3E000000 + ((int)j << 20) + (1 << 19));
+  } else {
+    pk = pack_index(m, rho);
+    mu = m;
+    sg = rho > 20.f ? rho : log1pf(expf(rho));
+  }
   (void)f;
 }
 
@@ -125,13 +157,14 @@ __global__ void k_ll_ar_params(const int32_t *__restrict__ Q, int P, int h, int 
   for (int e = warp; e < P * n; e += nw) {
     const int p = e / n, pos = e % n;
     const int32_t *sp = Q + (int64_t)p * n;
-    float mu, rho;
-    ar_params<C>(S, h, w, pos / w, pos % w, [&](int i) { return sp[i]; }, mu, rho);
+    uint32_t pk;
+    float mu, sg;
+    ar_params<C>(S, wd, h, w, pos / w, pos % w, [&](int i) { return sp[i]; }, pk, mu, sg);
     if ((threadIdx.x & 31) == 0) {
-      idx[(int64_t)p * n + pos] = pack_index(mu, rho);
+      idx[(int64_t)p * n + pos] = pk;
       if (mu_out) {
         mu_out[(int64_t)p * n + pos] = mu;
-        sg_out[(int64_t)p * n + pos] = rho > 20.f ? rho : log1pf(expf(rho));
+        sg_out[(int64_t)p * n + pos] = sg;
       }
     }
   }
@@ -182,11 +215,12 @@ __global__ void k_ll_ar_decode(const DecChunk *__restrict__ chunks, int P, int h
   };
   for (int pos = 0; pos < n; ++pos) {
     if (__shfl_sync(0xffffffffu, bad ? 1 : 0, 0)) break;
-    float mu, rho;
-    ar_params<C>(S, h, w, pos / w, pos % w, [&](int i) { return s_sym[i]; }, mu, rho);
+    uint32_t pk;
+    float mu, sg;
+    ar_params<C>(S, wd, h, w, pos / w, pos % w, [&](int i) { return s_sym[i]; }, pk, mu, sg);
     if (lane == 0) {
       int ctr, tid;
-      unpack_index(pack_index(mu, rho), ctr, tid);
+      unpack_index(pk, ctr, tid);
       const uint16_t *t = bank + (size_t)tid * (kNSym + 1);
       uint32_t slot = x & (kM - 1);
       const int s = find_sym(t, slot);

@@ -11,6 +11,9 @@ struct ArWeightsDev {
   const float *b1;  // [C]
   const float *wh;  // [2][C]
   const float *bh;  // [2]
+  // integer-network class: the arrays hold quantised integers, iq = 1, and
+  // the layers' outputs are requantised by n5 / n1 bits (head: n_mu, n_rho)
+  int iq = 0, n5 = 0, n1 = 0, n_mu = 0, n_rho = 0;
 };
 
 int launch_ll_ar_params(const int32_t *Q, int P, int h, int w, int C, const ArWeightsDev &wd,

@@ -308,7 +308,7 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
   // integer-network class: quantised copies of the context model
   delete intn;
   intn = nullptr;
-  if (c->precision == PW_PREC_INT8 && ll_mode == 0 && !mix && st == PW_OK) {
+  if (c->precision == PW_PREC_INT8 && !mix && st == PW_OK) {
     const int FA = 4, FH = 7;
     IntNets *in = new IntNets();
     std::vector<float> w, bb, wq, bq;
@@ -335,7 +335,34 @@ int Model::load(pw_ctx *c, const void *blob, size_t n) {
     } else {
       ok = false;
     }
-    for (int set = 0; set < 2 && ok; ++set) {
+    if (ok && ll_mode == 1) {
+      // autoregressive LL: the 5x5 weights masked to the 12 causal taps
+      // before quantisation (the mask decides the scale)
+      if (get("ar.w5", {C, 1, 5, 5}, w) && get("ar.b5", {C}, bb)) {
+        for (int co = 0; co < C; ++co)
+          for (int t = 0; t < 25; ++t)
+            if (!(t < 10 || t == 10 || t == 11)) w[(size_t)co * 25 + t] = 0.f;
+        in->ar_n5 = shift_ok(quantise(w, bb, C, 1, 25, {{0, 1, 0}}, wq, bq) - FA);
+        in->ar_w5 = up(wq); in->ar_b5 = up(bq);
+      } else {
+        ok = false;
+      }
+      if (ok && get("ar.w1", {C, C}, w) && get("ar.b1", {C}, bb)) {
+        in->ar_n1 = shift_ok(quantise(w, bb, C, C, 1, {{0, C, FA}}, wq, bq) - FA);
+        in->ar_w1 = up(wq); in->ar_b1 = up(bq);
+      } else {
+        ok = false;
+      }
+      if (ok && get("ar.wh", {2, C}, w) && get("ar.bh", {2}, bb)) {
+        const int Sh = quantise(w, bb, 2, C, 1, {{0, C, FA}}, wq, bq);
+        in->ar_nmu = shift_ok(Sh - 4);
+        in->ar_nrho = shift_ok(Sh - 3);
+        in->ar_wh = up(wq); in->ar_bh = up(bq);
+      } else {
+        ok = false;
+      }
+    }
+    for (int set = 0; set < (ll_mode == 0 ? 2 : 1) && ok; ++set) {
       const std::string ns = set ? "ll" : "sb";
       IntStepNet *nets = set ? in->ll : in->sb;
       auto q1 = [&](const std::string &name, int co, int ci, int kk,

@@ -113,9 +113,31 @@ def test_gpu_stream_equals_oracle_stream_fullsize(codec):
     gm.close()
 
 
+@pytest.mark.parametrize("gain", [1.0, 4.0])
+def test_integer_autoregressive_ll_equals_the_oracle(codec, gain):
+    """pWave++'s default LL model (autoregressive) in integer form: the
+    parameters at every position and the streams equal the oracle's."""
+    blob = _blob(seed=4, ll_mode=1, gain=gain)
+    gm = codec.load_model(blob)
+    om = K.Model(blob, integer=True)
+    img = S.gray_sinusoids(96, 128, seed=8)
+    qsb = _latent(om, img)[0]
+    mu_g, sg_g = codec.context_params(gm, 96, 128, _flat([qsb]))
+    tj = I.context_tj_all(om.int_context(), qsb)
+    t_o = np.concatenate([t.reshape(-1) for t, _ in tj])
+    j_o = np.concatenate([j.reshape(-1) for _, j in tj])
+    assert np.array_equal(np.rint(mu_g.astype(np.float64) * 16).astype(np.int64), t_o)
+    assert np.array_equal((sg_g.view(np.uint32).astype(np.int64) - 0x3E000000) >> 20, j_o)
+    bs_g = codec.encode_image(gm, img, q=8.0)
+    assert bs_g == K.encode_image(blob, img, q=8.0, integer=True)
+    assert np.array_equal(codec.decode_symbols(gm, bs_g), _flat([qsb]))
+    gm.close()
+
+
 def test_integer_class_limits(pw, codec):
-    with pytest.raises(pw.PwError) as e:            # AR LL: no integer model
-        codec.load_model(_blob(ll_mode=1))
+    cfg = S.ModelConfig(levels=4, C=32, prob=1)
+    with pytest.raises(pw.PwError) as e:            # mixture heads: no integer model
+        codec.load_model(S.pack_blob(cfg, S.random_model(cfg, 0)))
     assert e.value.code == pw.PW_EUNSUPPORTED
     blob = _blob(seed=3)
     gm = codec.load_model(blob)
