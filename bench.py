@@ -376,6 +376,11 @@ def batched_precision(pw, local, prec, imgs, qs, blob, stream_ptr, steps, warmup
     ptrs = [dev_all.data_ptr() + int(offs[i]) for i in range(len(enc))]
     out = torch.empty((len(enc), H, W, 3), dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    calib = 0   # autotuner calibration, as for the headline leg
+    while not pw.pw_autotune_settled() and calib < 24:
+        c.decode_batch_device(m, ptrs, lens, out.data_ptr(), (H, W, 3))
+        torch.cuda.synchronize()
+        calib += 1
     for _ in range(warmup):
         c.decode_batch_device(m, ptrs, lens, out.data_ptr(), (H, W, 3))
     torch.cuda.synchronize()
@@ -852,6 +857,15 @@ def run_gpu(args):
                  "ms": float(stats[i].ms), "flops": float(stats[i].flops),
                  "bytes": float(stats[i].bytes)} for i in range(max(nst, 0))]
 
+    # autotuner calibration (untimed set-up, like the encodes above): the
+    # convolution classes of this batch size sample their candidate
+    # schedules on the first launches; decode until every class has its
+    # schedule, so that no warm-up or timed launch is a tuning sample
+    calib = 0
+    while not pw.pw_autotune_settled() and calib < 24:
+        step()
+        torch.cuda.synchronize()
+        calib += 1
     for _ in range(max(args.warmup - 1, 0)):
         step()
     if args.nvtx_step:
@@ -971,6 +985,7 @@ def run_gpu(args):
         "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
                    "reasons": clocks["reasons"]},
         "wall_s_timed_region": t_wall,
+        "autotune_calibration_steps": calib,
         "paper": PAPER,
     }
     if world == 1 and not args.no_compare:

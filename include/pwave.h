@@ -435,6 +435,10 @@ uint64_t pw_ctx_launch_count(const pw_ctx *ctx);
  * into buf (NUL-terminated, truncated to n) and returns the full length. */
 int pw_autotune(int enable);
 int pw_autotune_report(char *buf, size_t n);
+/* 1 when no convolution class seen so far is still being sampled (every
+ * one has its schedule), else 0. A service can run its warm-up decodes
+ * until this holds, so that no later launch is a tuning sample. */
+int pw_autotune_settled(void);
 
 /* Per-kernel-class timing. pw_ctx_profile(ctx, 1) resets the counters and
  * records a CUDA event pair on the context's stream around every launch that

@@ -123,6 +123,7 @@ _sig = {
     "pw_server_stats": (C.c_int, [_P, C.POINTER(pw_stats)]),
     "pw_server_destroy": (None, [_P]),
     "pw_autotune": (C.c_int, [C.c_int]),
+    "pw_autotune_settled": (C.c_int, []),
     "pw_autotune_report": (C.c_int, [C.c_char_p, C.c_size_t]),
     "pw_ctx_profile": (C.c_int, [_P, C.c_int]),
     "pw_ctx_kernel_stats": (C.c_int, [_P, C.POINTER(pw_kernel_stat), C.c_int]),

@@ -898,6 +898,8 @@ uint64_t pw_ctx_launch_count(const pw_ctx *c) { return c ? c->launches : 0; }
 
 int pw_autotune(int enable) { return tune_set_enabled(enable); }
 
+int pw_autotune_settled(void) { return tune_settled() ? 1 : 0; }
+
 int pw_autotune_report(char *buf, size_t n) {
   const std::string r = tune_report();
   if (buf && n) {
