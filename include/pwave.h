@@ -142,8 +142,8 @@ int pw_model_init_random(pw_ctx *ctx, const pw_model_cfg *cfg, uint64_t seed,
  * batch image decode - stream parsing, every context-model pass, the rANS
  * passes, dequantisation, inverse lifting and post-processing - depends only
  * on the cached plan (image size, channels, batch, model, chunk layout), so
- * after one direct run of a plan, and once the convolution autotuner has
- * settled, the context captures that chain into a CUDA graph (on a private
+ * after a direct run of a plan in which every convolution used its final
+ * (tuned) schedule, the context captures that chain into a CUDA graph (on a private
  * stream, so any user stream works, including the legacy default stream)
  * and replays it for later decodes of the plan: one launch instead of
  * hundreds. While per-kernel profiling is on, decodes run directly.
@@ -435,9 +435,10 @@ uint64_t pw_ctx_launch_count(const pw_ctx *ctx);
  * into buf (NUL-terminated, truncated to n) and returns the full length. */
 int pw_autotune(int enable);
 int pw_autotune_report(char *buf, size_t n);
-/* 1 when no convolution class seen so far is still being sampled (every
- * one has its schedule), else 0. A service can run its warm-up decodes
- * until this holds, so that no later launch is a tuning sample. */
+/* 1 when no convolution launch since the previous call (the first call:
+ * since the library loaded) was of a class still being tuned, else 0. A
+ * service can repeat its warm-up decodes until a decode is followed by 1,
+ * so that no later launch of those shapes is a tuning sample. */
 int pw_autotune_settled(void);
 
 /* Per-kernel-class timing. pw_ctx_profile(ctx, 1) resets the counters and

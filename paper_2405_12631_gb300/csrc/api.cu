@@ -1,5 +1,6 @@
 // C ABI of libpwave (include/pwave.h) and the host-side batch drivers.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -81,7 +82,7 @@ struct Plan {
   cudaGraphExec_t gexec = nullptr;
   const float *graph_recon = nullptr;   // its reconstructed planes
   uint64_t graph_launches = 0;          // kernel launches it holds
-  int direct_runs = 0;
+  bool tuned_run = false;               // the last direct run used final schedules only
   bool graph_bad = false;               // capture failed: stay direct
   ~Plan() {
     if (gexec) {
@@ -458,13 +459,12 @@ static void capture_chain(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader &h
   cudaGetLastError();
 }
 
-// decode_chain, replayed from the plan's graph once the plan has run
-// directly (kernel attributes set, buffers in place) and no convolution
-// class is still being tuned; direct while the context profiles kernels.
+// decode_chain, replayed from the plan's graph once a direct run of the plan
+// (kernel attributes set, buffers in place) launched no convolution of a
+// class still being tuned; direct while the context profiles kernels.
 static int run_decode_chain(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader &h0,
                             const float **recon) {
-  const bool eligible = ctx->graphs && !prof_of(ctx).on && !pl.graph_bad &&
-                        pl.direct_runs > 0 && tune_settled();
+  const bool eligible = ctx->graphs && !prof_of(ctx).on && !pl.graph_bad && pl.tuned_run;
   if (eligible && !pl.gexec) capture_chain(ctx, m, pl, h0);
   if (eligible && pl.gexec) {
     PW_CUDA_TRY(cudaGraphLaunch(pl.gexec, ctx->stream));
@@ -473,8 +473,9 @@ static int run_decode_chain(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader 
     *recon = pl.graph_recon;
     return PW_OK;
   }
+  const uint64_t u0 = tune_untuned_uses();
   const int s = decode_chain(ctx, m, pl, h0, recon);
-  if (s == PW_OK) pl.direct_runs += 1;
+  pl.tuned_run = s == PW_OK && tune_untuned_uses() == u0;
   return s;
 }
 
@@ -898,7 +899,11 @@ uint64_t pw_ctx_launch_count(const pw_ctx *c) { return c ? c->launches : 0; }
 
 int pw_autotune(int enable) { return tune_set_enabled(enable); }
 
-int pw_autotune_settled(void) { return tune_settled() ? 1 : 0; }
+int pw_autotune_settled(void) {
+  static std::atomic<uint64_t> last{~0ull};
+  const uint64_t now = tune_untuned_uses();
+  return last.exchange(now) == now ? 1 : 0;
+}
 
 int pw_autotune_report(char *buf, size_t n) {
   const std::string r = tune_report();

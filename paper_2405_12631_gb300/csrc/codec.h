@@ -228,8 +228,8 @@ struct pw_ctx {
   void *plan_cache = nullptr;      // cached workspaces per geometry (api.cu)
   void *prof = nullptr;            // per-kernel-class event timing (prof.cpp)
   int lane_shift = 7;              // encoders: 2^lane_shift symbols per rANS state
-  // image decodes replay a CUDA graph of their plan's pass chain once the
-  // plan has run directly and the autotuner has settled (pw_ctx_set_graphs)
+  // image decodes replay a CUDA graph of their plan's pass chain once a
+  // direct run of the plan used only tuned schedules (pw_ctx_set_graphs)
   int graphs = 1;
   cudaStream_t cap_stream = nullptr;   // private stream the chains are captured on
   uint64_t graph_replays = 0;

@@ -1125,6 +1125,8 @@ static std::mutex g_tune_mu;
 static std::map<uint64_t, TuneEntry> g_tune;
 static std::vector<TunePending> g_tune_pending;
 static std::atomic<int> g_tune_on{1};
+// launches of a class still being tuned (sampled or waiting for read-back)
+static std::atomic<uint64_t> g_untuned_uses{0};
 
 static uint64_t tune_key(const TcWeights::Conv &cv, int epi, int tiles) {
   int cls = 0;
@@ -1184,6 +1186,7 @@ static TuneChoice tune_next(uint64_t key, bool can_pair, bool has_alt, cudaStrea
     return c;
   }
   if (!g_tune_on.load()) return c;
+  g_untuned_uses.fetch_add(1);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
@@ -1213,13 +1216,10 @@ static void tune_record(uint64_t key, int cand, cudaEvent_t e0, cudaEvent_t e1) 
   g_tune_pending.push_back(TunePending{key, cand, e0, e1});
 }
 
-bool tune_settled() {
+uint64_t tune_untuned_uses() {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   tune_poll_locked();
-  if (!g_tune_on.load()) return true;
-  for (const auto &kv : g_tune)
-    if (!kv.second.tuned) return false;
-  return g_tune_pending.empty();
+  return g_untuned_uses.load();
 }
 
 int tune_set_enabled(int on) {

@@ -22,9 +22,10 @@ int tc_conv_host(pw_ctx *ctx, int P, int H, int W, int cin, int cout, int ks, in
 // Autotuner of the tensor-core convolutions (ctx_tc.cu): enable / disable
 // (returns the previous setting) and a text report of the tuned classes.
 int tune_set_enabled(int on);
-// True when no convolution class is still being tuned (every class seen has
-// its schedule): launches then no longer record sampling events, so a pass
-// chain can be captured into a CUDA graph with its final schedules.
-bool tune_settled();
+// Count of convolution launches so far whose class was still being tuned
+// (sampled, or waiting for its samples to be read back; read-backs are
+// polled first). A pass chain during which it did not change used final
+// schedules only, so it can be captured into a CUDA graph.
+uint64_t tune_untuned_uses();
 std::string tune_report();
 }  // namespace pw

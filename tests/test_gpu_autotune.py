@@ -45,3 +45,20 @@ def test_autotune_does_not_change_results(pw, prec):
                              f"tiles: choice {e['choice']} us {e['us']}" for e in rep))
     model.close()
     codec.close()
+
+
+def test_autotune_settles(pw):
+    """Repeated decodes of one plan finish every class's sampling, after
+    which pw_autotune_settled reports it (what a service waits for)."""
+    codec = pw.Codec(0, "fp8")
+    cfg = S.ModelConfig(levels=4, C=64, ll_mode=0)
+    model = codec.load_model(S.pack_blob(cfg, S.random_model(cfg, 5)))
+    bs = codec.encode_image(model, S.rgb_natural(136, 200, seed=14), q=8.0)
+    ref = codec.decode_image(model, bs)
+    n = 0
+    while not pw.pw_autotune_settled() and n < 40:
+        assert np.array_equal(codec.decode_image(model, bs), ref)
+        n += 1
+    assert pw.pw_autotune_settled() == 1, n
+    model.close()
+    codec.close()
