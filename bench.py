@@ -725,11 +725,11 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
 # is kept under profiles/); valid only while the sources
 # of the convolution kernels hash to "src" (the capture's), else reported
 # as null.
-TRAFFIC = {"src": "5b4c3e4b54ccb221", "precision": "fp8", "batch": 24,
-           "bytes_per_launch": {"ctx_conv1x1": 346.45e6, "ctx_lstm_gates_conv3x3": 1160.93e6,
-                                "ctx_conv3x3": 247.12e6, "ctx_head_conv3x3": 210.79e6,
-                                "rans_decode": 5.87e6, "lift_step": 31.08e6,
-                                "ctx_small": 173.85e6}}
+TRAFFIC = {"src": "c155661860b53346", "precision": "fp8", "batch": 24,
+           "bytes_per_launch": {"ctx_conv1x1": 346.21e6, "ctx_lstm_gates_conv3x3": 1178.65e6,
+                                "ctx_conv3x3": 246.70e6, "ctx_head_conv3x3": 210.79e6,
+                                "rans_decode": 5.87e6, "lift_step": 31.09e6,
+                                "ctx_small": 173.86e6}}
 
 
 def conv_src_hash() -> str:
