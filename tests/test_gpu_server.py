@@ -32,10 +32,13 @@ def _requests(n, seed):
     return reqs, imgs
 
 
-@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp8"])
-def test_server_results_identical_to_single_decode(pw, prec):
+@pytest.mark.parametrize("prec,prob", [("fp32", 0), ("bf16", 0), ("fp8", 0), ("int8", 0),
+                                       ("fp32", 1)])
+def test_server_results_identical_to_single_decode(pw, prec, prob):
+    """prob = 1: the logistic-mixture model (FP32); int8: the integer-network
+    class."""
     codec = pw.Codec(0, prec)
-    cfg = S.ModelConfig(levels=4, C=32, ll_mode=0)
+    cfg = S.ModelConfig(levels=4, C=32, ll_mode=0, prob=prob)
     model = codec.load_model(S.pack_blob(cfg, S.random_model(cfg, 11)))
     reqs, imgs = _requests(14, seed=3)
     # two requests repeated so that same-geometry batches form
