@@ -155,3 +155,25 @@ def test_integer_class_limits(pw, codec):
     m32.close()
     f32.close()
     gm.close()
+
+
+def test_integer_class_escapes_and_lossless_equal_the_oracle(codec):
+    """Large symbols: a fine quantiser (residuals beyond +-62 take the
+    escape path) and a 12-bit lossless RGB image (context inputs clamped at
+    +-127): the GPU's streams equal the oracle's byte for byte and the
+    lossless image decodes exactly."""
+    blob = _blob(seed=6)
+    gm = codec.load_model(blob)
+    img = S.rgb_natural(48, 80, seed=10)
+    bs_g = codec.encode_image(gm, img, q=1.0 / 8.0)
+    bs_o = K.encode_image(blob, img, q=1.0 / 8.0, integer=True)
+    assert bs_g == bs_o
+    q = codec.analyse(gm, img, q=1.0 / 8.0)
+    assert np.max(np.abs(q)) > 62                     # escapes were coded
+    assert np.array_equal(codec.decode_symbols(gm, bs_g), q)
+    img12 = S.lossless_blobs(48, 64, seed=11)
+    bs_g = codec.encode_image(gm, img12, lossless=True, bitdepth=12)
+    bs_o = K.encode_image(blob, img12, lossless=True, bitdepth=12, integer=True)
+    assert bs_g == bs_o
+    assert np.array_equal(codec.decode_image(gm, bs_g), img12)
+    gm.close()
