@@ -177,3 +177,23 @@ def test_integer_class_escapes_and_lossless_equal_the_oracle(codec):
     assert bs_g == bs_o
     assert np.array_equal(codec.decode_image(gm, bs_g), img12)
     gm.close()
+
+
+def test_integer_class_gop_reconstructs_like_the_float_class(pw, codec):
+    """A motion-compensated GOP through the INT8 class: the temporal and
+    spatial transforms are the FP32 ones, so the frames decode exactly as the
+    FP32 class decodes its own stream of the same GOP (the context model
+    changes only the rate)."""
+    bl, bh = _blob(seed=7), _blob(seed=8)
+    frames = S.video_gop(48, 64, 8, seed=13)
+    ml, mh = codec.load_model(bl), codec.load_model(bh)
+    gs = codec.encode_gop(ml, mh, frames, q=8.0)
+    out = codec.decode_gop(ml, mh, gs, 8, frames.shape[1:])
+    f32 = pw.Codec(0, "fp32")
+    fl, fh = f32.load_model(bl), f32.load_model(bh)
+    gs32 = f32.encode_gop(fl, fh, frames, q=8.0)
+    assert gs != gs32
+    assert np.array_equal(out, f32.decode_gop(fl, fh, gs32, 8, frames.shape[1:]))
+    for m in (ml, mh, fl, fh):
+        m.close()
+    f32.close()
