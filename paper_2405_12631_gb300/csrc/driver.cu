@@ -34,9 +34,11 @@ __global__ void k_parse_streams(const uint8_t *const *streams, const uint64_t *l
     const uint64_t len = lens[b];
     const uint32_t nch = (uint32_t)nck * ex.ncomp;
     const uint64_t base = 64ull + 4ull * (nch + 1);
-    bool ok = s != nullptr && len >= base;
-    if (ok) {
-      ok = s[0] == 'P' && s[1] == 'W' && s[2] == 'B' && s[3] == 'S' && rd16(s + 4) == 1 &&
+    // header fields that must match the plan (a mismatch: kStHeader), then
+    // the payload and offset table (out of range or out of order: kStCorrupt)
+    bool hdr = s != nullptr && len >= base;
+    if (hdr) {
+      hdr = s[0] == 'P' && s[1] == 'W' && s[2] == 'B' && s[3] == 'S' && rd16(s + 4) == 1 &&
            rd16(s + 6) == ex.flags && rd32(s + 8) == ex.width && rd32(s + 12) == ex.height &&
            s[16] == ex.ncomp && s[17] == ex.levels && s[18] == ex.bitdepth &&
            s[19] == ex.colour && rd16(s + 28) == kT && s[30] == kLogM && s[31] == kMaxLanes &&
@@ -44,8 +46,8 @@ __global__ void k_parse_streams(const uint8_t *const *streams, const uint64_t *l
            rd32(s + 40) == (uint32_t)ex.hash && rd32(s + 44) == (uint32_t)(ex.hash >> 32) &&
            s[52] == ex.lane_byte;
     }
-    uint32_t pb = ok ? rd32(s + 48) : 0;
-    ok = ok && base + pb <= len;
+    uint32_t pb = hdr ? rd32(s + 48) : 0;
+    bool ok = hdr && base + pb <= len;
     const int gc = comp * nck + c;
     uint32_t o0 = 0, o1 = 0;
     if (ok) {
@@ -63,7 +65,8 @@ __global__ void k_parse_streams(const uint8_t *const *streams, const uint64_t *l
     const int p = b * ex.ncomp + comp;
     d.plane = (uint16_t)p;
     out[t.gbase + (int64_t)p * t.gcount + t.j] = d;
-    if (!ok) atomicOr(status, kStHeader);
+    if (!hdr) atomicOr(status, kStHeader);
+    else if (!ok) atomicOr(status, kStCorrupt);
     if (comp == 0 && c == 0) {
       float dl = 1.f, dh = 1.f;
       if (ok) {

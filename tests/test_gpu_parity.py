@@ -393,3 +393,42 @@ def test_lane_rules_share_one_context(codec, model32):
     for bs in streams + streams[::-1]:
         assert np.array_equal(codec.decode_symbols(gm, bs), q_ref)
     assert K.parse_header(lay)["n_chunks"] == K.parse_header(streams[1])["n_chunks"]
+
+
+def test_targeted_corruptions_reported(codec, model32, pw):
+    """Malformed offset tables and chunk sizes, each caught by the host's
+    header checks or by the device parser / decoder's own bounds checks
+    (PW_ECORRUPT), for host and device-resident streams; the context keeps
+    working after each."""
+    import struct
+    blob, gm, om = model32
+    img = S.gray_sinusoids(48, 64, seed=41)
+    bs = codec.encode_image(gm, img, q=8.0, chunk=256)
+    ref = codec.decode_image(gm, bs)
+    nch = struct.unpack_from("<I", bs, 36)[0]
+    pb = struct.unpack_from("<I", bs, 48)[0]
+    offs = list(struct.unpack_from(f"<{nch + 1}I", bs, 64))
+    assert nch > 8
+
+    def with_offsets(o):
+        b = bytearray(bs)
+        struct.pack_into(f"<{nch + 1}I", b, 64, *o)
+        return bytes(b)
+
+    cases = {
+        "offset beyond the payload": with_offsets(offs[:3] + [pb + 1000] + offs[4:]),
+        "offsets out of order": with_offsets(offs[:4] + [offs[2]] + offs[5:]),
+        "odd chunk size": with_offsets(offs[:5] + [offs[5] + 1] + offs[6:]),
+        "chunk shorter than its states": with_offsets(offs[:6] + [offs[5] + 2] + offs[7:]),
+    }
+    torch = pytest.importorskip("torch")
+    for name, bad in cases.items():
+        with pytest.raises(pw.PwError) as e:
+            codec.decode_image(gm, bad)
+        assert e.value.code == pw.PW_ECORRUPT, name
+        d = torch.from_numpy(np.frombuffer(bad, dtype=np.uint8).copy()).cuda()
+        out = torch.empty((48, 64), dtype=torch.uint8, device="cuda")
+        with pytest.raises(pw.PwError) as e:
+            codec.decode_batch_device(gm, [d.data_ptr()], [len(bad)], out.data_ptr(), (48, 64))
+        assert e.value.code == pw.PW_ECORRUPT, name
+        assert np.array_equal(codec.decode_image(gm, bs), ref), name
