@@ -98,8 +98,18 @@ struct Plan {
   }
 };
 
+// Scratch of the GOP calls, kept per context and grown on demand: hundreds
+// of MB per 1080p GOP, which allocating and freeing on every call would
+// cost (each cudaFree synchronises the device), and pinned staging for
+// host frames.
+struct GopBufs {
+  DevBuf bands, frames, t0, t1, img, mv, warp, luma;
+  HostBuf h_img;
+};
+
 struct PlanCache {
   std::vector<std::unique_ptr<Plan>> plans;
+  GopBufs gop;
 };
 
 Prof &prof_of(pw_ctx *ctx) { return *reinterpret_cast<Prof *>(ctx->prof); }
@@ -989,7 +999,9 @@ int pw_encode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, int nframes
   const int64_t F = (int64_t)nc * Hp * Wp;
   const int64_t row = (int64_t)W * nc, img = row * H;
   const size_t mv_bytes = gop_mv_bytes(nframes, Hp, Wp);
-  DevBuf dimg, dframes, dbands, dt0, dt1, dluma, dmv, dwarp;
+  GopBufs &gb = cache_of(c).gop;
+  DevBuf &dimg = gb.img, &dframes = gb.frames, &dbands = gb.bands, &dt0 = gb.t0, &dt1 = gb.t1,
+         &dluma = gb.luma, &dmv = gb.mv, &dwarp = gb.warp;
   int s;
   if ((s = dimg.ensure((size_t)img * nframes)) || (s = dframes.ensure((size_t)F * nframes * 4)) ||
       (s = dbands.ensure((size_t)F * nframes * 4)) || (s = dt0.ensure((size_t)F * nframes * 2)) ||
@@ -998,11 +1010,28 @@ int pw_encode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, int nframes
       (s = dwarp.ensure((size_t)F * (nframes / 2) * 4)))
     return s;
   cudaStream_t st = c->stream;
+  // host frames go through pinned staging (one copy to the device)
+  bool any_host = false;
+  for (int f = 0; f < nframes; ++f) any_host = any_host || !frames[f].is_device;
+  if (any_host && (s = gb.h_img.ensure((size_t)img * nframes))) return s;
   for (int f = 0; f < nframes; ++f) {
     const int64_t rs = frames[f].stride_bytes ? frames[f].stride_bytes : row;
-    PW_CUDA_TRY(cudaMemcpy2DAsync((uint8_t *)dimg.p + f * img, row, frames[f].data, rs, row, H,
-                                  frames[f].is_device ? cudaMemcpyDeviceToDevice
-                                                      : cudaMemcpyHostToDevice, st));
+    if (frames[f].is_device) {
+      PW_CUDA_TRY(cudaMemcpy2DAsync((uint8_t *)dimg.p + f * img, row, frames[f].data, rs, row, H,
+                                    cudaMemcpyDeviceToDevice, st));
+    } else {
+      uint8_t *hp = static_cast<uint8_t *>(gb.h_img.p) + f * img;
+      for (int y = 0; y < H; ++y)
+        std::memcpy(hp + y * row, static_cast<const uint8_t *>(frames[f].data) + y * rs,
+                    (size_t)row);
+    }
+  }
+  if (any_host) {
+    for (int f = 0; f < nframes; ++f)
+      if (!frames[f].is_device)
+        PW_CUDA_TRY(cudaMemcpyAsync((uint8_t *)dimg.p + f * img,
+                                    static_cast<uint8_t *>(gb.h_img.p) + f * img, (size_t)img,
+                                    cudaMemcpyHostToDevice, st));
   }
   launch_colour_in(dimg.p, img, row, nframes, nc, H, W, Hp, Wp, 0, 8, (float *)dframes.p, st);
   // motion of every temporal level and pair on the frames' integer luma
@@ -1094,7 +1123,9 @@ int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8
   const int mult = 1 << L.levels;
   const int Hp = (H + mult - 1) / mult * mult, Wp = (W + mult - 1) / mult * mult;
   const int64_t F = (int64_t)nc * Hp * Wp;
-  DevBuf dbands, dframes, dt0, dt1, dimg, dmv, dwarp;
+  GopBufs &gb = cache_of(c).gop;
+  DevBuf &dbands = gb.bands, &dframes = gb.frames, &dt0 = gb.t0, &dt1 = gb.t1, &dimg = gb.img,
+         &dmv = gb.mv, &dwarp = gb.warp;
   const int64_t row = (int64_t)W * nc, img = row * H;
   int s;
   if ((s = dbands.ensure((size_t)F * nframes * 4)) || (s = dframes.ensure((size_t)F * nframes * 4)) ||
@@ -1123,13 +1154,31 @@ int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8
   launch_colour_out((float *)dframes.p, nframes, nc, Hp, Wp, H, W, nc == 3 ? 1 : 0, 8, dimg.p, img,
                     row, st);
   bump(c);
+  // device frames directly; host frames through one copy into pinned staging
+  bool any_host = false;
   for (int f = 0; f < nframes; ++f) {
     const int64_t rs = frames[f].stride_bytes ? frames[f].stride_bytes : row;
-    PW_CUDA_TRY(cudaMemcpy2DAsync(frames[f].data, rs, (uint8_t *)dimg.p + f * img, row, row, H,
-                                  frames[f].is_device ? cudaMemcpyDeviceToDevice
-                                                      : cudaMemcpyDeviceToHost, st));
+    if (frames[f].is_device) {
+      PW_CUDA_TRY(cudaMemcpy2DAsync(frames[f].data, rs, (uint8_t *)dimg.p + f * img, row, row, H,
+                                    cudaMemcpyDeviceToDevice, st));
+    } else {
+      any_host = true;
+    }
   }
-  return finish(c);
+  if (any_host) {
+    if ((s = gb.h_img.ensure((size_t)img * nframes))) return s;
+    PW_CUDA_TRY(cudaMemcpyAsync(gb.h_img.p, dimg.p, (size_t)img * nframes, cudaMemcpyDeviceToHost,
+                                st));
+  }
+  if ((s = finish(c))) return s;
+  for (int f = 0; f < nframes; ++f) {
+    if (frames[f].is_device) continue;
+    const int64_t rs = frames[f].stride_bytes ? frames[f].stride_bytes : row;
+    const uint8_t *hp = static_cast<const uint8_t *>(gb.h_img.p) + f * img;
+    for (int y = 0; y < H; ++y)
+      std::memcpy(static_cast<uint8_t *>(frames[f].data) + y * rs, hp + y * row, (size_t)row);
+  }
+  return PW_OK;
 }
 
 int pw_temporal_lift(pw_ctx *c, const pw_model *mm, int nframes, int H, int W, int forward,
