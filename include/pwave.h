@@ -175,7 +175,9 @@ int pw_encode_batch(pw_ctx *ctx, const pw_model *m, int count, const pw_image *i
 /* Batched decode of count streams of identical size/channels/model into
  * out[0..count-1]. bs[i] are host pointers unless bs_on_device is set, in
  * which case they are device pointers (the streams then never visit the
- * host: headers are validated on the device). */
+ * host: headers are validated on the device). Page-locked host streams and
+ * host images (pinned or registered memory) are copied to and from the
+ * device directly; pageable ones go through the library's pinned staging. */
 int pw_decode_batch(pw_ctx *ctx, const pw_model *m, int count,
                     const uint8_t *const *bs, const size_t *n, int bs_on_device,
                     pw_image *out);

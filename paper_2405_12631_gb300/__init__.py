@@ -383,6 +383,22 @@ class Codec:
         n = (C.c_size_t * B)(*lens)
         check(pw_decode_batch(self.ctx, model.handle, B, p, n, 1, ims))
 
+    def decode_batch_host_ptrs(self, model: Model, ptrs, lens, out_ptr: int, shape,
+                               bitdepth: int = 8):
+        """Decode host-resident streams (host addresses and byte lengths)
+        into a contiguous host output [B, H, W, C] at out_ptr. Page-locked
+        buffers (e.g. pinned torch tensors) are copied to and from the device
+        directly; pageable ones go through the library's pinned staging."""
+        B = len(ptrs)
+        h, w = shape[:2]
+        ch = 1 if len(shape) == 2 else shape[2]
+        item = h * w * ch * (1 if bitdepth <= 8 else 2)
+        ims = (pw_image * B)(*[pw_image(w, h, ch, bitdepth, 0, 0, out_ptr + i * item, 0)
+                               for i in range(B)])
+        p = (C.c_void_p * B)(*ptrs)
+        n = (C.c_size_t * B)(*lens)
+        check(pw_decode_batch(self.ctx, model.handle, B, p, n, 0, ims))
+
     # ---- video GOPs -------------------------------------------------------
     def encode_gop(self, m_low: Model, m_high: Model, frames: np.ndarray, q: float = 8.0,
                    chunk: int = 16384) -> bytes:

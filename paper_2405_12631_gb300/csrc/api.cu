@@ -362,6 +362,17 @@ int stream_geometry(pw_ctx *ctx, const Model &m, const uint8_t *bs, size_t n, Ge
 }
 
 // Stage host streams in device memory; fills ptrs.
+// True when host memory at p is page-locked (registered or allocated
+// pinned): copies from or to it run asynchronously without staging.
+static bool pinned_host(const void *p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
 static int stage_streams(pw_ctx *ctx, Plan &pl, int B, const uint8_t *const *bs, const size_t *n,
                          int on_dev, std::vector<const uint8_t *> &ptrs) {
   ptrs.resize(B);
@@ -373,10 +384,20 @@ static int stage_streams(pw_ctx *ctx, Plan &pl, int B, const uint8_t *const *bs,
   std::vector<size_t> off(B);
   for (int b = 0; b < B; ++b) { off[b] = tot; tot += (n[b] + 255) / 256 * 256; }
   int s;
-  if ((s = pl.d_stage.ensure(tot)) || (s = pl.h_stage.ensure(tot))) return s;
-  uint8_t *hp = static_cast<uint8_t *>(pl.h_stage.p);
-  for (int b = 0; b < B; ++b) std::memcpy(hp + off[b], bs[b], n[b]);
-  PW_CUDA_TRY(cudaMemcpyAsync(pl.d_stage.p, hp, tot, cudaMemcpyHostToDevice, ctx->stream));
+  if ((s = pl.d_stage.ensure(tot))) return s;
+  bool pinned = true;
+  for (int b = 0; b < B && pinned; ++b) pinned = pinned_host(bs[b]);
+  if (pinned) {
+    // page-locked streams: copied to the device directly
+    for (int b = 0; b < B; ++b)
+      PW_CUDA_TRY(cudaMemcpyAsync(static_cast<uint8_t *>(pl.d_stage.p) + off[b], bs[b], n[b],
+                                  cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    if ((s = pl.h_stage.ensure(tot))) return s;
+    uint8_t *hp = static_cast<uint8_t *>(pl.h_stage.p);
+    for (int b = 0; b < B; ++b) std::memcpy(hp + off[b], bs[b], n[b]);
+    PW_CUDA_TRY(cudaMemcpyAsync(pl.d_stage.p, hp, tot, cudaMemcpyHostToDevice, ctx->stream));
+  }
   for (int b = 0; b < B; ++b) ptrs[b] = static_cast<uint8_t *>(pl.d_stage.p) + off[b];
   return PW_OK;
 }
@@ -535,27 +556,33 @@ int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const s
                       img, row, st);
   }
   bump(ctx);
-  // host outputs: one copy into pinned staging, then host memcpy (pageable
-  // destinations would make the DMA go through the driver's bounce buffer)
-  bool any_host = false;
-  for (int b = 0; b < B; ++b) any_host = any_host || !out[b].is_device;
+  // host outputs: page-locked ones are written by the copy engine directly;
+  // pageable ones get one copy into pinned staging, then a host memcpy
+  // (a DMA to pageable memory would go through the driver's bounce buffer)
+  bool any_staged = false;
   if (!direct) {
     for (int b = 0; b < B; ++b) {
-      if (!out[b].is_device) continue;
       const int64_t rs = out[b].stride_bytes ? out[b].stride_bytes : row;
-      PW_CUDA_TRY(cudaMemcpy2DAsync(out[b].data, rs, (uint8_t *)dst + b * img, row, row, g.H,
-                                    cudaMemcpyDeviceToDevice, st));
+      if (out[b].is_device) {
+        PW_CUDA_TRY(cudaMemcpy2DAsync(out[b].data, rs, (uint8_t *)dst + b * img, row, row, g.H,
+                                      cudaMemcpyDeviceToDevice, st));
+      } else if (pinned_host(out[b].data)) {
+        PW_CUDA_TRY(cudaMemcpy2DAsync(out[b].data, rs, (uint8_t *)dst + b * img, row, row, g.H,
+                                      cudaMemcpyDeviceToHost, st));
+      } else {
+        any_staged = true;
+      }
     }
-    if (any_host) {
+    if (any_staged) {
       if ((s = pl->h_out.ensure((size_t)img * B))) return s;
       PW_CUDA_TRY(cudaMemcpyAsync(pl->h_out.p, dst, (size_t)img * B, cudaMemcpyDeviceToHost, st));
     }
   }
   if ((s = check_status(ctx, &pl->ws))) return s;
-  if (!direct && any_host) {
+  if (!direct && any_staged) {
     const uint8_t *hp = static_cast<const uint8_t *>(pl->h_out.p);
     for (int b = 0; b < B; ++b) {
-      if (out[b].is_device) continue;
+      if (out[b].is_device || pinned_host(out[b].data)) continue;
       const int64_t rs = out[b].stride_bytes ? out[b].stride_bytes : row;
       if (rs == row) {
         std::memcpy(out[b].data, hp + b * img, (size_t)img);
