@@ -83,3 +83,28 @@ def test_replayed_single_image_device_output_and_corrupt_stream(pw):
     assert np.array_equal(codec.decode_image(model, bs), ref)
     model.close()
     codec.close()
+
+
+def test_page_locked_host_buffers_decode_like_pageable(pw):
+    """Streams and images in page-locked host memory take the direct copy
+    path; the results equal the pageable path's."""
+    torch = pytest.importorskip("torch")
+    codec = pw.Codec(0, "fp8")
+    model = codec.load_model(_blob(C=64))
+    imgs = [S.rgb_natural(64, 96, seed=s) for s in (5, 6, 7)]
+    streams = [codec.encode_image(model, im, q=8.0) for im in imgs]
+    ref = codec.decode_batch(model, streams, (64, 96, 3), np.uint8)
+    offs = np.cumsum([0] + [(len(b) + 255) // 256 * 256 for b in streams])
+    host = np.zeros(int(offs[-1]), dtype=np.uint8)
+    for i, b in enumerate(streams):
+        host[offs[i]:offs[i] + len(b)] = np.frombuffer(b, dtype=np.uint8)
+    h_in = torch.from_numpy(host).pin_memory()
+    h_out = torch.zeros((3, 64, 96, 3), dtype=torch.uint8).pin_memory()
+    ptrs = [h_in.data_ptr() + int(offs[i]) for i in range(3)]
+    for _ in range(3):                               # direct, then graph replays
+        h_out.zero_()
+        codec.decode_batch_host_ptrs(model, ptrs, [len(b) for b in streams], h_out.data_ptr(),
+                                     (64, 96, 3))
+        assert np.array_equal(h_out.numpy(), ref)
+    model.close()
+    codec.close()
