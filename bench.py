@@ -659,7 +659,7 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
     """Lossless at scale: n_img RGB 3840x2160 uint16 images with 12-bit values
     (Gaussian blobs + N(0, 15^2), seeds 5, 6, ...), RCT and integer lifting
     with 5 levels (padded to 3840x2176), C = 64 context model with FP8
-    convolutions. Decoded in sub-batches sized so that the decode workspace
+    convolutions. Decoded in equal sub-batches sized so that the decode workspace
     takes at most half the free device memory; device streams -> device
     images, CUDA events around every sub-batch; every decoded image is
     compared with its input (bit_exact)."""
@@ -676,6 +676,9 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
     per = c.decode_footprint(m, first, 1)
     free = torch.cuda.mem_get_info(dev)[0]
     sub = int(max(1, min(n_img, (free // 2) // max(per, 1), 8)))
+    # equal sub-batches (the largest divisor of the image count that fits):
+    # one decode plan for all of them, and no small remainder call
+    sub = max(d for d in range(1, sub + 1) if n_img % d == 0)
     streams = [first]
     for i in range(1, n_img, sub):
         streams += c.encode_batch(m, imgs[i:i + sub], lossless=True, bitdepth=12)
