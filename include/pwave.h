@@ -200,8 +200,11 @@ int pw_decode_batch(pw_ctx *ctx, const pw_model *m, int count,
 int pw_encode_gop(pw_ctx *ctx, const pw_model *m_low, const pw_model *m_high, int nframes,
                   const pw_image *frames, const pw_codec_opts *opts, uint8_t **bs, size_t *n);
 /* Inverse of pw_encode_gop into frames[0..nframes-1]; also decodes version-1
- * containers (no vectors: zero motion). Errors: PW_EINVAL (models / sizes do
- * not match the stream), PW_ECORRUPT. */
+ * containers (no vectors: zero motion). The lowpass band is decoded by an
+ * auxiliary context of ctx (same device and class, its own non-blocking
+ * stream, created on first use and destroyed with ctx) from a second host
+ * thread while ctx decodes the highpass bands; the call returns after both.
+ * Errors: PW_EINVAL (models / sizes do not match the stream), PW_ECORRUPT. */
 int pw_decode_gop(pw_ctx *ctx, const pw_model *m_low, const pw_model *m_high, const uint8_t *bs,
                   size_t n, int nframes, pw_image *frames);
 /* Temporal lifting alone on nframes host planes of H x W floats ([frame]

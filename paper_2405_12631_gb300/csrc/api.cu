@@ -4,6 +4,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <thread>
 
 #include "codec.h"
 #include "ctx_tc.h"
@@ -867,6 +868,10 @@ int pw_ctx_create(int device, void *stream, int precision, pw_ctx **out) {
 void pw_ctx_destroy(pw_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  if (c->aux) {
+    pw_ctx_destroy(c->aux);
+    cudaStreamDestroy(c->aux_stream);
+  }
   delete reinterpret_cast<PlanCache *>(c->plan_cache);
   delete reinterpret_cast<Prof *>(c->prof);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -1108,6 +1113,28 @@ int pw_encode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, int nframes
   return PW_OK;
 }
 
+// The auxiliary context of GOP decodes (same device and precision class,
+// own non-blocking stream), or null when it cannot be made (the decode then
+// runs both band sets on the caller's context, one after the other).
+static pw_ctx *gop_aux(pw_ctx *c) {
+  if (c->aux) return c->aux;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  pw_ctx *a = nullptr;
+  if (pw_ctx_create(c->device, s, c->precision, &a) != PW_OK) {
+    cudaStreamDestroy(s);
+    return nullptr;
+  }
+  a->lane_shift = c->lane_shift;
+  a->graphs = c->graphs;
+  c->aux = a;
+  c->aux_stream = s;
+  return a;
+}
+
 int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8_t *bs, size_t n,
                   int nframes, pw_image *frames) {
   if (!c || !ml || !mh || !bs || !frames || n < sizeof(GopHeader)) return PW_EINVAL;
@@ -1165,13 +1192,40 @@ int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8
   if (mv_bytes) {
     PW_CUDA_TRY(cudaMemcpyAsync(dmv.p, mv_src, mv_bytes, cudaMemcpyHostToDevice, st));
   }
-  float *planes;
-  Geometry g;
-  if ((s = decode_to_planes(c, L, 1, bp.data(), bn.data(), &planes, &g))) return s;
-  if (g.H != H || g.W != W || g.nc != nc || g.colour != 3) { set_last_error("GOP band geometry"); return PW_ECORRUPT; }
-  PW_CUDA_TRY(cudaMemcpyAsync(dbands.p, planes, (size_t)F * 4, cudaMemcpyDeviceToDevice, st));
-  if ((s = decode_to_planes(c, Hm, nframes - 1, bp.data() + 1, bn.data() + 1, &planes, &g))) return s;
-  if (g.H != H || g.W != W || g.nc != nc || g.colour != 3) { set_last_error("GOP band geometry"); return PW_ECORRUPT; }
+  // the lowpass band (one image, model L) and the highpass bands (a batch,
+  // model H) are independent: the auxiliary context decodes the former on
+  // its own stream from a second host thread while this one decodes the
+  // latter, so that the single-image decode's latency-bound passes overlap
+  // the batch
+  pw_ctx *ax = gop_aux(c);
+  float *lplanes = nullptr, *planes = nullptr;
+  Geometry lg, g;
+  int ls = PW_OK;
+  std::string lerr;
+  if (ax) {
+    const uint64_t l0 = ax->launches;
+    std::thread th([&] {
+      cudaSetDevice(c->device);
+      ls = decode_to_planes(ax, L, 1, bp.data(), bn.data(), &lplanes, &lg);
+      if (ls) lerr = pw_last_error();
+    });
+    s = decode_to_planes(c, Hm, nframes - 1, bp.data() + 1, bn.data() + 1, &planes, &g);
+    th.join();
+    c->launches += ax->launches - l0;
+    if (ls) { set_last_error(lerr); return ls; }
+  } else {
+    if ((s = decode_to_planes(c, L, 1, bp.data(), bn.data(), &lplanes, &lg))) return s;
+    PW_CUDA_TRY(cudaMemcpyAsync(dbands.p, lplanes, (size_t)F * 4, cudaMemcpyDeviceToDevice, st));
+    lplanes = nullptr;
+    s = decode_to_planes(c, Hm, nframes - 1, bp.data() + 1, bn.data() + 1, &planes, &g);
+  }
+  if (s) return s;
+  if (g.H != H || g.W != W || g.nc != nc || g.colour != 3 ||
+      (lplanes && (lg.H != H || lg.W != W || lg.nc != nc || lg.colour != 3))) {
+    set_last_error("GOP band geometry"); return PW_ECORRUPT;
+  }
+  if (lplanes)  // the auxiliary decode has completed (it synchronised its stream)
+    PW_CUDA_TRY(cudaMemcpyAsync(dbands.p, lplanes, (size_t)F * 4, cudaMemcpyDeviceToDevice, st));
   PW_CUDA_TRY(cudaMemcpyAsync((float *)dbands.p + F, planes, (size_t)F * (nframes - 1) * 4,
                               cudaMemcpyDeviceToDevice, st));
   if ((s = temporal_planes(c, L, nframes, nc, Hp, Wp, (float *)dbands.p, (float *)dframes.p,
@@ -1495,6 +1549,7 @@ int pw_ctx_set_graphs(pw_ctx *c, int enable) {
   if (!c) return -PW_EINVAL;
   const int old = c->graphs;
   c->graphs = enable ? 1 : 0;
+  if (c->aux) c->aux->graphs = c->graphs;
   return old;
 }
 

@@ -233,6 +233,11 @@ struct pw_ctx {
   int graphs = 1;
   cudaStream_t cap_stream = nullptr;   // private stream the chains are captured on
   uint64_t graph_replays = 0;
+  // GOP decodes: a second context on its own non-blocking stream decodes the
+  // lowpass band while this one decodes the highpass bands (created on first
+  // use, destroyed with this context)
+  pw_ctx *aux = nullptr;
+  cudaStream_t aux_stream = nullptr;
 };
 
 struct pw_model {
