@@ -414,13 +414,19 @@ class Codec:
 
     def decode_gop(self, m_low: Model, m_high: Model, gs: bytes, nframes: int, shape) -> np.ndarray:
         out = np.zeros((nframes,) + tuple(shape), dtype=np.uint8)
+        self.decode_gop_into(m_low, m_high, gs, nframes, shape, out.ctypes.data)
+        return out
+
+    def decode_gop_into(self, m_low: Model, m_high: Model, gs: bytes, nframes: int, shape,
+                        out_ptr: int, on_device: bool = False):
+        """pw_decode_gop into a caller's contiguous [nframes, H, W, C] uint8
+        buffer (host, page-locked or not, or device with on_device)."""
         h, w = shape[:2]
         ch = 1 if len(shape) == 2 else shape[2]
-        item = out[0].nbytes
-        ims = (pw_image * nframes)(*[pw_image(w, h, ch, 8, 0, 0, out.ctypes.data + f * item, 0)
+        item = h * w * ch
+        ims = (pw_image * nframes)(*[pw_image(w, h, ch, 8, int(on_device), 0, out_ptr + f * item, 0)
                                      for f in range(nframes)])
         check(pw_decode_gop(self.ctx, m_low.handle, m_high.handle, gs, len(gs), nframes, ims))
-        return out
 
     def temporal_lift(self, model: Model, frames: np.ndarray, forward: bool = True) -> np.ndarray:
         frames = np.ascontiguousarray(frames, dtype=np.float32)

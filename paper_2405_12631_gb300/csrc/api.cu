@@ -1235,15 +1235,19 @@ int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8
   launch_colour_out((float *)dframes.p, nframes, nc, Hp, Wp, H, W, nc == 3 ? 1 : 0, 8, dimg.p, img,
                     row, st);
   bump(c);
-  // device frames directly; host frames through one copy into pinned staging
+  // device and page-locked host frames directly; pageable host frames
+  // through one copy into pinned staging
   bool any_host = false;
+  std::vector<char> staged(nframes, 0);
   for (int f = 0; f < nframes; ++f) {
     const int64_t rs = frames[f].stride_bytes ? frames[f].stride_bytes : row;
-    if (frames[f].is_device) {
+    if (frames[f].is_device || pinned_host(frames[f].data)) {
       PW_CUDA_TRY(cudaMemcpy2DAsync(frames[f].data, rs, (uint8_t *)dimg.p + f * img, row, row, H,
-                                    cudaMemcpyDeviceToDevice, st));
+                                    frames[f].is_device ? cudaMemcpyDeviceToDevice
+                                                        : cudaMemcpyDeviceToHost, st));
     } else {
       any_host = true;
+      staged[f] = 1;
     }
   }
   if (any_host) {
@@ -1253,7 +1257,7 @@ int pw_decode_gop(pw_ctx *c, const pw_model *ml, const pw_model *mh, const uint8
   }
   if ((s = finish(c))) return s;
   for (int f = 0; f < nframes; ++f) {
-    if (frames[f].is_device) continue;
+    if (!staged[f]) continue;
     const int64_t rs = frames[f].stride_bytes ? frames[f].stride_bytes : row;
     const uint8_t *hp = static_cast<const uint8_t *>(gb.h_img.p) + f * img;
     for (int y = 0; y < H; ++y)
