@@ -513,10 +513,15 @@ int temporal_planes(pw_ctx *ctx, Model &m, int nf, int nc, int Hp, int Wp, const
   while ((1 << T) < nf) ++T;
   if ((1 << T) != nf || nf < 2) { set_last_error("GOP size must be a power of two >= 2"); return PW_EINVAL; }
   if (mv && !twarp) { set_last_error("motion-compensated lifting needs scratch"); return PW_EINVAL; }
+  // the inverse (decoder) runs the CNNs' middle layers on the tensor cores in
+  // the BF16 / FP8 classes, as the spatial inverse lifting does; the
+  // encoder's forward transform stays FP32
+  const int tc = (!forward && tc_precision(ctx->precision)) ? 1 : 0;
   auto step = [&](const float *src, int64_t ssrc, const float *oth, int64_t soth, float *dst,
                   int64_t sdst, int P, int lin, int sign, const LiftNetDev &net) {
     LiftStepParams a{};
     a.P = P; a.H = Hp; a.W = Wp; a.dir = 0; a.lin = lin; a.sign = sign; a.round = 0; a.net = net;
+    a.tc = tc; a.status = ctx->status;
     a.src = acc(const_cast<float *>(src), ssrc, Wp);
     a.other = acc(const_cast<float *>(oth), soth, Wp);
     a.out = acc(dst, sdst, Wp);

@@ -113,3 +113,23 @@ def test_version1_zero_motion_gop_still_decodes(codec):
     assert np.max(np.abs(out.astype(int) - ref.astype(int))) <= 1
     ml.close()
     mh.close()
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_gop_in_tensor_core_classes_close_to_fp32(pw, prec):
+    """The tensor-core classes' GOP decode (their temporal inverse lifting
+    runs the CNNs' middle layers on the tensor cores) reconstructs within
+    0.05 dB of the FP32 class's PSNR on the same GOP."""
+    frames = S.video_gop(48, 64, 8, seed=21)
+    cfg = S.ModelConfig(levels=4, C=32, ll_mode=0)
+    bl, bh = (S.pack_blob(cfg, S.random_model(cfg, s)) for s in (31, 32))
+    ps = {}
+    for p in ("fp32", prec):
+        c = pw.Codec(0, p)
+        ml, mh = c.load_model(bl), c.load_model(bh)
+        gs = c.encode_gop(ml, mh, frames, q=8.0)
+        ps[p] = _psnr(c.decode_gop(ml, mh, gs, 8, frames.shape[1:]), frames)
+        ml.close()
+        mh.close()
+        c.close()
+    assert abs(ps[prec] - ps["fp32"]) < 0.05, ps
