@@ -74,6 +74,39 @@ __device__ __forceinline__ float act(float v) {
   return kExact ? tanh32_spec(v) : tanhf(v);
 }
 
+// Two FP32 values in one 64-bit register pair, and a packed FP32 FMA (two
+// fused multiply-adds, each rounded like fmaf).
+__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// Packed FP32 product and sum: two correctly rounded multiplies / adds.
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// Two accumulators of mac<kExact> at once (per element the same operations:
+// a fused multiply-add, or (kExact) a rounded product and a rounded sum).
+template <bool kExact>
+__device__ __forceinline__ uint64_t mac2(uint64_t acc, uint64_t w, uint64_t x) {
+  return kExact ? add2(acc, mul2(w, x)) : fma2(w, x, acc);
+}
+
 __device__ __forceinline__ float acc_get(const PlaneAcc &a, int p, int y, int x) {
   return a.p[(int64_t)p * a.ps + (int64_t)y * a.rs + (int64_t)x * a.cs];
 }
@@ -167,15 +200,22 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
       const int ly = e / L1, lx = e % L1;
       const int yy = y0 + ly - 2, xx = x0 + lx - 2;
       const bool inside = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-      float acc[LF], w[LF];
-      ld16(S.b1, acc);
+      // output channels in pairs (packed FP32): each accumulator sees the
+      // same sequence of operations as one mac<kExact> chain
+      uint64_t accp[LF / 2];
+#pragma unroll
+      for (int c = 0; c < LF / 2; ++c) accp[c] = f2pack(S.b1[2 * c], S.b1[2 * c + 1]);
 #pragma unroll
       for (int tap = 0; tap < 9; ++tap) {
         const float iv = S.in[(ly + tap / 3) * LI + lx + tap % 3];
-        ld16(S.w1t + tap * LF, w);
+        const uint64_t xv = f2pack(iv, iv);
+        const uint64_t *wp = reinterpret_cast<const uint64_t *>(S.w1t + tap * LF);
 #pragma unroll
-        for (int c = 0; c < LF; ++c) acc[c] = mac<kExact>(acc[c], w[c], iv);
+        for (int c = 0; c < LF / 2; ++c) accp[c] = mac2<kExact>(accp[c], wp[c], xv);
       }
+      float acc[LF];
+#pragma unroll
+      for (int c = 0; c < LF / 2; ++c) f2unpack(accp[c], acc[2 * c], acc[2 * c + 1]);
       float4 *dst = reinterpret_cast<float4 *>(S.a1 + e * LF);
 #pragma unroll
       for (int i = 0; i < 4; ++i)
@@ -190,23 +230,31 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
     if (t < kHalf) {
       const int e0 = t, e1 = t + kHalf;
       const int ly0 = e0 / L2, lx0 = e0 % L2, ly1 = e1 / L2, lx1 = e1 % L2;
-      float acc0[LF], acc1[LF];
-      ld16(S.b2, acc0);
-      ld16(S.b2, acc1);
+      // output channels in pairs (packed FP32), as in layer 1
+      uint64_t p0[LF / 2], p1[LF / 2];
+#pragma unroll
+      for (int c = 0; c < LF / 2; ++c) p0[c] = p1[c] = f2pack(S.b2[2 * c], S.b2[2 * c + 1]);
       for (int tap = 0; tap < 9; ++tap) {
         float in0v[LF], in1v[LF];
         ld16(S.a1 + ((ly0 + tap / 3) * L1 + lx0 + tap % 3) * LF, in0v);
         ld16(S.a1 + ((ly1 + tap / 3) * L1 + lx1 + tap % 3) * LF, in1v);
 #pragma unroll
         for (int ci = 0; ci < LF; ++ci) {
-          float w[LF];
-          ld16(S.w2t + (tap * LF + ci) * LF, w);
+          const uint64_t *wp = reinterpret_cast<const uint64_t *>(S.w2t + (tap * LF + ci) * LF);
+          const uint64_t x0 = f2pack(in0v[ci], in0v[ci]), x1 = f2pack(in1v[ci], in1v[ci]);
 #pragma unroll
-          for (int c = 0; c < LF; ++c) {
-            acc0[c] = mac<kExact>(acc0[c], w[c], in0v[ci]);
-            acc1[c] = mac<kExact>(acc1[c], w[c], in1v[ci]);
+          for (int c = 0; c < LF / 2; ++c) {
+            const uint64_t w = wp[c];
+            p0[c] = mac2<kExact>(p0[c], w, x0);
+            p1[c] = mac2<kExact>(p1[c], w, x1);
           }
         }
+      }
+      float acc0[LF], acc1[LF];
+#pragma unroll
+      for (int c = 0; c < LF / 2; ++c) {
+        f2unpack(p0[c], acc0[2 * c], acc0[2 * c + 1]);
+        f2unpack(p1[c], acc1[2 * c], acc1[2 * c + 1]);
       }
       const int yy0 = y0 + ly0 - 1, xx0 = x0 + lx0 - 1, yy1 = y0 + ly1 - 1, xx1 = x0 + lx1 - 1;
       const bool in0 = yy0 >= 0 && yy0 < a.H && xx0 >= 0 && xx0 < a.W;
@@ -263,22 +311,6 @@ struct LiftTcSmem {
   uint32_t tmem;
   float b3;
 };
-
-// Two FP32 values in one 64-bit register pair, and a packed FP32 FMA (two
-// fused multiply-adds, each rounded like fmaf).
-__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2unpack(uint64_t v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
 
 // Bounded wait of every thread for completion phase `parity` of the MMA
 // barrier (lane 0 polls, the rest follow); false on expiry.
