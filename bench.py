@@ -674,20 +674,27 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
     stream = torch.cuda.current_stream(dev)
     Hh, Ww = 2160, 3840
     cfg = S.ModelConfig(levels=5, C=64, F=16, ll_mode=0)
-    c = pw.Codec(local, "fp8", stream=stream_ptr)
-    m = c.load_model(S.pack_blob(cfg, S.random_model(cfg, 0)))
+    blob = S.pack_blob(cfg, S.random_model(cfg, 0))
     imgs = [S.lossless_blobs(Hh, Ww, seed=5 + i) for i in range(n_img)]
-    first = c.encode_image(m, imgs[0], lossless=True, bitdepth=12)
-    per = c.decode_footprint(m, first, 1)
+    # the encoder runs on a context of its own, closed before decoding so
+    # that its cached workspaces give their device memory back
+    ce = pw.Codec(local, "fp8", stream=stream_ptr)
+    me = ce.load_model(blob)
+    first = ce.encode_image(me, imgs[0], lossless=True, bitdepth=12)
+    per = ce.decode_footprint(me, first, 1)
     free = torch.cuda.mem_get_info(dev)[0]
     sub = int(max(1, min(n_img, (free // 2) // max(per, 1), 8)))
     # equal sub-batches (the largest divisor of the image count that fits):
     # one decode plan for all of them, and no small remainder call
     sub = max(d for d in range(1, sub + 1) if n_img % d == 0)
-    streams = [first]
-    for i in range(1, n_img, sub):
-        streams += c.encode_batch(m, imgs[i:i + sub], lossless=True, bitdepth=12)
-    streams = streams[:n_img]
+    streams = []
+    for i in range(0, n_img, sub):
+        streams += ce.encode_batch(me, imgs[i:i + sub], lossless=True, bitdepth=12)
+    me.close()
+    ce.close()
+    torch.cuda.synchronize()
+    c = pw.Codec(local, "fp8", stream=stream_ptr)
+    m = c.load_model(blob)
     lens = [len(b) for b in streams]
     offs = np.cumsum([0] + [(n + 255) // 256 * 256 for n in lens])
     host_all = np.zeros(int(offs[-1]), dtype=np.uint8)
