@@ -16,6 +16,7 @@
 // slope 1/128, hard sigmoid / tanh cell, log-scale head): see rq_ll below.
 #include "pw_internal.cuh"
 #include "ctx_kernels.cuh"
+#include "f32x2.cuh"
 
 namespace pw {
 
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
   // bank conflicts of the channel-fastest fill below
   constexpr int PS = HH * HW + ((HH * HW) % 32 == 0 ? 4 : 0);
   __shared__ float s_in[CI * PS];
-  __shared__ float s_w[KS * KS][CI][CO_T];
+  __shared__ __align__(16) float s_w[KS * KS][CI][CO_T];
   __shared__ float s_head[EPI == EPI_HEAD ? 8 : 1][TH * TW][2];
 
   const int t = threadIdx.x;
@@ -73,11 +74,15 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
   const int co0 = blockIdx.y * CO_T;
   const float *inp = a.in + (int64_t)p * a.H * a.W * a.in_cs + a.in_co;
 
-  float acc[4][NC];
+  // accumulators of output channels (2k, 2k + 1) of pixel i in one packed
+  // FP32 pair: each element takes the same fused multiply-adds in the same
+  // order as a scalar accumulator (bit-identical results, half the
+  // instructions)
+  uint64_t accp[4][NC / 2];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < NC; ++j) acc[i][j] = 0.f;
+    for (int k = 0; k < NC / 2; ++k) accp[i][k] = 0ull;
 
   for (int c0 = 0; c0 < a.cin; c0 += CI) {
     __syncthreads();
@@ -108,15 +113,24 @@ __global__ void __launch_bounds__(256) k_conv_simt(ConvParams a) {
         float xv[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) xv[i] = s_in[c * PS + (prow + dy) * HW + pcol + i + dx];
+        const uint64_t *wrow = reinterpret_cast<const uint64_t *>(&s_w[tap][c][cg * NC]);
+        uint64_t wp[NC / 2];
 #pragma unroll
-        for (int j = 0; j < NC; ++j) {
-          float wv = s_w[tap][c][cg * NC + j];
+        for (int k = 0; k < NC / 2; ++k) wp[k] = wrow[k];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) acc[i][j] = fmaf(xv[i], wv, acc[i][j]);
+        for (int i = 0; i < 4; ++i) {
+          const uint64_t xx = f2pack(xv[i], xv[i]);
+#pragma unroll
+          for (int k = 0; k < NC / 2; ++k) accp[i][k] = fma2(wp[k], xx, accp[i][k]);
         }
       }
     }
   }
+  float acc[4][NC];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int k = 0; k < NC / 2; ++k) f2unpack(accp[i][k], acc[i][2 * k], acc[i][2 * k + 1]);
 
   const int y = y0 + prow;
   if (EPI == EPI_STORE) {

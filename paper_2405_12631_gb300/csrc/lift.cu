@@ -29,6 +29,7 @@
 #include "pw_internal.cuh"
 #include "lift_kernels.cuh"
 #include "spec_math.cuh"
+#include "f32x2.cuh"
 #include "tc_ptx.cuh"
 
 namespace pw {
@@ -74,32 +75,6 @@ __device__ __forceinline__ float act(float v) {
   return kExact ? tanh32_spec(v) : tanhf(v);
 }
 
-// Two FP32 values in one 64-bit register pair, and a packed FP32 FMA (two
-// fused multiply-adds, each rounded like fmaf).
-__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2unpack(uint64_t v, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-// Packed FP32 product and sum: two correctly rounded multiplies / adds.
-__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 // Two accumulators of mac<kExact> at once (per element the same operations:
 // a fused multiply-add, or (kExact) a rounded product and a rounded sum).
 template <bool kExact>
