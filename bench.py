@@ -664,8 +664,9 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
     """Lossless at scale: n_img RGB 3840x2160 uint16 images with 12-bit values
     (Gaussian blobs + N(0, 15^2), seeds 5, 6, ...), RCT and integer lifting
     with 5 levels (padded to 3840x2176), C = 64 context model with FP8
-    convolutions. Decoded in equal sub-batches sized so that the decode workspace
-    takes at most half the free device memory; device streams -> device
+    convolutions. Decoded in equal sub-batches of at most 8 images, sized so
+    that the decode workspace leaves 24 GB of the device memory that is free
+    once the encoder's context is closed; device streams -> device
     images, CUDA events around every sub-batch; every decoded image is
     compared with its input (bit_exact)."""
     import torch
@@ -680,21 +681,21 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
     # that its cached workspaces give their device memory back
     ce = pw.Codec(local, "fp8", stream=stream_ptr)
     me = ce.load_model(blob)
-    first = ce.encode_image(me, imgs[0], lossless=True, bitdepth=12)
-    per = ce.decode_footprint(me, first, 1)
-    free = torch.cuda.mem_get_info(dev)[0]
-    sub = int(max(1, min(n_img, (free // 2) // max(per, 1), 8)))
-    # equal sub-batches (the largest divisor of the image count that fits):
-    # one decode plan for all of them, and no small remainder call
-    sub = max(d for d in range(1, sub + 1) if n_img % d == 0)
     streams = []
-    for i in range(0, n_img, sub):
-        streams += ce.encode_batch(me, imgs[i:i + sub], lossless=True, bitdepth=12)
+    for i in range(0, n_img, 4):
+        streams += ce.encode_batch(me, imgs[i:i + 4], lossless=True, bitdepth=12)
     me.close()
     ce.close()
     torch.cuda.synchronize()
+    torch.cuda.empty_cache()
     c = pw.Codec(local, "fp8", stream=stream_ptr)
     m = c.load_model(blob)
+    per = c.decode_footprint(m, streams[0], 1)
+    free = torch.cuda.mem_get_info(dev)[0]
+    sub = int(max(1, min(n_img, (free - (24 << 30)) // max(per, 1), 8)))
+    # equal sub-batches (the largest divisor of the image count that fits):
+    # one decode plan for all of them, and no small remainder call
+    sub = max(d for d in range(1, sub + 1) if n_img % d == 0)
     lens = [len(b) for b in streams]
     offs = np.cumsum([0] + [(n + 255) // 256 * 256 for n in lens])
     host_all = np.zeros(int(offs[-1]), dtype=np.uint8)
@@ -724,7 +725,7 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
                        "5 levels), C=64, FP8 context convolutions",
            "value": px / (best / 1e3) / 1e6, "unit": "MPix/s", "ms_total": best,
            "sub_batch": sub, "sub_batches": len(groups),
-           "decode_workspace_bytes_per_image": int(per),
+           "decode_workspace_bytes_per_image": int(per), "device_free_bytes_at_sizing": int(free),
            "bpp": 8.0 * sum(lens) / px, "bits_per_sample": 8.0 * sum(lens) / (3 * px),
            "bit_exact": exact,
            "timing": "CUDA events around each sub-batch decode, device streams -> device images"}
