@@ -360,6 +360,24 @@ class Codec:
         check(pw_decode_batch(self.ctx, model.handle, B, ptrs, lens, 0, ims))
         return out
 
+    def decode_ragged(self, model: Model, streams) -> list:
+        """Decode host streams of one format whose image sizes differ, in one
+        batch call (a ragged batch on a canvas of the largest size); returns
+        one array per stream, each exactly what decoding it alone gives."""
+        B = len(streams)
+        outs = []
+        for s in streams:
+            shape, dtype = stream_image_shape(s)
+            outs.append(np.zeros(shape, dtype=dtype))
+        ims = (pw_image * B)(*[pw_image(o.shape[1], o.shape[0], 1 if o.ndim == 2 else o.shape[2],
+                                        8 if o.dtype == np.uint8 else 16, 0, 0, o.ctypes.data, 0)
+                               for o in outs])
+        bufs = [C.c_char_p(s) for s in streams]
+        ptrs = (C.c_void_p * B)(*[C.cast(b, C.c_void_p) for b in bufs])
+        lens = (C.c_size_t * B)(*[len(s) for s in streams])
+        check(pw_decode_batch(self.ctx, model.handle, B, ptrs, lens, 0, ims))
+        return outs
+
     def decode_footprint(self, model: Model, bs: bytes, count: int = 1) -> int:
         """Estimated device workspace bytes to decode `count` streams like bs."""
         b = C.c_uint64()

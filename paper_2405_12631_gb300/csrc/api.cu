@@ -75,6 +75,10 @@ struct Plan {
   // decode
   PoolBuf d_chunks, d_tpl, d_deltas, d_ptrs, d_lens, d_stage, d_out;
   HostBuf h_stage, h_small, h_out;
+  // ragged batches: the streams' sizes, the planes' extents and the parse
+  // table (one pinned host image, one device copy)
+  PoolBuf d_rag;
+  HostBuf h_rag;
   std::vector<int64_t> gbase;   // decode descriptor block of each group
   // encode
   PoolBuf d_enc, d_ops, d_scratch, d_states, d_nwords, d_outoff, d_payload, d_img;
@@ -93,7 +97,7 @@ struct Plan {
   }
   void set_stream(cudaStream_t s) {
     stream = s;
-    for (PoolBuf *b : {&d_chunks, &d_tpl, &d_deltas, &d_ptrs, &d_lens, &d_stage, &d_out, &d_enc,
+    for (PoolBuf *b : {&d_chunks, &d_tpl, &d_deltas, &d_ptrs, &d_lens, &d_stage, &d_out, &d_rag, &d_enc,
                        &d_ops, &d_scratch, &d_states, &d_nwords, &d_outoff, &d_payload, &d_img})
       b->st = s;
   }
@@ -173,6 +177,12 @@ static int get_plan(pw_ctx *ctx, Model &m, const Geometry &g, int B, const char 
     if (nck)
       cudaMemcpyAsync(p->d_tpl.p, tpl.data(), nck * sizeof(TplDev), cudaMemcpyHostToDevice,
                       ctx->stream);
+    if ((s = p->d_deltas.ensure(2 * B * sizeof(float)))) return s;
+    if ((s = p->d_ptrs.ensure(B * sizeof(void *)))) return s;
+    if ((s = p->d_lens.ensure(B * sizeof(uint64_t)))) return s;
+    if ((s = p->h_small.ensure(B * 16 + 64))) return s;
+  } else if (!strcmp(kind, "rag")) {
+    // ragged batches build their descriptor tables per call
     if ((s = p->d_deltas.ensure(2 * B * sizeof(float)))) return s;
     if ((s = p->d_ptrs.ensure(B * sizeof(void *)))) return s;
     if ((s = p->d_lens.ensure(B * sizeof(uint64_t)))) return s;
@@ -511,6 +521,231 @@ static int run_decode_chain(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader 
   return s;
 }
 
+// --------------------------------------------------------------------------
+// Ragged batches: streams of one class (format, model, precision class)
+// whose image sizes differ, decoded together on a canvas of the largest
+// padded size. Every convolution, coder pass and lifting step of the chain
+// covers all streams in one launch; each plane keeps its own extent
+// (Workspace::ext): activations are zeroed outside it before a spatial
+// convolution reads them, the coder maps each chunk's symbols to its own
+// plane's step positions and the lifting steps take each plane's borders,
+// so every image decodes exactly as it does alone.
+struct RagTables {
+  std::vector<int64_t> gbase, gtot;   // descriptor block and chunk count of each group
+};
+
+static int decode_ragged_dev(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader &h0,
+                             const RagTables &rt, const uint32_t *d_wh, const RagTpl *d_tpl,
+                             int64_t ntpl, double stream_bytes) {
+  const Geometry &g = pl.g;
+  const int B = pl.B, P = B * g.nc;
+  cudaStream_t st = ctx->stream;
+  const uint64_t *hs = reinterpret_cast<const uint64_t *>(pl.h_small.p);
+  PW_CUDA_TRY(cudaMemcpyAsync(pl.d_ptrs.p, hs, B * 8, cudaMemcpyHostToDevice, st));
+  PW_CUDA_TRY(cudaMemcpyAsync(pl.d_lens.p, hs + B, B * 8, cudaMemcpyHostToDevice, st));
+  PW_CUDA_TRY(cudaMemsetAsync(ctx->status, 0, 4, st));
+  if (tc_precision(ctx->precision)) tc_error_reset(pl.ws, st);
+  // symbols outside every plane's extent stay 0 (the context convolutions'
+  // zero padding)
+  PW_CUDA_TRY(cudaMemsetAsync(pl.ws.Q, 0, (size_t)P * g.plane_elems * 4, st));
+  ParseExpect ex{};
+  ex.ncomp = g.nc; ex.levels = g.levels; ex.bitdepth = g.bitdepth; ex.colour = g.colour;
+  ex.flags = h0.flags; ex.chunk = g.chunk; ex.lane_byte = h0.lane_shift; ex.hash = m.hash;
+  DecChunk *dch = reinterpret_cast<DecChunk *>(pl.d_chunks.p);
+  const double total_syms = (double)P * g.plane_elems;
+  {
+    ProfScope ps(ctx, KC_PARSE, 0.0, (double)ntpl * (8 + sizeof(DecChunk) + sizeof(RagTpl)));
+    launch_parse_ragged(reinterpret_cast<const uint8_t *const *>(pl.d_ptrs.p),
+                        reinterpret_cast<const uint64_t *>(pl.d_lens.p), d_wh, ex, d_tpl, ntpl,
+                        dch, reinterpret_cast<float *>(pl.d_deltas.p), ctx->status, st);
+  }
+  {
+    ProfScope ps(ctx, KC_CDF, 0.0, (double)kNTables * (kNSym + 1) * 2);
+    launch_cdf_bank(ctx->bank, ctx->coarse, st);
+  }
+  bump(ctx, 2);
+  for (int sb = 0; sb < g.nsb; ++sb) {
+    const int lv = sb_level(g, sb);
+    if (sb == 0 && g.ll_ar) {
+      if (rt.gtot[0] != P) { set_last_error("bad LL chunk layout"); return PW_ECORRUPT; }
+      ProfScope ps(ctx, KC_RANS_DEC, 0.0, (double)P * g.sh[0] * g.sw[0] * 8.0);
+      int s = launch_ll_ar_decode(dch + rt.gbase[0], P, g.sh[0], g.sw[0], m.C, ar_weights(ctx, m),
+                                  ctx->bank, pl.ws.Q, ctx->status, st, pl.ws.ext, lv);
+      bump(ctx);
+      if (s) return s;
+      continue;
+    }
+    if (sb >= 1) {
+      int s = run_lstm(ctx, m, g, pl.ws, sb);
+      if (s) return s;
+    }
+    for (int k = 0; k < 4; ++k) {
+      int s = run_context_pass(ctx, m, g, pl.ws, sb, k, true);
+      if (s) return s;
+      const int gi = sb * 4 + k;
+      if (!rt.gtot[gi]) continue;
+      const int h = g.sh[sb], w = g.sw[sb];
+      const double nsym = (double)P * step_count(h, w, k);
+      ProfScope ps(ctx, KC_RANS_DEC, 0.0, nsym * 8.0 + stream_bytes * nsym / total_syms);
+      launch_rans_decode(dch + rt.gbase[gi], (int)rt.gtot[gi], ctx->bank, ctx->coarse,
+                         pl.ws.idx + (int64_t)P * g.ioff[gi], step_count(h, w, k),
+                         pl.ws.Q + (int64_t)P * g.soff[sb], (int64_t)h * w, h, w, k,
+                         ctx->status, st, false, pl.ws.ext, lv);
+      bump(ctx);
+    }
+  }
+  return PW_OK;
+}
+
+static int decode_ragged(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,
+                         const std::vector<StreamHeader> &hd, pw_image *out) {
+  const StreamHeader &h0 = hd[0];
+  std::vector<Geometry> gs(B);
+  int Hc = 0, Wc = 0, s;
+  for (int b = 0; b < B; ++b) {
+    const StreamHeader &h = hd[b];
+    if (h.flags != h0.flags || h.ncomp != h0.ncomp || h.levels != h0.levels ||
+        h.bitdepth != h0.bitdepth || h.colour != h0.colour ||
+        h.chunk_symbols != h0.chunk_symbols || h.lane_shift != h0.lane_shift) {
+      set_last_error("streams of a batch differ in format (only their sizes may differ)");
+      return PW_EINVAL;
+    }
+    if ((s = check_header_model(ctx, m, h)) || (s = build_geo(h, gs[b]))) return s;
+    Hc = std::max(Hc, gs[b].Hp);
+    Wc = std::max(Wc, gs[b].Wp);
+  }
+  const Geometry &g0 = gs[0];
+  Geometry gc;
+  gc.build(Hc, Wc, g0.nc, g0.levels, g0.colour, g0.bitdepth, g0.lossless, g0.ll_ar, g0.chunk,
+           g0.balanced, g0.lane_shift);
+  const int bps = gc.bitdepth > 8 ? 2 : 1, nc = gc.nc, P = B * nc, NG = gc.nsb * 4;
+  for (int b = 0; b < B; ++b)
+    if (out[b].width != gs[b].W || out[b].height != gs[b].H || out[b].channels != nc ||
+        !out[b].data || (out[b].bitdepth > 8 ? 2 : 1) != bps) {
+      set_last_error("output image does not match the stream (size, channels, bit depth)");
+      return PW_EINVAL;
+    }
+  Plan *pl;
+  if ((s = get_plan(ctx, m, gc, B, "rag", false, &pl))) return s;
+  // descriptor blocks: group gi holds, stream by stream and component by
+  // component, every chunk of that group
+  RagTables rt;
+  rt.gtot.assign(NG, 0);
+  rt.gbase.assign(NG, 0);
+  for (int b = 0; b < B; ++b)
+    for (int gi = 0; gi < NG; ++gi) rt.gtot[gi] += (int64_t)nc * gs[b].group_count[gi];
+  int64_t total = 0;
+  for (int gi = 0; gi < NG; ++gi) { rt.gbase[gi] = total; total += rt.gtot[gi]; }
+  int64_t ntpl = 0;
+  for (int b = 0; b < B; ++b) ntpl += (int64_t)nc * gs[b].chunks.size();
+  // pinned image of the tables: [wh: 2B u32][ext: P int2][tpl]
+  const size_t o_ext = ((size_t)B * 8 + 15) / 16 * 16;
+  const size_t o_tpl = (o_ext + (size_t)P * sizeof(int2) + 15) / 16 * 16;
+  const size_t nbytes = o_tpl + (size_t)std::max<int64_t>(ntpl, 1) * sizeof(RagTpl);
+  if ((s = pl->h_rag.ensure(nbytes)) || (s = pl->d_rag.ensure(nbytes)) ||
+      (s = pl->d_chunks.ensure(std::max<int64_t>(total, 1) * sizeof(DecChunk))))
+    return s;
+  uint8_t *hb = static_cast<uint8_t *>(pl->h_rag.p);
+  uint32_t *wh = reinterpret_cast<uint32_t *>(hb);
+  int2 *ext = reinterpret_cast<int2 *>(hb + o_ext);
+  RagTpl *tpl = reinterpret_cast<RagTpl *>(hb + o_tpl);
+  std::vector<int64_t> run(rt.gbase);   // next free descriptor of each group
+  int64_t e = 0;
+  for (int b = 0; b < B; ++b) {
+    const Geometry &g = gs[b];
+    wh[2 * b] = (uint32_t)g.W;
+    wh[2 * b + 1] = (uint32_t)g.H;
+    const int nck = (int)g.chunks.size();
+    for (int c = 0; c < nc; ++c) ext[b * nc + c] = make_int2(g.Hp, g.Wp);
+    for (int comp = 0; comp < nc; ++comp)
+      for (int c = 0; c < nck; ++c) {
+        const ChunkTpl &t = g.chunks[c];
+        const int gi = t.sb * 4 + (t.step < 0 ? 0 : t.step);
+        RagTpl &r = tpl[e++];
+        r.out = run[gi] + (int64_t)comp * g.group_count[gi] + (c - g.group_first[gi]);
+        r.first = t.first;
+        r.count = t.count;
+        r.lanes = t.lanes;
+        r.comp = (uint16_t)comp;
+        r.b = (uint32_t)b;
+        r.gc = (uint32_t)(comp * nck + c);
+        r.nch = (uint32_t)(nck * nc);
+      }
+    for (int gi = 0; gi < NG; ++gi) run[gi] += (int64_t)nc * g.group_count[gi];
+  }
+  cudaStream_t st = ctx->stream;
+  PW_CUDA_TRY(cudaMemcpyAsync(pl->d_rag.p, hb, nbytes, cudaMemcpyHostToDevice, st));
+  uint8_t *db = static_cast<uint8_t *>(pl->d_rag.p);
+  pl->ws.ext = reinterpret_cast<const int2 *>(db + o_ext);
+  std::vector<const uint8_t *> ptrs;
+  if ((s = stage_streams(ctx, *pl, B, bs, n, 0, ptrs))) return s;
+  fill_stream_table(*pl, ptrs.data(), n);
+  double stream_bytes = 0;
+  for (int b = 0; b < B; ++b) stream_bytes += (double)n[b];
+  if ((s = decode_ragged_dev(ctx, m, *pl, h0, rt, reinterpret_cast<const uint32_t *>(db),
+                             reinterpret_cast<const RagTpl *>(db + o_tpl), ntpl, stream_bytes)))
+    return s;
+  {
+    ProfScope ps(ctx, KC_QUANT, 0.0, (double)P * gc.plane_elems * 8.0);
+    launch_dequant_all(pl->ws.Q, pl->ws.Yf, (int64_t)P * gc.plane_elems, make_sbtable(gc, P), nc,
+                       reinterpret_cast<float *>(pl->d_deltas.p), st);
+  }
+  bump(ctx);
+  if ((s = lift_inverse_planes(ctx, m, gc, pl->ws, pl->ws.planes))) return s;
+  const float *recon = pl->ws.planes;
+  if (m.has_post && !gc.lossless) {
+    if ((s = post_process_planes(ctx, m, gc, P, pl->ws.planes, pl->ws.Yf, pl->ws.ext))) return s;
+    recon = pl->ws.Yf;
+  }
+  // colour conversion per stream: device outputs directly, host outputs
+  // through a packed device image
+  std::vector<int64_t> off(B + 1, 0);
+  for (int b = 0; b < B; ++b) off[b + 1] = off[b] + (int64_t)gs[b].W * nc * bps * gs[b].H;
+  bool any_host = false;
+  for (int b = 0; b < B; ++b) any_host = any_host || !out[b].is_device;
+  if (any_host && (s = pl->d_out.ensure((size_t)off[B]))) return s;
+  const int64_t cplane = (int64_t)gc.Hp * gc.Wp;
+  for (int b = 0; b < B; ++b) {
+    const Geometry &g = gs[b];
+    const int64_t row = (int64_t)g.W * nc * bps;
+    const int64_t rs = out[b].is_device ? (out[b].stride_bytes ? out[b].stride_bytes : row) : row;
+    void *dst = out[b].is_device ? out[b].data : static_cast<uint8_t *>(pl->d_out.p) + off[b];
+    ProfScope ps(ctx, KC_COLOUR, 0.0, (double)nc * g.H * g.W * 4.0 + (double)row * g.H);
+    launch_colour_out(recon + (int64_t)b * nc * cplane, 1, nc, gc.Hp, gc.Wp, g.H, g.W, gc.colour,
+                      gc.bitdepth, dst, row * g.H, rs, st);
+    bump(ctx);
+  }
+  bool any_staged = false;
+  for (int b = 0; b < B; ++b) {
+    if (out[b].is_device) continue;
+    const int64_t row = (int64_t)gs[b].W * nc * bps;
+    const int64_t rs = out[b].stride_bytes ? out[b].stride_bytes : row;
+    if (pinned_host(out[b].data)) {
+      PW_CUDA_TRY(cudaMemcpy2DAsync(out[b].data, rs, static_cast<uint8_t *>(pl->d_out.p) + off[b],
+                                    row, row, gs[b].H, cudaMemcpyDeviceToHost, st));
+    } else {
+      any_staged = true;
+    }
+  }
+  if (any_staged) {
+    if ((s = pl->h_out.ensure((size_t)off[B]))) return s;
+    PW_CUDA_TRY(cudaMemcpyAsync(pl->h_out.p, pl->d_out.p, (size_t)off[B], cudaMemcpyDeviceToHost,
+                                st));
+  }
+  if ((s = check_status(ctx, &pl->ws))) return s;
+  if (any_staged) {
+    const uint8_t *hp = static_cast<const uint8_t *>(pl->h_out.p);
+    for (int b = 0; b < B; ++b) {
+      if (out[b].is_device || pinned_host(out[b].data)) continue;
+      const int64_t row = (int64_t)gs[b].W * nc * bps;
+      const int64_t rs = out[b].stride_bytes ? out[b].stride_bytes : row;
+      for (int y = 0; y < gs[b].H; ++y)
+        std::memcpy((uint8_t *)out[b].data + y * rs, hp + off[b] + y * row, (size_t)row);
+    }
+  }
+  return PW_OK;
+}
+
 int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,
                  int on_dev, pw_image *out) {
   if (B < 1 || !bs || !n || !out) { set_last_error("bad arguments"); return PW_EINVAL; }
@@ -518,6 +753,35 @@ int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const s
   int s = read_header(bs[0], n[0], on_dev, h0);
   if (s) return s;
   if ((s = check_header_model(ctx, m, h0))) return s;
+  if (!on_dev && B > 1) {
+    // host streams of different sizes: one ragged batch (the mixture model:
+    // one batch per size)
+    std::vector<StreamHeader> hd(B);
+    hd[0] = h0;
+    bool ragged = false;
+    for (int b = 1; b < B; ++b) {
+      if ((s = read_header(bs[b], n[b], 0, hd[b]))) return s;
+      ragged = ragged || hd[b].width != h0.width || hd[b].height != h0.height;
+    }
+    if (ragged && !m.mix) return decode_ragged(ctx, m, B, bs, n, hd, out);
+    if (ragged) {
+      std::vector<char> done(B, 0);
+      for (int b = 0; b < B; ++b) {
+        if (done[b]) continue;
+        std::vector<const uint8_t *> sp;
+        std::vector<size_t> sn;
+        std::vector<pw_image> so;
+        for (int c = b; c < B; ++c)
+          if (!done[c] && hd[c].width == hd[b].width && hd[c].height == hd[b].height) {
+            sp.push_back(bs[c]); sn.push_back(n[c]); so.push_back(out[c]);
+            done[c] = 1;
+          }
+        if ((s = decode_batch(ctx, m, (int)sp.size(), sp.data(), sn.data(), 0, so.data())))
+          return s;
+      }
+      return PW_OK;
+    }
+  }
   Geometry g;
   if ((s = build_geo(h0, g))) return s;
   const int bps = g.bitdepth > 8 ? 2 : 1;

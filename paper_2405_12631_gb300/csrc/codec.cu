@@ -227,6 +227,10 @@ int run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb) {
     launch_lstm_in(sprev, ws.X2, 2 * C, C, in ? in->we : m.lstm_we, in ? in->be : m.lstm_be,
                    ws.X, P, h, w, C, up, first, ctx->stream, in ? in->n_e : kRqFloat);
   }
+  if (ws.ext) {  // the gates conv reads X over 3 x 3 neighbourhoods
+    launch_zero_outside(ws.X, ZL_PIXEL, P, h, w, 2 * C / 4, ws.ext, sb_level(g, sb), ctx->stream);
+    bump(ctx);
+  }
   ConvParams a{};
   a.in = ws.X; a.in_cs = 2 * C; a.in_co = 0; a.cin = 2 * C;
   a.w = in ? in->wg : m.lstm_wg; a.b = in ? in->bg : m.lstm_bg; a.cout_total = 4 * C;
@@ -292,6 +296,13 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
     ProfScope ps(ctx, ks == 3 ? (epi == EPI_HEAD ? KC_HEAD3 : KC_CONV3) : KC_CONV1, fl, by);
     launch_conv_simt(ks, cp, epi, st);
   };
+  // ragged batches: zero a C-channel buffer outside the planes' extents
+  // before a spatial convolution reads it
+  auto mask = [&](float *buf) {
+    if (!ws.ext) return;
+    launch_zero_outside(buf, ZL_PIXEL, P, h, w, C / 4, ws.ext, sb_level(g, sb), st);
+    bump(ctx);
+  };
   ConvParams a{};
   a.P = P; a.H = h; a.W = w;
   auto base = [&]() {
@@ -311,6 +322,7 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
     a.out = ws.U; a.out_cs = C; a.act = 1;
     a.iq = iq; a.rq = iq ? in->n_w1 : 0;
     conv(1, a, EPI_STORE);
+    mask(ws.U);
     {
       ProfScope ps(ctx, KC_SMALL_CTX, 2.0 * pix * 9 * C, pix * 8.0 * C);
       launch_dw3x3(ws.U, n.wdw, n.bdw, ws.V, P, h, w, C, st, iq ? in->n_dw : kRqFloat);
@@ -352,11 +364,13 @@ int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, in
     a.out = ws.Z; a.out_cs = C;
     a.iq = iq; a.rq = iq ? in->n_wz : 0;
     conv(1, a, EPI_STORE);
+    mask(ws.Z);
     a = base();  // u = lrelu(conv3x3 z)
     a.in = ws.Z; a.in_cs = C; a.cin = C; a.w = n.c1w; a.b = n.c1b; a.cout_total = C;
     a.out = ws.U; a.out_cs = C; a.act = 1;
     a.iq = iq; a.rq = iq ? in->n_c1 : 0;
     conv(3, a, EPI_STORE);
+    mask(ws.U);
     a = base();  // z' = z + conv3x3 u; head
     a.in = ws.U; a.in_cs = C; a.cin = C; a.w = n.c2w; a.b = n.c2b; a.cout_total = C;
     a.res = ws.Z; a.res_cs = C;
@@ -391,9 +405,10 @@ static void lift_step(pw_ctx *ctx, const LiftStepParams &a) {
 }
 
 int post_process_planes(pw_ctx *ctx, Model &m, const Geometry &g, int P, const float *src,
-                        float *dst) {
+                        float *dst, const int2 *ext) {
   LiftStepParams a{};
   a.P = P; a.H = g.Hp; a.W = g.Wp; a.dir = 0; a.lin = LIN_ZERO; a.sign = +1; a.round = 0;
+  a.ext = ext; a.esh = 0; a.ehmul = 1;
   a.net = m.post; a.status = ctx->status;
   a.tc = tc_precision(ctx->precision) ? 1 : 0;
   const int64_t hw = (int64_t)g.Hp * g.Wp;
@@ -425,6 +440,7 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
     auto colinv = [&](float *Lb, float *Hb, float *out) {
       LiftStepParams a{};
       a.P = P; a.H = h; a.W = w; a.dir = 1; a.tc = tc; a.status = ctx->status;
+      a.ext = ws.ext; a.esh = lv; a.ehmul = 1;
       a.src = acc(Hb, hw, w); a.other = acc(Lb, hw, w); a.out = acc(E, hw, w);
       a.copy = acc(nullptr, 0, 0); a.net = m.lift[1][1]; a.lin = LIN_U53; a.sign = -1;
       a.round = rU;
@@ -438,6 +454,7 @@ int lift_inverse_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
     colinv(HL, HH, Hi);
     LiftStepParams a{};
     a.P = P; a.H = 2 * h; a.W = w; a.dir = 0; a.tc = tc; a.status = ctx->status;
+    a.ext = ws.ext; a.esh = lv; a.ehmul = 2;
     a.src = acc(Hi, 2 * hw, w); a.other = acc(Lo, 2 * hw, w); a.out = acc(E, 2 * hw, w);
     a.copy = acc(nullptr, 0, 0); a.net = m.lift[0][1]; a.lin = LIN_U53; a.sign = -1;
     a.round = rU;

@@ -166,6 +166,11 @@ struct Workspace {
   float *mpar = nullptr;
   void *tc = nullptr;          // BF16 / FP8 activations (tensor-core path)
   int lstm_cur = 0;            // which Cst holds the current cell state
+  // ragged batches: the planes' own padded sizes (Hp, Wp) on the device, one
+  // per plane, when they differ from the workspace's geometry (the canvas);
+  // the passes then zero activations outside every plane's extent before a
+  // spatial convolution reads them. Not owned; null for plain batches.
+  const int2 *ext = nullptr;
   // prec: the context's pw_precision (tensor-core buffers unless FP32)
   // mix: buffers of the logistic-mixture model
   int alloc(const Geometry &g, int P, int C, bool params, int prec, cudaStream_t st,
@@ -177,6 +182,12 @@ struct Workspace {
   ~Workspace() { release(); }
 };
 
+// Decomposition level of subband sb (coding order: LL_L, then HL/LH/HH of
+// levels L .. 1).
+inline int sb_level(const Geometry &g, int sb) {
+  return sb == 0 ? g.levels : g.levels - (sb - 1) / 3;
+}
+
 // Host entry points implemented in codec.cu (all on ctx's stream).
 int run_context_pass(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
                      int step, bool decoding);
@@ -187,8 +198,9 @@ int lift_forward_planes(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws,
                         const float *src_planes);
 // Post-processing of the reconstructed component planes ([P][Hp][Wp]):
 // dst = src + CNN_post(src) (dst != src).
+// ext: ragged batches' per-plane padded sizes (see Workspace::ext) or null.
 int post_process_planes(pw_ctx *ctx, Model &m, const Geometry &g, int P, const float *src,
-                        float *dst);
+                        float *dst, const int2 *ext = nullptr);
 // Temporal lifting of a GOP (Section 3.3). mv: device block motion vectors
 // of every level and pair (the order of the motion search: level 1 pairs
 // first), or null for zero motion; twarp: (nf / 2) frames of scratch for the

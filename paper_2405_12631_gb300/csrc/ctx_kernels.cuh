@@ -60,6 +60,17 @@ struct MixHeadParams {
 void launch_mix_head(const MixHeadParams &a, cudaStream_t st);
 // Stage entry: rows of n keys given as int32 (q0 q1 q2 j0 j1 j2 g0 g1 g2).
 void launch_mix_tables(const int32_t *key9, int64_t n, uint16_t *rows, cudaStream_t st);
+// Ragged batches (planes of different sizes decoded on one canvas of
+// P x H x W): zero every 16-byte unit of an activation buffer that lies
+// outside its plane's own extent (ext[p] >> esh, the padded full-resolution
+// sizes shifted to the subband level), so that a convolution over the
+// canvas sees the same zero padding as one over the plane alone. Layouts
+// of the NG units per position: group-major [P][NG][H][W], pixel-major
+// [P][H][W][NG], or phase-split pixel-major [P][H][4][W4 / 4][NG]
+// (x = 4 j + phase, W4 = W rounded up to a multiple of 4).
+enum { ZL_GROUP = 0, ZL_PIXEL = 1, ZL_PHASE = 2 };
+void launch_zero_outside(void *buf, int layout, int P, int H, int W, int NG, const int2 *ext,
+                         int esh, cudaStream_t st);
 // Set when a launcher found no kernel for its arguments (checked and cleared
 // by the host drivers).
 bool &launch_failed();
@@ -94,7 +105,8 @@ void launch_cdf_bank(uint16_t *bank, uint16_t *coarse, cudaStream_t st);
 void launch_rans_decode(const DecChunk *chunks, int nchunks, const uint16_t *bank,
                         const uint16_t *coarse, const uint32_t *idx, int64_t idx_stride,
                         int32_t *out, int64_t out_stride, int h, int w, int step,
-                        uint32_t *status, cudaStream_t st, bool mix = false);
+                        uint32_t *status, cudaStream_t st, bool mix = false,
+                        const int2 *ext = nullptr, int esh = 0);
 // cf (logistic mixture, else null): per symbol (cdf | frequency << 16) of its
 // coded symbol; idx then holds the centres (int32) and bank is unused.
 void launch_rans_count_ops(const EncChunk *chunks, int nchunks, const uint32_t *idx,

@@ -1866,6 +1866,10 @@ int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     ProfScope ps(ctx, KC_SMALL_CTX, 0.0, pix * (4.0 + 32.0 + (copy_h ? (f8 ? 2.0 : 4.0) * C : 0)));
     k_lstm_v<<<P * h, 256, 0, ctx->stream>>>(sprev, t.V16, P, h, w, up);
     ctx->launches += 1;
+    if (ws.ext) {  // ragged batch: the gates conv reads v over 3 x 3 neighbourhoods
+      launch_zero_outside(t.V16, ZL_GROUP, P, h, w, 2, ws.ext, sb_level(g, sb), ctx->stream);
+      ctx->launches += 1;
+    }
     if (copy_h) {
       if (f8)
         k_copy_up16<<<P * h, 256, 0, ctx->stream>>>(
@@ -1890,12 +1894,22 @@ int tc_run_lstm(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   // MMA work: the 16-channel v block and the C h channels, 9 taps, 4C outputs
   ProfScope ps(ctx, KC_LSTM_GATES, 2.0 * pix * 9 * (16 + C) * 4 * C,
                pix * (32.0 + (f8 ? 1.0 : 2.0) * C + 2.0 * C + 4.0 * C + (f8 ? C : 0)));
+  int s;
   if (f8) {
-    if (copy_h) return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X8, 2 * G16, G16, 0);
-    return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.L8[(sb - 1) & 1], G16, 0, 0);
+    if (copy_h) s = conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X8, 2 * G16, G16, 0);
+    else s = conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.L8[(sb - 1) & 1], G16, 0, 0);
+  } else {
+    if (copy_h) s = conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X, 2 * G, G, 0);
+    else s = conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, lprev, G, 0, 0);
   }
-  if (copy_h) return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, t.X, 2 * G, G, 0);
-  return conv_tc(ctx, gates, t.V16, 2, 0, P, h, w, a, t.err, lprev, G, 0, 0);
+  if (s == PW_OK && ws.ext) {
+    // ragged batch: h feeds the next gates conv over 3 x 3 neighbourhoods
+    launch_zero_outside(lout, ZL_GROUP, P, h, w, G, ws.ext, sb_level(g, sb), ctx->stream);
+    if (f8) launch_zero_outside(t.L8[sb & 1], ZL_GROUP, P, h, w, G16, ws.ext, sb_level(g, sb),
+                                ctx->stream);
+    ctx->launches += f8 ? 2 : 1;
+  }
+  return s;
 }
 
 int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb, int step,
@@ -1916,6 +1930,13 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     return conv_tc(ctx, cv, in, in_G, in_goff, P, h, w, a, t.err);
   };
   int s;
+  // ragged batch: zero a buffer outside the planes' extents before a
+  // spatial convolution reads it (NG 16-byte units per position)
+  auto mask = [&](void *buf, int layout, int NG) {
+    if (!ws.ext) return;
+    launch_zero_outside(buf, layout, P, h, w, NG, ws.ext, sb_level(g, sb), st);
+    ctx->launches += 1;
+  };
   if (ll && step == 0) {  // l = 0 for LL
     cudaMemsetAsync(l, 0, (size_t)P * h * w * C * 2, st);
     if (ctx->precision == PW_PREC_FP8) cudaMemsetAsync(t.L8[sb & 1], 0, (size_t)P * h * w * C, st);
@@ -1927,6 +1948,7 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
     TcConvArgs a{};
     a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G;
     if ((s = conv(c1, l, G, 0, a, 0))) return s;                   // u = lrelu(W1 Win l + .)
+    mask(t.U, ZL_GROUP, G);
     // Everything after the depthwise conv is per position and only the
     // step-1 positions' parameters are used: run it on those alone, in the
     // compact layout (hc row pairs x wc positions per pair).
@@ -1988,6 +2010,8 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
                  pix * (32.0 + 2.0 * zt.cin + (f8 ? C + C / 2 : 2.0 * zt.cout)));
     if ((s = conv_tc(ctx, zt, t.T, 2, 0, P, h, w, a, t.err, l, G, 0, 0))) return s;
   }
+  if (f8) mask(t.Z8, ZL_GROUP, G16);
+  else mask(t.Z, ZL_GROUP, G);
   // The head conv's outputs are used at this step's positions only (a
   // quarter of the plane): where the subband is large enough it runs on
   // those alone (TE_HEADC), reading u in the phase-split layout.
@@ -2001,6 +2025,7 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
       ProfScope ps(ctx, KC_CONV3, 2.0 * pix * 9 * C * C, pix * 2.0 * C);
       if ((s = conv_tc(ctx, c1, t.Z8, G16, 0, P, h, w, a, t.err))) return s;  // u = lrelu(3x3 z)
     }
+    mask(t.U8, ups ? ZL_PHASE : ZL_GROUP, G16);
     a = TcConvArgs{}; a.epi = hcm ? TE_HEADC : TE_HEAD; a.res = t.Zc; a.res_G = G;
     a.res_compact_n = (int)nk;
     a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
@@ -2010,6 +2035,7 @@ int tc_run_step(pw_ctx *ctx, Model &m, const Geometry &g, Workspace &ws, int sb,
   }
   a = TcConvArgs{}; a.epi = TE_STORE; a.act = 1; a.out = t.U; a.out_G = G; a.out_ps = ups;
   if ((s = conv(c1, t.Z, G, 0, a, 0))) return s;                  // u = lrelu(conv3x3 z)
+  mask(t.U, ups ? ZL_PHASE : ZL_GROUP, G);
   a = TcConvArgs{}; a.epi = hcm ? TE_HEADC : TE_HEAD; a.res = t.Z; a.res_G = G;
   a.wh = n.wh; a.bh = n.bh; a.step = step; a.idx = idx; a.idx_stride = nk;
   a.mu_out = mu; a.sg_out = sgp;

@@ -21,6 +21,17 @@ struct TplDev {
   uint32_t first, count, lanes;
 };
 
+// Ragged batches: one entry per (stream, component, chunk); streams of one
+// class (format, model) but their own sizes, so every entry says where its
+// descriptor goes and which chunk of which stream it is.
+struct RagTpl {
+  int64_t out;            // index of the decode descriptor
+  uint32_t first, count;
+  uint16_t lanes, comp;
+  uint32_t b;             // stream
+  uint32_t gc, nch;       // chunk index within the stream, chunks in the stream
+};
+
 struct SbTable {
   int nsb;
   int64_t base[20];  // element offset of subband i over all planes (+ end)
@@ -37,5 +48,10 @@ void launch_quant_all(const float *Yf, int32_t *Q, int64_t n, const SbTable &tb,
 void launch_parse_streams(const uint8_t *const *streams, const uint64_t *lens, int B,
                           const ParseExpect &ex, const TplDev *tpl, int nck, DecChunk *out,
                           float *deltas, uint32_t *status, cudaStream_t st);
+// wh: the streams' expected (width, height), 2 per stream
+void launch_parse_ragged(const uint8_t *const *streams, const uint64_t *lens,
+                         const uint32_t *wh, const ParseExpect &ex, const RagTpl *tpl,
+                         int64_t ntpl, DecChunk *out, float *deltas, uint32_t *status,
+                         cudaStream_t st);
 
 }  // namespace pw

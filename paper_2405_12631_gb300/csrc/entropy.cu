@@ -142,12 +142,17 @@ __device__ __forceinline__ int cdf_search_r(const uint16_t *__restrict__ row, co
 // the row's last 16), written just before by the mixture head; idx holds
 // the centres. The coarse entries of a lane's symbol are loaded two rounds
 // ahead, its fine row prefetched into L1 two rounds ahead.
-template <bool kMix>
+// kRag (ragged batches, Laplace, step >= 0): planes of different sizes on
+// one canvas of width w. A chunk's symbols are the step positions of its
+// own plane, whose subband width is ext[plane].y >> esh; their packed
+// indices sit at the canvas's step positions (the context model runs on the
+// canvas) and their values go to canvas rows of stride w.
+template <bool kMix, bool kRag>
 __global__ void __launch_bounds__(256) k_rans_decode(
     const DecChunk *__restrict__ chunks, int nchunks, const uint16_t *__restrict__ bank,
     const uint16_t *__restrict__ coarse, const uint32_t *__restrict__ idx, int64_t idx_stride,
     int32_t *__restrict__ out, int64_t out_stride, int h, int w, int step,
-    uint32_t *status) {
+    uint32_t *status, const int2 *__restrict__ ext, int esh) {
   extern __shared__ uint4 s_coarse4[];
   if constexpr (!kMix) {
     // the coarse level (64 KB) in one asynchronous bulk copy, whatever the
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(256) k_rans_decode(
       wb += 64;
     }
   };
-  const uint32_t *idxp = idx + (int64_t)ch.plane * idx_stride + ch.first;
+  const uint32_t *idxp = idx + (int64_t)ch.plane * idx_stride;
   int32_t *outp = out + (int64_t)ch.plane * out_stride;
   const int count = (int)ch.count;
   if (kMix && count == 0) {  // chunk layouts hold no empty chunks
@@ -222,23 +227,39 @@ __global__ void __launch_bounds__(256) k_rans_decode(
   const int niter = (count + nl - 1) / nl;
   // output position of symbol q = first + p (step layout): row pair y2,
   // index r within the pair, advanced by nl per iteration
-  int ae = 0, ao = 0, ne = 1, pair = 1, y2 = 0, rr = 0;
+  int ae = 0, ao = 0, ne = 1, pair = 1, y2 = 0, rr = 0, neC = 0, pairC = 0;
   if (step >= 0) {
     ae = step_phase(step, 0); ao = step_phase(step, 1);
-    ne = row_count(w, ae);
-    pair = ne + row_count(w, ao);
-    if (pair == 0) {  // a step without positions has no chunks
+    const int wq = kRag ? (ext[ch.plane].y >> esh) : w;
+    ne = row_count(wq, ae);
+    pair = ne + row_count(wq, ao);
+    if (kRag) {
+      neC = row_count(w, ae);
+      pairC = neC + row_count(w, ao);
+    }
+    if (pair == 0 || wq > w) {  // a step without positions has no chunks
       if (lane == 0) atomicOr(status, kStCorrupt);
       return;
     }
     const int q0 = (int)ch.first + lane;
     y2 = q0 / pair; rr = q0 - y2 * pair;
   }
+  // idx element of the chunk's symbol i: its step index, or (kRag) the
+  // canvas step index of its position
+  auto ix = [&](int i) -> int64_t {
+    const int q = (int)ch.first + i;
+    if constexpr (kRag) {
+      const int a2 = q / pair, r = q - a2 * pair;
+      return (int64_t)a2 * pairC + (r < ne ? r : neC + (r - ne));
+    } else {
+      return q;
+    }
+  };
   // packed indices of this lane's next two symbols and the coarse row of
   // the next one, fetched a round ahead so that neither load is on the
   // round's dependent chain (every unpacked index is a valid table)
-  uint32_t pk_a = (lane < nl && lane < count) ? __ldg(idxp + lane) : 0u;
-  uint32_t pk_b = (lane < nl && lane + nl < count) ? __ldg(idxp + lane + nl) : 0u;
+  uint32_t pk_a = (lane < nl && lane < count) ? __ldg(idxp + ix(lane)) : 0u;
+  uint32_t pk_b = (lane < nl && lane + nl < count) ? __ldg(idxp + ix(lane + nl)) : 0u;
   uint4 ca0, ca1, cb0, cb1;
   // kMix: row of the chunk's symbol i (inactive lanes use the first one)
   const uint16_t *mrows = bank + ((int64_t)ch.plane * idx_stride + ch.first) * kMixRow;
@@ -278,7 +299,7 @@ __global__ void __launch_bounds__(256) k_rans_decode(
       asm volatile("prefetch.global.L1 [%0];" ::"l"(frow + 64));
     }
     pk_a = pk_b;
-    pk_b = (active && p + 2 * nl < count) ? __ldg(idxp + p + 2 * nl) : 0u;
+    pk_b = (active && p + 2 * nl < count) ? __ldg(idxp + ix(p + 2 * nl)) : 0u;
     // every lane runs the search (inactive lanes on a valid table, their
     // state kept), so the round has no branch around it
     int ctr;
@@ -540,28 +561,38 @@ void launch_cdf_bank(uint16_t *bank, uint16_t *coarse, cudaStream_t st) {
 void launch_rans_decode(const DecChunk *chunks, int nchunks, const uint16_t *bank,
                         const uint16_t *coarse, const uint32_t *idx, int64_t idx_stride,
                         int32_t *out, int64_t out_stride, int h, int w, int step,
-                        uint32_t *status, cudaStream_t st, bool mix) {
+                        uint32_t *status, cudaStream_t st, bool mix, const int2 *ext,
+                        int esh) {
   if (nchunks <= 0) return;
   const int nsm = sm_count();
   if (mix) {
     int wpb = 8;
     while (wpb > 1 && (nchunks + wpb - 1) / wpb < nsm) wpb >>= 1;
-    k_rans_decode<true><<<(nchunks + wpb - 1) / wpb, 32 * wpb, 0, st>>>(
-        chunks, nchunks, bank, nullptr, idx, idx_stride, out, out_stride, h, w, step, status);
+    k_rans_decode<true, false><<<(nchunks + wpb - 1) / wpb, 32 * wpb, 0, st>>>(
+        chunks, nchunks, bank, nullptr, idx, idx_stride, out, out_stride, h, w, step, status,
+        nullptr, 0);
     return;
   }
   constexpr int smem = kNTables * kCoarse * 2 + 16;   // coarse level + mbarrier
   static std::atomic<uint64_t> attr{0};
   once_per_device(attr, [] {
-    cudaFuncSetAttribute(k_rans_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem);
+    cudaFuncSetAttribute(k_rans_decode<false, false>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_rans_decode<false, true>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   });
   // one warp per chunk; with few chunks, fewer warps per block so that the
   // chunks spread over the SMs (one warp per scheduler)
   int wpb = 8;
   while (wpb > 1 && (nchunks + wpb - 1) / wpb < nsm) wpb >>= 1;
-  k_rans_decode<false><<<(nchunks + wpb - 1) / wpb, 32 * wpb, smem, st>>>(
-      chunks, nchunks, bank, coarse, idx, idx_stride, out, out_stride, h, w, step, status);
+  if (ext && step >= 0)
+    k_rans_decode<false, true><<<(nchunks + wpb - 1) / wpb, 32 * wpb, smem, st>>>(
+        chunks, nchunks, bank, coarse, idx, idx_stride, out, out_stride, h, w, step, status,
+        ext, esh);
+  else
+    k_rans_decode<false, false><<<(nchunks + wpb - 1) / wpb, 32 * wpb, smem, st>>>(
+        chunks, nchunks, bank, coarse, idx, idx_stride, out, out_stride, h, w, step, status,
+        nullptr, 0);
 }
 void launch_rans_count_ops(const EncChunk *chunks, int nchunks, const uint32_t *idx,
                            const int32_t *vals, uint32_t *ops, cudaStream_t st, bool mix) {

@@ -95,9 +95,10 @@ __device__ __forceinline__ void acc_set(const PlaneAcc &a, int p, int y, int x, 
 // input region (origin y0 - 3, x0 - 3).
 // rout (optional): the CNN residual of the tile's outputs, already computed.
 template <bool kExact>
-__device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int y0, int x0,
-                                            const float *in, const float *a2, const float *w3t,
-                                            const float *b3, const float *rout = nullptr) {
+__device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int H, int W, int y0,
+                                            int x0, const float *in, const float *a2,
+                                            const float *w3t, const float *b3,
+                                            const float *rout = nullptr) {
   const int t = threadIdx.x;
   const int ly = t / LT, lx = t % LT;
   float r_out = 0.f;
@@ -115,12 +116,12 @@ __device__ __forceinline__ void lift_finish(const LiftStepParams &a, int p, int 
     r_out = v;
   }
   const int y = y0 + ly, x = x0 + lx;
-  if (y >= a.H || x >= a.W) return;
+  if (y >= H || x >= W) return;
   const float s0 = in[(ly + 3) * LI + lx + 3];
   float lin;
   if (a.lin == LIN_P53) {
-    const float s1 = a.dir == 0 ? (x + 1 < a.W ? in[(ly + 3) * LI + lx + 4] : s0)
-                                : (y + 1 < a.H ? in[(ly + 4) * LI + lx + 3] : s0);
+    const float s1 = a.dir == 0 ? (x + 1 < W ? in[(ly + 3) * LI + lx + 4] : s0)
+                                : (y + 1 < H ? in[(ly + 4) * LI + lx + 3] : s0);
     lin = 0.5f * (s0 + s1);
   } else if (a.lin == LIN_U53) {
     const float sm = a.dir == 0 ? (x > 0 ? in[(ly + 3) * LI + lx + 2] : s0)
@@ -150,10 +151,13 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
   const int tiles_x = (a.W + LT - 1) / LT;
   const int y0 = (blockIdx.x / tiles_x) * LT, x0 = (blockIdx.x % tiles_x) * LT;
   const bool cnn = a.net.w1 != nullptr;
+  int H, W;
+  lift_extent(a, p, H, W);
+  if (y0 >= H || x0 >= W) return;  // a tile beyond this plane of a ragged batch
 
   for (int e = t; e < LI * LI; e += 256) {
     int yy = y0 + e / LI - 3, xx = x0 + e % LI - 3;
-    S.in[e] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? acc_get(a.src, p, yy, xx) : 0.f;
+    S.in[e] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? acc_get(a.src, p, yy, xx) : 0.f;
   }
   if (cnn) {
     for (int e = t; e < LF * 9; e += 256) {
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
     for (int e = t; e < L1 * L1; e += 256) {
       const int ly = e / L1, lx = e % L1;
       const int yy = y0 + ly - 2, xx = x0 + lx - 2;
-      const bool inside = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+      const bool inside = yy >= 0 && yy < H && xx >= 0 && xx < W;
       // output channels in pairs (packed FP32): each accumulator sees the
       // same sequence of operations as one mac<kExact> chain
       uint64_t accp[LF / 2];
@@ -232,8 +236,8 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
         f2unpack(p1[c], acc1[2 * c], acc1[2 * c + 1]);
       }
       const int yy0 = y0 + ly0 - 1, xx0 = x0 + lx0 - 1, yy1 = y0 + ly1 - 1, xx1 = x0 + lx1 - 1;
-      const bool in0 = yy0 >= 0 && yy0 < a.H && xx0 >= 0 && xx0 < a.W;
-      const bool in1 = yy1 >= 0 && yy1 < a.H && xx1 >= 0 && xx1 < a.W;
+      const bool in0 = yy0 >= 0 && yy0 < H && xx0 >= 0 && xx0 < W;
+      const bool in1 = yy1 >= 0 && yy1 < H && xx1 >= 0 && xx1 < W;
       float4 *d0 = reinterpret_cast<float4 *>(S.a2 + e0 * LF);
       float4 *d1 = reinterpret_cast<float4 *>(S.a2 + e1 * LF);
 #pragma unroll
@@ -248,7 +252,7 @@ __global__ void __launch_bounds__(256) k_lift_step(LiftStepParams a) {
     }
     __syncthreads();
   }
-  lift_finish<kExact>(a, p, y0, x0, S.in, cnn ? S.a2 : nullptr, S.w3t, S.b3);
+  lift_finish<kExact>(a, p, H, W, y0, x0, S.in, cnn ? S.a2 : nullptr, S.w3t, S.b3);
 }
 
 // ---------------------------------------------------------------------------
@@ -314,6 +318,9 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
   const int p = blockIdx.z;
   const int tiles_x = (a.W + LT - 1) / LT;
   const int y0 = (blockIdx.x / tiles_x) * LT, x0 = (blockIdx.x % tiles_x) * LT;
+  int H, W;
+  lift_extent(a, p, H, W);
+  if (y0 >= H || x0 >= W) return;  // a tile beyond this plane of a ragged batch (uniform)
   // TMEM columns: layer 2 in [0, 64) (4 blocks x 16), then layer 3 in
   // [0, 48) once the layer-2 epilogue has read them
   constexpr uint32_t kCols = 64;
@@ -330,7 +337,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
   }
   for (int e = t; e < LI * LI; e += 256) {
     const int yy = y0 + e / LI - 3, xx = x0 + e % LI - 3;
-    S.in[e] = (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) ? acc_get(a.src, p, yy, xx) : 0.f;
+    S.in[e] = (yy >= 0 && yy < H && xx >= 0 && xx < W) ? acc_get(a.src, p, yy, xx) : 0.f;
   }
   for (int e = t; e < LF * 9; e += 256) {
     const int c = e / 9, tap = e % 9;  // source [c][tap]
@@ -362,7 +369,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
     const int r = pos / kRS, c = pos % kRS;
     const int yy = y0 - 2 + r, xx = x0 - 2 + c;
     float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    if (r < L1 && c < L1 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+    if (r < L1 && c < L1 && yy >= 0 && yy < H && xx >= 0 && xx < W) {
       // channel pairs in packed FP32 FMAs (the same rounding as fmaf)
       uint64_t acc[4];
 #pragma unroll
@@ -423,7 +430,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
       if (m < kA2) {
         const int r2 = m / kRS, c2 = m % kRS;
         const int yy = y0 - 1 + r2, xx = x0 - 1 + c2;
-        const bool live = r2 < L2 && c2 < L2 && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
+        const bool live = r2 < L2 && c2 < L2 && yy >= 0 && yy < H && xx >= 0 && xx < W;
         __align__(16) __nv_bfloat16 hb[LF];
 #pragma unroll
         for (int k = 0; k < LF; ++k)
@@ -474,7 +481,7 @@ __global__ void __launch_bounds__(256) k_lift_tc(LiftStepParams a) {
     __syncwarp();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(kCols));
   }
-  if (ok) lift_finish<false>(a, p, y0, x0, S.in, nullptr, nullptr, nullptr, S.rout);
+  if (ok) lift_finish<false>(a, p, H, W, y0, x0, S.in, nullptr, nullptr, nullptr, S.rout);
 }
 
 // Component planes [B][nc][Hp][Wp] -> interleaved samples (crop, inverse

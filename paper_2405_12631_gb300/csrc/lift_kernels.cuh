@@ -32,7 +32,25 @@ struct LiftStepParams {
   int tc;                          // 1: middle CNN layer on the tensor cores
                                    // (BF16 operands; round must be 0)
   uint32_t *status;                // kStTimeout is set here (tc only)
+  // ragged batches (planes of different sizes on one canvas of P x H x W):
+  // plane p's own extent is ((ext[p].x >> esh) * ehmul) x (ext[p].y >> esh)
+  // (ext = the planes' padded full-resolution sizes); tiles beyond it do no
+  // work and its borders take the place of the canvas's. Null: every plane
+  // is H x W.
+  const int2 *ext;
+  int esh, ehmul;
 };
+// Extent of plane p of a lifting step (see LiftStepParams::ext).
+__host__ __device__ __forceinline__ void lift_extent(const LiftStepParams &a, int p, int &H,
+                                                     int &W) {
+  if (a.ext) {
+    H = (a.ext[p].x >> a.esh) * a.ehmul;
+    W = a.ext[p].y >> a.esh;
+  } else {
+    H = a.H;
+    W = a.W;
+  }
+}
 
 void launch_lift_step(const LiftStepParams &a, cudaStream_t st);
 void launch_colour_out(const float *planes, int B, int nc, int Hp, int Wp, int H, int W,

@@ -183,11 +183,14 @@ __device__ __forceinline__ int find_sym(const uint16_t *__restrict__ t, uint32_t
 }
 
 // Decoder: one warp per plane (one warp per CTA); the plane's symbols live
-// in shared memory while it is decoded.
+// in shared memory while it is decoded. Ragged batches (ext): plane p's LL
+// is (ext[p].x >> esh) x (ext[p].y >> esh), written into the canvas's
+// h x w plane.
 template <int C>
 __global__ void k_ll_ar_decode(const DecChunk *__restrict__ chunks, int P, int h, int w,
                                ArWeightsDev wd, const uint16_t *__restrict__ bank,
-                               int32_t *__restrict__ Q, uint32_t *status) {
+                               int32_t *__restrict__ Q, uint32_t *status,
+                               const int2 *__restrict__ ext, int esh) {
   extern __shared__ float smem[];
   ArSmem S;
   ar_load_weights<C>(wd, smem, 1, S);
@@ -196,7 +199,8 @@ __global__ void k_ll_ar_decode(const DecChunk *__restrict__ chunks, int P, int h
   if (p >= P) return;
   const int lane = threadIdx.x & 31;
   const DecChunk ch = chunks[p];
-  const int n = h * w;
+  const int hv = ext ? min(ext[p].x >> esh, h) : h, wv = ext ? min(ext[p].y >> esh, w) : w;
+  const int n = hv * wv;
   bool bad = ch.lanes != 1 || ch.count != (uint32_t)n || ch.nbytes < 4 || ((ch.nbytes - 4) & 1);
   uint32_t x = kRansL, ptr = 0, nwords = 0;
   const uint8_t *wp = ch.data + 4;
@@ -217,7 +221,8 @@ __global__ void k_ll_ar_decode(const DecChunk *__restrict__ chunks, int P, int h
     if (__shfl_sync(0xffffffffu, bad ? 1 : 0, 0)) break;
     uint32_t pk;
     float mu, sg;
-    ar_params<C>(S, wd, h, w, pos / w, pos % w, [&](int i) { return s_sym[i]; }, pk, mu, sg);
+    ar_params<C>(S, wd, hv, wv, pos / wv, pos % wv, [&](int i) { return s_sym[i]; }, pk, mu,
+                 sg);
     if (lane == 0) {
       int ctr, tid;
       unpack_index(pk, ctr, tid);
@@ -254,7 +259,7 @@ __global__ void k_ll_ar_decode(const DecChunk *__restrict__ chunks, int P, int h
     __syncwarp();
   }
   if (lane == 0 && (x != kRansL || ptr != nwords)) bad = true;
-  for (int i = lane; i < n; i += 32) Q[(int64_t)p * n + i] = s_sym[i];
+  for (int i = lane; i < n; i += 32) Q[(int64_t)p * h * w + (int64_t)(i / wv) * w + i % wv] = s_sym[i];
   if (lane == 0 && bad) atomicOr(status, kStCorrupt);
 }
 
@@ -277,7 +282,8 @@ int launch_ll_ar_params(const int32_t *Q, int P, int h, int w, int C, const ArWe
 }
 
 int launch_ll_ar_decode(const DecChunk *chunks, int P, int h, int w, int C, const ArWeightsDev &wd,
-                        const uint16_t *bank, int32_t *Q, uint32_t *status, cudaStream_t st) {
+                        const uint16_t *bank, int32_t *Q, uint32_t *status, cudaStream_t st,
+                        const int2 *ext, int esh) {
   const size_t sm = ar_smem_weights(C, 1) + (size_t)h * w * sizeof(int32_t);
   if (sm > 227 * 1024) {
     set_last_error("autoregressive LL subband too large for one CTA");
@@ -287,7 +293,7 @@ int launch_ll_ar_decode(const DecChunk *chunks, int P, int h, int w, int C, cons
   if (C == C_) {                                                                            \
     cudaFuncSetAttribute(k_ll_ar_decode<C_>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                          (int)sm);                                                          \
-    k_ll_ar_decode<C_><<<P, 32, sm, st>>>(chunks, P, h, w, wd, bank, Q, status);            \
+    k_ll_ar_decode<C_><<<P, 32, sm, st>>>(chunks, P, h, w, wd, bank, Q, status, ext, esh);  \
     return PW_OK;                                                                           \
   }
   PW_AR(32) PW_AR(64) PW_AR(128)

@@ -18,7 +18,9 @@ struct ArWeightsDev {
 
 int launch_ll_ar_params(const int32_t *Q, int P, int h, int w, int C, const ArWeightsDev &wd,
                         uint32_t *idx, float *mu, float *sg, cudaStream_t st);
+// ext / esh: ragged batches (every plane's own LL extent, see the kernel)
 int launch_ll_ar_decode(const DecChunk *chunks, int P, int h, int w, int C, const ArWeightsDev &wd,
-                        const uint16_t *bank, int32_t *Q, uint32_t *status, cudaStream_t st);
+                        const uint16_t *bank, int32_t *Q, uint32_t *status, cudaStream_t st,
+                        const int2 *ext = nullptr, int esh = 0);
 
 }  // namespace pw

@@ -2,8 +2,13 @@
 //
 // Requests (host bitstreams) enter a queue. Worker lanes, each with its own
 // CUDA stream and workspace cache, repeatedly take the oldest queued request
-// together with every queued request of the same geometry (size, channels,
-// format; up to max_batch) and decode them as one batch. A batch is admitted
+// together with queued requests of the same format (channels, levels, bit
+// depth, coder layout; up to max_batch) whose sizes are close enough: a
+// request joins while the batch's canvas (the largest padded size) times
+// its image count stays within kCanvasWaste times the images' own padded
+// area. The batch is decoded in one call - a ragged batch when the sizes
+// differ, whose every launch covers all its images. (Logistic-mixture
+// models batch identical sizes only.) A batch is admitted
 // only when the device memory it needs (its workspace estimate) fits in the
 // HBM budget next to what the other lanes hold, so requests that arrive while
 // others are on the GPU start as soon as a lane and memory free up, and the
@@ -28,7 +33,8 @@ namespace pw {
 struct Req {
   uint64_t ticket = 0;
   std::vector<uint8_t> bs;
-  std::string key;
+  std::string key;           // geometry (size and format)
+  std::string fkey;          // format only (ragged batches share it)
   Geometry g;
   int64_t need = 0;          // workspace bytes of a batch of one (estimate)
   Clock::time_point t_submit, t_done;
@@ -67,11 +73,61 @@ struct pw_server {
 
 namespace pw {
 
-static std::string req_key(const Geometry &g) {
+static std::string fmt_key(const Geometry &g) {
   char b[160];
-  snprintf(b, sizeof(b), "%d:%d:%d:%d:%d:%d:%d:%d:%d:%d:%d", g.H, g.W, g.nc, g.levels, g.colour,
-           g.bitdepth, g.lossless, g.ll_ar, g.chunk, g.balanced, g.lane_shift);
+  snprintf(b, sizeof(b), "%d:%d:%d:%d:%d:%d:%d:%d:%d", g.nc, g.levels, g.colour, g.bitdepth,
+           g.lossless, g.ll_ar, g.chunk, g.balanced, g.lane_shift);
   return b;
+}
+static std::string req_key(const Geometry &g) {
+  return std::to_string(g.H) + "x" + std::to_string(g.W) + ":" + fmt_key(g);
+}
+
+// A ragged batch's canvas area may exceed its images' own padded area by at
+// most this factor (the work spent on the canvas outside the images).
+constexpr double kCanvasWaste = 1.5;
+
+// Geometry of the canvas of a batch: the largest padded size (the first
+// request's geometry when all sizes are equal).
+static Geometry canvas_of(const std::vector<Req *> &batch) {
+  const Geometry &g0 = batch[0]->g;
+  int Hc = 0, Wc = 0;
+  bool same = true;
+  for (Req *q : batch) {
+    Hc = std::max(Hc, q->g.Hp);
+    Wc = std::max(Wc, q->g.Wp);
+    same = same && q->g.H == g0.H && q->g.W == g0.W;
+  }
+  if (same) return g0;
+  Geometry gc;
+  gc.build(Hc, Wc, g0.nc, g0.levels, g0.colour, g0.bitdepth, g0.lossless, g0.ll_ar, g0.chunk,
+           g0.balanced, g0.lane_shift);
+  return gc;
+}
+
+// The oldest queued request and the queued requests that batch with it.
+static std::vector<Req *> form_batch(const std::deque<Req *> &queue, int max_batch, bool ragged) {
+  Req *r0 = queue.front();
+  std::vector<Req *> batch{r0};
+  int Hc = r0->g.Hp, Wc = r0->g.Wp;
+  double area = (double)r0->g.Hp * r0->g.Wp;
+  for (Req *q : queue) {
+    if ((int)batch.size() >= max_batch) break;
+    if (q == r0) continue;
+    if (!ragged) {
+      if (q->key == r0->key) batch.push_back(q);
+      continue;
+    }
+    if (q->fkey != r0->fkey) continue;
+    const int h = std::max(Hc, q->g.Hp), w = std::max(Wc, q->g.Wp);
+    const double a = area + (double)q->g.Hp * q->g.Wp;
+    if ((double)(batch.size() + 1) * h * w > kCanvasWaste * a) continue;
+    batch.push_back(q);
+    Hc = h;
+    Wc = w;
+    area = a;
+  }
+  return batch;
 }
 
 static void lane_main(pw_server *s, int li) {
@@ -95,16 +151,14 @@ static void lane_main(pw_server *s, int li) {
       s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
       continue;
     }
-    Req *r0 = s->queue.front();
-    std::vector<Req *> batch;
-    for (Req *q : s->queue)
-      if (q->key == r0->key && (int)batch.size() < s->max_batch) batch.push_back(q);
+    std::vector<Req *> batch = form_batch(s->queue, s->max_batch, !s->m->mix);
     // the largest batch whose workspace fits next to the other lanes'
     const int64_t others = s->held - s->lane_bytes[li];
     int64_t need = 0;
+    Geometry gc;
     for (;;) {
-      need = Workspace::estimate(r0->g, (int)batch.size() * r0->g.nc, s->m->C, false, prec,
-                                  s->m->mix);
+      gc = canvas_of(batch);
+      need = Workspace::estimate(gc, (int)batch.size() * gc.nc, s->m->C, false, prec, s->m->mix);
       if (others + need <= s->budget || batch.size() == 1) break;
       batch.pop_back();
     }
@@ -116,9 +170,9 @@ static void lane_main(pw_server *s, int li) {
       continue;
     }
     for (Req *q : batch) s->queue.erase(std::find(s->queue.begin(), s->queue.end(), q));
-    // a context caches one workspace per (geometry, batch size): keep it
-    // only when both repeat
-    const std::string lkey = r0->key + "#" + std::to_string(batch.size());
+    // a context caches one workspace per (canvas geometry, batch size): keep
+    // it only when both repeat
+    const std::string lkey = req_key(gc) + "#" + std::to_string(batch.size());
     const bool same = s->lane_key[li] == lkey;
     s->held = others + need;
     s->lane_bytes[li] = need;
@@ -126,13 +180,13 @@ static void lane_main(pw_server *s, int li) {
     lk.unlock();
     if (!same) drop_plans(s->lanes[li]);
     const int B = (int)batch.size();
-    const Geometry &g = r0->g;
-    const int bps = g.bitdepth > 8 ? 2 : 1;
     std::vector<const uint8_t *> ptrs(B);
     std::vector<size_t> lens(B);
     std::vector<pw_image> outs(B);
     for (int b = 0; b < B; ++b) {
       Req *q = batch[b];
+      const Geometry &g = q->g;
+      const int bps = g.bitdepth > 8 ? 2 : 1;
       ptrs[b] = q->bs.data();
       lens[b] = q->bs.size();
       q->out.assign((size_t)g.H * g.W * g.nc * bps, 0);
@@ -160,7 +214,7 @@ static void lane_main(pw_server *s, int li) {
       s->lat_ms.push_back(std::chrono::duration<double, std::milli>(now - q->t_submit).count());
       if (st[b] == PW_OK) {
         ++s->completed;
-        s->pixels += (double)g.H * g.W;
+        s->pixels += (double)q->g.H * q->g.W;
       } else {
         ++s->failed;
       }
@@ -227,6 +281,7 @@ int pw_server_submit(pw_server *s, const uint8_t *bs, size_t n, uint64_t *ticket
     return st;
   }
   r->key = req_key(r->g);
+  r->fkey = fmt_key(r->g);
   r->need = Workspace::estimate(r->g, r->g.nc, s->m->C, false, s->ctx->precision, s->m->mix);
   std::lock_guard<std::mutex> lk(s->mu);
   if (r->need > s->budget || s->queue.size() >= 4096) {

@@ -1,0 +1,138 @@
+"""Ragged batches: streams of one format whose image sizes differ, decoded in
+one pw_decode_batch call on a canvas of the largest padded size (every
+convolution, coder pass and lifting step covers all of them in one launch).
+
+Bar: bit-identical to decoding every stream alone, in every precision class,
+for both LL models, lossless 12-bit streams (also equal to the input), a
+post-processing model, and the logistic-mixture model (decoded one batch per
+size); a corrupt stream in a ragged batch is reported and streams of
+different formats are refused.
+"""
+import numpy as np
+import pytest
+
+import synthetic as S
+from tests._lib import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+# (H, W): multiples of 16 and not, taller and wider than the rest, and one
+# whose level-4 subbands are smaller than the canvas's compact-head minimum
+SIZES = [(64, 96), (48, 80), (96, 64), (37, 53), (112, 128), (64, 96)]
+
+
+@pytest.fixture(scope="module")
+def pw():
+    ensure_built()
+    import paper_2405_12631_gb300 as m
+    return m
+
+
+def _blob(C=32, seed=0, ll_mode=0, prob=0, post=0, levels=4):
+    cfg = S.ModelConfig(levels=levels, C=C, ll_mode=ll_mode, prob=prob, post=post)
+    return S.pack_blob(cfg, S.random_model(cfg, seed))
+
+
+def _imgs(rgb, sizes=SIZES, seed=0):
+    if rgb:
+        return [S.rgb_natural(h, w, seed=seed + i) for i, (h, w) in enumerate(sizes)]
+    return [S.gray_sinusoids(h, w, seed=seed + i) for i, (h, w) in enumerate(sizes)]
+
+
+def _check(codec, model, streams):
+    alone = [codec.decode_image(model, bs) for bs in streams]
+    got = codec.decode_ragged(model, streams)
+    for i, (a, g) in enumerate(zip(alone, got)):
+        assert g.shape == a.shape, i
+        assert np.array_equal(a, g), f"stream {i} ({a.shape}) differs from its single decode"
+    # twice: the plan's tables are rebuilt per call
+    got2 = codec.decode_ragged(model, streams[::-1])
+    for a, g in zip(alone[::-1], got2):
+        assert np.array_equal(a, g)
+    return alone
+
+
+@pytest.mark.parametrize("prec,C", [("fp32", 32), ("int8", 32), ("bf16", 32), ("fp8", 32),
+                                    ("fp8", 64)])
+@pytest.mark.parametrize("rgb", [False, True])
+def test_ragged_batch_equals_single_decodes(pw, prec, C, rgb):
+    codec = pw.Codec(0, prec)
+    model = codec.load_model(_blob(C=C, seed=1))
+    qs = [4.0, 8.0, 16.0, 32.0, 8.0, 2.0]
+    streams = [codec.encode_image(model, im, q=q) for im, q in zip(_imgs(rgb, seed=3), qs)]
+    _check(codec, model, streams)
+    model.close()
+    codec.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp8", "int8"])
+def test_ragged_autoregressive_ll(pw, prec):
+    codec = pw.Codec(0, prec)
+    model = codec.load_model(_blob(seed=2, ll_mode=1))
+    streams = [codec.encode_image(model, im, q=8.0) for im in _imgs(True, seed=5)]
+    _check(codec, model, streams)
+    model.close()
+    codec.close()
+
+
+def test_ragged_lossless_12bit_exact(pw):
+    codec = pw.Codec(0, "fp8")
+    model = codec.load_model(_blob(seed=4, levels=5))
+    sizes = [(96, 160), (64, 64), (130, 100), (32, 200)]
+    imgs = [S.lossless_blobs(h, w, seed=20 + i) for i, (h, w) in enumerate(sizes)]
+    streams = [codec.encode_image(model, im, lossless=True, bitdepth=12) for im in imgs]
+    got = codec.decode_ragged(model, streams)
+    for im, g in zip(imgs, got):
+        assert np.array_equal(im, g)
+    _check(codec, model, streams)
+    model.close()
+    codec.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_ragged_post_processing_model(pw, prec):
+    codec = pw.Codec(0, prec)
+    model = codec.load_model(_blob(seed=6, post=1))
+    streams = [codec.encode_image(model, im, q=8.0) for im in _imgs(True, seed=9)]
+    _check(codec, model, streams)
+    model.close()
+    codec.close()
+
+
+def test_ragged_mixture_model_one_batch_per_size(pw):
+    codec = pw.Codec(0, "fp32")
+    model = codec.load_model(_blob(seed=7, prob=1))
+    streams = [codec.encode_image(model, im, q=8.0) for im in _imgs(False, seed=11)]
+    _check(codec, model, streams)
+    model.close()
+    codec.close()
+
+
+def test_ragged_larger_sizes_fp8(pw):
+    """Several tiles per plane in every convolution and lifting step."""
+    codec = pw.Codec(0, "fp8")
+    model = codec.load_model(_blob(C=64, seed=8))
+    sizes = [(256, 384), (200, 300), (320, 240), (512, 512)]
+    streams = [codec.encode_image(model, im, q=8.0) for im in _imgs(True, sizes, seed=13)]
+    _check(codec, model, streams)
+    model.close()
+    codec.close()
+
+
+def test_ragged_corrupt_stream_and_mixed_formats(pw):
+    codec = pw.Codec(0, "fp8")
+    model = codec.load_model(_blob(seed=9))
+    streams = [codec.encode_image(model, im, q=8.0) for im in _imgs(True, seed=15)]
+    bad = bytearray(streams[2])
+    bad[len(bad) - 40] ^= 0x5A                      # a payload byte
+    with pytest.raises(pw.PwError) as e:
+        codec.decode_ragged(model, streams[:2] + [bytes(bad)] + streams[3:])
+    assert e.value.code == pw.PW_ECORRUPT
+    gray = codec.encode_image(model, S.gray_sinusoids(48, 64, seed=1), q=8.0)
+    with pytest.raises(pw.PwError) as e:
+        codec.decode_ragged(model, streams[:2] + [gray])
+    assert e.value.code == pw.PW_EINVAL
+    # the context still decodes afterwards
+    _check(codec, model, streams)
+    model.close()
+    codec.close()

@@ -98,3 +98,30 @@ def test_server_admission_and_errors(pw):
     other.close()
     model.close()
     codec.close()
+
+
+@pytest.mark.parametrize("prec", ["fp8", "fp32"])
+def test_server_forms_ragged_batches_of_similar_sizes(pw, prec):
+    """A burst of requests of one format and similar (not equal) sizes, on
+    one lane: the server batches them across sizes (fewer batches than
+    requests) and every result equals the stream's single decode."""
+    codec = pw.Codec(0, prec)
+    cfg = S.ModelConfig(levels=4, C=32, ll_mode=0)
+    model = codec.load_model(S.pack_blob(cfg, S.random_model(cfg, 13)))
+    rng = np.random.default_rng(5)
+    sizes = [(int(rng.integers(100, 129)), int(rng.integers(140, 161))) for _ in range(12)]
+    imgs = [S.rgb_natural(h, w, seed=40 + i) for i, (h, w) in enumerate(sizes)]
+    streams = [codec.encode_image(model, im, q=8.0) for im in imgs]
+    alone = [codec.decode_image(model, bs) for bs in streams]
+    srv = pw.Server(codec, model, hbm_budget=8 << 30, lanes=1, max_batch=6)
+    tickets = [srv.submit(bs) for bs in streams]
+    got = [srv.poll(t, timeout_ms=120000) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    for i, (a, g) in enumerate(zip(alone, got)):
+        assert np.array_equal(a, g), f"request {i} differs"
+    print(f"\n{prec}: {len(streams)} requests of sizes {sizes[:3]}... in {st['batches']} batches")
+    assert st["completed"] == len(streams)
+    assert st["batches"] < len(streams)
+    model.close()
+    codec.close()
