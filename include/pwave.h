@@ -172,12 +172,19 @@ int pw_decode_image(pw_ctx *ctx, const pw_model *m, const uint8_t *bs, size_t n,
 int pw_encode_batch(pw_ctx *ctx, const pw_model *m, int count, const pw_image *in,
                     const pw_codec_opts *opts, uint8_t **bs, size_t *n);
 
-/* Batched decode of count streams of identical size/channels/model into
- * out[0..count-1]. bs[i] are host pointers unless bs_on_device is set, in
- * which case they are device pointers (the streams then never visit the
- * host: headers are validated on the device). Page-locked host streams and
- * host images (pinned or registered memory) are copied to and from the
- * device directly; pageable ones go through the library's pinned staging. */
+/* Batched decode of count streams of one model into out[0..count-1]
+ * (out[i] sized like stream i). bs[i] are host pointers unless bs_on_device
+ * is set, in which case they are device pointers (the streams then never
+ * visit the host: headers are validated on the device) and must all have
+ * the first stream's size. Host streams may differ in image size (not in
+ * channels, levels, bit depth, colour mode, lossless / LL-model flags,
+ * precision class or coder layout: PW_EINVAL): such a ragged batch is
+ * decoded on a canvas of the largest padded size, every convolution, coder
+ * pass and lifting step covering all streams in one launch, and each image
+ * is bit-identical to its single decode (logistic-mixture models decode it
+ * as one batch per size). Page-locked host streams and host images (pinned
+ * or registered memory) are copied to and from the device directly;
+ * pageable ones go through the library's pinned staging. */
 int pw_decode_batch(pw_ctx *ctx, const pw_model *m, int count,
                     const uint8_t *const *bs, const size_t *n, int bs_on_device,
                     pw_image *out);
@@ -373,9 +380,13 @@ int pw_conv_bf16(pw_ctx *ctx, int P, int H, int W, int cin, int cout, int ks, in
  * CUDA stream and a context of ctx's device and precision; all lanes share
  * the model m (read only; m and ctx must outlive the server, and ctx itself
  * is not used by the lanes). A lane repeatedly takes the oldest queued
- * request together with every queued request of the same geometry (size,
- * channels, bit depth, format; at most max_batch) and decodes them as one
- * batch. A batch starts only when its device workspace fits in hbm_budget
+ * request together with queued requests of the same format (channels, bit
+ * depth, levels, coder layout; at most max_batch) whose sizes are close:
+ * a request joins while the batch's canvas (its largest padded size) times
+ * its image count stays within 1.5 times the images' own padded area. The
+ * batch is decoded in one call (a ragged batch when the sizes differ, see
+ * pw_decode_batch; logistic-mixture models batch equal sizes only). A
+ * batch starts only when its device workspace fits in hbm_budget
  * bytes next to the workspaces the other lanes hold; an idle lane frees its
  * workspace. Lanes run concurrently, so different sizes overlap on the GPU.
  * Each result is bit-identical to pw_decode_image of the same stream on a
