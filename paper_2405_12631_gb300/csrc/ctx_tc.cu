@@ -248,14 +248,23 @@ constexpr int kMaxStages = 24;
 // weights and the stages
 constexpr int kConvHeader = 8192;
 
-constexpr int kEpiWarps = 8;                    // two per TMEM lane quadrant
-constexpr int kConvThreads = 64 + 32 * kEpiWarps;
+// Epilogue warps: 16 (four per TMEM lane quadrant, 16 columns each) for the
+// 1x1 plain stores of 64 columns, whose short epilogue is latency-bound
+// (measured: 1x1 class 9.04 -> 8.53 ms per batch of 24; the 3x3 stores lost
+// as much, their MMA and load warps need the issue slots), else 8 (two per
+// quadrant, NCTA / 2 columns each).
+__host__ __device__ constexpr int conv_epi_warps(int ks, int epi, int ncta) {
+  return (ks == 1 && (epi == TE_STORE || epi == TE_STOREV) && ncta == 64) ? 16 : 8;
+}
+__host__ __device__ constexpr int conv_threads(int ks, int epi, int ncta) {
+  return 64 + 32 * conv_epi_warps(ks, epi, ncta);
+}
 constexpr int kAcc = 4;                         // TMEM accumulator buffers
 
 // KB: input channels per K-block; F8: E4M3 operands (kind::f8f6f4, 16
 // channels per 16-byte core-matrix row) instead of BF16 (8 per row).
 template <int KS, int KB, int NCTA, int EPI, bool F8>
-__global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap,
+__global__ void __launch_bounds__(conv_threads(KS, EPI, NCTA), 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap,
                                                     const __grid_constant__ CUtensorMap tmap1,
                                                     const TcConvArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -316,7 +325,10 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
   }
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.stages; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-    for (int i = 0; i < kAcc; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], kEpiWarps); }
+    for (int i = 0; i < kAcc; ++i) {
+      mbar_init(&accf[i], 1);
+      mbar_init(&acce[i], conv_epi_warps(KS, EPI, NCTA));
+    }
     if (HEADK)
       for (int i = 0; i < kAcc * 4; ++i) mbar_init(&hbar[i], 1);
     mbar_init(wbar, 1);
@@ -584,12 +596,13 @@ __global__ void __launch_bounds__(kConvThreads, 1) k_conv_tc(const __grid_consta
       if (acc >= kAcc) { acc -= kAcc; aphase ^= 1; }
     }
   } else if (warp >= 2) {
-    // ---- epilogue: warps 2..9; warp w reads TMEM lanes 32 (w % 4) .. +31
-    // (output pixels), half (w - 2) / 4 of the columns (the head epilogue
-    // needs all columns of a pixel and runs on half 0 only) --------------
+    // ---- epilogue: warps 2 .. 2 + EW - 1; warp w reads TMEM lanes
+    // 32 (w % 4) .. +31 (output pixels), part (w - 2) / 4 of the columns
+    // (two halves, or four quarters for the 16-warp plain stores; the head
+    // epilogue needs all columns of a pixel and runs on half 0 only) -----
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
-    constexpr int NH = NCTA / 2;
+    constexpr int NH = NCTA / (conv_epi_warps(KS, EPI, NCTA) / 4);
     const bool work = true;
     const int col0 = half * NH;
     const int m = 32 * q + lane;
@@ -1253,9 +1266,9 @@ std::string tune_report() {
 // previous kernel of the stream (its set-up overlaps that kernel's tail; it
 // touches activations only after griddep_wait).
 template <typename K>
-static int launch_pdl(pw_ctx *ctx, K kern, int grid, size_t smem, cudaStream_t st,
+static int launch_pdl(pw_ctx *ctx, K kern, int threads, int grid, size_t smem, cudaStream_t st,
                       const CUtensorMap &map, const CUtensorMap &map1, const TcConvArgs &la) {
-  const cudaError_t e = launch_dep(kern, dim3((unsigned)grid), dim3(kConvThreads), smem, st,
+  const cudaError_t e = launch_dep(kern, dim3((unsigned)grid), dim3((unsigned)threads), smem, st,
                                    map, map1, la);
   if (e != cudaSuccess) {
     set_last_error(std::string("tensor-core conv launch: ") + cudaGetErrorString(e));
@@ -1407,7 +1420,8 @@ static int conv_tc(pw_ctx *ctx, const TcWeights::Conv &cv, const void *in, int i
         cudaFuncSetAttribute(k_conv_tc<KS_, KB_, N_, E_, F8_>,                              \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxsm);      \
       });                                                                                   \
-      return launch_pdl(ctx, k_conv_tc<KS_, KB_, N_, E_, F8_>, grid, smem, st, map, map1, la); \
+      return launch_pdl(ctx, k_conv_tc<KS_, KB_, N_, E_, F8_>, conv_threads(KS_, E_, N_), grid, smem, \
+                        st, map, map1, la);                                                  \
     }
     // BF16 plain stores (all shapes the stage entry accepts)
     PW_TC_CASE(1, 32, 32, TE_STORE, false) PW_TC_CASE(1, 32, 64, TE_STORE, false)
