@@ -162,8 +162,10 @@ int pw_encode_image(pw_ctx *ctx, const pw_model *m, const pw_image *in,
 
 /* Decode one host bitstream into `out`. out->data must hold
  * height * width * channels samples of the stream's bit depth (checked
- * against out->width/height/channels, which must match the stream).
- * Errors: PW_EINVAL (model hash or size mismatch), PW_ECORRUPT. */
+ * against out->width/height/channels, which must match the stream). With
+ * out->data == NULL the library allocates a packed host image of the
+ * stream's size and fills all of *out (release out->data with pw_free).
+ * Errors: PW_EINVAL (model hash or size mismatch), PW_ECORRUPT, PW_ENOMEM. */
 int pw_decode_image(pw_ctx *ctx, const pw_model *m, const uint8_t *bs, size_t n,
                     pw_image *out);
 

@@ -343,6 +343,21 @@ class Codec:
     def decode_image(self, model: Model, bs: bytes, shape=None, dtype=None) -> np.ndarray:
         return self.decode_batch(model, [bs], shape, dtype)[0]
 
+    def decode_image_alloc(self, model: Model, bs: bytes) -> np.ndarray:
+        """pw_decode_image with no output buffer: the library allocates the
+        image (its size from the stream); copied out and released here."""
+        im = pw_image(0, 0, 0, 0, 0, 0, None, 0)
+        check(pw_decode_image(self.ctx, model.handle, bs, len(bs), C.byref(im)))
+        try:
+            dtype = np.uint8 if im.bitdepth <= 8 else np.uint16
+            n = im.width * im.height * im.channels
+            arr = np.ctypeslib.as_array(C.cast(im.data, C.POINTER(
+                C.c_uint8 if dtype == np.uint8 else C.c_uint16)), shape=(n,)).copy()
+        finally:
+            pw_free(im.data)
+        shape = (im.height, im.width) if im.channels == 1 else (im.height, im.width, im.channels)
+        return arr.reshape(shape)
+
     def decode_batch(self, model: Model, streams, shape=None, dtype=None) -> np.ndarray:
         if shape is None or dtype is None:
             shape, dtype = stream_image_shape(streams[0])

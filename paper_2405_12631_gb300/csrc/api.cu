@@ -1252,7 +1252,21 @@ int pw_decode_batch(pw_ctx *c, const pw_model *m, int count, const uint8_t *cons
 }
 
 int pw_decode_image(pw_ctx *c, const pw_model *m, const uint8_t *bs, size_t n, pw_image *out) {
-  return pw_decode_batch(c, m, 1, &bs, &n, 0, out);
+  if (!c || !m || !out) return PW_EINVAL;
+  if (out->data) return pw_decode_batch(c, m, 1, &bs, &n, 0, out);
+  // no buffer given: a host image of the stream's size, owned by the caller
+  StreamHeader h;
+  int s = read_header(bs, n, 0, h);
+  if (s) return s;
+  const int bps = h.bitdepth > 8 ? 2 : 1;
+  const size_t bytes = (size_t)h.width * h.height * h.ncomp * bps;
+  void *buf = std::malloc(bytes ? bytes : 1);
+  if (!buf) { set_last_error("host allocation failed"); return PW_ENOMEM; }
+  pw_image im{(int)h.width, (int)h.height, (int)h.ncomp, (int)h.bitdepth, 0, 0, buf, 0};
+  s = pw_decode_batch(c, m, 1, &bs, &n, 0, &im);
+  if (s != PW_OK) { std::free(buf); return s; }
+  *out = im;
+  return PW_OK;
 }
 
 // ---- video GOPs (Section 3.3) ----------------------------------------------

@@ -136,3 +136,19 @@ def test_ragged_corrupt_stream_and_mixed_formats(pw):
     _check(codec, model, streams)
     model.close()
     codec.close()
+
+
+def test_decode_image_allocates_when_no_buffer(pw):
+    """pw_decode_image with out->data == NULL allocates the image itself."""
+    codec = pw.Codec(0, "fp8")
+    model = codec.load_model(_blob(seed=10))
+    for img in (S.rgb_natural(40, 72, seed=2), S.gray_sinusoids(33, 50, seed=3)):
+        bs = codec.encode_image(model, img, q=8.0)
+        got = codec.decode_image_alloc(model, bs)
+        assert got.shape == img.shape and got.dtype == img.dtype
+        assert np.array_equal(got, codec.decode_image(model, bs))
+    img12 = S.lossless_blobs(48, 64, seed=4)
+    bs = codec.encode_image(model, img12, lossless=True, bitdepth=12)
+    assert np.array_equal(codec.decode_image_alloc(model, bs), img12)
+    model.close()
+    codec.close()
