@@ -795,11 +795,11 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
 # is kept under profiles/); valid only while the sources
 # of the convolution kernels hash to "src" (the capture's), else reported
 # as null.
-TRAFFIC = {"src": "01f5c870c1fb5cac", "precision": "fp8", "batch": 24,
-           "bytes_per_launch": {"ctx_conv1x1": 346.09e6, "ctx_lstm_gates_conv3x3": 1180.23e6,
-                                "ctx_conv3x3": 246.67e6, "ctx_head_conv3x3": 210.78e6,
-                                "rans_decode": 5.87e6, "lift_step": 31.07e6,
-                                "ctx_small": 173.86e6}}
+TRAFFIC = {"src": "d2aa2cffd8c1a643", "precision": "fp8", "batch": 24,
+           "bytes_per_launch": {"ctx_conv1x1": 346.34e6, "ctx_lstm_gates_conv3x3": 1172.32e6,
+                                "ctx_conv3x3": 247.02e6, "ctx_head_conv3x3": 210.81e6,
+                                "rans_decode": 5.88e6, "lift_step": 31.10e6,
+                                "ctx_small": 173.85e6}}
 
 
 def conv_src_hash() -> str:
