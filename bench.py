@@ -793,9 +793,9 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
 # the kernel classes of one decode step of this workload (batch 24, FP8),
 # from one ncu capture of `bench.py --nvtx-step` at full size (its summary
 # is kept under profiles/); valid only while the sources
-# of the convolution kernels hash to "src" (the capture's), else reported
+# of the captured kernels hash to "src" (the capture's), else reported
 # as null.
-TRAFFIC = {"src": "d2aa2cffd8c1a643", "precision": "fp8", "batch": 24,
+TRAFFIC = {"src": "0e026e92e4bc238c", "precision": "fp8", "batch": 24,
            "bytes_per_launch": {"ctx_conv1x1": 346.34e6, "ctx_lstm_gates_conv3x3": 1172.32e6,
                                 "ctx_conv3x3": 247.02e6, "ctx_head_conv3x3": 210.81e6,
                                 "rans_decode": 5.88e6, "lift_step": 31.10e6,
@@ -806,7 +806,10 @@ def conv_src_hash() -> str:
     import hashlib
     d = os.path.join(ROOT, "paper_2405_12631_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("ctx_tc.cu", "tc_ptx.cuh", "pw_internal.cuh"):
+    # every source of the captured kernels (convolutions, producers, coder,
+    # lifting, parse / dequantisation / colour)
+    for f in ("ctx_tc.cu", "tc_ptx.cuh", "pw_internal.cuh", "entropy.cu", "cdf_warp.cuh",
+              "lift.cu", "f32x2.cuh", "spec_math.cuh", "driver.cu"):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
