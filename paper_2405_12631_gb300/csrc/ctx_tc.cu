@@ -33,6 +33,7 @@
 #include "ctx_tc.h"
 #include "prof.h"
 #include "tc_ptx.cuh"
+#include "f32x2.cuh"
 
 namespace pw {
 
@@ -320,7 +321,8 @@ __global__ void __launch_bounds__(conv_threads(KS, EPI, NCTA), 1) k_conv_tc(cons
       s_bias[j] = a.bias[nb0 + j] * k;
       s_wsc[j] = (F8 ? a.w_scale[nb0 + j] : 1.f) * k;
       s_osc[j] = os;
-      if (HEADK) { s_wh[j] = a.wh[j]; s_wh[NCTA + j] = a.wh[NCTA + j]; }
+      // head weights interleaved: (w_mu[j], w_rho[j]) as one FP32 pair
+      if (HEADK) { s_wh[2 * j] = a.wh[j]; s_wh[2 * j + 1] = a.wh[NCTA + j]; }
     }
   }
   if (threadIdx.x == 0) {
@@ -713,7 +715,21 @@ __global__ void __launch_bounds__(conv_threads(KS, EPI, NCTA), 1) k_conv_tc(cons
       if (++acc == kAcc) { acc = 0; aphase ^= 1; }
       if (!work) continue;
 
-      if (F8 || (STORE && fold8)) {
+      if constexpr (STORE) {
+        // column pairs in packed FP32 (per element the same fmaf / add)
+        const uint64_t *wsc2 = reinterpret_cast<const uint64_t *>(s_wsc + col0);
+        const uint64_t *bia2 = reinterpret_cast<const uint64_t *>(s_bias + col0);
+        if (F8 || fold8) {
+#pragma unroll
+          for (int j = 0; j < NH / 2; ++j)
+            f2unpack(fma2(f2pack(v[2 * j], v[2 * j + 1]), wsc2[j], bia2[j]), v[2 * j],
+                     v[2 * j + 1]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < NH / 2; ++j)
+            f2unpack(add2(f2pack(v[2 * j], v[2 * j + 1]), bia2[j]), v[2 * j], v[2 * j + 1]);
+        }
+      } else if (F8) {
 #pragma unroll
         for (int j = 0; j < NH; ++j) v[j] = fmaf(v[j], s_wsc[col0 + j], s_bias[col0 + j]);
       } else {
@@ -760,8 +776,15 @@ __global__ void __launch_bounds__(conv_threads(KS, EPI, NCTA), 1) k_conv_tc(cons
             for (int e = 0; e < 8; ++e) v[8 * g + e] += rv[e];
           }
           if (a.act) {
+            // lrelu(x) = max(x, 0.01 x), the products in packed FP32
+            const uint64_t k01 = f2pack(0.01f, 0.01f);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) v[8 * g + e] = lrelu_f(v[8 * g + e]);
+            for (int e = 0; e < 8; e += 2) {
+              float lo, hi;
+              f2unpack(mul2(f2pack(v[8 * g + e], v[8 * g + e + 1]), k01), lo, hi);
+              v[8 * g + e] = fmaxf(v[8 * g + e], lo);
+              v[8 * g + e + 1] = fmaxf(v[8 * g + e + 1], hi);
+            }
           }
           if (a.out) store_bf16x8(a.out + off_out(g), v + 8 * g);
         }
@@ -816,6 +839,10 @@ __global__ void __launch_bounds__(conv_threads(KS, EPI, NCTA), 1) k_conv_tc(cons
         // partial sums of this half's columns (half 0 adds the head bias)
         float mu = half == 0 ? a.bh[0] : 0.f, rho = half == 0 ? a.bh[1] : 0.f;
         if (mine) {
+          // (mu, rho) as one packed FP32 pair: per element the same fmaf
+          // chain over the columns in order
+          const uint64_t *wh2 = reinterpret_cast<const uint64_t *>(s_wh) + col0;
+          uint64_t mr = f2pack(mu, rho);
 #pragma unroll
           for (int g = 0; g < NH / 8; ++g) {
             float rv[8];
@@ -823,10 +850,10 @@ __global__ void __launch_bounds__(conv_threads(KS, EPI, NCTA), 1) k_conv_tc(cons
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
               const float z = v[8 * g + e] + rv[e];
-              mu = fmaf(s_wh[col0 + 8 * g + e], z, mu);
-              rho = fmaf(s_wh[NCTA + col0 + 8 * g + e], z, rho);
+              mr = fma2(wh2[8 * g + e], f2pack(z, z), mr);
             }
           }
+          f2unpack(mr, mu, rho);
         }
         float2 *slot = s_part + (cur_acc * 4 + q) * 32 + lane;
         if (half == 1) {
