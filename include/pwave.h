@@ -169,7 +169,8 @@ int pw_encode_image(pw_ctx *ctx, const pw_model *m, const pw_image *in,
 int pw_decode_image(pw_ctx *ctx, const pw_model *m, const uint8_t *bs, size_t n,
                     pw_image *out);
 
-/* Batched encode: count images of identical size and channel count;
+/* Batched encode: count images of identical size and channel count (at most
+ * 65535 planes, count x channels, per call: PW_EUNSUPPORTED beyond);
  * bs[i], n[i] receive the streams (free each with pw_free). */
 int pw_encode_batch(pw_ctx *ctx, const pw_model *m, int count, const pw_image *in,
                     const pw_codec_opts *opts, uint8_t **bs, size_t *n);
@@ -186,7 +187,8 @@ int pw_encode_batch(pw_ctx *ctx, const pw_model *m, int count, const pw_image *i
  * is bit-identical to its single decode (logistic-mixture models decode it
  * as one batch per size). Page-locked host streams and host images (pinned
  * or registered memory) are copied to and from the device directly;
- * pageable ones go through the library's pinned staging. */
+ * pageable ones go through the library's pinned staging. At most 65535
+ * planes (count x channels) per call: PW_EUNSUPPORTED beyond. */
 int pw_decode_batch(pw_ctx *ctx, const pw_model *m, int count,
                     const uint8_t *const *bs, const size_t *n, int bs_on_device,
                     pw_image *out);

@@ -14,6 +14,10 @@
 
 namespace pw {
 
+// Planes (images x components) of one batch: every launch indexes them with
+// a 16-bit descriptor field or as the grid's z dimension.
+constexpr int64_t kMaxPlanes = 65535;
+
 static thread_local std::string g_last_error;
 void set_last_error(const std::string &s) { g_last_error = s; }
 
@@ -753,6 +757,10 @@ int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const s
   int s = read_header(bs[0], n[0], on_dev, h0);
   if (s) return s;
   if ((s = check_header_model(ctx, m, h0))) return s;
+  if ((int64_t)B * h0.ncomp > kMaxPlanes) {
+    set_last_error("too many planes in one batch");
+    return PW_EUNSUPPORTED;
+  }
   if (!on_dev && B > 1) {
     // host streams of different sizes: one ragged batch (the mixture model:
     // one batch per size)
@@ -1049,6 +1057,7 @@ static int encode_batch(pw_ctx *ctx, Model &m, int B, const pw_image *in,
       set_last_error("batch images differ in size or format"); return PW_EINVAL;
     }
   if (!g.lossless && !(o && o->q > 0.f)) { set_last_error("quantiser step must be > 0"); return PW_EINVAL; }
+  if ((int64_t)B * g.nc > kMaxPlanes) { set_last_error("too many planes in one batch"); return PW_EUNSUPPORTED; }
   Plan *pl;
   if ((s = get_plan(ctx, m, g, B, "enc", false, &pl))) return s;
   const int bps = g.bitdepth > 8 ? 2 : 1;

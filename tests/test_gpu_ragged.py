@@ -152,3 +152,18 @@ def test_decode_image_allocates_when_no_buffer(pw):
     assert np.array_equal(codec.decode_image_alloc(model, bs), img12)
     model.close()
     codec.close()
+
+
+def test_batch_plane_limit(pw):
+    """More than 65535 planes (images x components) in one call are refused
+    before any device work."""
+    codec = pw.Codec(0, "fp32")
+    model = codec.load_model(_blob(seed=11))
+    bs = codec.encode_image(model, S.rgb_natural(16, 16, seed=1), q=8.0)
+    n = 65535 // 3 + 1
+    with pytest.raises(pw.PwError) as e:
+        codec.decode_batch(model, [bs] * n)
+    assert e.value.code == pw.PW_EUNSUPPORTED
+    assert np.array_equal(codec.decode_batch(model, [bs] * 4)[3], codec.decode_image(model, bs))
+    model.close()
+    codec.close()
