@@ -177,11 +177,12 @@ int pw_encode_batch(pw_ctx *ctx, const pw_model *m, int count, const pw_image *i
 
 /* Batched decode of count streams of one model into out[0..count-1]
  * (out[i] sized like stream i). bs[i] are host pointers unless bs_on_device
- * is set, in which case they are device pointers (the streams then never
- * visit the host: headers are validated on the device) and must all have
- * the first stream's size. Host streams may differ in image size (not in
- * channels, levels, bit depth, colour mode, lossless / LL-model flags,
- * precision class or coder layout: PW_EINVAL): such a ragged batch is
+ * is set, in which case they are device pointers (the streams never visit
+ * the host: one kernel gathers their 64-byte headers, which the host reads
+ * to form the batch, and the parse kernel validates them again). The
+ * streams may differ in image size (not in channels, levels, bit depth,
+ * colour mode, lossless / LL-model flags, precision class or coder layout:
+ * PW_EINVAL): such a ragged batch is
  * decoded on a canvas of the largest padded size, every convolution, coder
  * pass and lifting step covering all streams in one launch, and each image
  * is bit-identical to its single decode (logistic-mixture models decode it

@@ -343,6 +343,17 @@ class Codec:
     def decode_image(self, model: Model, bs: bytes, shape=None, dtype=None) -> np.ndarray:
         return self.decode_batch(model, [bs], shape, dtype)[0]
 
+    def decode_ragged_device(self, model: Model, ptrs, lens, out_ptrs, shapes,
+                             bitdepth: int = 8):
+        """Decode device-resident streams of one format and different sizes
+        in one call: out_ptrs[i] is a packed device image of shapes[i]."""
+        B = len(ptrs)
+        ims = (pw_image * B)(*[pw_image(sh[1], sh[0], 1 if len(sh) == 2 else sh[2], bitdepth, 1,
+                                        0, o, 0) for o, sh in zip(out_ptrs, shapes)])
+        p = (C.c_void_p * B)(*ptrs)
+        n = (C.c_size_t * B)(*lens)
+        check(pw_decode_batch(self.ctx, model.handle, B, p, n, 1, ims))
+
     def decode_image_alloc(self, model: Model, bs: bytes) -> np.ndarray:
         """pw_decode_image with no output buffer: the library allocates the
         image (its size from the stream); copied out and released here."""

@@ -119,6 +119,9 @@ struct GopBufs {
 struct PlanCache {
   std::vector<std::unique_ptr<Plan>> plans;
   GopBufs gop;
+  // headers of device-resident stream batches (pointer table and headers)
+  DevBuf d_hdr;
+  HostBuf h_hdr;
 };
 
 Prof &prof_of(pw_ctx *ctx) { return *reinterpret_cast<Prof *>(ctx->prof); }
@@ -337,6 +340,36 @@ static int read_header(const uint8_t *bs, size_t n, int on_dev, StreamHeader &h)
     std::memcpy(&h, bs, sizeof(h));
   }
   if (std::memcmp(h.magic, "PWBS", 4) != 0 || h.version != 1) { set_last_error("not a PWBS stream"); return PW_ECORRUPT; }
+  return PW_OK;
+}
+
+// Headers of B device-resident streams: one gather kernel and one copy.
+static int read_headers_dev(pw_ctx *ctx, int B, const uint8_t *const *bs, const size_t *n,
+                            std::vector<StreamHeader> &hd) {
+  PlanCache &pc = *reinterpret_cast<PlanCache *>(ctx->plan_cache);
+  const size_t tab = (size_t)B * 16, bytes = tab + (size_t)B * 64;
+  int s;
+  if ((s = pc.d_hdr.ensure(bytes)) || (s = pc.h_hdr.ensure(bytes))) return s;
+  uint64_t *ht = static_cast<uint64_t *>(pc.h_hdr.p);
+  for (int b = 0; b < B; ++b) { ht[b] = (uint64_t)(uintptr_t)bs[b]; ht[B + b] = n[b]; }
+  uint8_t *dt = static_cast<uint8_t *>(pc.d_hdr.p);
+  PW_CUDA_TRY(cudaMemcpyAsync(dt, ht, tab, cudaMemcpyHostToDevice, ctx->stream));
+  launch_gather_headers(reinterpret_cast<const uint8_t *const *>(dt),
+                        reinterpret_cast<const uint64_t *>(dt + (size_t)B * 8), B, dt + tab,
+                        ctx->stream);
+  bump(ctx);
+  uint8_t *hh = static_cast<uint8_t *>(pc.h_hdr.p) + tab;
+  PW_CUDA_TRY(cudaMemcpyAsync(hh, dt + tab, (size_t)B * 64, cudaMemcpyDeviceToHost, ctx->stream));
+  PW_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  hd.resize(B);
+  for (int b = 0; b < B; ++b) {
+    if (!bs[b] || n[b] < sizeof(StreamHeader)) { set_last_error("stream too short"); return PW_ECORRUPT; }
+    std::memcpy(&hd[b], hh + (size_t)b * 64, sizeof(StreamHeader));
+    if (std::memcmp(hd[b].magic, "PWBS", 4) != 0 || hd[b].version != 1) {
+      set_last_error("not a PWBS stream");
+      return PW_ECORRUPT;
+    }
+  }
   return PW_OK;
 }
 
@@ -602,7 +635,7 @@ static int decode_ragged_dev(pw_ctx *ctx, Model &m, Plan &pl, const StreamHeader
 }
 
 static int decode_ragged(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const size_t *n,
-                         const std::vector<StreamHeader> &hd, pw_image *out) {
+                         const std::vector<StreamHeader> &hd, pw_image *out, int on_dev) {
   const StreamHeader &h0 = hd[0];
   std::vector<Geometry> gs(B);
   int Hc = 0, Wc = 0, s;
@@ -682,7 +715,7 @@ static int decode_ragged(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs,
   uint8_t *db = static_cast<uint8_t *>(pl->d_rag.p);
   pl->ws.ext = reinterpret_cast<const int2 *>(db + o_ext);
   std::vector<const uint8_t *> ptrs;
-  if ((s = stage_streams(ctx, *pl, B, bs, n, 0, ptrs))) return s;
+  if ((s = stage_streams(ctx, *pl, B, bs, n, on_dev, ptrs))) return s;
   fill_stream_table(*pl, ptrs.data(), n);
   double stream_bytes = 0;
   for (int b = 0; b < B; ++b) stream_bytes += (double)n[b];
@@ -754,24 +787,33 @@ int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const s
                  int on_dev, pw_image *out) {
   if (B < 1 || !bs || !n || !out) { set_last_error("bad arguments"); return PW_EINVAL; }
   StreamHeader h0;
-  int s = read_header(bs[0], n[0], on_dev, h0);
-  if (s) return s;
+  std::vector<StreamHeader> hd;
+  int s;
+  if (on_dev && B > 1) {
+    // every header of a device batch (one gather and one copy)
+    if ((s = read_headers_dev(ctx, B, bs, n, hd))) return s;
+    h0 = hd[0];
+  } else if ((s = read_header(bs[0], n[0], on_dev, h0))) {
+    return s;
+  }
   if ((s = check_header_model(ctx, m, h0))) return s;
   if ((int64_t)B * h0.ncomp > kMaxPlanes) {
     set_last_error("too many planes in one batch");
     return PW_EUNSUPPORTED;
   }
-  if (!on_dev && B > 1) {
-    // host streams of different sizes: one ragged batch (the mixture model:
-    // one batch per size)
-    std::vector<StreamHeader> hd(B);
-    hd[0] = h0;
-    bool ragged = false;
-    for (int b = 1; b < B; ++b) {
-      if ((s = read_header(bs[b], n[b], 0, hd[b]))) return s;
-      ragged = ragged || hd[b].width != h0.width || hd[b].height != h0.height;
+  if (B > 1) {
+    // streams of different sizes: one ragged batch (the mixture model: one
+    // batch per size)
+    if (!on_dev) {
+      hd.resize(B);
+      hd[0] = h0;
+      for (int b = 1; b < B; ++b)
+        if ((s = read_header(bs[b], n[b], 0, hd[b]))) return s;
     }
-    if (ragged && !m.mix) return decode_ragged(ctx, m, B, bs, n, hd, out);
+    bool ragged = false;
+    for (int b = 1; b < B; ++b)
+      ragged = ragged || hd[b].width != h0.width || hd[b].height != h0.height;
+    if (ragged && !m.mix) return decode_ragged(ctx, m, B, bs, n, hd, out, on_dev);
     if (ragged) {
       std::vector<char> done(B, 0);
       for (int b = 0; b < B; ++b) {
@@ -784,7 +826,7 @@ int decode_batch(pw_ctx *ctx, Model &m, int B, const uint8_t *const *bs, const s
             sp.push_back(bs[c]); sn.push_back(n[c]); so.push_back(out[c]);
             done[c] = 1;
           }
-        if ((s = decode_batch(ctx, m, (int)sp.size(), sp.data(), sn.data(), 0, so.data())))
+        if ((s = decode_batch(ctx, m, (int)sp.size(), sp.data(), sn.data(), on_dev, so.data())))
           return s;
       }
       return PW_OK;

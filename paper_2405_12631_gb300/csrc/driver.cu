@@ -116,6 +116,16 @@ __global__ void k_parse_ragged(const uint8_t *const *streams, const uint64_t *le
   }
 }
 
+// The 64-byte headers of device-resident streams (zeros past a stream's
+// end), one block per stream: read on the host to form a batch.
+__global__ void k_gather_headers(const uint8_t *const *ptrs, const uint64_t *lens, int B,
+                                 uint8_t *out) {
+  const int b = blockIdx.x, i = threadIdx.x;
+  if (b >= B || i >= 64) return;
+  const uint8_t *s = ptrs[b];
+  out[(int64_t)b * 64 + i] = (s && (uint64_t)i < lens[b]) ? s[i] : 0;
+}
+
 // Ragged batches: zero the 16-byte units of an activation buffer outside
 // each plane's extent. One block per canvas row (plane p, row y).
 __global__ void __launch_bounds__(128) k_zero_outside(uint4 *__restrict__ buf, int layout,
@@ -223,6 +233,10 @@ void launch_parse_ragged(const uint8_t *const *streams, const uint64_t *lens,
                          cudaStream_t st) {
   k_parse_ragged<<<grid_for(ntpl), 256, 0, st>>>(streams, lens, wh, ex, tpl, ntpl, out, deltas,
                                                  status);
+}
+void launch_gather_headers(const uint8_t *const *ptrs, const uint64_t *lens, int B, uint8_t *out,
+                           cudaStream_t st) {
+  if (B > 0) k_gather_headers<<<B, 64, 0, st>>>(ptrs, lens, B, out);
 }
 void launch_zero_outside(void *buf, int layout, int P, int H, int W, int NG, const int2 *ext,
                          int esh, cudaStream_t st) {

@@ -48,6 +48,9 @@ void launch_quant_all(const float *Yf, int32_t *Q, int64_t n, const SbTable &tb,
 void launch_parse_streams(const uint8_t *const *streams, const uint64_t *lens, int B,
                           const ParseExpect &ex, const TplDev *tpl, int nck, DecChunk *out,
                           float *deltas, uint32_t *status, cudaStream_t st);
+// out[b * 64 ..]: the first 64 bytes of device stream b (zeros past its end)
+void launch_gather_headers(const uint8_t *const *ptrs, const uint64_t *lens, int B, uint8_t *out,
+                           cudaStream_t st);
 // wh: the streams' expected (width, height), 2 per stream
 void launch_parse_ragged(const uint8_t *const *streams, const uint64_t *lens,
                          const uint32_t *wh, const ParseExpect &ex, const RagTpl *tpl,

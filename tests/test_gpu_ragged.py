@@ -167,3 +167,29 @@ def test_batch_plane_limit(pw):
     assert np.array_equal(codec.decode_batch(model, [bs] * 4)[3], codec.decode_image(model, bs))
     model.close()
     codec.close()
+
+
+@pytest.mark.parametrize("prec", ["fp8", "fp32"])
+def test_ragged_device_streams_and_images(pw, prec):
+    """Device-resident streams of different sizes into device images in one
+    call; equal sizes still take the plain batch path."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    codec = pw.Codec(0, prec)
+    model = codec.load_model(_blob(seed=12))
+    imgs = _imgs(True, seed=21)
+    streams = [codec.encode_image(model, im, q=8.0) for im in imgs]
+    d_bs = [torch.from_numpy(np.frombuffer(b, dtype=np.uint8).copy()).to(dev) for b in streams]
+    outs = [torch.zeros(im.shape, dtype=torch.uint8, device=dev) for im in imgs]
+    for _ in range(2):
+        codec.decode_ragged_device(model, [t.data_ptr() for t in d_bs], [len(b) for b in streams],
+                                   [o.data_ptr() for o in outs], [im.shape for im in imgs])
+        for o, bs in zip(outs, streams):
+            assert np.array_equal(o.cpu().numpy(), codec.decode_image(model, bs))
+    same = [streams[0], streams[5]]                    # both 64 x 96
+    o2 = torch.zeros((2,) + imgs[0].shape, dtype=torch.uint8, device=dev)
+    codec.decode_batch_device(model, [d_bs[0].data_ptr(), d_bs[5].data_ptr()],
+                              [len(b) for b in same], o2.data_ptr(), imgs[0].shape)
+    assert np.array_equal(o2[1].cpu().numpy(), codec.decode_image(model, streams[5]))
+    model.close()
+    codec.close()
