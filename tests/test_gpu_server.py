@@ -125,3 +125,32 @@ def test_server_forms_ragged_batches_of_similar_sizes(pw, prec):
     assert st["batches"] < len(streams)
     model.close()
     codec.close()
+
+
+def test_server_ragged_batch_with_a_corrupt_stream(pw):
+    """A corrupt stream inside a ragged batch fails only its own ticket: the
+    batch is re-decoded one request at a time and the others are exact."""
+    codec = pw.Codec(0, "fp8")
+    cfg = S.ModelConfig(levels=4, C=32, ll_mode=0)
+    model = codec.load_model(S.pack_blob(cfg, S.random_model(cfg, 14)))
+    sizes = [(112, 144), (120, 150), (104, 160), (116, 148), (110, 152)]
+    streams = [codec.encode_image(model, S.rgb_natural(h, w, seed=60 + i), q=8.0)
+               for i, (h, w) in enumerate(sizes)]
+    bad = bytearray(streams[2])
+    bad[len(bad) - 40] ^= 0x5A
+    streams[2] = bytes(bad)
+    srv = pw.Server(codec, model, hbm_budget=8 << 30, lanes=1, max_batch=5)
+    tickets = [srv.submit(bs) for bs in streams]
+    for i, t in enumerate(tickets):
+        if i == 2:
+            with pytest.raises(pw.PwError) as e:
+                srv.poll(t, timeout_ms=120000)
+            assert e.value.code == pw.PW_ECORRUPT
+        else:
+            assert np.array_equal(srv.poll(t, timeout_ms=120000),
+                                  codec.decode_image(model, streams[i]))
+    st = srv.stats()
+    srv.close()
+    assert st["failed"] == 1 and st["completed"] == len(streams) - 1
+    model.close()
+    codec.close()
