@@ -798,9 +798,17 @@ __global__ void __launch_bounds__(conv_threads(KS, EPI, NCTA), 1) k_conv_tc(cons
 #pragma unroll
           for (int g = 0; g < NH / 16; ++g) {
             float f[16];
+            if (fold8) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e)
-              f[e] = fold8 ? v[16 * g + e] : v[16 * g + e] * s_osc[col0 + 16 * g + e];
+              for (int e = 0; e < 16; ++e) f[e] = v[16 * g + e];
+            } else {
+              // the output scale in packed FP32 pairs (per element one fmul)
+              const uint64_t *osc2 = reinterpret_cast<const uint64_t *>(s_osc + col0 + 16 * g);
+#pragma unroll
+              for (int e = 0; e < 16; e += 2)
+                f2unpack(mul2(f2pack(v[16 * g + e], v[16 * g + e + 1]), osc2[e / 2]), f[e],
+                         f[e + 1]);
+            }
             store_fp8x16(a.out8 + off_out8(g), f);
           }
         }
