@@ -795,10 +795,10 @@ def lossless_run(pw, local, stream_ptr, n_img: int = 16, reps: int = 2):
 # is kept under profiles/); valid only while the sources
 # of the captured kernels hash to "src" (the capture's), else reported
 # as null.
-TRAFFIC = {"src": "7edc1765f6266875", "precision": "fp8", "batch": 24,
-           "bytes_per_launch": {"ctx_conv1x1": 346.07e6, "ctx_lstm_gates_conv3x3": 1172.71e6,
-                                "ctx_conv3x3": 246.47e6, "ctx_head_conv3x3": 210.75e6,
-                                "rans_decode": 5.9e6, "lift_step": 31.09e6,
+TRAFFIC = {"src": "593c57cf64cb08e5", "precision": "fp8", "batch": 24,
+           "bytes_per_launch": {"ctx_conv1x1": 346.65e6, "ctx_lstm_gates_conv3x3": 1175.22e6,
+                                "ctx_conv3x3": 246.54e6, "ctx_head_conv3x3": 210.79e6,
+                                "rans_decode": 5.87e6, "lift_step": 31.08e6,
                                 "ctx_small": 173.86e6}}
 
 
