@@ -193,3 +193,17 @@ def test_ragged_device_streams_and_images(pw, prec):
     assert np.array_equal(o2[1].cpu().numpy(), codec.decode_image(model, streams[5]))
     model.close()
     codec.close()
+
+
+def test_ragged_fast_coder_format(pw):
+    """Streams in the coder's fast format (one rANS state per 32 symbols,
+    6144-symbol chunks, recorded in their headers) form ragged batches too."""
+    codec = pw.Codec(0, "fp8")
+    model = codec.load_model(_blob(C=64, seed=13))
+    codec.set_lane_rule(5)
+    sizes = [(96, 128), (80, 144), (112, 96), (64, 64)]
+    streams = [codec.encode_image(model, im, q=8.0, chunk=6144)
+               for im in _imgs(True, sizes, seed=31)]
+    _check(codec, model, streams)
+    model.close()
+    codec.close()
